@@ -1,0 +1,261 @@
+"""Plain FP64 CPU oracle of the WRF-Fire fire step (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use this package; the product library never
+imports it, and it never imports the product library.  The arithmetic lives in
+``wrffire_oracle.c`` (plain C, -O2 -ffp-contract=off); this module only
+marshals numpy arrays.
+
+Inputs come in the neutral form produced by ``paper_1102_1343_gb300.synth``
+(fuel classes as dicts of Table 1 identifiers, ignitions as dicts), which holds
+no arithmetic of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wrffire_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# order of the 13 doubles of one fuel class (Table 1), as in wrffire_oracle.c
+FUEL_FIELDS = ("windrf", "weight", "weight_is_tf", "fgi", "fueldepthm", "savr",
+               "fuelmce", "fueldens", "st", "se", "cmbcnst", "fuelmc_g", "chaparral")
+# order of the 9 coefficients (eq. spread-WRF-Fire + T_f + heat factors)
+COEF_FIELDS = ("S0", "R0", "b", "c", "d", "e", "Tf", "Hs", "Hq")
+IGN_FIELDS = ("ax", "ay", "bx", "by", "t_start", "radius", "speed")
+STATUS_BOUNDARY = 1
+STATUS_NONFINITE = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nxa", C.c_int), ("nya", C.c_int), ("srx", C.c_int), ("sry", C.c_int),
+                ("dx_atm", C.c_double), ("dy_atm", C.c_double), ("eps", C.c_double),
+                ("band", C.c_int)]
+
+
+_D = C.POINTER(C.c_double)
+_U8 = C.POINTER(C.c_ubyte)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_rothermel_rate.restype = C.c_double
+            L.orc_rothermel_rate.argtypes = [_D, C.c_double, C.c_double, C.c_double]
+            L.orc_fuel_coefficients.restype = None
+            L.orc_fuel_coefficients.argtypes = [_D, C.c_double, _D]
+            L.orc_spread_rate.restype = C.c_double
+            L.orc_spread_rate.argtypes = [_D, C.c_double, C.c_double]
+            L.orc_node_coefficients.restype = None
+            L.orc_node_coefficients.argtypes = [_D, C.c_int, _U8, _D, C.c_long, _D]
+            L.orc_godunov.restype = C.c_double
+            L.orc_godunov.argtypes = [C.c_double, C.c_double]
+            L.orc_extend.restype = None
+            L.orc_extend.argtypes = [C.c_int, C.c_int, _D, _D]
+            L.orc_wind_at_nodes.restype = None
+            L.orc_wind_at_nodes.argtypes = [C.c_int] * 4 + [_D, _D, _D, _D]
+            L.orc_rhs.restype = None
+            L.orc_rhs.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                  _D, _D, _D, _D, _D, _D, _D, _D]
+            L.orc_cell_fuel_fraction.restype = C.c_double
+            L.orc_cell_fuel_fraction.argtypes = [_D, _D, C.c_double, C.c_double]
+            L.orc_ignite.restype = None
+            L.orc_ignite.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _D, C.c_int,
+                                     _U8, C.c_double, _D, _D]
+            L.orc_init_state.restype = None
+            L.orc_init_state.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                         _D, C.c_int, _U8, _D, _D, _D]
+            L.orc_step.restype = C.c_int
+            L.orc_step.argtypes = [C.POINTER(_Grid), _D, _D, _D, _D, _D, _D, _D, C.c_int, _U8,
+                                   C.c_double, C.c_double, _D, _D, _D, _D, _D]
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def fuel_vector(cls: dict) -> np.ndarray:
+    """One fuel class (dict of Table 1 identifiers) as the oracle's 13 doubles."""
+    return np.array([float(cls.get(k, 0.0)) for k in FUEL_FIELDS], dtype=np.float64)
+
+
+def fuel_table(classes) -> np.ndarray:
+    return np.ascontiguousarray(np.stack([fuel_vector(c) for c in classes]))
+
+
+def ignition_table(ignitions) -> np.ndarray:
+    if not ignitions:
+        return np.zeros((1, len(IGN_FIELDS)), dtype=np.float64)
+    return np.ascontiguousarray(
+        np.array([[float(g[k]) for k in IGN_FIELDS] for g in ignitions], dtype=np.float64))
+
+
+def rothermel_rate(cls: dict, U: float, tanphi: float, Mf: float | None = None) -> float:
+    v = fuel_vector(cls)
+    return lib().orc_rothermel_rate(_dp(v), -1.0 if Mf is None else float(Mf), float(U),
+                                    float(tanphi))
+
+
+def fuel_coefficients(cls: dict, Mf: float | None = None) -> np.ndarray:
+    v = fuel_vector(cls)
+    out = np.zeros(9)
+    lib().orc_fuel_coefficients(_dp(v), -1.0 if Mf is None else float(Mf), _dp(out))
+    return out
+
+
+def spread_rate(coef, U: float, tanphi: float) -> float:
+    co = _f64(coef)
+    return lib().orc_spread_rate(_dp(co), float(U), float(tanphi))
+
+
+def node_coefficients(classes, fuel, moisture=None) -> np.ndarray:
+    tab = fuel_table(classes)
+    fuel = np.ascontiguousarray(fuel, dtype=np.uint8)
+    mo = _f64(moisture)
+    out = np.zeros(fuel.shape + (9,))
+    lib().orc_node_coefficients(_dp(tab), len(classes), fuel.ctypes.data_as(_U8), _dp(mo),
+                                fuel.size, _dp(out))
+    return out
+
+
+def godunov(dm: float, dp: float) -> float:
+    return lib().orc_godunov(float(dm), float(dp))
+
+
+def extend(a) -> np.ndarray:
+    a = _f64(a)
+    ny, nx = a.shape
+    ext = np.zeros((ny + 2, nx + 2))
+    lib().orc_extend(nx, ny, _dp(a), _dp(ext))
+    return ext
+
+
+def wind_at_nodes(nxa, nya, srx, sry, u, v):
+    u, v = _f64(u), _f64(v)
+    assert u.shape == (nya, nxa + 1) and v.shape == (nya + 1, nxa)
+    un = np.zeros((nya * sry, nxa * srx))
+    vn = np.zeros_like(un)
+    lib().orc_wind_at_nodes(nxa, nya, srx, sry, _dp(u), _dp(v), _dp(un), _dp(vn))
+    return un, vn
+
+
+def rhs(psi, dx, dy, eps, coef, un, vn, dzdx, dzdy, mult=None) -> np.ndarray:
+    """Right-hand side of eq. (F-disc) for every node (ghosts extrapolated)."""
+    psi = _f64(psi)
+    ny, nx = psi.shape
+    ext = extend(psi)
+    co = _f64(coef)
+    if co.ndim == 1:
+        co = np.ascontiguousarray(np.broadcast_to(co, (ny, nx, 9)))
+    un, vn, dzdx, dzdy, mult = map(_f64, (un, vn, dzdx, dzdy, mult))
+    F = np.zeros_like(psi)
+    lib().orc_rhs(nx, ny, float(dx), float(dy), float(eps), _dp(ext), _dp(co), _dp(mult),
+                  _dp(un), _dp(vn), _dp(dzdx), _dp(dzdy), _dp(F))
+    return F
+
+
+def cell_fuel_fraction(psi3, tign3, t: float, Tf: float) -> float:
+    """Fuel fraction of the cell at the centre of a 3x3 node neighbourhood.
+
+    tign3 holds node ignition times; eq. (ti-comp) is applied here (t where
+    psi >= 0), as in the step."""
+    p = _f64(psi3).reshape(3, 3)
+    ti = _f64(tign3).reshape(3, 3)
+    th = np.ascontiguousarray(np.where(p < 0.0, ti, t))
+    p = np.ascontiguousarray(p)
+    return lib().orc_cell_fuel_fraction(_dp(p), _dp(th), float(t), float(Tf))
+
+
+def default_psi_far(nx, ny, dx, dy) -> float:
+    """Reading of "const > 0" for the initial level-set function: the domain diagonal."""
+    return float(np.hypot(nx * dx, ny * dy))
+
+
+class OracleFire:
+    """The oracle's fire model: state + the six-item step, FP64."""
+
+    def __init__(self, nxa, nya, sr, dx_atm, classes, fuel, dzdx, dzdy, ignitions=(),
+                 moisture=None, mult=None, eps=0.4, band=1, psi_far=None, dy_atm=None):
+        srx, sry = (sr, sr) if np.isscalar(sr) else sr
+        dy_atm = dx_atm if dy_atm is None else dy_atm
+        self.g = _Grid(nxa, nya, srx, sry, float(dx_atm), float(dy_atm), float(eps), int(band))
+        self.nx, self.ny = nxa * srx, nya * sry
+        self.dx, self.dy = dx_atm / srx, dy_atm / sry
+        fuel = np.ascontiguousarray(fuel, dtype=np.uint8)
+        assert fuel.shape == (self.ny, self.nx)
+        self.coef = node_coefficients(classes, fuel, moisture)
+        self.mult = _f64(mult)
+        self.dzdx, self.dzdy = _f64(dzdx), _f64(dzdy)
+        self.ign = ignition_table(list(ignitions))
+        self.n_ign = len(list(ignitions))
+        self.applied = np.zeros(max(1, self.n_ign), dtype=np.uint8)
+        self.psi_far = (default_psi_far(self.nx, self.ny, self.dx, self.dy)
+                        if psi_far is None else float(psi_far))
+        self.psi = np.zeros((self.ny, self.nx))
+        self.tign = np.zeros_like(self.psi)
+        self.frac = np.zeros_like(self.psi)
+        lib().orc_init_state(self.nx, self.ny, self.dx, self.dy, self.psi_far, _dp(self.ign),
+                             self.n_ign, self.applied.ctypes.data_as(_U8), _dp(self.psi),
+                             _dp(self.tign), _dp(self.frac))
+        self.t = 0.0
+        self.status = 0
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        args = dict(nxa=w.nxa, nya=w.nya, sr=(w.srx, w.sry), dx_atm=w.dx_atm, dy_atm=w.dy_atm,
+                    classes=w.classes, fuel=w.fuel, dzdx=w.dzdx, dzdy=w.dzdy,
+                    ignitions=w.ignitions, moisture=w.moisture, mult=w.mult, eps=w.eps,
+                    band=w.band)
+        args.update(kw)
+        return cls(**args)
+
+    def step(self, u, v, dt):
+        u, v = _f64(u), _f64(v)
+        g = self.g
+        assert u.shape == (g.nya, g.nxa + 1) and v.shape == (g.nya + 1, g.nxa)
+        hs = np.zeros((g.nya, g.nxa))
+        hl = np.zeros_like(hs)
+        st = lib().orc_step(C.byref(g), _dp(self.coef), _dp(self.mult), _dp(self.dzdx),
+                            _dp(self.dzdy), _dp(u), _dp(v), _dp(self.ign), self.n_ign,
+                            self.applied.ctypes.data_as(_U8), self.t, float(dt),
+                            _dp(self.psi), _dp(self.tign), _dp(self.frac), _dp(hs), _dp(hl))
+        self.t = self.t + float(dt)
+        self.status |= st
+        return hs, hl, st
+
+    def set_state(self, psi, tign, frac, t):
+        self.psi = _f64(psi).copy()
+        self.tign = _f64(tign).copy()
+        self.frac = _f64(frac).copy()
+        self.t = float(t)

@@ -1,0 +1,649 @@
+/*
+ * Plain FP64 CPU oracle of the WRF-Fire fire-model step
+ * (Mandel, Beezley & Kochanski, "Coupled atmosphere-wildland fire modeling
+ * with WRF-Fire version 3.3").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference that the CUDA path
+ * is checked against.  Only the tests, the smoke check of the entry module
+ * and the CPU-baseline leg of the benchmark may load it.  It shares no code,
+ * header, table or helper with the CUDA library, and it is deliberately
+ * slow: one loop per step of the method, in the paper's order, no blocking,
+ * no fusion.  Build with -O2 -ffp-contract=off so that every product and
+ * sum is rounded separately.
+ *
+ * Each function cites the section / equation / table it follows.  Where the
+ * paper is silent, garbled or ambiguous the reading taken is stated in the
+ * comment ("Reading:").
+ *
+ * Parity status: every function below is pinned by a CPU test against a
+ * closed form, an exactness claim of the paper, an invariant or a brute
+ * force computation, except where its comment says "parity unpinned".
+ *
+ * Layout conventions: fire mesh nodes (cell centres) are indexed (i, j),
+ * i = 0..nx-1 along x, j = 0..ny-1 along y, stored row-major a[j*nx + i];
+ * node (i, j) sits at ((i+1/2) dx, (j+1/2) dy).  The atmospheric mesh has
+ * nxa x nya cells; nx = srx*nxa, ny = sry*nya.  The wind is given on the
+ * staggered C-grid of Sect. "Domain, grids, and nodes": u[J*(nxa+1) + I]
+ * at x-faces (I*DX, (J+1/2)*DY), v[J*nxa + I] at y-faces ((I+1/2)*DX, J*DY).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Fuel properties (Table 1), one class = 13 doubles in this order.    */
+/* ------------------------------------------------------------------ */
+enum {
+    FC_WINDRF = 0,   /* a: wind reduction from 6.1 m to midflame height */
+    FC_WEIGHT,       /* w: fuel weight (s); or T_f directly, see next */
+    FC_WEIGHT_IS_TF, /* nonzero: FC_WEIGHT holds the burn time T_f (s) */
+    FC_FGI,          /* w_l: total fuel load (kg m^-2) */
+    FC_DEPTH,        /* delta_m: fuel depth (m) */
+    FC_SAVR,         /* sigma: surface-area-to-volume ratio (1/m) */
+    FC_MX,           /* M_x: moisture content of extinction */
+    FC_DENS,         /* rho_P: ovendry particle density (kg m^-3) */
+    FC_ST,           /* S_T: total mineral content */
+    FC_SE,           /* S_E: effective mineral content */
+    FC_H,            /* h: heat content of dry fuel (J/kg) */
+    FC_MF,           /* M_f: fuel particle moisture content */
+    FC_CHAPARRAL,    /* nonzero: chaparral rule, eq. (chapparal) */
+    FC_N
+};
+
+/* Coefficient vector of eq. (spread-WRF-Fire) plus the burn time and the
+ * two heat factors of eqs. (sensible-heat-flux), (latent-heat-flux). */
+enum { CO_S0 = 0, CO_R0, CO_B, CO_C, CO_D, CO_E, CO_TF, CO_HS, CO_HQ, CO_N };
+
+/* Unit conversions to the BTU-lb-ft-min system of Table 2. */
+#define M_PER_FT   0.3048
+#define KG_PER_LB  0.45359237
+#define J_PER_BTU  1055.05585262
+#define LATENT_L   2.5e6          /* L, J/kg, Sect. "Fuel burned and heat released" */
+#define WIND_MAX   30.0           /* CAWFE wind limit, caption of Table 2 */
+
+
+/* Rothermel quantities that do not depend on wind or slope (Table 2).
+ * Returns R0 in ft/min and the wind/slope factors' ingredients.
+ * Reading (garbles in Table 2):
+ *   - Gamma_max = sigma^1.5/(495 + 0.0594 sigma^1.5): Rothermel's Eq. (36)
+ *     constant is 0.0594; the table prints 0.594.
+ *   - Q_ig = 250 + 1116 M_f: Rothermel's Eq. (12); the table's "250 beta"
+ *     is a typesetting slip.
+ *   - phi_W = C U_a^B (beta/beta_op)^(-E) with B = 0.02526 sigma^0.54 and
+ *     beta_op = 3.348 sigma^(-0.8189) (Rothermel Eqs. 47-49, 37); the table
+ *     leaves B and beta_op undefined.
+ *   - eta_M is clamped to [0, 1] (zero when M_f >= M_x): silent in the paper.
+ *   - a class with no fuel (w_l <= 0) does not spread: silent in the paper. */
+typedef struct {
+    double R0_ftmin, B, C, E, beta, beta_op;
+    int nofuel;
+} orc_rothermel_parts;
+
+static orc_rothermel_parts rothermel_parts(const double *fc, double Mf)
+{
+    orc_rothermel_parts p;
+    memset(&p, 0, sizeof p);
+    if (!(fc[FC_FGI] > 0.0)) { p.nofuel = 1; return p; }
+    /* metric -> English (caption of Table 2) */
+    double sigma  = fc[FC_SAVR] * M_PER_FT;                       /* 1/ft */
+    double wl     = fc[FC_FGI] * (M_PER_FT * M_PER_FT) / KG_PER_LB; /* lb/ft^2 */
+    double depth  = fc[FC_DEPTH] / M_PER_FT;                      /* ft */
+    double rho_p  = fc[FC_DENS] * (M_PER_FT * M_PER_FT * M_PER_FT) / KG_PER_LB; /* lb/ft^3 */
+    double h      = fc[FC_H] * KG_PER_LB / J_PER_BTU;             /* BTU/lb */
+    double Mx     = fc[FC_MX];
+    double ST     = fc[FC_ST];
+    double SE     = fc[FC_SE];
+
+    double w0     = wl / (1.0 + Mf);                 /* net of moisture (CAWFE) */
+    double rho_b  = w0 / depth;                      /* Eq. (40) */
+    double beta   = rho_b / rho_p;                   /* Eq. (31) */
+    double beta_op = 3.348 * pow(sigma, -0.8189);    /* Eq. (37) */
+    double A      = 1.0 / (4.77 * pow(sigma, 0.1) - 7.27);          /* Eq. (39) */
+    double s15    = pow(sigma, 1.5);
+    double Gmax   = s15 / (495.0 + 0.0594 * s15);    /* Eq. (36), reading */
+    double ratio  = beta / beta_op;
+    double Gamma  = Gmax * pow(ratio, A) * exp(A * (1.0 - ratio));  /* Eq. (36) */
+    double wn     = w0 / (1.0 + ST);                 /* Eq. (24) as printed */
+    double rm     = Mf / Mx;
+    double etaM   = 1.0 - 2.59 * rm + 5.11 * rm * rm - 3.52 * rm * rm * rm; /* Eq. (29) */
+    if (rm >= 1.0 || etaM < 0.0) etaM = 0.0;
+    if (etaM > 1.0) etaM = 1.0;
+    double etaS   = 0.174 * pow(SE, -0.19);          /* Eq. (30) */
+    double IR     = Gamma * wn * h * etaM * etaS;    /* Eq. (52) */
+    double xi     = exp((0.792 + 0.681 * sqrt(sigma)) * (beta + 0.1))
+                    / (192.0 + 0.2595 * sigma);      /* Eq. (42) */
+    double epsh   = exp(-138.0 / sigma);             /* Eq. (14) */
+    double Qig    = 250.0 + 1116.0 * Mf;             /* Eq. (12), reading */
+    p.R0_ftmin    = IR * xi / (rho_b * epsh * Qig);  /* Eq. (52) */
+    p.C           = 7.47 * exp(-0.133 * pow(sigma, 0.55));  /* Eq. (48) */
+    p.B           = 0.02526 * pow(sigma, 0.54);      /* Rothermel Eq. (49) */
+    p.E           = 0.715 * exp(-3.59e-4 * sigma);   /* Eq. (50) */
+    p.beta        = beta;
+    p.beta_op     = beta_op;
+    return p;
+}
+
+/* Direct evaluation of eq. (spread): S = R0 (1 + phi_W + phi_S), in m/s,
+ * with the CAWFE limits of the caption of Table 2 (0 <= U <= 30 m/s,
+ * tan(phi) >= 0) and the chaparral rule eq. (chapparal).  Mf < 0 means
+ * "use the class moisture". */
+double orc_rothermel_rate(const double *fc, double Mf, double U, double tanphi)
+{
+    if (Mf < 0.0) Mf = fc[FC_MF];
+    if (fc[FC_CHAPARRAL] != 0.0) {
+        double s = 1.2974 * U;
+        if (s < 0.03333) s = 0.03333;
+        if (s > 6.0) s = 6.0;
+        return s;
+    }
+    orc_rothermel_parts p = rothermel_parts(fc, Mf);
+    if (p.nofuel) return 0.0;
+    double Ul = U;
+    if (Ul < 0.0) Ul = 0.0;
+    if (Ul > WIND_MAX) Ul = WIND_MAX;
+    double tp = tanphi > 0.0 ? tanphi : 0.0;
+    double Ua = fc[FC_WINDRF] * Ul * (60.0 / M_PER_FT);  /* U_a = a U, ft/min */
+    double phiW = p.C * pow(Ua, p.B) * pow(p.beta / p.beta_op, -p.E);  /* Eq. (47) */
+    double phiS = 5.275 * pow(p.beta, -0.3) * tp * tp;   /* Eq. (51) */
+    return p.R0_ftmin * (1.0 + phiW + phiS) * (M_PER_FT / 60.0);
+}
+
+/* Coefficients of eq. (spread-WRF-Fire), SI units (U in m/s, S in m/s),
+ * the burn time T_f (Sect. "Fuel burned and heat released") and the heat
+ * factors H_s = w_l h/(1+M_f) and H_q = (M_f+0.56)/(1+M_f) L w_l of
+ * eqs. (sensible-heat-flux), (latent-heat-flux).
+ * Reading of the coefficient mapping (the paper gives the form only):
+ *   R0 := R0 [m/s], b := B, c := R0 C (196.85 a)^B (beta/beta_op)^(-E),
+ *   d := R0 5.275 beta^(-0.3), e := 30 m/s, S0 := 0;
+ *   chaparral: S0 = 0.03333, R0 = 0, b = 1, c = 1.2974, d = 0, e = 6/1.2974.
+ * Mf < 0 means "use the class moisture". */
+void orc_fuel_coefficients(const double *fc, double Mf, double *co)
+{
+    if (Mf < 0.0) Mf = fc[FC_MF];
+    for (int k = 0; k < CO_N; ++k) co[k] = 0.0;
+    /* burn time: 0.6^((t-ti)/600 * 1000/w) = exp(-(t-ti)/T_f) */
+    if (fc[FC_WEIGHT_IS_TF] != 0.0) co[CO_TF] = fc[FC_WEIGHT];
+    else co[CO_TF] = -600.0 * fc[FC_WEIGHT] / (1000.0 * log(0.6));
+    co[CO_HS] = fc[FC_FGI] * fc[FC_H] / (1.0 + Mf);
+    co[CO_HQ] = (Mf + 0.56) / (1.0 + Mf) * LATENT_L * fc[FC_FGI];
+    if (fc[FC_CHAPARRAL] != 0.0) {
+        co[CO_S0] = 0.03333;
+        co[CO_R0] = 0.0;
+        co[CO_B]  = 1.0;
+        co[CO_C]  = 1.2974;
+        co[CO_D]  = 0.0;
+        co[CO_E]  = 6.0 / 1.2974;
+        return;
+    }
+    orc_rothermel_parts p = rothermel_parts(fc, Mf);
+    co[CO_E] = WIND_MAX;
+    co[CO_B] = 1.0;
+    if (p.nofuel) return;
+    double R0 = p.R0_ftmin * (M_PER_FT / 60.0);
+    co[CO_R0] = R0;
+    co[CO_B]  = p.B;
+    co[CO_C]  = R0 * p.C * pow(fc[FC_WINDRF] * (60.0 / M_PER_FT), p.B)
+                   * pow(p.beta / p.beta_op, -p.E);
+    co[CO_D]  = R0 * 5.275 * pow(p.beta, -0.3);
+}
+
+/* Eq. (spread-WRF-Fire): S = max{S0, R0 + c min{e, max{0,U}}^b + d max{0,tan phi}^2}. */
+double orc_spread_rate(const double *co, double U, double tanphi)
+{
+    double Up = U > 0.0 ? U : 0.0;
+    double Ue = Up < co[CO_E] ? Up : co[CO_E];
+    double tp = tanphi > 0.0 ? tanphi : 0.0;
+    double s = co[CO_R0] + co[CO_C] * pow(Ue, co[CO_B]) + co[CO_D] * tp * tp;
+    return s > co[CO_S0] ? s : co[CO_S0];
+}
+
+/* Per-node coefficients: class table [ncls][13], class map, optional per-node
+ * moisture (NULL: the class moisture).  Output [n][9]. */
+void orc_node_coefficients(const double *classes, int ncls, const unsigned char *fuel,
+                           const double *moisture, long n, double *co)
+{
+    for (long k = 0; k < n; ++k) {
+        int c = fuel[k];
+        if (c >= ncls) c = ncls - 1;
+        orc_fuel_coefficients(classes + (long)c * FC_N,
+                              moisture ? moisture[k] : -1.0, co + k * CO_N);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Level-set core (Sect. "Fire propagation by the level-set method").  */
+/* ------------------------------------------------------------------ */
+
+/* Godunov upwind selection, eq. (Godunov), cases tested in the printed
+ * order.  Reading: on a tie |D-| = |D+| in the last case, D- is taken
+ * (both printed branches give the same magnitude). */
+double orc_godunov(double dm, double dp)
+{
+    if (dm <= 0.0 && dp <= 0.0) return dp;
+    if (dm >= 0.0 && dp >= 0.0) return dm;
+    if (dm <= 0.0 && dp >= 0.0) return 0.0;
+    if (fabs(dm) >= fabs(dp)) return dm;
+    return dp;
+}
+
+/* One extrapolated ghost value (Sect. level set, boundary): the node beyond
+ * the boundary gets max{p0 + (p0 - p1), p0, p1}, p0 the last node, p1 the
+ * one before it. */
+static double ghost(double p0, double p1)
+{
+    double g = p0 + (p0 - p1);
+    if (p0 > g) g = p0;
+    if (p1 > g) g = p1;
+    return g;
+}
+
+/* Extend a field by one layer of ghost nodes.  ext is (nx+2) x (ny+2),
+ * ext[(j+1)*(nx+2) + (i+1)] = a[j*nx + i].  Reading of "similarly in the
+ * other cases": the x direction first (ghost columns for every real row),
+ * then the y direction over the extended rows (this fills the corners).
+ * Requires nx >= 2 and ny >= 2. */
+void orc_extend(int nx, int ny, const double *a, double *ext)
+{
+    int W = nx + 2;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            ext[(j + 1) * W + (i + 1)] = a[j * nx + i];
+    for (int j = 0; j < ny; ++j) {
+        double *row = ext + (j + 1) * W;
+        row[0]      = ghost(row[1], row[2]);
+        row[nx + 1] = ghost(row[nx], row[nx - 1]);
+    }
+    for (int i = 0; i < W; ++i) {
+        ext[i]                = ghost(ext[W + i], ext[2 * W + i]);
+        ext[(ny + 1) * W + i] = ghost(ext[ny * W + i], ext[(ny - 1) * W + i]);
+    }
+}
+
+/* Horizontal bilinear interpolation of the staggered wind to the fire-mesh
+ * nodes (Sect. "Coupling", last paragraph of the wind interpolation).
+ * Reading: beyond the outermost u-rows (y) and v-columns (x) the value of
+ * the edge row/column is used (constant extension). */
+static void interp_weights(double f, int n, int *k0, int *k1, double *w)
+{
+    /* f is a coordinate in index units on points 0..n-1 */
+    if (f < 0.0) f = 0.0;
+    if (f > (double)(n - 1)) f = (double)(n - 1);
+    int k = (int)floor(f);
+    if (k > n - 2) k = n - 2;
+    if (k < 0) k = 0;
+    if (n == 1) { *k0 = 0; *k1 = 0; *w = 0.0; return; }
+    *k0 = k;
+    *k1 = k + 1;
+    *w = f - (double)k;
+}
+
+void orc_wind_at_nodes(int nxa, int nya, int srx, int sry,
+                       const double *u, const double *v, double *un, double *vn)
+{
+    int nx = nxa * srx, ny = nya * sry;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            double xa = ((double)i + 0.5) / (double)srx;  /* atmos index units */
+            double ya = ((double)j + 0.5) / (double)sry;
+            int i0, i1, j0, j1;
+            double wx, wy;
+            /* u: points at (I, J+1/2), I = 0..nxa, J = 0..nya-1 */
+            interp_weights(xa, nxa + 1, &i0, &i1, &wx);
+            interp_weights(ya - 0.5, nya, &j0, &j1, &wy);
+            const double *ur0 = u + (long)j0 * (nxa + 1);
+            const double *ur1 = u + (long)j1 * (nxa + 1);
+            un[(long)j * nx + i] = (1.0 - wy) * ((1.0 - wx) * ur0[i0] + wx * ur0[i1])
+                                 + wy * ((1.0 - wx) * ur1[i0] + wx * ur1[i1]);
+            /* v: points at (I+1/2, J), I = 0..nxa-1, J = 0..nya */
+            interp_weights(xa - 0.5, nxa, &i0, &i1, &wx);
+            interp_weights(ya, nya + 1, &j0, &j1, &wy);
+            const double *vr0 = v + (long)j0 * nxa;
+            const double *vr1 = v + (long)j1 * nxa;
+            vn[(long)j * nx + i] = (1.0 - wy) * ((1.0 - wx) * vr0[i0] + wx * vr0[i1])
+                                 + wy * ((1.0 - wx) * vr1[i0] + wx * vr1[i1]);
+        }
+    }
+}
+
+/* Right-hand side of eq. (F-disc) at every node, from the ghost-extended
+ * level-set function ext ((nx+2) x (ny+2)).
+ *   - one-sided differences D+-x, D+-y and the Godunov selection eq. (Godunov);
+ *   - the normal n from central differences (paragraph after eq. Godunov),
+ *     n = 0 where the central gradient vanishes (reading: silent);
+ *   - U = wind . n, tan(phi) = grad z . n, S from eq. (spread-WRF-Fire),
+ *     times the optional per-node spread multiplier m;
+ *   - the scaled Laplacian D+x - D-x + D+y - D-y;
+ *   - Reading of the viscosity units: F = -S |grad psi| + eps S Lap~(psi).
+ *     The scaled Laplacian is dimensionless, so the speed S makes the term a
+ *     speed, consistent with calling eps "scale-free". */
+void orc_rhs(int nx, int ny, double dx, double dy, double eps,
+             const double *ext, const double *co, const double *mult,
+             const double *un, const double *vn,
+             const double *dzdx, const double *dzdy, double *F)
+{
+    int W = nx + 2;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            const double *e = ext + (j + 1) * W + (i + 1);
+            double p = e[0], pl = e[-1], pr = e[1], pd = e[-W], pu = e[W];
+            double dxm = (p - pl) / dx, dxp = (pr - p) / dx;
+            double dym = (p - pd) / dy, dyp = (pu - p) / dy;
+            double gx = orc_godunov(dxm, dxp);
+            double gy = orc_godunov(dym, dyp);
+            double cx = (pr - pl) / (2.0 * dx);
+            double cy = (pu - pd) / (2.0 * dy);
+            double cn = sqrt(cx * cx + cy * cy);
+            double nxv = 0.0, nyv = 0.0;
+            if (cn > 0.0) { nxv = cx / cn; nyv = cy / cn; }
+            double U = un[k] * nxv + vn[k] * nyv;
+            double tanphi = dzdx[k] * nxv + dzdy[k] * nyv;
+            double S = orc_spread_rate(co + k * CO_N, U, tanphi);
+            if (mult) S = mult[k] * S;
+            double lap = (dxp - dxm) + (dyp - dym);
+            double grad = sqrt(gx * gx + gy * gy);
+            F[k] = -S * grad + eps * S * lap;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Ignition (Sect. "Ignition").                                        */
+/* ------------------------------------------------------------------ */
+
+/* One ignition segment: 7 doubles {ax, ay, bx, by, t_g, r_g, S_g}.
+ * S_g > 0: the fire grows from the segment at S_g until r_g is reached,
+ * eqs. (ignition-lfn), (ignition-min); active at the start of every step
+ * with t_g <= t <= t_g + r_g/S_g; newly ignited nodes get the arrival time
+ * t_g + dist/S_g.
+ * S_g <= 0: reading for an instantaneous ignition of radius r_g (the earlier
+ * mechanism the section describes): applied once, at the first step start
+ * t >= t_g (or at initialisation when t_g <= 0), with ignition time t_g. */
+enum { IG_AX = 0, IG_AY, IG_BX, IG_BY, IG_TG, IG_RG, IG_SG, IG_N };
+
+static double dist_to_segment(double x, double y, const double *g)
+{
+    double dxs = g[IG_BX] - g[IG_AX], dys = g[IG_BY] - g[IG_AY];
+    double qx = x - g[IG_AX], qy = y - g[IG_AY];
+    double L2 = dxs * dxs + dys * dys;
+    double s = 0.0;
+    if (L2 > 0.0) {
+        s = (qx * dxs + qy * dys) / L2;
+        if (s < 0.0) s = 0.0;
+        if (s > 1.0) s = 1.0;
+    }
+    double rx = qx - s * dxs, ry = qy - s * dys;
+    return sqrt(rx * rx + ry * ry);
+}
+
+/* Apply one segment at step start t: psi := min(psi, psi_g), eq.
+ * (ignition-min); t_i of newly ignited nodes (psi > 0 >= psi_g, t_i not yet
+ * set) := arrival time.  Reading: a node's ignition time is set once, at its
+ * first ignition, and never overwritten. */
+static void apply_segment(int nx, int ny, double dx, double dy, const double *g,
+                          double t, double *psi, double *tign)
+{
+    int instant = !(g[IG_SG] > 0.0);
+    double rho = instant ? g[IG_RG] : g[IG_SG] * (t - g[IG_TG]);
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            double x = ((double)i + 0.5) * dx, y = ((double)j + 0.5) * dy;
+            double d = dist_to_segment(x, y, g);
+            double pg = d - rho;
+            if (psi[k] > 0.0 && pg <= 0.0 && isinf(tign[k]))
+                tign[k] = instant ? g[IG_TG] : g[IG_TG] + d / g[IG_SG];
+            if (pg < psi[k]) psi[k] = pg;
+        }
+    }
+}
+
+/* Step 1 of the fire step (Sect. "Coupling", list item 1): apply every
+ * active ignition in list order.  applied[] records instantaneous ignitions
+ * already done. */
+void orc_ignite(int nx, int ny, double dx, double dy, const double *ign, int n_ign,
+                unsigned char *applied, double t, double *psi, double *tign)
+{
+    for (int q = 0; q < n_ign; ++q) {
+        const double *g = ign + q * IG_N;
+        if (!(g[IG_SG] > 0.0)) {
+            if (!applied[q] && g[IG_TG] <= t) {
+                apply_segment(nx, ny, dx, dy, g, t, psi, tign);
+                applied[q] = 1;
+            }
+        } else if (g[IG_TG] <= t && t <= g[IG_TG] + g[IG_RG] / g[IG_SG]) {
+            apply_segment(nx, ny, dx, dy, g, t, psi, tign);
+        }
+    }
+}
+
+/* Initial state (Sect. "Ignition", first paragraph): psi = psi_far > 0,
+ * no ignition time, fuel fraction 1; then the instantaneous ignitions with
+ * t_g <= 0 (reading: the model starts at t = 0). */
+void orc_init_state(int nx, int ny, double dx, double dy, double psi_far,
+                    const double *ign, int n_ign, unsigned char *applied,
+                    double *psi, double *tign, double *frac)
+{
+    long n = (long)nx * ny;
+    for (long k = 0; k < n; ++k) { psi[k] = psi_far; tign[k] = INFINITY; frac[k] = 1.0; }
+    for (int q = 0; q < n_ign; ++q) applied[q] = 0;
+    for (int q = 0; q < n_ign; ++q) {
+        const double *g = ign + q * IG_N;
+        if (!(g[IG_SG] > 0.0) && g[IG_TG] <= 0.0) {
+            apply_segment(nx, ny, dx, dy, g, 0.0, psi, tign);
+            applied[q] = 1;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Fuel fraction (Sect. "Computation of the fuel fraction").           */
+/* ------------------------------------------------------------------ */
+
+/* Burned fraction of one subcell from its 4 corner values, eqs.
+ * (approx-area) and (approx-fraction).
+ * Reading of the sign in eq. (approx-fraction): the exponent is
+ * -(1/4) sum (t - t_i(x_k))/T_f, as in eqs. (fuel) and (fuel_left); the
+ * printed t_i - t would make the burned fraction negative.
+ * Reading: beta = 0 when all four corner values vanish (then every corner
+ * has t_i = t, so the burned fraction is 0 for any beta). */
+static double subcell_burned(const double ps[4], const double ts[4], double t, double Tf)
+{
+    double sp = 0.0, sa = 0.0;
+    for (int k = 0; k < 4; ++k) { sp += ps[k]; sa += fabs(ps[k]); }
+    double beta = sa > 0.0 ? 0.5 * (1.0 - sp / sa) : 0.0;
+    double s = 0.0;
+    for (int k = 0; k < 4; ++k) s += t - ts[k];
+    return beta * (1.0 - exp(-0.25 * s / Tf));
+}
+
+/* Fuel fraction of one cell from the 3x3 node neighbourhood of its centre
+ * node.  p and th are 3x3 arrays (row-major, [1][1] is the cell's node) of
+ * the level-set function and of the compatible ignition time (t_i where
+ * psi < 0, t elsewhere: eq. (ti-comp)).
+ * The cell is split into 4 subcells (eq. fuel_left_subcells, Fig. subcells):
+ * each has the cell centre, two edge midpoints and one cell corner as
+ * vertices.  psi and t_i are interpolated bilinearly between the node
+ * centres: an edge midpoint is the mean of 2 nodes, a cell corner the mean
+ * of 4.  Where the interpolated psi >= 0 the interpolated t_i is replaced by
+ * t (eq. ti-comp applied at the vertices).
+ * Reading: the cell fraction burned is the mean of the 4 subcell fractions
+ * (the subcells have a quarter of the cell's area). */
+double orc_cell_fuel_fraction(const double *p, const double *th, double t, double Tf)
+{
+    double ps[3][3], ts[3][3];  /* [b][a]: sample at (a-1)/2, (b-1)/2 cell widths */
+    for (int b = 0; b < 3; ++b) {
+        for (int a = 0; a < 3; ++a) {
+            /* nodes that bracket this sample point */
+            int ia0 = a == 0 ? 0 : 1, ia1 = a == 2 ? 2 : 1;
+            int ib0 = b == 0 ? 0 : 1, ib1 = b == 2 ? 2 : 1;
+            double pv, tv;
+            if (ia0 == ia1 && ib0 == ib1) {
+                pv = p[4];
+                tv = th[4];
+            } else if (ib0 == ib1) {
+                pv = 0.5 * (p[ib0 * 3 + ia0] + p[ib0 * 3 + ia1]);
+                tv = 0.5 * (th[ib0 * 3 + ia0] + th[ib0 * 3 + ia1]);
+            } else if (ia0 == ia1) {
+                pv = 0.5 * (p[ib0 * 3 + ia0] + p[ib1 * 3 + ia0]);
+                tv = 0.5 * (th[ib0 * 3 + ia0] + th[ib1 * 3 + ia0]);
+            } else {
+                pv = 0.25 * (p[ib0 * 3 + ia0] + p[ib0 * 3 + ia1]
+                           + p[ib1 * 3 + ia0] + p[ib1 * 3 + ia1]);
+                tv = 0.25 * (th[ib0 * 3 + ia0] + th[ib0 * 3 + ia1]
+                           + th[ib1 * 3 + ia0] + th[ib1 * 3 + ia1]);
+            }
+            if (pv >= 0.0) tv = t;
+            ps[b][a] = pv;
+            ts[b][a] = tv;
+        }
+    }
+    double burned = 0.0;
+    for (int sb = 0; sb < 2; ++sb) {
+        for (int sa = 0; sa < 2; ++sa) {
+            /* subcell with the cell centre (1,1) and the corner (2*sa, 2*sb) */
+            int ax = 2 * sa, by = 2 * sb;
+            double pc[4] = { ps[1][1], ps[1][ax], ps[by][1], ps[by][ax] };
+            double tc[4] = { ts[1][1], ts[1][ax], ts[by][1], ts[by][ax] };
+            burned += subcell_burned(pc, tc, t, Tf);
+        }
+    }
+    return 1.0 - 0.25 * burned;
+}
+
+/* ------------------------------------------------------------------ */
+/* The fire step (Sect. "Coupling", the six-item list).                */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int nxa, nya, srx, sry;
+    double dx_atm, dy_atm;
+    double eps;        /* artificial viscosity, 0.4 in the paper */
+    int band;          /* width of the boundary ring checked for fire */
+} orc_grid;
+
+enum { ORC_BOUNDARY = 1, ORC_NONFINITE = 2 };
+
+/* One fire step from time t to t + dt.  State (psi, tign, frac) is updated
+ * in place; heat_s, heat_l ([nya][nxa]) receive the averaged sensible and
+ * latent heat flux densities (W m^-2).  Returns status bits.
+ *   1. ignitions active at t                 (Sect. Ignition)
+ *   2. Heun stages of eq. (Heun) with eq. (F-disc); wind fixed in the step;
+ *      ghosts re-extrapolated for each stage
+ *   3. ignition time by eq. (set-ignition-time) where psi crossed from > 0
+ *      to <= 0; fire in the boundary ring sets ORC_BOUNDARY
+ *   4. fuel fraction at t + dt (Sect. fuel fraction)
+ *   5. heat flux densities per fire cell, eqs. (sensible-/latent-heat-flux)
+ *   6. average over the fire cells of each atmospheric cell
+ * co: per-node coefficients [n][9]; mult: per-node multiplier or NULL. */
+int orc_step(const orc_grid *g, const double *co, const double *mult,
+             const double *dzdx, const double *dzdy,
+             const double *u, const double *v,
+             const double *ign, int n_ign, unsigned char *applied,
+             double t, double dt,
+             double *psi, double *tign, double *frac,
+             double *heat_s, double *heat_l)
+{
+    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
+    long n = (long)nx * ny;
+    long ne = (long)(nx + 2) * (ny + 2);
+    double dx = g->dx_atm / g->srx, dy = g->dy_atm / g->sry;
+    int status = 0;
+
+    double *un = malloc(sizeof(double) * n), *vn = malloc(sizeof(double) * n);
+    double *ext = malloc(sizeof(double) * ne);
+    double *F1 = malloc(sizeof(double) * n), *F2 = malloc(sizeof(double) * n);
+    double *ps = malloc(sizeof(double) * n), *pn = malloc(sizeof(double) * n);
+    double *th = malloc(sizeof(double) * n), *fnew = malloc(sizeof(double) * n);
+    double *ext_t = malloc(sizeof(double) * ne);
+
+    /* 1. ignition */
+    orc_ignite(nx, ny, dx, dy, ign, n_ign, applied, t, psi, tign);
+
+    /* wind at the fire nodes; a non-finite wind is reported (the clamps of
+     * eq. spread-WRF-Fire would otherwise read it as calm) */
+    orc_wind_at_nodes(g->nxa, g->nya, g->srx, g->sry, u, v, un, vn);
+    for (long k = 0; k < n; ++k)
+        if (!isfinite(un[k]) || !isfinite(vn[k])) status |= ORC_NONFINITE;
+
+    /* 2. Heun: psi* = psi + dt F(psi); psi^{n+1} = psi + dt (F(psi)/2 + F(psi*)/2) */
+    orc_extend(nx, ny, psi, ext);
+    orc_rhs(nx, ny, dx, dy, g->eps, ext, co, mult, un, vn, dzdx, dzdy, F1);
+    for (long k = 0; k < n; ++k) ps[k] = psi[k] + dt * F1[k];
+    orc_extend(nx, ny, ps, ext);
+    orc_rhs(nx, ny, dx, dy, g->eps, ext, co, mult, un, vn, dzdx, dzdy, F2);
+    for (long k = 0; k < n; ++k) pn[k] = psi[k] + dt * (0.5 * F1[k] + 0.5 * F2[k]);
+
+    /* 3. ignition time at the sign change, eq. (set-ignition-time) */
+    for (long k = 0; k < n; ++k) {
+        if (psi[k] > 0.0 && pn[k] <= 0.0 && isinf(tign[k]))
+            tign[k] = t + psi[k] * dt / (psi[k] - pn[k]);
+    }
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            double pv = pn[(long)j * nx + i];
+            if (!isfinite(pv)) status |= ORC_NONFINITE;
+            int edge = i < g->band || j < g->band || i >= nx - g->band || j >= ny - g->band;
+            if (edge && pv < 0.0) status |= ORC_BOUNDARY;
+        }
+    }
+    for (long k = 0; k < n; ++k) psi[k] = pn[k];
+
+    /* 4. fuel fraction at t1 = t + dt */
+    double t1 = t + dt;
+    for (long k = 0; k < n; ++k) th[k] = psi[k] < 0.0 ? tign[k] : t1;   /* eq. (ti-comp) */
+    orc_extend(nx, ny, psi, ext);
+    /* Reading: ghost ignition times copy the adjacent node's (x first, then
+     * y, as for psi), then eq. (ti-comp) is applied with the ghost psi. */
+    {
+        int W = nx + 2;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                ext_t[(j + 1) * W + (i + 1)] = th[(long)j * nx + i];
+        for (int j = 1; j <= ny; ++j) {
+            ext_t[j * W] = ext_t[j * W + 1];
+            ext_t[j * W + nx + 1] = ext_t[j * W + nx];
+        }
+        for (int i = 0; i < W; ++i) {
+            ext_t[i] = ext_t[W + i];
+            ext_t[(ny + 1) * W + i] = ext_t[ny * W + i];
+        }
+        for (long k = 0; k < ne; ++k)
+            if (ext[k] >= 0.0) ext_t[k] = t1;
+    }
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            int W = nx + 2;
+            double p9[9], t9[9];
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    p9[b * 3 + a] = ext[(j + b) * W + (i + a)];
+                    t9[b * 3 + a] = ext_t[(j + b) * W + (i + a)];
+                }
+            long k = (long)j * nx + i;
+            fnew[k] = orc_cell_fuel_fraction(p9, t9, t1, co[k * CO_N + CO_TF]);
+        }
+    }
+
+    /* 5-6. heat flux densities and their average over each atmos cell */
+    for (int J = 0; J < g->nya; ++J) {
+        for (int I = 0; I < g->nxa; ++I) {
+            double sh = 0.0, sl = 0.0;
+            for (int j = J * g->sry; j < (J + 1) * g->sry; ++j) {
+                for (int i = I * g->srx; i < (I + 1) * g->srx; ++i) {
+                    long k = (long)j * nx + i;
+                    double rate = (frac[k] - fnew[k]) / dt;
+                    sh += rate * co[k * CO_N + CO_HS];
+                    sl += rate * co[k * CO_N + CO_HQ];
+                }
+            }
+            heat_s[J * g->nxa + I] = sh / (double)(g->srx * g->sry);
+            heat_l[J * g->nxa + I] = sl / (double)(g->srx * g->sry);
+        }
+    }
+    for (long k = 0; k < n; ++k) frac[k] = fnew[k];
+
+    free(un); free(vn); free(ext); free(F1); free(F2); free(ps); free(pn);
+    free(th); free(fnew); free(ext_t);
+    return status;
+}
