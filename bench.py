@@ -1,0 +1,428 @@
+"""Benchmark of the GB300 fire-model step: fire-mesh cell-steps per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+A step is one fire_step (Sect. 5 items 1-6 of the paper) over the whole
+fire mesh.  The default workload is the large forward case: an 820x820
+atmospheric mesh refined 10x to 8200x8200 fire nodes, seeded wind / hills /
+13-class fuel map, 50 point ignitions, FP32 state with FP64 ignition time and
+heat reduction, 2000 steps of 0.5 s (the state, 2.2 GB, is larger than L2, so
+no flush is needed between steps).  Under torchrun every rank runs its own
+replica of the workload (the problems are independent: weak scaling, no
+collective on the data path); the time is the max over ranks.
+
+One JSON line is printed by rank 0.  Besides the device-timed value it carries
+the end-to-end value through fire_step_host (host wind in, host heat out),
+the roofline of the fused step kernel against the measured HBM copy
+bandwidth, the FP64 GPU path on the same mesh, and the FP64 CPU oracle timed
+on a bounded sample of the same recipe on the host cores.
+
+--impl reference times the oracle itself (single host core) on a bounded
+sample of the same workload, one oracle step per bench step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fire-mesh cell-steps/s"
+UNIT = "cell-steps/s"
+# algorithmic bytes per cell-step of the one-pass FP32 step: psi r/w 4+4,
+# F r/w 4+4, ignition time read 8, fuel class 1, terrain gradient 8
+BYTES_PER_CELL_STEP = {"fp32": 33, "fp64": 57}
+KERNEL_SOURCES = ["paper_1102_1343_gb300/csrc/step_kernel.cuh",
+                  "paper_1102_1343_gb300/csrc/fire_internal.h",
+                  "paper_1102_1343_gb300/csrc/step_f32.cu"]
+PROFILE_SUMMARY = "profiles/fire_step_f32_points8200.md"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, PROFILE_SUMMARY)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, _, v = line.strip()[2:].partition(":")
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax),
+                       reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str):
+    from paper_1102_1343_gb300 import synth
+    if name == "points8200":
+        return synth.points_fire_8200()
+    if name == "line2000":
+        return synth.line_fire_2000()
+    if name == "circle100":
+        return synth.plain_circle()
+    raise ValueError(name)
+
+
+def oracle_sample(name: str, budget_cell_steps: float):
+    """A bounded sample of the same recipe for the CPU oracle: a smaller
+    square mesh with the same generators, sized to the cell-step budget."""
+    from paper_1102_1343_gb300 import synth
+    if name == "circle100":
+        return synth.plain_circle(), 1
+    side_atm = int(max(10, min(82, math.sqrt(budget_cell_steps) / 10)))
+    ign = "points" if name == "points8200" else "line"
+    w = synth.random_landscape(side_atm, side_atm, seed=synth.BASE_SEED, ignition=ign,
+                               n_points=max(1, round(50 * (side_atm / 820) ** 2)),
+                               edge_margin=2000.0 * side_atm / 820, steps=1)
+    return w, side_atm
+
+
+def time_oracle(name: str, seconds: float = 12.0, max_steps: int | None = None):
+    """Oracle cell-steps/s on a sample of the workload, single host thread."""
+    import oracle
+    w, side = oracle_sample(name, budget_cell_steps=0.67e6)
+    o = oracle.OracleFire.from_workload(w)
+    o.step(w.u, w.v, w.dt)  # first-touch
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(w.u, w.v, w.dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and n >= max_steps):
+            break
+    cells = w.nx * w.ny
+    return dict(value=cells * n / el, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{w.nx}x{w.ny} fire mesh of the same recipe ({w.name}), "
+                       f"{n} FP64 oracle steps, single thread, {el:.1f} s")
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the oracle, one sample step per bench step
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1102_1343_gb300 import synth
+    total = args.steps + args.warmup
+    budget = 100.0 * 2.5e6 / max(1, total)  # ~100 s of oracle time at ~2.5e6 cell-steps/s
+    side = int(max(10, min(82, math.sqrt(budget) / 10)))
+    w = synth.random_landscape(side, side, seed=synth.BASE_SEED, ignition="points",
+                               n_points=max(1, round(50 * (side / 820) ** 2)),
+                               edge_margin=2000.0 * side / 820, steps=1)
+    o = oracle.OracleFire.from_workload(w)
+    for _ in range(args.warmup):
+        o.step(w.u, w.v, w.dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(w.u, w.v, w.dt)
+    el = time.perf_counter() - t0
+    cells = w.nx * w.ny
+    val = cells * args.steps / el
+    sample = (f"{w.nx}x{w.ny} fire mesh of the {args.workload} recipe, one FP64 oracle step "
+              f"per bench step, single host thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1000 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "oracle_sample": f"{w.nx}x{w.ny}"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+WORKLOAD_NAMES = {"points8200": "points-fire-8200x8200 (820x820 atmos x10, 50 point ignitions)",
+                  "line2000": "line-fire-2000x2000 (200x200 atmos x10, 1 km line ignition)",
+                  "circle100": "circle-fp64-100x100 (10x10 atmos x10)"}
+
+
+# ---------------------------------------------------------------------------
+# the GB300 arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1102_1343_gb300 as pkg
+    from paper_1102_1343_gb300 import build
+
+    build.build()
+    pkg.load_library()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = make_workload(args.workload)
+    cells = w.nx * w.ny
+    prec = args.precision
+    m = pkg.FireModel.from_workload(w, precision=prec, device=dev)
+    if args.tile:
+        pkg.fire_set_tile(m.ctx, *args.tile)
+    tile = pkg.fire_get_tile(m.ctx)
+    u, v = m.wind(w.u, w.v)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        m.step(u, v, w.dt)
+    barrier()
+
+    # ---- device-timed region: K fire steps, inputs resident in HBM
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop() if rank == 0 else {}
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = cells * args.steps * world / (ms / 1000.0)
+    status = m.status()
+
+    # ---- kernel duration of the fused step kernel (events on the launching stream)
+    kt_steps = min(args.steps, 200)
+    pkg.fire_enable_timing(m.ctx, True)
+    pkg.fire_kernel_time_ms(m.ctx)
+    for _ in range(kt_steps):
+        pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
+    k_ms, k_n = pkg.fire_kernel_time_ms(m.ctx)
+    pkg.fire_enable_timing(m.ctx, False)
+    k_avg = k_ms / max(1, k_n)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = BYTES_PER_CELL_STEP[prec] * cells
+    achieved = alg_bytes / (k_avg / 1000.0) / 1e9
+    traffic = profiled_traffic() if (args.workload == "points8200" and prec == "fp32") else None
+
+    # ---- end to end through the public host-buffer entry point
+    e2e_steps = min(args.steps, args.e2e_steps)
+    npdt = np.float32 if prec == "fp32" else np.float64
+    uh = torch.from_numpy(np.ascontiguousarray(w.u, npdt)).pin_memory().numpy()
+    vh = torch.from_numpy(np.ascontiguousarray(w.v, npdt)).pin_memory().numpy()
+    hs_h = torch.zeros((w.nya, w.nxa), dtype=torch.float64).pin_memory().numpy()
+    hl_h = torch.zeros((w.nya, w.nxa), dtype=torch.float64).pin_memory().numpy()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pkg.fire_step_host(m.ctx, uh, vh, w.dt, hs_h, hl_h)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = cells * e2e_steps * world / float(te.item())
+    h2d = uh.nbytes + vh.nbytes
+    d2h = hs_h.nbytes + hl_h.nbytes
+    final_status = m.status()
+    m.close()
+    del m
+    torch.cuda.empty_cache()
+
+    # ---- the plain FP64 GPU path on the same mesh (speedup reference)
+    fp64 = None
+    if prec == "fp32" and not args.no_fp64:
+        m64 = pkg.FireModel.from_workload(w, precision="fp64", device=dev)
+        u64, v64 = m64.wind(w.u, w.v)
+        n64 = args.fp64_steps
+        for _ in range(2):
+            m64.step(u64, v64, w.dt)
+        barrier()
+        e0.record(stream)
+        for _ in range(n64):
+            pkg.fire_step(m64.ctx, u64, v64, w.dt, m64.heat_s, m64.heat_l)
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1)
+        v64 = cells * n64 / (ms64 / 1000.0)
+        fp64 = {"value": v64, "unit": UNIT, "steps": n64, "ms_per_step": ms64 / n64,
+                "speedup_fp32_over_fp64": value / world / v64}
+        m64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(args.workload, seconds=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES[args.workload], "fire_mesh": [w.nx, w.ny],
+                       "refinement": [w.srx, w.sry], "precision": prec,
+                       "state_in_hbm": "yes; state 2.2 GB > L2, no flush needed"
+                       if args.workload == "points8200" else "yes",
+                       "tile_atmos_cells": list(tile), "parallelism": f"replicas x{world}"},
+            "gpu_launches": args.steps,
+            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_fire_step<float>", "kernel_ms": k_avg,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "cpu_baseline": cpu,
+            "fp64_plain_gpu": fp64,
+            "clocks": clk,
+            "status": pkg.fire_strerror(status if status else final_status),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["points8200", "line2000", "circle100"],
+                    default="points8200")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--tile", type=int, nargs=2, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        if args.impl == "gb300":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * wrffire.h -- C ABI of the GB300 (sm_103a) fire-model step of WRF-Fire
+ * (Mandel, Beezley & Kochanski, "Coupled atmosphere-wildland fire modeling
+ * with WRF-Fire version 3.3", arXiv:1102.1343).
+ *
+ * One call of fire_step is the fire model's time step of Sect. 5 ("Coupling
+ * of the fire and the atmospheric models", the six-item list):
+ *   1. active ignitions update the level-set function     (Sect. 3.4)
+ *   2. Heun / Godunov advance of the level-set equation   (eqs. Heun, F-disc, Godunov)
+ *   3. ignition time of newly ignited nodes               (eq. set-ignition-time)
+ *   4. fuel fraction by submesh quadrature                (Sect. 3.3)
+ *   5. sensible and latent heat flux per fire cell        (eqs. sensible-/latent-heat-flux)
+ *   6. average of the fluxes over each atmospheric cell   (Sect. 5, item 6)
+ * The surface wind (already at the 6.1 m height of Sect. 5) is the input, on
+ * the staggered atmospheric grid of Sect. 3 ("Domain, grids, and nodes");
+ * the averaged heat fluxes are the output.
+ *
+ * Conventions for every entry point:
+ *  - Grids.  The atmospheric mesh has nx_atm x ny_atm cells of dx_atm x dy_atm
+ *    metres.  The fire mesh refines it sr_x x sr_y times: NX = sr_x*nx_atm,
+ *    NY = sr_y*ny_atm nodes at the cell centres ((i+1/2) dx, (j+1/2) dy),
+ *    dx = dx_atm/sr_x.  Fire-mesh arrays are row-major [NY][NX]; the wind u is
+ *    [ny_atm][nx_atm+1] at the x-faces (I dx_atm, (J+1/2) dy_atm), v is
+ *    [ny_atm+1][nx_atm] at the y-faces; heat outputs are [ny_atm][nx_atm].
+ *    NX, NY >= 2.
+ *  - Precision.  FIRE_FP64 keeps every field in double.  FIRE_FP32 keeps the
+ *    level-set function, fuel fraction, terrain gradient, multiplier and wind
+ *    in float and the ignition time, the time and the heat reduction in
+ *    double.  Pointers typed "const void*" point to elements of the context's
+ *    precision (double for FIRE_FP64, float for FIRE_FP32).
+ *  - Memory.  Pointers named *_dev are device pointers on the context's
+ *    device; pointers named *_host are host pointers (pinned memory gives the
+ *    fastest copies).  The caller owns every buffer it passes; fire_init
+ *    copies what it needs, so its inputs may be freed after it returns.  The
+ *    library owns the fire state (level set, ignition time, fuel fraction).
+ *  - Streams.  All device work of a context is enqueued on the stream given
+ *    to fire_init (a cudaStream_t; NULL = legacy default stream), in call
+ *    order.  No call synchronises except fire_status, fire_get_state's time
+ *    read-back, fire_kernel_time_ms and the *_host variants.
+ *  - Errors.  Every call returns FIRE_OK (0) or a negative FIRE_ERR_* code and
+ *    never aborts.  Faults detected on the device (fire reaching the boundary
+ *    band, a non-finite level set or wind) are recorded in a sticky status
+ *    word that fire_status reads.
+ *  - Threads.  A context may be used by one host thread at a time.
+ */
+#ifndef WRFFIRE_H
+#define WRFFIRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fire_ctx fire_ctx; /* opaque; created by fire_init, freed by fire_destroy */
+
+enum fire_precision { FIRE_FP64 = 0, FIRE_FP32 = 1 };
+
+enum fire_error {
+    FIRE_OK = 0,
+    FIRE_ERR_ARG = -1,       /* invalid argument or size */
+    FIRE_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    FIRE_ERR_OOM = -3,       /* device or pinned host memory exhausted */
+    FIRE_ERR_BOUNDARY = -4,  /* fire reached the boundary band (Sect. 3.1, last paragraph) */
+    FIRE_ERR_NONFINITE = -5, /* non-finite wind or level-set value */
+    FIRE_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
+    FIRE_ERR_STATE = -7      /* call not valid in the context's state */
+};
+
+/* Grid and numerical parameters.
+ *   eps_visc       artificial viscosity eps of eq. (F-disc), 0.4 in the paper.
+ *                  The term is applied as eps * S * (scaled 5-point Laplacian),
+ *                  the reading that makes it a speed.
+ *   boundary_band  width (nodes) of the outer ring in which psi < 0 is reported
+ *                  as FIRE_ERR_BOUNDARY; >= 1.
+ *   psi_far        initial level-set value ("const > 0", Sect. 3.4); <= 0
+ *                  selects the domain diagonal. */
+typedef struct {
+    int nx_atm, ny_atm;
+    int sr_x, sr_y;
+    double dx_atm, dy_atm;
+    int precision;
+    int boundary_band;
+    double eps_visc;
+    double psi_far;
+} fire_grid_desc;
+
+/* One fuel category: the properties of Table 1, in the units of Table 1.
+ * Setting chaparral != 0 selects the chaparral rate of eq. (chapparal).
+ * weight is the fuel weight w (s) of Table 1, from which the burn time is
+ * T_f = -600 w / (1000 ln 0.6); with weight_is_tf != 0 it is T_f itself. */
+typedef struct {
+    double windrf;      /* a, wind reduction from 6.1 m to midflame height */
+    double weight;      /* w (s), or T_f (s) when weight_is_tf */
+    int weight_is_tf;
+    int chaparral;
+    double fgi;         /* w_l, total fuel load (kg m^-2) */
+    double fueldepthm;  /* delta_m, fuel depth (m) */
+    double savr;        /* sigma, surface-area-to-volume ratio (1/m) */
+    double fuelmce;     /* M_x, moisture content of extinction */
+    double fueldens;    /* rho_P, ovendry particle density (kg m^-3) */
+    double st;          /* S_T, total mineral content */
+    double se;          /* S_E, effective mineral content */
+    double cmbcnst;     /* h, heat content of dry fuel (J kg^-1) */
+    double fuelmc_g;    /* M_f, fuel particle moisture content */
+} fire_fuel_class;
+
+/* One ignition (Sect. 3.4): the segment from (ax, ay) to (bx, by) in metres
+ * (a == b is a point).
+ *   speed > 0: from time t_start the fire spreads from the segment at this
+ *     speed S_g until the distance radius r_g is reached (eqs. ignition-lfn,
+ *     ignition-min); applied at the start of every step with
+ *     t_start <= t <= t_start + radius/speed; newly ignited nodes get the
+ *     arrival time t_start + dist/speed.
+ *   speed <= 0: instantaneous ignition of every node within radius of the
+ *     segment, applied once at the first step start t >= t_start (at fire_init
+ *     when t_start <= 0), with ignition time t_start. */
+typedef struct {
+    double ax, ay, bx, by;
+    double t_start;
+    double radius;
+    double speed;
+} fire_ignition;
+
+#define FIRE_MAX_CLASSES 64
+#define FIRE_MAX_IGNITIONS 256
+
+/* Create a context: validates the grid, allocates the state on the current
+ * device, evaluates the spread-rate coefficients of eq. (spread-WRF-Fire) per
+ * fuel class from Table 2 (on the device, in double), and initialises the
+ * state: psi = psi_far, no ignition time, fuel fraction 1, then the
+ * instantaneous ignitions with t_start <= 0 (Sect. 3.4, "initialized with no
+ * fire"; Sect. 5 "terrain gradient ... interpolated to the fire mesh in
+ * preprocessing").
+ *   classes[n_classes]    host array, 1 <= n_classes <= FIRE_MAX_CLASSES
+ *   fuel_class_dev        uint8 [NY][NX] device, class index per node (< n_classes)
+ *   moisture_dev          reserved, must be NULL (per-node moisture is not
+ *                         supported by this version)
+ *   spread_mult_dev       [NY][NX] device per-node multiplier of S, or NULL (= 1)
+ *   dzdx_dev, dzdy_dev    [NY][NX] device terrain gradient at the nodes
+ *   ignitions[n_ign]      host array, 0 <= n_ign <= FIRE_MAX_IGNITIONS
+ *   cuda_stream           cudaStream_t for all work of this context
+ * On success *out receives the context; on failure *out is NULL. */
+int fire_init(fire_ctx **out, const fire_grid_desc *grid,
+              const fire_fuel_class *classes, int n_classes,
+              const uint8_t *fuel_class_dev, const void *moisture_dev,
+              const void *spread_mult_dev, const void *dzdx_dev, const void *dzdy_dev,
+              const fire_ignition *ignitions, int n_ign, void *cuda_stream);
+
+/* One fire time step t -> t + dt with the given wind (Sect. 5, items 1-6).
+ *   wind_u_dev [ny_atm][nx_atm+1], wind_v_dev [ny_atm+1][nx_atm]: device,
+ *     context precision, m/s at 6.1 m; constant within the step.
+ *   dt > 0 (s).
+ *   heat_sens_dev, heat_lat_dev: device double [ny_atm][nx_atm], receive the
+ *     sensible and latent heat flux densities (W m^-2) averaged over each
+ *     atmospheric cell for this step; either may be NULL to skip it.
+ * Returns FIRE_OK once the step is enqueued (device faults show up in
+ * fire_status). */
+int fire_step(fire_ctx *ctx, const void *wind_u_dev, const void *wind_v_dev, double dt,
+              double *heat_sens_dev, double *heat_lat_dev);
+
+/* fire_step with host buffers: copies the wind to the device, runs the step,
+ * copies the heat fluxes back and waits for them.  Buffers as in fire_step
+ * but on the host; heat outputs may be NULL. */
+int fire_step_host(fire_ctx *ctx, const void *wind_u_host, const void *wind_v_host,
+                   double dt, double *heat_sens_host, double *heat_lat_host);
+
+/* nsteps fire steps with a wind held constant over all of them; the heat
+ * outputs (nullable) receive the fluxes of the last step.  Steps without an
+ * active ignition are replayed from a CUDA graph captured on first use. */
+int fire_run(fire_ctx *ctx, int nsteps, double dt, const void *wind_u_dev,
+             const void *wind_v_dev, double *heat_sens_dev, double *heat_lat_dev);
+
+/* Copy the state out (checkpoint): psi and frac in the context precision,
+ * tign double, each [NY][NX] device; any pointer may be NULL.  *t_host (if
+ * not NULL) receives the model time. */
+int fire_get_state(fire_ctx *ctx, void *psi_dev, double *tign_dev, void *frac_dev,
+                   double *t_host);
+
+/* Replace the state (resume): psi, frac in the context precision, tign double
+ * (+inf = not ignited), each [NY][NX] device and all required; t the model
+ * time.  Ignitions keep their applied/pending record. */
+int fire_set_state(fire_ctx *ctx, const void *psi_dev, const double *tign_dev,
+                   const void *frac_dev, double t);
+
+/* Waits for the context's stream and returns the first sticky device fault
+ * (FIRE_ERR_BOUNDARY, FIRE_ERR_NONFINITE, FIRE_ERR_TIMEOUT) or FIRE_OK;
+ * FIRE_ERR_CUDA if the stream reports a CUDA error. */
+int fire_status(fire_ctx *ctx);
+
+/* Clears the sticky device status word (enqueued on the stream). */
+int fire_clear_status(fire_ctx *ctx);
+
+/* Fire-mesh size and the model time (host value, no synchronisation). */
+int fire_mesh_size(const fire_ctx *ctx, int *nx, int *ny);
+double fire_time(const fire_ctx *ctx);
+
+/* Tile shape of the fused step kernel in atmospheric cells per CTA
+ * (tile = kx*sr_x by ky*sr_y fire nodes); chosen by the autotuner, settable
+ * for sweeps.  FIRE_ERR_ARG if the shared-memory footprint does not fit. */
+int fire_set_tile(fire_ctx *ctx, int kx, int ky);
+int fire_get_tile(const fire_ctx *ctx, int *kx, int *ky);
+
+/* Kernel timing: when enabled, CUDA events bracket every launch of the fused
+ * step kernel on the context's stream; fire_kernel_time_ms waits for them and
+ * returns the summed device time and the launch count since the last reset. */
+int fire_enable_timing(fire_ctx *ctx, int on);
+int fire_kernel_time_ms(fire_ctx *ctx, double *ms, long *launches);
+
+const char *fire_strerror(int code);
+
+void fire_destroy(fire_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WRFFIRE_H */

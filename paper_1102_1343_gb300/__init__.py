@@ -1,0 +1,347 @@
+"""GB300 (sm_103a) fire-model step of WRF-Fire: thin Python binding.
+
+The binding mirrors the C ABI of ``include/wrffire.h`` name for name
+(``fire_init``, ``fire_step``, ``fire_step_host``, ``fire_run``,
+``fire_get_state``, ``fire_set_state``, ``fire_status``, ...).  It only marshals
+arguments: torch CUDA tensors are passed as device pointers, numpy arrays as
+host pointers, and every step of the fire model runs in the CUDA library
+``libwrffire_gb300.so``.  There is no CPU fallback: if the library is missing
+the import of the native handle raises.
+
+``FireModel`` wraps one context with torch-allocated inputs and outputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwrffire_gb300.so")
+
+FIRE_FP64 = 0
+FIRE_FP32 = 1
+FIRE_OK = 0
+FIRE_ERR_ARG = -1
+FIRE_ERR_CUDA = -2
+FIRE_ERR_OOM = -3
+FIRE_ERR_BOUNDARY = -4
+FIRE_ERR_NONFINITE = -5
+FIRE_ERR_TIMEOUT = -6
+FIRE_ERR_STATE = -7
+FIRE_MAX_CLASSES = 64
+FIRE_MAX_IGNITIONS = 256
+
+# every entry point the header declares (checked by the ABI test)
+ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get_state",
+               "fire_set_state", "fire_status", "fire_clear_status", "fire_mesh_size",
+               "fire_time", "fire_set_tile", "fire_get_tile", "fire_enable_timing",
+               "fire_kernel_time_ms", "fire_strerror", "fire_destroy")
+
+
+class FireError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {fire_strerror(code)} ({code})" if what else
+                         f"{fire_strerror(code)} ({code})")
+
+
+class fire_grid_desc(C.Structure):
+    _fields_ = [("nx_atm", C.c_int), ("ny_atm", C.c_int), ("sr_x", C.c_int), ("sr_y", C.c_int),
+                ("dx_atm", C.c_double), ("dy_atm", C.c_double), ("precision", C.c_int),
+                ("boundary_band", C.c_int), ("eps_visc", C.c_double), ("psi_far", C.c_double)]
+
+
+class fire_fuel_class(C.Structure):
+    _fields_ = [("windrf", C.c_double), ("weight", C.c_double), ("weight_is_tf", C.c_int),
+                ("chaparral", C.c_int), ("fgi", C.c_double), ("fueldepthm", C.c_double),
+                ("savr", C.c_double), ("fuelmce", C.c_double), ("fueldens", C.c_double),
+                ("st", C.c_double), ("se", C.c_double), ("cmbcnst", C.c_double),
+                ("fuelmc_g", C.c_double)]
+
+
+class fire_ignition(C.Structure):
+    _fields_ = [("ax", C.c_double), ("ay", C.c_double), ("bx", C.c_double), ("by", C.c_double),
+                ("t_start", C.c_double), ("radius", C.c_double), ("speed", C.c_double)]
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def load_library(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -m paper_1102_1343_gb300.build` (needs nvcc)")
+    L = C.CDLL(path)
+    L.fire_init.argtypes = [C.POINTER(_P), C.POINTER(fire_grid_desc), C.POINTER(fire_fuel_class),
+                            C.c_int, _P, _P, _P, _P, _P, C.POINTER(fire_ignition), C.c_int, _P]
+    L.fire_step.argtypes = [_P, _P, _P, C.c_double, _P, _P]
+    L.fire_step_host.argtypes = [_P, _P, _P, C.c_double, _P, _P]
+    L.fire_run.argtypes = [_P, C.c_int, C.c_double, _P, _P, _P, _P]
+    L.fire_get_state.argtypes = [_P, _P, _P, _P, C.POINTER(C.c_double)]
+    L.fire_set_state.argtypes = [_P, _P, _P, _P, C.c_double]
+    L.fire_status.argtypes = [_P]
+    L.fire_clear_status.argtypes = [_P]
+    L.fire_mesh_size.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fire_time.argtypes = [_P]
+    L.fire_time.restype = C.c_double
+    L.fire_set_tile.argtypes = [_P, C.c_int, C.c_int]
+    L.fire_get_tile.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fire_enable_timing.argtypes = [_P, C.c_int]
+    L.fire_kernel_time_ms.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_long)]
+    L.fire_strerror.argtypes = [C.c_int]
+    L.fire_strerror.restype = C.c_char_p
+    L.fire_destroy.argtypes = [_P]
+    L.fire_destroy.restype = None
+    for name in ABI_SYMBOLS:
+        f = getattr(L, name)
+        if f.restype is C.c_int or name in ("fire_init", "fire_step", "fire_step_host",
+                                             "fire_run", "fire_get_state", "fire_set_state",
+                                             "fire_status", "fire_clear_status",
+                                             "fire_mesh_size", "fire_set_tile", "fire_get_tile",
+                                             "fire_enable_timing", "fire_kernel_time_ms"):
+            f.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, host pointer of a numpy array, or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous (row-major)")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot pass {type(x)} as a buffer")
+
+
+def _check(code, what):
+    if code != FIRE_OK:
+        raise FireError(code, what)
+    return code
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, name for name
+# ---------------------------------------------------------------------------
+
+def fire_strerror(code: int) -> str:
+    return load_library().fire_strerror(int(code)).decode()
+
+
+def make_grid(nx_atm, ny_atm, sr_x, sr_y, dx_atm, dy_atm, precision=FIRE_FP32, boundary_band=1,
+              eps_visc=0.4, psi_far=0.0) -> fire_grid_desc:
+    return fire_grid_desc(int(nx_atm), int(ny_atm), int(sr_x), int(sr_y), float(dx_atm),
+                          float(dy_atm), int(precision), int(boundary_band), float(eps_visc),
+                          float(psi_far))
+
+
+def make_classes(classes) -> C.Array:
+    arr = (fire_fuel_class * len(classes))()
+    for k, c in enumerate(classes):
+        for name, typ in fire_fuel_class._fields_:
+            val = c.get(name, 0)
+            setattr(arr[k], name, int(val) if typ is C.c_int else float(val))
+    return arr
+
+
+def make_ignitions(ignitions) -> C.Array:
+    arr = (fire_ignition * max(1, len(ignitions)))()
+    for k, g in enumerate(ignitions):
+        for name, _ in fire_ignition._fields_:
+            setattr(arr[k], name, float(g[name]))
+    return arr
+
+
+def fire_init(grid: fire_grid_desc, classes, fuel_class_dev, moisture_dev, spread_mult_dev,
+              dzdx_dev, dzdy_dev, ignitions, cuda_stream=None) -> int:
+    """Returns the context handle (an int); raises FireError on failure."""
+    L = load_library()
+    cls = make_classes(classes)
+    ign = make_ignitions(list(ignitions))
+    out = _P()
+    code = L.fire_init(C.byref(out), C.byref(grid), cls, len(classes), _ptr(fuel_class_dev),
+                       _ptr(moisture_dev), _ptr(spread_mult_dev), _ptr(dzdx_dev),
+                       _ptr(dzdy_dev), ign, len(list(ignitions)), _ptr(cuda_stream) or None)
+    _check(code, "fire_init")
+    return out.value
+
+
+def fire_step(ctx, wind_u_dev, wind_v_dev, dt, heat_sens_dev=None, heat_lat_dev=None) -> int:
+    return _check(load_library().fire_step(ctx, _ptr(wind_u_dev), _ptr(wind_v_dev), float(dt),
+                                           _ptr(heat_sens_dev), _ptr(heat_lat_dev)), "fire_step")
+
+
+def fire_step_host(ctx, wind_u_host, wind_v_host, dt, heat_sens_host=None,
+                   heat_lat_host=None) -> int:
+    return _check(load_library().fire_step_host(ctx, _ptr(wind_u_host), _ptr(wind_v_host),
+                                                float(dt), _ptr(heat_sens_host),
+                                                _ptr(heat_lat_host)), "fire_step_host")
+
+
+def fire_run(ctx, nsteps, dt, wind_u_dev, wind_v_dev, heat_sens_dev=None,
+             heat_lat_dev=None) -> int:
+    return _check(load_library().fire_run(ctx, int(nsteps), float(dt), _ptr(wind_u_dev),
+                                          _ptr(wind_v_dev), _ptr(heat_sens_dev),
+                                          _ptr(heat_lat_dev)), "fire_run")
+
+
+def fire_get_state(ctx, psi_dev=None, tign_dev=None, frac_dev=None) -> float:
+    t = C.c_double()
+    _check(load_library().fire_get_state(ctx, _ptr(psi_dev), _ptr(tign_dev), _ptr(frac_dev),
+                                         C.byref(t)), "fire_get_state")
+    return t.value
+
+
+def fire_set_state(ctx, psi_dev, tign_dev, frac_dev, t) -> int:
+    return _check(load_library().fire_set_state(ctx, _ptr(psi_dev), _ptr(tign_dev),
+                                                _ptr(frac_dev), float(t)), "fire_set_state")
+
+
+def fire_status(ctx) -> int:
+    """Synchronises; returns FIRE_OK or a device fault code (not raised)."""
+    return load_library().fire_status(ctx)
+
+
+def fire_clear_status(ctx) -> int:
+    return _check(load_library().fire_clear_status(ctx), "fire_clear_status")
+
+
+def fire_mesh_size(ctx):
+    nx, ny = C.c_int(), C.c_int()
+    _check(load_library().fire_mesh_size(ctx, C.byref(nx), C.byref(ny)), "fire_mesh_size")
+    return nx.value, ny.value
+
+
+def fire_time(ctx) -> float:
+    return load_library().fire_time(ctx)
+
+
+def fire_set_tile(ctx, kx, ky) -> int:
+    return _check(load_library().fire_set_tile(ctx, int(kx), int(ky)), "fire_set_tile")
+
+
+def fire_get_tile(ctx):
+    kx, ky = C.c_int(), C.c_int()
+    _check(load_library().fire_get_tile(ctx, C.byref(kx), C.byref(ky)), "fire_get_tile")
+    return kx.value, ky.value
+
+
+def fire_enable_timing(ctx, on=True) -> int:
+    return _check(load_library().fire_enable_timing(ctx, int(bool(on))), "fire_enable_timing")
+
+
+def fire_kernel_time_ms(ctx):
+    ms, n = C.c_double(), C.c_long()
+    _check(load_library().fire_kernel_time_ms(ctx, C.byref(ms), C.byref(n)),
+           "fire_kernel_time_ms")
+    return ms.value, n.value
+
+
+def fire_destroy(ctx) -> None:
+    if ctx:
+        load_library().fire_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper (torch for memory and streams only)
+# ---------------------------------------------------------------------------
+
+class FireModel:
+    """One fire-model context on the current CUDA device.
+
+    Inputs are copied to the device once; ``step`` takes the wind (torch CUDA
+    tensors of the context precision, or anything torch can convert) and
+    returns the averaged sensible and latent heat flux densities as float64
+    CUDA tensors."""
+
+    def __init__(self, nxa, nya, sr, dx_atm, classes, fuel, dzdx, dzdy, ignitions=(),
+                 precision="fp32", mult=None, eps=0.4, band=1, psi_far=0.0, dy_atm=None,
+                 stream=None, device=None):
+        import torch
+        self.torch = torch
+        srx, sry = (sr, sr) if np.isscalar(sr) else sr
+        dy_atm = dx_atm if dy_atm is None else dy_atm
+        self.precision = FIRE_FP64 if precision in ("fp64", FIRE_FP64, "f64") else FIRE_FP32
+        self.dtype = torch.float64 if self.precision == FIRE_FP64 else torch.float32
+        self.device = torch.device(device or "cuda")
+        self.nxa, self.nya, self.srx, self.sry = nxa, nya, srx, sry
+        self.nx, self.ny = nxa * srx, nya * sry
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        dev = self.device
+
+        def t(a, dtype):
+            return torch.as_tensor(np.ascontiguousarray(a)).to(dev, dtype).contiguous()
+
+        fuel_d = t(fuel, torch.uint8)
+        zx, zy = t(dzdx, self.dtype), t(dzdy, self.dtype)
+        m = None if mult is None else t(mult, self.dtype)
+        grid = make_grid(nxa, nya, srx, sry, dx_atm, dy_atm, self.precision, band, eps, psi_far)
+        torch.cuda.synchronize(dev)
+        self.ctx = fire_init(grid, classes, fuel_d, None, m, zx, zy, list(ignitions),
+                             self.stream.cuda_stream)
+        self.heat_s = torch.zeros((nya, nxa), dtype=torch.float64, device=dev)
+        self.heat_l = torch.zeros_like(self.heat_s)
+
+    @classmethod
+    def from_workload(cls, w, precision="fp32", **kw):
+        return cls(w.nxa, w.nya, (w.srx, w.sry), w.dx_atm, w.classes, w.fuel, w.dzdx, w.dzdy,
+                   w.ignitions, precision=precision, mult=w.mult, eps=w.eps, band=w.band,
+                   dy_atm=w.dy_atm, **kw)
+
+    def wind(self, u, v):
+        torch = self.torch
+        return (torch.as_tensor(np.ascontiguousarray(u)).to(self.device, self.dtype).contiguous(),
+                torch.as_tensor(np.ascontiguousarray(v)).to(self.device, self.dtype).contiguous())
+
+    def step(self, u, v, dt):
+        fire_step(self.ctx, u, v, dt, self.heat_s, self.heat_l)
+        return self.heat_s, self.heat_l
+
+    def run(self, nsteps, u, v, dt):
+        fire_run(self.ctx, nsteps, dt, u, v, self.heat_s, self.heat_l)
+        return self.heat_s, self.heat_l
+
+    def state(self):
+        torch = self.torch
+        psi = torch.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
+        tign = torch.empty((self.ny, self.nx), dtype=torch.float64, device=self.device)
+        frac = torch.empty_like(psi)
+        t = fire_get_state(self.ctx, psi, tign, frac)
+        return psi, tign, frac, t
+
+    def set_state(self, psi, tign, frac, t):
+        fire_set_state(self.ctx, psi.contiguous(), tign.contiguous(), frac.contiguous(), t)
+
+    def status(self):
+        return fire_status(self.ctx)
+
+    @property
+    def time(self):
+        return fire_time(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fire_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

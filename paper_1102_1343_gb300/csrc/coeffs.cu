@@ -1,0 +1,108 @@
+// Init-time kernel: fuel-class properties (Table 1) -> the per-class
+// coefficients of eq. (spread-WRF-Fire), the burn time T_f and the heat
+// factors of eqs. (sensible-heat-flux), (latent-heat-flux).  One thread per
+// class, FP64.
+//
+// The Rothermel chain of Table 2 runs in English units (the caption of
+// Table 2 converts inputs from metric); the spread rate is
+//   S = R0 (1 + phi_W + phi_S),  phi_W = C U_a^B (beta/beta_op)^(-E),
+//   phi_S = 5.275 beta^(-0.3) tan^2(phi),  U_a = a U,
+// with the CAWFE limits 0 <= U <= 30 m/s and tan(phi) >= 0, which gives the
+// coefficient form S = max{S0, R0 + c min{e, max{0,U}}^b + d max{0,tan}^2}
+// with b = B, c = R0 C (a * 196.85)^B (beta/beta_op)^(-E), d = 5.275 R0
+// beta^(-0.3), e = 30 m/s, S0 = 0 (SI, U in m/s).  Chaparral (eq. chapparal):
+// S0 = 0.03333, R0 = 0, b = 1, c = 1.2974, d = 0, e = 6/1.2974.
+// Readings of the table's garbled entries: Gamma_max uses Rothermel's
+// constant 0.0594; Q_ig = 250 + 1116 M_f; B = 0.02526 sigma^0.54 and
+// beta_op = 3.348 sigma^(-0.8189).  eta_M is clamped to [0, 1]; a class
+// without fuel load does not spread.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "fire_internal.h"
+
+namespace wf {
+
+namespace {
+
+constexpr double kFt = 0.3048;          // m per ft
+constexpr double kLb = 0.45359237;      // kg per lb
+constexpr double kBtu = 1055.05585262;  // J per BTU
+constexpr double kLatent = 2.5e6;       // L (J/kg)
+constexpr double kWindMax = 30.0;       // m/s
+
+__global__ void k_coefficients(const fire_fuel_class *cls, int n, double *coef) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const fire_fuel_class f = cls[k];
+    double *co = coef + (size_t)k * K_N;
+    const double Mf = f.fuelmc_g;
+    co[K_TF] = f.weight_is_tf ? f.weight : f.weight / (-1000.0 * log(0.6) / 600.0);
+    co[K_HS] = f.fgi * f.cmbcnst / (1.0 + Mf);
+    co[K_HQ] = (Mf + 0.56) / (1.0 + Mf) * kLatent * f.fgi;
+    if (f.chaparral) {
+        co[K_S0] = 0.03333;
+        co[K_R0] = 0.0;
+        co[K_B] = 1.0;
+        co[K_C] = 1.2974;
+        co[K_D] = 0.0;
+        co[K_E] = 6.0 / 1.2974;
+        return;
+    }
+    co[K_S0] = 0.0;
+    co[K_E] = kWindMax;
+    if (!(f.fgi > 0.0)) {
+        co[K_R0] = 0.0;
+        co[K_B] = 1.0;
+        co[K_C] = 0.0;
+        co[K_D] = 0.0;
+        return;
+    }
+    // English units
+    const double sig = f.savr * kFt;                       // 1/ft
+    const double load = f.fgi * kFt * kFt / kLb;           // lb/ft^2
+    const double dep = f.fueldepthm / kFt;                 // ft
+    const double rhoP = f.fueldens * kFt * kFt * kFt / kLb;  // lb/ft^3
+    const double heat = f.cmbcnst * kLb / kBtu;            // BTU/lb
+    // packing
+    const double w0 = load / (1.0 + Mf);
+    const double rhob = w0 / dep;
+    const double beta = rhob / rhoP;
+    const double bop = 3.348 * pow(sig, -0.8189);
+    const double rel = beta / bop;
+    // reaction intensity
+    const double sig15 = pow(sig, 1.5);
+    const double gmax = sig15 / (495.0 + 0.0594 * sig15);
+    const double A = 1.0 / (4.77 * pow(sig, 0.1) - 7.27);
+    const double gam = gmax * pow(rel, A) * exp(A * (1.0 - rel));
+    const double wn = w0 / (1.0 + f.st);
+    const double x = Mf / f.fuelmce;
+    double etaM = 1.0 - 2.59 * x + 5.11 * x * x - 3.52 * x * x * x;
+    if (x >= 1.0 || etaM < 0.0) etaM = 0.0;
+    if (etaM > 1.0) etaM = 1.0;
+    const double etaS = 0.174 * pow(f.se, -0.19);
+    const double IR = gam * wn * heat * etaM * etaS;
+    // propagating flux, heat sink
+    const double xi = exp((0.792 + 0.681 * sqrt(sig)) * (beta + 0.1)) / (192.0 + 0.2595 * sig);
+    const double epsh = exp(-138.0 / sig);
+    const double Qig = 250.0 + 1116.0 * Mf;
+    const double R0 = IR * xi / (rhob * epsh * Qig) * (kFt / 60.0);  // ft/min -> m/s
+    // wind and slope factors
+    const double B = 0.02526 * pow(sig, 0.54);
+    const double C = 7.47 * exp(-0.133 * pow(sig, 0.55));
+    const double E = 0.715 * exp(-3.59e-4 * sig);
+    co[K_R0] = R0;
+    co[K_B] = B;
+    co[K_C] = R0 * C * pow(f.windrf * (60.0 / kFt), B) * pow(rel, -E);
+    co[K_D] = R0 * 5.275 * pow(beta, -0.3);
+}
+
+}  // namespace
+
+cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
+                                cudaStream_t s) {
+    k_coefficients<<<(n + 63) / 64, 64, 0, s>>>(classes_dev, n, coef_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace wf

@@ -1,0 +1,579 @@
+// Host side of the C ABI (include/wrffire.h): the model layer of the fire
+// module -- state buffers, step sequencing (Sect. 5, the six-item list),
+// ignition bookkeeping (Sect. 3.4), CUDA-graph replay of plain steps, the
+// sticky status word, checkpoint/resume and kernel timing.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "fire_internal.h"
+
+using namespace wf;
+
+struct fire_ctx {
+    fire_grid_desc g{};
+    int nx = 0, ny = 0;
+    size_t n = 0;
+    double dx = 0, dy = 0, psi_far = 0;
+    int prec = FIRE_FP32;
+    size_t esz = 4;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    void *psi[2] = {nullptr, nullptr};
+    void *frac[2] = {nullptr, nullptr};
+    double *tign = nullptr;
+    uint8_t *fuel = nullptr;
+    void *dzdx = nullptr, *dzdy = nullptr, *mult = nullptr;
+    fire_fuel_class *classes_dev = nullptr;
+    double *coef = nullptr;
+    int ncls = 0;
+    int *status = nullptr;  // device word
+    double *tdev = nullptr;  // [2] device model time, ping-pong with psi
+    int cur = 0;
+    double t = 0.0;  // host copy of the model time
+
+    std::vector<fire_ignition> ign;
+    std::vector<unsigned char> applied;
+
+    int kx = 0, ky = 0;
+    size_t smem = 0;
+    size_t smem_max = 0;
+
+    // host-buffer staging
+    void *stage_u = nullptr, *stage_v = nullptr;
+    double *stage_hs = nullptr, *stage_hl = nullptr;
+
+    // graph of two plain steps (cur 0 -> 1 -> 0)
+    cudaGraphExec_t graph = nullptr;
+    const void *g_u = nullptr, *g_v = nullptr;
+    double g_dt = 0;
+    double *g_hs = nullptr, *g_hl = nullptr;
+    int g_kx = 0, g_ky = 0;
+
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pairs
+    long launches = 0;
+    double ms_done = 0;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return FIRE_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FIRE_ERR_OOM;
+    }
+    return FIRE_ERR_CUDA;
+}
+
+#define WF_CHECK(call)                         \
+    do {                                       \
+        int _r = cuda_err(call);               \
+        if (_r != FIRE_OK) return _r;          \
+    } while (0)
+
+void release(fire_ctx *c) {
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    void *bufs[] = {c->psi[0], c->psi[1], c->frac[0], c->frac[1], c->tign, c->fuel, c->dzdx,
+                    c->dzdy, c->mult, c->classes_dev, c->coef, c->status, c->tdev,
+                    c->stage_u, c->stage_v, c->stage_hs, c->stage_hl};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete c;
+}
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+int step_kernel_args(fire_ctx *c, const void *u, const void *v, double dt, double *hs,
+                     double *hl, StepArgs &a) {
+    memset(&a, 0, sizeof a);
+    a.psi_in = c->psi[c->cur];
+    a.psi_out = c->psi[1 - c->cur];
+    a.F_in = c->frac[c->cur];
+    a.F_out = c->frac[1 - c->cur];
+    a.tign = c->tign;
+    a.fuel = c->fuel;
+    a.dzdx = c->dzdx;
+    a.dzdy = c->dzdy;
+    a.mult = c->mult;
+    a.u = u;
+    a.v = v;
+    a.coef = c->coef;
+    a.ncls = c->ncls;
+    a.heat_s = hs;
+    a.heat_l = hl;
+    a.status = c->status;
+    a.t_in = c->tdev + c->cur;
+    a.t_out = c->tdev + (1 - c->cur);
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nxa = c->g.nx_atm;
+    a.nya = c->g.ny_atm;
+    a.srx = c->g.sr_x;
+    a.sry = c->g.sr_y;
+    a.kx = c->kx;
+    a.ky = c->ky;
+    a.band = c->g.boundary_band;
+    a.dx = c->dx;
+    a.dy = c->dy;
+    a.eps = c->g.eps_visc;
+    a.dt = dt;
+    return FIRE_OK;
+}
+
+cudaError_t launch_step_prec(fire_ctx *c, const StepArgs &a) {
+    return c->prec == FIRE_FP64 ? launch_step<double>(a, c->stream)
+                                : launch_step<float>(a, c->stream);
+}
+
+// Ignitions active at a step starting at time t (Sect. 3.4), in list order.
+// mark: record instantaneous ignitions as applied.
+void active_segments(fire_ctx *c, double t, bool mark, std::vector<IgnSeg> &out) {
+    out.clear();
+    for (size_t q = 0; q < c->ign.size(); ++q) {
+        const fire_ignition &g = c->ign[q];
+        IgnSeg s;
+        s.ax = g.ax;
+        s.ay = g.ay;
+        s.bx = g.bx;
+        s.by = g.by;
+        s.tg = g.t_start;
+        s.sg = g.speed;
+        if (!(g.speed > 0.0)) {
+            if (c->applied[q] || !(g.t_start <= t)) continue;
+            s.rho = g.radius;
+            if (mark) c->applied[q] = 1;
+        } else {
+            if (!(g.t_start <= t && t <= g.t_start + g.radius / g.speed)) continue;
+            s.rho = g.speed * (t - g.t_start);
+        }
+        out.push_back(s);
+    }
+}
+
+int apply_ignitions(fire_ctx *c, const std::vector<IgnSeg> &segs) {
+    size_t k = 0;
+    while (k < segs.size()) {
+        IgniteArgs a;
+        memset(&a, 0, sizeof a);
+        a.psi = c->psi[c->cur];
+        a.tign = c->tign;
+        a.nx = c->nx;
+        a.ny = c->ny;
+        a.dx = c->dx;
+        a.dy = c->dy;
+        int m = 0;
+        while (k < segs.size() && m < kMaxSegPerLaunch) a.seg[m++] = segs[k++];
+        a.nseg = m;
+        cudaError_t e = c->prec == FIRE_FP64 ? launch_ignite<double>(a, c->stream)
+                                             : launch_ignite<float>(a, c->stream);
+        WF_CHECK(e);
+    }
+    return FIRE_OK;
+}
+
+int record_event(fire_ctx *c) {
+    cudaEvent_t e;
+    WF_CHECK(cudaEventCreate(&e));
+    c->ev.push_back(e);
+    WF_CHECK(cudaEventRecord(e, c->stream));
+    return FIRE_OK;
+}
+
+int configure_tile(fire_ctx *c, int kx, int ky) {
+    if (kx < 1 || ky < 1) return FIRE_ERR_ARG;
+    size_t sm = c->prec == FIRE_FP64
+                    ? step_smem_bytes<double>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls)
+                    : step_smem_bytes<float>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls);
+    if (sm > c->smem_max) return FIRE_ERR_ARG;
+    cudaError_t e = c->prec == FIRE_FP64 ? prepare_step_kernel<double>(sm)
+                                         : prepare_step_kernel<float>(sm);
+    WF_CHECK(e);
+    c->kx = kx;
+    c->ky = ky;
+    c->smem = sm;
+    return FIRE_OK;
+}
+
+int default_tile(fire_ctx *c) {
+    // about 80 x 40 fire nodes for FP32 and 40 x 40 for FP64, whole atmos cells
+    int tx = c->prec == FIRE_FP64 ? 40 : 80, tyy = 40;
+    int kx = tx / c->g.sr_x, ky = tyy / c->g.sr_y;
+    if (kx < 1) kx = 1;
+    if (ky < 1) ky = 1;
+    if (kx > c->g.nx_atm) kx = c->g.nx_atm;
+    if (ky > c->g.ny_atm) ky = c->g.ny_atm;
+    while (configure_tile(c, kx, ky) != FIRE_OK) {
+        if (kx == 1 && ky == 1) return FIRE_ERR_ARG;
+        if (kx >= ky && kx > 1) kx = (kx + 1) / 2;
+        else ky = (ky + 1) / 2;
+    }
+    return FIRE_OK;
+}
+
+int one_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, double *hl) {
+    std::vector<IgnSeg> segs;
+    active_segments(c, c->t, true, segs);
+    if (!segs.empty()) {
+        int r = apply_ignitions(c, segs);
+        if (r) return r;
+    }
+    StepArgs a;
+    step_kernel_args(c, u, v, dt, hs, hl, a);
+    if (c->timing) {
+        int r = record_event(c);
+        if (r) return r;
+    }
+    WF_CHECK(launch_step_prec(c, a));
+    if (c->timing) {
+        int r = record_event(c);
+        if (r) return r;
+        c->launches += 1;
+    }
+    c->cur = 1 - c->cur;
+    c->t = c->t + dt;
+    return FIRE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fire_strerror(int code) {
+    switch (code) {
+        case FIRE_OK: return "ok";
+        case FIRE_ERR_ARG: return "invalid argument";
+        case FIRE_ERR_CUDA: return "CUDA runtime error";
+        case FIRE_ERR_OOM: return "out of memory";
+        case FIRE_ERR_BOUNDARY: return "fire reached the domain boundary";
+        case FIRE_ERR_NONFINITE: return "non-finite wind or level-set value";
+        case FIRE_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case FIRE_ERR_STATE: return "call not valid in this state";
+        default: return "unknown error";
+    }
+}
+
+int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class *classes,
+              int n_classes, const uint8_t *fuel_class_dev, const void *moisture_dev,
+              const void *spread_mult_dev, const void *dzdx_dev, const void *dzdy_dev,
+              const fire_ignition *ignitions, int n_ign, void *cuda_stream) {
+    if (!out) return FIRE_ERR_ARG;
+    *out = nullptr;
+    if (!grid || !classes || !fuel_class_dev || !dzdx_dev || !dzdy_dev) return FIRE_ERR_ARG;
+    if (moisture_dev) return FIRE_ERR_ARG;
+    if (n_classes < 1 || n_classes > FIRE_MAX_CLASSES) return FIRE_ERR_ARG;
+    if (n_ign < 0 || n_ign > FIRE_MAX_IGNITIONS || (n_ign > 0 && !ignitions)) return FIRE_ERR_ARG;
+    const fire_grid_desc &g = *grid;
+    if (g.nx_atm < 1 || g.ny_atm < 1 || g.sr_x < 1 || g.sr_y < 1) return FIRE_ERR_ARG;
+    if (!finite_pos(g.dx_atm) || !finite_pos(g.dy_atm)) return FIRE_ERR_ARG;
+    if (g.precision != FIRE_FP32 && g.precision != FIRE_FP64) return FIRE_ERR_ARG;
+    if (g.boundary_band < 1 || !(g.eps_visc >= 0.0) || !isfinite(g.eps_visc)) return FIRE_ERR_ARG;
+    if (!isfinite(g.psi_far)) return FIRE_ERR_ARG;
+    const long long NX = (long long)g.nx_atm * g.sr_x, NY = (long long)g.ny_atm * g.sr_y;
+    if (NX < 2 || NY < 2 || NX > (1 << 30) || NY > (1 << 30)) return FIRE_ERR_ARG;
+    if (NX * NY > (1LL << 34)) return FIRE_ERR_OOM;
+    for (int q = 0; q < n_ign; ++q) {
+        const fire_ignition &s = ignitions[q];
+        if (!isfinite(s.ax) || !isfinite(s.ay) || !isfinite(s.bx) || !isfinite(s.by) ||
+            !isfinite(s.t_start) || !isfinite(s.radius) || !isfinite(s.speed) || s.radius < 0)
+            return FIRE_ERR_ARG;
+    }
+    for (int k = 0; k < n_classes; ++k) {
+        const fire_fuel_class &f = classes[k];
+        if (f.fgi > 0 && !f.chaparral &&
+            !(f.savr > 0 && f.fueldepthm > 0 && f.fueldens > 0 && f.fuelmce > 0 && f.se > 0))
+            return FIRE_ERR_ARG;
+        if (!(f.weight > 0)) return FIRE_ERR_ARG;
+    }
+
+    fire_ctx *c = new (std::nothrow) fire_ctx();
+    if (!c) return FIRE_ERR_OOM;
+    c->g = g;
+    c->nx = (int)NX;
+    c->ny = (int)NY;
+    c->n = (size_t)NX * (size_t)NY;
+    c->dx = g.dx_atm / g.sr_x;
+    c->dy = g.dy_atm / g.sr_y;
+    c->psi_far = g.psi_far > 0 ? g.psi_far : hypot(NX * c->dx, NY * c->dy);
+    c->prec = g.precision;
+    c->esz = c->prec == FIRE_FP64 ? 8 : 4;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->ncls = n_classes;
+    c->ign.assign(ignitions, ignitions + n_ign);
+    c->applied.assign(n_ign, 0);
+    int r = FIRE_OK;
+#define WF_TRY(call)              \
+    do {                          \
+        r = cuda_err(call);       \
+        if (r) {                  \
+            release(c);           \
+            return r;             \
+        }                         \
+    } while (0)
+    WF_TRY(cudaGetDevice(&c->device));
+    int smo = 0;
+    WF_TRY(cudaDeviceGetAttribute(&smo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    c->smem_max = (size_t)smo;
+    const size_t N = c->n, E = c->esz;
+    WF_TRY(cudaMalloc(&c->psi[0], N * E));
+    WF_TRY(cudaMalloc(&c->psi[1], N * E));
+    WF_TRY(cudaMalloc(&c->frac[0], N * E));
+    WF_TRY(cudaMalloc(&c->frac[1], N * E));
+    WF_TRY(cudaMalloc(&c->tign, N * sizeof(double)));
+    WF_TRY(cudaMalloc(&c->fuel, N));
+    WF_TRY(cudaMalloc(&c->dzdx, N * E));
+    WF_TRY(cudaMalloc(&c->dzdy, N * E));
+    if (spread_mult_dev) WF_TRY(cudaMalloc(&c->mult, N * E));
+    WF_TRY(cudaMalloc(&c->classes_dev, sizeof(fire_fuel_class) * n_classes));
+    WF_TRY(cudaMalloc(&c->coef, sizeof(double) * K_N * n_classes));
+    WF_TRY(cudaMalloc(&c->status, sizeof(int)));
+    WF_TRY(cudaMalloc(&c->tdev, 2 * sizeof(double)));
+    cudaStream_t s = c->stream;
+    WF_TRY(cudaMemcpyAsync(c->fuel, fuel_class_dev, N, cudaMemcpyDeviceToDevice, s));
+    WF_TRY(cudaMemcpyAsync(c->dzdx, dzdx_dev, N * E, cudaMemcpyDeviceToDevice, s));
+    WF_TRY(cudaMemcpyAsync(c->dzdy, dzdy_dev, N * E, cudaMemcpyDeviceToDevice, s));
+    if (spread_mult_dev)
+        WF_TRY(cudaMemcpyAsync(c->mult, spread_mult_dev, N * E, cudaMemcpyDeviceToDevice, s));
+    WF_TRY(cudaMemcpyAsync(c->classes_dev, classes, sizeof(fire_fuel_class) * n_classes,
+                           cudaMemcpyHostToDevice, s));
+    WF_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+    WF_TRY(cudaMemsetAsync(c->tdev, 0, 2 * sizeof(double), s));
+    WF_TRY(launch_coefficients(c->classes_dev, n_classes, c->coef, s));
+    WF_TRY(c->prec == FIRE_FP64 ? launch_fill<double>(c->psi[0], c->tign, c->frac[0], N,
+                                                      c->psi_far, s)
+                                : launch_fill<float>(c->psi[0], c->tign, c->frac[0], N,
+                                                     c->psi_far, s));
+    // the model starts at t = 0: instantaneous ignitions with t_start <= 0
+    {
+        std::vector<IgnSeg> segs;
+        for (size_t q = 0; q < c->ign.size(); ++q) {
+            const fire_ignition &gq = c->ign[q];
+            if (!(gq.speed > 0.0) && gq.t_start <= 0.0) {
+                IgnSeg sg;
+                sg.ax = gq.ax;
+                sg.ay = gq.ay;
+                sg.bx = gq.bx;
+                sg.by = gq.by;
+                sg.tg = gq.t_start;
+                sg.sg = gq.speed;
+                sg.rho = gq.radius;
+                segs.push_back(sg);
+                c->applied[q] = 1;
+            }
+        }
+        r = apply_ignitions(c, segs);
+        if (r) {
+            release(c);
+            return r;
+        }
+    }
+    r = default_tile(c);
+    if (r) {
+        release(c);
+        return r;
+    }
+    // the copies above read caller buffers: finish before returning
+    WF_TRY(cudaStreamSynchronize(s));
+#undef WF_TRY
+    *out = c;
+    return FIRE_OK;
+}
+
+int fire_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, double *hl) {
+    if (!c || !u || !v || !finite_pos(dt)) return FIRE_ERR_ARG;
+    return one_step(c, u, v, dt, hs, hl);
+}
+
+int fire_step_host(fire_ctx *c, const void *u, const void *v, double dt, double *hs,
+                   double *hl) {
+    if (!c || !u || !v || !finite_pos(dt)) return FIRE_ERR_ARG;
+    const size_t nu = (size_t)c->g.ny_atm * (c->g.nx_atm + 1) * c->esz;
+    const size_t nv = (size_t)(c->g.ny_atm + 1) * c->g.nx_atm * c->esz;
+    const size_t nh = (size_t)c->g.ny_atm * c->g.nx_atm * sizeof(double);
+    if (!c->stage_u) {
+        WF_CHECK(cudaMalloc(&c->stage_u, nu));
+        WF_CHECK(cudaMalloc(&c->stage_v, nv));
+        WF_CHECK(cudaMalloc(&c->stage_hs, nh));
+        WF_CHECK(cudaMalloc(&c->stage_hl, nh));
+    }
+    WF_CHECK(cudaMemcpyAsync(c->stage_u, u, nu, cudaMemcpyHostToDevice, c->stream));
+    WF_CHECK(cudaMemcpyAsync(c->stage_v, v, nv, cudaMemcpyHostToDevice, c->stream));
+    int r = one_step(c, c->stage_u, c->stage_v, dt, hs ? c->stage_hs : nullptr,
+                     hl ? c->stage_hl : nullptr);
+    if (r) return r;
+    if (hs) WF_CHECK(cudaMemcpyAsync(hs, c->stage_hs, nh, cudaMemcpyDeviceToHost, c->stream));
+    if (hl) WF_CHECK(cudaMemcpyAsync(hl, c->stage_hl, nh, cudaMemcpyDeviceToHost, c->stream));
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    return FIRE_OK;
+}
+
+int fire_run(fire_ctx *c, int nsteps, double dt, const void *u, const void *v, double *hs,
+             double *hl) {
+    if (!c || !u || !v || nsteps < 0 || !finite_pos(dt)) return FIRE_ERR_ARG;
+    int k = 0;
+    std::vector<IgnSeg> segs;
+    while (k < nsteps) {
+        // two plain steps starting from cur == 0 replay the captured graph
+        bool plain = c->cur == 0 && nsteps - k >= 2 && !c->timing;
+        if (plain) {
+            active_segments(c, c->t, false, segs);
+            plain = segs.empty();
+        }
+        if (plain) {
+            active_segments(c, c->t + dt, false, segs);
+            plain = segs.empty();
+        }
+        if (!plain) {
+            int r = one_step(c, u, v, dt, hs, hl);
+            if (r) return r;
+            ++k;
+            continue;
+        }
+        if (!c->graph || c->g_u != u || c->g_v != v || c->g_dt != dt || c->g_hs != hs ||
+            c->g_hl != hl || c->g_kx != c->kx || c->g_ky != c->ky) {
+            if (c->graph) {
+                cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+            }
+            cudaStream_t cs;
+            WF_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t gr = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                StepArgs a;
+                for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
+                    step_kernel_args(c, u, v, dt, hs, hl, a);
+                    a.psi_in = c->psi[h];
+                    a.psi_out = c->psi[1 - h];
+                    a.F_in = c->frac[h];
+                    a.F_out = c->frac[1 - h];
+                    a.t_in = c->tdev + h;
+                    a.t_out = c->tdev + (1 - h);
+                    e = c->prec == FIRE_FP64 ? launch_step<double>(a, cs) : launch_step<float>(a, cs);
+                }
+                cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            cudaStreamDestroy(cs);
+            WF_CHECK(e);
+            c->g_u = u;
+            c->g_v = v;
+            c->g_dt = dt;
+            c->g_hs = hs;
+            c->g_hl = hl;
+            c->g_kx = c->kx;
+            c->g_ky = c->ky;
+        }
+        WF_CHECK(cudaGraphLaunch(c->graph, c->stream));
+        c->t = c->t + dt;
+        c->t = c->t + dt;
+        k += 2;
+    }
+    return FIRE_OK;
+}
+
+int fire_get_state(fire_ctx *c, void *psi, double *tign, void *frac, double *t_host) {
+    if (!c) return FIRE_ERR_ARG;
+    const size_t N = c->n, E = c->esz;
+    if (psi) WF_CHECK(cudaMemcpyAsync(psi, c->psi[c->cur], N * E, cudaMemcpyDeviceToDevice, c->stream));
+    if (tign)
+        WF_CHECK(cudaMemcpyAsync(tign, c->tign, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (frac) WF_CHECK(cudaMemcpyAsync(frac, c->frac[c->cur], N * E, cudaMemcpyDeviceToDevice, c->stream));
+    if (t_host) *t_host = c->t;
+    return FIRE_OK;
+}
+
+int fire_set_state(fire_ctx *c, const void *psi, const double *tign, const void *frac, double t) {
+    if (!c || !psi || !tign || !frac || !isfinite(t)) return FIRE_ERR_ARG;
+    const size_t N = c->n, E = c->esz;
+    WF_CHECK(cudaMemcpyAsync(c->psi[c->cur], psi, N * E, cudaMemcpyDeviceToDevice, c->stream));
+    WF_CHECK(cudaMemcpyAsync(c->tign, tign, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    WF_CHECK(cudaMemcpyAsync(c->frac[c->cur], frac, N * E, cudaMemcpyDeviceToDevice, c->stream));
+    c->t = t;
+    // the device time follows through a host-pinned-free path: synchronous copy
+    WF_CHECK(cudaMemcpyAsync(c->tdev + c->cur, &c->t, sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    return FIRE_OK;
+}
+
+int fire_status(fire_ctx *c) {
+    if (!c) return FIRE_ERR_ARG;
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    int st = 0;
+    WF_CHECK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_NONFINITE) return FIRE_ERR_NONFINITE;
+    if (st & ST_BOUNDARY) return FIRE_ERR_BOUNDARY;
+    if (st & ST_TIMEOUT) return FIRE_ERR_TIMEOUT;
+    return FIRE_OK;
+}
+
+int fire_clear_status(fire_ctx *c) {
+    if (!c) return FIRE_ERR_ARG;
+    WF_CHECK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    return FIRE_OK;
+}
+
+int fire_mesh_size(const fire_ctx *c, int *nx, int *ny) {
+    if (!c) return FIRE_ERR_ARG;
+    if (nx) *nx = c->nx;
+    if (ny) *ny = c->ny;
+    return FIRE_OK;
+}
+
+double fire_time(const fire_ctx *c) { return c ? c->t : NAN; }
+
+int fire_set_tile(fire_ctx *c, int kx, int ky) {
+    if (!c) return FIRE_ERR_ARG;
+    return configure_tile(c, kx, ky);
+}
+
+int fire_get_tile(const fire_ctx *c, int *kx, int *ky) {
+    if (!c) return FIRE_ERR_ARG;
+    if (kx) *kx = c->kx;
+    if (ky) *ky = c->ky;
+    return FIRE_OK;
+}
+
+int fire_enable_timing(fire_ctx *c, int on) {
+    if (!c) return FIRE_ERR_ARG;
+    c->timing = on != 0;
+    return FIRE_OK;
+}
+
+int fire_kernel_time_ms(fire_ctx *c, double *ms, long *launches) {
+    if (!c) return FIRE_ERR_ARG;
+    double total = c->ms_done;
+    for (size_t k = 0; k + 1 < c->ev.size(); k += 2) {
+        WF_CHECK(cudaEventSynchronize(c->ev[k + 1]));
+        float m = 0;
+        WF_CHECK(cudaEventElapsedTime(&m, c->ev[k], c->ev[k + 1]));
+        total += m;
+    }
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    if (ms) *ms = total;
+    if (launches) *launches = c->launches;
+    c->ms_done = 0;
+    c->launches = 0;
+    return FIRE_OK;
+}
+
+void fire_destroy(fire_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Host-side declarations shared by the translation units of the library.
+// (CUDA path only; nothing here is shared with the CPU oracle.)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/wrffire.h"
+
+namespace wf {
+
+// sticky device status bits
+enum { ST_BOUNDARY = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
+
+// per-class coefficient slots: eq. (spread-WRF-Fire) + T_f + heat factors
+enum { K_S0 = 0, K_R0, K_B, K_C, K_D, K_E, K_TF, K_HS, K_HQ, K_N };
+
+constexpr int kThreadsX = 32;
+constexpr int kThreadsY = 8;
+constexpr int kThreads = kThreadsX * kThreadsY;
+constexpr int kMaxSegPerLaunch = 64;
+
+// Arguments of the fused step kernel.  Element type of the void pointers is
+// the path precision T.
+struct StepArgs {
+    const void *psi_in;
+    void *psi_out;
+    const void *F_in;
+    void *F_out;
+    double *tign;
+    const uint8_t *fuel;
+    const void *dzdx, *dzdy, *mult;
+    const void *u, *v;
+    const double *coef;  // [ncls][K_N]
+    int ncls;
+    double *heat_s, *heat_l;  // nullable
+    int *status;
+    const double *t_in;  // model time at the step start (device scalar)
+    double *t_out;       // receives t_in + dt (written by one thread)
+    int nx, ny, nxa, nya, srx, sry;
+    int kx, ky;  // tile = kx*srx by ky*sry nodes
+    int band;
+    double dx, dy, eps, dt;
+};
+
+struct IgnSeg {
+    double ax, ay, bx, by;
+    double rho;      // current radius term: r_g (instantaneous) or S_g (t - t_g)
+    double tg, sg;   // start time and growth speed (sg <= 0: instantaneous)
+};
+
+struct IgniteArgs {
+    void *psi;
+    double *tign;
+    int nx, ny;
+    double dx, dy;
+    int nseg;
+    IgnSeg seg[kMaxSegPerLaunch];
+};
+
+template <typename T>
+size_t step_smem_bytes(int kx, int ky, int srx, int sry, int ncls);
+
+template <typename T>
+cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_ignite(const IgniteArgs &a, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_fill(void *psi, double *tign, void *frac, size_t n, double psi_far,
+                        cudaStream_t s);
+
+template <typename T>
+cudaError_t prepare_step_kernel(size_t smem_bytes);
+
+cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
+                                cudaStream_t s);
+
+}  // namespace wf

@@ -1,0 +1,58 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry
+point include/wrffire.h declares; argument validation answers without touching
+the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "wrffire.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fire_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1102_1343_gb300 import build
+    build.build()
+    import paper_1102_1343_gb300 as pkg
+    return pkg.load_library()
+
+
+def test_header_declares_the_abi():
+    syms = declared_symbols()
+    for s in ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_status",
+              "fire_get_state", "fire_set_state", "fire_destroy", "fire_strerror"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_1102_1343_gb300 as pkg
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+    assert set(pkg.ABI_SYMBOLS) <= set(declared_symbols())
+
+
+def test_strerror_and_argument_checks_without_gpu(lib):
+    import paper_1102_1343_gb300 as pkg
+    assert pkg.fire_strerror(pkg.FIRE_ERR_BOUNDARY).startswith("fire reached")
+    out = C.c_void_p()
+    assert lib.fire_init(C.byref(out), None, None, 0, None, None, None, None, None, None, 0,
+                         None) == pkg.FIRE_ERR_ARG
+    assert out.value is None
+    g = pkg.make_grid(10, 10, 10, 10, 60.0, 60.0)
+    cls = pkg.make_classes([{"fgi": 0.5, "weight": 7.0, "savr": 1e4, "fueldepthm": 0.3,
+                             "fueldens": 500.0, "fuelmce": 0.3, "se": 0.01}])
+    # moisture per node is not supported: rejected before any device call
+    assert lib.fire_init(C.byref(out), C.byref(g), cls, 1, 1, 1, None, 1, 1, None, 0,
+                         None) == pkg.FIRE_ERR_ARG
+    bad = pkg.make_grid(1, 1, 1, 1, 60.0, 60.0)  # a 1x1 fire mesh cannot be extrapolated
+    assert lib.fire_init(C.byref(out), C.byref(bad), cls, 1, 1, None, None, 1, 1, None, 0,
+                         None) == pkg.FIRE_ERR_ARG
+    assert lib.fire_step(None, None, None, 0.5, None, None) == pkg.FIRE_ERR_ARG
+    assert lib.fire_status(None) == pkg.FIRE_ERR_ARG

@@ -212,3 +212,43 @@ def test_circle_growth(orc, eps):
     assert np.all(np.abs(rad - r) < tol), (rad, r)
     if eps == 0.0:
         assert r == pytest.approx(r0 + S * T, rel=1e-12)
+
+
+@pytest.mark.parametrize("c_target", [0.1, 0.3, 0.5])
+def test_checkerboard_amplification_linear_theory(orc, c_target):
+    """Linear stability of eqs. (Heun), (F-disc), (Godunov) on a planar front
+    psi = x with constant S, perturbed by a checkerboard d (-1)^(i+j):
+    central differences do not see the checkerboard (n stays (1,0)), the
+    upwind x-difference adds 2 d s/dx, the scaled Laplacian -4 d s (1/dx+1/dy)
+    and the y-terms are second order, so one Euler stage multiplies the
+    checkerboard by 1 + z with z = -S dt (2/dx + 4 eps (1/dx + 1/dy)), and a
+    Heun step by 1 + z + z^2/2 (above 1 in magnitude when z < -2)."""
+    nxa, sr, dxa, eps = 6, 8, 8.0, 0.4
+    nx = nxa * sr
+    dx = dxa / sr
+    cls = synth.nominal_class(fgi=0.5)
+    S = orc.rothermel_rate(cls, 0.0, 0.0)
+    dt = c_target * dx / S
+    x = (np.arange(nx)[None, :] + 0.5) * dx + np.zeros((nx, 1))
+    s = (-1.0) ** (np.arange(nx)[None, :] + np.arange(nx)[:, None])
+    d = 1e-7 * dx
+    o, u, v = _uniform_run(orc, nxa, nxa, sr, dxa, x + 1000.0 + d * s, 0, dt, eps)
+    o.step(u, v, dt)
+    core = (slice(6, -6), slice(6, -6))
+    pert = (o.psi - (x + 1000.0 - S * dt))[core] / (d * s[core])
+    z = -S * dt * (2 / dx + 4 * eps * (1 / dx + 1 / dx))
+    assert np.allclose(pert, 1 + z + z * z / 2, rtol=1e-5, atol=1e-5)
+
+
+def test_synthetic_landscapes_within_stability_limit(orc):
+    """The random landscapes used as workloads keep the explicit scheme stable:
+    with the fastest class at the largest wind of the field and the largest
+    slope, the worst linear factor z = -c (2 sqrt 2 + 8 eps) (c = S dt/dx,
+    diagonal front) stays inside Heun's interval [-2, 0] with margin."""
+    for seed, nxa in [(synth.BASE_SEED, 200), (21, 23), (44, 32), (33, 31)]:
+        w = synth.random_landscape(nxa, nxa, seed=seed, steps=1)
+        umax = float(np.hypot(np.abs(w.u).max(), np.abs(w.v).max()))
+        smax = max(orc.rothermel_rate(c, umax, 0.4) for c in w.classes)
+        c = smax * w.dt / w.dx
+        z = -c * (2 * np.sqrt(2) + 8 * w.eps)
+        assert z > -1.5, (seed, smax, z)

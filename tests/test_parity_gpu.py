@@ -1,0 +1,295 @@
+"""GPU parity of the CUDA fire step against the FP64 oracle, through the C ABI.
+
+FP64 path: every result within 1e-10 norm-wise relative error of the oracle.
+FP32 path: ignition time within 0.1 s (nodes ignited in both), burnt area
+within 0.5 %, integrated heat within 1e-4 relative (multi-step runs); one-step
+results from a shared state within bounds derived from FP32 rounding.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import as_path_precision, compare_fp64, crop_step, rel_inf, state_np
+from paper_1102_1343_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    from paper_1102_1343_gb300 import build
+    build.build()
+    import paper_1102_1343_gb300 as p
+    p.load_library()
+    assert torch.cuda.is_available()
+    return p
+
+
+def run_pair(pkg, w, prec, steps=None, tile=None, check_every=None, heat_tol=1e-10):
+    """Run the CUDA path and the oracle side by side; returns both and the
+    worst per-step heat error and the integrated heats."""
+    import torch
+    steps = w.steps if steps is None else steps
+    wp = as_path_precision(w, prec)
+    orc = oracle.OracleFire.from_workload(wp)
+    m = pkg.FireModel.from_workload(w, precision=prec)
+    if tile:
+        pkg.fire_set_tile(m.ctx, *tile)
+    u, v = m.wind(w.u, w.v)
+    worst = 0.0
+    Qg = Qo = 0.0
+    area = w.dx_atm * w.dy_atm
+    for n in range(steps):
+        hs, hl = m.step(u, v, w.dt)
+        hs_o, hl_o, _ = orc.step(wp.u, wp.v, w.dt)
+        hs_g = hs.cpu().numpy()
+        hl_g = hl.cpu().numpy()
+        worst = max(worst, rel_inf(hs_g, hs_o), rel_inf(hl_g, hl_o))
+        Qg += hs_g.sum() * w.dt * area
+        Qo += hs_o.sum() * w.dt * area
+    torch.cuda.synchronize()
+    return m, orc, worst, Qg, Qo
+
+
+# ---------------------------------------------------------------------------
+# FP64: 1e-10
+# ---------------------------------------------------------------------------
+
+def test_fp64_plain_circle(pkg):
+    """100x100 FP64 circle, constant wind 3 m/s, 120 steps of 0.5 s."""
+    w = synth.plain_circle()
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64")
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    assert Qo > 0 and abs(Qg - Qo) <= 1e-10 * Qo
+    assert m.status() == pkg.FIRE_OK
+
+
+@pytest.mark.parametrize("tile", [None, (1, 1), (3, 2), (5, 3)])
+def test_fp64_landscape_ragged_tiles(pkg, tile):
+    """Hills, 13 fuels, smooth wind, line ignition on 230x170 nodes: several
+    tiles with a ragged last row and column of tiles."""
+    w = synth.random_landscape(23, 17, seed=21, ignition="line", steps=120)
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    assert Qo > 0
+
+
+def test_fp64_anisotropic_multiplier_and_segments(pkg):
+    """Refinement 4 x 6 with unequal atmos spacing, a per-node spread
+    multiplier, a growing segment ignition and a delayed instantaneous one."""
+    w = synth.random_landscape(31, 19, sr=5, seed=33, ignition="center", steps=90)
+    nx, ny = 31 * 4, 19 * 6
+    zx, zy = synth.hills_gradient(np.random.default_rng(3), nx, ny, 10.0, 9.0)
+    w = dataclasses.replace(w, srx=4, sry=6, dx_atm=40.0, dy_atm=54.0,
+                            fuel=synth.voronoi_fuel(np.random.default_rng(1), nx, ny, 10.0),
+                            dzdx=zx, dzdy=zy)
+    rng = np.random.default_rng(2)
+    w.mult = rng.uniform(0.5, 1.5, (ny, nx))
+    w.ignitions = [synth.line_ignition(200.0, 300.0, 330.0, 420.0, radius=12.0, t_start=1.0,
+                                       speed=0.8),
+                   synth.point_ignition(600.0, 250.0, radius=9.0, t_start=7.25),
+                   synth.point_ignition(300.0, 700.0, radius=15.0)]
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64")
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+
+
+def test_fp64_chaparral(pkg):
+    """The chaparral rate of eq. (chapparal) (6 m/s in a wind above 4.6 m/s)
+    with a time step inside the scheme's stability limit (c = S dt/dx = 0.2)."""
+    w = synth.random_landscape(20, 16, seed=77, ignition="center", steps=100, dt=0.2)
+    w.classes = synth.random_classes(np.random.default_rng(78), chaparral_index=3)
+    jj, ii = np.nonzero(w.fuel[40:-40, 40:-40] == 3)
+    k = len(jj) // 2
+    w.ignitions = [synth.point_ignition((ii[k] + 40.5) * w.dx, (jj[k] + 40.5) * w.dy, 10.0)]
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64")
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# FP32: ignition time 0.1 s, burnt area 0.5 %, integrated heat 1e-4
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["line", "points"])
+def test_fp32_against_fp64_oracle(pkg, case):
+    w = synth.random_landscape(32, 26, seed=44, ignition=case, n_points=6, edge_margin=300.0,
+                               steps=300)
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp32")
+    psi, tign, frac, _ = state_np(m)
+    both = np.isfinite(tign) & np.isfinite(orc.tign)
+    assert both.sum() > 100
+    dti = np.abs(tign[both] - orc.tign[both]).max()
+    A, Ao = (psi <= 0).sum(), (orc.psi <= 0).sum()
+    B, Bo = (1 - frac).sum(), (1 - orc.frac).sum()
+    errs = dict(tign_max_s=dti, area=abs(A - Ao) / Ao, burned=abs(B - Bo) / Bo,
+                heat=abs(Qg - Qo) / Qo)
+    print("fp32 errors vs fp64 oracle:", errs)
+    assert dti <= 0.1, errs
+    assert errs["area"] <= 0.005 and errs["burned"] <= 0.005, errs
+    assert errs["heat"] <= 1e-4, errs
+
+
+# ---------------------------------------------------------------------------
+# faults, equivalences of the entry points
+# ---------------------------------------------------------------------------
+
+def test_boundary_and_nonfinite_status(pkg):
+    w = synth.plain_circle(steps=2)
+    w.ignitions = [synth.point_ignition(3.0, 300.0, radius=8.0)]
+    m = pkg.FireModel.from_workload(w, precision="fp32")
+    u, v = m.wind(w.u, w.v)
+    m.step(u, v, w.dt)
+    assert m.status() == pkg.FIRE_ERR_BOUNDARY
+    pkg.fire_clear_status(m.ctx)
+    assert m.status() == pkg.FIRE_OK
+    w2 = synth.plain_circle(steps=1)
+    m2 = pkg.FireModel.from_workload(w2, precision="fp64")
+    uu = w2.u.copy()
+    uu[3, 4] = np.nan
+    u2, v2 = m2.wind(uu, w2.v)
+    m2.step(u2, v2, w2.dt)
+    assert m2.status() == pkg.FIRE_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_run_graph_and_host_path_equal_steps(pkg, prec):
+    """fire_run (graph replay) and fire_step_host give the same bits as a
+    sequence of fire_step calls."""
+    import torch
+    w = synth.random_landscape(12, 9, seed=5, ignition="center", steps=15)
+    a = pkg.FireModel.from_workload(w, precision=prec)
+    b = pkg.FireModel.from_workload(w, precision=prec)
+    c = pkg.FireModel.from_workload(w, precision=prec)
+    u, v = a.wind(w.u, w.v)
+    for _ in range(w.steps):
+        hs_a, hl_a = a.step(u, v, w.dt)
+    hs_b, hl_b = b.run(w.steps, u, v, w.dt)
+    dt_np = np.float64 if prec == "fp64" else np.float32
+    uh = np.ascontiguousarray(w.u, dt_np)
+    vh = np.ascontiguousarray(w.v, dt_np)
+    hs_c = np.zeros((w.nya, w.nxa))
+    hl_c = np.zeros((w.nya, w.nxa))
+    for _ in range(w.steps):
+        pkg.fire_step_host(c.ctx, uh, vh, w.dt, hs_c, hl_c)
+    torch.cuda.synchronize()
+    sa, sb, sc = state_np(a), state_np(b), state_np(c)
+    for x, y in ((sa, sb), (sa, sc)):
+        for k in range(3):
+            assert np.array_equal(x[k], y[k])
+        assert x[3] == y[3]
+    assert np.array_equal(hs_a.cpu().numpy(), hs_b.cpu().numpy())
+    assert np.array_equal(hs_a.cpu().numpy(), hs_c)
+    assert np.array_equal(hl_a.cpu().numpy(), hl_c)
+
+
+def test_checkpoint_resume(pkg):
+    """get_state / set_state: a resumed run continues with the same bits."""
+    import torch
+    w = synth.random_landscape(12, 9, seed=6, ignition="center", steps=10)
+    a = pkg.FireModel.from_workload(w, precision="fp32")
+    u, v = a.wind(w.u, w.v)
+    for _ in range(5):
+        a.step(u, v, w.dt)
+    ck = a.state()
+    ck = tuple(x.clone() if hasattr(x, "clone") else x for x in ck)
+    for _ in range(5):
+        a.step(u, v, w.dt)
+    b = pkg.FireModel.from_workload(w, precision="fp32")
+    b.set_state(*ck)
+    for _ in range(5):
+        b.step(u, v, w.dt)
+    torch.cuda.synchronize()
+    sa, sb = state_np(a), state_np(b)
+    for k in range(3):
+        assert np.array_equal(sa[k], sb[k])
+    assert sa[3] == sb[3]
+
+
+# ---------------------------------------------------------------------------
+# full-size meshes: one step from the GPU's own state, sampled atmos cells
+# recomputed by the oracle on crops
+# ---------------------------------------------------------------------------
+
+def _sample_cells(w, rng, n_random, near):
+    cells = set()
+    for g in w.ignitions:
+        I = int(g["ax"] / w.dx_atm)
+        J = int(g["ay"] / w.dy_atm)
+        for dI in (-1, 0, 1):
+            for dJ in (-1, 0, 1):
+                cells.add((I + dI, J + dJ))
+        if len(cells) >= near:
+            break
+    while len(cells) < near + n_random:
+        cells.add((int(rng.integers(1, w.nxa - 1)), int(rng.integers(1, w.nya - 1))))
+    return [(I, J) for I, J in cells if 1 <= I < w.nxa - 1 and 1 <= J < w.nya - 1]
+
+
+@pytest.mark.parametrize("name,prec,warm", [("line2000", "fp64", 60), ("line2000", "fp32", 200),
+                                            ("points8200", "fp32", 200)])
+def test_full_size_sampled_cells(pkg, name, prec, warm):
+    """The 2000x2000 line-fire mesh (FP64 and FP32) and the 8200x8200
+    50-point mesh (FP32) in the tile shape the benchmark uses: after `warm`
+    steps, one more GPU step is compared on sampled atmospheric cells (around
+    the ignitions and at random) with the oracle run on 3x3-cell crops from the
+    same state."""
+    import torch
+    w = synth.line_fire_2000() if name == "line2000" else synth.points_fire_8200()
+    wp = as_path_precision(w, prec)
+    m = pkg.FireModel.from_workload(w, precision=prec)
+    u, v = m.wind(w.u, w.v)
+    m.run(warm, u, v, w.dt)
+    psi0, tign0, frac0, t0 = state_np(m)
+    hs, hl = m.step(u, v, w.dt)
+    torch.cuda.synchronize()
+    psi1, tign1, frac1, _ = state_np(m)
+    hs = hs.cpu().numpy()
+    hl = hl.cpu().numpy()
+    assert m.status() == pkg.FIRE_OK
+    rng = np.random.default_rng(9)
+    cells = _sample_cells(w, rng, n_random=24, near=36)
+    Hs_max = max(oracle.fuel_coefficients(c)[7] for c in w.classes)
+    Hq_max = max(oracle.fuel_coefficients(c)[8] for c in w.classes)
+    burning_cells = 0
+    for I, J in cells:
+        sub, hs_o, hl_o, (cy, cx), (ys, xs) = crop_step(wp, psi0, tign0, frac0, t0, I, J, w.dt)
+        pg = psi1[ys, xs][cy, cx]
+        fg = frac1[ys, xs][cy, cx]
+        tg = tign1[ys, xs][cy, cx]
+        po, fo, to = sub.psi[cy, cx], sub.frac[cy, cx], sub.tign[cy, cx]
+        if (po <= 0).any():
+            burning_cells += 1
+        if prec == "fp64":
+            scale = max(np.abs(psi0[ys, xs]).max(), 1.0)
+            assert np.abs(pg - po).max() <= 1e-10 * scale
+            assert np.abs(fg - fo).max() <= 1e-10
+            assert np.array_equal(np.isfinite(tg), np.isfinite(to))
+            f = np.isfinite(to)
+            assert np.abs(tg[f] - to[f]).max(initial=0) <= 1e-10 * max(1.0, t0)
+            assert abs(hs[J, I] - hs_o) <= 1e-10 * max(abs(hs_o), 1.0)
+            assert abs(hl[J, I] - hl_o) <= 1e-10 * max(abs(hl_o), 1.0)
+        else:
+            # FP32 rounding of psi (relative 6e-8), of the spread rate
+            # (fast pow/exp, ~1e-6) over one step
+            tol_psi = 2e-6 * (1.0 + np.abs(po))
+            assert np.all(np.abs(pg - po) <= tol_psi)
+            # crossings may differ only where psi^{n+1} is within rounding of 0
+            diff = np.isfinite(tg) != np.isfinite(to)
+            assert np.all(np.abs(po[diff]) <= tol_psi[diff])
+            f = np.isfinite(tg) & np.isfinite(to)
+            assert np.abs(tg[f] - to[f]).max(initial=0) <= 1e-2
+            assert np.abs(fg - fo).max() <= 1e-4
+            # heat: per-node F error bound times the largest heat factor / dt
+            assert abs(hs[J, I] - hs_o) <= 1e-4 * Hs_max / w.dt
+            assert abs(hl[J, I] - hl_o) <= 1e-4 * Hq_max / w.dt
+    assert burning_cells >= 4
