@@ -44,10 +44,11 @@ UNIT = "cell-steps/s"
 # algorithmic bytes per cell-step of the one-pass FP32 step: psi r/w 4+4,
 # F r/w 4+4, ignition time read 8, fuel class 1, terrain gradient 8
 BYTES_PER_CELL_STEP = {"fp32": 33, "fp64": 57}
-KERNEL_SOURCES = ["paper_1102_1343_gb300/csrc/step_kernel.cuh",
+KERNEL_SOURCES = ["paper_1102_1343_gb300/csrc/march_kernel.cuh",
+                  "paper_1102_1343_gb300/csrc/fire_device.cuh",
                   "paper_1102_1343_gb300/csrc/fire_internal.h",
                   "paper_1102_1343_gb300/csrc/step_f32.cu"]
-PROFILE_SUMMARY = "profiles/fire_step_f32_points8200.md"
+PROFILE_SUMMARY = "profiles/fire_march_f32_points8200.md"
 
 
 def kernel_hash() -> str:
@@ -262,9 +263,9 @@ def run_gpu(args, rank, world):
     cells = w.nx * w.ny
     prec = args.precision
     m = pkg.FireModel.from_workload(w, precision=prec, device=dev)
-    if args.tile:
-        pkg.fire_set_tile(m.ctx, *args.tile)
-    tile = pkg.fire_get_tile(m.ctx)
+    if args.kernel:
+        pkg.fire_set_kernel(m.ctx, *args.kernel)
+    kernel = pkg.fire_get_kernel(m.ctx)
     u, v = m.wind(w.u, w.v)
     stream = torch.cuda.current_stream(dev)
 
@@ -365,13 +366,16 @@ def run_gpu(args, rank, world):
                        "refinement": [w.srx, w.sry], "precision": prec,
                        "state_in_hbm": "yes; state 2.2 GB > L2, no flush needed"
                        if args.workload == "points8200" else "yes",
-                       "tile_atmos_cells": list(tile), "parallelism": f"replicas x{world}"},
+                       "kernel": {"variant": ["tile", "march"][kernel[0]],
+                                  "tile_atmos_cells": list(kernel[1:])},
+                       "parallelism": f"replicas x{world}"},
             "gpu_launches": args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_fire_step<float>", "kernel_ms": k_avg,
+                         "kernel": ["k_fire_step<float>", "k_fire_march<float>"][kernel[0]],
+                         "kernel_ms": k_avg,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "cpu_baseline": cpu,
@@ -391,7 +395,9 @@ def main():
     ap.add_argument("--workload", choices=["points8200", "line2000", "circle100"],
                     default="points8200")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--tile", type=int, nargs=2, default=None)
+    ap.add_argument("--kernel", type=int, nargs=3, default=None,
+                    metavar=("VARIANT", "KX", "KY"),
+                    help="step kernel: 0 = 2-D tile, 1 = column march; tile in atmos cells")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -196,11 +196,16 @@ int fire_clear_status(fire_ctx *ctx);
 int fire_mesh_size(const fire_ctx *ctx, int *nx, int *ny);
 double fire_time(const fire_ctx *ctx);
 
-/* Tile shape of the fused step kernel in atmospheric cells per CTA
- * (tile = kx*sr_x by ky*sr_y fire nodes); chosen by the autotuner, settable
- * for sweeps.  FIRE_ERR_ARG if the shared-memory footprint does not fit. */
-int fire_set_tile(fire_ctx *ctx, int kx, int ky);
-int fire_get_tile(const fire_ctx *ctx, int *kx, int *ky);
+/* Step-kernel variant and its tile shape, in atmospheric cells per CTA
+ * (chosen by fire_init's defaults or the autotuner, settable for sweeps):
+ *   FIRE_KERNEL_MARCH  one thread per fire column marching down a strip of
+ *                      kx*sr_x columns (kx*sr_x <= 120) and ky*sr_y rows;
+ *   FIRE_KERNEL_TILE   a 2-D tile of kx*sr_x by ky*sr_y nodes staged with
+ *                      a 3-node halo in shared memory (any refinement).
+ * FIRE_ERR_ARG if the shape does not fit the variant or the device. */
+enum fire_kernel_variant { FIRE_KERNEL_TILE = 0, FIRE_KERNEL_MARCH = 1 };
+int fire_set_kernel(fire_ctx *ctx, int variant, int kx, int ky);
+int fire_get_kernel(const fire_ctx *ctx, int *variant, int *kx, int *ky);
 
 /* Kernel timing: when enabled, CUDA events bracket every launch of the fused
  * step kernel on the context's stream; fire_kernel_time_ms waits for them and

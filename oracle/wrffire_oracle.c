@@ -60,6 +60,7 @@ enum { CO_S0 = 0, CO_R0, CO_B, CO_C, CO_D, CO_E, CO_TF, CO_HS, CO_HQ, CO_N };
 #define J_PER_BTU  1055.05585262
 #define LATENT_L   2.5e6          /* L, J/kg, Sect. "Fuel burned and heat released" */
 #define WIND_MAX   30.0           /* CAWFE wind limit, caption of Table 2 */
+#define ORC_GRAD_ZERO 1e-9        /* relative rounding level of a central difference */
 
 
 /* Rothermel quantities that do not depend on wind or slope (Table 2).
@@ -309,7 +310,12 @@ void orc_wind_at_nodes(int nxa, int nya, int srx, int sry,
  * level-set function ext ((nx+2) x (ny+2)).
  *   - one-sided differences D+-x, D+-y and the Godunov selection eq. (Godunov);
  *   - the normal n from central differences (paragraph after eq. Godunov),
- *     n = 0 where the central gradient vanishes (reading: silent);
+ *     n = 0 where the central gradient vanishes (reading: silent).  Reading:
+ *     a central difference psi_{i+1} - psi_{i-1} at the rounding level of its
+ *     two values (|diff| <= 1e-9 (|psi_{i+1}| + |psi_{i-1}|)) counts as zero,
+ *     so that rounding noise at a symmetric point does not pick a direction
+ *     for n (the spread rate, and through the viscosity the level set, jumps
+ *     with that direction);
  *   - U = wind . n, tan(phi) = grad z . n, S from eq. (spread-WRF-Fire),
  *     times the optional per-node spread multiplier m;
  *   - the scaled Laplacian D+x - D-x + D+y - D-y;
@@ -331,8 +337,11 @@ void orc_rhs(int nx, int ny, double dx, double dy, double eps,
             double dym = (p - pd) / dy, dyp = (pu - p) / dy;
             double gx = orc_godunov(dxm, dxp);
             double gy = orc_godunov(dym, dyp);
-            double cx = (pr - pl) / (2.0 * dx);
-            double cy = (pu - pd) / (2.0 * dy);
+            double ax = pr - pl, ay = pu - pd;
+            if (fabs(ax) <= ORC_GRAD_ZERO * (fabs(pr) + fabs(pl))) ax = 0.0;
+            if (fabs(ay) <= ORC_GRAD_ZERO * (fabs(pu) + fabs(pd))) ay = 0.0;
+            double cx = ax / (2.0 * dx);
+            double cy = ay / (2.0 * dy);
             double cn = sqrt(cx * cx + cy * cy);
             double nxv = 0.0, nyv = 0.0;
             if (cn > 0.0) { nxv = cx / cn; nyv = cy / cn; }

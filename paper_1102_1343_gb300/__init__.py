@@ -31,13 +31,15 @@ FIRE_ERR_BOUNDARY = -4
 FIRE_ERR_NONFINITE = -5
 FIRE_ERR_TIMEOUT = -6
 FIRE_ERR_STATE = -7
+FIRE_KERNEL_TILE = 0
+FIRE_KERNEL_MARCH = 1
 FIRE_MAX_CLASSES = 64
 FIRE_MAX_IGNITIONS = 256
 
 # every entry point the header declares (checked by the ABI test)
 ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get_state",
                "fire_set_state", "fire_status", "fire_clear_status", "fire_mesh_size",
-               "fire_time", "fire_set_tile", "fire_get_tile", "fire_enable_timing",
+               "fire_time", "fire_set_kernel", "fire_get_kernel", "fire_enable_timing",
                "fire_kernel_time_ms", "fire_strerror", "fire_destroy")
 
 
@@ -93,8 +95,8 @@ def load_library(path: str | None = None):
     L.fire_mesh_size.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.fire_time.argtypes = [_P]
     L.fire_time.restype = C.c_double
-    L.fire_set_tile.argtypes = [_P, C.c_int, C.c_int]
-    L.fire_get_tile.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fire_set_kernel.argtypes = [_P, C.c_int, C.c_int, C.c_int]
+    L.fire_get_kernel.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.fire_enable_timing.argtypes = [_P, C.c_int]
     L.fire_kernel_time_ms.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_long)]
     L.fire_strerror.argtypes = [C.c_int]
@@ -106,7 +108,7 @@ def load_library(path: str | None = None):
         if f.restype is C.c_int or name in ("fire_init", "fire_step", "fire_step_host",
                                              "fire_run", "fire_get_state", "fire_set_state",
                                              "fire_status", "fire_clear_status",
-                                             "fire_mesh_size", "fire_set_tile", "fire_get_tile",
+                                             "fire_mesh_size", "fire_set_kernel", "fire_get_kernel",
                                              "fire_enable_timing", "fire_kernel_time_ms"):
             f.restype = C.c_int
     _lib = L
@@ -232,14 +234,16 @@ def fire_time(ctx) -> float:
     return load_library().fire_time(ctx)
 
 
-def fire_set_tile(ctx, kx, ky) -> int:
-    return _check(load_library().fire_set_tile(ctx, int(kx), int(ky)), "fire_set_tile")
+def fire_set_kernel(ctx, variant, kx, ky) -> int:
+    return _check(load_library().fire_set_kernel(ctx, int(variant), int(kx), int(ky)),
+                  "fire_set_kernel")
 
 
-def fire_get_tile(ctx):
-    kx, ky = C.c_int(), C.c_int()
-    _check(load_library().fire_get_tile(ctx, C.byref(kx), C.byref(ky)), "fire_get_tile")
-    return kx.value, ky.value
+def fire_get_kernel(ctx):
+    v, kx, ky = C.c_int(), C.c_int(), C.c_int()
+    _check(load_library().fire_get_kernel(ctx, C.byref(v), C.byref(kx), C.byref(ky)),
+           "fire_get_kernel")
+    return v.value, kx.value, ky.value
 
 
 def fire_enable_timing(ctx, on=True) -> int:

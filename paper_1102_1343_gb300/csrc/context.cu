@@ -40,6 +40,7 @@ struct fire_ctx {
     std::vector<fire_ignition> ign;
     std::vector<unsigned char> applied;
 
+    int variant = FIRE_KERNEL_MARCH;
     int kx = 0, ky = 0;
     size_t smem = 0;
     size_t smem_max = 0;
@@ -53,7 +54,7 @@ struct fire_ctx {
     const void *g_u = nullptr, *g_v = nullptr;
     double g_dt = 0;
     double *g_hs = nullptr, *g_hl = nullptr;
-    int g_kx = 0, g_ky = 0;
+    int g_kx = 0, g_ky = 0, g_variant = -1;
 
     // timing
     bool timing = false;
@@ -130,9 +131,10 @@ int step_kernel_args(fire_ctx *c, const void *u, const void *v, double dt, doubl
     return FIRE_OK;
 }
 
-cudaError_t launch_step_prec(fire_ctx *c, const StepArgs &a) {
-    return c->prec == FIRE_FP64 ? launch_step<double>(a, c->stream)
-                                : launch_step<float>(a, c->stream);
+cudaError_t launch_variant(const fire_ctx *c, const StepArgs &a, cudaStream_t s) {
+    if (c->variant == FIRE_KERNEL_MARCH)
+        return c->prec == FIRE_FP64 ? launch_march<double>(a, s) : launch_march<float>(a, s);
+    return c->prec == FIRE_FP64 ? launch_step<double>(a, s) : launch_step<float>(a, s);
 }
 
 // Ignitions active at a step starting at time t (Sect. 3.4), in list order.
@@ -189,30 +191,49 @@ int record_event(fire_ctx *c) {
     return FIRE_OK;
 }
 
-int configure_tile(fire_ctx *c, int kx, int ky) {
+int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
     if (kx < 1 || ky < 1) return FIRE_ERR_ARG;
-    size_t sm = c->prec == FIRE_FP64
-                    ? step_smem_bytes<double>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls)
-                    : step_smem_bytes<float>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls);
-    if (sm > c->smem_max) return FIRE_ERR_ARG;
-    cudaError_t e = c->prec == FIRE_FP64 ? prepare_step_kernel<double>(sm)
-                                         : prepare_step_kernel<float>(sm);
+    size_t sm;
+    cudaError_t e;
+    if (variant == FIRE_KERNEL_MARCH) {
+        if (kx * c->g.sr_x > kMarchMaxColumns) return FIRE_ERR_ARG;
+        sm = c->prec == FIRE_FP64 ? march_smem_bytes<double>(ky, c->g.sr_y)
+                                  : march_smem_bytes<float>(ky, c->g.sr_y);
+        if (sm + 48 * 1024 > c->smem_max) return FIRE_ERR_ARG;
+        e = c->prec == FIRE_FP64 ? prepare_march_kernel<double>(sm) : prepare_march_kernel<float>(sm);
+    } else if (variant == FIRE_KERNEL_TILE) {
+        sm = c->prec == FIRE_FP64 ? step_smem_bytes<double>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls)
+                                  : step_smem_bytes<float>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls);
+        if (sm > c->smem_max) return FIRE_ERR_ARG;
+        e = c->prec == FIRE_FP64 ? prepare_step_kernel<double>(sm) : prepare_step_kernel<float>(sm);
+    } else {
+        return FIRE_ERR_ARG;
+    }
     WF_CHECK(e);
+    c->variant = variant;
     c->kx = kx;
     c->ky = ky;
     c->smem = sm;
     return FIRE_OK;
 }
 
-int default_tile(fire_ctx *c) {
-    // about 80 x 40 fire nodes for FP32 and 40 x 40 for FP64, whole atmos cells
+int default_kernel(fire_ctx *c) {
+    // marching strips of up to 120 columns x ~200 rows when the refinement
+    // allows; else 2-D tiles of ~80 x 40 (FP32) / 40 x 40 (FP64) nodes
+    if (c->g.sr_x <= kMarchMaxColumns) {
+        int kx = kMarchMaxColumns / c->g.sr_x, ky = 200 / c->g.sr_y;
+        if (kx > c->g.nx_atm) kx = c->g.nx_atm;
+        if (ky < 1) ky = 1;
+        if (ky > c->g.ny_atm) ky = c->g.ny_atm;
+        if (configure_kernel(c, FIRE_KERNEL_MARCH, kx, ky) == FIRE_OK) return FIRE_OK;
+    }
     int tx = c->prec == FIRE_FP64 ? 40 : 80, tyy = 40;
     int kx = tx / c->g.sr_x, ky = tyy / c->g.sr_y;
     if (kx < 1) kx = 1;
     if (ky < 1) ky = 1;
     if (kx > c->g.nx_atm) kx = c->g.nx_atm;
     if (ky > c->g.ny_atm) ky = c->g.ny_atm;
-    while (configure_tile(c, kx, ky) != FIRE_OK) {
+    while (configure_kernel(c, FIRE_KERNEL_TILE, kx, ky) != FIRE_OK) {
         if (kx == 1 && ky == 1) return FIRE_ERR_ARG;
         if (kx >= ky && kx > 1) kx = (kx + 1) / 2;
         else ky = (ky + 1) / 2;
@@ -233,7 +254,7 @@ int one_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, d
         int r = record_event(c);
         if (r) return r;
     }
-    WF_CHECK(launch_step_prec(c, a));
+    WF_CHECK(launch_variant(c, a, c->stream));
     if (c->timing) {
         int r = record_event(c);
         if (r) return r;
@@ -376,7 +397,7 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
             return r;
         }
     }
-    r = default_tile(c);
+    r = default_kernel(c);
     if (r) {
         release(c);
         return r;
@@ -439,7 +460,7 @@ int fire_run(fire_ctx *c, int nsteps, double dt, const void *u, const void *v, d
             continue;
         }
         if (!c->graph || c->g_u != u || c->g_v != v || c->g_dt != dt || c->g_hs != hs ||
-            c->g_hl != hl || c->g_kx != c->kx || c->g_ky != c->ky) {
+            c->g_hl != hl || c->g_kx != c->kx || c->g_ky != c->ky || c->g_variant != c->variant) {
             if (c->graph) {
                 cudaGraphExecDestroy(c->graph);
                 c->graph = nullptr;
@@ -458,7 +479,7 @@ int fire_run(fire_ctx *c, int nsteps, double dt, const void *u, const void *v, d
                     a.F_out = c->frac[1 - h];
                     a.t_in = c->tdev + h;
                     a.t_out = c->tdev + (1 - h);
-                    e = c->prec == FIRE_FP64 ? launch_step<double>(a, cs) : launch_step<float>(a, cs);
+                    e = launch_variant(c, a, cs);
                 }
                 cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
                 if (e == cudaSuccess) e = e2;
@@ -474,6 +495,7 @@ int fire_run(fire_ctx *c, int nsteps, double dt, const void *u, const void *v, d
             c->g_hl = hl;
             c->g_kx = c->kx;
             c->g_ky = c->ky;
+            c->g_variant = c->variant;
         }
         WF_CHECK(cudaGraphLaunch(c->graph, c->stream));
         c->t = c->t + dt;
@@ -534,13 +556,14 @@ int fire_mesh_size(const fire_ctx *c, int *nx, int *ny) {
 
 double fire_time(const fire_ctx *c) { return c ? c->t : NAN; }
 
-int fire_set_tile(fire_ctx *c, int kx, int ky) {
+int fire_set_kernel(fire_ctx *c, int variant, int kx, int ky) {
     if (!c) return FIRE_ERR_ARG;
-    return configure_tile(c, kx, ky);
+    return configure_kernel(c, variant, kx, ky);
 }
 
-int fire_get_tile(const fire_ctx *c, int *kx, int *ky) {
+int fire_get_kernel(const fire_ctx *c, int *variant, int *kx, int *ky) {
     if (!c) return FIRE_ERR_ARG;
+    if (variant) *variant = c->variant;
     if (kx) *kx = c->kx;
     if (ky) *ky = c->ky;
     return FIRE_OK;

@@ -1,0 +1,207 @@
+// Device functions shared by the fire-step kernels: precision-dependent
+// math, the extrapolated ghost value, the spread rate of eq.
+// (spread-WRF-Fire), the bilinear wind interpolation and the right-hand side
+// of eq. (F-disc).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fire_internal.h"
+
+namespace wf {
+
+// ---------------------------------------------------------------------------
+// precision-dependent math.  FP32: hardware approximations (the FP32 path is
+// judged on ignition time, burnt area and total heat, not ulps); FP64: the
+// IEEE operations the plain formulas name.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Mth;
+
+template <>
+struct Mth<float> {
+    static constexpr float kGradZero = 1e-6f;
+    static __device__ __forceinline__ float pw(float x, float b) { return __powf(x, b); }
+    static __device__ __forceinline__ float ex(float x) { return __expf(x); }
+    static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float sqr(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+    // unit vector of (cx, cy); zero vector when the norm vanishes
+    static __device__ __forceinline__ void unit(float cx, float cy, float &nx, float &ny) {
+        float n2 = cx * cx + cy * cy;
+        float r = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+        nx = cx * r;
+        ny = cy * r;
+    }
+};
+
+template <>
+struct Mth<double> {
+    static constexpr double kGradZero = 1e-9;
+    static __device__ __forceinline__ double pw(double x, double b) { return pow(x, b); }
+    static __device__ __forceinline__ double ex(double x) { return exp(x); }
+    static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
+    static __device__ __forceinline__ void unit(double cx, double cy, double &nx, double &ny) {
+        double n = sqrt(cx * cx + cy * cy);
+        if (n > 0.0) {
+            nx = cx / n;
+            ny = cy / n;
+        } else {
+            nx = 0.0;
+            ny = 0.0;
+        }
+    }
+};
+
+// extrapolated ghost value beyond the last node p0 (p1 the one before it),
+// Sect. 3.1: max{p0 + (p0 - p1), p0, p1}
+template <typename T>
+__device__ __forceinline__ T ghost_value(T p0, T p1) {
+    T g = p0 + (p0 - p1);
+    g = p0 > g ? p0 : g;
+    g = p1 > g ? p1 : g;
+    return g;
+}
+
+// eq. (spread-WRF-Fire): S = max{S0, R0 + c min{e, max{0,U}}^b + d max{0,tan}^2}
+template <typename T>
+__device__ __forceinline__ T spread_rate(const T *co, T U, T tanphi) {
+    T Up = U > T(0) ? U : T(0);
+    T Ue = Up < co[K_E] ? Up : co[K_E];
+    T tp = tanphi > T(0) ? tanphi : T(0);
+    T s = co[K_R0] + co[K_C] * Mth<T>::pw(Ue, co[K_B]) + co[K_D] * tp * tp;
+    return s > co[K_S0] ? s : co[K_S0];
+}
+
+// bilinear weights on points 0..n-1 at coordinate f, clamped to the end points
+template <typename T>
+__device__ __forceinline__ void lin_idx(T f, int n, int &k0, int &k1, T &w) {
+    if (n == 1) {
+        k0 = k1 = 0;
+        w = T(0);
+        return;
+    }
+    f = f < T(0) ? T(0) : f;
+    f = f > T(n - 1) ? T(n - 1) : f;
+    int k = (int)floor(f);
+    k = k > n - 2 ? n - 2 : k;
+    k = k < 0 ? 0 : k;
+    k0 = k;
+    k1 = k + 1;
+    w = f - T(k);
+}
+
+// horizontal bilinear interpolation of the staggered wind to fire node
+// (gx, gy) (Sect. 5, wind paragraph): u at (I, J+1/2), v at (I+1/2, J)
+template <typename T>
+__device__ __forceinline__ void wind_at(const T *__restrict__ u, const T *__restrict__ v,
+                                        int nxa, int nya, int srx, int sry, int gx, int gy,
+                                        T &un, T &vn) {
+    T xa = (T(gx) + T(0.5)) / T(srx);
+    T ya = (T(gy) + T(0.5)) / T(sry);
+    int i0, i1, j0, j1;
+    T wx, wy;
+    lin_idx<T>(xa, nxa + 1, i0, i1, wx);
+    lin_idx<T>(ya - T(0.5), nya, j0, j1, wy);
+    const T *r0 = u + (size_t)j0 * (nxa + 1);
+    const T *r1 = u + (size_t)j1 * (nxa + 1);
+    un = (T(1) - wy) * ((T(1) - wx) * __ldg(r0 + i0) + wx * __ldg(r0 + i1)) +
+         wy * ((T(1) - wx) * __ldg(r1 + i0) + wx * __ldg(r1 + i1));
+    lin_idx<T>(xa - T(0.5), nxa, i0, i1, wx);
+    lin_idx<T>(ya, nya + 1, j0, j1, wy);
+    r0 = v + (size_t)j0 * nxa;
+    r1 = v + (size_t)j1 * nxa;
+    vn = (T(1) - wy) * ((T(1) - wx) * __ldg(r0 + i0) + wx * __ldg(r0 + i1)) +
+         wy * ((T(1) - wx) * __ldg(r1 + i0) + wx * __ldg(r1 + i1));
+}
+
+// Right-hand side of eq. (F-disc) at a node from its value p and its four
+// neighbours (left, right, down, up): Godunov upwinded norm (eq. Godunov; its
+// square is max(max(D-,0)^2, min(D+,0)^2)), normal from central differences,
+// spread rate from the normal wind and slope, scaled Laplacian, viscosity
+// eps*S*Lap.
+template <typename T>
+__device__ __forceinline__ T rhs_vals(T p, T pl, T pr, T pd, T pu, T idx, T idy, T i2dx, T i2dy,
+                                      T eps, const T *co, T m, T un, T vn, T zx, T zy) {
+    T dxm = (p - pl) * idx, dxp = (pr - p) * idx;
+    T dym = (p - pd) * idy, dyp = (pu - p) * idy;
+    T ax = dxm > T(0) ? dxm : T(0), bx = dxp < T(0) ? dxp : T(0);
+    T ay = dym > T(0) ? dym : T(0), by = dyp < T(0) ? dyp : T(0);
+    T gx2 = ax * ax > bx * bx ? ax * ax : bx * bx;
+    T gy2 = ay * ay > by * by ? ay * ay : by * by;
+    // a central difference at the rounding level of its two values counts
+    // as zero: rounding noise at a symmetric point must not pick the normal
+    T ddx = pr - pl, ddy = pu - pd;
+    ddx = fabs(ddx) <= Mth<T>::kGradZero * (fabs(pr) + fabs(pl)) ? T(0) : ddx;
+    ddy = fabs(ddy) <= Mth<T>::kGradZero * (fabs(pu) + fabs(pd)) ? T(0) : ddy;
+    T nxv, nyv;
+    Mth<T>::unit(ddx * i2dx, ddy * i2dy, nxv, nyv);
+    T U = un * nxv + vn * nyv;
+    T tp = zx * nxv + zy * nyv;
+    T S = m * spread_rate<T>(co, U, tp);
+    T lap = (dxp - dxm) + (dyp - dym);
+    T grad = Mth<T>::sqr(gx2 + gy2);
+    return -S * grad + eps * S * lap;
+}
+
+// the same at index c of a staged field B of row pitch W
+template <typename T>
+__device__ __forceinline__ T rhs_at(const T *B, int c, int W, T idx, T idy, T i2dx, T i2dy,
+                                    T eps, const T *co, T m, T un, T vn, T zx, T zy) {
+    return rhs_vals<T>(B[c], B[c - 1], B[c + 1], B[c - W], B[c + W], idx, idy, i2dx, i2dy, eps,
+                       co, m, un, vn, zx, zy);
+}
+
+
+// burned fraction of one subcell from its 4 vertex values (eqs. approx-area,
+// approx-fraction with the exponent -(1/4) sum (t - t_i)/T_f)
+template <typename T>
+__device__ __forceinline__ T subcell_burned(T p0, T p1, T p2, T p3, T d0, T d1, T d2, T d3,
+                                            T mquarter_over_tf) {
+    T sp = ((p0 + p1) + p2) + p3;
+    T sa = ((fabs(p0) + fabs(p1)) + fabs(p2)) + fabs(p3);
+    T beta = sa > T(0) ? T(0.5) * (T(1) - Mth<T>::dv(sp, sa)) : T(0);
+    T s = ((d0 + d1) + d2) + d3;
+    return beta * (T(1) - Mth<T>::ex(s * mquarter_over_tf));
+}
+
+// Fuel fraction of a cell from the 3x3 node neighbourhood of psi^{n+1}
+// (pba = node (i + a - 1, j + b - 1)) and Dl = t - t_i (0 where psi >= 0)
+// (Sect. 3.3, Fig. subcells): 9 vertices (centre, 4 edge midpoints = 2-node
+// means, 4 corners = 4-node means), Dl zeroed where the interpolated psi >= 0,
+// 4 subcells.
+template <typename T>
+__device__ __forceinline__ T cell_fraction_vals(T p00, T p01, T p02, T p10, T p11, T p12, T p20,
+                                                T p21, T p22, T d00, T d01, T d02, T d10, T d11,
+                                                T d12, T d20, T d21, T d22, T Tf) {
+    T mn = fmin(fmin(fmin(p00, p01), fmin(p02, p10)), fmin(fmin(p11, p12), fmin(fmin(p20, p21), p22)));
+    if (mn >= T(0)) return T(1);  // no vertex burning: every beta is 0 exactly
+    const T h = T(0.5), q = T(0.25);
+    // edge midpoints W, E, S, N and corners SW, SE, NW, NE
+    T pW = h * (p10 + p11), pE = h * (p11 + p12), pS = h * (p01 + p11), pN = h * (p11 + p21);
+    T dW = h * (d10 + d11), dE = h * (d11 + d12), dS = h * (d01 + d11), dN = h * (d11 + d21);
+    T pSW = q * (((p00 + p01) + p10) + p11), pSE = q * (((p01 + p02) + p11) + p12);
+    T pNW = q * (((p10 + p11) + p20) + p21), pNE = q * (((p11 + p12) + p21) + p22);
+    T dSW = q * (((d00 + d01) + d10) + d11), dSE = q * (((d01 + d02) + d11) + d12);
+    T dNW = q * (((d10 + d11) + d20) + d21), dNE = q * (((d11 + d12) + d21) + d22);
+    // compatibility at the vertices: t_i := t where psi >= 0
+    T dC = p11 >= T(0) ? T(0) : d11;
+    dW = pW >= T(0) ? T(0) : dW;
+    dE = pE >= T(0) ? T(0) : dE;
+    dS = pS >= T(0) ? T(0) : dS;
+    dN = pN >= T(0) ? T(0) : dN;
+    dSW = pSW >= T(0) ? T(0) : dSW;
+    dSE = pSE >= T(0) ? T(0) : dSE;
+    dNW = pNW >= T(0) ? T(0) : dNW;
+    dNE = pNE >= T(0) ? T(0) : dNE;
+    const T k = T(-0.25) / Tf;
+    T bSW = subcell_burned<T>(p11, pW, pS, pSW, dC, dW, dS, dSW, k);
+    T bSE = subcell_burned<T>(p11, pE, pS, pSE, dC, dE, dS, dSE, k);
+    T bNW = subcell_burned<T>(p11, pW, pN, pNW, dC, dW, dN, dNW, k);
+    T bNE = subcell_burned<T>(p11, pE, pN, pNE, dC, dE, dN, dNE, k);
+    return T(1) - q * (((bSW + bSE) + bNW) + bNE);
+}
+
+}  // namespace wf

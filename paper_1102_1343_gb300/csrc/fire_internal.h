@@ -75,6 +75,17 @@ cudaError_t launch_fill(void *psi, double *tign, void *frac, size_t n, double ps
 template <typename T>
 cudaError_t prepare_step_kernel(size_t smem_bytes);
 
+template <typename T>
+size_t march_smem_bytes(int ky, int sry);
+
+template <typename T>
+cudaError_t launch_march(const StepArgs &a, cudaStream_t s);
+
+template <typename T>
+cudaError_t prepare_march_kernel(size_t smem_bytes);
+
+constexpr int kMarchMaxColumns = 120;  // output columns of one marching strip
+
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s);
 

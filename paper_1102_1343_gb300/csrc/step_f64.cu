@@ -1,6 +1,8 @@
 // FP64 instantiation of the fire-step kernels (every field in double).
+#include "march_kernel.cuh"
 #include "step_kernel.cuh"
 
 namespace wf {
 WF_INSTANTIATE(double)
+WF_INSTANTIATE_MARCH(double)
 }  // namespace wf

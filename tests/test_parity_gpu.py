@@ -37,7 +37,7 @@ def run_pair(pkg, w, prec, steps=None, tile=None, check_every=None, heat_tol=1e-
     orc = oracle.OracleFire.from_workload(wp)
     m = pkg.FireModel.from_workload(w, precision=prec)
     if tile:
-        pkg.fire_set_tile(m.ctx, *tile)
+        pkg.fire_set_kernel(m.ctx, *tile)
     u, v = m.wind(w.u, w.v)
     worst = 0.0
     Qg = Qo = 0.0
@@ -69,10 +69,12 @@ def test_fp64_plain_circle(pkg):
     assert m.status() == pkg.FIRE_OK
 
 
-@pytest.mark.parametrize("tile", [None, (1, 1), (3, 2), (5, 3)])
+@pytest.mark.parametrize("tile", [None, (1, 1, 1), (1, 7, 3), (1, 12, 17), (0, 1, 1), (0, 3, 2),
+                                  (0, 5, 3)])
 def test_fp64_landscape_ragged_tiles(pkg, tile):
     """Hills, 13 fuels, smooth wind, line ignition on 230x170 nodes: several
-    tiles with a ragged last row and column of tiles."""
+    strips (marching kernel) or tiles (2-D tile kernel), with a ragged last
+    row and column."""
     w = synth.random_landscape(23, 17, seed=21, ignition="line", steps=120)
     m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
     ok, e = compare_fp64(state_np(m), orc)
@@ -120,11 +122,11 @@ def test_fp64_chaparral(pkg):
 # FP32: ignition time 0.1 s, burnt area 0.5 %, integrated heat 1e-4
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["line", "points"])
-def test_fp32_against_fp64_oracle(pkg, case):
+@pytest.mark.parametrize("case,tile", [("line", None), ("points", None), ("line", (0, 8, 4))])
+def test_fp32_against_fp64_oracle(pkg, case, tile):
     w = synth.random_landscape(32, 26, seed=44, ignition=case, n_points=6, edge_margin=300.0,
                                steps=300)
-    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp32")
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp32", tile=tile)
     psi, tign, frac, _ = state_np(m)
     both = np.isfinite(tign) & np.isfinite(orc.tign)
     assert both.sum() > 100
