@@ -198,8 +198,9 @@ double fire_time(const fire_ctx *ctx);
 
 /* Step-kernel variant and its tile shape, in atmospheric cells per CTA
  * (chosen by fire_init's defaults or the autotuner, settable for sweeps):
- *   FIRE_KERNEL_MARCH  one thread per fire column marching down a strip of
- *                      kx*sr_x columns (kx*sr_x <= 120) and ky*sr_y rows;
+ *   FIRE_KERNEL_MARCH  two fire columns per thread marching down a strip of
+ *                      kx*sr_x columns (an even number <= 248) and ky*sr_y
+ *                      rows;
  *   FIRE_KERNEL_TILE   a 2-D tile of kx*sr_x by ky*sr_y nodes staged with
  *                      a 3-node halo in shared memory (any refinement).
  * FIRE_ERR_ARG if the shape does not fit the variant or the device. */

@@ -196,10 +196,11 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
     size_t sm;
     cudaError_t e;
     if (variant == FIRE_KERNEL_MARCH) {
-        if (kx * c->g.sr_x > kMarchMaxColumns) return FIRE_ERR_ARG;
-        sm = c->prec == FIRE_FP64 ? march_smem_bytes<double>(ky, c->g.sr_y)
-                                  : march_smem_bytes<float>(ky, c->g.sr_y);
-        if (sm + 48 * 1024 > c->smem_max) return FIRE_ERR_ARG;
+        const long long W = (long long)kx * c->g.sr_x;
+        if (W > kMarchMaxColumns || (W & 1)) return FIRE_ERR_ARG;
+        sm = c->prec == FIRE_FP64 ? march_smem_bytes<double>(ky, c->g.sr_y, c->ncls)
+                                  : march_smem_bytes<float>(ky, c->g.sr_y, c->ncls);
+        if (sm > c->smem_max) return FIRE_ERR_ARG;
         e = c->prec == FIRE_FP64 ? prepare_march_kernel<double>(sm) : prepare_march_kernel<float>(sm);
     } else if (variant == FIRE_KERNEL_TILE) {
         sm = c->prec == FIRE_FP64 ? step_smem_bytes<double>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls)
@@ -218,11 +219,13 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
 }
 
 int default_kernel(fire_ctx *c) {
-    // marching strips of up to 120 columns x ~200 rows when the refinement
-    // allows; else 2-D tiles of ~80 x 40 (FP32) / 40 x 40 (FP64) nodes
-    if (c->g.sr_x <= kMarchMaxColumns) {
+    // marching strips of up to 248 columns (an even number) x ~200 rows when
+    // the refinement allows; else 2-D tiles of ~80 x 40 (FP32) / 40 x 40
+    // (FP64) nodes
+    if (c->g.sr_x <= kMarchMaxColumns / 2) {
         int kx = kMarchMaxColumns / c->g.sr_x, ky = 200 / c->g.sr_y;
         if (kx > c->g.nx_atm) kx = c->g.nx_atm;
+        if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 2;
         if (ky < 1) ky = 1;
         if (ky > c->g.ny_atm) ky = c->g.ny_atm;
         if (configure_kernel(c, FIRE_KERNEL_MARCH, kx, ky) == FIRE_OK) return FIRE_OK;
@@ -266,6 +269,50 @@ int one_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, d
 }
 
 }  // namespace
+
+// accessors used by the ensemble (ensemble.cu)
+namespace wf {
+int ctx_step_args(fire_ctx *c, int parity, const void *u, const void *v, double dt, double *hs,
+                  double *hl, StepArgs &a) {
+    const int save = c->cur;
+    c->cur = parity;
+    step_kernel_args(c, u, v, dt, hs, hl, a);
+    c->cur = save;
+    return FIRE_OK;
+}
+
+int ctx_info(const fire_ctx *c, int *prec, int *variant, int *nx, int *ny, int *srx, int *sry,
+             int *kx, int *ky, int *ncls, int *cur, double *t) {
+    *prec = c->prec;
+    *variant = c->variant;
+    *nx = c->nx;
+    *ny = c->ny;
+    *srx = c->g.sr_x;
+    *sry = c->g.sr_y;
+    *kx = c->kx;
+    *ky = c->ky;
+    *ncls = c->ncls;
+    *cur = c->cur;
+    *t = c->t;
+    return FIRE_OK;
+}
+
+int ctx_advance(fire_ctx *c, int nsteps, double dt) {
+    for (int k = 0; k < nsteps; ++k) {
+        c->cur = 1 - c->cur;
+        c->t = c->t + dt;
+    }
+    return FIRE_OK;
+}
+
+bool ctx_ignition_active(fire_ctx *c, double t) {
+    std::vector<IgnSeg> segs;
+    active_segments(c, t, false, segs);
+    return !segs.empty();
+}
+
+cudaStream_t ctx_stream(const fire_ctx *c) { return c->stream; }
+}  // namespace wf
 
 extern "C" {
 

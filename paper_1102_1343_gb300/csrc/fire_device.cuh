@@ -55,6 +55,19 @@ struct Mth<double> {
     }
 };
 
+// float and double versions of |x|, min and the finiteness test, so that no
+// float operand is ever widened to double on the (1/64-rate) FP64 pipe
+__device__ __forceinline__ float abs_val(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_val(double x) { return fabs(x); }
+__device__ __forceinline__ float min_val(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double min_val(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ bool finite_val(float x) {
+    return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+}
+__device__ __forceinline__ bool finite_val(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
 // extrapolated ghost value beyond the last node p0 (p1 the one before it),
 // Sect. 3.1: max{p0 + (p0 - p1), p0, p1}
 template <typename T>
@@ -134,8 +147,8 @@ __device__ __forceinline__ T rhs_vals(T p, T pl, T pr, T pd, T pu, T idx, T idy,
     // a central difference at the rounding level of its two values counts
     // as zero: rounding noise at a symmetric point must not pick the normal
     T ddx = pr - pl, ddy = pu - pd;
-    ddx = fabs(ddx) <= Mth<T>::kGradZero * (fabs(pr) + fabs(pl)) ? T(0) : ddx;
-    ddy = fabs(ddy) <= Mth<T>::kGradZero * (fabs(pu) + fabs(pd)) ? T(0) : ddy;
+    ddx = abs_val(ddx) <= Mth<T>::kGradZero * (abs_val(pr) + abs_val(pl)) ? T(0) : ddx;
+    ddy = abs_val(ddy) <= Mth<T>::kGradZero * (abs_val(pu) + abs_val(pd)) ? T(0) : ddy;
     T nxv, nyv;
     Mth<T>::unit(ddx * i2dx, ddy * i2dy, nxv, nyv);
     T U = un * nxv + vn * nyv;
@@ -161,7 +174,7 @@ template <typename T>
 __device__ __forceinline__ T subcell_burned(T p0, T p1, T p2, T p3, T d0, T d1, T d2, T d3,
                                             T mquarter_over_tf) {
     T sp = ((p0 + p1) + p2) + p3;
-    T sa = ((fabs(p0) + fabs(p1)) + fabs(p2)) + fabs(p3);
+    T sa = ((abs_val(p0) + abs_val(p1)) + abs_val(p2)) + abs_val(p3);
     T beta = sa > T(0) ? T(0.5) * (T(1) - Mth<T>::dv(sp, sa)) : T(0);
     T s = ((d0 + d1) + d2) + d3;
     return beta * (T(1) - Mth<T>::ex(s * mquarter_over_tf));
@@ -176,7 +189,8 @@ template <typename T>
 __device__ __forceinline__ T cell_fraction_vals(T p00, T p01, T p02, T p10, T p11, T p12, T p20,
                                                 T p21, T p22, T d00, T d01, T d02, T d10, T d11,
                                                 T d12, T d20, T d21, T d22, T Tf) {
-    T mn = fmin(fmin(fmin(p00, p01), fmin(p02, p10)), fmin(fmin(p11, p12), fmin(fmin(p20, p21), p22)));
+    T mn = min_val(min_val(min_val(p00, p01), min_val(p02, p10)),
+                   min_val(min_val(p11, p12), min_val(min_val(p20, p21), p22)));
     if (mn >= T(0)) return T(1);  // no vertex burning: every beta is 0 exactly
     const T h = T(0.5), q = T(0.25);
     // edge midpoints W, E, S, N and corners SW, SE, NW, NE

@@ -76,7 +76,7 @@ template <typename T>
 cudaError_t prepare_step_kernel(size_t smem_bytes);
 
 template <typename T>
-size_t march_smem_bytes(int ky, int sry);
+size_t march_smem_bytes(int ky, int sry, int ncls);
 
 template <typename T>
 cudaError_t launch_march(const StepArgs &a, cudaStream_t s);
@@ -84,7 +84,7 @@ cudaError_t launch_march(const StepArgs &a, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_march_kernel(size_t smem_bytes);
 
-constexpr int kMarchMaxColumns = 120;  // output columns of one marching strip
+constexpr int kMarchMaxColumns = 248;  // output columns of one marching strip (even)
 
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s);

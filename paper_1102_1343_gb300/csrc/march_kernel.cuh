@@ -1,25 +1,29 @@
 // Column-marching fire-step kernel: the whole step of Sect. 5 (items 2-6)
-// in one pass over the state, one thread per fire-mesh column.
+// in one pass over the state, two fire-mesh columns per thread.
 //
-// A CTA of 128 threads owns a strip of W = kx*srx output columns (W <= 120)
-// and L = ky*sry output rows; its threads cover the strip's columns plus 4
-// halo columns on each side.  It marches down the strip one row per
-// iteration, with the stages lagging behind the loads:
-//   iteration k:  A  store psi^n of row k+4 (loaded one iteration earlier)
-//                 B  stage 1 (eq. Heun, first line) on row k+3
+// A CTA of 128 threads owns a strip of W = kx*srx output columns (W even,
+// W <= 248) and L = ky*sry output rows; thread c holds the columns
+// x0 - 4 + 2c and x0 - 3 + 2c, so the CTA covers the strip plus 4 halo
+// columns on each side.  It marches down the strip one row per iteration,
+// the stages lagging behind the loads:
+//   iteration k:  A  stage psi^n of row k+3 (loaded one iteration earlier)
+//                 B  stage 1 (eq. Heun, first line) on row k+2
 //                 C  stage 2 (eq. Heun, second line), ignition-time crossing
 //                    (eq. set-ignition-time) and t - t_i on row k+1
 //                 D  fuel-fraction quadrature (Sect. 3.3) and heat flux
 //                    (eqs. sensible-/latent-heat-flux) on row k-1
 //                 one __syncthreads
-// Every shared-memory value a phase reads from another thread was written in
-// an earlier iteration, so one barrier per row suffices; each stage keeps a
-// ring of 4 rows.  Vertical neighbours cost no recomputation, so the only
-// redundant work is the 2+1 halo columns of the two stages.  Ghost values
-// beyond the domain (Sect. 3.1, x first then y) are computed by the thread
-// that needs them from values it reads anyway.  Heat is summed per column
-// over each band of sry rows, then per atmospheric cell in double after the
-// band's last row: the average of Sect. 5, item 6, reduced inside the CTA.
+// Every shared value read from another thread was written in an earlier
+// iteration (values of the thread's own columns may come from the same
+// iteration), so one barrier per row suffices; each stage keeps a ring of 4
+// rows.  Stage 2 runs one row behind stage 1, so the fuel class, terrain
+// gradient and wind of a row are loaded once and carried in registers.  Vertical neighbours cost no recomputation: the only redundant
+// work is the 2+1 halo columns of the two stages.  Ghost values beyond the
+// domain (Sect. 3.1, x first then y) are computed by the thread that needs
+// them.  The wind is interpolated in x once per atmospheric row and column
+// (a per-thread ring of 4 rows) and in y per node.  Heat is summed per
+// column over each band of sry rows, then per atmospheric cell in double
+// after the band's last row: the average of Sect. 5, item 6, inside the CTA.
 #pragma once
 
 #include "fire_device.cuh"
@@ -28,302 +32,601 @@
 namespace wf {
 
 constexpr int kMarchThreads = 128;
-constexpr int kMarchHalo = 4;   // columns on each side of the strip
-constexpr int kRing = 4;        // rows kept per stage
+constexpr int kMarchHalo = 4;  // columns on each side of the strip
+constexpr int kMarchCols = 2;  // columns per thread
+
+// resident CTAs per SM the register allocation aims for (FP64 needs more
+// registers per thread)
+template <typename T>
+struct MarchOccupancy {
+    static constexpr int blocks = 5;
+};
+template <>
+struct MarchOccupancy<double> {
+    static constexpr int blocks = 2;
+};
 
 template <typename T>
-struct RowWeights {
-    int ju0, ju1, jv0, jv1;  // atmos rows bracketing the node (u centres, v faces)
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
+template <typename T>
+struct MarchRow {  // y-interpolation of the wind for one fire row
+    int ju0, jv0;
     T wyu, wyv;
 };
 
 template <typename T>
-__host__ __device__ inline int march_max_width(int srx) {
-    return (kMarchThreads - 2 * kMarchHalo) / srx;  // atmos cells per strip
-}
+struct MarchCol {  // x-interpolation of the wind for one fire column
+    int iu0, iu1, iv0, iv1;
+    T wxu, wxv;
+};
+
+// dynamic shared memory layout of the marching kernel
+template <typename T>
+struct MarchSmem {
+    using T2 = typename Vec2<T>::type;
+    T2 *S0, *S1, *SF, *SQ, *SD;  // [4][NT] psi^n, psi*, F(psi^n), psi^{n+1}, t - t_i
+    T2 *UX, *VX;                 // [4][NT] x-interpolated wind of 4 atmos rows (per thread)
+    T *lut;                      // [ncls][8] S0 R0 b c d e Tf Hs
+    T *lutq;                     // [ncls] Hq
+    T *HB;                       // [2][2][2 NT] heat column partials of 2 bands
+    MarchCol<T> *col;            // [2 NT]
+    MarchRow<T> *row;            // [L + 4]
+    int *status;
+
+    static __host__ __device__ size_t bytes(int L, int ncls) {
+        const size_t NT = kMarchThreads;
+        size_t b = 0;
+        b += 7 * 4 * NT * sizeof(T2);
+        b += (size_t)ncls * 8 * sizeof(T) + (size_t)ncls * sizeof(T);
+        b = (b + 15) & ~(size_t)15;
+        b += 2 * 2 * 2 * NT * sizeof(T);
+        b += 2 * NT * sizeof(MarchCol<T>);
+        b = (b + 15) & ~(size_t)15;
+        b += (size_t)(L + 4) * sizeof(MarchRow<T>);
+        b += 16;
+        return b;
+    }
+
+    __device__ void carve(unsigned char *p, int L, int ncls) {
+        const int NT = kMarchThreads;
+        T2 *v = reinterpret_cast<T2 *>(p);
+        S0 = v;
+        S1 = v + 4 * NT;
+        SF = v + 8 * NT;
+        SQ = v + 12 * NT;
+        SD = v + 16 * NT;
+        UX = v + 20 * NT;
+        VX = v + 24 * NT;
+        unsigned char *q = reinterpret_cast<unsigned char *>(v + 28 * NT);
+        lut = reinterpret_cast<T *>(q);
+        lutq = lut + ncls * 8;
+        q += (size_t)ncls * 9 * sizeof(T);
+        q = reinterpret_cast<unsigned char *>(((uintptr_t)q + 15) & ~(uintptr_t)15);
+        HB = reinterpret_cast<T *>(q);
+        q += 2 * 2 * 2 * NT * sizeof(T);
+        col = reinterpret_cast<MarchCol<T> *>(q);
+        q += 2 * NT * sizeof(MarchCol<T>);
+        q = reinterpret_cast<unsigned char *>(((uintptr_t)q + 15) & ~(uintptr_t)15);
+        row = reinterpret_cast<MarchRow<T> *>(q);
+        q += (size_t)(L + 4) * sizeof(MarchRow<T>);
+        status = reinterpret_cast<int *>(q);
+    }
+};
 
 template <typename T>
-__global__ void __launch_bounds__(kMarchThreads) k_fire_march(const StepArgs a) {
-    constexpr int NT = kMarchThreads;
-    __shared__ T S0[kRing][NT];  // psi^n
-    __shared__ T S1[kRing][NT];  // psi*
-    __shared__ T SF[kRing][NT];  // F(psi^n)
-    __shared__ T SQ[kRing][NT];  // psi^{n+1}
-    __shared__ T SD[kRing][NT];  // t - t_i where psi^{n+1} < 0, else 0
-    __shared__ T lut[FIRE_MAX_CLASSES * K_N];
-    __shared__ T HB[2][2][NT];   // per-column heat partials of a band (2 bands in flight)
-    __shared__ int s_status;
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
-    RowWeights<T> *rw = reinterpret_cast<RowWeights<T> *>(dyn_smem);
+__device__ __forceinline__ T pick(const typename Vec2<T>::type &v, int j) {
+    return j == 0 ? v.x : v.y;
+}
 
-    const int c = threadIdx.x;
-    const int srx = a.srx, sry = a.sry, nx = a.nx, ny = a.ny, nxa = a.nxa, nya = a.nya;
-    const int W = a.kx * srx, L = a.ky * sry;
-    const int x0 = blockIdx.x * W, y0 = blockIdx.y * L;
-    const int Wa = min(W, nx - x0), La = min(L, ny - y0);
-    const int x = x0 - kMarchHalo + c;
-    const bool xin = x >= 0 && x < nx;
-    const bool c_load = xin && c >= 1 && c < Wa + 7;
-    const bool c_s1 = xin && c >= 2 && c < Wa + 6;
-    const bool c_s2 = xin && c >= 3 && c < Wa + 5;
-    const bool c_out = c >= 4 && c < Wa + 4;
+// Per-thread state of one strip.
+template <typename T>
+struct MarchStrip {
+    using T2 = typename Vec2<T>::type;
+    const StepArgs &a;
+    MarchSmem<T> &sm;
+    int c, x0, y0, Wa, La, nx, ny, nxa, nya, srx, sry, ncm1, band;
+    int xa;  // global column of this thread's first column
+    bool vec;  // paired vector access allowed (nx and x even)
+    bool m_load[2], m_s1[2], m_s2[2], m_out[2];
+    T dt, idx, idy, i2dx, i2dy, eps;
+    double tstart, t1;
+    // running state
+    T2 pf_psi;    // psi^n of the next row to stage
+    T2 cur_psi;   // psi^n of the row staged this iteration
+    int pf_cls[2];
+    T2 pf_zx, pf_zy, pf_m;
+    T2 pf_F;
+    int e_cls[2];       // environment of the row stage 1 handled last iteration
+    T2 e_zx, e_zy, e_m, e_un, e_vn;
+    T acc_s[2], acc_q[2];
+    double hscale;     // 1 / (dt srx sry)
+    int ju_hi, jv_hi;  // highest atmos rows in this thread's wind ring
+    int bcnt, bpar;    // rows done in the current band, band parity
+    int st;
 
-    const T *__restrict__ psi_in = static_cast<const T *>(a.psi_in);
-    T *__restrict__ psi_out = static_cast<T *>(a.psi_out);
-    const T *__restrict__ F_in = static_cast<const T *>(a.F_in);
-    T *__restrict__ F_out = static_cast<T *>(a.F_out);
-    const T *__restrict__ dzdx = static_cast<const T *>(a.dzdx);
-    const T *__restrict__ dzdy = static_cast<const T *>(a.dzdy);
-    const T *__restrict__ mult = static_cast<const T *>(a.mult);
-    const T *__restrict__ wu = static_cast<const T *>(a.u);
-    const T *__restrict__ wv = static_cast<const T *>(a.v);
-    const uint8_t *__restrict__ fuel = a.fuel;
-    double *__restrict__ tign = a.tign;
+    __device__ __forceinline__ MarchStrip(const StepArgs &args, MarchSmem<T> &s) : a(args), sm(s) {}
 
-    const T dt = T(a.dt);
-    const T idx = T(1) / T(a.dx), idy = T(1) / T(a.dy);
-    const T i2dx = T(1) / (T(2) * T(a.dx)), i2dy = T(1) / (T(2) * T(a.dy));
-    const T eps = T(a.eps);
-    const double tstart = *a.t_in;
-    const double t1 = tstart + a.dt;
-    const int ncm1 = a.ncls - 1;
-    const int band = a.band;
-
-    // ---- set-up: coefficient table, row weights, this column's wind weights
-    if (c == 0) {
-        s_status = 0;
-        if (blockIdx.x == 0 && blockIdx.y == 0) *a.t_out = t1;
+    __device__ __forceinline__ bool in_rows(int r, int lo, int hi) const {
+        return r >= lo && r < hi && r >= 0 && r < ny;
     }
-    for (int k = c; k < a.ncls * K_N; k += NT) lut[k] = T(a.coef[k]);
-    for (int i = c; i < La + 4; i += NT) {
-        const int r = y0 - 2 + i;
-        RowWeights<T> w;
-        w.ju0 = w.ju1 = w.jv0 = w.jv1 = 0;
-        w.wyu = w.wyv = T(0);
-        if (r >= 0 && r < ny) {
-            const T ya = (T(r) + T(0.5)) / T(sry);
-            lin_idx<T>(ya - T(0.5), nya, w.ju0, w.ju1, w.wyu);
-            lin_idx<T>(ya, nya + 1, w.jv0, w.jv1, w.wyv);
+
+    // paired load of a T field at (r, xa), masked per column
+    __device__ __forceinline__ T2 ld2(const T *__restrict__ f, int r, bool m0, bool m1) const {
+        T2 v;
+        const size_t g = (size_t)r * nx + xa;
+        if (vec && m0 && m1) {
+            v = *reinterpret_cast<const T2 *>(f + g);
+        } else {
+            v.x = m0 ? f[g] : T(0);
+            v.y = m1 ? f[g + 1] : T(0);
         }
-        rw[i] = w;
+        return v;
     }
-    int iu0 = 0, iu1 = 0, iv0 = 0, iv1 = 0;
-    T wxu = T(0), wxv = T(0);
-    if (xin) {
-        const T xa = (T(x) + T(0.5)) / T(srx);
-        lin_idx<T>(xa, nxa + 1, iu0, iu1, wxu);
-        lin_idx<T>(xa - T(0.5), nxa, iv0, iv1, wxv);
+
+    __device__ __forceinline__ void load_env(int r) {
+        if (!in_rows(r, y0 - 2, y0 + La + 2) || !(m_s1[0] || m_s1[1])) return;
+        const size_t g = (size_t)r * nx + xa;
+        if (vec && m_s1[0] && m_s1[1]) {
+            const uint16_t f2 = *reinterpret_cast<const uint16_t *>(a.fuel + g);
+            pf_cls[0] = f2 & 0xff;
+            pf_cls[1] = f2 >> 8;
+        } else {
+            pf_cls[0] = m_s1[0] ? a.fuel[g] : 0;
+            pf_cls[1] = m_s1[1] ? a.fuel[g + 1] : 0;
+        }
+        pf_zx = ld2(static_cast<const T *>(a.dzdx), r, m_s1[0], m_s1[1]);
+        pf_zy = ld2(static_cast<const T *>(a.dzdy), r, m_s1[0], m_s1[1]);
+        if (a.mult) pf_m = ld2(static_cast<const T *>(a.mult), r, m_s1[0], m_s1[1]);
     }
-    __syncthreads();
 
-    // wind at (x, r), same formula as the bilinear interpolation of wind_at
-    auto wind = [&](int r, T &un, T &vn) {
-        const RowWeights<T> &w = rw[r - (y0 - 2)];
-        const T *u0 = wu + (size_t)w.ju0 * (nxa + 1), *u1 = wu + (size_t)w.ju1 * (nxa + 1);
-        un = (T(1) - w.wyu) * ((T(1) - wxu) * __ldg(u0 + iu0) + wxu * __ldg(u0 + iu1)) +
-             w.wyu * ((T(1) - wxu) * __ldg(u1 + iu0) + wxu * __ldg(u1 + iu1));
-        const T *v0 = wv + (size_t)w.jv0 * nxa, *v1 = wv + (size_t)w.jv1 * nxa;
-        vn = (T(1) - w.wyv) * ((T(1) - wxv) * __ldg(v0 + iv0) + wxv * __ldg(v0 + iv1)) +
-             w.wyv * ((T(1) - wxv) * __ldg(v1 + iv0) + wxv * __ldg(v1 + iv1));
-    };
+    // x-interpolated wind of atmos u-row J / v-row J for this thread's columns
+    __device__ __forceinline__ void fill_wind_u(int J) {
+        const T *u = static_cast<const T *>(a.u) + (size_t)J * (nxa + 1);
+        T2 v;
+        const MarchCol<T> &c0 = sm.col[2 * c], &c1 = sm.col[2 * c + 1];
+        v.x = (T(1) - c0.wxu) * __ldg(u + c0.iu0) + c0.wxu * __ldg(u + c0.iu1);
+        v.y = (T(1) - c1.wxu) * __ldg(u + c1.iu0) + c1.wxu * __ldg(u + c1.iu1);
+        sm.UX[(J & 3) * kMarchThreads + c] = v;
+    }
+    __device__ __forceinline__ void fill_wind_v(int J) {
+        const T *w = static_cast<const T *>(a.v) + (size_t)J * nxa;
+        T2 v;
+        const MarchCol<T> &c0 = sm.col[2 * c], &c1 = sm.col[2 * c + 1];
+        v.x = (T(1) - c0.wxv) * __ldg(w + c0.iv0) + c0.wxv * __ldg(w + c0.iv1);
+        v.y = (T(1) - c1.wxv) * __ldg(w + c1.iv0) + c1.wxv * __ldg(w + c1.iv1);
+        sm.VX[(J & 3) * kMarchThreads + c] = v;
+    }
 
-    const int k0 = y0 - 7, k1 = y0 + La;  // iterations: rows k0+4 .. k1-1
-    const int a_lo = y0 - 3, a_hi = y0 + La + 3;  // psi^n rows staged
-    auto load_psi = [&](int r) -> T {
-        return (c_load && r >= 0 && r < ny && r >= a_lo && r < a_hi) ? psi_in[(size_t)r * nx + x]
-                                                                      : T(0);
-    };
-    // prefetched values for the next iteration
-    T pf_psi = load_psi(k0 + 4);
-    int pf_cls = 0;
-    T pf_zx = T(0), pf_zy = T(0), pf_m = T(1);
-    auto load_env = [&](int r, int &cls, T &zx, T &zy, T &m) {
-        if (c_s1 && r >= 0 && r < ny && r >= y0 - 2 && r < y0 + La + 2) {
-            const size_t g = (size_t)r * nx + x;
-            cls = fuel[g];
-            zx = dzdx[g];
-            zy = dzdy[g];
-            m = mult ? mult[g] : T(1);
+    // wind at fire row r for both columns (bilinear, as the staggered-grid
+    // interpolation of Sect. 5); ensure=true extends this thread's ring
+    __device__ __forceinline__ void wind(int r, bool ensure, T2 &un, T2 &vn) {
+        const MarchRow<T> w = sm.row[r - (y0 - 2)];
+        const int ju1 = nya == 1 ? w.ju0 : w.ju0 + 1;
+        const int jv1 = w.jv0 + 1;
+        if (ensure) {
+            if (ju_hi < w.ju0 - 1) ju_hi = w.ju0 - 1;
+            if (jv_hi < w.jv0 - 1) jv_hi = w.jv0 - 1;
+            while (ju_hi < ju1) fill_wind_u(++ju_hi);
+            while (jv_hi < jv1) fill_wind_v(++jv_hi);
         }
-    };
-    load_env(k0 + 3, pf_cls, pf_zx, pf_zy, pf_m);
-    T pf_F = T(0);
-    T acc_s = T(0), acc_q = T(0);
-    int st = 0;
+        const T2 ua = sm.UX[(w.ju0 & 3) * kMarchThreads + c];
+        const T2 ub = sm.UX[(ju1 & 3) * kMarchThreads + c];
+        const T2 va = sm.VX[(w.jv0 & 3) * kMarchThreads + c];
+        const T2 vb = sm.VX[(jv1 & 3) * kMarchThreads + c];
+        un.x = (T(1) - w.wyu) * ua.x + w.wyu * ub.x;
+        un.y = (T(1) - w.wyu) * ua.y + w.wyu * ub.y;
+        vn.x = (T(1) - w.wyv) * va.x + w.wyv * vb.x;
+        vn.y = (T(1) - w.wyv) * va.y + w.wyv * vb.y;
+    }
 
-    for (int k = k0; k <= k1; ++k) {
-        // ---- A: stage psi^n of row k+4; prefetch row k+5
-        {
-            const int r = k + 4;
-            if (r >= a_lo && r < a_hi) S0[r & 3][c] = pf_psi;
-            pf_psi = load_psi(k + 5);
+    // the 5-point values of column j at row r from ring slot sr of a staged
+    // field B (down: slot sd, up: value pu given), with ghosts at the domain
+    // boundary (Sect. 3.1)
+    __device__ __forceinline__ T stage_rhs(const T2 *B, int sr, int sd, T2 up, int r, int j,
+                                           int cls, T zx, T zy, T m, T un, T vn) const {
+        const int NT = kMarchThreads;
+        const T2 own = B[sr * NT + c];
+        const T p = pick<T>(own, j);
+        T pl = j == 0 ? B[sr * NT + c - 1].y : own.x;
+        T pr = j == 0 ? own.y : B[sr * NT + c + 1].x;
+        T pd = pick<T>(B[sd * NT + c], j);
+        T pu = pick<T>(up, j);
+        const int x = xa + j;
+        if (x == 0 || x == nx - 1 || r == 0 || r == ny - 1) {
+            const T pl0 = pl, pr0 = pr, pd0 = pd, pu0 = pu;
+            if (x == 0) pl = ghost_value<T>(p, pr0);
+            if (x == nx - 1) pr = ghost_value<T>(p, pl0);
+            if (r == 0) pd = ghost_value<T>(p, pu0);
+            if (r == ny - 1) pu = ghost_value<T>(p, pd0);
         }
-        // ---- B: stage 1 on row k+3
+        const T *co = sm.lut + cls * 8;
+        return rhs_vals<T>(p, pl, pr, pd, pu, idx, idy, i2dx, i2dy, eps, co, m, un, vn, zx, zy);
+    }
+
+    __device__ __forceinline__ void iter(int k) {
+        const int NT = kMarchThreads;
+        // ring slots: row k+3 -> s3, k+2 -> s2, k+1 -> s1, k -> s0, k-1 -> s3, k-2 -> s2
+        const int s0 = k & 3, s1 = (k + 1) & 3, s2 = (k + 2) & 3, s3 = (k + 3) & 3;
+        // ---- A: stage psi^n of row k+3, prefetch row k+4
         {
             const int r = k + 3;
-            const int cls0 = pf_cls;
-            const T zx = pf_zx, zy = pf_zy, m = pf_m;
-            load_env(k + 4, pf_cls, pf_zx, pf_zy, pf_m);
-            if (c_s1 && r >= y0 - 2 && r < y0 + La + 2 && r >= 0 && r < ny) {
-                const T *R = S0[r & 3];
-                const T p = R[c], pl0 = R[c - 1], pr0 = R[c + 1];
-                const T pd0 = S0[(r - 1) & 3][c], pu0 = S0[(r + 1) & 3][c];
-                const T pl = x > 0 ? pl0 : ghost_value<T>(p, pr0);
-                const T pr = x < nx - 1 ? pr0 : ghost_value<T>(p, pl0);
-                const T pd = r > 0 ? pd0 : ghost_value<T>(p, pu0);
-                const T pu = r < ny - 1 ? pu0 : ghost_value<T>(p, pd0);
-                T un, vn;
-                wind(r, un, vn);
-                if (!isfinite(un) || !isfinite(vn)) st |= ST_NONFINITE;
-                const int cls = cls0 > ncm1 ? ncm1 : cls0;
-                const T F = rhs_vals<T>(p, pl, pr, pd, pu, idx, idy, i2dx, i2dy, eps,
-                                        lut + cls * K_N, m, un, vn, zx, zy);
-                S1[r & 3][c] = p + dt * F;
-                SF[r & 3][c] = F;
+            cur_psi = pf_psi;
+            if (r >= y0 - 3 && r < y0 + La + 3) sm.S0[s3 * NT + c] = cur_psi;
+            const int rn = k + 4;
+            if (in_rows(rn, y0 - 3, y0 + La + 3))
+                pf_psi = ld2(static_cast<const T *>(a.psi_in), rn, m_load[0], m_load[1]);
+        }
+        // ---- B: stage 1 on row k+2 (its environment is carried to C)
+        const int eb_cls0 = e_cls[0], eb_cls1 = e_cls[1];
+        const T2 eb_zx = e_zx, eb_zy = e_zy, eb_m = e_m, eb_un = e_un, eb_vn = e_vn;
+        {
+            const int r = k + 2;
+            e_cls[0] = pf_cls[0];
+            e_cls[1] = pf_cls[1];
+            e_zx = pf_zx;
+            e_zy = pf_zy;
+            e_m = pf_m;
+            load_env(k + 3);
+            if (in_rows(r, y0 - 2, y0 + La + 2) && (m_s1[0] || m_s1[1])) {
+                wind(r, true, e_un, e_vn);
+                T2 F, P;
+                const T2 own = sm.S0[s2 * NT + c];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    T f = T(0);
+                    if (m_s1[j]) {
+                        const T uj = pick<T>(e_un, j), vj = pick<T>(e_vn, j);
+                        if (!finite_val(uj) || !finite_val(vj)) st |= ST_NONFINITE;
+                        int cls = e_cls[j];
+                        cls = cls > ncm1 ? ncm1 : cls;
+                        f = stage_rhs(sm.S0, s2, s1, cur_psi, r, j, cls, pick<T>(e_zx, j),
+                                      pick<T>(e_zy, j), pick<T>(e_m, j), uj, vj);
+                    }
+                    if (j == 0) { F.x = f; P.x = own.x + dt * f; }
+                    else { F.y = f; P.y = own.y + dt * f; }
+                }
+                sm.S1[s2 * NT + c] = P;
+                sm.SF[s2 * NT + c] = F;
             }
         }
-        // ---- C: stage 2, crossing and t - t_i on row k+1
+        // ---- C: stage 2, crossing, t - t_i on row k+1 (environment from B)
         {
             const int r = k + 1;
-            if (c_s2 && r >= y0 - 1 && r < y0 + La + 1 && r >= 0 && r < ny) {
-                const size_t g = (size_t)r * nx + x;
-                const T *R = S1[r & 3];
-                const T q = R[c], ql0 = R[c - 1], qr0 = R[c + 1];
-                const T qd0 = S1[(r - 1) & 3][c], qu0 = S1[(r + 1) & 3][c];
-                const T ql = x > 0 ? ql0 : ghost_value<T>(q, qr0);
-                const T qr = x < nx - 1 ? qr0 : ghost_value<T>(q, ql0);
-                const T qd = r > 0 ? qd0 : ghost_value<T>(q, qu0);
-                const T qu = r < ny - 1 ? qu0 : ghost_value<T>(q, qd0);
-                int cls = fuel[g];
-                cls = cls > ncm1 ? ncm1 : cls;
-                const T m = mult ? mult[g] : T(1);
-                T un, vn;
-                wind(r, un, vn);
-                const T F2 = rhs_vals<T>(q, ql, qr, qd, qu, idx, idy, i2dx, i2dy, eps,
-                                         lut + cls * K_N, m, un, vn, dzdx[g], dzdy[g]);
-                const T p0 = S0[r & 3][c];
-                const T pn = p0 + dt * (T(0.5) * SF[r & 3][c] + T(0.5) * F2);
-                const bool own = c_out && r >= y0 && r < y0 + La;
-                T d = T(0);
-                const bool cross = p0 > T(0) && pn <= T(0);
-                if (cross || pn < T(0)) {
-                    double ti = tign[g];
-                    if (cross && isinf(ti)) {
-                        const double q0 = (double)p0, q1 = (double)pn;
-                        ti = tstart + q0 * a.dt / (q0 - q1);
-                        if (own) tign[g] = ti;
+            if (in_rows(r, y0 - 1, y0 + La + 1) && (m_s2[0] || m_s2[1])) {
+                const size_t g = (size_t)r * nx + xa;
+                const T2 up = sm.S1[s2 * NT + c];
+                const T2 p0v = sm.S0[s1 * NT + c];
+                const T2 f1v = sm.SF[s1 * NT + c];
+                const bool own_row = r >= y0 && r < y0 + La;
+                T2 PN, DL;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    T pn = T(0), d = T(0);
+                    if (m_s2[j]) {
+                        int cls = j == 0 ? eb_cls0 : eb_cls1;
+                        cls = cls > ncm1 ? ncm1 : cls;
+                        const T F2 = stage_rhs(sm.S1, s1, s0, up, r, j, cls, pick<T>(eb_zx, j),
+                                               pick<T>(eb_zy, j), pick<T>(eb_m, j),
+                                               pick<T>(eb_un, j), pick<T>(eb_vn, j));
+                        const T p0 = pick<T>(p0v, j);
+                        pn = p0 + dt * (T(0.5) * pick<T>(f1v, j) + T(0.5) * F2);
+                        const bool own = own_row && m_out[j];
+                        const bool cross = p0 > T(0) && pn <= T(0);
+                        if (cross || pn < T(0)) {
+                            double ti = a.tign[g + j];
+                            if (cross && isinf(ti)) {
+                                const double q0 = (double)p0, q1 = (double)pn;
+                                ti = tstart + q0 * a.dt / (q0 - q1);
+                                if (own) a.tign[g + j] = ti;
+                            }
+                            if (pn < T(0)) d = T(t1 - ti);
+                        }
+                        if (own) {
+                            if (!finite_val(pn)) st |= ST_NONFINITE;
+                            const int x = xa + j;
+                            const bool edge = x < band || r < band || x >= nx - band || r >= ny - band;
+                            if (edge && pn < T(0)) st |= ST_BOUNDARY;
+                        }
                     }
-                    if (pn < T(0)) d = T(t1 - ti);
+                    if (j == 0) { PN.x = pn; DL.x = d; }
+                    else { PN.y = pn; DL.y = d; }
                 }
-                SQ[r & 3][c] = pn;
-                SD[r & 3][c] = d;
-                if (own) {
-                    psi_out[g] = pn;
-                    if (!isfinite(pn)) st |= ST_NONFINITE;
-                    const bool edge = x < band || r < band || x >= nx - band || r >= ny - band;
-                    if (edge && pn < T(0)) st |= ST_BOUNDARY;
+                sm.SQ[s1 * NT + c] = PN;
+                sm.SD[s1 * NT + c] = DL;
+                if (own_row) {
+                    T *po = static_cast<T *>(a.psi_out);
+                    if (vec && m_out[0] && m_out[1]) {
+                        *reinterpret_cast<T2 *>(po + g) = PN;
+                    } else {
+                        if (m_out[0]) po[g] = PN.x;
+                        if (m_out[1]) po[g + 1] = PN.y;
+                    }
                 }
             }
         }
         // ---- D: fuel fraction and heat on row k-1
         const int rd = k - 1;
         const bool drow = rd >= y0 && rd < y0 + La;
-        if (drow && c_out) {
-            T p[3][3], d[3][3];
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const int s = (rd + b - 1) & 3;
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    p[b][e] = SQ[s][c + e - 1];
-                    d[b][e] = SD[s][c + e - 1];
-                }
-            }
-            if (x == 0 || x == nx - 1 || rd == 0 || rd == ny - 1) {
-                // ghost ring of psi^{n+1} (x first, then y) and of t - t_i
-                // (inner neighbour's value, 0 where the ghost psi >= 0)
+        if (drow && (m_out[0] || m_out[1])) {
+            // psi^{n+1} on rows rd-1 (slot s2), rd (s3), rd+1 (s0), columns -1..2
+            T p[3][4];
+            {
+                const int sl[3] = {s2, s3, s0};
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    const int yy = rd + b - 1;
-                    if (yy < 0 || yy >= ny) continue;
-                    if (x == 0) {
-                        p[b][0] = ghost_value<T>(p[b][1], p[b][2]);
-                        d[b][0] = p[b][0] >= T(0) ? T(0) : d[b][1];
-                    }
-                    if (x == nx - 1) {
-                        p[b][2] = ghost_value<T>(p[b][1], p[b][0]);
-                        d[b][2] = p[b][2] >= T(0) ? T(0) : d[b][1];
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    if (rd == 0) {
-                        p[0][e] = ghost_value<T>(p[1][e], p[2][e]);
-                        d[0][e] = p[0][e] >= T(0) ? T(0) : d[1][e];
-                    }
-                    if (rd == ny - 1) {
-                        p[2][e] = ghost_value<T>(p[1][e], p[0][e]);
-                        d[2][e] = p[2][e] >= T(0) ? T(0) : d[1][e];
-                    }
+                    const T2 o = sm.SQ[sl[b] * NT + c];
+                    p[b][0] = sm.SQ[sl[b] * NT + c - 1].y;
+                    p[b][1] = o.x;
+                    p[b][2] = o.y;
+                    p[b][3] = sm.SQ[sl[b] * NT + c + 1].x;
                 }
             }
-            const size_t g = (size_t)rd * nx + x;
-            int cls = fuel[g];
-            cls = cls > ncm1 ? ncm1 : cls;
-            const T *co = lut + cls * K_N;
-            const T Fn = cell_fraction_vals<T>(p[0][0], p[0][1], p[0][2], p[1][0], p[1][1], p[1][2],
-                                               p[2][0], p[2][1], p[2][2], d[0][0], d[0][1], d[0][2],
-                                               d[1][0], d[1][1], d[1][2], d[2][0], d[2][1], d[2][2],
-                                               co[K_TF]);
-            F_out[g] = Fn;
-            const T dF = pf_F - Fn;
-            acc_s += dF * co[K_HS];
-            acc_q += dF * co[K_HQ];
+            T vmin[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) vmin[h] = min_val(min_val(p[0][h], p[1][h]), p[2][h]);
+            const T mid = min_val(vmin[1], vmin[2]);
+            const T mn0 = min_val(vmin[0], mid), mn1 = min_val(mid, vmin[3]);
+            const bool edge = xa <= 0 || xa + 1 >= nx - 1 || rd == 0 || rd == ny - 1;
+            T Fn[2] = {T(1), T(1)};
+            if (mn0 < T(0) || mn1 < T(0) || edge) {
+                T d[3][4];
+                const int sl[3] = {s2, s3, s0};
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const T2 o = sm.SD[sl[b] * NT + c];
+                    d[b][0] = sm.SD[sl[b] * NT + c - 1].y;
+                    d[b][1] = o.x;
+                    d[b][2] = o.y;
+                    d[b][3] = sm.SD[sl[b] * NT + c + 1].x;
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (!m_out[j]) continue;
+                    T q[3][3], e[3][3];
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+#pragma unroll
+                        for (int h = 0; h < 3; ++h) {
+                            q[b][h] = p[b][j + h];
+                            e[b][h] = d[b][j + h];
+                        }
+                    const int x = xa + j;
+                    if (x == 0 || x == nx - 1 || rd == 0 || rd == ny - 1) {
+                        // ghost ring of psi^{n+1} (x first, then y) and of t - t_i
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            const int yy = rd + b - 1;
+                            if (yy < 0 || yy >= ny) continue;
+                            if (x == 0) {
+                                q[b][0] = ghost_value<T>(q[b][1], q[b][2]);
+                                e[b][0] = q[b][0] >= T(0) ? T(0) : e[b][1];
+                            }
+                            if (x == nx - 1) {
+                                q[b][2] = ghost_value<T>(q[b][1], q[b][0]);
+                                e[b][2] = q[b][2] >= T(0) ? T(0) : e[b][1];
+                            }
+                        }
+#pragma unroll
+                        for (int h = 0; h < 3; ++h) {
+                            if (rd == 0) {
+                                q[0][h] = ghost_value<T>(q[1][h], q[2][h]);
+                                e[0][h] = q[0][h] >= T(0) ? T(0) : e[1][h];
+                            }
+                            if (rd == ny - 1) {
+                                q[2][h] = ghost_value<T>(q[1][h], q[0][h]);
+                                e[2][h] = q[2][h] >= T(0) ? T(0) : e[1][h];
+                            }
+                        }
+                    }
+                    const int cls0 = a.fuel[(size_t)rd * nx + x];
+                    const int cls = cls0 > ncm1 ? ncm1 : cls0;
+                    Fn[j] = cell_fraction_vals<T>(q[0][0], q[0][1], q[0][2], q[1][0], q[1][1],
+                                                  q[1][2], q[2][0], q[2][1], q[2][2], e[0][0],
+                                                  e[0][1], e[0][2], e[1][0], e[1][1], e[1][2],
+                                                  e[2][0], e[2][1], e[2][2], sm.lut[cls * 8 + 6]);
+                }
+            }
+            const size_t g = (size_t)rd * nx + xa;
+            T *fo = static_cast<T *>(a.F_out);
+            T2 FN;
+            FN.x = Fn[0];
+            FN.y = Fn[1];
+            if (vec && m_out[0] && m_out[1]) {
+                *reinterpret_cast<T2 *>(fo + g) = FN;
+            } else {
+                if (m_out[0]) fo[g] = FN.x;
+                if (m_out[1]) fo[g + 1] = FN.y;
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const T dF = pick<T>(pf_F, j) - Fn[j];
+                if (m_out[j] && dF != T(0)) {
+                    const int cls0 = a.fuel[g + j];
+                    const int cls = cls0 > ncm1 ? ncm1 : cls0;
+                    acc_s[j] += dF * sm.lut[cls * 8 + 7];
+                    acc_q[j] += dF * sm.lutq[cls];
+                }
+            }
         }
         // prefetch F^n of row k for the next iteration's quadrature
-        pf_F = (c_out && k >= y0 && k < y0 + La) ? F_in[(size_t)k * nx + x] : T(0);
-        const bool band_end = drow && ((rd - y0 + 1) % sry == 0);
-        const int par = ((rd - y0) / sry) & 1;
-        if (band_end) {
-            HB[par][0][c] = acc_s;
-            HB[par][1][c] = acc_q;
-            acc_s = T(0);
-            acc_q = T(0);
+        if (k >= y0 && k < y0 + La && (m_out[0] || m_out[1]))
+            pf_F = ld2(static_cast<const T *>(a.F_in), k, m_out[0], m_out[1]);
+        bool band_end = false;
+        if (drow) {
+            if (++bcnt == sry) {
+                band_end = true;
+                bcnt = 0;
+                T *hb = sm.HB + bpar * 4 * NT;
+                hb[2 * c] = acc_s[0];
+                hb[2 * c + 1] = acc_s[1];
+                hb[2 * NT + 2 * c] = acc_q[0];
+                hb[2 * NT + 2 * c + 1] = acc_q[1];
+                acc_s[0] = acc_s[1] = acc_q[0] = acc_q[1] = T(0);
+            }
         }
         __syncthreads();
-        // ---- average of the band's atmospheric cells (after its last row)
+        // ---- average over the band's atmospheric cells (after its last row)
         if (band_end) {
             const int kxa = Wa / srx;
             if (c < kxa) {
+                const T *hb = sm.HB + bpar * 4 * NT;
                 double h0 = 0.0, h1 = 0.0;
                 for (int e = 0; e < srx; ++e) {
-                    const T v0 = HB[par][0][kMarchHalo + c * srx + e];
-                    const T v1 = HB[par][1][kMarchHalo + c * srx + e];
+                    const int lc = kMarchHalo + c * srx + e;
+                    const T v0 = hb[lc], v1 = hb[2 * NT + lc];
                     if (v0 != T(0)) h0 += (double)v0;
                     if (v1 != T(0)) h1 += (double)v1;
                 }
-                const double scale = 1.0 / (a.dt * (double)srx * (double)sry);
                 const size_t ga = (size_t)(rd / sry) * nxa + (x0 / srx + c);
-                if (a.heat_s) a.heat_s[ga] = h0 * scale;
-                if (a.heat_l) a.heat_l[ga] = h1 * scale;
+                if (a.heat_s) a.heat_s[ga] = h0 * hscale;
+                if (a.heat_l) a.heat_l[ga] = h1 * hscale;
             }
+            bpar ^= 1;
         }
     }
-    if (st) atomicOr(&s_status, st);
+
+    // one step of the strip with output origin (x0_, y0_); tstart_ is the
+    // model time at the step start
+    __device__ __forceinline__ void run(int x0_, int y0_, double tstart_) {
+        const int NT = kMarchThreads;
+        c = threadIdx.x;
+        srx = a.srx;
+        sry = a.sry;
+        nx = a.nx;
+        ny = a.ny;
+        nxa = a.nxa;
+        nya = a.nya;
+        x0 = x0_;
+        y0 = y0_;
+        const int W = a.kx * srx, L = a.ky * sry;
+        Wa = min(W, nx - x0);
+        La = min(L, ny - y0);
+        xa = x0 - kMarchHalo + kMarchCols * c;
+        vec = (nx % 2) == 0;  // x0 and xa are even (W even)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int lc = kMarchCols * c + j, x = xa + j;
+            const bool xin = x >= 0 && x < nx;
+            m_load[j] = xin && lc >= 1 && lc < Wa + 7;
+            m_s1[j] = xin && lc >= 2 && lc < Wa + 6;
+            m_s2[j] = xin && lc >= 3 && lc < Wa + 5;
+            m_out[j] = lc >= 4 && lc < Wa + 4;
+        }
+        dt = T(a.dt);
+        idx = T(1) / T(a.dx);
+        idy = T(1) / T(a.dy);
+        i2dx = T(1) / (T(2) * T(a.dx));
+        i2dy = T(1) / (T(2) * T(a.dy));
+        eps = T(a.eps);
+        tstart = tstart_;
+        t1 = tstart + a.dt;
+        ncm1 = a.ncls - 1;
+        band = a.band;
+        st = 0;
+        acc_s[0] = acc_s[1] = acc_q[0] = acc_q[1] = T(0);
+        bcnt = 0;
+        bpar = 0;
+        ju_hi = -1;
+        jv_hi = -1;
+
+        // ---- set-up: coefficients, row and column wind weights
+        for (int k = c; k < a.ncls; k += NT) {
+            const double *co = a.coef + (size_t)k * K_N;
+            T *l = sm.lut + k * 8;
+            l[0] = T(co[K_S0]);
+            l[1] = T(co[K_R0]);
+            l[2] = T(co[K_B]);
+            l[3] = T(co[K_C]);
+            l[4] = T(co[K_D]);
+            l[5] = T(co[K_E]);
+            l[6] = T(co[K_TF]);
+            l[7] = T(co[K_HS]);
+            sm.lutq[k] = T(co[K_HQ]);
+        }
+        for (int i = c; i < La + 4; i += NT) {
+            const int r = y0 - 2 + i;
+            MarchRow<T> w;
+            w.ju0 = w.jv0 = 0;
+            w.wyu = w.wyv = T(0);
+            if (r >= 0 && r < ny) {
+                int j1;
+                const T yr = (T(r) + T(0.5)) / T(sry);
+                lin_idx<T>(yr - T(0.5), nya, w.ju0, j1, w.wyu);
+                lin_idx<T>(yr, nya + 1, w.jv0, j1, w.wyv);
+            }
+            sm.row[i] = w;
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            MarchCol<T> cw;
+            cw.iu0 = cw.iu1 = cw.iv0 = cw.iv1 = 0;
+            cw.wxu = cw.wxv = T(0);
+            const int x = xa + j;
+            if (x >= 0 && x < nx) {
+                const T xr = (T(x) + T(0.5)) / T(srx);
+                lin_idx<T>(xr, nxa + 1, cw.iu0, cw.iu1, cw.wxu);
+                lin_idx<T>(xr - T(0.5), nxa, cw.iv0, cw.iv1, cw.wxv);
+            }
+            sm.col[kMarchCols * c + j] = cw;
+        }
+        __syncthreads();
+
+        const int k0 = y0 - 6, k1 = y0 + La;
+        hscale = 1.0 / (a.dt * (double)srx * (double)sry);
+        pf_psi.x = pf_psi.y = T(0);
+        if (in_rows(k0 + 3, y0 - 3, y0 + La + 3))
+            pf_psi = ld2(static_cast<const T *>(a.psi_in), k0 + 3, m_load[0], m_load[1]);
+        pf_cls[0] = pf_cls[1] = 0;
+        pf_zx.x = pf_zx.y = pf_zy.x = pf_zy.y = T(0);
+        pf_m.x = pf_m.y = T(1);
+        load_env(k0 + 2);
+        e_cls[0] = e_cls[1] = 0;
+        e_zx = pf_zx;
+        e_zy = pf_zy;
+        e_m = pf_m;
+        e_un = pf_zx;
+        e_vn = pf_zx;
+        pf_F.x = pf_F.y = T(1);
+#pragma unroll 1
+        for (int k = k0; k <= k1; ++k) iter(k);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks) k_fire_march(const StepArgs a) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    MarchSmem<T> sm;
+    sm.carve(dyn_smem, a.ky * a.sry, a.ncls);
+    if (threadIdx.x == 0) {
+        *sm.status = 0;
+        if (blockIdx.x == 0 && blockIdx.y == 0) *a.t_out = *a.t_in + a.dt;
+    }
+    MarchStrip<T> s(a, sm);
+    s.run(blockIdx.x * a.kx * a.srx, blockIdx.y * a.ky * a.sry, *a.t_in);
+    if (s.st) atomicOr(sm.status, s.st);
     __syncthreads();
-    if (c == 0 && s_status) atomicOr(a.status, s_status);
+    if (threadIdx.x == 0 && *sm.status) atomicOr(a.status, *sm.status);
 }
 
 template <typename T>
-size_t march_smem_bytes(int ky, int sry) {
-    return (size_t)(ky * sry + 4) * sizeof(RowWeights<T>);
+size_t march_smem_bytes(int ky, int sry, int ncls) {
+    return MarchSmem<T>::bytes(ky * sry, ncls);
 }
 
 template <typename T>
 cudaError_t launch_march(const StepArgs &a, cudaStream_t s) {
     const int W = a.kx * a.srx, L = a.ky * a.sry;
     dim3 grid((a.nx + W - 1) / W, (a.ny + L - 1) / L);
-    k_fire_march<T><<<grid, kMarchThreads, march_smem_bytes<T>(a.ky, a.sry), s>>>(a);
+    k_fire_march<T><<<grid, kMarchThreads, march_smem_bytes<T>(a.ky, a.sry, a.ncls), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -334,7 +637,7 @@ cudaError_t prepare_march_kernel(size_t smem_bytes) {
 }
 
 #define WF_INSTANTIATE_MARCH(T)                                               \
-    template size_t march_smem_bytes<T>(int, int);                            \
+    template size_t march_smem_bytes<T>(int, int, int);                       \
     template cudaError_t launch_march<T>(const StepArgs &, cudaStream_t);     \
     template cudaError_t prepare_march_kernel<T>(size_t);
 

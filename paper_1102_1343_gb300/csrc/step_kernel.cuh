@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
             cls = cls > ncm1 ? ncm1 : cls;
             T un, vn;
             wind_at<T>(wu, wv, a.nxa, a.nya, srx, sry, gx, gy, un, vn);
-            if (!isfinite(un) || !isfinite(vn)) st |= ST_NONFINITE;
+            if (!finite_val(un) || !finite_val(vn)) st |= ST_NONFINITE;
             const T m = mult ? mult[g] : T(1);
             const int c = (ly + 1) * BW3 + (lx + 1);
             const T F = rhs_at<T>(P0, c, BW3, idx, idy, i2dx, i2dy, eps, lut + cls * K_N, m, un,
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
             Dl[l1] = d;
             if (own) {
                 psi_out[g] = pn;
-                if (!isfinite(pn)) st |= ST_NONFINITE;
+                if (!finite_val(pn)) st |= ST_NONFINITE;
                 const bool band = gx < a.band || gy < a.band || gx >= nx - a.band || gy >= ny - a.band;
                 if (band && pn < T(0)) st |= ST_BOUNDARY;
             }
@@ -328,6 +328,27 @@ __global__ void k_ignite(const IgniteArgs a) {
         bool changed = false, tchanged = false;
         for (int q = 0; q < a.nseg; ++q) {
             const IgnSeg &s = a.seg[q];
+            // FP32 prefilter (offsets taken in double, then rounded): skip the
+            // segment only when the exact test below can change neither psi
+            // (needs dist < psi + rho) nor the ignition time (dist <= rho);
+            // delta bounds the FP32 error of the distance
+            {
+                const float qx = (float)(x - s.ax), qy = (float)(y - s.ay);
+                const float sx = (float)(s.bx - s.ax), sy = (float)(s.by - s.ay);
+                const float L2f = sx * sx + sy * sy;
+                float u = L2f > 0.0f ? (qx * sx + qy * sy) / L2f : 0.0f;
+                u = fminf(fmaxf(u, 0.0f), 1.0f);
+                const float rx = qx - u * sx, ry = qy - u * sy;
+                const float d2 = rx * rx + ry * ry;
+                const float delta = 4e-7f * (fabsf(qx) + fabsf(qy) + fabsf(sx) + fabsf(sy)) + 1e-6f;
+                const float lim = (float)((double)p + s.rho);
+                const float dl = lim + delta + 1e-6f * fabsf(lim);
+                const float rho = (float)s.rho;
+                const float dr = rho + delta + 1e-6f * rho;
+                const bool may_min = dl > 0.0f && d2 <= dl * dl;
+                const bool may_ti = (double)p > 0.0 && isinf(ti) && d2 <= dr * dr;
+                if (!may_min && !may_ti) continue;
+            }
             const double dxs = s.bx - s.ax, dys = s.by - s.ay;
             const double qx = x - s.ax, qy = y - s.ay;
             const double L2 = dxs * dxs + dys * dys;

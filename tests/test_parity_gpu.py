@@ -83,6 +83,18 @@ def test_fp64_landscape_ragged_tiles(pkg, tile):
     assert Qo > 0
 
 
+@pytest.mark.parametrize("tile", [None, (1, 2, 3), (0, 4, 4)])
+def test_fp64_odd_mesh_width(pkg, tile):
+    """Refinement 5 on 23x17 atmos cells: an odd fire-mesh width (115), so the
+    marching kernel takes its unpaired (scalar) loads and stores."""
+    w = synth.random_landscape(23, 17, sr=5, seed=22, ignition="points", n_points=4,
+                               edge_margin=150.0, steps=80)
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+
+
 def test_fp64_anisotropic_multiplier_and_segments(pkg):
     """Refinement 4 x 6 with unequal atmos spacing, a per-node spread
     multiplier, a growing segment ignition and a delayed instantaneous one."""
