@@ -214,6 +214,43 @@ int fire_get_kernel(const fire_ctx *ctx, int *variant, int *kx, int *ky);
 int fire_enable_timing(fire_ctx *ctx, int on);
 int fire_kernel_time_ms(fire_ctx *ctx, double *ms, long *launches);
 
+/* One fire step on caller-owned state that allocates no memory: no
+ * cudaMalloc, cudaFree or allocating library call, and no context.  For
+ * callers that cannot allocate device memory while they run: code being
+ * captured into a CUDA graph, applications whose device memory comes from
+ * their own pool or from a host framework that forbids driver allocations
+ * after start-up, coupled models that must not touch the allocator inside
+ * their time loop.  The paper has no counterpart: it is a way of calling the
+ * same step as fire_step (same kernels, same results) without a fire_ctx.
+ *   grid, classes[n_classes]  as for fire_init; 1 <= n_classes <= 64
+ *                             (FIRE_MAX_CLASSES), more is FIRE_ERR_ARG
+ *   psi_in/out, frac_in/out   [NY][NX] device, context precision; in and out
+ *                             must be different buffers
+ *   tign_dev                  [NY][NX] device double, updated in place
+ *   fuel_class_dev, spread_mult_dev (nullable), dzdx_dev, dzdy_dev,
+ *   wind_u_dev, wind_v_dev    as for fire_init / fire_step
+ *   t, dt                     model time at the step start, time step (s)
+ *   heat_sens_dev, heat_lat_dev  [ny_atm][nx_atm] device double, nullable
+ *   status_dev                device int that faults are OR-ed into
+ *                             (bit 1 boundary, 2 non-finite), nullable
+ *   cuda_stream               stream for all work of the call
+ * Ignitions are not applied: the state passed in already holds them.
+ * Intermediate values (the class table, its coefficients, the start and end
+ * time, and the status word when status_dev is NULL) live in one file-scope
+ * device array of about 11 KB per device, held until the process exits.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make it before any stream
+ * capture.  Every call shares the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (other streams, other host
+ * threads) race with each other: serialise them. */
+int fire_step_noalloc(const fire_grid_desc *grid, const fire_fuel_class *classes, int n_classes,
+                      const void *psi_in_dev, void *psi_out_dev, const void *frac_in_dev,
+                      void *frac_out_dev, double *tign_dev, const uint8_t *fuel_class_dev,
+                      const void *spread_mult_dev, const void *dzdx_dev, const void *dzdy_dev,
+                      const void *wind_u_dev, const void *wind_v_dev, double t, double dt,
+                      double *heat_sens_dev, double *heat_lat_dev, int *status_dev,
+                      void *cuda_stream);
+
 const char *fire_strerror(int code);
 
 void fire_destroy(fire_ctx *ctx);

@@ -103,6 +103,9 @@ def load_library(path: str | None = None):
     L.fire_strerror.restype = C.c_char_p
     L.fire_destroy.argtypes = [_P]
     L.fire_destroy.restype = None
+    L.fire_step_noalloc.argtypes = ([C.POINTER(fire_grid_desc), C.POINTER(fire_fuel_class), C.c_int]
+                                    + [_P] * 11 + [C.c_double, C.c_double] + [_P] * 4)
+    L.fire_step_noalloc.restype = C.c_int
     for name in ABI_SYMBOLS:
         f = getattr(L, name)
         if f.restype is C.c_int or name in ("fire_init", "fire_step", "fire_step_host",
@@ -255,6 +258,23 @@ def fire_kernel_time_ms(ctx):
     _check(load_library().fire_kernel_time_ms(ctx, C.byref(ms), C.byref(n)),
            "fire_kernel_time_ms")
     return ms.value, n.value
+
+
+def fire_step_noalloc(grid: fire_grid_desc, classes, psi_in_dev, psi_out_dev, frac_in_dev,
+                      frac_out_dev, tign_dev, fuel_class_dev, spread_mult_dev, dzdx_dev,
+                      dzdy_dev, wind_u_dev, wind_v_dev, t, dt, heat_sens_dev=None,
+                      heat_lat_dev=None, status_dev=None, cuda_stream=None) -> int:
+    """One fire step on caller-owned buffers without any allocation (see the
+    header): the state is passed in and out, nothing is kept between calls."""
+    L = load_library()
+    cls = make_classes(classes)
+    code = L.fire_step_noalloc(C.byref(grid), cls, len(classes), _ptr(psi_in_dev),
+                               _ptr(psi_out_dev), _ptr(frac_in_dev), _ptr(frac_out_dev),
+                               _ptr(tign_dev), _ptr(fuel_class_dev), _ptr(spread_mult_dev),
+                               _ptr(dzdx_dev), _ptr(dzdy_dev), _ptr(wind_u_dev), _ptr(wind_v_dev),
+                               float(t), float(dt), _ptr(heat_sens_dev), _ptr(heat_lat_dev),
+                               _ptr(status_dev), _ptr(cuda_stream) or None)
+    return _check(code, "fire_step_noalloc")
 
 
 def fire_destroy(ctx) -> None:
