@@ -251,7 +251,78 @@ int fire_step_noalloc(const fire_grid_desc *grid, const fire_fuel_class *classes
                       double *heat_sens_dev, double *heat_lat_dev, int *status_dev,
                       void *cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Batched ensemble: independent fire runs (different mesh sizes, fuels,
+ * terrain, winds) advanced together.  Each fire_ensemble_step call runs all
+ * members for nsteps steps in ONE persistent cooperative kernel launch (a
+ * work list of member strips per step, a bounded grid-wide barrier between
+ * steps), captured in a CUDA graph and replayed while its shape is
+ * unchanged.  A member advanced here matches the same member advanced alone
+ * by fire_step with the same kernel configuration.  Motivation: ensemble
+ * data assimilation (Sect. 7, "Data assimilation"); not part of the paper's
+ * fire step itself.
+ * --------------------------------------------------------------------- */
+typedef struct fire_ensemble fire_ensemble;
+#define FIRE_MAX_MEMBERS 1024
+
+/* One member: the arguments of fire_init (device arrays as there; moisture
+ * per node is not supported).  All members must share the precision. */
+typedef struct {
+    fire_grid_desc grid;
+    const fire_fuel_class *classes;
+    int n_classes;
+    const uint8_t *fuel_class_dev;
+    const void *spread_mult_dev;
+    const void *dzdx_dev;
+    const void *dzdy_dev;
+    const fire_ignition *ignitions;
+    int n_ign;
+} fire_member_desc;
+
+/* Creates the members (fire_init each, on cuda_stream) and the work list.
+ * Members need refinements that the marching kernel supports (sr_x <= 124). */
+int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_desc *members,
+                         void *cuda_stream);
+
+/* nsteps steps of every member with member winds wind_u_dev[m],
+ * wind_v_dev[m] (host arrays of device pointers, context precision, held
+ * constant over the call); heat_sens_dev / heat_lat_dev: host arrays of device
+ * pointers (the arrays and their entries may be NULL) receiving each member's
+ * last-step fluxes.  Steps in which a member has an active ignition window run
+ * one by one through fire_step; the others in one persistent launch. */
+int fire_ensemble_step(fire_ensemble *ens, int nsteps, double dt, const void *const *wind_u_dev,
+                       const void *const *wind_v_dev, double *const *heat_sens_dev,
+                       double *const *heat_lat_dev);
+
+/* The member's context (owned by the ensemble: use it for fire_get_state,
+ * fire_set_state, fire_status; do not destroy it). */
+int fire_ensemble_member(fire_ensemble *ens, int member, fire_ctx **ctx);
+
+/* Waits; returns FIRE_ERR_TIMEOUT if a barrier wait gave up, else the worst
+ * member status; member_status (nullable host array [n]) receives each. */
+int fire_ensemble_status(fire_ensemble *ens, int *member_status);
+int fire_ensemble_clear_status(fire_ensemble *ens);
+
+/* Strip shape of the persistent kernel in fire nodes (rounded to whole
+ * atmospheric cells and an even width per member); the launch grid is sized
+ * to the CTAs that fit on the device at once.  fire_ensemble_get_kernel
+ * reports the grid and the number of work items per step. */
+int fire_ensemble_set_kernel(fire_ensemble *ens, int strip_columns, int strip_rows);
+int fire_ensemble_get_kernel(const fire_ensemble *ens, int *grid_ctas, int *work_items);
+
+/* Test hook for the bounded barrier: CTA skip_block (-1: none) never
+ * arrives at the barriers, and waits give up after spin_limit polls (about
+ * 100 ns each), setting FIRE_ERR_TIMEOUT and ending the launch. */
+int fire_ensemble_set_barrier_test(fire_ensemble *ens, int skip_block, long long spin_limit);
+
+void fire_ensemble_destroy(fire_ensemble *ens);
+
 const char *fire_strerror(int code);
+
+/* Name and message of the last CUDA error an entry point saw on the calling
+ * host thread, with the call that returned it ("no error" if none): detail
+ * behind FIRE_ERR_CUDA / FIRE_ERR_OOM.  The string is owned by the library. */
+const char *fire_last_cuda_error(void);
 
 void fire_destroy(fire_ctx *ctx);
 

@@ -40,14 +40,21 @@ FIRE_MAX_IGNITIONS = 256
 ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get_state",
                "fire_set_state", "fire_status", "fire_clear_status", "fire_mesh_size",
                "fire_time", "fire_set_kernel", "fire_get_kernel", "fire_enable_timing",
-               "fire_kernel_time_ms", "fire_strerror", "fire_destroy")
+               "fire_kernel_time_ms", "fire_strerror", "fire_last_cuda_error", "fire_destroy",
+               "fire_step_noalloc",
+               "fire_ensemble_create", "fire_ensemble_step", "fire_ensemble_member",
+               "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
+               "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test",
+               "fire_ensemble_destroy")
 
 
 class FireError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
-        super().__init__(f"{what}: {fire_strerror(code)} ({code})" if what else
-                         f"{fire_strerror(code)} ({code})")
+        msg = f"{what}: {fire_strerror(code)} ({code})" if what else f"{fire_strerror(code)} ({code})"
+        if code in (FIRE_ERR_CUDA, FIRE_ERR_OOM):
+            msg += f" [{fire_last_cuda_error()}]"
+        super().__init__(msg)
 
 
 class fire_grid_desc(C.Structure):
@@ -69,8 +76,17 @@ class fire_ignition(C.Structure):
                 ("t_start", C.c_double), ("radius", C.c_double), ("speed", C.c_double)]
 
 
-_lib = None
 _P = C.c_void_p
+
+
+class fire_member_desc(C.Structure):
+    _fields_ = [("grid", fire_grid_desc), ("classes", C.POINTER(fire_fuel_class)),
+                ("n_classes", C.c_int), ("fuel_class_dev", _P), ("spread_mult_dev", _P),
+                ("dzdx_dev", _P), ("dzdy_dev", _P), ("ignitions", C.POINTER(fire_ignition)),
+                ("n_ign", C.c_int)]
+
+
+_lib = None
 
 
 def load_library(path: str | None = None):
@@ -101,11 +117,28 @@ def load_library(path: str | None = None):
     L.fire_kernel_time_ms.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_long)]
     L.fire_strerror.argtypes = [C.c_int]
     L.fire_strerror.restype = C.c_char_p
+    L.fire_last_cuda_error.argtypes = []
+    L.fire_last_cuda_error.restype = C.c_char_p
     L.fire_destroy.argtypes = [_P]
     L.fire_destroy.restype = None
     L.fire_step_noalloc.argtypes = ([C.POINTER(fire_grid_desc), C.POINTER(fire_fuel_class), C.c_int]
                                     + [_P] * 11 + [C.c_double, C.c_double] + [_P] * 4)
     L.fire_step_noalloc.restype = C.c_int
+    L.fire_ensemble_create.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(fire_member_desc), _P]
+    L.fire_ensemble_step.argtypes = [_P, C.c_int, C.c_double, C.POINTER(_P), C.POINTER(_P),
+                                     C.POINTER(_P), C.POINTER(_P)]
+    L.fire_ensemble_member.argtypes = [_P, C.c_int, C.POINTER(_P)]
+    L.fire_ensemble_status.argtypes = [_P, C.POINTER(C.c_int)]
+    L.fire_ensemble_clear_status.argtypes = [_P]
+    L.fire_ensemble_set_kernel.argtypes = [_P, C.c_int, C.c_int]
+    L.fire_ensemble_get_kernel.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fire_ensemble_set_barrier_test.argtypes = [_P, C.c_int, C.c_longlong]
+    L.fire_ensemble_destroy.argtypes = [_P]
+    L.fire_ensemble_destroy.restype = None
+    for name in ("fire_ensemble_create", "fire_ensemble_step", "fire_ensemble_member",
+                 "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
+                 "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test"):
+        getattr(L, name).restype = C.c_int
     for name in ABI_SYMBOLS:
         f = getattr(L, name)
         if f.restype is C.c_int or name in ("fire_init", "fire_step", "fire_step_host",
@@ -147,6 +180,10 @@ def _check(code, what):
 
 def fire_strerror(code: int) -> str:
     return load_library().fire_strerror(int(code)).decode()
+
+
+def fire_last_cuda_error() -> str:
+    return load_library().fire_last_cuda_error().decode()
 
 
 def make_grid(nx_atm, ny_atm, sr_x, sr_y, dx_atm, dy_atm, precision=FIRE_FP32, boundary_band=1,
@@ -275,6 +312,91 @@ def fire_step_noalloc(grid: fire_grid_desc, classes, psi_in_dev, psi_out_dev, fr
                                float(t), float(dt), _ptr(heat_sens_dev), _ptr(heat_lat_dev),
                                _ptr(status_dev), _ptr(cuda_stream) or None)
     return _check(code, "fire_step_noalloc")
+
+
+def _ptr_array(items):
+    arr = (_P * len(items))()
+    for k, x in enumerate(items):
+        arr[k] = _ptr(x)
+    return arr
+
+
+def fire_ensemble_create(members, cuda_stream=None) -> int:
+    """members: list of dicts with the fire_init arguments (grid, classes,
+    fuel_class_dev, spread_mult_dev, dzdx_dev, dzdy_dev, ignitions)."""
+    L = load_library()
+    descs = (fire_member_desc * len(members))()
+    keep = []
+    for k, m in enumerate(members):
+        cls = make_classes(m["classes"])
+        ign = make_ignitions(list(m.get("ignitions", ())))
+        keep += [cls, ign]
+        descs[k].grid = m["grid"]
+        descs[k].classes = C.cast(cls, C.POINTER(fire_fuel_class))
+        descs[k].n_classes = len(m["classes"])
+        descs[k].fuel_class_dev = _ptr(m["fuel_class_dev"])
+        descs[k].spread_mult_dev = _ptr(m.get("spread_mult_dev"))
+        descs[k].dzdx_dev = _ptr(m["dzdx_dev"])
+        descs[k].dzdy_dev = _ptr(m["dzdy_dev"])
+        descs[k].ignitions = C.cast(ign, C.POINTER(fire_ignition))
+        descs[k].n_ign = len(list(m.get("ignitions", ())))
+    out = _P()
+    _check(L.fire_ensemble_create(C.byref(out), len(members), descs, _ptr(cuda_stream) or None),
+           "fire_ensemble_create")
+    return out.value
+
+
+def fire_ensemble_step(ens, nsteps, dt, wind_u_dev, wind_v_dev, heat_sens_dev=None,
+                       heat_lat_dev=None) -> int:
+    L = load_library()
+    hs = _ptr_array(heat_sens_dev) if heat_sens_dev is not None else None
+    hl = _ptr_array(heat_lat_dev) if heat_lat_dev is not None else None
+    return _check(L.fire_ensemble_step(ens, int(nsteps), float(dt), _ptr_array(wind_u_dev),
+                                       _ptr_array(wind_v_dev), hs, hl), "fire_ensemble_step")
+
+
+def fire_ensemble_member(ens, member) -> int:
+    out = _P()
+    _check(load_library().fire_ensemble_member(ens, int(member), C.byref(out)),
+           "fire_ensemble_member")
+    return out.value
+
+
+def fire_ensemble_status(ens, n_members=None):
+    """Synchronises; returns (code, per-member codes or None)."""
+    if n_members:
+        arr = (C.c_int * n_members)()
+        code = load_library().fire_ensemble_status(ens, arr)
+        return code, list(arr)
+    return load_library().fire_ensemble_status(ens, None), None
+
+
+def fire_ensemble_clear_status(ens) -> int:
+    return _check(load_library().fire_ensemble_clear_status(ens), "fire_ensemble_clear_status")
+
+
+def fire_ensemble_set_kernel(ens, strip_columns, strip_rows) -> int:
+    return _check(load_library().fire_ensemble_set_kernel(ens, int(strip_columns),
+                                                          int(strip_rows)),
+                  "fire_ensemble_set_kernel")
+
+
+def fire_ensemble_get_kernel(ens):
+    g, n = C.c_int(), C.c_int()
+    _check(load_library().fire_ensemble_get_kernel(ens, C.byref(g), C.byref(n)),
+           "fire_ensemble_get_kernel")
+    return g.value, n.value
+
+
+def fire_ensemble_set_barrier_test(ens, skip_block, spin_limit) -> int:
+    return _check(load_library().fire_ensemble_set_barrier_test(ens, int(skip_block),
+                                                                int(spin_limit)),
+                  "fire_ensemble_set_barrier_test")
+
+
+def fire_ensemble_destroy(ens) -> None:
+    if ens:
+        load_library().fire_ensemble_destroy(ens)
 
 
 def fire_destroy(ctx) -> None:

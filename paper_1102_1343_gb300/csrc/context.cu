@@ -4,6 +4,7 @@
 // sticky status word, checkpoint/resume and kernel timing.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -63,10 +64,22 @@ struct fire_ctx {
     double ms_done = 0;
 };
 
+namespace wf {
+namespace {
+thread_local char g_last_error[256] = "no error";
+}
+const char *g_last_error_ptr() { return g_last_error; }
+void record_cuda_error(cudaError_t e, const char *where) {
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s)", where, cudaGetErrorName(e),
+             cudaGetErrorString(e));
+}
+}  // namespace wf
+
 namespace {
 
-int cuda_err(cudaError_t e) {
+int cuda_err_at(cudaError_t e, const char *where) {
     if (e == cudaSuccess) return FIRE_OK;
+    record_cuda_error(e, where);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return FIRE_ERR_OOM;
@@ -74,6 +87,7 @@ int cuda_err(cudaError_t e) {
     return FIRE_ERR_CUDA;
 }
 
+#define cuda_err(call) cuda_err_at((call), #call)
 #define WF_CHECK(call)                         \
     do {                                       \
         int _r = cuda_err(call);               \
@@ -316,6 +330,8 @@ cudaStream_t ctx_stream(const fire_ctx *c) { return c->stream; }
 
 extern "C" {
 
+const char *fire_last_cuda_error(void) { return wf::g_last_error_ptr(); }
+
 const char *fire_strerror(int code) {
     switch (code) {
         case FIRE_OK: return "ok";
@@ -509,6 +525,7 @@ int fire_run(fire_ctx *c, int nsteps, double dt, const void *u, const void *v, d
         if (!c->graph || c->g_u != u || c->g_v != v || c->g_dt != dt || c->g_hs != hs ||
             c->g_hl != hl || c->g_kx != c->kx || c->g_ky != c->ky || c->g_variant != c->variant) {
             if (c->graph) {
+                WF_CHECK(cudaStreamSynchronize(c->stream));  // the old graph may be in flight
                 cudaGraphExecDestroy(c->graph);
                 c->graph = nullptr;
             }

@@ -1,0 +1,505 @@
+// Batched ensemble of independent fire runs (members of different mesh
+// sizes, fuels, winds) advanced together by ONE persistent cooperative
+// launch per call: the kernel loops over the steps, and within a step over
+// a work list of (member, strip) items handed out round-robin to the
+// resident CTAs; a grid-wide barrier separates the steps.  Each member is an
+// ordinary fire context (same state layout, same marching-strip device code
+// as fire_step), so a member advanced here matches the same member advanced
+// alone.  The launch (with the reset of the barrier word) is captured in a
+// CUDA graph and replayed while its arguments do not change.
+//
+// The barrier's wait is bounded: a CTA that waits longer than the spin limit
+// sets the ensemble's TIMEOUT bit and an abort flag, and every CTA leaves the
+// kernel at its next barrier, so a lost CTA ends the launch with an error
+// instead of hanging the device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fire_internal.h"
+#include "march_kernel.cuh"
+
+using namespace wf;
+
+namespace {
+
+struct EnsItem {
+    int member, x0, y0;
+};
+
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    int abort;
+    int status;  // ensemble-wide status bits (TIMEOUT)
+};
+
+// values that change from call to call, read by the kernel from device memory
+// so that a captured launch can be replayed
+struct EnsRun {
+    double t0;
+    int parity0;
+    int nsteps;
+    long long spin_limit;
+    int skip_block;  // test hook: this CTA never arrives at a barrier (-1: none)
+};
+
+struct EnsembleArgs {
+    const StepArgs *margs;  // [2 * n_members]: parity 0 and 1 of each member
+    const EnsItem *items;
+    int n_items;
+    int n_members;
+    double dt;
+    GridBar *bar;
+    const EnsRun *run;
+};
+
+// grid-wide barrier with a bounded wait; returns false when the launch must end
+__device__ bool grid_barrier(GridBar *b, long long spin_limit, bool skip) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile GridBar *vb = b;
+        bool ok = vb->abort == 0;
+        if (ok && !skip) {
+            const unsigned int g = vb->gen;
+            __threadfence();
+            const unsigned int arrived = atomicAdd(&b->count, 1u);
+            if (arrived == gridDim.x - 1) {
+                b->count = 0;
+                __threadfence();
+                atomicAdd(&b->gen, 1u);
+            } else {
+                long long it = 0;
+                while (vb->gen == g) {
+                    if (vb->abort) {
+                        ok = false;
+                        break;
+                    }
+                    if (++it > spin_limit) {
+                        atomicOr(&b->status, ST_TIMEOUT);
+                        atomicExch(&b->abort, 1);
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks)
+    k_fire_ensemble(const EnsembleArgs e) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const EnsRun run = *e.run;
+    double t = run.t0;
+    for (int s = 0; s < run.nsteps; ++s) {
+        const int par = (run.parity0 + s) & 1;
+        for (int i = blockIdx.x; i < e.n_items; i += gridDim.x) {
+            const EnsItem it = e.items[i];
+            const StepArgs &a = e.margs[2 * it.member + par];
+            MarchSmem<T> sm;
+            sm.carve(dyn_smem, a.ky * a.sry, a.ncls);
+            MarchStrip<T> strip(a, sm);
+            strip.run(it.x0, it.y0, t);
+            if (strip.st) atomicOr(a.status, strip.st);
+            __syncthreads();  // shared memory is reused by the next item
+        }
+        t = t + e.dt;
+        if (s + 1 < run.nsteps) {
+            const bool skip = (int)blockIdx.x == run.skip_block;
+            if (!grid_barrier(e.bar, run.spin_limit, skip)) return;
+        }
+    }
+    // the members' device time after the last step
+    if (blockIdx.x == 0) {
+        const int pf = (run.parity0 + run.nsteps) & 1;
+        for (int m = threadIdx.x; m < e.n_members; m += blockDim.x)
+            *const_cast<double *>(e.margs[2 * m + pf].t_in) = t;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+// members are ordinary contexts: the accessors below are defined in context.cu
+namespace wf {
+int ctx_step_args(fire_ctx *c, int parity, const void *u, const void *v, double dt, double *hs,
+                  double *hl, StepArgs &a);
+int ctx_info(const fire_ctx *c, int *prec, int *variant, int *nx, int *ny, int *srx, int *sry,
+             int *kx, int *ky, int *ncls, int *cur, double *t);
+int ctx_advance(fire_ctx *c, int nsteps, double dt);
+bool ctx_ignition_active(fire_ctx *c, double t);
+cudaStream_t ctx_stream(const fire_ctx *c);
+}  // namespace wf
+
+struct fire_ensemble {
+    std::vector<fire_ctx *> members;
+    int n = 0;
+    int prec = FIRE_FP32;
+    cudaStream_t stream = nullptr;
+    StepArgs *margs_dev = nullptr;
+    StepArgs *margs_host = nullptr;  // pinned
+    EnsItem *items_dev = nullptr;
+    int n_items = 0;
+    GridBar *bar = nullptr;
+    EnsRun *run_dev = nullptr;
+    EnsRun *run_host = nullptr;  // pinned
+    cudaEvent_t staged = nullptr;  // the pinned staging buffers may be rewritten
+    int grid = 0;
+    size_t smem = 0;
+    long long spin_limit = 20000000;  // x ~100 ns: about 2 s
+    int skip_block = -1;
+    cudaGraphExec_t graph = nullptr;
+    bool capture_failed = false;
+    int g_nsteps = -1;
+    double g_dt = 0;
+    int g_grid = 0;
+    size_t g_smem = 0;
+    const void *g_first_u = nullptr;
+};
+
+namespace {
+
+int ens_cuda_at(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return FIRE_OK;
+    record_cuda_error(e, where);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FIRE_ERR_OOM;
+    }
+    return FIRE_ERR_CUDA;
+}
+
+#define ens_cuda(call) ens_cuda_at((call), #call)
+#define ENS_CHECK(call)                   \
+    do {                                  \
+        int _r = ens_cuda(call);          \
+        if (_r != FIRE_OK) return _r;     \
+    } while (0)
+
+void ens_release(fire_ensemble *e) {
+    if (!e) return;
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    if (e->staged) cudaEventDestroy(e->staged);
+    for (fire_ctx *c : e->members) fire_destroy(c);
+    if (e->margs_dev) cudaFree(e->margs_dev);
+    if (e->items_dev) cudaFree(e->items_dev);
+    if (e->bar) cudaFree(e->bar);
+    if (e->run_dev) cudaFree(e->run_dev);
+    if (e->margs_host) cudaFreeHost(e->margs_host);
+    if (e->run_host) cudaFreeHost(e->run_host);
+    delete e;
+}
+
+// work list and launch shape for the members' current kernel configuration
+int ens_plan(fire_ensemble *e) {
+    std::vector<EnsItem> items;
+    size_t smem = 0;
+    for (int m = 0; m < e->n; ++m) {
+        int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+        double t;
+        ctx_info(e->members[m], &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
+        if (variant != FIRE_KERNEL_MARCH) return FIRE_ERR_STATE;
+        const int W = kx * srx, L = ky * sry;
+        for (int y0 = 0; y0 < ny; y0 += L)
+            for (int x0 = 0; x0 < nx; x0 += W) items.push_back(EnsItem{m, x0, y0});
+        const size_t sm = e->prec == FIRE_FP64 ? march_smem_bytes<double>(ky, sry, ncls)
+                                               : march_smem_bytes<float>(ky, sry, ncls);
+        smem = std::max(smem, sm);
+    }
+    // interleave the members so that each round of the CTAs mixes sizes
+    std::stable_sort(items.begin(), items.end(), [](const EnsItem &a, const EnsItem &b) {
+        return a.y0 != b.y0 ? a.y0 < b.y0 : a.member < b.member;
+    });
+    if (e->items_dev) cudaFree(e->items_dev);
+    e->items_dev = nullptr;
+    ENS_CHECK(cudaMalloc(&e->items_dev, sizeof(EnsItem) * items.size()));
+    ENS_CHECK(cudaMemcpy(e->items_dev, items.data(), sizeof(EnsItem) * items.size(),
+                         cudaMemcpyHostToDevice));
+    e->n_items = (int)items.size();
+    const void *fn = e->prec == FIRE_FP64 ? (const void *)k_fire_ensemble<double>
+                                          : (const void *)k_fire_ensemble<float>;
+    {
+        // the limit is a property of the kernel function shared by all ensembles
+        static std::mutex mu;
+        static size_t current[2] = {0, 0};
+        std::lock_guard<std::mutex> lock(mu);
+        size_t &cur = current[e->prec == FIRE_FP64 ? 1 : 0];
+        if (smem > cur) {
+            ENS_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            cur = smem;
+        }
+    }
+    int per_sm = 0, dev = 0, sms = 0;
+    ENS_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMarchThreads, smem));
+    ENS_CHECK(cudaGetDevice(&dev));
+    ENS_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return FIRE_ERR_ARG;
+    e->grid = std::min(e->n_items, per_sm * sms);
+    e->smem = smem;
+    return FIRE_OK;
+}
+
+cudaError_t ens_launch(fire_ensemble *e, double dt, cudaStream_t s) {
+    EnsembleArgs ea;
+    ea.margs = e->margs_dev;
+    ea.items = e->items_dev;
+    ea.n_items = e->n_items;
+    ea.n_members = e->n;
+    ea.dt = dt;
+    ea.bar = e->bar;
+    ea.run = e->run_dev;
+    cudaError_t err = cudaMemsetAsync(e->bar, 0, offsetof(GridBar, status), s);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(e->grid);
+    cfg.blockDim = dim3(kMarchThreads);
+    cfg.dynamicSmemBytes = e->smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (e->prec == FIRE_FP64) return cudaLaunchKernelEx(&cfg, k_fire_ensemble<double>, ea);
+    return cudaLaunchKernelEx(&cfg, k_fire_ensemble<float>, ea);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_desc *members,
+                         void *cuda_stream) {
+    if (!out) return FIRE_ERR_ARG;
+    *out = nullptr;
+    if (n_members < 1 || n_members > FIRE_MAX_MEMBERS || !members) return FIRE_ERR_ARG;
+    const int prec = members[0].grid.precision;
+    for (int m = 0; m < n_members; ++m)
+        if (members[m].grid.precision != prec) return FIRE_ERR_ARG;
+    fire_ensemble *e = new (std::nothrow) fire_ensemble();
+    if (!e) return FIRE_ERR_OOM;
+    e->n = n_members;
+    e->prec = prec;
+    e->stream = static_cast<cudaStream_t>(cuda_stream);
+    int r = FIRE_OK;
+    for (int m = 0; m < n_members && r == FIRE_OK; ++m) {
+        const fire_member_desc &d = members[m];
+        fire_ctx *c = nullptr;
+        r = fire_init(&c, &d.grid, d.classes, d.n_classes, d.fuel_class_dev, nullptr,
+                      d.spread_mult_dev, d.dzdx_dev, d.dzdy_dev, d.ignitions, d.n_ign, cuda_stream);
+        if (r == FIRE_OK) {
+            e->members.push_back(c);
+            int prc, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+            double t;
+            ctx_info(c, &prc, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
+            if (variant != FIRE_KERNEL_MARCH) r = FIRE_ERR_ARG;  // refinement too large
+        }
+    }
+#define ENS_TRY(call)                 \
+    do {                              \
+        if (r == FIRE_OK) r = ens_cuda(call); \
+    } while (0)
+    ENS_TRY(cudaMalloc(&e->margs_dev, sizeof(StepArgs) * 2 * n_members));
+    ENS_TRY(cudaMallocHost(&e->margs_host, sizeof(StepArgs) * 2 * n_members));
+    ENS_TRY(cudaMalloc(&e->bar, sizeof(GridBar)));
+    ENS_TRY(cudaMalloc(&e->run_dev, sizeof(EnsRun)));
+    ENS_TRY(cudaMallocHost(&e->run_host, sizeof(EnsRun)));
+    ENS_TRY(cudaEventCreateWithFlags(&e->staged, cudaEventDisableTiming));
+    ENS_TRY(cudaMemsetAsync(e->bar, 0, sizeof(GridBar), e->stream));
+#undef ENS_TRY
+    if (r == FIRE_OK) r = ens_plan(e);
+    if (r == FIRE_OK) r = ens_cuda(cudaStreamSynchronize(e->stream));
+    if (r != FIRE_OK) {
+        ens_release(e);
+        return r;
+    }
+    *out = e;
+    return FIRE_OK;
+}
+
+int fire_ensemble_step(fire_ensemble *e, int nsteps, double dt, const void *const *wind_u_dev,
+                       const void *const *wind_v_dev, double *const *heat_sens_dev,
+                       double *const *heat_lat_dev) {
+    if (!e || nsteps < 0 || !isfinite(dt) || !(dt > 0) || !wind_u_dev || !wind_v_dev)
+        return FIRE_ERR_ARG;
+    for (int m = 0; m < e->n; ++m)
+        if (!wind_u_dev[m] || !wind_v_dev[m]) return FIRE_ERR_ARG;
+    int done = 0;
+    while (done < nsteps) {
+        // an active ignition window needs its own step (fire_step applies it)
+        bool ign = false;
+        for (int m = 0; m < e->n; ++m) {
+            int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+            double t;
+            ctx_info(e->members[m], &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
+            if (ctx_ignition_active(e->members[m], t)) ign = true;
+        }
+        if (ign) {
+            for (int m = 0; m < e->n; ++m) {
+                int r = fire_step(e->members[m], wind_u_dev[m], wind_v_dev[m], dt,
+                                  heat_sens_dev ? heat_sens_dev[m] : nullptr,
+                                  heat_lat_dev ? heat_lat_dev[m] : nullptr);
+                if (r) return r;
+            }
+            ++done;
+            continue;
+        }
+        // the rest (up to the next ignition window) in one persistent launch
+        int chunk = 0;
+        {
+            int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+            double t0;
+            ctx_info(e->members[0], &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t0);
+            double t = t0;
+            while (done + chunk < nsteps) {
+                bool any = false;
+                for (int m = 0; m < e->n && !any; ++m) any = ctx_ignition_active(e->members[m], t);
+                if (any) break;
+                t = t + dt;
+                ++chunk;
+            }
+            ENS_CHECK(cudaEventSynchronize(e->staged));
+            for (int m = 0; m < e->n; ++m) {
+                for (int p = 0; p < 2; ++p) {
+                    int r = ctx_step_args(e->members[m], p, wind_u_dev[m], wind_v_dev[m], dt,
+                                          heat_sens_dev ? heat_sens_dev[m] : nullptr,
+                                          heat_lat_dev ? heat_lat_dev[m] : nullptr,
+                                          e->margs_host[2 * m + p]);
+                    if (r) return r;
+                }
+            }
+            e->run_host->t0 = t0;
+            e->run_host->parity0 = cur;
+            e->run_host->nsteps = chunk;
+            e->run_host->spin_limit = e->spin_limit;
+            e->run_host->skip_block = e->skip_block;
+        }
+        ENS_CHECK(cudaMemcpyAsync(e->margs_dev, e->margs_host, sizeof(StepArgs) * 2 * e->n,
+                                  cudaMemcpyHostToDevice, e->stream));
+        ENS_CHECK(cudaMemcpyAsync(e->run_dev, e->run_host, sizeof(EnsRun), cudaMemcpyHostToDevice,
+                                  e->stream));
+        ENS_CHECK(cudaEventRecord(e->staged, e->stream));
+        // replay the captured launch when its shape is unchanged
+        if (!e->capture_failed && (!e->graph || e->g_nsteps != chunk || e->g_dt != dt ||
+                                   e->g_grid != e->grid || e->g_smem != e->smem)) {
+            if (e->graph) {
+                ENS_CHECK(cudaStreamSynchronize(e->stream));  // the old graph may be in flight
+                cudaGraphExecDestroy(e->graph);
+                e->graph = nullptr;
+            }
+            cudaStream_t cs;
+            ENS_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t gr = nullptr;
+            cudaError_t err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                err = ens_launch(e, dt, cs);
+                cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+                if (err == cudaSuccess) err = e2;
+            }
+            if (err == cudaSuccess) err = cudaGraphInstantiate(&e->graph, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            cudaStreamDestroy(cs);
+            if (err != cudaSuccess) {
+                // capture of the cooperative launch refused: launch directly
+                record_cuda_error(err, "capture of the ensemble launch");
+                cudaGetLastError();
+                e->graph = nullptr;
+                e->capture_failed = true;
+            } else {
+                e->g_nsteps = chunk;
+                e->g_dt = dt;
+                e->g_grid = e->grid;
+                e->g_smem = e->smem;
+            }
+        }
+        if (e->graph) ENS_CHECK(cudaGraphLaunch(e->graph, e->stream));
+        else ENS_CHECK(ens_launch(e, dt, e->stream));
+        for (int m = 0; m < e->n; ++m) ctx_advance(e->members[m], chunk, dt);
+        done += chunk;
+    }
+    return FIRE_OK;
+}
+
+int fire_ensemble_member(fire_ensemble *e, int member, fire_ctx **ctx) {
+    if (!e || !ctx || member < 0 || member >= e->n) return FIRE_ERR_ARG;
+    *ctx = e->members[member];
+    return FIRE_OK;
+}
+
+int fire_ensemble_status(fire_ensemble *e, int *member_status) {
+    if (!e) return FIRE_ERR_ARG;
+    ENS_CHECK(cudaStreamSynchronize(e->stream));
+    GridBar b;
+    ENS_CHECK(cudaMemcpy(&b, e->bar, sizeof b, cudaMemcpyDeviceToHost));
+    int worst = FIRE_OK;
+    for (int m = 0; m < e->n; ++m) {
+        const int s = fire_status(e->members[m]);
+        if (member_status) member_status[m] = s;
+        if (s != FIRE_OK && (worst == FIRE_OK || s == FIRE_ERR_NONFINITE)) worst = s;
+    }
+    if (b.status & ST_TIMEOUT) return FIRE_ERR_TIMEOUT;
+    return worst;
+}
+
+int fire_ensemble_clear_status(fire_ensemble *e) {
+    if (!e) return FIRE_ERR_ARG;
+    for (fire_ctx *c : e->members) {
+        int r = fire_clear_status(c);
+        if (r) return r;
+    }
+    ENS_CHECK(cudaMemsetAsync(e->bar, 0, sizeof(GridBar), e->stream));
+    return FIRE_OK;
+}
+
+int fire_ensemble_set_kernel(fire_ensemble *e, int strip_columns, int strip_rows) {
+    if (!e || strip_columns < 2 || strip_rows < 1) return FIRE_ERR_ARG;
+    for (fire_ctx *c : e->members) {
+        int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+        double t;
+        ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
+        int kxn = std::max(1, strip_columns / srx), kyn = std::max(1, strip_rows / sry);
+        if ((kxn * srx) & 1) kxn = kxn > 1 ? kxn - 1 : 2;
+        int r = fire_set_kernel(c, FIRE_KERNEL_MARCH, kxn, kyn);
+        if (r) return r;
+    }
+    return ens_plan(e);
+}
+
+int fire_ensemble_get_kernel(const fire_ensemble *e, int *grid_ctas, int *work_items) {
+    if (!e) return FIRE_ERR_ARG;
+    if (grid_ctas) *grid_ctas = e->grid;
+    if (work_items) *work_items = e->n_items;
+    return FIRE_OK;
+}
+
+int fire_ensemble_set_barrier_test(fire_ensemble *e, int skip_block, long long spin_limit) {
+    if (!e || spin_limit < 1) return FIRE_ERR_ARG;
+    e->skip_block = skip_block;
+    e->spin_limit = spin_limit;
+    return FIRE_OK;
+}
+
+void fire_ensemble_destroy(fire_ensemble *e) {
+    if (!e) return;
+    cudaStreamSynchronize(e->stream);
+    ens_release(e);
+}
+
+}  // extern "C"

@@ -89,4 +89,9 @@ constexpr int kMarchMaxColumns = 248;  // output columns of one marching strip (
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s);
 
+// remembers the last CUDA error an entry point saw on this host thread
+// (read back through fire_last_cuda_error)
+void record_cuda_error(cudaError_t e, const char *where);
+const char *g_last_error_ptr();
+
 }  // namespace wf

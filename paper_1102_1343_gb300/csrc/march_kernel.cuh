@@ -26,6 +26,8 @@
 // after the band's last row: the average of Sect. 5, item 6, inside the CTA.
 #pragma once
 
+#include <mutex>
+
 #include "fire_device.cuh"
 #include "fire_internal.h"
 
@@ -622,18 +624,29 @@ size_t march_smem_bytes(int ky, int sry, int ncls) {
     return MarchSmem<T>::bytes(ky * sry, ncls);
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel function,
+// shared by every context in the process: raise it monotonically.
+template <typename T>
+cudaError_t prepare_march_kernel(size_t smem_bytes) {
+    static std::mutex mu;
+    static size_t current = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem_bytes <= current) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fire_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e == cudaSuccess) current = smem_bytes;
+    return e;
+}
+
 template <typename T>
 cudaError_t launch_march(const StepArgs &a, cudaStream_t s) {
     const int W = a.kx * a.srx, L = a.ky * a.sry;
     dim3 grid((a.nx + W - 1) / W, (a.ny + L - 1) / L);
-    k_fire_march<T><<<grid, kMarchThreads, march_smem_bytes<T>(a.ky, a.sry, a.ncls), s>>>(a);
+    const size_t smem = march_smem_bytes<T>(a.ky, a.sry, a.ncls);
+    cudaError_t e = prepare_march_kernel<T>(smem);
+    if (e != cudaSuccess) return e;
+    k_fire_march<T><<<grid, kMarchThreads, smem, s>>>(a);
     return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t prepare_march_kernel(size_t smem_bytes) {
-    return cudaFuncSetAttribute(k_fire_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes);
 }
 
 #define WF_INSTANTIATE_MARCH(T)                                               \

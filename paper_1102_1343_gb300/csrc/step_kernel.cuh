@@ -20,6 +20,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <mutex>
 #include <math.h>
 #include <stdint.h>
 
@@ -394,10 +395,17 @@ size_t step_smem_bytes(int kx, int ky, int srx, int sry, int ncls) {
     return n * sizeof(T);
 }
 
+// raised monotonically: the limit is shared by every context in the process
 template <typename T>
 cudaError_t prepare_step_kernel(size_t smem_bytes) {
-    return cudaFuncSetAttribute(k_fire_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes);
+    static std::mutex mu;
+    static size_t current = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem_bytes <= current) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fire_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e == cudaSuccess) current = smem_bytes;
+    return e;
 }
 
 template <typename T>
@@ -406,6 +414,8 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s) {
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
     dim3 block(kThreadsX, kThreadsY);
     size_t smem = step_smem_bytes<T>(a.kx, a.ky, a.srx, a.sry, a.ncls);
+    cudaError_t e = prepare_step_kernel<T>(smem);
+    if (e != cudaSuccess) return e;
     k_fire_step<T><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
