@@ -93,6 +93,13 @@ def lib():
             L.orc_step.restype = C.c_int
             L.orc_step.argtypes = [C.POINTER(_Grid), _D, _D, _D, _D, _D, _D, _D, C.c_int, _U8,
                                    C.c_double, C.c_double, _D, _D, _D, _D, _D]
+            L.orc_fuel_coefficients_dMf.restype = None
+            L.orc_fuel_coefficients_dMf.argtypes = [_D, C.c_double, _D]
+            L.orc_node_coefficients_dMf.restype = None
+            L.orc_node_coefficients_dMf.argtypes = [_D, C.c_int, _U8, _D, C.c_long, _D]
+            L.orc_adjoint.restype = C.c_double
+            L.orc_adjoint.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double, C.c_double,
+                                      C.c_int] + [_D] * 8)
             _lib = L
     return _lib
 
@@ -146,6 +153,24 @@ def node_coefficients(classes, fuel, moisture=None) -> np.ndarray:
     out = np.zeros(fuel.shape + (9,))
     lib().orc_node_coefficients(_dp(tab), len(classes), fuel.ctypes.data_as(_U8), _dp(mo),
                                 fuel.size, _dp(out))
+    return out
+
+
+def fuel_coefficients_dMf(cls: dict, Mf: float | None = None) -> np.ndarray:
+    """d(coefficients)/d(M_f) of one class (dual-number evaluation of Table 2)."""
+    v = fuel_vector(cls)
+    out = np.zeros(9)
+    lib().orc_fuel_coefficients_dMf(_dp(v), -1.0 if Mf is None else float(Mf), _dp(out))
+    return out
+
+
+def node_coefficients_dMf(classes, fuel, moisture=None) -> np.ndarray:
+    tab = fuel_table(classes)
+    fuel = np.ascontiguousarray(fuel, dtype=np.uint8)
+    mo = _f64(moisture)
+    out = np.zeros(fuel.shape + (9,))
+    lib().orc_node_coefficients_dMf(_dp(tab), len(classes), fuel.ctypes.data_as(_U8), _dp(mo),
+                                    fuel.size, _dp(out))
     return out
 
 
@@ -215,6 +240,7 @@ class OracleFire:
         fuel = np.ascontiguousarray(fuel, dtype=np.uint8)
         assert fuel.shape == (self.ny, self.nx)
         self.coef = node_coefficients(classes, fuel, moisture)
+        self.classes, self.fuel, self.moisture = list(classes), fuel, _f64(moisture)
         self.mult = _f64(mult)
         self.dzdx, self.dzdy = _f64(dzdx), _f64(dzdy)
         self.ign = ignition_table(list(ignitions))
@@ -253,6 +279,28 @@ class OracleFire:
         self.t = self.t + float(dt)
         self.status |= st
         return hs, hl, st
+
+    def adjoint(self, u, v, dt, nsteps, tobs):
+        """Reference adjoint: advance nsteps (no ignition may become active),
+        return J = 1/2 sum over nodes ignited in both of (t_i - tobs)^2 and
+        dJ/d(multiplier) [ny][nx], dJ/d(M_f) per node [ny][nx], dJ/du
+        [nya][nxa+1], dJ/dv [nya+1][nxa].  tobs is NaN/inf where unobserved."""
+        u, v = _f64(u), _f64(v)
+        g = self.g
+        tobs = _f64(tobs)
+        assert tobs.shape == (self.ny, self.nx)
+        dco = node_coefficients_dMf(self.classes, self.fuel, self.moisture)
+        gm = np.zeros((self.ny, self.nx))
+        gM = np.zeros_like(gm)
+        gu = np.zeros((g.nya, g.nxa + 1))
+        gv = np.zeros((g.nya + 1, g.nxa))
+        J = lib().orc_adjoint(C.byref(g), _dp(self.coef), _dp(dco), _dp(self.mult),
+                              _dp(self.dzdx), _dp(self.dzdy), _dp(u), _dp(v), self.t,
+                              float(dt), int(nsteps), _dp(self.psi), _dp(self.tign),
+                              _dp(self.frac), _dp(tobs), _dp(gm), _dp(gM), _dp(gu), _dp(gv))
+        for _ in range(int(nsteps)):
+            self.t = self.t + float(dt)
+        return J, gm, gM, gu, gv
 
     def set_state(self, psi, tign, frac, t):
         self.psi = _f64(psi).copy()

@@ -656,3 +656,361 @@ int orc_step(const orc_grid *g, const double *co, const double *mult,
     free(th); free(fnew); free(ext_t);
     return status;
 }
+
+/* ------------------------------------------------------------------ */
+/* Reference adjoint of the arrival-time misfit.                       */
+/* Not in the paper: data assimilation is its stated reason for the    */
+/* level-set formulation (Sect. 7, "Data assimilation").  Plain reverse */
+/* sweep through eqs. (Heun), (F-disc), (Godunov) and                  */
+/* (set-ignition-time), every forward state stored, the branches of    */
+/* the forward step (Godunov cases, max/min, extrapolation, zeroed     */
+/* central differences) frozen.                                        */
+/* J = 1/2 sum over nodes ignited in both runs of (t_i - t_obs)^2.     */
+/* ------------------------------------------------------------------ */
+
+/* forward-mode dual numbers for d(coefficients)/d(M_f) */
+typedef struct { double v, d; } dnum;
+static dnum dn(double v, double d) { dnum r; r.v = v; r.d = d; return r; }
+static dnum dn_add(dnum a, dnum b) { return dn(a.v + b.v, a.d + b.d); }
+static dnum dn_sub(dnum a, dnum b) { return dn(a.v - b.v, a.d - b.d); }
+static dnum dn_mul(dnum a, dnum b) { return dn(a.v * b.v, a.d * b.v + a.v * b.d); }
+static dnum dn_div(dnum a, dnum b) { return dn(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+static dnum dn_scale(dnum a, double s) { return dn(a.v * s, a.d * s); }
+static dnum dn_powc(dnum a, double p) { return dn(pow(a.v, p), p * pow(a.v, p - 1.0) * a.d); }
+static dnum dn_exp(dnum a) { double e = exp(a.v); return dn(e, e * a.d); }
+
+/* d(S0, R0, b, c, d, e, T_f, H_s, H_q)/d(M_f) of orc_fuel_coefficients, the
+ * same Table 2 chain evaluated on dual numbers (clamped branches and the
+ * chaparral rule have zero derivative). */
+void orc_fuel_coefficients_dMf(const double *fc, double Mf, double *dco)
+{
+    if (Mf < 0.0) Mf = fc[FC_MF];
+    for (int k = 0; k < CO_N; ++k) dco[k] = 0.0;
+    dco[CO_HS] = -fc[FC_FGI] * fc[FC_H] / ((1.0 + Mf) * (1.0 + Mf));
+    dco[CO_HQ] = 0.44 / ((1.0 + Mf) * (1.0 + Mf)) * LATENT_L * fc[FC_FGI];
+    if (fc[FC_CHAPARRAL] != 0.0 || !(fc[FC_FGI] > 0.0)) return;
+    double sigma  = fc[FC_SAVR] * M_PER_FT;
+    double wl     = fc[FC_FGI] * (M_PER_FT * M_PER_FT) / KG_PER_LB;
+    double depth  = fc[FC_DEPTH] / M_PER_FT;
+    double rho_p  = fc[FC_DENS] * (M_PER_FT * M_PER_FT * M_PER_FT) / KG_PER_LB;
+    double h      = fc[FC_H] * KG_PER_LB / J_PER_BTU;
+    dnum mf = dn(Mf, 1.0);
+    dnum w0 = dn_div(dn(wl, 0.0), dn_add(dn(1.0, 0.0), mf));
+    dnum rho_b = dn_scale(w0, 1.0 / depth);
+    dnum beta = dn_scale(rho_b, 1.0 / rho_p);
+    double beta_op = 3.348 * pow(sigma, -0.8189);
+    double A = 1.0 / (4.77 * pow(sigma, 0.1) - 7.27);
+    double s15 = pow(sigma, 1.5);
+    double Gmax = s15 / (495.0 + 0.0594 * s15);
+    dnum ratio = dn_scale(beta, 1.0 / beta_op);
+    dnum Gamma = dn_scale(dn_mul(dn_powc(ratio, A), dn_exp(dn_scale(dn_sub(dn(1.0, 0.0), ratio), A))), Gmax);
+    dnum wn = dn_scale(w0, 1.0 / (1.0 + fc[FC_ST]));
+    dnum rm = dn_scale(mf, 1.0 / fc[FC_MX]);
+    dnum etaM = dn_add(dn_sub(dn(1.0, 0.0), dn_scale(rm, 2.59)),
+                       dn_sub(dn_scale(dn_mul(rm, rm), 5.11), dn_scale(dn_mul(dn_mul(rm, rm), rm), 3.52)));
+    if (rm.v >= 1.0 || etaM.v < 0.0) etaM = dn(0.0, 0.0);
+    if (etaM.v > 1.0) etaM = dn(1.0, 0.0);
+    double etaS = 0.174 * pow(fc[FC_SE], -0.19);
+    dnum IR = dn_scale(dn_mul(dn_mul(Gamma, wn), etaM), h * etaS);
+    dnum xi = dn_scale(dn_exp(dn_scale(dn_add(beta, dn(0.1, 0.0)), 0.792 + 0.681 * sqrt(sigma))),
+                       1.0 / (192.0 + 0.2595 * sigma));
+    double epsh = exp(-138.0 / sigma);
+    dnum Qig = dn_add(dn(250.0, 0.0), dn_scale(mf, 1116.0));
+    dnum R0f = dn_div(dn_mul(IR, xi), dn_scale(dn_mul(rho_b, Qig), epsh));
+    dnum R0 = dn_scale(R0f, M_PER_FT / 60.0);
+    double B = 0.02526 * pow(sigma, 0.54);
+    double C = 7.47 * exp(-0.133 * pow(sigma, 0.55));
+    double E = 0.715 * exp(-3.59e-4 * sigma);
+    dnum c = dn_scale(dn_mul(R0, dn_powc(ratio, -E)), C * pow(fc[FC_WINDRF] * (60.0 / M_PER_FT), B));
+    dnum d = dn_scale(dn_mul(R0, dn_powc(beta, -0.3)), 5.275);
+    dco[CO_R0] = R0.d;
+    dco[CO_C] = c.d;
+    dco[CO_D] = d.d;
+}
+
+void orc_node_coefficients_dMf(const double *classes, int ncls, const unsigned char *fuel,
+                               const double *moisture, long n, double *dco)
+{
+    for (long k = 0; k < n; ++k) {
+        int c = fuel[k];
+        if (c >= ncls) c = ncls - 1;
+        orc_fuel_coefficients_dMf(classes + (long)c * FC_N, moisture ? moisture[k] : -1.0,
+                                  dco + k * CO_N);
+    }
+}
+
+/* value of eq. (Godunov) and which one-sided difference it took
+ * (-1: D-, +1: D+, 0: neither) */
+static double godunov_sel(double dm, double dp, int *sel)
+{
+    if (dm <= 0.0 && dp <= 0.0) { *sel = 1; return dp; }
+    if (dm >= 0.0 && dp >= 0.0) { *sel = -1; return dm; }
+    if (dm <= 0.0 && dp >= 0.0) { *sel = 0; return 0.0; }
+    if (fabs(dm) >= fabs(dp)) { *sel = -1; return dm; }
+    *sel = 1;
+    return dp;
+}
+
+/* Partial derivatives of F at one node (the computation of orc_rhs with
+ * its branches frozen) with respect to the 5 stencil values
+ * (centre, left, right, down, up), the multiplier m, the coefficients
+ * (S0, R0, c, d) and the node wind (un, vn). */
+typedef struct {
+    double dpsi[5];
+    double dm, dS0, dR0, dc, dd, dun, dvn;
+} orc_partials;
+
+static void rhs_partials(double p, double pl, double pr, double pd, double pu, double dx,
+                         double dy, double eps, const double *co, double m, double un,
+                         double vn, double zx, double zy, orc_partials *o)
+{
+    memset(o, 0, sizeof *o);
+    double dxm = (p - pl) / dx, dxp = (pr - p) / dx;
+    double dym = (p - pd) / dy, dyp = (pu - p) / dy;
+    int sx, sy;
+    double gx = godunov_sel(dxm, dxp, &sx);
+    double gy = godunov_sel(dym, dyp, &sy);
+    double ax = pr - pl, ay = pu - pd;
+    int zxk = 1, zyk = 1;
+    if (fabs(ax) <= ORC_GRAD_ZERO * (fabs(pr) + fabs(pl))) { ax = 0.0; zxk = 0; }
+    if (fabs(ay) <= ORC_GRAD_ZERO * (fabs(pu) + fabs(pd))) { ay = 0.0; zyk = 0; }
+    double cx = ax / (2.0 * dx), cy = ay / (2.0 * dy);
+    double cn = sqrt(cx * cx + cy * cy);
+    double nxv = 0.0, nyv = 0.0;
+    if (cn > 0.0) { nxv = cx / cn; nyv = cy / cn; }
+    double U = un * nxv + vn * nyv;
+    double T = zx * nxv + zy * nyv;
+    /* spread rate, eq. (spread-WRF-Fire), with its branches */
+    double Up = U > 0.0 ? U : 0.0;
+    double Ue = Up < co[CO_E] ? Up : co[CO_E];
+    double tp = T > 0.0 ? T : 0.0;
+    double inner = co[CO_R0] + co[CO_C] * pow(Ue, co[CO_B]) + co[CO_D] * tp * tp;
+    int active = inner > co[CO_S0];
+    double St = active ? inner : co[CO_S0];
+    double S = m * St;
+    double lap = (dxp - dxm) + (dyp - dym);
+    double grad = sqrt(gx * gx + gy * gy);
+    double Fs = -grad + eps * lap;                      /* dF/dS */
+    double dSt_dU = (active && U > 0.0 && U < co[CO_E])
+                        ? co[CO_C] * co[CO_B] * pow(Ue, co[CO_B] - 1.0) : 0.0;
+    double dSt_dT = (active && T > 0.0) ? 2.0 * co[CO_D] * T : 0.0;
+    /* normal: dn/dc = (I - n n^T)/|c| */
+    double dU_dcx = 0.0, dU_dcy = 0.0, dT_dcx = 0.0, dT_dcy = 0.0;
+    if (cn > 0.0) {
+        dU_dcx = (un - U * nxv) / cn;
+        dU_dcy = (vn - U * nyv) / cn;
+        dT_dcx = (zx - T * nxv) / cn;
+        dT_dcy = (zy - T * nyv) / cn;
+    }
+    double dS_dcx = m * (dSt_dU * dU_dcx + dSt_dT * dT_dcx);
+    double dS_dcy = m * (dSt_dU * dU_dcy + dSt_dT * dT_dcy);
+    double dcx_dpr = zxk ? 1.0 / (2.0 * dx) : 0.0, dcy_dpu = zyk ? 1.0 / (2.0 * dy) : 0.0;
+    /* dS/dpsi: C, L, R, D, U */
+    double dS[5] = {0.0, -dS_dcx * dcx_dpr, dS_dcx * dcx_dpr, -dS_dcy * dcy_dpu, dS_dcy * dcy_dpu};
+    /* d|grad|/dpsi through the selected one-sided differences */
+    double dG[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (grad > 0.0) {
+        double wx = gx / grad, wy = gy / grad;
+        if (sx == -1) { dG[0] += wx / dx; dG[1] -= wx / dx; }
+        if (sx == 1) { dG[2] += wx / dx; dG[0] -= wx / dx; }
+        if (sy == -1) { dG[0] += wy / dy; dG[3] -= wy / dy; }
+        if (sy == 1) { dG[4] += wy / dy; dG[0] -= wy / dy; }
+    }
+    double dL[5] = {-2.0 / dx - 2.0 / dy, 1.0 / dx, 1.0 / dx, 1.0 / dy, 1.0 / dy};
+    for (int k = 0; k < 5; ++k)
+        o->dpsi[k] = Fs * dS[k] - S * dG[k] + eps * S * dL[k];
+    o->dm = Fs * St;
+    o->dS0 = Fs * m * (active ? 0.0 : 1.0);
+    o->dR0 = Fs * m * (active ? 1.0 : 0.0);
+    o->dc = Fs * m * (active ? pow(Ue, co[CO_B]) : 0.0);
+    o->dd = Fs * m * (active ? tp * tp : 0.0);
+    o->dun = Fs * m * dSt_dU * nxv;
+    o->dvn = Fs * m * dSt_dU * nyv;
+}
+
+/* d(ghost)/d(p0), d(ghost)/d(p1) for the extrapolation's taken branch */
+static void ghost_partials(double p0, double p1, double *d0, double *d1)
+{
+    double g = p0 + (p0 - p1);
+    *d0 = 2.0;
+    *d1 = -1.0;
+    if (p0 > g) { g = p0; *d0 = 1.0; *d1 = 0.0; }
+    if (p1 > g) { *d0 = 0.0; *d1 = 1.0; }
+}
+
+/* r += J_F(psi)^T v for the field psi (with its extrapolated ghosts), and
+ * the parameter terms v^T dF/dp accumulated per node. */
+static void rhs_vjp(int nx, int ny, double dx, double dy, double eps, const double *psi,
+                    const double *ext, const double *co, const double *dco, const double *mult,
+                    const double *un, const double *vn, const double *dzdx, const double *dzdy,
+                    const double *v, double *r, double *gm, double *gMf, double *gun, double *gvn)
+{
+    int W = nx + 2;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            if (v[k] == 0.0) continue;
+            const double *e = ext + (j + 1) * W + (i + 1);
+            orc_partials o;
+            rhs_partials(e[0], e[-1], e[1], e[-W], e[W], dx, dy, eps, co + k * CO_N,
+                         mult ? mult[k] : 1.0, un[k], vn[k], dzdx[k], dzdy[k], &o);
+            double vk = v[k];
+            /* stencil positions: C, L, R, D, U */
+            int ii[5] = {i, i - 1, i + 1, i, i};
+            int jj[5] = {j, j, j, j - 1, j + 1};
+            for (int q = 0; q < 5; ++q) {
+                double c = vk * o.dpsi[q];
+                int a = ii[q], b = jj[q];
+                if (a >= 0 && a < nx && b >= 0 && b < ny) {
+                    r[(long)b * nx + a] += c;
+                } else if (a < 0 || a >= nx) {  /* x-ghost of row b */
+                    int i0 = a < 0 ? 0 : nx - 1, i1 = a < 0 ? 1 : nx - 2;
+                    double d0, d1;
+                    ghost_partials(psi[(long)b * nx + i0], psi[(long)b * nx + i1], &d0, &d1);
+                    r[(long)b * nx + i0] += c * d0;
+                    r[(long)b * nx + i1] += c * d1;
+                } else {                        /* y-ghost of column a */
+                    int j0 = b < 0 ? 0 : ny - 1, j1 = b < 0 ? 1 : ny - 2;
+                    double d0, d1;
+                    ghost_partials(psi[(long)j0 * nx + a], psi[(long)j1 * nx + a], &d0, &d1);
+                    r[(long)j0 * nx + a] += c * d0;
+                    r[(long)j1 * nx + a] += c * d1;
+                }
+            }
+            gm[k] += vk * o.dm;
+            const double *dc = dco + k * CO_N;
+            gMf[k] += vk * (o.dS0 * dc[CO_S0] + o.dR0 * dc[CO_R0] + o.dc * dc[CO_C] + o.dd * dc[CO_D]);
+            gun[k] += vk * o.dun;
+            gvn[k] += vk * o.dvn;
+        }
+    }
+}
+
+/* Adjoint of the level-set part of one step (eq. Heun): given
+ * mu = dJ/dpsi^{n+1} returns lam = dJ/dpsi^n and accumulates the parameter
+ * terms:  lam* = dt/2 J_F(psi*)^T mu,  w = dt/2 mu + dt lam*,
+ *         lam = mu + lam* + J_F(psi^n)^T w. */
+static void adjoint_step(int nx, int ny, double dx, double dy, double eps, const double *psi,
+                         const double *co, const double *dco, const double *mult,
+                         const double *un, const double *vn, const double *dzdx,
+                         const double *dzdy, double dt, const double *mu, double *lam,
+                         double *gm, double *gMf, double *gun, double *gvn)
+{
+    long n = (long)nx * ny, ne = (long)(nx + 2) * (ny + 2);
+    double *ext0 = malloc(sizeof(double) * ne), *ext1 = malloc(sizeof(double) * ne);
+    double *F1 = malloc(sizeof(double) * n), *ps = malloc(sizeof(double) * n);
+    double *v = malloc(sizeof(double) * n), *ls = calloc(n, sizeof(double));
+    double *r1 = calloc(n, sizeof(double));
+    orc_extend(nx, ny, psi, ext0);
+    orc_rhs(nx, ny, dx, dy, eps, ext0, co, mult, un, vn, dzdx, dzdy, F1);
+    for (long k = 0; k < n; ++k) ps[k] = psi[k] + dt * F1[k];
+    orc_extend(nx, ny, ps, ext1);
+    for (long k = 0; k < n; ++k) v[k] = 0.5 * dt * mu[k];
+    rhs_vjp(nx, ny, dx, dy, eps, ps, ext1, co, dco, mult, un, vn, dzdx, dzdy, v, ls, gm, gMf,
+            gun, gvn);
+    for (long k = 0; k < n; ++k) v[k] = 0.5 * dt * mu[k] + dt * ls[k];
+    rhs_vjp(nx, ny, dx, dy, eps, psi, ext0, co, dco, mult, un, vn, dzdx, dzdy, v, r1, gm, gMf,
+            gun, gvn);
+    for (long k = 0; k < n; ++k) lam[k] = mu[k] + ls[k] + r1[k];
+    free(ext0); free(ext1); free(F1); free(ps); free(v); free(ls); free(r1);
+}
+
+/* Whether node k's ignition time was set in the step [t_s, t_s + dt] that
+ * took psi from a to b (eq. set-ignition-time): it was not ignited before
+ * the run, the step crossed from > 0 to <= 0, and the recorded time lies in
+ * the step (a later crossing after the level set rose again sets nothing). */
+static int crossed_in_step(double tign0, double ti, double ts, double ts1, double a, double b)
+{
+    return isinf(tign0) && isfinite(ti) && a > 0.0 && b <= 0.0 && ti >= ts && ti <= ts1;
+}
+
+/* Forward run of nsteps steps from the given state (no ignitions during the
+ * run), misfit J and its gradient with respect to the per-node multiplier
+ * (at the given multiplier, 1 where mult is NULL), the per-node fuel
+ * moisture (at the values that made co, with dco = dco/dM_f) and the
+ * staggered wind u, v.  On return psi, tign, frac hold the final state.
+ * Outputs g_* are overwritten.  Nodes without an observation carry a
+ * non-finite tobs. */
+double orc_adjoint(const orc_grid *g, const double *co, const double *dco, const double *mult,
+                   const double *dzdx, const double *dzdy, const double *u, const double *v,
+                   double t0, double dt, int nsteps, double *psi, double *tign, double *frac,
+                   const double *tobs, double *g_mult, double *g_moist, double *g_u, double *g_v)
+{
+    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
+    long n = (long)nx * ny;
+    double dx = g->dx_atm / g->srx, dy = g->dy_atm / g->sry;
+    double *states = malloc(sizeof(double) * n * (nsteps + 1));
+    double *times = malloc(sizeof(double) * (nsteps + 1));
+    double *tign0 = malloc(sizeof(double) * n);
+    double *hs = malloc(sizeof(double) * g->nxa * g->nya), *hl = malloc(sizeof(double) * g->nxa * g->nya);
+    unsigned char applied[1] = {1};
+    memcpy(tign0, tign, sizeof(double) * n);
+    memcpy(states, psi, sizeof(double) * n);
+    double t = t0;
+    times[0] = t;
+    for (int s = 0; s < nsteps; ++s) {
+        orc_step(g, co, mult, dzdx, dzdy, u, v, NULL, 0, applied, t, dt, psi, tign, frac, hs, hl);
+        t = t + dt;
+        times[s + 1] = t;
+        memcpy(states + (long)(s + 1) * n, psi, sizeof(double) * n);
+    }
+    double J = 0.0;
+    for (long k = 0; k < n; ++k)
+        if (isfinite(tign[k]) && isfinite(tobs[k])) J += 0.5 * (tign[k] - tobs[k]) * (tign[k] - tobs[k]);
+
+    double *un = malloc(sizeof(double) * n), *vn = malloc(sizeof(double) * n);
+    double *gun = calloc(n, sizeof(double)), *gvn = calloc(n, sizeof(double));
+    double *lam = calloc(n, sizeof(double)), *mu = malloc(sizeof(double) * n);
+    orc_wind_at_nodes(g->nxa, g->nya, g->srx, g->sry, u, v, un, vn);
+    for (long k = 0; k < n; ++k) { g_mult[k] = 0.0; g_moist[k] = 0.0; }
+    for (int s = nsteps - 1; s >= 0; --s) {
+        const double *pa = states + (long)s * n, *pb = states + (long)(s + 1) * n;
+        /* eq. (set-ignition-time) at the nodes whose first crossing was this step */
+        for (long k = 0; k < n; ++k) {
+            mu[k] = lam[k];
+            if (isfinite(tobs[k]) &&
+                crossed_in_step(tign0[k], tign[k], times[s], times[s + 1], pa[k], pb[k])) {
+                double a = pa[k], b = pb[k], r = tign[k] - tobs[k];
+                mu[k] += r * dt * a / ((a - b) * (a - b));
+            }
+        }
+        adjoint_step(nx, ny, dx, dy, g->eps, pa, co, dco, mult, un, vn, dzdx, dzdy, dt, mu, lam,
+                     g_mult, g_moist, gun, gvn);
+        for (long k = 0; k < n; ++k) {
+            if (isfinite(tobs[k]) &&
+                crossed_in_step(tign0[k], tign[k], times[s], times[s + 1], pa[k], pb[k])) {
+                double a = pa[k], b = pb[k], r = tign[k] - tobs[k];
+                lam[k] += r * (-dt * b / ((a - b) * (a - b)));
+            }
+        }
+    }
+    /* wind: adjoint of the bilinear interpolation of Sect. 5 */
+    for (long q = 0; q < (long)g->nya * (g->nxa + 1); ++q) g_u[q] = 0.0;
+    for (long q = 0; q < (long)(g->nya + 1) * g->nxa; ++q) g_v[q] = 0.0;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            double xa = ((double)i + 0.5) / (double)g->srx;
+            double ya = ((double)j + 0.5) / (double)g->sry;
+            int i0, i1, j0, j1;
+            double wx, wy;
+            interp_weights(xa, g->nxa + 1, &i0, &i1, &wx);
+            interp_weights(ya - 0.5, g->nya, &j0, &j1, &wy);
+            int W = g->nxa + 1;
+            g_u[j0 * W + i0] += gun[k] * (1.0 - wy) * (1.0 - wx);
+            g_u[j0 * W + i1] += gun[k] * (1.0 - wy) * wx;
+            g_u[j1 * W + i0] += gun[k] * wy * (1.0 - wx);
+            g_u[j1 * W + i1] += gun[k] * wy * wx;
+            interp_weights(xa - 0.5, g->nxa, &i0, &i1, &wx);
+            interp_weights(ya, g->nya + 1, &j0, &j1, &wy);
+            W = g->nxa;
+            g_v[j0 * W + i0] += gvn[k] * (1.0 - wy) * (1.0 - wx);
+            g_v[j0 * W + i1] += gvn[k] * (1.0 - wy) * wx;
+            g_v[j1 * W + i0] += gvn[k] * wy * (1.0 - wx);
+            g_v[j1 * W + i1] += gvn[k] * wy * wx;
+        }
+    }
+    free(states); free(times); free(tign0); free(hs); free(hl); free(un); free(vn);
+    free(gun); free(gvn); free(lam); free(mu);
+    return J;
+}

@@ -110,11 +110,14 @@ def random_classes(rng, n=13, chaparral_index=None) -> list:
 
 def smooth_wind(rng, nxa, nya, mean=(5.0, 0.0), std=1.5, sigma_cells=5.0):
     """Staggered wind: mean + white noise Gaussian-filtered (sigma in atmos
-    cells) and rescaled to the given standard deviation."""
+    cells), centred and rescaled to the given standard deviation (centring
+    matters on meshes not much larger than the filter, where the filtered
+    noise is nearly constant)."""
     from scipy.ndimage import gaussian_filter
 
     def field(shape, m):
         w = gaussian_filter(rng.standard_normal(shape), sigma=sigma_cells, mode="reflect")
+        w = w - w.mean()
         s = w.std()
         if s > 0:
             w = w * (std / s)

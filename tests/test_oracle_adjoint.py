@@ -1,0 +1,191 @@
+"""Pins of the oracle's reference adjoint of the arrival-time misfit
+J = 1/2 sum over nodes ignited in both runs of (t_i - t_obs)^2 (the data
+assimilation use of Sect. 7 that motivates the level-set formulation):
+
+- d(coefficients)/d(M_f) against central differences of the Table 2 chain;
+- a planar front under uniform spread rate, where the discrete scheme moves
+  the front exactly at S, so t_i = t0 + (x - x0)/(m S) and the derivative of J
+  along a uniform change of the multiplier, the moisture or the wind has a
+  closed form (the sum of the per-node / per-face gradient);
+- central finite differences along random directions on a random landscape
+  (wind, slope, patchy fuel), away from switch points (the set of ignited nodes
+  is the same in the perturbed runs);
+- a zero misfit gives a zero gradient.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_1343_gb300 import synth
+
+
+def test_coefficient_moisture_derivative_matches_fd(orc):
+    rng = np.random.default_rng(5)
+    classes = synth.random_classes(rng) + [synth.nominal_class()]
+    for c in classes:
+        Mf = c["fuelmc_g"]
+        d = orc.fuel_coefficients_dMf(c)
+        h = 1e-6
+        fd = (orc.fuel_coefficients(c, Mf + h) - orc.fuel_coefficients(c, Mf - h)) / (2 * h)
+        scale = np.maximum(np.abs(fd), 1e-12)
+        assert np.all(np.abs(d - fd) <= 1e-6 * scale + 1e-14), (c, d, fd)
+        # b, e, T_f and S0 do not depend on the moisture
+        assert d[2] == 0.0 and d[5] == 0.0 and d[6] == 0.0 and d[0] == 0.0
+    chap = synth.nominal_class(chaparral=1.0)
+    d = orc.fuel_coefficients_dMf(chap)
+    assert np.all(d[:7] == 0.0)
+
+
+def planar_case(U0):
+    """Planar front x = x0 moving in +x on a flat, uniform-fuel mesh of 1 m
+    cells; uniform wind (U0, 0)."""
+    nxa, nya, sr = 12, 2, 10
+    dx_atm = 10.0
+    cls = [synth.nominal_class()]
+    nx, ny = nxa * sr, nya * sr
+    fuel = np.zeros((ny, nx), np.uint8)
+    z = np.zeros((ny, nx))
+    co = oracle.fuel_coefficients(cls[0])
+    S = oracle.spread_rate(co, U0, 0.0)
+    dt = 0.25 / S  # z = -S dt (2/dx + 4 eps 2/dx) = -1.3: stable
+    fire = oracle.OracleFire(nxa, nya, sr, dx_atm, cls, fuel, z, z.copy(), ignitions=[],
+                             mult=np.ones((ny, nx)))
+    x = (np.arange(nx) + 0.5) * 1.0
+    x0 = 70.3
+    psi = np.broadcast_to(x - x0, (ny, nx)).copy()
+    tign = np.where(psi <= 0, 0.0, np.inf)
+    fire.set_state(psi, tign, np.ones((ny, nx)), 0.0)
+    u = np.full((nya, nxa + 1), U0)
+    v = np.zeros((nya + 1, nxa))
+    return fire, cls, co, S, dt, u, v, x, x0
+
+
+@pytest.mark.parametrize("U0", [0.0, 3.0])
+def test_planar_front_uniform_directions_closed_form(orc, U0):
+    fire, cls, co, S, dt, u, v, x, x0 = planar_case(U0)
+    nsteps = 24
+    ny, nx = fire.ny, fire.nx
+    # observations from a slower front: residuals of both signs along x
+    tobs = np.broadcast_to((x - x0) / (0.9 * S) - 2.0 * dt, (ny, nx)).copy()
+    J, gm, gM, gu, gv = fire.adjoint(u, v, dt, nsteps, tobs)
+    ti = fire.tign
+    ign = np.isfinite(ti) & (fire.psi <= 0) & (np.broadcast_to(x, (ny, nx)) > x0)
+    assert ign.sum() >= 5 * ny  # several columns crossed
+    # the scheme moves the planar front exactly at S
+    expect_t = np.broadcast_to((x - x0) / S, (ny, nx))
+    assert np.max(np.abs(ti[ign] - expect_t[ign])) < 1e-9
+    r = np.where(ign, ti - tobs, 0.0)
+    dti_dS = -(np.broadcast_to(x, (ny, nx)) - x0) / S ** 2  # dt_i/dS at each crossed node
+    # uniform multiplier: dS/dm = S
+    want_m = np.sum(r * dti_dS * S)
+    assert abs(gm.sum() - want_m) <= 1e-8 * abs(want_m)
+    # uniform moisture: dS/dM_f = dR0 + dc U^b (+ dd tan^2 = 0), by central
+    # differences of the coefficient chain
+    h = 1e-6
+    Mf = cls[0]["fuelmc_g"]
+    cp = orc.fuel_coefficients(cls[0], Mf + h)
+    cm = orc.fuel_coefficients(cls[0], Mf - h)
+    dS = (orc.spread_rate(cp, U0, 0.0) - orc.spread_rate(cm, U0, 0.0)) / (2 * h)
+    want_M = np.sum(r * dti_dS * dS)
+    assert abs(gM.sum() - want_M) <= 1e-6 * abs(want_M)
+    # uniform wind u (every face): dS/dU; v is perpendicular to the normal
+    if U0 > 0:
+        dSdU = (orc.spread_rate(co, U0 + 1e-5, 0.0) - orc.spread_rate(co, U0 - 1e-5, 0.0)) / 2e-5
+        want_u = np.sum(r * dti_dS * dSdU)
+        assert abs(gu.sum() - want_u) <= 1e-6 * abs(want_u)
+    else:
+        # max{0, U} has a kink at 0: one-sided (frozen) derivative 0
+        assert gu.sum() == 0.0
+    assert np.max(np.abs(gv)) <= 1e-12 * np.max(np.abs(gu) + 1.0)
+    # J itself
+    assert abs(J - 0.5 * np.sum(np.where(np.isfinite(ti), (ti - tobs) ** 2, 0.0))) <= 1e-12 * J
+
+
+def landscape(seed=7, nxa=8, nya=8, sr=5, dx_atm=10.0, dy_atm=None):
+    """Small random landscape (2 m cells; dy_atm != dx_atm gives anisotropic
+    cells) with a centred ignition; with the multiplier 3 used below the
+    front crosses several cells in 60 steps of 0.25 s."""
+    w = synth.random_landscape(nxa, nya, sr=sr, dx_atm=dx_atm, seed=seed, ignition="center",
+                               steps=60, dt=0.25)
+    if dy_atm is not None:
+        w.dy_atm = dy_atm
+    # no chaparral class (its rate does not depend on the moisture, fine, but
+    # its 6 m/s cap needs a smaller step)
+    for c in w.classes:
+        c["chaparral"] = 0.0
+    return w
+
+
+def run_J(w, mult, moist, u, v, nsteps, tobs):
+    f = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    for _ in range(nsteps):
+        f.step(u, v, w.dt)
+    ok = np.isfinite(f.tign) & np.isfinite(tobs)
+    return 0.5 * np.sum((f.tign[ok] - tobs[ok]) ** 2), np.isfinite(f.tign)
+
+
+@pytest.mark.parametrize("dy_atm", [None, 14.0])
+def test_gradient_matches_central_differences(orc, dy_atm):
+    w = landscape(dy_atm=dy_atm)
+    nsteps = 60
+    ny, nx = w.ny, w.nx
+    rng = np.random.default_rng(11)
+    mult = 3.0 * (1.0 + 0.05 * rng.standard_normal((ny, nx)))
+    moist = np.array([w.classes[c]["fuelmc_g"] for c in w.fuel.ravel()]).reshape(ny, nx)
+    # truth: stronger fire, drier fuel, stronger wind
+    truth_mult = mult * 1.2
+    f = oracle.OracleFire.from_workload(w, mult=truth_mult, moisture=moist - 0.02)
+    for _ in range(nsteps):
+        f.step(w.u * 1.1, w.v * 1.1, w.dt)
+    tobs = np.where(np.isfinite(f.tign), f.tign, np.nan)
+
+    base = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    J, gm, gM, gu, gv = base.adjoint(w.u, w.v, w.dt, nsteps, tobs)
+    J0, ign0 = run_J(w, mult, moist, w.u, w.v, nsteps, tobs)
+    assert abs(J - J0) <= 1e-12 * J0
+    assert J > 0 and np.count_nonzero(np.isfinite(tobs) & ign0) > 20
+
+    checked, worst = 0, 0.0
+    for q in range(8):
+        dm = rng.standard_normal((ny, nx))
+        dM = rng.standard_normal((ny, nx))
+        du = rng.standard_normal(w.u.shape)
+        dv = rng.standard_normal(w.v.shape)
+        for which in ("m", "M", "u", "v"):
+            h = 1e-6
+            args_p = [mult, moist, w.u, w.v]
+            args_m = [mult, moist, w.u, w.v]
+            k = "mMuv".index(which)
+            d = (dm, dM * 0.01, du, dv)[k]
+            args_p[k] = args_p[k] + h * d
+            args_m[k] = args_m[k] - h * d
+            Jp, ip = run_J(w, *args_p, nsteps, tobs)
+            Jm, im = run_J(w, *args_m, nsteps, tobs)
+            if not (np.array_equal(ip, ign0) and np.array_equal(im, ign0)):
+                continue  # a node entered or left the ignited set: switch point
+            fd = (Jp - Jm) / (2 * h)
+            g = (gm, gM, gu, gv)[k]
+            ad = float(np.sum(g * d))
+            assert abs(fd - ad) <= 1e-6 * max(abs(fd), 1e-3 * J), (which, q, fd, ad)
+            worst = max(worst, abs(fd - ad) / max(abs(fd), 1e-3 * J))
+            checked += 1
+    print("checked", checked, "worst rel", worst)
+    assert checked >= 28
+
+
+def test_zero_misfit_zero_gradient(orc):
+    w = landscape(seed=8)
+    nsteps = 20
+    w.mult = np.full((w.ny, w.nx), 3.0)
+    f = oracle.OracleFire.from_workload(w)
+    for _ in range(nsteps):
+        f.step(w.u, w.v, w.dt)
+    tobs = np.where(np.isfinite(f.tign), f.tign, np.nan)
+    g = oracle.OracleFire.from_workload(w)
+    J, gm, gM, gu, gv = g.adjoint(w.u, w.v, w.dt, nsteps, tobs)
+    assert J == 0.0
+    for a in (gm, gM, gu, gv):
+        assert np.all(a == 0.0)
+    # the adjoint call advanced the state exactly like the plain steps
+    assert np.array_equal(g.psi, f.psi) and np.array_equal(g.tign, f.tign)
+    assert np.array_equal(g.frac, f.frac) and g.t == f.t
