@@ -184,6 +184,48 @@ int fire_get_state(fire_ctx *ctx, void *psi_dev, double *tign_dev, void *frac_de
 int fire_set_state(fire_ctx *ctx, const void *psi_dev, const double *tign_dev,
                    const void *frac_dev, double t);
 
+/* Replace the per-node spread multiplier m (S := m S, [NY][NX] device,
+ * context precision) by a copy of mult_dev; NULL removes it (m = 1).  Waits
+ * for the copy.  Not for the context of an ensemble member. */
+int fire_set_spread_mult(fire_ctx *ctx, const void *mult_dev);
+
+/* Replace the fuel-class table (Table 1 properties, e.g. other moisture
+ * values) by n_classes host records; n_classes must equal fire_init's.  The
+ * per-class coefficients of eq. (spread-WRF-Fire) are recomputed; waits. */
+int fire_set_fuel_classes(fire_ctx *ctx, const fire_fuel_class *classes, int n_classes);
+
+/* Adjoint of the arrival-time misfit (data assimilation, the use the paper
+ * gives for the level-set formulation in Sect. 7):
+ *
+ *     J = 1/2 sum over nodes with finite t_i and finite t_obs of (t_i - t_obs)^2
+ *
+ * after nsteps steps of dt from the current state with the wind held constant
+ * (wind_u_dev, wind_v_dev as in fire_step).  No ignition may be active or
+ * pending in those steps (else FIRE_ERR_STATE).  The context advances exactly
+ * as fire_run would (same kernels, same state afterwards); its psi is saved
+ * every ckpt_every steps and the states in between are recomputed during the
+ * reverse sweep.
+ *
+ *   t_obs_dev    [NY][NX] double device; NaN or +-inf where not observed
+ *   J_host       receives J (host double)
+ *   g_mult_dev   dJ/dm per node, [NY][NX] double device, at the context's
+ *                multiplier (1 where none was given)
+ *   g_moist_dev  dJ/dM_f per node, [NY][NX] double device: the derivative for
+ *                a change of the fuel moisture of that node alone, at the
+ *                class moisture (the forward path itself takes M_f per class)
+ *   g_u_dev      dJ/du on the x-faces [ny_atm][nx_atm + 1], double device
+ *   g_v_dev      dJ/dv on the y-faces [ny_atm + 1][nx_atm], double device
+ * Gradient pointers may be NULL; with all four NULL only J is computed.
+ * Derivatives follow the branches the forward values take (upwind
+ * selection, limits of the spread rate, boundary extrapolation), so they are
+ * one-sided at switch points.  Workspace: about (nsteps/ckpt_every +
+ * ckpt_every + 4) states plus 19 doubles per node, kept by the context.
+ * Synchronous: returns after J and the gradients are written. */
+int fire_adjoint(fire_ctx *ctx, int nsteps, double dt, const void *wind_u_dev,
+                 const void *wind_v_dev, const double *t_obs_dev, int ckpt_every,
+                 double *J_host, double *g_mult_dev, double *g_moist_dev, double *g_u_dev,
+                 double *g_v_dev);
+
 /* Waits for the context's stream and returns the first sticky device fault
  * (FIRE_ERR_BOUNDARY, FIRE_ERR_NONFINITE, FIRE_ERR_TIMEOUT) or FIRE_OK;
  * FIRE_ERR_CUDA if the stream reports a CUDA error. */

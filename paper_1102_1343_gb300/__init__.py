@@ -45,7 +45,8 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_create", "fire_ensemble_step", "fire_ensemble_member",
                "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
                "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test",
-               "fire_ensemble_destroy")
+               "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
+               "fire_adjoint")
 
 
 class FireError(RuntimeError):
@@ -135,6 +136,13 @@ def load_library(path: str | None = None):
     L.fire_ensemble_set_barrier_test.argtypes = [_P, C.c_int, C.c_longlong]
     L.fire_ensemble_destroy.argtypes = [_P]
     L.fire_ensemble_destroy.restype = None
+    L.fire_set_spread_mult.argtypes = [_P, _P]
+    L.fire_set_spread_mult.restype = C.c_int
+    L.fire_set_fuel_classes.argtypes = [_P, C.POINTER(fire_fuel_class), C.c_int]
+    L.fire_set_fuel_classes.restype = C.c_int
+    L.fire_adjoint.argtypes = [_P, C.c_int, C.c_double, _P, _P, _P, C.c_int,
+                               C.POINTER(C.c_double), _P, _P, _P, _P]
+    L.fire_adjoint.restype = C.c_int
     for name in ("fire_ensemble_create", "fire_ensemble_step", "fire_ensemble_member",
                  "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
                  "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test"):
@@ -399,6 +407,28 @@ def fire_ensemble_destroy(ens) -> None:
         load_library().fire_ensemble_destroy(ens)
 
 
+def fire_set_spread_mult(ctx, mult_dev) -> int:
+    return _check(load_library().fire_set_spread_mult(ctx, _ptr(mult_dev)),
+                  "fire_set_spread_mult")
+
+
+def fire_set_fuel_classes(ctx, classes) -> int:
+    cls = make_classes(classes)
+    return _check(load_library().fire_set_fuel_classes(ctx, cls, len(classes)),
+                  "fire_set_fuel_classes")
+
+
+def fire_adjoint(ctx, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, ckpt_every=20,
+                 g_mult_dev=None, g_moist_dev=None, g_u_dev=None, g_v_dev=None) -> float:
+    """Runs the misfit and its adjoint; returns J (gradients written in place)."""
+    J = C.c_double()
+    _check(load_library().fire_adjoint(ctx, int(nsteps), float(dt), _ptr(wind_u_dev),
+                                       _ptr(wind_v_dev), _ptr(t_obs_dev), int(ckpt_every),
+                                       C.byref(J), _ptr(g_mult_dev), _ptr(g_moist_dev),
+                                       _ptr(g_u_dev), _ptr(g_v_dev)), "fire_adjoint")
+    return J.value
+
+
 def fire_destroy(ctx) -> None:
     if ctx:
         load_library().fire_destroy(ctx)
@@ -441,6 +471,8 @@ class FireModel:
         torch.cuda.synchronize(dev)
         self.ctx = fire_init(grid, classes, fuel_d, None, m, zx, zy, list(ignitions),
                              self.stream.cuda_stream)
+        self.classes = [dict(c) for c in classes]
+        self.fuel_dev = fuel_d
         self.heat_s = torch.zeros((nya, nxa), dtype=torch.float64, device=dev)
         self.heat_l = torch.zeros_like(self.heat_s)
 
@@ -477,6 +509,31 @@ class FireModel:
     def status(self):
         return fire_status(self.ctx)
 
+    def set_mult(self, mult):
+        """Per-node spread multiplier (None: 1)."""
+        m = None if mult is None else self.torch.as_tensor(mult).to(self.device, self.dtype).contiguous()
+        fire_set_spread_mult(self.ctx, m)
+
+    def set_classes(self, classes):
+        self.classes = [dict(c) for c in classes]
+        fire_set_fuel_classes(self.ctx, self.classes)
+
+    def adjoint(self, u, v, dt, nsteps, tobs, ckpt_every=20, grads=True):
+        """J = 1/2 sum (t_i - t_obs)^2 after nsteps steps and (if grads) its
+        gradients dJ/dm, dJ/dM_f per node and dJ/du, dJ/dv (float64 CUDA
+        tensors).  Advances the model like run()."""
+        torch = self.torch
+        tobs = torch.as_tensor(tobs).to(self.device, torch.float64).contiguous()
+        if not grads:
+            return fire_adjoint(self.ctx, nsteps, dt, u, v, tobs, ckpt_every), None, None, None, None
+        f64 = dict(dtype=torch.float64, device=self.device)
+        gm = torch.empty((self.ny, self.nx), **f64)
+        gM = torch.empty_like(gm)
+        gu = torch.empty((self.nya, self.nxa + 1), **f64)
+        gv = torch.empty((self.nya + 1, self.nxa), **f64)
+        J = fire_adjoint(self.ctx, nsteps, dt, u, v, tobs, ckpt_every, gm, gM, gu, gv)
+        return J, gm, gM, gu, gv
+
     @property
     def time(self):
         return fire_time(self.ctx)
@@ -491,3 +548,57 @@ class FireModel:
             self.close()
         except Exception:
             pass
+
+
+def _fire_adjoint_function():
+    import torch
+
+    class FireAdjointFn(torch.autograd.Function):
+        """J(m, M_f, u, v) = 1/2 sum over nodes ignited in both of
+        (t_i - t_obs)^2 after nsteps steps from the given initial state, as a
+        differentiable torch function of the per-node spread multiplier m
+        [ny][nx], the per-class fuel moisture [n_classes] and the staggered
+        wind u [nya][nxa+1], v [nya+1][nxa].  The forward call runs
+        fire_adjoint (forward sweep, checkpoints and the reverse sweep in the
+        CUDA library) and keeps the gradients; backward scales them.  The
+        per-class moisture gradient sums the per-node one over the class map.
+
+        apply(model, state0, mult, moisture, u, v, t_obs, dt, nsteps, ckpt_every)
+        with state0 = (psi, tign, frac, t) as returned by FireModel.state()."""
+
+        @staticmethod
+        def forward(ctx, model, state0, mult, moisture, u, v, t_obs, dt, nsteps, ckpt_every):
+            psi0, tign0, frac0, t0 = state0
+            model.set_state(psi0, tign0, frac0, t0)
+            model.set_mult(mult.detach())
+            classes = [dict(c) for c in model.classes]
+            for k, mf in enumerate(moisture.detach().double().cpu().tolist()):
+                classes[k]["fuelmc_g"] = mf
+            model.set_classes(classes)
+            ud = u.detach().to(model.device, model.dtype).contiguous()
+            vd = v.detach().to(model.device, model.dtype).contiguous()
+            J, gm, gM, gu, gv = model.adjoint(ud, vd, dt, nsteps, t_obs, ckpt_every)
+            gcls = torch.zeros(len(classes), dtype=torch.float64, device=model.device)
+            gcls.index_add_(0, model.fuel_dev.long().clamp(max=len(classes) - 1).flatten(),
+                            gM.flatten())
+            ctx.save_for_backward(gm, gcls, gu, gv)
+            ctx.dtypes = (mult.dtype, moisture.dtype, u.dtype, v.dtype)
+            ctx.devices = (mult.device, moisture.device, u.device, v.device)
+            return torch.tensor(J, dtype=torch.float64, device=model.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gm, gcls, gu, gv = ctx.saved_tensors
+            out = [(gJ * g).to(d, dt_) for g, dt_, d in zip((gm, gcls, gu, gv), ctx.dtypes,
+                                                             ctx.devices)]
+            return (None, None, out[0], out[1], out[2], out[3], None, None, None, None)
+
+    return FireAdjointFn
+
+
+def __getattr__(name):
+    if name == "FireAdjointFn":
+        fn = _fire_adjoint_function()
+        globals()["FireAdjointFn"] = fn
+        return fn
+    raise AttributeError(name)

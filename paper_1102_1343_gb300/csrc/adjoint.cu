@@ -1,0 +1,676 @@
+// fire_adjoint: gradient of the arrival-time misfit
+//   J = 1/2 sum over nodes ignited in both runs of (t_i - t_obs)^2
+// with respect to the per-node spread multiplier, the per-node fuel moisture
+// and the staggered wind, by a reverse sweep through the Heun stages
+// (eq. Heun), the upwinded right-hand side (eqs. F-disc, Godunov,
+// spread-WRF-Fire) and the ignition-time interpolation
+// (eq. set-ignition-time).  The paper motivates the level-set formulation by
+// data assimilation (Sect. 7); the adjoint is what variational assimilation
+// needs.
+//
+// Forward: the context advances nsteps steps with the step kernel it uses
+// for fire_step, saving psi every K steps (checkpoints).  Reverse: for each
+// K-step segment, last first, the states psi^s of the segment are recomputed
+// from its checkpoint with the same step kernel (bitwise the same values,
+// hence the same branches), then each step is reversed:
+//   mu      = lambda + dJ/dpsi^{s+1}   (nodes whose t_i was set in step s)
+//   psi*    = psi^s + dt F(psi^s)
+//   lam*    = J_F(psi*)^T (dt/2 mu)
+//   w       = dt/2 mu + dt lam*
+//   lambda  = mu + lam* + J_F(psi^s)^T w + dJ/dpsi^s (same nodes)
+// with the parameter terms v^T dF/dp of both products summed per node.
+// Branches (Godunov selection, max/min of the spread rate, the
+// extrapolated ghosts, zeroed central differences) are those the forward
+// values take.  Each product J^T v is formed without atomics: one kernel
+// writes every node's five stencil contributions v_j dF_j/dpsi_k, the next
+// gathers them per node k, so results do not depend on scheduling.
+//
+// Precision: the state and the partial derivatives are evaluated in the
+// path precision T; adjoint fields, contributions and gradients are double.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "fire_device.cuh"
+#include "fire_internal.h"
+
+namespace wf {
+
+int ctx_step_args(fire_ctx *c, int parity, const void *u, const void *v, double dt, double *hs,
+                  double *hl, StepArgs &a);
+int ctx_info(const fire_ctx *c, int *prec, int *variant, int *nx, int *ny, int *srx, int *sry,
+             int *kx, int *ky, int *ncls, int *cur, double *t);
+bool ctx_ignition_active(fire_ctx *c, double t);
+cudaStream_t ctx_stream(const fire_ctx *c);
+const fire_fuel_class *ctx_classes_dev(const fire_ctx *c);
+int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+template <typename T>
+struct AdjArgs {
+    const T *pa, *pb;  // psi^s, psi^{s+1}
+    const T *X;        // field of the current Jacobian product
+    T *pstar;          // psi* of step s
+    const uint8_t *fuel;
+    const T *zx, *zy, *mult;  // mult nullable (1)
+    const T *u, *v;
+    const double *coef, *dcoef;  // [ncls][K_N]
+    int ncls;
+    const double *tign0, *tign, *tobs;
+    double ts, ts1, dt;
+    double *lam, *mu, *ls;
+    const double *Cin;  // contributions gathered by this kernel [5][n]
+    double *Cout;       // contributions written by this kernel [5][n]
+    double *gm, *gM, *gun, *gvn;
+    int nx, ny, nxa, nya, srx, sry;
+    T idx, idy, i2dx, i2dy, eps, dtT;
+    size_t n;
+};
+
+// stencil slots: centre, left, right, down, up
+enum { P_C = 0, P_L, P_R, P_D, P_U };
+
+template <typename T>
+__device__ __forceinline__ void stencil(const T *X, int nx, int ny, int i, int j, T &p, T &pl,
+                                        T &pr, T &pd, T &pu) {
+    const size_t k = (size_t)j * nx + i;
+    p = X[k];
+    pl = i > 0 ? X[k - 1] : ghost_value<T>(p, X[k + 1]);
+    pr = i < nx - 1 ? X[k + 1] : ghost_value<T>(p, X[k - 1]);
+    pd = j > 0 ? X[k - nx] : ghost_value<T>(p, X[k + nx]);
+    pu = j < ny - 1 ? X[k + nx] : ghost_value<T>(p, X[k - nx]);
+}
+
+// d(ghost)/d(p0), d(ghost)/d(p1) for the branch ghost_value takes
+template <typename T>
+__device__ __forceinline__ void ghost_partials(T p0, T p1, double &d0, double &d1) {
+    const T g = p0 + (p0 - p1);
+    d0 = 2.0;
+    d1 = -1.0;
+    T h = g;
+    if (p0 > h) {
+        h = p0;
+        d0 = 1.0;
+        d1 = 0.0;
+    }
+    if (p1 > h) {
+        d0 = 0.0;
+        d1 = 1.0;
+    }
+}
+
+template <typename T>
+struct NodeEnv {
+    T co[6];
+    int cls;
+    T m, un, vn, zx, zy;
+};
+
+template <typename T>
+__device__ __forceinline__ void node_env(const AdjArgs<T> &a, int i, int j, NodeEnv<T> &e) {
+    const size_t k = (size_t)j * a.nx + i;
+    int cls = a.fuel[k];
+    cls = cls > a.ncls - 1 ? a.ncls - 1 : cls;
+    e.cls = cls;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) e.co[q] = T(a.coef[(size_t)cls * K_N + q]);
+    e.m = a.mult ? a.mult[k] : T(1);
+    e.zx = a.zx[k];
+    e.zy = a.zy[k];
+    wind_at<T>(a.u, a.v, a.nxa, a.nya, a.srx, a.sry, i, j, e.un, e.vn);
+}
+
+// Partial derivatives of the right-hand side of eq. (F-disc) at one node,
+// F = -S |grad psi| + eps S Lap psi with S = m max{S0, R0 + c Ue^b + d tp^2},
+// with respect to the five stencil values and to m, S0, R0, c, d and the
+// node wind, along the branches the values take (the forward arithmetic of
+// rhs_vals, differentiated).
+template <typename T>
+struct Partials {
+    T dpsi[5];
+    T dm, dS0, dR0, dc, dd, dun, dvn;
+};
+
+template <typename T>
+__device__ __forceinline__ void node_partials(T p, T pl, T pr, T pd, T pu, T idx, T idy, T i2dx,
+                                              T i2dy, T eps, const NodeEnv<T> &e,
+                                              Partials<T> &o) {
+    const T dxm = (p - pl) * idx, dxp = (pr - p) * idx;
+    const T dym = (p - pd) * idy, dyp = (pu - p) * idy;
+    const T ax = dxm > T(0) ? dxm : T(0), bx = dxp < T(0) ? dxp : T(0);
+    const T ay = dym > T(0) ? dym : T(0), by = dyp < T(0) ? dyp : T(0);
+    const bool xm = ax * ax > bx * bx;  // D- taken along x (else D+)
+    const bool ym = ay * ay > by * by;
+    const T gx = xm ? ax : bx, gy = ym ? ay : by;
+    const T grad = Mth<T>::sqr(gx * gx + gy * gy);
+    // central differences, zeroed at the rounding level as in the forward
+    T ddx = pr - pl, ddy = pu - pd;
+    const bool kx = !(abs_val(ddx) <= Mth<T>::kGradZero * (abs_val(pr) + abs_val(pl)));
+    const bool ky = !(abs_val(ddy) <= Mth<T>::kGradZero * (abs_val(pu) + abs_val(pd)));
+    ddx = kx ? ddx : T(0);
+    ddy = ky ? ddy : T(0);
+    const T cx = ddx * i2dx, cy = ddy * i2dy;
+    T nxv, nyv;
+    Mth<T>::unit(cx, cy, nxv, nyv);
+    const T cn2 = cx * cx + cy * cy;
+    const T U = e.un * nxv + e.vn * nyv;
+    const T tp = e.zx * nxv + e.zy * nyv;
+    // spread rate and its branches
+    const T Up = U > T(0) ? U : T(0);
+    const T Ue = Up < e.co[K_E] ? Up : e.co[K_E];
+    const T tpp = tp > T(0) ? tp : T(0);
+    const T pwv = Mth<T>::pw(Ue, e.co[K_B]);
+    const T inner = e.co[K_R0] + e.co[K_C] * pwv + e.co[K_D] * tpp * tpp;
+    const bool active = inner > e.co[K_S0];
+    const T St = active ? inner : e.co[K_S0];
+    const T S = e.m * St;
+    const T lap = (dxp - dxm) + (dyp - dym);
+    const T Fs = -grad + eps * lap;  // dF/dS
+    const T dSt_dU = (active && U > T(0) && U < e.co[K_E]) ? e.co[K_C] * e.co[K_B] * pwv / Ue : T(0);
+    const T dSt_dT = (active && tp > T(0)) ? T(2) * e.co[K_D] * tp : T(0);
+    // the unit normal n = c/|c|: dn/dc = (I - n n^T)/|c|
+    T dS_dcx = T(0), dS_dcy = T(0);
+    if (cn2 > T(0)) {
+        const T rc = T(1) / Mth<T>::sqr(cn2);
+        const T dU_dcx = (e.un - U * nxv) * rc, dU_dcy = (e.vn - U * nyv) * rc;
+        const T dT_dcx = (e.zx - tp * nxv) * rc, dT_dcy = (e.zy - tp * nyv) * rc;
+        dS_dcx = e.m * (dSt_dU * dU_dcx + dSt_dT * dT_dcx);
+        dS_dcy = e.m * (dSt_dU * dU_dcy + dSt_dT * dT_dcy);
+    }
+    const T dcx = kx ? i2dx : T(0), dcy = ky ? i2dy : T(0);
+    // d|grad|/d(one-sided differences) through the taken branch
+    T wx = T(0), wy = T(0);
+    if (grad > T(0)) {
+        wx = gx / grad;
+        wy = gy / grad;
+    }
+    T dG[5] = {T(0), T(0), T(0), T(0), T(0)};
+    if (xm) {
+        dG[P_C] += wx * idx;
+        dG[P_L] -= wx * idx;
+    } else {
+        dG[P_R] += wx * idx;
+        dG[P_C] -= wx * idx;
+    }
+    if (ym) {
+        dG[P_C] += wy * idy;
+        dG[P_D] -= wy * idy;
+    } else {
+        dG[P_U] += wy * idy;
+        dG[P_C] -= wy * idy;
+    }
+    const T dL[5] = {-T(2) * idx - T(2) * idy, idx, idx, idy, idy};
+    const T dS[5] = {T(0), -dS_dcx * dcx, dS_dcx * dcx, -dS_dcy * dcy, dS_dcy * dcy};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) o.dpsi[q] = Fs * dS[q] - S * dG[q] + eps * S * dL[q];
+    const T fm = Fs * e.m;
+    o.dm = Fs * St;
+    o.dS0 = active ? T(0) : fm;
+    o.dR0 = active ? fm : T(0);
+    o.dc = active ? fm * pwv : T(0);
+    o.dd = active ? fm * tpp * tpp : T(0);
+    o.dun = fm * dSt_dU * nxv;
+    o.dvn = fm * dSt_dU * nyv;
+}
+
+// whether node k's ignition time was set in step s (the forward test of
+// eq. set-ignition-time: first crossing from > 0 to <= 0, the recorded time
+// inside the step) and the node is observed
+template <typename T>
+__device__ __forceinline__ bool crossed(const AdjArgs<T> &a, size_t k, double &q0, double &q1,
+                                        double &r) {
+    const double t0 = a.tign0[k], ti = a.tign[k], to = a.tobs[k];
+    if (!isinf(t0) || !isfinite(ti) || !isfinite(to)) return false;
+    q0 = (double)a.pa[k];
+    q1 = (double)a.pb[k];
+    if (!(q0 > 0.0 && q1 <= 0.0 && ti >= a.ts && ti <= a.ts1)) return false;
+    r = ti - to;
+    return true;
+}
+
+// seeds mu = lambda + dJ/dpsi^{s+1} and forms psi* = psi^s + dt F(psi^s)
+template <typename T>
+__global__ void k_adj_stage1(const AdjArgs<T> a) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % a.nx), j = (int)(k / a.nx);
+        double mu = a.lam[k], q0, q1, r;
+        if (crossed(a, k, q0, q1, r)) {
+            const double den = q0 - q1;
+            mu += r * a.dt * q0 / (den * den);
+        }
+        a.mu[k] = mu;
+        NodeEnv<T> e;
+        node_env(a, i, j, e);
+        T p, pl, pr, pd, pu;
+        stencil(a.pa, a.nx, a.ny, i, j, p, pl, pr, pd, pu);
+        const T F = rhs_vals<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e.co,
+                                e.m, e.un, e.vn, e.zx, e.zy);
+        a.pstar[k] = p + a.dtT * F;
+    }
+}
+
+// v^T dF/dp at node k added to the parameter gradients, and the node's five
+// stencil contributions v dF/dpsi written to Cout
+template <typename T>
+__device__ __forceinline__ void vjp_node(const AdjArgs<T> &a, size_t k, int i, int j, double v) {
+    NodeEnv<T> e;
+    node_env(a, i, j, e);
+    T p, pl, pr, pd, pu;
+    stencil(a.X, a.nx, a.ny, i, j, p, pl, pr, pd, pu);
+    Partials<T> o;
+    node_partials<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e, o);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) a.Cout[q * a.n + k] = v * (double)o.dpsi[q];
+    const double *dc = a.dcoef + (size_t)e.cls * K_N;
+    a.gm[k] += v * (double)o.dm;
+    a.gM[k] += v * ((double)o.dS0 * dc[K_S0] + (double)o.dR0 * dc[K_R0] +
+                    (double)o.dc * dc[K_C] + (double)o.dd * dc[K_D]);
+    if (a.gun) {
+        a.gun[k] += v * (double)o.dun;
+        a.gvn[k] += v * (double)o.dvn;
+    }
+}
+
+// (J_X^T v)_k: the contributions of the stencils that contain node k, with
+// the extrapolated ghosts of the boundary rows and columns mapped back to
+// the two nodes each was extrapolated from
+template <typename T>
+__device__ __forceinline__ double gather(const AdjArgs<T> &a, const double *C, const T *X,
+                                         int i, int j) {
+    const int nx = a.nx, ny = a.ny;
+    const size_t n = a.n, k = (size_t)j * nx + i;
+    double r = C[P_C * n + k];
+    if (i > 0) r += C[P_R * n + k - 1];
+    if (i < nx - 1) r += C[P_L * n + k + 1];
+    if (j > 0) r += C[P_U * n + k - nx];
+    if (j < ny - 1) r += C[P_D * n + k + nx];
+    double d0, d1;
+    const size_t row = (size_t)j * nx, col = (size_t)i;
+    if (i <= 1) {  // left ghost of row j = ghost(X[j][0], X[j][1])
+        ghost_partials<T>(X[row], X[row + 1], d0, d1);
+        r += C[P_L * n + row] * (i == 0 ? d0 : d1);
+    }
+    if (i >= nx - 2) {  // right ghost = ghost(X[j][nx-1], X[j][nx-2])
+        ghost_partials<T>(X[row + nx - 1], X[row + nx - 2], d0, d1);
+        r += C[P_R * n + row + nx - 1] * (i == nx - 1 ? d0 : d1);
+    }
+    if (j <= 1) {  // bottom ghost of column i = ghost(X[0][i], X[1][i])
+        ghost_partials<T>(X[col], X[col + nx], d0, d1);
+        r += C[P_D * n + col] * (j == 0 ? d0 : d1);
+    }
+    if (j >= ny - 2) {  // top ghost = ghost(X[ny-1][i], X[ny-2][i])
+        const size_t top = (size_t)(ny - 1) * nx + col;
+        ghost_partials<T>(X[top], X[top - nx], d0, d1);
+        r += C[P_U * n + top] * (j == ny - 1 ? d0 : d1);
+    }
+    return r;
+}
+
+// first product, at psi*: v = dt/2 mu
+template <typename T>
+__global__ void k_adj_vjp_star(const AdjArgs<T> a) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % a.nx), j = (int)(k / a.nx);
+        vjp_node(a, k, i, j, 0.5 * a.dt * a.mu[k]);
+    }
+}
+
+// lam* = gather of the first product; second product at psi^s with
+// w = dt/2 mu + dt lam*
+template <typename T>
+__global__ void k_adj_vjp_n(AdjArgs<T> a) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % a.nx), j = (int)(k / a.nx);
+        const double ls = gather(a, a.Cin, a.pstar, i, j);
+        a.ls[k] = ls;
+        vjp_node(a, k, i, j, 0.5 * a.dt * a.mu[k] + a.dt * ls);
+    }
+}
+
+// lambda = mu + lam* + J_F(psi^s)^T w + dJ/dpsi^s
+template <typename T>
+__global__ void k_adj_finish(const AdjArgs<T> a) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % a.nx), j = (int)(k / a.nx);
+        double lam = a.mu[k] + a.ls[k] + gather(a, a.Cin, a.pa, i, j);
+        double q0, q1, r;
+        if (crossed(a, k, q0, q1, r)) {
+            const double den = q0 - q1;
+            lam += r * (-a.dt * q1 / (den * den));
+        }
+        a.lam[k] = lam;
+    }
+}
+
+// Adjoint of the bilinear wind interpolation (Sect. 5): every staggered
+// face sums the node gradients times the weights the forward gave it.
+// One thread per face; the candidate nodes are those within two cells.
+template <typename T>
+__global__ void k_adj_wind(const AdjArgs<T> a, double *gu, double *gv) {
+    const int nu = a.nya * (a.nxa + 1), nv = (a.nya + 1) * a.nxa;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nu + nv; f += gridDim.x * blockDim.x) {
+        const bool isu = f < nu;
+        const int q = isu ? f : f - nu;
+        const int W = isu ? a.nxa + 1 : a.nxa;
+        const int I = q % W, J = q / W;
+        const int i_lo = max(0, (I - 2) * a.srx), i_hi = min(a.nx, (I + 2) * a.srx);
+        const int j_lo = max(0, (J - 2) * a.sry), j_hi = min(a.ny, (J + 2) * a.sry);
+        double s = 0.0;
+        for (int j = j_lo; j < j_hi; ++j) {
+            const T yr = (T(j) + T(0.5)) / T(a.sry);
+            int j0, j1;
+            T wy;
+            if (isu) lin_idx<T>(yr - T(0.5), a.nya, j0, j1, wy);
+            else lin_idx<T>(yr, a.nya + 1, j0, j1, wy);
+            double cy = 0.0;
+            if (j0 == J) cy += (double)(T(1) - wy);
+            if (j1 == J) cy += (double)wy;
+            if (cy == 0.0) continue;
+            const double *gn = (isu ? a.gun : a.gvn) + (size_t)j * a.nx;
+            for (int i = i_lo; i < i_hi; ++i) {
+                const T xr = (T(i) + T(0.5)) / T(a.srx);
+                int i0, i1;
+                T wx;
+                if (isu) lin_idx<T>(xr, a.nxa + 1, i0, i1, wx);
+                else lin_idx<T>(xr - T(0.5), a.nxa, i0, i1, wx);
+                double cx = 0.0;
+                if (i0 == I) cx += (double)(T(1) - wx);
+                if (i1 == I) cx += (double)wx;
+                if (cx != 0.0) s += gn[i] * (cy * cx);
+            }
+        }
+        if (isu) gu[q] = s;
+        else gv[q] = s;
+    }
+}
+
+// J = 1/2 sum (t_i - t_obs)^2 over nodes ignited in both: fixed-shape tree
+// sums (block partials, then one block), so the result is reproducible
+__global__ void k_misfit_partial(const double *tign, const double *tobs, size_t n, double *part) {
+    __shared__ double sh[kAdjThreads];
+    double s = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const double ti = tign[k], to = tobs[k];
+        if (isfinite(ti) && isfinite(to)) s += 0.5 * (ti - to) * (ti - to);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_misfit_final(const double *part, int nb, double *J) {
+    __shared__ double sh[kAdjThreads];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nb; k += kAdjThreads) s += part[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *J = sh[0];
+}
+
+constexpr int kMisfitBlocks = 304;
+
+int cuda_fail(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return FIRE_OK;
+    record_cuda_error(e, where);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FIRE_ERR_OOM;
+    }
+    return FIRE_ERR_CUDA;
+}
+#define ADJ_CHECK(call)                                   \
+    do {                                                  \
+        int _r = cuda_fail((call), #call);                \
+        if (_r != FIRE_OK) return _r;                     \
+    } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int c_nxa(fire_ctx *c) {
+    StepArgs a;
+    ctx_step_args(c, 0, nullptr, nullptr, 1.0, nullptr, nullptr, a);
+    return a.nxa;
+}
+int c_nya(fire_ctx *c) {
+    StepArgs a;
+    ctx_step_args(c, 0, nullptr, nullptr, 1.0, nullptr, nullptr, a);
+    return a.nya;
+}
+
+template <typename T>
+int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v,
+                const double *tobs, int K, double *J_host, double *g_mult, double *g_moist,
+                double *g_u, double *g_v) {
+    int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+    double t0;
+    ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t0);
+    const cudaStream_t st = ctx_stream(c);
+    const size_t n = (size_t)nx * ny, E = sizeof(T);
+    const bool grads = g_mult || g_moist || g_u || g_v;
+    const int nseg = (nsteps + K - 1) / K;
+
+    // host times of the step starts, as the context advances its clock
+    std::vector<double> times(nsteps + 1);
+    times[0] = t0;
+    for (int s = 0; s < nsteps; ++s) times[s + 1] = times[s] + dt;
+    for (int s = 0; s <= nsteps; ++s)
+        if (ctx_ignition_active(c, times[s])) return FIRE_ERR_STATE;
+
+    // workspace
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t o_ck = take((size_t)nseg * n * E);
+    const size_t o_ring = take((size_t)(K + 1) * n * E);
+    const size_t o_pstar = take(n * E);
+    const size_t o_F = take(2 * n * E);
+    const size_t o_t0 = take(n * sizeof(double));
+    const size_t o_ts = take(n * sizeof(double));
+    const size_t o_times = take((nsteps + 2) * sizeof(double));
+    const size_t o_small = take(16 + kMisfitBlocks * sizeof(double) + 16);
+    const size_t o_lam = take(3 * n * sizeof(double));
+    const size_t o_C = take(10 * n * sizeof(double));
+    const size_t o_g = take(4 * n * sizeof(double));
+    const size_t nu = (size_t)c_nya(c) * (c_nxa(c) + 1), nv = (size_t)(c_nya(c) + 1) * c_nxa(c);
+    const size_t o_dco = take(sizeof(double) * K_N * ncls);
+    const size_t o_wind = take(sizeof(double) * (nu + nv));
+    void *wsv = nullptr;
+    int r = ctx_workspace(c, grads ? off : o_lam, &wsv);
+    if (r) return r;
+    unsigned char *ws = static_cast<unsigned char *>(wsv);
+    T *ck = reinterpret_cast<T *>(ws + o_ck);
+    T *ring = reinterpret_cast<T *>(ws + o_ring);
+    T *pstar = reinterpret_cast<T *>(ws + o_pstar);
+    T *Fs = reinterpret_cast<T *>(ws + o_F);
+    double *tign0 = reinterpret_cast<double *>(ws + o_t0);
+    double *tsc = reinterpret_cast<double *>(ws + o_ts);
+    double *tdev = reinterpret_cast<double *>(ws + o_times);
+    double *Jdev = reinterpret_cast<double *>(ws + o_small);
+    int *stdev = reinterpret_cast<int *>(ws + o_small + 8);
+    double *part = reinterpret_cast<double *>(ws + o_small + 16);
+
+    StepArgs sa;
+    ctx_step_args(c, cur, u, v, dt, nullptr, nullptr, sa);
+    ADJ_CHECK(cudaMemcpyAsync(tign0, sa.tign, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ADJ_CHECK(cudaMemcpyAsync(tdev, times.data(), (nsteps + 1) * sizeof(double),
+                              cudaMemcpyHostToDevice, st));
+
+    // forward with checkpoints
+    for (int q = 0; q < nseg; ++q) {
+        StepArgs now;
+        int pc, pv, a1, a2, a3, a4, a5, a6, a7, pcur;
+        double tt;
+        ctx_info(c, &pc, &pv, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &pcur, &tt);
+        ctx_step_args(c, pcur, u, v, dt, nullptr, nullptr, now);
+        ADJ_CHECK(cudaMemcpyAsync(ck + (size_t)q * n, now.psi_in, n * E, cudaMemcpyDeviceToDevice,
+                                  st));
+        const int len = (q + 1) * K <= nsteps ? K : nsteps - q * K;
+        r = fire_run(c, len, dt, u, v, nullptr, nullptr);
+        if (r) return r;
+    }
+    const double *tign_final = sa.tign;
+    ADJ_CHECK(cudaGetLastError());
+    k_misfit_partial<<<kMisfitBlocks, kAdjThreads, 0, st>>>(tign_final, tobs, n, part);
+    k_misfit_final<<<1, kAdjThreads, 0, st>>>(part, kMisfitBlocks, Jdev);
+    ADJ_CHECK(cudaGetLastError());
+    ADJ_CHECK(cudaMemcpyAsync(J_host, Jdev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!grads) {
+        ADJ_CHECK(cudaStreamSynchronize(st));
+        return FIRE_OK;
+    }
+
+    double *lam = reinterpret_cast<double *>(ws + o_lam);
+    double *mu = lam + n, *ls = lam + 2 * n;
+    double *C1 = reinterpret_cast<double *>(ws + o_C), *C2 = C1 + 5 * n;
+    double *gm = reinterpret_cast<double *>(ws + o_g);
+    double *gM = gm + n, *gun = gm + 2 * n, *gvn = gm + 3 * n;
+    ADJ_CHECK(cudaMemsetAsync(lam, 0, n * sizeof(double), st));
+    ADJ_CHECK(cudaMemsetAsync(gm, 0, 4 * n * sizeof(double), st));
+    ADJ_CHECK(cudaMemsetAsync(Fs, 0, 2 * n * E, st));
+
+    // per-class d(coefficients)/d(M_f)
+    double *dcoef = reinterpret_cast<double *>(ws + o_dco);
+    ADJ_CHECK(launch_coefficients_dMf(ctx_classes_dev(c), ncls, dcoef, st));
+
+    AdjArgs<T> a;
+    memset(&a, 0, sizeof a);
+    a.fuel = sa.fuel;
+    a.zx = static_cast<const T *>(sa.dzdx);
+    a.zy = static_cast<const T *>(sa.dzdy);
+    a.mult = static_cast<const T *>(sa.mult);
+    a.u = static_cast<const T *>(u);
+    a.v = static_cast<const T *>(v);
+    a.coef = sa.coef;
+    a.dcoef = dcoef;
+    a.ncls = ncls;
+    a.tign0 = tign0;
+    a.tign = tign_final;
+    a.tobs = tobs;
+    a.dt = dt;
+    a.lam = lam;
+    a.mu = mu;
+    a.ls = ls;
+    a.gm = gm;
+    a.gM = gM;
+    a.gun = gun;
+    a.gvn = gvn;
+    a.nx = nx;
+    a.ny = ny;
+    a.nxa = sa.nxa;
+    a.nya = sa.nya;
+    a.srx = srx;
+    a.sry = sry;
+    // the step kernels' constants, rounded the same way
+    a.idx = T(1) / T(sa.dx);
+    a.idy = T(1) / T(sa.dy);
+    a.i2dx = T(1) / (T(2) * T(sa.dx));
+    a.i2dy = T(1) / (T(2) * T(sa.dy));
+    a.eps = T(sa.eps);
+    a.dtT = T(dt);
+    a.n = n;
+    a.pstar = pstar;
+
+    int dev = 0, sms = 0;
+    ADJ_CHECK(cudaGetDevice(&dev));
+    ADJ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t want = (n + kAdjThreads - 1) / kAdjThreads;
+    const int grid = (int)(want < (size_t)sms * 8 ? want : (size_t)sms * 8);
+
+    for (int q = nseg - 1; q >= 0; --q) {
+        const int s0 = q * K, s1 = (q + 1) * K <= nsteps ? (q + 1) * K : nsteps;
+        auto state = [&](int s) -> T * {
+            return s == s0 ? ck + (size_t)q * n : ring + (size_t)(s - s0) * n;
+        };
+        // recompute psi^{s0+1..s1} with the forward's step kernel
+        ADJ_CHECK(cudaMemcpyAsync(tsc, tign0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        for (int s = s0; s < s1; ++s) {
+            StepArgs ra = sa;
+            ra.psi_in = state(s);
+            ra.psi_out = state(s + 1);
+            ra.F_in = Fs + (size_t)(s & 1) * n;
+            ra.F_out = Fs + (size_t)((s + 1) & 1) * n;
+            ra.tign = tsc;
+            ra.heat_s = nullptr;
+            ra.heat_l = nullptr;
+            ra.status = stdev;
+            ra.t_in = tdev + s;
+            ra.t_out = tdev + nsteps + 1;
+            ra.dt = dt;
+            cudaError_t e = variant == FIRE_KERNEL_MARCH ? launch_march<T>(ra, st)
+                                                         : launch_step<T>(ra, st);
+            ADJ_CHECK(e);
+        }
+        for (int s = s1 - 1; s >= s0; --s) {
+            a.pa = state(s);
+            a.pb = state(s + 1);
+            a.ts = times[s];
+            a.ts1 = times[s + 1];
+            k_adj_stage1<T><<<grid, kAdjThreads, 0, st>>>(a);
+            a.X = pstar;
+            a.Cout = C1;
+            k_adj_vjp_star<T><<<grid, kAdjThreads, 0, st>>>(a);
+            a.X = a.pa;
+            a.Cin = C1;
+            a.Cout = C2;
+            k_adj_vjp_n<T><<<grid, kAdjThreads, 0, st>>>(a);
+            a.Cin = C2;
+            k_adj_finish<T><<<grid, kAdjThreads, 0, st>>>(a);
+            ADJ_CHECK(cudaGetLastError());
+        }
+    }
+    if (g_u || g_v) {
+        double *tmp = reinterpret_cast<double *>(ws + o_wind);
+        double *gu = g_u ? g_u : tmp, *gv = g_v ? g_v : tmp + nu;
+        const int wg = (int)((nu + nv + kAdjThreads - 1) / kAdjThreads);
+        k_adj_wind<T><<<wg, kAdjThreads, 0, st>>>(a, gu, gv);
+        ADJ_CHECK(cudaGetLastError());
+    }
+    if (g_mult)
+        ADJ_CHECK(cudaMemcpyAsync(g_mult, gm, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (g_moist)
+        ADJ_CHECK(cudaMemcpyAsync(g_moist, gM, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ADJ_CHECK(cudaStreamSynchronize(st));
+    return FIRE_OK;
+}
+
+}  // namespace
+}  // namespace wf
+
+extern "C" int fire_adjoint(fire_ctx *c, int nsteps, double dt, const void *wind_u_dev,
+                            const void *wind_v_dev, const double *t_obs_dev, int ckpt_every,
+                            double *J_host, double *g_mult_dev, double *g_moist_dev,
+                            double *g_u_dev, double *g_v_dev) {
+    if (!c || !wind_u_dev || !wind_v_dev || !t_obs_dev || !J_host || nsteps < 1 ||
+        ckpt_every < 1 || !isfinite(dt) || !(dt > 0.0))
+        return FIRE_ERR_ARG;
+    int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+    double t;
+    wf::ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
+    const int K = ckpt_every < nsteps ? ckpt_every : nsteps;
+    return prec == FIRE_FP64
+               ? wf::run_adjoint<double>(c, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, K,
+                                         J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev)
+               : wf::run_adjoint<float>(c, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, K,
+                                        J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev);
+}

@@ -31,31 +31,67 @@ constexpr double kBtu = 1055.05585262;  // J per BTU
 constexpr double kLatent = 2.5e6;       // L (J/kg)
 constexpr double kWindMax = 30.0;       // m/s
 
-__global__ void k_coefficients(const fire_fuel_class *cls, int n, double *coef) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const fire_fuel_class f = cls[k];
-    double *co = coef + (size_t)k * K_N;
-    const double Mf = f.fuelmc_g;
-    co[K_TF] = f.weight_is_tf ? f.weight : f.weight / (-1000.0 * log(0.6) / 600.0);
+// Scalars of the chain: double, or a forward-mode dual number (value and
+// derivative with respect to the fuel moisture M_f) for the adjoint.
+struct Dual {
+    double v, d;
+};
+__device__ __forceinline__ Dual mk(double v, double d) { return Dual{v, d}; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return mk(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return mk(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return mk(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+    return mk(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return mk(a.v + b, a.d); }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return mk(a + b.v, b.d); }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return mk(a - b.v, -b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return mk(a.v * b, a.d * b); }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return mk(a * b.v, a * b.d); }
+__device__ __forceinline__ Dual operator/(Dual a, double b) { return mk(a.v / b, a.d / b); }
+__device__ __forceinline__ Dual operator/(double a, Dual b) {
+    return mk(a / b.v, -a * b.d / (b.v * b.v));
+}
+__device__ __forceinline__ Dual pow_c(Dual a, double p) {
+    return mk(pow(a.v, p), p * pow(a.v, p - 1.0) * a.d);
+}
+__device__ __forceinline__ double pow_c(double a, double p) { return pow(a, p); }
+__device__ __forceinline__ Dual exp_s(Dual a) {
+    const double e = exp(a.v);
+    return mk(e, e * a.d);
+}
+__device__ __forceinline__ double exp_s(double a) { return exp(a); }
+__device__ __forceinline__ double val(Dual a) { return a.v; }
+__device__ __forceinline__ double val(double a) { return a; }
+template <typename S>
+__device__ __forceinline__ S constant(double x);
+template <>
+__device__ __forceinline__ double constant<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ Dual constant<Dual>(double x) { return mk(x, 0.0); }
+
+// The chain for one class at moisture Mf; co receives the K_N slots.
+template <typename S>
+__device__ void coefficient_chain(const fire_fuel_class &f, S Mf, S *co) {
+    co[K_TF] = constant<S>(f.weight_is_tf ? f.weight : f.weight / (-1000.0 * log(0.6) / 600.0));
     co[K_HS] = f.fgi * f.cmbcnst / (1.0 + Mf);
     co[K_HQ] = (Mf + 0.56) / (1.0 + Mf) * kLatent * f.fgi;
     if (f.chaparral) {
-        co[K_S0] = 0.03333;
-        co[K_R0] = 0.0;
-        co[K_B] = 1.0;
-        co[K_C] = 1.2974;
-        co[K_D] = 0.0;
-        co[K_E] = 6.0 / 1.2974;
+        co[K_S0] = constant<S>(0.03333);
+        co[K_R0] = constant<S>(0.0);
+        co[K_B] = constant<S>(1.0);
+        co[K_C] = constant<S>(1.2974);
+        co[K_D] = constant<S>(0.0);
+        co[K_E] = constant<S>(6.0 / 1.2974);
         return;
     }
-    co[K_S0] = 0.0;
-    co[K_E] = kWindMax;
+    co[K_S0] = constant<S>(0.0);
+    co[K_E] = constant<S>(kWindMax);
     if (!(f.fgi > 0.0)) {
-        co[K_R0] = 0.0;
-        co[K_B] = 1.0;
-        co[K_C] = 0.0;
-        co[K_D] = 0.0;
+        co[K_R0] = constant<S>(0.0);
+        co[K_B] = constant<S>(1.0);
+        co[K_C] = constant<S>(0.0);
+        co[K_D] = constant<S>(0.0);
         return;
     }
     // English units
@@ -65,36 +101,54 @@ __global__ void k_coefficients(const fire_fuel_class *cls, int n, double *coef) 
     const double rhoP = f.fueldens * kFt * kFt * kFt / kLb;  // lb/ft^3
     const double heat = f.cmbcnst * kLb / kBtu;            // BTU/lb
     // packing
-    const double w0 = load / (1.0 + Mf);
-    const double rhob = w0 / dep;
-    const double beta = rhob / rhoP;
+    const S w0 = load / (1.0 + Mf);
+    const S rhob = w0 / dep;
+    const S beta = rhob / rhoP;
     const double bop = 3.348 * pow(sig, -0.8189);
-    const double rel = beta / bop;
+    const S rel = beta / bop;
     // reaction intensity
     const double sig15 = pow(sig, 1.5);
     const double gmax = sig15 / (495.0 + 0.0594 * sig15);
     const double A = 1.0 / (4.77 * pow(sig, 0.1) - 7.27);
-    const double gam = gmax * pow(rel, A) * exp(A * (1.0 - rel));
-    const double wn = w0 / (1.0 + f.st);
-    const double x = Mf / f.fuelmce;
-    double etaM = 1.0 - 2.59 * x + 5.11 * x * x - 3.52 * x * x * x;
-    if (x >= 1.0 || etaM < 0.0) etaM = 0.0;
-    if (etaM > 1.0) etaM = 1.0;
+    const S gam = gmax * pow_c(rel, A) * exp_s(A * (1.0 - rel));
+    const S wn = w0 / (1.0 + f.st);
+    const S x = Mf / f.fuelmce;
+    S etaM = 1.0 - 2.59 * x + 5.11 * x * x - 3.52 * x * x * x;
+    if (val(x) >= 1.0 || val(etaM) < 0.0) etaM = constant<S>(0.0);
+    if (val(etaM) > 1.0) etaM = constant<S>(1.0);
     const double etaS = 0.174 * pow(f.se, -0.19);
-    const double IR = gam * wn * heat * etaM * etaS;
+    const S IR = gam * wn * heat * etaM * etaS;
     // propagating flux, heat sink
-    const double xi = exp((0.792 + 0.681 * sqrt(sig)) * (beta + 0.1)) / (192.0 + 0.2595 * sig);
+    const S xi = exp_s((0.792 + 0.681 * sqrt(sig)) * (beta + 0.1)) / (192.0 + 0.2595 * sig);
     const double epsh = exp(-138.0 / sig);
-    const double Qig = 250.0 + 1116.0 * Mf;
-    const double R0 = IR * xi / (rhob * epsh * Qig) * (kFt / 60.0);  // ft/min -> m/s
+    const S Qig = 250.0 + 1116.0 * Mf;
+    const S R0 = IR * xi / (rhob * epsh * Qig) * (kFt / 60.0);  // ft/min -> m/s
     // wind and slope factors
     const double B = 0.02526 * pow(sig, 0.54);
     const double C = 7.47 * exp(-0.133 * pow(sig, 0.55));
     const double E = 0.715 * exp(-3.59e-4 * sig);
     co[K_R0] = R0;
-    co[K_B] = B;
-    co[K_C] = R0 * C * pow(f.windrf * (60.0 / kFt), B) * pow(rel, -E);
-    co[K_D] = R0 * 5.275 * pow(beta, -0.3);
+    co[K_B] = constant<S>(B);
+    co[K_C] = R0 * C * pow(f.windrf * (60.0 / kFt), B) * pow_c(rel, -E);
+    co[K_D] = R0 * 5.275 * pow_c(beta, -0.3);
+}
+
+__global__ void k_coefficients(const fire_fuel_class *cls, int n, double *coef) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const fire_fuel_class f = cls[k];
+    coefficient_chain<double>(f, f.fuelmc_g, coef + (size_t)k * K_N);
+}
+
+// d(coefficients)/d(M_f) at the class moisture (clamped branches of eta_M
+// and the chaparral rule have derivative 0)
+__global__ void k_coefficients_dMf(const fire_fuel_class *cls, int n, double *dcoef) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const fire_fuel_class f = cls[k];
+    Dual co[K_N];
+    coefficient_chain<Dual>(f, mk(f.fuelmc_g, 1.0), co);
+    for (int q = 0; q < K_N; ++q) dcoef[(size_t)k * K_N + q] = co[q].d;
 }
 
 }  // namespace
@@ -102,6 +156,12 @@ __global__ void k_coefficients(const fire_fuel_class *cls, int n, double *coef) 
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s) {
     k_coefficients<<<(n + 63) / 64, 64, 0, s>>>(classes_dev, n, coef_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coefficients_dMf(const fire_fuel_class *classes_dev, int n, double *dcoef_dev,
+                                    cudaStream_t s) {
+    k_coefficients_dMf<<<(n + 63) / 64, 64, 0, s>>>(classes_dev, n, dcoef_dev);
     return cudaGetLastError();
 }
 

@@ -57,6 +57,10 @@ struct fire_ctx {
     double *g_hs = nullptr, *g_hl = nullptr;
     int g_kx = 0, g_ky = 0, g_variant = -1;
 
+    // workspace of fire_adjoint (grown on demand, freed with the context)
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;  // pairs
@@ -100,7 +104,7 @@ void release(fire_ctx *c) {
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     void *bufs[] = {c->psi[0], c->psi[1], c->frac[0], c->frac[1], c->tign, c->fuel, c->dzdx,
                     c->dzdy, c->mult, c->classes_dev, c->coef, c->status, c->tdev,
-                    c->stage_u, c->stage_v, c->stage_hs, c->stage_hl};
+                    c->stage_u, c->stage_v, c->stage_hs, c->stage_hl, c->ws};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -326,6 +330,23 @@ bool ctx_ignition_active(fire_ctx *c, double t) {
 }
 
 cudaStream_t ctx_stream(const fire_ctx *c) { return c->stream; }
+
+const fire_fuel_class *ctx_classes_dev(const fire_ctx *c) { return c->classes_dev; }
+
+int ctx_workspace(fire_ctx *c, size_t bytes, void **out) {
+    if (bytes > c->ws_bytes) {
+        if (c->ws) {
+            WF_CHECK(cudaStreamSynchronize(c->stream));  // the old one may be in use
+            cudaFree(c->ws);
+            c->ws = nullptr;
+            c->ws_bytes = 0;
+        }
+        WF_CHECK(cudaMalloc(&c->ws, bytes));
+        c->ws_bytes = bytes;
+    }
+    *out = c->ws;
+    return FIRE_OK;
+}
 }  // namespace wf
 
 extern "C" {
@@ -590,6 +611,46 @@ int fire_set_state(fire_ctx *c, const void *psi, const double *tign, const void 
     // the device time follows through a host-pinned-free path: synchronous copy
     WF_CHECK(cudaMemcpyAsync(c->tdev + c->cur, &c->t, sizeof(double), cudaMemcpyHostToDevice,
                              c->stream));
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    return FIRE_OK;
+}
+
+int fire_set_spread_mult(fire_ctx *c, const void *mult_dev) {
+    if (!c) return FIRE_ERR_ARG;
+    const size_t N = c->n, E = c->esz;
+    const bool had = c->mult != nullptr;
+    if (had != (mult_dev != nullptr)) {
+        // the multiplier pointer changes: the captured step graph is stale
+        WF_CHECK(cudaStreamSynchronize(c->stream));
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        if (had) {
+            cudaFree(c->mult);
+            c->mult = nullptr;
+        } else {
+            WF_CHECK(cudaMalloc(&c->mult, N * E));
+        }
+    }
+    if (mult_dev)
+        WF_CHECK(cudaMemcpyAsync(c->mult, mult_dev, N * E, cudaMemcpyDeviceToDevice, c->stream));
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    return FIRE_OK;
+}
+
+int fire_set_fuel_classes(fire_ctx *c, const fire_fuel_class *classes, int n_classes) {
+    if (!c || !classes || n_classes != c->ncls) return FIRE_ERR_ARG;
+    for (int k = 0; k < n_classes; ++k) {
+        const fire_fuel_class &f = classes[k];
+        if (f.fgi > 0 && !f.chaparral &&
+            !(f.savr > 0 && f.fueldepthm > 0 && f.fueldens > 0 && f.fuelmce > 0 && f.se > 0))
+            return FIRE_ERR_ARG;
+        if (!(f.weight > 0)) return FIRE_ERR_ARG;
+    }
+    WF_CHECK(cudaMemcpyAsync(c->classes_dev, classes, sizeof(fire_fuel_class) * n_classes,
+                             cudaMemcpyHostToDevice, c->stream));
+    WF_CHECK(launch_coefficients(c->classes_dev, n_classes, c->coef, c->stream));
     WF_CHECK(cudaStreamSynchronize(c->stream));
     return FIRE_OK;
 }

@@ -88,6 +88,10 @@ constexpr int kMarchMaxColumns = 248;  // output columns of one marching strip (
 
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s);
+// d(coefficients)/d(M_f) per class at the class moisture (forward-mode dual
+// numbers through the same chain)
+cudaError_t launch_coefficients_dMf(const fire_fuel_class *classes_dev, int n, double *dcoef_dev,
+                                    cudaStream_t s);
 
 // remembers the last CUDA error an entry point saw on this host thread
 // (read back through fire_last_cuda_error)

@@ -283,5 +283,31 @@ def ensemble_member(k, nxa, seed=BASE_SEED, steps=600) -> Workload:
                             wind_scale=ws, moisture_shift=ms, name=f"member{k}-{nxa * 10}")
 
 
+def smooth_field(rng, ny, nx, sigma_nodes):
+    """Gaussian-filtered white noise, centred and scaled to max |f| = 1."""
+    from scipy.ndimage import gaussian_filter
+    f = gaussian_filter(rng.standard_normal((ny, nx)), sigma=sigma_nodes, mode="reflect")
+    f = f - f.mean()
+    m = np.abs(f).max()
+    return f / m if m > 0 else f
+
+
+def adjoint_case(nxa=51, sr=10, seed=BASE_SEED, steps=400, dt=0.5):
+    """Adjoint workload: the landscape recipe on an nxa x nxa atmospheric mesh
+    (51 -> 510x510 fire mesh) with one central point ignition, and the
+    perturbations of the synthetic 'truth' run whose arrival times serve as
+    observations: multiplier 1 + 0.2 f (f a smooth field of 300 m length,
+    max |f| = 1), fuel moisture + 0.02 in every class, wind x 1.1.
+    Returns (workload, truth) with truth = dict(mult, classes, wind_scale)."""
+    w = random_landscape(nxa, nxa, sr=sr, seed=seed, steps=steps, dt=dt, ignition="center",
+                         name=f"adjoint-{nxa * sr}x{nxa * sr}")
+    rng = np.random.default_rng(seed + 77)
+    mult = 1.0 + 0.2 * smooth_field(rng, w.ny, w.nx, 300.0 / w.dx)
+    classes = [dict(c) for c in w.classes]
+    for c in classes:
+        c["fuelmc_g"] = c["fuelmc_g"] + 0.02
+    return w, dict(mult=mult, classes=classes, wind_scale=1.1)
+
+
 def wind_arrays_like(w: Workload, dtype=np.float64):
     return np.ascontiguousarray(w.u, dtype=dtype), np.ascontiguousarray(w.v, dtype=dtype)

@@ -1,0 +1,251 @@
+"""GPU adjoint of the arrival-time misfit (fire_adjoint, FireAdjointFn)
+against the oracle's reference adjoint and against central finite
+differences of the GPU forward, FP64 and FP32."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1102_1343_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    from paper_1102_1343_gb300 import build
+    build.build()
+    import paper_1102_1343_gb300 as p
+    p.load_library()
+    assert torch.cuda.is_available()
+    return p
+
+
+def small_case(seed=7, dy_atm=None):
+    """2 m cells, centred ignition, spread multiplier 3 (the front crosses
+    several cells in 60 steps of 0.25 s); no ignition after t = 0."""
+    w = synth.random_landscape(8, 8, sr=5, dx_atm=10.0, seed=seed, ignition="center", steps=60,
+                               dt=0.25)
+    if dy_atm is not None:
+        w.dy_atm = dy_atm
+    rng = np.random.default_rng(seed + 5)
+    w.mult = 3.0 * (1.0 + 0.05 * rng.standard_normal((w.ny, w.nx)))
+    return w
+
+
+def observations(w, nsteps):
+    """Arrival times of an oracle 'truth' run: multiplier x1.2, moisture -0.02,
+    wind x1.1 (NaN where the truth did not burn)."""
+    classes = [dict(c, fuelmc_g=max(0.01, c["fuelmc_g"] - 0.02)) for c in w.classes]
+    f = oracle.OracleFire.from_workload(w, classes=classes, mult=w.mult * 1.2)
+    for _ in range(nsteps):
+        f.step(w.u * 1.1, w.v * 1.1, w.dt)
+    return np.where(np.isfinite(f.tign), f.tign, np.nan)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def gpu_adjoint(pkg, w, prec, nsteps, tobs, ckpt):
+    m = pkg.FireModel.from_workload(w, precision=prec)
+    u, v = m.wind(w.u, w.v)
+    J, gm, gM, gu, gv = m.adjoint(u, v, w.dt, nsteps, tobs, ckpt_every=ckpt)
+    out = (J, gm.cpu().numpy(), gM.cpu().numpy(), gu.cpu().numpy(), gv.cpu().numpy())
+    st = m.state()
+    m.close()
+    return out, st
+
+
+@pytest.mark.parametrize("dy_atm", [None, 14.0])
+def test_fp64_matches_oracle_adjoint(pkg, dy_atm):
+    w = small_case(dy_atm=dy_atm)
+    nsteps = 60
+    tobs = observations(w, nsteps)
+    ref = oracle.OracleFire.from_workload(w)
+    Jr, gmr, gMr, gur, gvr = ref.adjoint(w.u, w.v, w.dt, nsteps, tobs)
+    assert Jr > 0
+    (J, gm, gM, gu, gv), st = gpu_adjoint(pkg, w, "fp64", nsteps, tobs, ckpt=7)
+    assert abs(J - Jr) <= 1e-10 * Jr
+    for g, gr, name in ((gm, gmr, "mult"), (gM, gMr, "moist"), (gu, gur, "u"), (gv, gvr, "v")):
+        e = rel(g, gr)
+        print(f"fp64 d{name}: rel err {e:.2e}")
+        assert e <= 1e-8, (name, e)
+    # the call advanced the context like the forward steps: same state
+    assert np.array_equal(st[1].cpu().numpy() == np.inf, ref.tign == np.inf)
+    assert np.max(np.abs(st[0].cpu().numpy() - ref.psi)) <= 1e-10 * np.max(np.abs(ref.psi))
+
+
+def test_checkpoint_interval_does_not_change_the_result(pkg):
+    w = small_case(seed=9)
+    nsteps = 40
+    tobs = observations(w, nsteps)
+    outs = [gpu_adjoint(pkg, w, "fp64", nsteps, tobs, ckpt=k)[0] for k in (1, 7, 40, 100)]
+    for o in outs[1:]:
+        assert o[0] == outs[0][0]
+        for a, b in zip(o[1:], outs[0][1:]):
+            assert np.array_equal(a, b)
+
+
+def test_fp32_against_fp64_oracle(pkg):
+    """FP32 state and partial derivatives, double adjoint fields: the gradient
+    differs from the FP64 oracle's by the FP32 rounding of the forward states
+    (relative 1e-7 per operation, amplified through the 1/(psi^n - psi^{n+1})
+    of the ignition-time interpolation); bound 2e-3 in norm."""
+    w = small_case(seed=7)
+    nsteps = 60
+    tobs = observations(w, nsteps)
+    ref = oracle.OracleFire.from_workload(w)
+    Jr, gmr, gMr, gur, gvr = ref.adjoint(w.u, w.v, w.dt, nsteps, tobs)
+    (J, gm, gM, gu, gv), _ = gpu_adjoint(pkg, w, "fp32", nsteps, tobs, ckpt=20)
+    print(f"fp32: J rel {abs(J - Jr) / Jr:.2e}")
+    assert abs(J - Jr) <= 2e-3 * Jr
+    for g, gr, name in ((gm, gmr, "mult"), (gM, gMr, "moist"), (gu, gur, "u"), (gv, gvr, "v")):
+        e = rel(g, gr)
+        print(f"fp32 d{name}: rel err {e:.2e}")
+        assert e <= 2e-3, (name, e)
+
+
+def test_fp64_gradient_matches_gpu_central_differences(pkg):
+    """Directional derivatives of the GPU forward misfit (J-only calls) along
+    random multiplier, wind and class-moisture directions, away from switch
+    points (same set of ignited nodes in the perturbed runs)."""
+    import torch
+    w = small_case(seed=11)
+    nsteps = 50
+    tobs = observations(w, nsteps)
+    m = pkg.FireModel.from_workload(w, precision="fp64")
+    st0 = m.state()
+    st0 = tuple(x.clone() if hasattr(x, "clone") else x for x in st0)
+    u0, v0 = m.wind(w.u, w.v)
+    mult0 = torch.as_tensor(w.mult).cuda().double()
+    classes0 = [dict(c) for c in w.classes]
+    J, gm, gM, gu, gv = m.adjoint(u0, v0, w.dt, nsteps, tobs)
+    fuel = torch.as_tensor(w.fuel).cuda().long()
+    gcls = torch.zeros(len(classes0), dtype=torch.float64, device="cuda").index_add_(
+        0, fuel.flatten(), gM.flatten())
+    ign0 = torch.isfinite(m.state()[1]).cpu().numpy()
+
+    def J_at(mult, classes, u, v):
+        m.set_state(*st0)
+        m.set_mult(mult)
+        m.set_classes(classes)
+        Jv, *_ = m.adjoint(u, v, w.dt, nsteps, tobs, grads=False)
+        ign = torch.isfinite(m.state()[1]).cpu().numpy()
+        return Jv, ign
+
+    rng = np.random.default_rng(3)
+    checked = 0
+    for q in range(4):
+        dm = torch.as_tensor(rng.standard_normal((w.ny, w.nx))).cuda()
+        du = torch.as_tensor(rng.standard_normal(w.u.shape)).cuda()
+        dv = torch.as_tensor(rng.standard_normal(w.v.shape)).cuda()
+        dc = rng.standard_normal(len(classes0)) * 0.01
+        h = 1e-6
+        cases = {
+            "m": (lambda s: (mult0 + s * h * dm, classes0, u0, v0), float((gm * dm).sum())),
+            "u": (lambda s: (mult0, classes0, u0 + s * h * du, v0), float((gu * du).sum())),
+            "v": (lambda s: (mult0, classes0, u0, v0 + s * h * dv), float((gv * dv).sum())),
+            "M": (lambda s: (mult0, [dict(c, fuelmc_g=c["fuelmc_g"] + s * h * dc[k])
+                                     for k, c in enumerate(classes0)], u0, v0),
+                  float(np.dot(gcls.cpu().numpy(), dc))),
+        }
+        for name, (args, ad) in cases.items():
+            Jp, ip = J_at(*args(1.0))
+            Jm, im = J_at(*args(-1.0))
+            if not (np.array_equal(ip, ign0) and np.array_equal(im, ign0)):
+                continue
+            fd = (Jp - Jm) / (2 * h)
+            print(f"{name}: fd {fd:.6e} adjoint {ad:.6e}")
+            assert abs(fd - ad) <= 1e-5 * max(abs(fd), 1e-3 * J), (name, q, fd, ad)
+            checked += 1
+    assert checked >= 12
+    m.close()
+
+
+def test_autograd_function(pkg):
+    import torch
+    w = small_case(seed=13)
+    nsteps = 40
+    tobs = torch.as_tensor(observations(w, nsteps)).cuda()
+    m = pkg.FireModel.from_workload(w, precision="fp64")
+    st0 = tuple(x.clone() if hasattr(x, "clone") else x for x in m.state())
+    mult = torch.as_tensor(w.mult).cuda().double().requires_grad_(True)
+    moist = torch.tensor([c["fuelmc_g"] for c in w.classes], dtype=torch.float64,
+                         requires_grad=True)
+    u = torch.as_tensor(w.u).cuda().double().requires_grad_(True)
+    v = torch.as_tensor(w.v).cuda().double().requires_grad_(True)
+    J = pkg.FireAdjointFn.apply(m, st0, mult, moist, u, v, tobs, w.dt, nsteps, 10)
+    (2.0 * J).backward()
+    # against the raw entry point
+    m2 = pkg.FireModel.from_workload(w, precision="fp64")
+    J2, gm, gM, gu, gv = m2.adjoint(*m2.wind(w.u, w.v), w.dt, nsteps, tobs, ckpt_every=10)
+    assert float(J.detach()) == J2
+    assert torch.equal(mult.grad, 2.0 * gm)
+    assert torch.equal(u.grad, 2.0 * gu) and torch.equal(v.grad, 2.0 * gv)
+    fuel = torch.as_tensor(w.fuel).cuda().long().flatten()
+    gcls = torch.zeros(len(w.classes), dtype=torch.float64, device="cuda").index_add_(
+        0, fuel, gM.flatten())
+    assert torch.allclose(moist.grad, 2.0 * gcls.cpu(), rtol=1e-14, atol=0)
+    assert moist.grad.device.type == "cpu"
+    # a second evaluation from the same initial state gives the same J
+    J3 = pkg.FireAdjointFn.apply(m, st0, mult.detach(), moist.detach(), u.detach(),
+                                 v.detach(), tobs, w.dt, nsteps, 10)
+    assert float(J3) == float(J)
+    m.close()
+    m2.close()
+
+
+def test_misfit_only_call_advances_like_run(pkg):
+    import torch
+    w = small_case(seed=7)
+    nsteps = 30
+    tobs = observations(w, nsteps)
+    a = pkg.FireModel.from_workload(w, precision="fp32")
+    b = pkg.FireModel.from_workload(w, precision="fp32")
+    u, v = a.wind(w.u, w.v)
+    J, *_ = a.adjoint(u, v, w.dt, nsteps, tobs, grads=False)
+    b.run(nsteps, u, v, w.dt)
+    sa, sb = a.state(), b.state()
+    for x, y in zip(sa[:3], sb[:3]):
+        assert torch.equal(x, y)
+    assert sa[3] == sb[3]
+    ti = sb[1].cpu().numpy()
+    ok = np.isfinite(ti) & np.isfinite(tobs)
+    assert abs(J - 0.5 * np.sum((ti[ok] - tobs[ok]) ** 2)) <= 1e-12 * max(J, 1.0)
+    a.close()
+    b.close()
+
+
+def test_pending_ignition_is_rejected(pkg):
+    w = small_case(seed=7)
+    w.ignitions = w.ignitions + [synth.point_ignition(30.0, 30.0, radius=4.0, t_start=2.0)]
+    m = pkg.FireModel.from_workload(w, precision="fp64")
+    u, v = m.wind(w.u, w.v)
+    tobs = np.full((w.ny, w.nx), np.nan)
+    with pytest.raises(pkg.FireError) as e:
+        m.adjoint(u, v, w.dt, 20, tobs)
+    assert e.value.code == pkg.FIRE_ERR_STATE
+    m.close()
+
+
+def test_full_size_fp64_matches_oracle(pkg):
+    """The 510x510 adjoint workload (51 atmos cells x 10), 400 steps of 0.5 s,
+    checkpoints every 20 steps, against the oracle's reference adjoint."""
+    w, truth = synth.adjoint_case()
+    f = oracle.OracleFire.from_workload(w, classes=truth["classes"], mult=truth["mult"])
+    for _ in range(w.steps):
+        f.step(w.u * truth["wind_scale"], w.v * truth["wind_scale"], w.dt)
+    tobs = np.where(np.isfinite(f.tign), f.tign, np.nan)
+    ref = oracle.OracleFire.from_workload(w)
+    Jr, gmr, gMr, gur, gvr = ref.adjoint(w.u, w.v, w.dt, w.steps, tobs)
+    assert Jr > 0
+    (J, gm, gM, gu, gv), _ = gpu_adjoint(pkg, w, "fp64", w.steps, tobs, ckpt=20)
+    assert abs(J - Jr) <= 1e-10 * Jr
+    for g, gr, name in ((gm, gmr, "mult"), (gM, gMr, "moist"), (gu, gur, "u"), (gv, gvr, "v")):
+        e = rel(g, gr)
+        print(f"510x510 fp64 d{name}: rel err {e:.2e}")
+        assert e <= 1e-8, (name, e)
