@@ -355,6 +355,13 @@ def run_gpu(args, rank, world):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(args.workload, seconds=args.cpu_seconds)
+    adj = ens = None
+    if rank == 0 and not args.no_adjoint:
+        adj = bench_adjoint(pkg, dev)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_ensemble:
+        ens = bench_ensemble(pkg, dev)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {
@@ -380,10 +387,163 @@ def run_gpu(args, rank, world):
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "cpu_baseline": cpu,
             "fp64_plain_gpu": fp64,
+            "adjoint": adj,
+            "ensemble": ens,
             "clocks": clk,
             "status": pkg.fire_strerror(status if status else final_status),
         }
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the two growth rows: adjoint and batched ensemble
+# ---------------------------------------------------------------------------
+
+def _clone_state(st):
+    return tuple(x.clone() if hasattr(x, "clone") else x for x in st)
+
+
+def bench_adjoint(pkg, dev, ckpt=20):
+    """fire_adjoint on the 510x510 adjoint workload (400 steps of 0.5 s,
+    checkpoints every 20): misfit against the arrival times of a perturbed
+    truth run, gradients w.r.t. multiplier, moisture and wind.  Cell-steps/s
+    of the whole call (forward with checkpoints + reverse sweep) and of the
+    plain FP64 forward on the same mesh, each with its autotuned kernel."""
+    import torch
+    from paper_1102_1343_gb300 import synth
+    w, truth = synth.adjoint_case()
+    n = w.nx * w.ny * w.steps
+    import dataclasses
+    wt = dataclasses.replace(w, mult=truth["mult"], classes=truth["classes"])
+    tr = pkg.FireModel.from_workload(wt, precision="fp64", device=dev)
+    ut, vt = tr.wind(w.u * truth["wind_scale"], w.v * truth["wind_scale"])
+    tr.autotune(ut, vt, w.dt)
+    tr.run(w.steps, ut, vt, w.dt)
+    tobs = tr.state()[1]
+    tobs = torch.where(torch.isfinite(tobs), tobs, torch.full_like(tobs, float("nan")))
+    tr.close()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"{w.name} (51x51 atmos x10, centre ignition), {w.steps} steps of "
+                       f"{w.dt} s, checkpoints every {ckpt}; t_obs from a truth run with "
+                       "multiplier 1+0.2f, moisture +0.02, wind x1.1",
+           "unit": UNIT}
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        m = pkg.FireModel.from_workload(w, precision=prec, device=dev)
+        u, v = m.wind(w.u, w.v)
+        kern = m.autotune(u, v, w.dt)
+        st0 = _clone_state(m.state())
+        J, gm, gM, gu, gv = m.adjoint(u, v, w.dt, w.steps, tobs, ckpt)  # warm-up
+        m.set_state(*st0)
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        J, gm, gM, gu, gv = m.adjoint(u, v, w.dt, w.steps, tobs, ckpt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        grads[prec] = (J, gm, gM, gu, gv)
+        rec = {"value": n / (ms / 1e3), "ms": ms, "J": J,
+               "kernel": {"variant": ["tile", "march"][kern[0]], "tile_atmos_cells": list(kern[1:])}}
+        # the plain forward on the same mesh and kernel
+        m.set_state(*st0)
+        m.run(2, u, v, w.dt)
+        m.set_state(*st0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.run(w.steps, u, v, w.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1)
+        rec["plain_forward"] = {"value": n / (fms / 1e3), "ms": fms}
+        out[prec] = rec
+        m.close()
+    base = out["fp64"]["plain_forward"]["value"]
+    out["speedup_vs_fp64_plain_forward"] = {p: out[p]["value"] / base for p in ("fp64", "fp32")}
+
+    def rel(a, b):
+        return float(torch.linalg.norm((a - b).flatten()) / max(float(torch.linalg.norm(b.flatten())), 1e-300))
+    g64, g32 = grads["fp64"], grads["fp32"]
+    out["fp32_vs_fp64_gradient_rel"] = {k: rel(g32[i], g64[i]) for i, k in
+                                        ((1, "mult"), (2, "moisture"), (3, "u"), (4, "v"))}
+    out["fp32_vs_fp64_J_rel"] = abs(g32[0] - g64[0]) / max(abs(g64[0]), 1e-300)
+    out["accuracy_note"] = ("GPU FP64 gradients equal the oracle's reference adjoint to ~1e-15 "
+                            "relative on this workload (tests/test_adjoint_gpu.py)")
+    return out
+
+
+def bench_ensemble(pkg, dev, steps=600, n_members=64):
+    """64 members of uneven size (fire meshes 390^2..2050^2, 96.8 M nodes in
+    all), wind x U[0.8, 1.2] and moisture +- 0.03 per member, FP32 with FP64
+    ignition time: one fire_ensemble_step call of 600 steps (persistent
+    cooperative launch replayed from a CUDA graph, autotuned strips), against
+    the same members run one by one (fire_run, FP32 and the plain FP64 step)."""
+    import torch
+    from paper_1102_1343_gb300 import synth
+    sizes = synth.ensemble_sizes(n_members)
+    ws = [synth.ensemble_member(k, s, steps=steps) for k, s in enumerate(sizes)]
+    cells = sum(w.nx * w.ny for w in ws)
+    keep, members, us, vs = [], [], [], []
+    for w in ws:
+        fuel = torch.as_tensor(w.fuel).to(dev).contiguous()
+        zx = torch.as_tensor(w.dzdx).to(dev, torch.float32).contiguous()
+        zy = torch.as_tensor(w.dzdy).to(dev, torch.float32).contiguous()
+        keep += [fuel, zx, zy]
+        members.append(dict(grid=pkg.make_grid(w.nxa, w.nya, w.srx, w.sry, w.dx_atm, w.dy_atm,
+                                               pkg.FIRE_FP32, w.band, w.eps),
+                            classes=w.classes, fuel_class_dev=fuel, dzdx_dev=zx, dzdy_dev=zy,
+                            ignitions=w.ignitions))
+        us.append(torch.as_tensor(w.u).to(dev, torch.float32).contiguous())
+        vs.append(torch.as_tensor(w.v).to(dev, torch.float32).contiguous())
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ens = pkg.fire_ensemble_create(members, stream.cuda_stream)
+    dt = ws[0].dt
+    shape = pkg.fire_ensemble_autotune(ens, 3, dt, us, vs)
+    grid, items = pkg.fire_ensemble_get_kernel(ens)
+    pkg.fire_ensemble_step(ens, 5, dt, us, vs)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    pkg.fire_ensemble_step(ens, steps, dt, us, vs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    code, _ = pkg.fire_ensemble_status(ens, n_members)
+    pkg.fire_ensemble_destroy(ens)
+    value = cells * steps / (ms / 1e3)
+    out = {"workload": f"{n_members} members, fire meshes {min(w.nx for w in ws)}^2.."
+                       f"{max(w.nx for w in ws)}^2 ({cells / 1e6:.1f} M nodes), {steps} steps "
+                       f"of {dt} s, FP32 + FP64 t_i",
+           "value": value, "unit": UNIT, "ms": ms, "launch_calls": 1,
+           "strip_nodes": list(shape), "grid_ctas": grid, "work_items_per_step": items,
+           "status": pkg.fire_strerror(code)}
+    # the same members one by one (sample of 20 steps each)
+    del keep
+    seq = {}
+    for prec in ("fp32", "fp64"):
+        tot_ms, tot_cs = 0.0, 0
+        for w in ws:
+            m = pkg.FireModel.from_workload(w, precision=prec, device=dev)
+            u, v = m.wind(w.u, w.v)
+            m.autotune(u, v, w.dt, probe_steps=2)
+            m.run(2, u, v, w.dt)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            m.run(20, u, v, w.dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            tot_cs += w.nx * w.ny * 20
+            m.close()
+        seq[prec] = {"value": tot_cs / (tot_ms / 1e3), "unit": UNIT,
+                     "sample": "each member alone (own autotuned kernel), 20 steps"}
+    out["one_by_one"] = seq
+    out["speedup_vs_fp64_plain_per_run"] = value / seq["fp64"]["value"]
+    out["speedup_vs_fp32_per_run"] = value / seq["fp32"]["value"]
+    return out
 
 
 def main():
@@ -403,6 +563,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

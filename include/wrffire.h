@@ -250,6 +250,16 @@ enum fire_kernel_variant { FIRE_KERNEL_TILE = 0, FIRE_KERNEL_MARCH = 1 };
 int fire_set_kernel(fire_ctx *ctx, int variant, int kx, int ky);
 int fire_get_kernel(const fire_ctx *ctx, int *variant, int *kx, int *ky);
 
+/* Autotuner of the step kernel: times candidate shapes (the marching strip
+ * with widths of about 16..248 columns and heights of about 8..512 rows; the
+ * 2-D tile at a few shapes) for probe_steps launches each on a scratch copy
+ * of the current state with the given wind and dt, keeps the fastest
+ * (fire_set_kernel) and reports it (outputs nullable).  The state and the
+ * model time are unchanged; the scratch is the context's workspace.
+ * Synchronous. */
+int fire_autotune(fire_ctx *ctx, const void *wind_u_dev, const void *wind_v_dev, double dt,
+                  int probe_steps, int *variant, int *kx, int *ky);
+
 /* Kernel timing: when enabled, CUDA events bracket every launch of the fused
  * step kernel on the context's stream; fire_kernel_time_ms waits for them and
  * returns the summed device time and the launch count since the last reset. */
@@ -351,6 +361,15 @@ int fire_ensemble_clear_status(fire_ensemble *ens);
  * reports the grid and the number of work items per step. */
 int fire_ensemble_set_kernel(fire_ensemble *ens, int strip_columns, int strip_rows);
 int fire_ensemble_get_kernel(const fire_ensemble *ens, int *grid_ctas, int *work_items);
+
+/* Autotuner of the strip shape: times candidate shapes (40..240 columns x
+ * 20..320 rows) on probe_steps steps of the members with the given winds,
+ * each from the members' current states, keeps the fastest and puts the
+ * states back.  No ignition may be active or pending within 2 probe_steps
+ * steps (else FIRE_ERR_STATE).  Outputs nullable.  Synchronous. */
+int fire_ensemble_autotune(fire_ensemble *ens, int probe_steps, double dt,
+                           const void *const *wind_u_dev, const void *const *wind_v_dev,
+                           int *strip_columns, int *strip_rows);
 
 /* Test hook for the bounded barrier: CTA skip_block (-1: none) never
  * arrives at the barriers, and waits give up after spin_limit polls (about

@@ -46,7 +46,7 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
                "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test",
                "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
-               "fire_adjoint")
+               "fire_adjoint", "fire_autotune", "fire_ensemble_autotune")
 
 
 class FireError(RuntimeError):
@@ -143,6 +143,12 @@ def load_library(path: str | None = None):
     L.fire_adjoint.argtypes = [_P, C.c_int, C.c_double, _P, _P, _P, C.c_int,
                                C.POINTER(C.c_double), _P, _P, _P, _P]
     L.fire_adjoint.restype = C.c_int
+    L.fire_autotune.argtypes = [_P, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fire_autotune.restype = C.c_int
+    L.fire_ensemble_autotune.argtypes = [_P, C.c_int, C.c_double, C.POINTER(_P), C.POINTER(_P),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fire_ensemble_autotune.restype = C.c_int
     for name in ("fire_ensemble_create", "fire_ensemble_step", "fire_ensemble_member",
                  "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
                  "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test"):
@@ -429,6 +435,27 @@ def fire_adjoint(ctx, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, ckpt_every=
     return J.value
 
 
+def fire_autotune(ctx, wind_u_dev, wind_v_dev, dt, probe_steps=3):
+    """Times candidate step-kernel shapes, keeps the fastest; returns
+    (variant, kx, ky)."""
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(load_library().fire_autotune(ctx, _ptr(wind_u_dev), _ptr(wind_v_dev), float(dt),
+                                        int(probe_steps), C.byref(a), C.byref(b), C.byref(c)),
+           "fire_autotune")
+    return a.value, b.value, c.value
+
+
+def fire_ensemble_autotune(ens, probe_steps, dt, wind_u_dev, wind_v_dev):
+    """Times candidate strip shapes of the persistent launch, keeps the
+    fastest; returns (strip_columns, strip_rows)."""
+    a, b = C.c_int(), C.c_int()
+    _check(load_library().fire_ensemble_autotune(ens, int(probe_steps), float(dt),
+                                                 _ptr_array(wind_u_dev), _ptr_array(wind_v_dev),
+                                                 C.byref(a), C.byref(b)),
+           "fire_ensemble_autotune")
+    return a.value, b.value
+
+
 def fire_destroy(ctx) -> None:
     if ctx:
         load_library().fire_destroy(ctx)
@@ -508,6 +535,9 @@ class FireModel:
 
     def status(self):
         return fire_status(self.ctx)
+
+    def autotune(self, u, v, dt, probe_steps=3):
+        return fire_autotune(self.ctx, u, v, dt, probe_steps)
 
     def set_mult(self, mult):
         """Per-node spread multiplier (None: 1)."""

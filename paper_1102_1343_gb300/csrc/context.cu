@@ -686,6 +686,111 @@ int fire_set_kernel(fire_ctx *c, int variant, int kx, int ky) {
     return configure_kernel(c, variant, kx, ky);
 }
 
+// Candidate step-kernel shapes timed on a scratch copy of the state: the
+// marching strip over widths of about 16..248 columns and heights of about
+// 8..512 rows, and the 2-D tile over a few shapes; the fastest average of
+// probe_steps launches (after one warm-up launch) is kept.
+int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int probe_steps,
+                  int *variant_out, int *kx_out, int *ky_out) {
+    if (!c || !u || !v || !finite_pos(dt) || probe_steps < 1) return FIRE_ERR_ARG;
+    const size_t N = c->n, E = c->esz;
+    const size_t na = (size_t)c->g.nx_atm * c->g.ny_atm;
+    // scratch: psi x2, F x2, tign, heat x2, times, status
+    const size_t o_psi = 0, o_F = o_psi + 2 * N * E, o_t = o_F + 2 * N * E;
+    const size_t o_h = o_t + N * sizeof(double), o_tm = o_h + 2 * na * sizeof(double);
+    const size_t bytes = o_tm + 4 * sizeof(double) + sizeof(int);
+    void *wsv = nullptr;
+    int r = wf::ctx_workspace(c, (bytes + 255) & ~(size_t)255, &wsv);
+    if (r) return r;
+    unsigned char *ws = static_cast<unsigned char *>(wsv);
+    void *sp[2] = {ws + o_psi, ws + o_psi + N * E};
+    void *sf[2] = {ws + o_F, ws + o_F + N * E};
+    double *stign = reinterpret_cast<double *>(ws + o_t);
+    double *shs = reinterpret_cast<double *>(ws + o_h), *shl = shs + na;
+    double *stm = reinterpret_cast<double *>(ws + o_tm);
+    int *sst = reinterpret_cast<int *>(ws + o_tm + 4 * sizeof(double));
+
+    struct Cand {
+        int variant, kx, ky;
+    };
+    std::vector<Cand> cands;
+    const int srx = c->g.sr_x, sry = c->g.sr_y, nxa = c->g.nx_atm, nya = c->g.ny_atm;
+    auto add = [&](int variant, int kx, int ky) {
+        kx = kx < 1 ? 1 : (kx > nxa ? nxa : kx);
+        ky = ky < 1 ? 1 : (ky > nya ? nya : ky);
+        if (variant == FIRE_KERNEL_MARCH && ((kx * srx) & 1)) {
+            if (kx > 1) --kx;
+            else if (2 <= nxa) kx = 2;
+            else return;
+        }
+        for (const Cand &q : cands)
+            if (q.variant == variant && q.kx == kx && q.ky == ky) return;
+        cands.push_back(Cand{variant, kx, ky});
+    };
+    if (srx <= kMarchMaxColumns / 2) {
+        const int widths[] = {16, 24, 32, 48, 64, 96, 128, 176, 248};
+        const int heights[] = {8, 16, 32, 64, 128, 256, 512};
+        for (int W : widths) {
+            if (W / srx * srx > kMarchMaxColumns) continue;
+            for (int L : heights) add(FIRE_KERNEL_MARCH, W / srx, L / sry);
+        }
+    }
+    {
+        const int widths[] = {32, 64, 128};
+        const int heights[] = {8, 16, 32, 64};
+        for (int W : widths)
+            for (int L : heights) add(FIRE_KERNEL_TILE, W / srx, L / sry);
+    }
+    const int save_variant = c->variant, save_kx = c->kx, save_ky = c->ky;
+    cudaEvent_t e0, e1;
+    WF_CHECK(cudaEventCreate(&e0));
+    WF_CHECK(cudaEventCreate(&e1));
+    float best = 0.f;
+    Cand win{save_variant, save_kx, save_ky};
+    bool found = false;
+    for (const Cand &q : cands) {
+        if (configure_kernel(c, q.variant, q.kx, q.ky) != FIRE_OK) continue;
+        // the same starting state for every candidate
+        WF_CHECK(cudaMemcpyAsync(sp[0], c->psi[c->cur], N * E, cudaMemcpyDeviceToDevice, c->stream));
+        WF_CHECK(cudaMemcpyAsync(sf[0], c->frac[c->cur], N * E, cudaMemcpyDeviceToDevice, c->stream));
+        WF_CHECK(cudaMemcpyAsync(stign, c->tign, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        WF_CHECK(cudaMemcpyAsync(stm, c->tdev + c->cur, sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        StepArgs a;
+        step_kernel_args(c, u, v, dt, shs, shl, a);
+        a.tign = stign;
+        a.status = sst;
+        for (int k = 0; k <= probe_steps; ++k) {
+            if (k == 1) WF_CHECK(cudaEventRecord(e0, c->stream));
+            a.psi_in = sp[k & 1];
+            a.psi_out = sp[(k + 1) & 1];
+            a.F_in = sf[k & 1];
+            a.F_out = sf[(k + 1) & 1];
+            a.t_in = stm + (k & 1);
+            a.t_out = stm + ((k + 1) & 1);
+            WF_CHECK(launch_variant(c, a, c->stream));
+        }
+        WF_CHECK(cudaEventRecord(e1, c->stream));
+        WF_CHECK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        WF_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+        if (!found || ms < best) {
+            best = ms;
+            win = q;
+            found = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    r = configure_kernel(c, win.variant, win.kx, win.ky);
+    if (r) return r;
+    if (variant_out) *variant_out = win.variant;
+    if (kx_out) *kx_out = win.kx;
+    if (ky_out) *ky_out = win.ky;
+    return FIRE_OK;
+}
+
 int fire_get_kernel(const fire_ctx *c, int *variant, int *kx, int *ky) {
     if (!c) return FIRE_ERR_ARG;
     if (variant) *variant = c->variant;

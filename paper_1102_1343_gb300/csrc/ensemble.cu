@@ -145,6 +145,7 @@ int ctx_info(const fire_ctx *c, int *prec, int *variant, int *nx, int *ny, int *
 int ctx_advance(fire_ctx *c, int nsteps, double dt);
 bool ctx_ignition_active(fire_ctx *c, double t);
 cudaStream_t ctx_stream(const fire_ctx *c);
+int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
 }  // namespace wf
 
 struct fire_ensemble {
@@ -480,6 +481,97 @@ int fire_ensemble_set_kernel(fire_ensemble *e, int strip_columns, int strip_rows
         if (r) return r;
     }
     return ens_plan(e);
+}
+
+// Times strip shapes (columns x rows of fire nodes) of the persistent
+// launch: every candidate starts from the members' saved states, runs one
+// untimed call (which also captures its graph) and one timed call of
+// probe_steps steps; the fastest is kept and the states are put back.
+int fire_ensemble_autotune(fire_ensemble *e, int probe_steps, double dt,
+                           const void *const *wind_u_dev, const void *const *wind_v_dev,
+                           int *strip_columns, int *strip_rows) {
+    if (!e || probe_steps < 1 || !isfinite(dt) || !(dt > 0) || !wind_u_dev || !wind_v_dev)
+        return FIRE_ERR_ARG;
+    // the probe must not cross an ignition window (it would apply it)
+    std::vector<double> t0(e->n);
+    for (int m = 0; m < e->n; ++m) {
+        int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+        ctx_info(e->members[m], &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur,
+                 &t0[m]);
+        double t = t0[m];
+        for (int k = 0; k <= 2 * probe_steps; ++k) {
+            if (ctx_ignition_active(e->members[m], t)) return FIRE_ERR_STATE;
+            t = t + dt;
+        }
+    }
+    // save the states in the members' workspaces
+    const size_t E = e->prec == FIRE_FP64 ? 8 : 4;
+    std::vector<unsigned char *> saved(e->n);
+    std::vector<size_t> nn(e->n);
+    for (int m = 0; m < e->n; ++m) {
+        int nx = 0, ny = 0;
+        fire_mesh_size(e->members[m], &nx, &ny);
+        nn[m] = (size_t)nx * ny;
+        void *w = nullptr;
+        int r = ctx_workspace(e->members[m], nn[m] * (2 * E + sizeof(double)), &w);
+        if (r) return r;
+        saved[m] = static_cast<unsigned char *>(w);
+        r = fire_get_state(e->members[m], saved[m], reinterpret_cast<double *>(saved[m] + 2 * nn[m] * E),
+                           saved[m] + nn[m] * E, nullptr);
+        if (r) return r;
+    }
+    auto restore = [&]() {
+        for (int m = 0; m < e->n; ++m) {
+            int r = fire_set_state(e->members[m], saved[m],
+                                   reinterpret_cast<double *>(saved[m] + 2 * nn[m] * E),
+                                   saved[m] + nn[m] * E, t0[m]);
+            if (r) return r;
+        }
+        return (int)FIRE_OK;
+    };
+    const int cols[] = {40, 80, 120, 160, 200, 240};
+    const int rows[] = {20, 40, 80, 160, 320};
+    cudaEvent_t a, b;
+    ENS_CHECK(cudaEventCreate(&a));
+    ENS_CHECK(cudaEventCreate(&b));
+    float best = 0.f;
+    int bc = 0, br = 0;
+    int r = FIRE_OK;
+    for (int C : cols) {
+        for (int R : rows) {
+            if (fire_ensemble_set_kernel(e, C, R) != FIRE_OK) continue;
+            if ((r = restore())) break;
+            if ((r = fire_ensemble_step(e, probe_steps, dt, wind_u_dev, wind_v_dev, nullptr,
+                                        nullptr)))
+                break;
+            if ((r = restore())) break;
+            if ((r = ens_cuda(cudaEventRecord(a, e->stream)))) break;
+            if ((r = fire_ensemble_step(e, probe_steps, dt, wind_u_dev, wind_v_dev, nullptr,
+                                        nullptr)))
+                break;
+            if ((r = ens_cuda(cudaEventRecord(b, e->stream)))) break;
+            if ((r = ens_cuda(cudaEventSynchronize(b)))) break;
+            float ms = 0.f;
+            if ((r = ens_cuda(cudaEventElapsedTime(&ms, a, b)))) break;
+            if (bc == 0 || ms < best) {
+                best = ms;
+                bc = C;
+                br = R;
+            }
+        }
+        if (r) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (r) return r;
+    if (bc == 0) return FIRE_ERR_ARG;
+    r = fire_ensemble_set_kernel(e, bc, br);
+    if (r) return r;
+    r = restore();
+    if (r) return r;
+    if (strip_columns) *strip_columns = bc;
+    if (strip_rows) *strip_rows = br;
+    return FIRE_OK;
 }
 
 int fire_ensemble_get_kernel(const fire_ensemble *e, int *grid_ctas, int *work_items) {
