@@ -310,9 +310,10 @@ struct MarchStrip {
                 const T2 f1v = sm.SF[s1 * NT + c];
                 const bool own_row = r >= y0 && r < y0 + La;
                 T2 PN, DL;
+                bool need[2] = {false, false};
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    T pn = T(0), d = T(0);
+                    T pn = T(0);
                     if (m_s2[j]) {
                         int cls = j == 0 ? eb_cls0 : eb_cls1;
                         cls = cls > ncm1 ? ncm1 : cls;
@@ -321,26 +322,38 @@ struct MarchStrip {
                                                pick<T>(eb_un, j), pick<T>(eb_vn, j));
                         const T p0 = pick<T>(p0v, j);
                         pn = p0 + dt * (T(0.5) * pick<T>(f1v, j) + T(0.5) * F2);
-                        const bool own = own_row && m_out[j];
-                        const bool cross = p0 > T(0) && pn <= T(0);
-                        if (cross || pn < T(0)) {
-                            double ti = a.tign[g + j];
-                            if (cross && isinf(ti)) {
-                                const double q0 = (double)p0, q1 = (double)pn;
-                                ti = tstart + q0 * a.dt / (q0 - q1);
-                                if (own) a.tign[g + j] = ti;
-                            }
-                            if (pn < T(0)) d = T(t1 - ti);
-                        }
-                        if (own) {
+                        need[j] = pn <= T(0);  // a crossing, or burning
+                        if (own_row && m_out[j]) {
                             if (!finite_val(pn)) st |= ST_NONFINITE;
                             const int x = xa + j;
                             const bool edge = x < band || r < band || x >= nx - band || r >= ny - band;
                             if (edge && pn < T(0)) st |= ST_BOUNDARY;
                         }
                     }
-                    if (j == 0) { PN.x = pn; DL.x = d; }
-                    else { PN.y = pn; DL.y = d; }
+                    if (j == 0) PN.x = pn;
+                    else PN.y = pn;
+                }
+                DL.x = DL.y = T(0);
+                // ignition time and t - t_i (double arithmetic) only in warps
+                // that have a crossing or burning node: elsewhere the FP64
+                // pipe is not touched at all
+                if (__any_sync(__activemask(), need[0] || need[1])) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        if (!need[j]) continue;
+                        const T p0 = pick<T>(p0v, j), pn = pick<T>(PN, j);
+                        const bool cross = p0 > T(0);
+                        double ti = a.tign[g + j];
+                        if (cross && isinf(ti)) {
+                            const double q0 = (double)p0, q1 = (double)pn;
+                            ti = tstart + q0 * a.dt / (q0 - q1);
+                            if (own_row && m_out[j]) a.tign[g + j] = ti;
+                        }
+                        if (pn < T(0)) {
+                            if (j == 0) DL.x = T(t1 - ti);
+                            else DL.y = T(t1 - ti);
+                        }
+                    }
                 }
                 sm.SQ[s1 * NT + c] = PN;
                 sm.SD[s1 * NT + c] = DL;
@@ -481,16 +494,17 @@ struct MarchStrip {
             const int kxa = Wa / srx;
             if (c < kxa) {
                 const T *hb = sm.HB + bpar * 4 * NT;
-                double h0 = 0.0, h1 = 0.0;
+                // the cell's column sums in the path precision, one
+                // conversion to double per atmospheric cell
+                T h0 = T(0), h1 = T(0);
                 for (int e = 0; e < srx; ++e) {
                     const int lc = kMarchHalo + c * srx + e;
-                    const T v0 = hb[lc], v1 = hb[2 * NT + lc];
-                    if (v0 != T(0)) h0 += (double)v0;
-                    if (v1 != T(0)) h1 += (double)v1;
+                    h0 += hb[lc];
+                    h1 += hb[2 * NT + lc];
                 }
                 const size_t ga = (size_t)(rd / sry) * nxa + (x0 / srx + c);
-                if (a.heat_s) a.heat_s[ga] = h0 * hscale;
-                if (a.heat_l) a.heat_l[ga] = h1 * hscale;
+                if (a.heat_s) a.heat_s[ga] = (double)h0 * hscale;
+                if (a.heat_l) a.heat_l[ga] = (double)h1 * hscale;
             }
             bpar ^= 1;
         }
