@@ -244,9 +244,12 @@ double fire_time(const fire_ctx *ctx);
  *                      kx*sr_x columns (an even number <= 248) and ky*sr_y
  *                      rows;
  *   FIRE_KERNEL_TILE   a 2-D tile of kx*sr_x by ky*sr_y nodes staged with
- *                      a 3-node halo in shared memory (any refinement).
+ *                      a 3-node halo in shared memory (any refinement);
+ *   FIRE_KERNEL_WARP   each warp marches alone down a strip of kx*sr_x
+ *                      columns (an even number <= 60) and ky*sr_y rows, rows
+ *                      held in registers, neighbours exchanged by shuffles.
  * FIRE_ERR_ARG if the shape does not fit the variant or the device. */
-enum fire_kernel_variant { FIRE_KERNEL_TILE = 0, FIRE_KERNEL_MARCH = 1 };
+enum fire_kernel_variant { FIRE_KERNEL_TILE = 0, FIRE_KERNEL_MARCH = 1, FIRE_KERNEL_WARP = 2 };
 int fire_set_kernel(fire_ctx *ctx, int variant, int kx, int ky);
 int fire_get_kernel(const fire_ctx *ctx, int *variant, int *kx, int *ky);
 

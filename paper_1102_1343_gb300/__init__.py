@@ -33,6 +33,7 @@ FIRE_ERR_TIMEOUT = -6
 FIRE_ERR_STATE = -7
 FIRE_KERNEL_TILE = 0
 FIRE_KERNEL_MARCH = 1
+FIRE_KERNEL_WARP = 2
 FIRE_MAX_CLASSES = 64
 FIRE_MAX_IGNITIONS = 256
 

@@ -617,8 +617,9 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
             ra.t_in = tdev + s;
             ra.t_out = tdev + nsteps + 1;
             ra.dt = dt;
-            cudaError_t e = variant == FIRE_KERNEL_MARCH ? launch_march<T>(ra, st)
-                                                         : launch_step<T>(ra, st);
+            cudaError_t e = variant == FIRE_KERNEL_MARCH  ? launch_march<T>(ra, st)
+                            : variant == FIRE_KERNEL_WARP ? launch_warp<T>(ra, st)
+                                                          : launch_step<T>(ra, st);
             ADJ_CHECK(e);
         }
         for (int s = s1 - 1; s >= s0; --s) {

@@ -152,6 +152,8 @@ int step_kernel_args(fire_ctx *c, const void *u, const void *v, double dt, doubl
 cudaError_t launch_variant(const fire_ctx *c, const StepArgs &a, cudaStream_t s) {
     if (c->variant == FIRE_KERNEL_MARCH)
         return c->prec == FIRE_FP64 ? launch_march<double>(a, s) : launch_march<float>(a, s);
+    if (c->variant == FIRE_KERNEL_WARP)
+        return c->prec == FIRE_FP64 ? launch_warp<double>(a, s) : launch_warp<float>(a, s);
     return c->prec == FIRE_FP64 ? launch_step<double>(a, s) : launch_step<float>(a, s);
 }
 
@@ -220,6 +222,11 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
                                   : march_smem_bytes<float>(ky, c->g.sr_y, c->ncls);
         if (sm > c->smem_max) return FIRE_ERR_ARG;
         e = c->prec == FIRE_FP64 ? prepare_march_kernel<double>(sm) : prepare_march_kernel<float>(sm);
+    } else if (variant == FIRE_KERNEL_WARP) {
+        const long long W = (long long)kx * c->g.sr_x;
+        if (W > kWarpMaxColumns || (W & 1)) return FIRE_ERR_ARG;
+        sm = 0;
+        e = cudaSuccess;
     } else if (variant == FIRE_KERNEL_TILE) {
         sm = c->prec == FIRE_FP64 ? step_smem_bytes<double>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls)
                                   : step_smem_bytes<float>(kx, ky, c->g.sr_x, c->g.sr_y, c->ncls);
@@ -718,7 +725,7 @@ int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int prob
     auto add = [&](int variant, int kx, int ky) {
         kx = kx < 1 ? 1 : (kx > nxa ? nxa : kx);
         ky = ky < 1 ? 1 : (ky > nya ? nya : ky);
-        if (variant == FIRE_KERNEL_MARCH && ((kx * srx) & 1)) {
+        if (variant != FIRE_KERNEL_TILE && ((kx * srx) & 1)) {
             if (kx > 1) --kx;
             else if (2 <= nxa) kx = 2;
             else return;
@@ -733,6 +740,14 @@ int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int prob
         for (int W : widths) {
             if (W / srx * srx > kMarchMaxColumns) continue;
             for (int L : heights) add(FIRE_KERNEL_MARCH, W / srx, L / sry);
+        }
+    }
+    if (srx <= kWarpMaxColumns / 2) {
+        const int widths[] = {20, 30, 40, 50, 60};
+        const int heights[] = {16, 32, 64, 128, 256, 512};
+        for (int W : widths) {
+            if (W / srx * srx > kWarpMaxColumns || W / srx < 1) continue;
+            for (int L : heights) add(FIRE_KERNEL_WARP, W / srx, L / sry);
         }
     }
     {

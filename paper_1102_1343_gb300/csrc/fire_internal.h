@@ -86,6 +86,11 @@ cudaError_t prepare_march_kernel(size_t smem_bytes);
 
 constexpr int kMarchMaxColumns = 248;  // output columns of one marching strip (even)
 
+template <typename T>
+cudaError_t launch_warp(const StepArgs &a, cudaStream_t s);
+
+constexpr int kWarpMaxColumns = 60;  // output columns of one warp strip (even)
+
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s);
 // d(coefficients)/d(M_f) per class at the class moisture (forward-mode dual

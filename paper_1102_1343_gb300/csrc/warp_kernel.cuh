@@ -1,0 +1,646 @@
+// Warp-marching fire-step kernel: the whole step of Sect. 5 (items 2-6) in
+// one pass over the state, each warp marching down its own strip with the
+// rows it needs in registers.
+//
+// A warp owns W <= 60 output columns (W = kx*srx, even) and L = ky*sry
+// output rows; lane l holds the two columns x0 - 2 + 2l and x0 - 1 + 2l, so
+// the warp computes 64 columns: the strip, two halo columns on the left and
+// up to two on the right (the outermost of them are garbage nobody reads).
+// Horizontal neighbours come from the adjacent lane by shuffle, vertical
+// ones from the rows the lane keeps in registers; nothing goes through
+// shared memory and warps never wait for one another.  Per row (iteration
+// k) the stages lag behind the loads:
+//   B  stage 1 (eq. Heun, first line) on row k+1
+//   C  stage 2 (eq. Heun, second line), ignition-time crossing
+//      (eq. set-ignition-time) and t - t_i on row k
+//   D  fuel-fraction quadrature (Sect. 3.3) and heat flux
+//      (eqs. sensible-/latent-heat-flux) on row k-1
+// The two columns of a lane are one float2 and the FP32 arithmetic of the
+// right-hand side uses the packed f32x2 instructions.  The quadrature, the
+// ignition-time arithmetic (double) and the domain-boundary ghosts
+// (Sect. 3.1) run only in warps that need them (warp votes / uniform
+// branches).  Heat is summed per column over each band of sry rows, then per
+// atmospheric cell (Sect. 5, item 6) through a small per-warp buffer.
+#pragma once
+
+#include <mutex>
+
+#include "fire_device.cuh"
+#include "fire_internal.h"
+
+namespace wf {
+
+constexpr int kWarpStrips = 4;  // warps (strips) per CTA
+constexpr int kWarpCtaThreads = 32 * kWarpStrips;
+
+template <typename T>
+struct WOcc {
+    static constexpr int blocks = 3;
+};
+template <>
+struct WOcc<double> {
+    static constexpr int blocks = 1;
+};
+
+// ---------------------------------------------------------------------------
+// pairs of values (the two columns of a lane)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PairT;
+template <>
+struct PairT<float> {
+    using t = float2;
+};
+template <>
+struct PairT<double> {
+    using t = double2;
+};
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename V, typename T>
+__device__ __forceinline__ V splat(T v) {
+    return mk2(v, v);
+}
+
+__device__ __forceinline__ float max_val(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_val(double a, double b) { return fmax(a, b); }
+
+// per-lane coefficients of eq. (spread-WRF-Fire) for the two columns
+template <typename T>
+struct WCoef {
+    using V = typename PairT<T>::t;
+    V S0, R0, b, c, d, e;
+};
+
+template <typename T>
+struct WEnv {  // what stage 2 reuses from stage 1 of the same row
+    using V = typename PairT<T>::t;
+    int cls0, cls1;
+    V zx, zy, m, un, vn;
+};
+
+// Right-hand side of eq. (F-disc) for the two columns of a lane (the
+// arithmetic of rhs_vals on pairs).
+template <typename T>
+__device__ __forceinline__ typename PairT<T>::t rhs2(
+    typename PairT<T>::t p, typename PairT<T>::t pl, typename PairT<T>::t pr,
+    typename PairT<T>::t pd, typename PairT<T>::t pu, typename PairT<T>::t idx2,
+    typename PairT<T>::t idy2, typename PairT<T>::t i2dx2, typename PairT<T>::t i2dy2,
+    typename PairT<T>::t eps2, const WCoef<T> &co, const WEnv<T> &e) {
+    using V = typename PairT<T>::t;
+    const V dxm = mul2(sub2(p, pl), idx2), dxp = mul2(sub2(pr, p), idx2);
+    const V dym = mul2(sub2(p, pd), idy2), dyp = mul2(sub2(pu, p), idy2);
+    // Godunov (eq. Godunov): |D| = max(D-, -D+, 0) per direction
+    V gx, gy;
+    gx.x = max_val(max_val(dxm.x, -dxp.x), T(0));
+    gx.y = max_val(max_val(dxm.y, -dxp.y), T(0));
+    gy.x = max_val(max_val(dym.x, -dyp.x), T(0));
+    gy.y = max_val(max_val(dym.y, -dyp.y), T(0));
+    const V g2 = fma2(gx, gx, mul2(gy, gy));
+    // central differences, zeroed at the rounding level of their values
+    V ddx = sub2(pr, pl), ddy = sub2(pu, pd);
+    const T z = Mth<T>::kGradZero;
+    ddx.x = abs_val(ddx.x) <= z * (abs_val(pr.x) + abs_val(pl.x)) ? T(0) : ddx.x;
+    ddx.y = abs_val(ddx.y) <= z * (abs_val(pr.y) + abs_val(pl.y)) ? T(0) : ddx.y;
+    ddy.x = abs_val(ddy.x) <= z * (abs_val(pu.x) + abs_val(pd.x)) ? T(0) : ddy.x;
+    ddy.y = abs_val(ddy.y) <= z * (abs_val(pu.y) + abs_val(pd.y)) ? T(0) : ddy.y;
+    const V cx = mul2(ddx, i2dx2), cy = mul2(ddy, i2dy2);
+    V nxv, nyv;
+    Mth<T>::unit(cx.x, cy.x, nxv.x, nyv.x);
+    Mth<T>::unit(cx.y, cy.y, nxv.y, nyv.y);
+    const V U = fma2(e.un, nxv, mul2(e.vn, nyv));
+    const V tp = fma2(e.zx, nxv, mul2(e.zy, nyv));
+    // spread rate, eq. (spread-WRF-Fire)
+    V Ue, tq, pw;
+    Ue.x = min_val(max_val(U.x, T(0)), co.e.x);
+    Ue.y = min_val(max_val(U.y, T(0)), co.e.y);
+    tq.x = max_val(tp.x, T(0));
+    tq.y = max_val(tp.y, T(0));
+    pw.x = Mth<T>::pw(Ue.x, co.b.x);
+    pw.y = Mth<T>::pw(Ue.y, co.b.y);
+    V s = fma2(mul2(co.d, tq), tq, fma2(co.c, pw, co.R0));
+    s.x = max_val(s.x, co.S0.x);
+    s.y = max_val(s.y, co.S0.y);
+    const V S = mul2(e.m, s);
+    const V lap = add2(sub2(dxp, dxm), sub2(dyp, dym));
+    V grad;
+    grad.x = Mth<T>::sqr(g2.x);
+    grad.y = Mth<T>::sqr(g2.y);
+    // -S |grad| + eps S Lap
+    return mul2(S, sub2(mul2(eps2, lap), grad));
+}
+
+template <typename T>
+struct WarpStrip {
+    using V = typename PairT<T>::t;
+    const StepArgs &a;
+    const T *lut;   // [ncls][8] S0 R0 b c d e Tf Hs
+    const T *lutq;  // [ncls] Hq
+    T *hw;          // [2][64] heat column sums of this warp
+    int lane, x0, y0, W, La, Wa, nx, ny, nxa, nya, srx, sry, ncm1, band;
+    int xa;          // global column of the lane's first column
+    bool vec;        // paired vector access (nx even)
+    bool inA, inB;   // columns inside the domain
+    bool outA, outB; // output columns of this warp
+    bool xedge;      // the strip touches the left or right domain boundary
+    bool bedge;      // the strip touches the boundary band in x
+    V idx2, idy2, i2dx2, i2dy2, eps2, dt2, hlf2;
+    double tstart, t1, hscale;
+    int st;
+    V poison;
+    // wind: x-interpolation per column, two atmos rows held per component
+    int iu0[2], iu1[2], iv0[2], iv1[2];
+    T wxu[2], wxv[2];
+    int ju_cur, jv_cur;
+    V UA, UB, VA, VB;
+    V acc_s, acc_q;
+
+    __device__ __forceinline__ WarpStrip(const StepArgs &args, const T *l, const T *lq, T *h)
+        : a(args), lut(l), lutq(lq), hw(h) {}
+
+    __device__ __forceinline__ V ld(const T *__restrict__ f, int r) const {
+        const size_t g = (size_t)r * nx + xa;
+        V v;
+        if (vec && inA && inB) {
+            v = *reinterpret_cast<const V *>(f + g);
+        } else {
+            v.x = inA ? f[g] : T(0);
+            v.y = inB ? f[g + 1] : T(0);
+        }
+        return v;
+    }
+
+    __device__ __forceinline__ void load_env(int r, WEnv<T> &e) const {
+        const size_t g = (size_t)r * nx + xa;
+        if (vec && inA && inB) {
+            const uint16_t f2 = *reinterpret_cast<const uint16_t *>(a.fuel + g);
+            e.cls0 = f2 & 0xff;
+            e.cls1 = f2 >> 8;
+        } else {
+            e.cls0 = inA ? a.fuel[g] : 0;
+            e.cls1 = inB ? a.fuel[g + 1] : 0;
+        }
+        e.cls0 = e.cls0 > ncm1 ? ncm1 : e.cls0;
+        e.cls1 = e.cls1 > ncm1 ? ncm1 : e.cls1;
+        e.zx = ld(static_cast<const T *>(a.dzdx), r);
+        e.zy = ld(static_cast<const T *>(a.dzdy), r);
+        e.m = a.mult ? ld(static_cast<const T *>(a.mult), r) : splat<V>(T(1));
+    }
+
+    __device__ __forceinline__ void coef(const WEnv<T> &e, WCoef<T> &co) const {
+        const T *l0 = lut + e.cls0 * 8, *l1 = lut + e.cls1 * 8;
+        if constexpr (sizeof(T) == 4) {
+            // two 16-byte shared loads per class record
+            const float4 a0 = *reinterpret_cast<const float4 *>(l0);
+            const float4 b0 = *reinterpret_cast<const float4 *>(l0 + 4);
+            const float4 a1 = *reinterpret_cast<const float4 *>(l1);
+            const float4 b1 = *reinterpret_cast<const float4 *>(l1 + 4);
+            co.S0 = mk2(a0.x, a1.x);
+            co.R0 = mk2(a0.y, a1.y);
+            co.b = mk2(a0.z, a1.z);
+            co.c = mk2(a0.w, a1.w);
+            co.d = mk2(b0.x, b1.x);
+            co.e = mk2(b0.y, b1.y);
+        } else {
+            co.S0 = mk2(l0[0], l1[0]);
+            co.R0 = mk2(l0[1], l1[1]);
+            co.b = mk2(l0[2], l1[2]);
+            co.c = mk2(l0[3], l1[3]);
+            co.d = mk2(l0[4], l1[4]);
+            co.e = mk2(l0[5], l1[5]);
+        }
+    }
+
+    // x-interpolated wind of atmos row J at this lane's columns
+    __device__ __forceinline__ V wind_u_row(int J) const {
+        const T *u = static_cast<const T *>(a.u) + (size_t)J * (nxa + 1);
+        return mk2((T(1) - wxu[0]) * __ldg(u + iu0[0]) + wxu[0] * __ldg(u + iu1[0]),
+                   (T(1) - wxu[1]) * __ldg(u + iu0[1]) + wxu[1] * __ldg(u + iu1[1]));
+    }
+    __device__ __forceinline__ V wind_v_row(int J) const {
+        const T *v = static_cast<const T *>(a.v) + (size_t)J * nxa;
+        return mk2((T(1) - wxv[0]) * __ldg(v + iv0[0]) + wxv[0] * __ldg(v + iv1[0]),
+                   (T(1) - wxv[1]) * __ldg(v + iv0[1]) + wxv[1] * __ldg(v + iv1[1]));
+    }
+
+    // bilinear wind at fire row r (Sect. 5), rows of the atmos wind cached
+    __device__ __forceinline__ void wind(int r, V &un, V &vn) {
+        const T yr = (T(r) + T(0.5)) / T(sry);
+        int ju0, ju1, jv0, jv1;
+        T wyu, wyv;
+        lin_idx<T>(yr - T(0.5), nya, ju0, ju1, wyu);
+        lin_idx<T>(yr, nya + 1, jv0, jv1, wyv);
+        if (ju0 != ju_cur) {
+            UA = wind_u_row(ju0);
+            UB = ju1 == ju0 ? UA : wind_u_row(ju1);
+            ju_cur = ju0;
+        }
+        if (jv0 != jv_cur) {
+            VA = wind_v_row(jv0);
+            VB = wind_v_row(jv1);
+            jv_cur = jv0;
+        }
+        un = mk2((T(1) - wyu) * UA.x + wyu * UB.x, (T(1) - wyu) * UA.y + wyu * UB.y);
+        vn = mk2((T(1) - wyv) * VA.x + wyv * VB.x, (T(1) - wyv) * VA.y + wyv * VB.y);
+    }
+
+    // horizontal neighbours of a row of pairs: left of .x, right of .y
+    __device__ __forceinline__ void sides(V v, T &l, T &r) const {
+        l = __shfl_up_sync(0xffffffffu, v.y, 1);
+        r = __shfl_down_sync(0xffffffffu, v.x, 1);
+    }
+
+    // 5-point values of the lane's two columns at row r from the rows below
+    // (d), at (c) and above (u), with the ghosts of Sect. 3.1 at the domain
+    // boundary; hl / hr replace the left / right neighbour of lanes 0 / 31
+    __device__ __forceinline__ void stencil(V d, V c, V u, int r, bool use_halo, T hl, T hr, V &L,
+                                            V &R, V &D, V &Uu) const {
+        T l, rr;
+        sides(c, l, rr);
+        if (use_halo) {
+            if (lane == 0) l = hl;
+            if (lane == 31) rr = hr;
+        }
+        L = mk2(l, c.x);
+        R = mk2(c.y, rr);
+        D = d;
+        Uu = u;
+        if (xedge) {
+            if (xa == 0) L.x = ghost_value<T>(c.x, c.y);
+            if (xa + 1 == nx - 1) R.y = ghost_value<T>(c.y, c.x);
+            if (xa == nx - 1) R.x = ghost_value<T>(c.x, L.x);
+        }
+        if (r == 0) D = mk2(ghost_value<T>(c.x, u.x), ghost_value<T>(c.y, u.y));
+        if (r == ny - 1) Uu = mk2(ghost_value<T>(c.x, d.x), ghost_value<T>(c.y, d.y));
+    }
+
+    __device__ __forceinline__ void run(int x0_, int y0_, double tstart_) {
+        lane = threadIdx.x & 31;
+        srx = a.srx;
+        sry = a.sry;
+        nx = a.nx;
+        ny = a.ny;
+        nxa = a.nxa;
+        nya = a.nya;
+        x0 = x0_;
+        y0 = y0_;
+        W = a.kx * srx;
+        La = min(a.ky * sry, ny - y0);
+        Wa = min(W, nx - x0);
+        xa = x0 - 2 + 2 * lane;
+        vec = (nx & 1) == 0;
+        inA = xa >= 0 && xa < nx;
+        inB = xa + 1 >= 0 && xa + 1 < nx;
+        outA = xa >= x0 && xa < x0 + Wa;
+        outB = xa + 1 >= x0 && xa + 1 < x0 + Wa;
+        xedge = x0 - 2 <= 0 || x0 + 62 >= nx - 1;
+        band = a.band;
+        bedge = x0 < band || x0 + Wa > nx - band;
+        ncm1 = a.ncls - 1;
+        idx2 = splat<V>(T(1) / T(a.dx));
+        idy2 = splat<V>(T(1) / T(a.dy));
+        i2dx2 = splat<V>(T(1) / (T(2) * T(a.dx)));
+        i2dy2 = splat<V>(T(1) / (T(2) * T(a.dy)));
+        eps2 = splat<V>(T(a.eps));
+        dt2 = splat<V>(T(a.dt));
+        hlf2 = splat<V>(T(0.5));
+        tstart = tstart_;
+        t1 = tstart + a.dt;
+        hscale = 1.0 / (a.dt * (double)srx * (double)sry);
+        st = 0;
+        poison = splat<V>(T(0));
+        acc_s = acc_q = splat<V>(T(0));
+        // x-weights of the wind
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int x = min(max(xa + j, 0), nx - 1);
+            const T xr = (T(x) + T(0.5)) / T(srx);
+            lin_idx<T>(xr, nxa + 1, iu0[j], iu1[j], wxu[j]);
+            lin_idx<T>(xr - T(0.5), nxa, iv0[j], iv1[j], wxv[j]);
+        }
+        ju_cur = jv_cur = -1;
+
+        const int kb = y0 - 3, ke = y0 + La;
+        // rows in registers (names by offset from the iteration's row k)
+        V P0 = splat<V>(T(0)), P1 = P0, P2 = P0, Ppre = P0;  // psi^n rows k, k+1, k+2, prefetch
+        T hl1 = T(0), hr1 = T(0), hl2 = T(0), hr2 = T(0), hlp = T(0), hrp = T(0);
+        V Qm = P0, Q0 = P0, Q1 = P0;       // psi* rows k-1, k, k+1
+        V FA0 = P0, FA1 = P0;              // F(psi^n) rows k, k+1
+        V Nm2 = P0, Nm1 = P0, N0 = P0;     // psi^{n+1} rows k-2, k-1, k
+        V Dm2 = P0, Dm1 = P0, D0 = P0;     // t - t_i rows k-2, k-1, k
+        V Fpre = splat<V>(T(1));           // F^n of row k-1
+        WEnv<T> envB, envC, envPre;
+        envB.cls0 = envB.cls1 = 0;
+        envB.zx = envB.zy = envB.un = envB.vn = P0;
+        envB.m = splat<V>(T(1));
+        envC = envB;
+        envPre = envB;
+        const T *psi_in = static_cast<const T *>(a.psi_in);
+        auto load_psi = [&](int r, V &v, T &hl, T &hr) {
+            if (r >= 0 && r < ny) {
+                v = ld(psi_in, r);
+                const size_t g = (size_t)r * nx;
+                if (lane == 0) hl = xa - 1 >= 0 ? psi_in[g + xa - 1] : T(0);
+                if (lane == 31) hr = xa + 2 < nx ? psi_in[g + xa + 2] : T(0);
+            }
+        };
+        load_psi(kb, P0, hl1, hr1);  // hl1/hr1 of row kb are not used
+        load_psi(kb + 1, P1, hl1, hr1);
+        load_psi(kb + 2, Ppre, hlp, hrp);
+        if (kb + 1 >= 0 && kb + 1 < ny) load_env(kb + 1, envPre);
+
+#pragma unroll 1
+        for (int k = kb; k <= ke; ++k) {
+            // ---- A: psi^n of row k+2 arrives; prefetch row k+3
+            P2 = Ppre;
+            hl2 = hlp;
+            hr2 = hrp;
+            if (k + 3 <= ke + 2) load_psi(k + 3, Ppre, hlp, hrp);
+            // ---- B: stage 1 on row k+1
+            const int rB = k + 1;
+            envB = envPre;
+            if (rB + 1 >= 0 && rB + 1 < ny && rB + 1 <= ke + 1) load_env(rB + 1, envPre);
+            if (rB >= 0 && rB < ny) {
+                wind(rB, envB.un, envB.vn);
+                poison = fma2(envB.un, splat<V>(T(0)), poison);
+                poison = fma2(envB.vn, splat<V>(T(0)), poison);
+                V L, R, D, U;
+                stencil(P0, P1, P2, rB, true, hl1, hr1, L, R, D, U);
+                WCoef<T> co;
+                coef(envB, co);
+                FA1 = rhs2<T>(P1, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, envB);
+                Q1 = fma2(dt2, FA1, P1);
+            }
+            // ---- C: stage 2, crossing and t - t_i on row k
+            const int rC = k;
+            if (rC >= y0 - 1 && rC >= 0 && rC < ny) {
+                V L, R, D, U;
+                stencil(Qm, Q0, Q1, rC, false, T(0), T(0), L, R, D, U);
+                WCoef<T> co;
+                coef(envC, co);
+                const V F2 = rhs2<T>(Q0, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, envC);
+                N0 = fma2(dt2, fma2(hlf2, FA0, mul2(hlf2, F2)), P0);
+                const bool own_row = rC >= y0 && rC < y0 + La;
+                if (own_row) {
+                    if (outA) poison.x = fma(N0.x, T(0), poison.x);
+                    if (outB) poison.y = fma(N0.y, T(0), poison.y);
+                    if (bedge || rC < band || rC >= ny - band) {
+                        const bool ea = xa < band || xa >= nx - band || rC < band || rC >= ny - band;
+                        const bool eb = xa + 1 < band || xa + 1 >= nx - band || rC < band ||
+                                        rC >= ny - band;
+                        if ((outA && ea && N0.x < T(0)) || (outB && eb && N0.y < T(0)))
+                            st |= ST_BOUNDARY;
+                    }
+                }
+                // ignition time and t - t_i, only where a node is burning
+                const bool na = inA && lane > 0 && N0.x <= T(0);
+                const bool nb = inB && lane < 31 && N0.y <= T(0);
+                D0 = splat<V>(T(0));
+                if (__any_sync(0xffffffffu, na || nb)) {
+                    const size_t g = (size_t)rC * nx + xa;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        if (!(j == 0 ? na : nb)) continue;
+                        const T p0 = j == 0 ? P0.x : P0.y, pn = j == 0 ? N0.x : N0.y;
+                        double ti = a.tign[g + j];
+                        if (p0 > T(0) && isinf(ti)) {
+                            const double q0 = (double)p0, q1 = (double)pn;
+                            ti = tstart + q0 * a.dt / (q0 - q1);
+                            if (own_row && (j == 0 ? outA : outB)) a.tign[g + j] = ti;
+                        }
+                        if (pn < T(0)) {
+                            if (j == 0) D0.x = T(t1 - ti);
+                            else D0.y = T(t1 - ti);
+                        }
+                    }
+                }
+                if (own_row) {
+                    T *po = static_cast<T *>(a.psi_out);
+                    const size_t g = (size_t)rC * nx + xa;
+                    if (vec && outA && outB) {
+                        *reinterpret_cast<V *>(po + g) = N0;
+                    } else {
+                        if (outA) po[g] = N0.x;
+                        if (outB) po[g + 1] = N0.y;
+                    }
+                }
+            }
+            // ---- D: fuel fraction and heat on row k-1
+            const int rD = k - 1;
+            if (rD >= y0 && rD < y0 + La) {
+                quadrature(rD, Nm2, Nm1, N0, Dm2, Dm1, D0, Fpre);
+            }
+            // F^n of row k for the next iteration's quadrature
+            if (k >= y0 && k < y0 + La) Fpre = ld(static_cast<const T *>(a.F_in), k);
+            // ---- rotate
+            P0 = P1;
+            P1 = P2;
+            hl1 = hl2;
+            hr1 = hr2;
+            Qm = Q0;
+            Q0 = Q1;
+            FA0 = FA1;
+            Nm2 = Nm1;
+            Nm1 = N0;
+            Dm2 = Dm1;
+            Dm1 = D0;
+            envC = envB;
+        }
+        if (!finite_val(poison.x) || !finite_val(poison.y)) st |= ST_NONFINITE;
+    }
+
+    __device__ __forceinline__ void quadrature(int rD, V Na, V Nb, V Nc, V Da, V Db, V Dc, V Fn) {
+        // minimum of psi^{n+1} over the 3x3 neighbourhood of each output
+        // column (in-domain values only; ghosts are never below them)
+        const T big = T(1e30);
+        T va = min_val(min_val(Na.x, Nb.x), Nc.x), vb = min_val(min_val(Na.y, Nb.y), Nc.y);
+        if (rD == 0) {
+            va = min_val(Nb.x, Nc.x);
+            vb = min_val(Nb.y, Nc.y);
+        } else if (rD == ny - 1) {
+            va = min_val(Na.x, Nb.x);
+            vb = min_val(Na.y, Nb.y);
+        }
+        va = inA ? va : big;
+        vb = inB ? vb : big;
+        T vl, vr;
+        sides(mk2(va, vb), vl, vr);
+        const T ma = min_val(min_val(vl, va), vb), mb = min_val(min_val(va, vb), vr);
+        const bool ba = outA && ma < T(0), bb = outB && mb < T(0);
+        V F1 = splat<V>(T(1));
+        if (__any_sync(0xffffffffu, ba || bb)) {
+            // full quadrature: neighbours of three rows of psi and t - t_i
+            T pl[3], pr[3], dl[3], dr[3];
+            sides(Na, pl[0], pr[0]);
+            sides(Nb, pl[1], pr[1]);
+            sides(Nc, pl[2], pr[2]);
+            sides(Da, dl[0], dr[0]);
+            sides(Db, dl[1], dr[1]);
+            sides(Dc, dl[2], dr[2]);
+            const V Nr[3] = {Na, Nb, Nc}, Dr[3] = {Da, Db, Dc};
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (!(j == 0 ? ba : bb)) continue;
+                T q[3][3], e[3][3];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (j == 0) {
+                        q[b][0] = pl[b];
+                        q[b][1] = Nr[b].x;
+                        q[b][2] = Nr[b].y;
+                        e[b][0] = dl[b];
+                        e[b][1] = Dr[b].x;
+                        e[b][2] = Dr[b].y;
+                    } else {
+                        q[b][0] = Nr[b].x;
+                        q[b][1] = Nr[b].y;
+                        q[b][2] = pr[b];
+                        e[b][0] = Dr[b].x;
+                        e[b][1] = Dr[b].y;
+                        e[b][2] = dr[b];
+                    }
+                }
+                const int x = xa + j;
+                if (x == 0 || x == nx - 1 || rD == 0 || rD == ny - 1) {
+                    // ghost ring of psi^{n+1} (x first, then y) and of t - t_i
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const int yy = rD + b - 1;
+                        if (yy < 0 || yy >= ny) continue;
+                        if (x == 0) {
+                            q[b][0] = ghost_value<T>(q[b][1], q[b][2]);
+                            e[b][0] = q[b][0] >= T(0) ? T(0) : e[b][1];
+                        }
+                        if (x == nx - 1) {
+                            q[b][2] = ghost_value<T>(q[b][1], q[b][0]);
+                            e[b][2] = q[b][2] >= T(0) ? T(0) : e[b][1];
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < 3; ++h) {
+                        if (rD == 0) {
+                            q[0][h] = ghost_value<T>(q[1][h], q[2][h]);
+                            e[0][h] = q[0][h] >= T(0) ? T(0) : e[1][h];
+                        }
+                        if (rD == ny - 1) {
+                            q[2][h] = ghost_value<T>(q[1][h], q[0][h]);
+                            e[2][h] = q[2][h] >= T(0) ? T(0) : e[1][h];
+                        }
+                    }
+                }
+                const int cls0 = a.fuel[(size_t)rD * nx + x];
+                const int cls = cls0 > ncm1 ? ncm1 : cls0;
+                const T f = cell_fraction_vals<T>(q[0][0], q[0][1], q[0][2], q[1][0], q[1][1],
+                                                  q[1][2], q[2][0], q[2][1], q[2][2], e[0][0],
+                                                  e[0][1], e[0][2], e[1][0], e[1][1], e[1][2],
+                                                  e[2][0], e[2][1], e[2][2], lut[cls * 8 + 6]);
+                if (j == 0) F1.x = f;
+                else F1.y = f;
+            }
+        }
+        const size_t g = (size_t)rD * nx + xa;
+        T *fo = static_cast<T *>(a.F_out);
+        if (vec && outA && outB) {
+            *reinterpret_cast<V *>(fo + g) = F1;
+        } else {
+            if (outA) fo[g] = F1.x;
+            if (outB) fo[g + 1] = F1.y;
+        }
+        // heat flux densities of the row, summed per column over the band
+        const T dFa = outA ? Fn.x - F1.x : T(0), dFb = outB ? Fn.y - F1.y : T(0);
+        if (__any_sync(0xffffffffu, dFa != T(0) || dFb != T(0))) {
+            if (dFa != T(0)) {
+                int cls = a.fuel[g];
+                cls = cls > ncm1 ? ncm1 : cls;
+                acc_s.x += dFa * lut[cls * 8 + 7];
+                acc_q.x += dFa * lutq[cls];
+            }
+            if (dFb != T(0)) {
+                int cls = a.fuel[g + 1];
+                cls = cls > ncm1 ? ncm1 : cls;
+                acc_s.y += dFb * lut[cls * 8 + 7];
+                acc_q.y += dFb * lutq[cls];
+            }
+        }
+        // after the last row of an atmospheric band: average per cell
+        if ((rD + 1) % sry == 0 || rD == y0 + La - 1) {
+            hw[2 * lane] = acc_s.x;
+            hw[2 * lane + 1] = acc_s.y;
+            hw[64 + 2 * lane] = acc_q.x;
+            hw[64 + 2 * lane + 1] = acc_q.y;
+            __syncwarp();
+            const int cells = Wa / srx;
+            if (lane < cells) {
+                T h0 = T(0), h1 = T(0);
+                for (int e = 0; e < srx; ++e) {
+                    const int lc = 2 + lane * srx + e;
+                    h0 += hw[lc];
+                    h1 += hw[64 + lc];
+                }
+                const size_t ga = (size_t)(rD / sry) * nxa + (x0 / srx + lane);
+                if (a.heat_s) a.heat_s[ga] = (double)h0 * hscale;
+                if (a.heat_l) a.heat_l[ga] = (double)h1 * hscale;
+            }
+            __syncwarp();
+            acc_s = acc_q = splat<V>(T(0));
+        }
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(const StepArgs a) {
+    __shared__ __align__(16) T lut[FIRE_MAX_CLASSES * 8];
+    __shared__ T lutq[FIRE_MAX_CLASSES];
+    __shared__ __align__(16) T hw[kWarpStrips][128];
+    for (int k = threadIdx.x; k < a.ncls; k += kWarpCtaThreads) {
+        const double *co = a.coef + (size_t)k * K_N;
+        T *l = lut + k * 8;
+        l[0] = T(co[K_S0]);
+        l[1] = T(co[K_R0]);
+        l[2] = T(co[K_B]);
+        l[3] = T(co[K_C]);
+        l[4] = T(co[K_D]);
+        l[5] = T(co[K_E]);
+        l[6] = T(co[K_TF]);
+        l[7] = T(co[K_HS]);
+        lutq[k] = T(co[K_HQ]);
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    const double tstart = *a.t_in;
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) *a.t_out = tstart + a.dt;
+    const int W = a.kx * a.srx;
+    const int x0 = (blockIdx.x * kWarpStrips + w) * W;
+    if (x0 >= a.nx) return;  // whole warp
+    WarpStrip<T> s(a, lut, lutq, hw[w]);
+    s.run(x0, blockIdx.y * a.ky * a.sry, tstart);
+    const int stw = __reduce_or_sync(0xffffffffu, s.st);
+    if ((threadIdx.x & 31) == 0 && stw) atomicOr(a.status, stw);
+}
+
+template <typename T>
+cudaError_t launch_warp(const StepArgs &a, cudaStream_t s) {
+    const int W = a.kx * a.srx, L = a.ky * a.sry;
+    if (W > 60 || (W & 1) || W < 2) return cudaErrorInvalidValue;
+    const int strips = (a.nx + W - 1) / W;
+    dim3 grid((strips + kWarpStrips - 1) / kWarpStrips, (a.ny + L - 1) / L);
+    k_fire_warp<T><<<grid, kWarpCtaThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define WF_INSTANTIATE_WARP(T) template cudaError_t launch_warp<T>(const StepArgs &, cudaStream_t);
+
+}  // namespace wf

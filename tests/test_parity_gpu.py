@@ -70,11 +70,11 @@ def test_fp64_plain_circle(pkg):
 
 
 @pytest.mark.parametrize("tile", [None, (1, 1, 1), (1, 7, 3), (1, 12, 17), (0, 1, 1), (0, 3, 2),
-                                  (0, 5, 3)])
+                                  (0, 5, 3), (2, 1, 1), (2, 2, 3), (2, 6, 5), (2, 4, 17)])
 def test_fp64_landscape_ragged_tiles(pkg, tile):
     """Hills, 13 fuels, smooth wind, line ignition on 230x170 nodes: several
-    strips (marching kernel) or tiles (2-D tile kernel), with a ragged last
-    row and column."""
+    strips (marching and warp kernels) or tiles (2-D tile kernel), with a
+    ragged last row and column."""
     w = synth.random_landscape(23, 17, seed=21, ignition="line", steps=120)
     m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
     ok, e = compare_fp64(state_np(m), orc)
@@ -83,7 +83,7 @@ def test_fp64_landscape_ragged_tiles(pkg, tile):
     assert Qo > 0
 
 
-@pytest.mark.parametrize("tile", [None, (1, 2, 3), (0, 4, 4)])
+@pytest.mark.parametrize("tile", [None, (1, 2, 3), (0, 4, 4), (2, 12, 3), (2, 4, 7)])
 def test_fp64_odd_mesh_width(pkg, tile):
     """Refinement 5 on 23x17 atmos cells: an odd fire-mesh width (115), so the
     marching kernel takes its unpaired (scalar) loads and stores."""
@@ -95,7 +95,8 @@ def test_fp64_odd_mesh_width(pkg, tile):
     assert heat_err <= 1e-10
 
 
-def test_fp64_anisotropic_multiplier_and_segments(pkg):
+@pytest.mark.parametrize("tile", [None, (2, 5, 3)])
+def test_fp64_anisotropic_multiplier_and_segments(pkg, tile):
     """Refinement 4 x 6 with unequal atmos spacing, a per-node spread
     multiplier, a growing segment ignition and a delayed instantaneous one."""
     w = synth.random_landscape(31, 19, sr=5, seed=33, ignition="center", steps=90)
@@ -110,13 +111,14 @@ def test_fp64_anisotropic_multiplier_and_segments(pkg):
                                        speed=0.8),
                    synth.point_ignition(600.0, 250.0, radius=9.0, t_start=7.25),
                    synth.point_ignition(300.0, 700.0, radius=15.0)]
-    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64")
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
     ok, e = compare_fp64(state_np(m), orc)
     assert ok, e
     assert heat_err <= 1e-10
 
 
-def test_fp64_chaparral(pkg):
+@pytest.mark.parametrize("tile", [None, (2, 6, 4)])
+def test_fp64_chaparral(pkg, tile):
     """The chaparral rate of eq. (chapparal) (6 m/s in a wind above 4.6 m/s)
     with a time step inside the scheme's stability limit (c = S dt/dx = 0.2)."""
     w = synth.random_landscape(20, 16, seed=77, ignition="center", steps=100, dt=0.2)
@@ -124,7 +126,7 @@ def test_fp64_chaparral(pkg):
     jj, ii = np.nonzero(w.fuel[40:-40, 40:-40] == 3)
     k = len(jj) // 2
     w.ignitions = [synth.point_ignition((ii[k] + 40.5) * w.dx, (jj[k] + 40.5) * w.dy, 10.0)]
-    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64")
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
     ok, e = compare_fp64(state_np(m), orc)
     assert ok, e
     assert heat_err <= 1e-10
@@ -134,7 +136,8 @@ def test_fp64_chaparral(pkg):
 # FP32: ignition time 0.1 s, burnt area 0.5 %, integrated heat 1e-4
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case,tile", [("line", None), ("points", None), ("line", (0, 8, 4))])
+@pytest.mark.parametrize("case,tile", [("line", None), ("points", None), ("line", (0, 8, 4)),
+                                       ("line", (2, 6, 20)), ("points", (2, 6, 20))])
 def test_fp32_against_fp64_oracle(pkg, case, tile):
     w = synth.random_landscape(32, 26, seed=44, ignition=case, n_points=6, edge_margin=300.0,
                                steps=300)
@@ -249,9 +252,12 @@ def _sample_cells(w, rng, n_random, near):
     return [(I, J) for I, J in cells if 1 <= I < w.nxa - 1 and 1 <= J < w.nya - 1]
 
 
-@pytest.mark.parametrize("name,prec,warm", [("line2000", "fp64", 60), ("line2000", "fp32", 200),
-                                            ("points8200", "fp32", 200)])
-def test_full_size_sampled_cells(pkg, name, prec, warm):
+@pytest.mark.parametrize("name,prec,warm,tile", [("line2000", "fp64", 60, None),
+                                                 ("line2000", "fp32", 200, None),
+                                                 ("points8200", "fp32", 200, None),
+                                                 ("points8200", "fp32", 200, (2, 6, 20)),
+                                                 ("line2000", "fp64", 60, (2, 6, 20))])
+def test_full_size_sampled_cells(pkg, name, prec, warm, tile):
     """The 2000x2000 line-fire mesh (FP64 and FP32) and the 8200x8200
     50-point mesh (FP32) in the tile shape the benchmark uses: after `warm`
     steps, one more GPU step is compared on sampled atmospheric cells (around
@@ -261,6 +267,8 @@ def test_full_size_sampled_cells(pkg, name, prec, warm):
     w = synth.line_fire_2000() if name == "line2000" else synth.points_fire_8200()
     wp = as_path_precision(w, prec)
     m = pkg.FireModel.from_workload(w, precision=prec)
+    if tile:
+        pkg.fire_set_kernel(m.ctx, *tile)
     u, v = m.wind(w.u, w.v)
     m.run(warm, u, v, w.dt)
     psi0, tign0, frac0, t0 = state_np(m)
