@@ -30,6 +30,7 @@
 
 #include "fire_device.cuh"
 #include "fire_internal.h"
+#include "pair_math.cuh"
 
 namespace wf {
 
@@ -140,6 +141,7 @@ struct MarchStrip {
     bool vec;  // paired vector access allowed (nx and x even)
     bool m_load[2], m_s1[2], m_s2[2], m_out[2];
     T dt, idx, idy, i2dx, i2dy, eps;
+    T2 dt2, idx2, idy2, i2dx2, i2dy2, eps2, hlf2;
     double tstart, t1;
     // running state
     T2 pf_psi;    // psi^n of the next row to stage
@@ -254,6 +256,26 @@ struct MarchStrip {
         return rhs_vals<T>(p, pl, pr, pd, pu, idx, idy, i2dx, i2dy, eps, co, m, un, vn, zx, zy);
     }
 
+    // the same for both columns of the thread at once (pair arithmetic)
+    __device__ __forceinline__ T2 stage_rhs2(const T2 *B, int sr, int sd, T2 up, int r, int cls0,
+                                             int cls1, T2 zx, T2 zy, T2 m, T2 un, T2 vn) const {
+        const int NT = kMarchThreads;
+        const T2 own = B[sr * NT + c];
+        T2 L = mk2(B[sr * NT + c - 1].y, own.x), R = mk2(own.y, B[sr * NT + c + 1].x);
+        T2 D = B[sd * NT + c], U = up;
+        if (xa <= 0 || xa + 1 >= nx - 1 || r == 0 || r == ny - 1) {
+            const T2 L0 = L, D0 = D, U0 = U;
+            if (xa == 0) L.x = ghost_value<T>(own.x, own.y);
+            if (xa == nx - 1) R.x = ghost_value<T>(own.x, L0.x);
+            if (xa + 1 == nx - 1) R.y = ghost_value<T>(own.y, own.x);
+            if (r == 0) D = mk2(ghost_value<T>(own.x, U0.x), ghost_value<T>(own.y, U0.y));
+            if (r == ny - 1) U = mk2(ghost_value<T>(own.x, D0.x), ghost_value<T>(own.y, D0.y));
+        }
+        WCoef<T> co;
+        coef_pair<T>(sm.lut, cls0 > ncm1 ? ncm1 : cls0, cls1 > ncm1 ? ncm1 : cls1, co);
+        return rhs2<T>(own, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, m, un, vn, zx, zy);
+    }
+
     __device__ __forceinline__ void iter(int k) {
         const int NT = kMarchThreads;
         // ring slots: row k+3 -> s3, k+2 -> s2, k+1 -> s1, k -> s0, k-1 -> s3, k-2 -> s2
@@ -280,23 +302,15 @@ struct MarchStrip {
             load_env(k + 3);
             if (in_rows(r, y0 - 2, y0 + La + 2) && (m_s1[0] || m_s1[1])) {
                 wind(r, true, e_un, e_vn);
-                T2 F, P;
+                if ((m_s1[0] && (!finite_val(e_un.x) || !finite_val(e_vn.x))) ||
+                    (m_s1[1] && (!finite_val(e_un.y) || !finite_val(e_vn.y))))
+                    st |= ST_NONFINITE;
+                T2 F = stage_rhs2(sm.S0, s2, s1, cur_psi, r, e_cls[0], e_cls[1], e_zx, e_zy, e_m,
+                                  e_un, e_vn);
+                F.x = m_s1[0] ? F.x : T(0);
+                F.y = m_s1[1] ? F.y : T(0);
                 const T2 own = sm.S0[s2 * NT + c];
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    T f = T(0);
-                    if (m_s1[j]) {
-                        const T uj = pick<T>(e_un, j), vj = pick<T>(e_vn, j);
-                        if (!finite_val(uj) || !finite_val(vj)) st |= ST_NONFINITE;
-                        int cls = e_cls[j];
-                        cls = cls > ncm1 ? ncm1 : cls;
-                        f = stage_rhs(sm.S0, s2, s1, cur_psi, r, j, cls, pick<T>(e_zx, j),
-                                      pick<T>(e_zy, j), pick<T>(e_m, j), uj, vj);
-                    }
-                    if (j == 0) { F.x = f; P.x = own.x + dt * f; }
-                    else { F.y = f; P.y = own.y + dt * f; }
-                }
-                sm.S1[s2 * NT + c] = P;
+                sm.S1[s2 * NT + c] = fma2(dt2, F, own);
                 sm.SF[s2 * NT + c] = F;
             }
         }
@@ -309,29 +323,23 @@ struct MarchStrip {
                 const T2 p0v = sm.S0[s1 * NT + c];
                 const T2 f1v = sm.SF[s1 * NT + c];
                 const bool own_row = r >= y0 && r < y0 + La;
-                T2 PN, DL;
-                bool need[2] = {false, false};
+                T2 DL;
+                const T2 F2 = stage_rhs2(sm.S1, s1, s0, up, r, eb_cls0, eb_cls1, eb_zx, eb_zy, eb_m,
+                                         eb_un, eb_vn);
+                T2 PN = fma2(dt2, fma2(hlf2, f1v, mul2(hlf2, F2)), p0v);
+                PN.x = m_s2[0] ? PN.x : T(0);
+                PN.y = m_s2[1] ? PN.y : T(0);
+                bool need[2] = {m_s2[0] && PN.x <= T(0), m_s2[1] && PN.y <= T(0)};
+                if (own_row) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    T pn = T(0);
-                    if (m_s2[j]) {
-                        int cls = j == 0 ? eb_cls0 : eb_cls1;
-                        cls = cls > ncm1 ? ncm1 : cls;
-                        const T F2 = stage_rhs(sm.S1, s1, s0, up, r, j, cls, pick<T>(eb_zx, j),
-                                               pick<T>(eb_zy, j), pick<T>(eb_m, j),
-                                               pick<T>(eb_un, j), pick<T>(eb_vn, j));
-                        const T p0 = pick<T>(p0v, j);
-                        pn = p0 + dt * (T(0.5) * pick<T>(f1v, j) + T(0.5) * F2);
-                        need[j] = pn <= T(0);  // a crossing, or burning
-                        if (own_row && m_out[j]) {
-                            if (!finite_val(pn)) st |= ST_NONFINITE;
-                            const int x = xa + j;
-                            const bool edge = x < band || r < band || x >= nx - band || r >= ny - band;
-                            if (edge && pn < T(0)) st |= ST_BOUNDARY;
-                        }
+                    for (int j = 0; j < 2; ++j) {
+                        if (!m_out[j]) continue;
+                        const T pn = pick<T>(PN, j);
+                        if (!finite_val(pn)) st |= ST_NONFINITE;
+                        const int x = xa + j;
+                        const bool edge = x < band || r < band || x >= nx - band || r >= ny - band;
+                        if (edge && pn < T(0)) st |= ST_BOUNDARY;
                     }
-                    if (j == 0) PN.x = pn;
-                    else PN.y = pn;
                 }
                 DL.x = DL.y = T(0);
                 // ignition time and t - t_i (double arithmetic) only in warps
@@ -543,6 +551,13 @@ struct MarchStrip {
         i2dx = T(1) / (T(2) * T(a.dx));
         i2dy = T(1) / (T(2) * T(a.dy));
         eps = T(a.eps);
+        dt2 = mk2(dt, dt);
+        idx2 = mk2(idx, idx);
+        idy2 = mk2(idy, idy);
+        i2dx2 = mk2(i2dx, i2dx);
+        i2dy2 = mk2(i2dy, i2dy);
+        eps2 = mk2(eps, eps);
+        hlf2 = mk2(T(0.5), T(0.5));
         tstart = tstart_;
         t1 = tstart + a.dt;
         ncm1 = a.ncls - 1;

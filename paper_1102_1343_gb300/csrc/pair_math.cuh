@@ -1,0 +1,135 @@
+// Arithmetic on pairs of values: the two fire-mesh columns a thread holds.
+// FP32 uses the packed f32x2 instructions of sm_100 and later (one
+// instruction for both columns); FP64 works element by element.  rhs2 is the
+// right-hand side of eq. (F-disc) for such a pair.
+#pragma once
+
+#include "fire_device.cuh"
+
+namespace wf {
+
+// ---------------------------------------------------------------------------
+// pairs of values (the two columns of a lane)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PairT;
+template <>
+struct PairT<float> {
+    using t = float2;
+};
+template <>
+struct PairT<double> {
+    using t = double2;
+};
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename V, typename T>
+__device__ __forceinline__ V splat(T v) {
+    return mk2(v, v);
+}
+
+__device__ __forceinline__ float max_val(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_val(double a, double b) { return fmax(a, b); }
+
+// coefficients of eq. (spread-WRF-Fire) for the two columns
+template <typename T>
+struct WCoef {
+    using V = typename PairT<T>::t;
+    V S0, R0, b, c, d, e;
+};
+
+// Right-hand side of eq. (F-disc) for two columns (the arithmetic of
+// rhs_vals on pairs): node values p, neighbours left / right / down / up,
+// the grid constants 1/dx, 1/dy, 1/(2dx), 1/(2dy), eps as pairs, the
+// coefficients, multiplier, node wind and terrain gradient of each column.
+template <typename T>
+__device__ __forceinline__ typename PairT<T>::t rhs2(
+    typename PairT<T>::t p, typename PairT<T>::t pl, typename PairT<T>::t pr,
+    typename PairT<T>::t pd, typename PairT<T>::t pu, typename PairT<T>::t idx2,
+    typename PairT<T>::t idy2, typename PairT<T>::t i2dx2, typename PairT<T>::t i2dy2,
+    typename PairT<T>::t eps2, const WCoef<T> &co, typename PairT<T>::t m,
+    typename PairT<T>::t un, typename PairT<T>::t vn, typename PairT<T>::t zx,
+    typename PairT<T>::t zy) {
+    using V = typename PairT<T>::t;
+    const V dxm = mul2(sub2(p, pl), idx2), dxp = mul2(sub2(pr, p), idx2);
+    const V dym = mul2(sub2(p, pd), idy2), dyp = mul2(sub2(pu, p), idy2);
+    // Godunov (eq. Godunov): |D| = max(D-, -D+, 0) per direction
+    V gx, gy;
+    gx.x = max_val(max_val(dxm.x, -dxp.x), T(0));
+    gx.y = max_val(max_val(dxm.y, -dxp.y), T(0));
+    gy.x = max_val(max_val(dym.x, -dyp.x), T(0));
+    gy.y = max_val(max_val(dym.y, -dyp.y), T(0));
+    const V g2 = fma2(gx, gx, mul2(gy, gy));
+    // central differences, zeroed at the rounding level of their values
+    V ddx = sub2(pr, pl), ddy = sub2(pu, pd);
+    const T z = Mth<T>::kGradZero;
+    ddx.x = abs_val(ddx.x) <= z * (abs_val(pr.x) + abs_val(pl.x)) ? T(0) : ddx.x;
+    ddx.y = abs_val(ddx.y) <= z * (abs_val(pr.y) + abs_val(pl.y)) ? T(0) : ddx.y;
+    ddy.x = abs_val(ddy.x) <= z * (abs_val(pu.x) + abs_val(pd.x)) ? T(0) : ddy.x;
+    ddy.y = abs_val(ddy.y) <= z * (abs_val(pu.y) + abs_val(pd.y)) ? T(0) : ddy.y;
+    const V cx = mul2(ddx, i2dx2), cy = mul2(ddy, i2dy2);
+    V nxv, nyv;
+    Mth<T>::unit(cx.x, cy.x, nxv.x, nyv.x);
+    Mth<T>::unit(cx.y, cy.y, nxv.y, nyv.y);
+    const V U = fma2(un, nxv, mul2(vn, nyv));
+    const V tp = fma2(zx, nxv, mul2(zy, nyv));
+    // spread rate, eq. (spread-WRF-Fire)
+    V Ue, tq, pw;
+    Ue.x = min_val(max_val(U.x, T(0)), co.e.x);
+    Ue.y = min_val(max_val(U.y, T(0)), co.e.y);
+    tq.x = max_val(tp.x, T(0));
+    tq.y = max_val(tp.y, T(0));
+    pw.x = Mth<T>::pw(Ue.x, co.b.x);
+    pw.y = Mth<T>::pw(Ue.y, co.b.y);
+    V s = fma2(mul2(co.d, tq), tq, fma2(co.c, pw, co.R0));
+    s.x = max_val(s.x, co.S0.x);
+    s.y = max_val(s.y, co.S0.y);
+    const V S = mul2(m, s);
+    const V lap = add2(sub2(dxp, dxm), sub2(dyp, dym));
+    V grad;
+    grad.x = Mth<T>::sqr(g2.x);
+    grad.y = Mth<T>::sqr(g2.y);
+    // -S |grad| + eps S Lap
+    return mul2(S, sub2(mul2(eps2, lap), grad));
+}
+
+// the six coefficients of two classes from a per-class table of 8 values
+// (S0 R0 b c d e Tf Hs): 16-byte shared loads in FP32
+template <typename T>
+__device__ __forceinline__ void coef_pair(const T *lut, int cls0, int cls1, WCoef<T> &co) {
+    const T *l0 = lut + cls0 * 8, *l1 = lut + cls1 * 8;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(l0);
+        const float4 b0 = *reinterpret_cast<const float4 *>(l0 + 4);
+        const float4 a1 = *reinterpret_cast<const float4 *>(l1);
+        const float4 b1 = *reinterpret_cast<const float4 *>(l1 + 4);
+        co.S0 = mk2(a0.x, a1.x);
+        co.R0 = mk2(a0.y, a1.y);
+        co.b = mk2(a0.z, a1.z);
+        co.c = mk2(a0.w, a1.w);
+        co.d = mk2(b0.x, b1.x);
+        co.e = mk2(b0.y, b1.y);
+    } else {
+        co.S0 = mk2(l0[0], l1[0]);
+        co.R0 = mk2(l0[1], l1[1]);
+        co.b = mk2(l0[2], l1[2]);
+        co.c = mk2(l0[3], l1[3]);
+        co.d = mk2(l0[4], l1[4]);
+        co.e = mk2(l0[5], l1[5]);
+    }
+}
+
+}  // namespace wf
