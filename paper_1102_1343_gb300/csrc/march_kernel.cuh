@@ -146,7 +146,7 @@ struct MarchStrip {
     // running state
     T2 pf_psi;    // psi^n of the next row to stage
     T2 cur_psi;   // psi^n of the row staged this iteration
-    int pf_cls[2];
+    int pf_fa, pf_fb;  // raw fuel-class bytes of the prefetched row (decoded at use)
     T2 pf_zx, pf_zy, pf_m;
     T2 pf_F;
     int e_cls[2];       // environment of the row stage 1 handled last iteration
@@ -163,33 +163,33 @@ struct MarchStrip {
         return r >= lo && r < hi && r >= 0 && r < ny;
     }
 
-    // paired load of a T field at (r, xa), masked per column
-    __device__ __forceinline__ T2 ld2(const T *__restrict__ f, int r, bool m0, bool m1) const {
-        T2 v;
-        const size_t g = (size_t)r * nx + xa;
-        if (vec && m0 && m1) {
-            v = *reinterpret_cast<const T2 *>(f + g);
-        } else {
-            v.x = m0 ? f[g] : T(0);
-            v.y = m1 ? f[g + 1] : T(0);
+    // paired load of a T field at (r, xa).  Every thread loads, columns
+    // outside the domain from the nearest inside one (the values of those
+    // columns are never used), so the loaded registers are not touched
+    // before their use and a prefetch one row ahead hides the latency.
+    __device__ __forceinline__ T2 ld2(const T *__restrict__ f, int r) const {
+        const size_t rowb = (size_t)r * nx;
+        if (vec) {
+            const int xc = min(max(xa, 0), nx - 2);
+            return *reinterpret_cast<const T2 *>(f + rowb + xc);
         }
-        return v;
+        const int xA = min(max(xa, 0), nx - 1), xB = min(max(xa + 1, 0), nx - 1);
+        return mk2(f[rowb + xA], f[rowb + xB]);
     }
 
     __device__ __forceinline__ void load_env(int r) {
         if (!in_rows(r, y0 - 2, y0 + La + 2) || !(m_s1[0] || m_s1[1])) return;
-        const size_t g = (size_t)r * nx + xa;
-        if (vec && m_s1[0] && m_s1[1]) {
-            const uint16_t f2 = *reinterpret_cast<const uint16_t *>(a.fuel + g);
-            pf_cls[0] = f2 & 0xff;
-            pf_cls[1] = f2 >> 8;
+        const size_t rowb = (size_t)r * nx;
+        if (vec) {
+            const int xc = min(max(xa, 0), nx - 2);
+            pf_fa = *reinterpret_cast<const uint16_t *>(a.fuel + rowb + xc);
         } else {
-            pf_cls[0] = m_s1[0] ? a.fuel[g] : 0;
-            pf_cls[1] = m_s1[1] ? a.fuel[g + 1] : 0;
+            pf_fa = a.fuel[rowb + min(max(xa, 0), nx - 1)];
+            pf_fb = a.fuel[rowb + min(max(xa + 1, 0), nx - 1)];
         }
-        pf_zx = ld2(static_cast<const T *>(a.dzdx), r, m_s1[0], m_s1[1]);
-        pf_zy = ld2(static_cast<const T *>(a.dzdy), r, m_s1[0], m_s1[1]);
-        if (a.mult) pf_m = ld2(static_cast<const T *>(a.mult), r, m_s1[0], m_s1[1]);
+        pf_zx = ld2(static_cast<const T *>(a.dzdx), r);
+        pf_zy = ld2(static_cast<const T *>(a.dzdy), r);
+        if (a.mult) pf_m = ld2(static_cast<const T *>(a.mult), r);
     }
 
     // x-interpolated wind of atmos u-row J / v-row J for this thread's columns
@@ -287,15 +287,15 @@ struct MarchStrip {
             if (r >= y0 - 3 && r < y0 + La + 3) sm.S0[s3 * NT + c] = cur_psi;
             const int rn = k + 4;
             if (in_rows(rn, y0 - 3, y0 + La + 3))
-                pf_psi = ld2(static_cast<const T *>(a.psi_in), rn, m_load[0], m_load[1]);
+                pf_psi = ld2(static_cast<const T *>(a.psi_in), rn);
         }
         // ---- B: stage 1 on row k+2 (its environment is carried to C)
         const int eb_cls0 = e_cls[0], eb_cls1 = e_cls[1];
         const T2 eb_zx = e_zx, eb_zy = e_zy, eb_m = e_m, eb_un = e_un, eb_vn = e_vn;
         {
             const int r = k + 2;
-            e_cls[0] = pf_cls[0];
-            e_cls[1] = pf_cls[1];
+            e_cls[0] = vec ? (pf_fa & 0xff) : pf_fa;
+            e_cls[1] = vec ? (pf_fa >> 8) : pf_fb;
             e_zx = pf_zx;
             e_zy = pf_zy;
             e_m = pf_m;
@@ -482,7 +482,7 @@ struct MarchStrip {
         }
         // prefetch F^n of row k for the next iteration's quadrature
         if (k >= y0 && k < y0 + La && (m_out[0] || m_out[1]))
-            pf_F = ld2(static_cast<const T *>(a.F_in), k, m_out[0], m_out[1]);
+            pf_F = ld2(static_cast<const T *>(a.F_in), k);
         bool band_end = false;
         if (drow) {
             if (++bcnt == sry) {
@@ -615,8 +615,8 @@ struct MarchStrip {
         hscale = 1.0 / (a.dt * (double)srx * (double)sry);
         pf_psi.x = pf_psi.y = T(0);
         if (in_rows(k0 + 3, y0 - 3, y0 + La + 3))
-            pf_psi = ld2(static_cast<const T *>(a.psi_in), k0 + 3, m_load[0], m_load[1]);
-        pf_cls[0] = pf_cls[1] = 0;
+            pf_psi = ld2(static_cast<const T *>(a.psi_in), k0 + 3);
+        pf_fa = pf_fb = 0;
         pf_zx.x = pf_zx.y = pf_zy.x = pf_zy.y = T(0);
         pf_m.x = pf_m.y = T(1);
         load_env(k0 + 2);

@@ -46,7 +46,7 @@ struct WOcc<double> {
 template <typename T>
 struct WEnv {  // what stage 2 reuses from stage 1 of the same row
     using V = typename PairT<T>::t;
-    int cls0, cls1;
+    int cls0, cls1;  // raw fuel bytes when loaded (see decode), classes after
     V zx, zy, m, un, vn;
 };
 
@@ -78,33 +78,40 @@ struct WarpStrip {
     __device__ __forceinline__ WarpStrip(const StepArgs &args, const T *l, const T *lq, T *h)
         : a(args), lut(l), lutq(lq), hw(h) {}
 
+    // paired load of row r at the lane's columns.  Every lane loads, columns
+    // outside the domain from the nearest inside one (their values are never
+    // used), so a loaded register is not touched before its use one
+    // iteration later and the prefetch hides the memory latency.
     __device__ __forceinline__ V ld(const T *__restrict__ f, int r) const {
-        const size_t g = (size_t)r * nx + xa;
-        V v;
-        if (vec && inA && inB) {
-            v = *reinterpret_cast<const V *>(f + g);
-        } else {
-            v.x = inA ? f[g] : T(0);
-            v.y = inB ? f[g + 1] : T(0);
+        const size_t rowb = (size_t)r * nx;
+        if (vec) {
+            const int xc = min(max(xa, 0), nx - 2);
+            return *reinterpret_cast<const V *>(f + rowb + xc);
         }
-        return v;
+        const int xA = min(max(xa, 0), nx - 1), xB = min(max(xa + 1, 0), nx - 1);
+        return mk2(f[rowb + xA], f[rowb + xB]);
     }
 
+    // prefetch of a row's environment: raw fuel bytes (decoded by decode()
+    // at use), terrain gradient and multiplier
     __device__ __forceinline__ void load_env(int r, WEnv<T> &e) const {
-        const size_t g = (size_t)r * nx + xa;
-        if (vec && inA && inB) {
-            const uint16_t f2 = *reinterpret_cast<const uint16_t *>(a.fuel + g);
-            e.cls0 = f2 & 0xff;
-            e.cls1 = f2 >> 8;
+        const size_t rowb = (size_t)r * nx;
+        if (vec) {
+            const int xc = min(max(xa, 0), nx - 2);
+            e.cls0 = *reinterpret_cast<const uint16_t *>(a.fuel + rowb + xc);
         } else {
-            e.cls0 = inA ? a.fuel[g] : 0;
-            e.cls1 = inB ? a.fuel[g + 1] : 0;
+            e.cls0 = a.fuel[rowb + min(max(xa, 0), nx - 1)];
+            e.cls1 = a.fuel[rowb + min(max(xa + 1, 0), nx - 1)];
         }
-        e.cls0 = e.cls0 > ncm1 ? ncm1 : e.cls0;
-        e.cls1 = e.cls1 > ncm1 ? ncm1 : e.cls1;
         e.zx = ld(static_cast<const T *>(a.dzdx), r);
         e.zy = ld(static_cast<const T *>(a.dzdy), r);
         e.m = a.mult ? ld(static_cast<const T *>(a.mult), r) : splat<V>(T(1));
+    }
+
+    __device__ __forceinline__ void decode(WEnv<T> &e) const {
+        int c0 = vec ? (e.cls0 & 0xff) : e.cls0, c1 = vec ? (e.cls0 >> 8) : e.cls1;
+        e.cls0 = c0 > ncm1 ? ncm1 : c0;
+        e.cls1 = c1 > ncm1 ? ncm1 : c1;
     }
 
     __device__ __forceinline__ void coef(const WEnv<T> &e, WCoef<T> &co) const {
@@ -240,8 +247,8 @@ struct WarpStrip {
             if (r >= 0 && r < ny) {
                 v = ld(psi_in, r);
                 const size_t g = (size_t)r * nx;
-                if (lane == 0) hl = xa - 1 >= 0 ? psi_in[g + xa - 1] : T(0);
-                if (lane == 31) hr = xa + 2 < nx ? psi_in[g + xa + 2] : T(0);
+                if (lane == 0) hl = psi_in[g + min(max(xa - 1, 0), nx - 1)];
+                if (lane == 31) hr = psi_in[g + min(max(xa + 2, 0), nx - 1)];
             }
         };
         load_psi(kb, P0, hl1, hr1);  // hl1/hr1 of row kb are not used
@@ -259,6 +266,7 @@ struct WarpStrip {
             // ---- B: stage 1 on row k+1
             const int rB = k + 1;
             envB = envPre;
+            decode(envB);
             if (rB + 1 >= 0 && rB + 1 < ny && rB + 1 <= ke + 1) load_env(rB + 1, envPre);
             if (rB >= 0 && rB < ny) {
                 wind(rB, envB.un, envB.vn);
