@@ -45,6 +45,8 @@ UNIT = "cell-steps/s"
 # F r/w 4+4, ignition time read 8, fuel class 1, terrain gradient 8
 BYTES_PER_CELL_STEP = {"fp32": 33, "fp64": 57}
 KERNEL_SOURCES = ["paper_1102_1343_gb300/csrc/march_kernel.cuh",
+                  "paper_1102_1343_gb300/csrc/pair_math.cuh",
+                  "paper_1102_1343_gb300/csrc/warp_kernel.cuh",
                   "paper_1102_1343_gb300/csrc/fire_device.cuh",
                   "paper_1102_1343_gb300/csrc/fire_internal.h",
                   "paper_1102_1343_gb300/csrc/step_f32.cu"]
@@ -263,10 +265,12 @@ def run_gpu(args, rank, world):
     cells = w.nx * w.ny
     prec = args.precision
     m = pkg.FireModel.from_workload(w, precision=prec, device=dev)
+    u, v = m.wind(w.u, w.v)
     if args.kernel:
         pkg.fire_set_kernel(m.ctx, *args.kernel)
+    elif args.autotune:
+        m.autotune(u, v, w.dt, probe_steps=3)  # the library's own tuner, before timing
     kernel = pkg.fire_get_kernel(m.ctx)
-    u, v = m.wind(w.u, w.v)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):
@@ -373,15 +377,18 @@ def run_gpu(args, rank, world):
                        "refinement": [w.srx, w.sry], "precision": prec,
                        "state_in_hbm": "yes; state 2.2 GB > L2, no flush needed"
                        if args.workload == "points8200" else "yes",
-                       "kernel": {"variant": ["tile", "march"][kernel[0]],
-                                  "tile_atmos_cells": list(kernel[1:])},
+                       "kernel": {"variant": ["tile", "march", "warp"][kernel[0]],
+                                  "tile_atmos_cells": list(kernel[1:]),
+                                  "chosen_by": "--kernel" if args.kernel else
+                                  ("fire_autotune" if args.autotune else "fire_init default")},
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": ["k_fire_step<float>", "k_fire_march<float>"][kernel[0]],
+                         "kernel": ["k_fire_step", "k_fire_march", "k_fire_warp"][kernel[0]]
+                         + ("<float>" if prec == "fp32" else "<double>"),
                          "kernel_ms": k_avg,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_kind} hbm_gbs"},
@@ -445,7 +452,8 @@ def bench_adjoint(pkg, dev, ckpt=20):
         ms = e0.elapsed_time(e1)
         grads[prec] = (J, gm, gM, gu, gv)
         rec = {"value": n / (ms / 1e3), "ms": ms, "J": J,
-               "kernel": {"variant": ["tile", "march"][kern[0]], "tile_atmos_cells": list(kern[1:])}}
+               "kernel": {"variant": ["tile", "march", "warp"][kern[0]],
+                          "tile_atmos_cells": list(kern[1:])}}
         # the plain forward on the same mesh and kernel
         m.set_state(*st0)
         m.run(2, u, v, w.dt)
@@ -564,6 +572,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the shape fire_autotune picks instead of fire_init's default")
     ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

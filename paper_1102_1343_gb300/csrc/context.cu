@@ -244,11 +244,11 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
 }
 
 int default_kernel(fire_ctx *c) {
-    // marching strips of up to 248 columns (an even number) x ~200 rows when
+    // marching strips of up to 248 columns (an even number) x ~60 rows when
     // the refinement allows; else 2-D tiles of ~80 x 40 (FP32) / 40 x 40
     // (FP64) nodes
     if (c->g.sr_x <= kMarchMaxColumns / 2) {
-        int kx = kMarchMaxColumns / c->g.sr_x, ky = 200 / c->g.sr_y;
+        int kx = kMarchMaxColumns / c->g.sr_x, ky = 60 / c->g.sr_y;
         if (kx > c->g.nx_atm) kx = c->g.nx_atm;
         if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 2;
         if (ky < 1) ky = 1;

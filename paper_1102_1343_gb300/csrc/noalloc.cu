@@ -161,7 +161,7 @@ extern "C" int fire_step_noalloc(const fire_grid_desc *grid, const fire_fuel_cla
         return FIRE_ERR_CUDA;
     cudaError_t e = cudaErrorInvalidValue;
     if (g.sr_x <= kMarchMaxColumns / 2) {
-        int kx = kMarchMaxColumns / g.sr_x, ky = 200 / g.sr_y;
+        int kx = kMarchMaxColumns / g.sr_x, ky = 60 / g.sr_y;
         if (kx > g.nx_atm) kx = g.nx_atm;
         if ((kx * g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 2;
         if (ky < 1) ky = 1;
