@@ -157,6 +157,12 @@ def make_workload(name: str):
         return synth.line_fire_2000()
     if name == "circle100":
         return synth.plain_circle()
+    if name == "points4000":
+        # a smaller case of the same recipe (4000x4000 nodes, state 0.53 GB > L2) for
+        # profiler captures that the 8200x8200 mesh is too large for
+        return synth.random_landscape(400, 400, seed=synth.BASE_SEED, ignition="points",
+                                      n_points=12, edge_margin=500.0, steps=2000,
+                                      name="points-fire-4000x4000")
     raise ValueError(name)
 
 
@@ -167,7 +173,7 @@ def oracle_sample(name: str, budget_cell_steps: float):
     if name == "circle100":
         return synth.plain_circle(), 1
     side_atm = int(max(10, min(82, math.sqrt(budget_cell_steps) / 10)))
-    ign = "points" if name == "points8200" else "line"
+    ign = "points" if name.startswith("points") else "line"
     w = synth.random_landscape(side_atm, side_atm, seed=synth.BASE_SEED, ignition=ign,
                                n_points=max(1, round(50 * (side_atm / 820) ** 2)),
                                edge_margin=2000.0 * side_atm / 820, steps=1)
@@ -234,6 +240,7 @@ def run_reference(args, rank, world):
 
 
 WORKLOAD_NAMES = {"points8200": "points-fire-8200x8200 (820x820 atmos x10, 50 point ignitions)",
+                  "points4000": "points-fire-4000x4000 (400x400 atmos x10, 12 point ignitions)",
                   "line2000": "line-fire-2000x2000 (200x200 atmos x10, 1 km line ignition)",
                   "circle100": "circle-fp64-100x100 (10x10 atmos x10)"}
 
@@ -560,7 +567,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["points8200", "line2000", "circle100"],
+    ap.add_argument("--workload", choices=["points8200", "line2000", "circle100", "points4000"],
                     default="points8200")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--kernel", type=int, nargs=3, default=None,

@@ -469,14 +469,19 @@ struct MarchStrip {
                 if (m_out[0]) fo[g] = FN.x;
                 if (m_out[1]) fo[g + 1] = FN.y;
             }
+            // heat flux densities, only in warps where some fuel burned
+            const T dF0 = m_out[0] ? pf_F.x - Fn[0] : T(0);
+            const T dF1 = m_out[1] ? pf_F.y - Fn[1] : T(0);
+            if (__any_sync(__activemask(), dF0 != T(0) || dF1 != T(0))) {
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const T dF = pick<T>(pf_F, j) - Fn[j];
-                if (m_out[j] && dF != T(0)) {
-                    const int cls0 = a.fuel[g + j];
-                    const int cls = cls0 > ncm1 ? ncm1 : cls0;
-                    acc_s[j] += dF * sm.lut[cls * 8 + 7];
-                    acc_q[j] += dF * sm.lutq[cls];
+                for (int j = 0; j < 2; ++j) {
+                    const T dF = j == 0 ? dF0 : dF1;
+                    if (dF != T(0)) {
+                        const int cls0 = a.fuel[g + j];
+                        const int cls = cls0 > ncm1 ? ncm1 : cls0;
+                        acc_s[j] += dF * sm.lut[cls * 8 + 7];
+                        acc_q[j] += dF * sm.lutq[cls];
+                    }
                 }
             }
         }
