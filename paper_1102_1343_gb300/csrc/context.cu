@@ -223,8 +223,8 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
         if (sm > c->smem_max) return FIRE_ERR_ARG;
         e = c->prec == FIRE_FP64 ? prepare_march_kernel<double>(sm) : prepare_march_kernel<float>(sm);
     } else if (variant == FIRE_KERNEL_WARP) {
-        const long long W = (long long)kx * c->g.sr_x;
-        if (W > kWarpMaxColumns || (W & 1)) return FIRE_ERR_ARG;
+        const long long W = (long long)kx * c->g.sr_x, L = (long long)ky * c->g.sr_y;
+        if (W > kWarpMaxColumns || (W & 1) || L > kWarpMaxRows) return FIRE_ERR_ARG;
         sm = 0;
         e = cudaSuccess;
     } else if (variant == FIRE_KERNEL_TILE) {

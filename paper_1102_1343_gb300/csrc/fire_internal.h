@@ -90,6 +90,7 @@ template <typename T>
 cudaError_t launch_warp(const StepArgs &a, cudaStream_t s);
 
 constexpr int kWarpMaxColumns = 60;  // output columns of one warp strip (even)
+constexpr int kWarpMaxRows = 512;    // output rows of one warp strip
 
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s);

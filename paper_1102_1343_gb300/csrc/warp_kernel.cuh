@@ -35,6 +35,12 @@ constexpr int kWarpStrips = 4;  // warps (strips) per CTA
 constexpr int kWarpCtaThreads = 32 * kWarpStrips;
 
 template <typename T>
+struct WRow {  // y-interpolation of the wind for one fire row
+    int ju0, jv0;
+    T wyu, wyv;
+};
+
+template <typename T>
 struct WOcc {
     static constexpr int blocks = 3;
 };
@@ -57,6 +63,8 @@ struct WarpStrip {
     const T *lut;   // [ncls][8] S0 R0 b c d e Tf Hs
     const T *lutq;  // [ncls] Hq
     T *hw;          // [2][64] heat column sums of this warp
+    const WRow<T> *rows;  // rows y0 - 2 .. y0 + La + 1 of the CTA's strips
+    int bcnt;       // rows done in the current atmospheric band
     int lane, x0, y0, W, La, Wa, nx, ny, nxa, nya, srx, sry, ncm1, band;
     int xa;          // global column of the lane's first column
     bool vec;        // paired vector access (nx even)
@@ -75,8 +83,9 @@ struct WarpStrip {
     V UA, UB, VA, VB;
     V acc_s, acc_q;
 
-    __device__ __forceinline__ WarpStrip(const StepArgs &args, const T *l, const T *lq, T *h)
-        : a(args), lut(l), lutq(lq), hw(h) {}
+    __device__ __forceinline__ WarpStrip(const StepArgs &args, const T *l, const T *lq, T *h,
+                                         const WRow<T> *rw)
+        : a(args), lut(l), lutq(lq), hw(h), rows(rw) {}
 
     // paired load of row r at the lane's columns.  Every lane loads, columns
     // outside the domain from the nearest inside one (their values are never
@@ -132,11 +141,9 @@ struct WarpStrip {
 
     // bilinear wind at fire row r (Sect. 5), rows of the atmos wind cached
     __device__ __forceinline__ void wind(int r, V &un, V &vn) {
-        const T yr = (T(r) + T(0.5)) / T(sry);
-        int ju0, ju1, jv0, jv1;
-        T wyu, wyv;
-        lin_idx<T>(yr - T(0.5), nya, ju0, ju1, wyu);
-        lin_idx<T>(yr, nya + 1, jv0, jv1, wyv);
+        const WRow<T> w = rows[r - (y0 - 2)];
+        const int ju0 = w.ju0, jv0 = w.jv0, ju1 = nya == 1 ? ju0 : ju0 + 1, jv1 = jv0 + 1;
+        const T wyu = w.wyu, wyv = w.wyv;
         if (ju0 != ju_cur) {
             UA = wind_u_row(ju0);
             UB = ju1 == ju0 ? UA : wind_u_row(ju1);
@@ -217,6 +224,7 @@ struct WarpStrip {
         st = 0;
         poison = splat<V>(T(0));
         acc_s = acc_q = splat<V>(T(0));
+        bcnt = 0;
         // x-weights of the wind
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -473,7 +481,8 @@ struct WarpStrip {
             }
         }
         // after the last row of an atmospheric band: average per cell
-        if ((rD + 1) % sry == 0 || rD == y0 + La - 1) {
+        if (++bcnt == sry) {
+            bcnt = 0;
             hw[2 * lane] = acc_s.x;
             hw[2 * lane + 1] = acc_s.y;
             hw[64 + 2 * lane] = acc_q.x;
@@ -502,6 +511,22 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
     __shared__ __align__(16) T lut[FIRE_MAX_CLASSES * 8];
     __shared__ T lutq[FIRE_MAX_CLASSES];
     __shared__ __align__(16) T hw[kWarpStrips][128];
+    __shared__ __align__(16) WRow<T> rows[kWarpMaxRows + 4];
+    const int y0 = blockIdx.y * a.ky * a.sry;
+    const int La = min(a.ky * a.sry, a.ny - y0);
+    for (int i = threadIdx.x; i < La + 4; i += kWarpCtaThreads) {
+        const int r = y0 - 2 + i;
+        WRow<T> w;
+        w.ju0 = w.jv0 = 0;
+        w.wyu = w.wyv = T(0);
+        if (r >= 0 && r < a.ny) {
+            int j1;
+            const T yr = (T(r) + T(0.5)) / T(a.sry);
+            lin_idx<T>(yr - T(0.5), a.nya, w.ju0, j1, w.wyu);
+            lin_idx<T>(yr, a.nya + 1, w.jv0, j1, w.wyv);
+        }
+        rows[i] = w;
+    }
     for (int k = threadIdx.x; k < a.ncls; k += kWarpCtaThreads) {
         const double *co = a.coef + (size_t)k * K_N;
         T *l = lut + k * 8;
@@ -522,8 +547,8 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
     const int W = a.kx * a.srx;
     const int x0 = (blockIdx.x * kWarpStrips + w) * W;
     if (x0 >= a.nx) return;  // whole warp
-    WarpStrip<T> s(a, lut, lutq, hw[w]);
-    s.run(x0, blockIdx.y * a.ky * a.sry, tstart);
+    WarpStrip<T> s(a, lut, lutq, hw[w], rows);
+    s.run(x0, y0, tstart);
     const int stw = __reduce_or_sync(0xffffffffu, s.st);
     if ((threadIdx.x & 31) == 0 && stw) atomicOr(a.status, stw);
 }
@@ -531,7 +556,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
 template <typename T>
 cudaError_t launch_warp(const StepArgs &a, cudaStream_t s) {
     const int W = a.kx * a.srx, L = a.ky * a.sry;
-    if (W > 60 || (W & 1) || W < 2) return cudaErrorInvalidValue;
+    if (W > 60 || (W & 1) || W < 2 || L > kWarpMaxRows) return cudaErrorInvalidValue;
     const int strips = (a.nx + W - 1) / W;
     dim3 grid((strips + kWarpStrips - 1) / kWarpStrips, (a.ny + L - 1) / L);
     k_fire_warp<T><<<grid, kWarpCtaThreads, 0, s>>>(a);
