@@ -178,7 +178,7 @@ struct MarchStrip {
     }
 
     __device__ __forceinline__ void load_env(int r) {
-        if (!in_rows(r, y0 - 2, y0 + La + 2) || !(m_s1[0] || m_s1[1])) return;
+        r = min(max(r, 0), ny - 1);
         const size_t rowb = (size_t)r * nx;
         if (vec) {
             const int xc = min(max(xa, 0), nx - 2);
@@ -285,9 +285,10 @@ struct MarchStrip {
             const int r = k + 3;
             cur_psi = pf_psi;
             if (r >= y0 - 3 && r < y0 + La + 3) sm.S0[s3 * NT + c] = cur_psi;
-            const int rn = k + 4;
-            if (in_rows(rn, y0 - 3, y0 + La + 3))
-                pf_psi = ld2(static_cast<const T *>(a.psi_in), rn);
+            // unconditional prefetches (rows outside the domain from the
+            // nearest inside row, never used), so that a loaded register is
+            // not merged with its older value when the load arrives
+            pf_psi = ld2(static_cast<const T *>(a.psi_in), min(max(k + 4, 0), ny - 1));
         }
         // ---- B: stage 1 on row k+2 (its environment is carried to C)
         const int eb_cls0 = e_cls[0], eb_cls1 = e_cls[1];
@@ -486,8 +487,7 @@ struct MarchStrip {
             }
         }
         // prefetch F^n of row k for the next iteration's quadrature
-        if (k >= y0 && k < y0 + La && (m_out[0] || m_out[1]))
-            pf_F = ld2(static_cast<const T *>(a.F_in), k);
+        pf_F = ld2(static_cast<const T *>(a.F_in), min(max(k, 0), ny - 1));
         bool band_end = false;
         if (drow) {
             if (++bcnt == sry) {

@@ -251,18 +251,20 @@ struct WarpStrip {
         envC = envB;
         envPre = envB;
         const T *psi_in = static_cast<const T *>(a.psi_in);
+        // unconditional loads (rows outside the domain from the nearest
+        // inside row: their values are never used), so that the loaded
+        // registers are not merged with older values when they arrive
         auto load_psi = [&](int r, V &v, T &hl, T &hr) {
-            if (r >= 0 && r < ny) {
-                v = ld(psi_in, r);
-                const size_t g = (size_t)r * nx;
-                if (lane == 0) hl = psi_in[g + min(max(xa - 1, 0), nx - 1)];
-                if (lane == 31) hr = psi_in[g + min(max(xa + 2, 0), nx - 1)];
-            }
+            r = min(max(r, 0), ny - 1);
+            v = ld(psi_in, r);
+            const size_t g = (size_t)r * nx;
+            if (lane == 0) hl = psi_in[g + max(xa - 1, 0)];
+            if (lane == 31) hr = psi_in[g + min(xa + 2, nx - 1)];
         };
         load_psi(kb, P0, hl1, hr1);  // hl1/hr1 of row kb are not used
         load_psi(kb + 1, P1, hl1, hr1);
         load_psi(kb + 2, Ppre, hlp, hrp);
-        if (kb + 1 >= 0 && kb + 1 < ny) load_env(kb + 1, envPre);
+        load_env(min(max(kb + 1, 0), ny - 1), envPre);
 
 #pragma unroll 1
         for (int k = kb; k <= ke; ++k) {
@@ -270,12 +272,12 @@ struct WarpStrip {
             P2 = Ppre;
             hl2 = hlp;
             hr2 = hrp;
-            if (k + 3 <= ke + 2) load_psi(k + 3, Ppre, hlp, hrp);
+            load_psi(k + 3, Ppre, hlp, hrp);
             // ---- B: stage 1 on row k+1
             const int rB = k + 1;
             envB = envPre;
             decode(envB);
-            if (rB + 1 >= 0 && rB + 1 < ny && rB + 1 <= ke + 1) load_env(rB + 1, envPre);
+            load_env(min(max(rB + 1, 0), ny - 1), envPre);
             if (rB >= 0 && rB < ny) {
                 wind(rB, envB.un, envB.vn);
                 poison = fma2(envB.un, splat<V>(T(0)), poison);
@@ -349,7 +351,7 @@ struct WarpStrip {
                 quadrature(rD, Nm2, Nm1, N0, Dm2, Dm1, D0, Fpre);
             }
             // F^n of row k for the next iteration's quadrature
-            if (k >= y0 && k < y0 + La) Fpre = ld(static_cast<const T *>(a.F_in), k);
+            Fpre = ld(static_cast<const T *>(a.F_in), min(max(k, 0), ny - 1));
             // ---- rotate
             P0 = P1;
             P1 = P2;
