@@ -50,7 +50,7 @@ KERNEL_SOURCES = ["paper_1102_1343_gb300/csrc/march_kernel.cuh",
                   "paper_1102_1343_gb300/csrc/fire_device.cuh",
                   "paper_1102_1343_gb300/csrc/fire_internal.h",
                   "paper_1102_1343_gb300/csrc/step_f32.cu"]
-PROFILE_SUMMARY = "profiles/fire_march_f32_points8200.md"
+PROFILE_SUMMARY = "profiles/fire_warp_f32_points8200.md"
 
 
 def kernel_hash() -> str:

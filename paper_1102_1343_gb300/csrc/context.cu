@@ -243,18 +243,31 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
     return FIRE_OK;
 }
 
+// marching strips of up to 248 columns (an even number) x ~60 rows
+int default_march(fire_ctx *c) {
+    if (c->g.sr_x > kMarchMaxColumns / 2) return FIRE_ERR_ARG;
+    int kx = kMarchMaxColumns / c->g.sr_x, ky = 60 / c->g.sr_y;
+    if (kx > c->g.nx_atm) kx = c->g.nx_atm;
+    if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 2;
+    if (ky < 1) ky = 1;
+    if (ky > c->g.ny_atm) ky = c->g.ny_atm;
+    return configure_kernel(c, FIRE_KERNEL_MARCH, kx, ky);
+}
+
 int default_kernel(fire_ctx *c) {
-    // marching strips of up to 248 columns (an even number) x ~60 rows when
-    // the refinement allows; else 2-D tiles of ~80 x 40 (FP32) / 40 x 40
-    // (FP64) nodes
-    if (c->g.sr_x <= kMarchMaxColumns / 2) {
-        int kx = kMarchMaxColumns / c->g.sr_x, ky = 60 / c->g.sr_y;
+    // FP32: warp strips of up to 60 columns (an even number) x ~160 rows
+    // when the refinement allows; then marching strips of up to 248 columns
+    // x ~60 rows (FP64 starts here); else 2-D tiles of ~80 x 40 (FP32) /
+    // 40 x 40 (FP64) nodes
+    if (c->prec == FIRE_FP32 && c->g.sr_x <= kWarpMaxColumns / 2) {
+        int kx = kWarpMaxColumns / c->g.sr_x, ky = 160 / c->g.sr_y;
         if (kx > c->g.nx_atm) kx = c->g.nx_atm;
-        if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 2;
+        if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 0;
         if (ky < 1) ky = 1;
         if (ky > c->g.ny_atm) ky = c->g.ny_atm;
-        if (configure_kernel(c, FIRE_KERNEL_MARCH, kx, ky) == FIRE_OK) return FIRE_OK;
+        if (kx >= 1 && configure_kernel(c, FIRE_KERNEL_WARP, kx, ky) == FIRE_OK) return FIRE_OK;
     }
+    if (default_march(c) == FIRE_OK) return FIRE_OK;
     int tx = c->prec == FIRE_FP64 ? 40 : 80, tyy = 40;
     int kx = tx / c->g.sr_x, ky = tyy / c->g.sr_y;
     if (kx < 1) kx = 1;
@@ -337,6 +350,8 @@ bool ctx_ignition_active(fire_ctx *c, double t) {
 }
 
 cudaStream_t ctx_stream(const fire_ctx *c) { return c->stream; }
+
+int ctx_default_march(fire_ctx *c) { return default_march(c); }
 
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c) { return c->classes_dev; }
 

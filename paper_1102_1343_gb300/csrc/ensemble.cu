@@ -146,6 +146,7 @@ int ctx_advance(fire_ctx *c, int nsteps, double dt);
 bool ctx_ignition_active(fire_ctx *c, double t);
 cudaStream_t ctx_stream(const fire_ctx *c);
 int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
+int ctx_default_march(fire_ctx *c);
 }  // namespace wf
 
 struct fire_ensemble {
@@ -307,10 +308,8 @@ int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_d
                       d.spread_mult_dev, d.dzdx_dev, d.dzdy_dev, d.ignitions, d.n_ign, cuda_stream);
         if (r == FIRE_OK) {
             e->members.push_back(c);
-            int prc, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
-            double t;
-            ctx_info(c, &prc, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
-            if (variant != FIRE_KERNEL_MARCH) r = FIRE_ERR_ARG;  // refinement too large
+            // the persistent launch runs the marching-strip code
+            if (ctx_default_march(c) != FIRE_OK) r = FIRE_ERR_ARG;  // refinement too large
         }
     }
 #define ENS_TRY(call)                 \

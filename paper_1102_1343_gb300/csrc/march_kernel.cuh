@@ -280,6 +280,10 @@ struct MarchStrip {
         const int NT = kMarchThreads;
         // ring slots: row k+3 -> s3, k+2 -> s2, k+1 -> s1, k -> s0, k-1 -> s3, k-2 -> s2
         const int s0 = k & 3, s1 = (k + 1) & 3, s2 = (k + 2) & 3, s3 = (k + 3) & 3;
+        // F^n of row k, used by the quadrature of the next iteration: loaded
+        // here, a full iteration before the row k-1 value is used
+        const T2 Fcur = pf_F;
+        pf_F = ld2(static_cast<const T *>(a.F_in), min(max(k, 0), ny - 1));
         // ---- A: stage psi^n of row k+3, prefetch row k+4
         {
             const int r = k + 3;
@@ -471,8 +475,8 @@ struct MarchStrip {
                 if (m_out[1]) fo[g + 1] = FN.y;
             }
             // heat flux densities, only in warps where some fuel burned
-            const T dF0 = m_out[0] ? pf_F.x - Fn[0] : T(0);
-            const T dF1 = m_out[1] ? pf_F.y - Fn[1] : T(0);
+            const T dF0 = m_out[0] ? Fcur.x - Fn[0] : T(0);
+            const T dF1 = m_out[1] ? Fcur.y - Fn[1] : T(0);
             if (__any_sync(__activemask(), dF0 != T(0) || dF1 != T(0))) {
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
@@ -486,8 +490,6 @@ struct MarchStrip {
                 }
             }
         }
-        // prefetch F^n of row k for the next iteration's quadrature
-        pf_F = ld2(static_cast<const T *>(a.F_in), min(max(k, 0), ny - 1));
         bool band_end = false;
         if (drow) {
             if (++bcnt == sry) {

@@ -153,13 +153,26 @@ extern "C" int fire_step_noalloc(const fire_grid_desc *grid, const fire_fuel_cla
     a.eps = g.eps_visc;
     a.dt = dt;
 
-    // the step kernel fire_init would choose by default: marching strips when
-    // the refinement allows, 2-D tiles otherwise
+    // the step kernel fire_init would choose by default: warp strips (FP32)
+    // or marching strips when the refinement allows, 2-D tiles otherwise
     int smo = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smo, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return FIRE_ERR_CUDA;
     cudaError_t e = cudaErrorInvalidValue;
+    if (!fp64 && g.sr_x <= kWarpMaxColumns / 2) {
+        int kx = kWarpMaxColumns / g.sr_x, ky = 160 / g.sr_y;
+        if (kx > g.nx_atm) kx = g.nx_atm;
+        if ((kx * g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 0;
+        if (ky < 1) ky = 1;
+        if (ky > g.ny_atm) ky = g.ny_atm;
+        if (kx >= 1 && (long long)ky * g.sr_y <= kWarpMaxRows) {
+            a.kx = kx;
+            a.ky = ky;
+            e = launch_warp<float>(a, st);
+            return e == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
+        }
+    }
     if (g.sr_x <= kMarchMaxColumns / 2) {
         int kx = kMarchMaxColumns / g.sr_x, ky = 60 / g.sr_y;
         if (kx > g.nx_atm) kx = g.nx_atm;

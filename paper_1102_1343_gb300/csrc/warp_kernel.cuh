@@ -243,7 +243,7 @@ struct WarpStrip {
         V FA0 = P0, FA1 = P0;              // F(psi^n) rows k, k+1
         V Nm2 = P0, Nm1 = P0, N0 = P0;     // psi^{n+1} rows k-2, k-1, k
         V Dm2 = P0, Dm1 = P0, D0 = P0;     // t - t_i rows k-2, k-1, k
-        V Fpre = splat<V>(T(1));           // F^n of row k-1
+        V Fpre = splat<V>(T(1));           // F^n of row k-1 (at the top of iteration k)
         WEnv<T> envB, envC, envPre;
         envB.cls0 = envB.cls1 = 0;
         envB.zx = envB.zy = envB.un = envB.vn = P0;
@@ -269,6 +269,10 @@ struct WarpStrip {
 #pragma unroll 1
         for (int k = kb; k <= ke; ++k) {
             // ---- A: psi^n of row k+2 arrives; prefetch row k+3
+            // F^n of row k, used by the quadrature of the next iteration:
+            // loaded here, a full iteration before the row k-1 value is used
+            const V Fcur = Fpre;
+            Fpre = ld(static_cast<const T *>(a.F_in), min(max(k, 0), ny - 1));
             P2 = Ppre;
             hl2 = hlp;
             hr2 = hrp;
@@ -348,10 +352,9 @@ struct WarpStrip {
             // ---- D: fuel fraction and heat on row k-1
             const int rD = k - 1;
             if (rD >= y0 && rD < y0 + La) {
-                quadrature(rD, Nm2, Nm1, N0, Dm2, Dm1, D0, Fpre);
+                quadrature(rD, Nm2, Nm1, N0, Dm2, Dm1, D0, Fcur);
             }
             // F^n of row k for the next iteration's quadrature
-            Fpre = ld(static_cast<const T *>(a.F_in), min(max(k, 0), ny - 1));
             // ---- rotate
             P0 = P1;
             P1 = P2;
