@@ -249,6 +249,22 @@ WORKLOAD_NAMES = {"points8200": "points-fire-8200x8200 (820x820 atmos x10, 50 po
 # the GB300 arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(x: float, device, world: int) -> float:
+    """The largest value of x over the ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Cell-steps/s of the whole job: every rank advances its own replica."""
+    return cells_per_rank * steps * world / seconds
+
+
 def run_gpu(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -297,12 +313,8 @@ def run_gpu(args, rank, world):
     e1.record(stream)
     barrier()
     clk = clocks.stop() if rank == 0 else {}
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = cells * args.steps * world / (ms / 1000.0)
+    ms = max_over_ranks(e0.elapsed_time(e1), dev, world)
+    value = whole_job_rate(cells, args.steps, world, ms / 1000.0)
     status = m.status()
 
     # ---- kernel duration of the fused step kernel (events on the launching stream)
@@ -331,11 +343,8 @@ def run_gpu(args, rank, world):
     for _ in range(e2e_steps):
         pkg.fire_step_host(m.ctx, uh, vh, w.dt, hs_h, hl_h)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = cells * e2e_steps * world / float(te.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev, world)
+    e2e_value = whole_job_rate(cells, e2e_steps, world, e2e_s)
     h2d = uh.nbytes + vh.nbytes
     d2h = hs_h.nbytes + hl_h.nbytes
     final_status = m.status()
