@@ -8,6 +8,12 @@
 // alone.  The launch (with the reset of the barrier word) is captured in a
 // CUDA graph and replayed while its arguments do not change.
 //
+// Two forms of the persistent kernel: FP32 ensembles run the warp-strip code
+// of k_fire_warp, one (member, strip) item per warp, each warp loading its
+// member's class table and wind-row weights into its own slice of shared
+// memory; FP64 ensembles (or refinements above 30) run the marching-strip
+// code of k_fire_march, one item per CTA.
+//
 // The barrier's wait is bounded: a CTA that waits longer than the spin limit
 // sets the ensemble's TIMEOUT bit and an abort flag, and every CTA leaves the
 // kernel at its next barrier, so a lost CTA ends the launch with an error
@@ -23,6 +29,7 @@
 
 #include "fire_internal.h"
 #include "march_kernel.cuh"
+#include "warp_kernel.cuh"
 
 using namespace wf;
 
@@ -130,6 +137,84 @@ __global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks)
     }
 }
 
+// dynamic shared memory of the warp form: per warp a class table, its Hq
+// column, heat column sums and the wind-row weights of up to max_rows + 4 rows
+template <typename T>
+__host__ __device__ size_t ens_warp_slice(int max_rows) {
+    size_t b = (size_t)FIRE_MAX_CLASSES * 8 * sizeof(T) + (size_t)FIRE_MAX_CLASSES * sizeof(T) +
+               128 * sizeof(T);
+    b = (b + 15) & ~(size_t)15;
+    b += (size_t)(max_rows + 4) * sizeof(WRow<T>);
+    return (b + 15) & ~(size_t)15;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks)
+    k_fire_ensemble_warp(const EnsembleArgs e, int max_rows) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *slice = dyn_smem + (size_t)warp * ens_warp_slice<T>(max_rows);
+    T *lut = reinterpret_cast<T *>(slice);
+    T *lutq = lut + FIRE_MAX_CLASSES * 8;
+    T *hw = lutq + FIRE_MAX_CLASSES;
+    WRow<T> *rows = reinterpret_cast<WRow<T> *>(
+        slice + (((size_t)FIRE_MAX_CLASSES * 9 + 128) * sizeof(T) + 15 & ~(size_t)15));
+    const EnsRun run = *e.run;
+    double t = run.t0;
+    const int wid = blockIdx.x * kWarpStrips + warp, nw = gridDim.x * kWarpStrips;
+    for (int s = 0; s < run.nsteps; ++s) {
+        const int par = (run.parity0 + s) & 1;
+        for (int i = wid; i < e.n_items; i += nw) {
+            const EnsItem it = e.items[i];
+            const StepArgs &a = e.margs[2 * it.member + par];
+            // the member's class table and the wind-row weights of the strip
+            for (int k = lane; k < a.ncls; k += 32) {
+                const double *co = a.coef + (size_t)k * K_N;
+                T *l = lut + k * 8;
+                l[0] = T(co[K_S0]);
+                l[1] = T(co[K_R0]);
+                l[2] = T(co[K_B]);
+                l[3] = T(co[K_C]);
+                l[4] = T(co[K_D]);
+                l[5] = T(co[K_E]);
+                l[6] = T(co[K_TF]);
+                l[7] = T(co[K_HS]);
+                lutq[k] = T(co[K_HQ]);
+            }
+            const int La = min(a.ky * a.sry, a.ny - it.y0);
+            for (int q = lane; q < La + 4; q += 32) {
+                const int r = it.y0 - 2 + q;
+                WRow<T> w;
+                w.ju0 = w.jv0 = 0;
+                w.wyu = w.wyv = T(0);
+                if (r >= 0 && r < a.ny) {
+                    int j1;
+                    const T yr = (T(r) + T(0.5)) / T(a.sry);
+                    lin_idx<T>(yr - T(0.5), a.nya, w.ju0, j1, w.wyu);
+                    lin_idx<T>(yr, a.nya + 1, w.jv0, j1, w.wyv);
+                }
+                rows[q] = w;
+            }
+            __syncwarp();
+            WarpStrip<T> strip(a, lut, lutq, hw, rows);
+            strip.run(it.x0, it.y0, t);
+            const int stw = __reduce_or_sync(0xffffffffu, strip.st);
+            if (lane == 0 && stw) atomicOr(a.status, stw);
+            __syncwarp();  // the slice is reused by the next item
+        }
+        t = t + e.dt;
+        if (s + 1 < run.nsteps) {
+            const bool skip = (int)blockIdx.x == run.skip_block;
+            if (!grid_barrier(e.bar, run.spin_limit, skip)) return;
+        }
+    }
+    if (blockIdx.x == 0) {
+        const int pf = (run.parity0 + run.nsteps) & 1;
+        for (int m = threadIdx.x; m < e.n_members; m += blockDim.x)
+            *const_cast<double *>(e.margs[2 * m + pf].t_in) = t;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -168,6 +253,8 @@ struct fire_ensemble {
     int skip_block = -1;
     cudaGraphExec_t graph = nullptr;
     bool capture_failed = false;
+    int variant = FIRE_KERNEL_MARCH;  // member kernel: FIRE_KERNEL_MARCH or FIRE_KERNEL_WARP
+    int max_rows = 0;                 // warp form: tallest strip
     int g_nsteps = -1;
     double g_dt = 0;
     int g_grid = 0;
@@ -210,20 +297,34 @@ void ens_release(fire_ensemble *e) {
 
 // work list and launch shape for the members' current kernel configuration
 int ens_plan(fire_ensemble *e) {
+    // a captured launch holds the old work list (pointer and length): drop
+    // it, after the stream has finished with it, before the list is replaced
+    ENS_CHECK(cudaStreamSynchronize(e->stream));
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
     std::vector<EnsItem> items;
     size_t smem = 0;
+    int max_rows = 0;
     for (int m = 0; m < e->n; ++m) {
         int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
         double t;
         ctx_info(e->members[m], &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
-        if (variant != FIRE_KERNEL_MARCH) return FIRE_ERR_STATE;
+        if (variant != e->variant) return FIRE_ERR_STATE;
         const int W = kx * srx, L = ky * sry;
         for (int y0 = 0; y0 < ny; y0 += L)
             for (int x0 = 0; x0 < nx; x0 += W) items.push_back(EnsItem{m, x0, y0});
-        const size_t sm = e->prec == FIRE_FP64 ? march_smem_bytes<double>(ky, sry, ncls)
-                                               : march_smem_bytes<float>(ky, sry, ncls);
-        smem = std::max(smem, sm);
+        if (e->variant == FIRE_KERNEL_MARCH) {
+            const size_t sm = e->prec == FIRE_FP64 ? march_smem_bytes<double>(ky, sry, ncls)
+                                                   : march_smem_bytes<float>(ky, sry, ncls);
+            smem = std::max(smem, sm);
+        }
+        max_rows = std::max(max_rows, L);
     }
+    if (e->variant == FIRE_KERNEL_WARP)
+        smem = kWarpStrips * (e->prec == FIRE_FP64 ? ens_warp_slice<double>(max_rows)
+                                                   : ens_warp_slice<float>(max_rows));
     // interleave the members so that each round of the CTAs mixes sizes
     std::stable_sort(items.begin(), items.end(), [](const EnsItem &a, const EnsItem &b) {
         return a.y0 != b.y0 ? a.y0 < b.y0 : a.member < b.member;
@@ -234,26 +335,38 @@ int ens_plan(fire_ensemble *e) {
     ENS_CHECK(cudaMemcpy(e->items_dev, items.data(), sizeof(EnsItem) * items.size(),
                          cudaMemcpyHostToDevice));
     e->n_items = (int)items.size();
-    const void *fn = e->prec == FIRE_FP64 ? (const void *)k_fire_ensemble<double>
-                                          : (const void *)k_fire_ensemble<float>;
+    const void *fn;
+    int threads;
+    if (e->variant == FIRE_KERNEL_WARP) {
+        fn = e->prec == FIRE_FP64 ? (const void *)k_fire_ensemble_warp<double>
+                                  : (const void *)k_fire_ensemble_warp<float>;
+        threads = kWarpCtaThreads;
+    } else {
+        fn = e->prec == FIRE_FP64 ? (const void *)k_fire_ensemble<double>
+                                  : (const void *)k_fire_ensemble<float>;
+        threads = kMarchThreads;
+    }
     {
         // the limit is a property of the kernel function shared by all ensembles
         static std::mutex mu;
-        static size_t current[2] = {0, 0};
+        static size_t current[4] = {0, 0, 0, 0};
         std::lock_guard<std::mutex> lock(mu);
-        size_t &cur = current[e->prec == FIRE_FP64 ? 1 : 0];
+        size_t &cur = current[(e->prec == FIRE_FP64 ? 1 : 0) + (e->variant == FIRE_KERNEL_WARP ? 2 : 0)];
         if (smem > cur) {
             ENS_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             cur = smem;
         }
     }
     int per_sm = 0, dev = 0, sms = 0;
-    ENS_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMarchThreads, smem));
+    ENS_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
     ENS_CHECK(cudaGetDevice(&dev));
     ENS_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (per_sm < 1) return FIRE_ERR_ARG;
-    e->grid = std::min(e->n_items, per_sm * sms);
+    const int units = e->variant == FIRE_KERNEL_WARP ? (e->n_items + kWarpStrips - 1) / kWarpStrips
+                                                     : e->n_items;
+    e->grid = std::min(units, per_sm * sms);
     e->smem = smem;
+    e->max_rows = max_rows;
     return FIRE_OK;
 }
 
@@ -271,7 +384,7 @@ cudaError_t ens_launch(fire_ensemble *e, double dt, cudaStream_t s) {
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(e->grid);
-    cfg.blockDim = dim3(kMarchThreads);
+    cfg.blockDim = dim3(e->variant == FIRE_KERNEL_WARP ? kWarpCtaThreads : kMarchThreads);
     cfg.dynamicSmemBytes = e->smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -279,6 +392,11 @@ cudaError_t ens_launch(fire_ensemble *e, double dt, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (e->variant == FIRE_KERNEL_WARP) {
+        if (e->prec == FIRE_FP64)
+            return cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<double>, ea, e->max_rows);
+        return cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<float>, ea, e->max_rows);
+    }
     if (e->prec == FIRE_FP64) return cudaLaunchKernelEx(&cfg, k_fire_ensemble<double>, ea);
     return cudaLaunchKernelEx(&cfg, k_fire_ensemble<float>, ea);
 }
@@ -306,11 +424,22 @@ int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_d
         fire_ctx *c = nullptr;
         r = fire_init(&c, &d.grid, d.classes, d.n_classes, d.fuel_class_dev, nullptr,
                       d.spread_mult_dev, d.dzdx_dev, d.dzdy_dev, d.ignitions, d.n_ign, cuda_stream);
-        if (r == FIRE_OK) {
-            e->members.push_back(c);
-            // the persistent launch runs the marching-strip code
-            if (ctx_default_march(c) != FIRE_OK) r = FIRE_ERR_ARG;  // refinement too large
+        if (r == FIRE_OK) e->members.push_back(c);
+    }
+    // the warp form when every member took the warp kernel (FP32, refinement
+    // <= 30), else the marching form for all
+    if (r == FIRE_OK) {
+        bool warp = prec == FIRE_FP32;
+        for (fire_ctx *c : e->members) {
+            int prc, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+            double t;
+            ctx_info(c, &prc, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
+            warp = warp && variant == FIRE_KERNEL_WARP;
         }
+        e->variant = warp ? FIRE_KERNEL_WARP : FIRE_KERNEL_MARCH;
+        if (!warp)
+            for (fire_ctx *c : e->members)
+                if (r == FIRE_OK && ctx_default_march(c) != FIRE_OK) r = FIRE_ERR_ARG;
     }
 #define ENS_TRY(call)                 \
     do {                              \
@@ -474,9 +603,12 @@ int fire_ensemble_set_kernel(fire_ensemble *e, int strip_columns, int strip_rows
         int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
         double t;
         ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
-        int kxn = std::max(1, strip_columns / srx), kyn = std::max(1, strip_rows / sry);
+        const int maxw = e->variant == FIRE_KERNEL_WARP ? kWarpMaxColumns : kMarchMaxColumns;
+        int kxn = std::max(1, std::min(strip_columns, maxw) / srx);
+        int kyn = std::max(1, strip_rows / sry);
         if ((kxn * srx) & 1) kxn = kxn > 1 ? kxn - 1 : 2;
-        int r = fire_set_kernel(c, FIRE_KERNEL_MARCH, kxn, kyn);
+        if (e->variant == FIRE_KERNEL_WARP && kyn * sry > kWarpMaxRows) kyn = kWarpMaxRows / sry;
+        int r = fire_set_kernel(c, e->variant, kxn, kyn);
         if (r) return r;
     }
     return ens_plan(e);
@@ -528,16 +660,21 @@ int fire_ensemble_autotune(fire_ensemble *e, int probe_steps, double dt,
         }
         return (int)FIRE_OK;
     };
-    const int cols[] = {40, 80, 120, 160, 200, 240};
-    const int rows[] = {20, 40, 80, 160, 320};
+    const int cols_m[] = {40, 80, 120, 160, 200, 240}, rows_m[] = {20, 40, 80, 160, 320};
+    const int cols_w[] = {20, 30, 40, 50, 60, 60}, rows_w[] = {40, 80, 160, 256, 320};
+    const bool wv = e->variant == FIRE_KERNEL_WARP;
+    const int *cols = wv ? cols_w : cols_m, *rows = wv ? rows_w : rows_m;
     cudaEvent_t a, b;
     ENS_CHECK(cudaEventCreate(&a));
     ENS_CHECK(cudaEventCreate(&b));
     float best = 0.f;
     int bc = 0, br = 0;
     int r = FIRE_OK;
-    for (int C : cols) {
-        for (int R : rows) {
+    for (int ci = 0; ci < 6; ++ci) {
+        const int C = cols[ci];
+        if (ci > 0 && C == cols[ci - 1]) continue;
+        for (int ri = 0; ri < 5; ++ri) {
+            const int R = rows[ri];
             if (fire_ensemble_set_kernel(e, C, R) != FIRE_OK) continue;
             if ((r = restore())) break;
             if ((r = fire_ensemble_step(e, probe_steps, dt, wind_u_dev, wind_v_dev, nullptr,

@@ -86,7 +86,7 @@ def test_ensemble_autotune(pkg):
         for x, y in zip(a[:3], b[:3]):
             assert np.array_equal(x, y)
         assert a[3] == b[3]
-    assert 40 <= cols <= 240 and 20 <= rows <= 320
+    assert 20 <= cols <= 240 and 20 <= rows <= 320
     pkg.fire_ensemble_step(ens, 10, ws[0].dt, us, vs)
     code, per = pkg.fire_ensemble_status(ens, len(ws))
     assert code == pkg.FIRE_OK, per
