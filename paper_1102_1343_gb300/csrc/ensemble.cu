@@ -43,7 +43,8 @@ struct GridBar {
     unsigned int count;
     unsigned int gen;
     int abort;
-    int status;  // ensemble-wide status bits (TIMEOUT)
+    unsigned int next[2];  // work-item counters of alternate steps
+    int status;            // ensemble-wide status bits (TIMEOUT)
 };
 
 // values that change from call to call, read by the kernel from device memory
@@ -111,9 +112,18 @@ __global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const EnsRun run = *e.run;
     double t = run.t0;
+    __shared__ int s_item;
     for (int s = 0; s < run.nsteps; ++s) {
         const int par = (run.parity0 + s) & 1;
-        for (int i = blockIdx.x; i < e.n_items; i += gridDim.x) {
+        // the counter of the next step was last used two steps ago
+        if (blockIdx.x == 0 && threadIdx.x == 0) e.bar->next[(s + 1) & 1] = 0;
+        for (;;) {
+            // items are taken dynamically, largest first (the list is sorted)
+            if (threadIdx.x == 0) s_item = (int)atomicAdd(&e.bar->next[s & 1], 1u);
+            __syncthreads();
+            const int i = s_item;
+            __syncthreads();
+            if (i >= e.n_items) break;
             const EnsItem it = e.items[i];
             const StepArgs &a = e.margs[2 * it.member + par];
             MarchSmem<T> sm;
@@ -161,10 +171,16 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks)
         slice + (((size_t)FIRE_MAX_CLASSES * 9 + 128) * sizeof(T) + 15 & ~(size_t)15));
     const EnsRun run = *e.run;
     double t = run.t0;
-    const int wid = blockIdx.x * kWarpStrips + warp, nw = gridDim.x * kWarpStrips;
     for (int s = 0; s < run.nsteps; ++s) {
         const int par = (run.parity0 + s) & 1;
-        for (int i = wid; i < e.n_items; i += nw) {
+        // the counter of the next step was last used two steps ago
+        if (blockIdx.x == 0 && threadIdx.x == 0) e.bar->next[(s + 1) & 1] = 0;
+        for (;;) {
+            // items are taken dynamically, largest first (the list is sorted)
+            int i = 0;
+            if (lane == 0) i = (int)atomicAdd(&e.bar->next[s & 1], 1u);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            if (i >= e.n_items) break;
             const EnsItem it = e.items[i];
             const StepArgs &a = e.margs[2 * it.member + par];
             // the member's class table and the wind-row weights of the strip
@@ -325,10 +341,28 @@ int ens_plan(fire_ensemble *e) {
     if (e->variant == FIRE_KERNEL_WARP)
         smem = kWarpStrips * (e->prec == FIRE_FP64 ? ens_warp_slice<double>(max_rows)
                                                    : ens_warp_slice<float>(max_rows));
-    // interleave the members so that each round of the CTAs mixes sizes
-    std::stable_sort(items.begin(), items.end(), [](const EnsItem &a, const EnsItem &b) {
-        return a.y0 != b.y0 ? a.y0 < b.y0 : a.member < b.member;
+    // largest items first (the kernel hands them out dynamically), then by
+    // row and member
+    std::vector<long long> cost(items.size());
+    for (size_t q = 0; q < items.size(); ++q) {
+        int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+        double t;
+        ctx_info(e->members[items[q].member], &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky,
+                 &ncls, &cur, &t);
+        cost[q] = (long long)std::min(kx * srx, nx - items[q].x0) * std::min(ky * sry, ny - items[q].y0);
+    }
+    std::vector<size_t> order(items.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        if (cost[a] != cost[b]) return cost[a] > cost[b];
+        if (items[a].y0 != items[b].y0) return items[a].y0 < items[b].y0;
+        return items[a].member < items[b].member;
     });
+    {
+        std::vector<EnsItem> sorted(items.size());
+        for (size_t q = 0; q < order.size(); ++q) sorted[q] = items[order[q]];
+        items.swap(sorted);
+    }
     if (e->items_dev) cudaFree(e->items_dev);
     e->items_dev = nullptr;
     ENS_CHECK(cudaMalloc(&e->items_dev, sizeof(EnsItem) * items.size()));
