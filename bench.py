@@ -277,6 +277,12 @@ def run_gpu(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only in ("adjoint", "ensemble"):
+        # one section alone (for profiler captures): its own JSON object
+        if rank == 0:
+            out = bench_adjoint(pkg, dev) if args.only == "adjoint" else bench_ensemble(pkg, dev)
+            print(json.dumps({"section": args.only, **out}), flush=True)
+        return
 
     def barrier():
         torch.cuda.synchronize()
@@ -588,6 +594,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--only", choices=["adjoint", "ensemble"], default=None,
+                    help="run one growth section alone and print its object (profiling)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the shape fire_autotune picks instead of fire_init's default")
     ap.add_argument("--no-ensemble", action="store_true")
