@@ -65,6 +65,7 @@ struct WarpStrip {
     T *hw;          // [2][64] heat column sums of this warp
     const WRow<T> *rows;  // rows y0 - 2 .. y0 + La + 1 of the CTA's strips
     int bcnt;       // rows done in the current atmospheric band
+    unsigned hist;  // bit b: some node of row k-b had psi^{n+1} <= 0 (warp vote)
     int lane, x0, y0, W, La, Wa, nx, ny, nxa, nya, srx, sry, ncm1, band;
     int xa;          // global column of the lane's first column
     bool vec;        // paired vector access (nx even)
@@ -225,6 +226,7 @@ struct WarpStrip {
         poison = splat<V>(T(0));
         acc_s = acc_q = splat<V>(T(0));
         bcnt = 0;
+        hist = 0;
         // x-weights of the wind
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -320,7 +322,9 @@ struct WarpStrip {
                 const bool na = inA && lane > 0 && N0.x <= T(0);
                 const bool nb = inB && lane < 31 && N0.y <= T(0);
                 D0 = splat<V>(T(0));
-                if (__any_sync(0xffffffffu, na || nb)) {
+                const bool burn = __any_sync(0xffffffffu, na || nb);
+                hist |= burn ? 1u : 0u;
+                if (burn) {
                     const size_t g = (size_t)rC * nx + xa;
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
@@ -354,7 +358,6 @@ struct WarpStrip {
             if (rD >= y0 && rD < y0 + La) {
                 quadrature(rD, Nm2, Nm1, N0, Dm2, Dm1, D0, Fcur);
             }
-            // F^n of row k for the next iteration's quadrature
             // ---- rotate
             P0 = P1;
             P1 = P2;
@@ -368,13 +371,24 @@ struct WarpStrip {
             Dm2 = Dm1;
             Dm1 = D0;
             envC = envB;
+            hist <<= 1;
         }
         if (!finite_val(poison.x) || !finite_val(poison.y)) st |= ST_NONFINITE;
     }
 
     __device__ __forceinline__ void quadrature(int rD, V Na, V Nb, V Nc, V Da, V Db, V Dc, V Fn) {
-        // minimum of psi^{n+1} over the 3x3 neighbourhood of each output
-        // column (in-domain values only; ghosts are never below them)
+        V F1 = splat<V>(T(1));
+        // no node of the three rows had psi^{n+1} <= 0 (the votes of stage
+        // 2 cover every column the quadrature reads): every cell fraction is
+        // 1, skip the test below
+        if ((hist & 7u) != 0u) gate(rD, Na, Nb, Nc, Da, Db, Dc, F1);
+        finish_row(rD, Fn, F1);
+    }
+
+    // minimum of psi^{n+1} over the 3x3 neighbourhood of each output column
+    // (in-domain values only; ghosts are never below them), and the full
+    // quadrature where it is negative
+    __device__ __forceinline__ void gate(int rD, V Na, V Nb, V Nc, V Da, V Db, V Dc, V &F1) {
         const T big = T(1e30);
         T va = min_val(min_val(Na.x, Nb.x), Nc.x), vb = min_val(min_val(Na.y, Nb.y), Nc.y);
         if (rD == 0) {
@@ -390,7 +404,6 @@ struct WarpStrip {
         sides(mk2(va, vb), vl, vr);
         const T ma = min_val(min_val(vl, va), vb), mb = min_val(min_val(va, vb), vr);
         const bool ba = outA && ma < T(0), bb = outB && mb < T(0);
-        V F1 = splat<V>(T(1));
         if (__any_sync(0xffffffffu, ba || bb)) {
             // full quadrature: neighbours of three rows of psi and t - t_i
             T pl[3], pr[3], dl[3], dr[3];
@@ -461,6 +474,11 @@ struct WarpStrip {
                 else F1.y = f;
             }
         }
+    }
+
+    // store F^{n+1} of the row, heat flux densities summed per column over
+    // the band, and the per-cell average after the band's last row
+    __device__ __forceinline__ void finish_row(int rD, V Fn, V F1) {
         const size_t g = (size_t)rD * nx + xa;
         T *fo = static_cast<T *>(a.F_out);
         if (vec && outA && outB) {
