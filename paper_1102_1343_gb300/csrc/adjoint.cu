@@ -46,6 +46,7 @@ bool ctx_ignition_active(fire_ctx *c, double t);
 cudaStream_t ctx_stream(const fire_ctx *c);
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c);
 int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
+cudaGraphExec_t *ctx_adjoint_graphs(fire_ctx *c, unsigned long long **keys);
 
 namespace {
 
@@ -62,7 +63,8 @@ struct AdjArgs {
     const double *coef, *dcoef;  // [ncls][K_N]
     int ncls;
     const double *tign0, *tign, *tobs;
-    double ts, ts1, dt;
+    const double *tsp;  // [2] start and end time of the step (device)
+    double dt;
     double *lam, *mu, *ls;
     const double *Cin;  // contributions gathered by this kernel [5][n]
     double *Cout;       // contributions written by this kernel [5][n]
@@ -228,7 +230,7 @@ __device__ __forceinline__ bool crossed(const AdjArgs<T> &a, size_t k, double &q
     if (!isinf(t0) || !isfinite(ti) || !isfinite(to)) return false;
     q0 = (double)a.pa[k];
     q1 = (double)a.pb[k];
-    if (!(q0 > 0.0 && q1 <= 0.0 && ti >= a.ts && ti <= a.ts1)) return false;
+    if (!(q0 > 0.0 && q1 <= 0.0 && ti >= a.tsp[0] && ti <= a.tsp[1])) return false;
     r = ti - to;
     return true;
 }
@@ -488,6 +490,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t o_t0 = take(n * sizeof(double));
     const size_t o_ts = take(n * sizeof(double));
     const size_t o_times = take((nsteps + 2) * sizeof(double));
+    const size_t o_tseg = take((K + 2) * sizeof(double));
     const size_t o_small = take(16 + kMisfitBlocks * sizeof(double) + 16);
     const size_t o_lam = take(3 * n * sizeof(double));
     const size_t o_C = take(10 * n * sizeof(double));
@@ -506,6 +509,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     double *tign0 = reinterpret_cast<double *>(ws + o_t0);
     double *tsc = reinterpret_cast<double *>(ws + o_ts);
     double *tdev = reinterpret_cast<double *>(ws + o_times);
+    double *tseg = reinterpret_cast<double *>(ws + o_tseg);
     double *Jdev = reinterpret_cast<double *>(ws + o_small);
     int *stdev = reinterpret_cast<int *>(ws + o_small + 8);
     double *part = reinterpret_cast<double *>(ws + o_small + 16);
@@ -597,48 +601,103 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t want = (n + kAdjThreads - 1) / kAdjThreads;
     const int grid = (int)(want < (size_t)sms * 8 ? want : (size_t)sms * 8);
 
-    for (int q = nseg - 1; q >= 0; --q) {
-        const int s0 = q * K, s1 = (q + 1) * K <= nsteps ? (q + 1) * K : nsteps;
-        auto state = [&](int s) -> T * {
-            return s == s0 ? ck + (size_t)q * n : ring + (size_t)(s - s0) * n;
-        };
-        // recompute psi^{s0+1..s1} with the forward's step kernel
-        ADJ_CHECK(cudaMemcpyAsync(tsc, tign0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        for (int s = s0; s < s1; ++s) {
+    // One segment: ring slot 0 holds its checkpoint and tseg its step times,
+    // so every segment of a given length issues the same launches: the
+    // recomputed states psi^{1..len} with the forward's step kernel, then the
+    // reverse steps.  They are captured once per length in a CUDA graph (kept
+    // by the context while the key below is unchanged) and replayed.
+    auto issue_segment = [&](int len, cudaStream_t cs) -> cudaError_t {
+        for (int j = 0; j < len; ++j) {
             StepArgs ra = sa;
-            ra.psi_in = state(s);
-            ra.psi_out = state(s + 1);
-            ra.F_in = Fs + (size_t)(s & 1) * n;
-            ra.F_out = Fs + (size_t)((s + 1) & 1) * n;
+            ra.psi_in = ring + (size_t)j * n;
+            ra.psi_out = ring + (size_t)(j + 1) * n;
+            ra.F_in = Fs + (size_t)(j & 1) * n;
+            ra.F_out = Fs + (size_t)((j + 1) & 1) * n;
             ra.tign = tsc;
             ra.heat_s = nullptr;
             ra.heat_l = nullptr;
             ra.status = stdev;
-            ra.t_in = tdev + s;
-            ra.t_out = tdev + nsteps + 1;
+            ra.t_in = tseg + j;
+            ra.t_out = tseg + K + 1;
             ra.dt = dt;
-            cudaError_t e = variant == FIRE_KERNEL_MARCH  ? launch_march<T>(ra, st)
-                            : variant == FIRE_KERNEL_WARP ? launch_warp<T>(ra, st)
-                                                          : launch_step<T>(ra, st);
-            ADJ_CHECK(e);
+            cudaError_t e = variant == FIRE_KERNEL_MARCH  ? launch_march<T>(ra, cs)
+                            : variant == FIRE_KERNEL_WARP ? launch_warp<T>(ra, cs)
+                                                          : launch_step<T>(ra, cs);
+            if (e != cudaSuccess) return e;
         }
-        for (int s = s1 - 1; s >= s0; --s) {
-            a.pa = state(s);
-            a.pb = state(s + 1);
-            a.ts = times[s];
-            a.ts1 = times[s + 1];
-            k_adj_stage1<T><<<grid, kAdjThreads, 0, st>>>(a);
-            a.X = pstar;
-            a.Cout = C1;
-            k_adj_vjp_star<T><<<grid, kAdjThreads, 0, st>>>(a);
-            a.X = a.pa;
-            a.Cin = C1;
-            a.Cout = C2;
-            k_adj_vjp_n<T><<<grid, kAdjThreads, 0, st>>>(a);
-            a.Cin = C2;
-            k_adj_finish<T><<<grid, kAdjThreads, 0, st>>>(a);
-            ADJ_CHECK(cudaGetLastError());
+        AdjArgs<T> b = a;
+        for (int j = len - 1; j >= 0; --j) {
+            b.pa = ring + (size_t)j * n;
+            b.pb = ring + (size_t)(j + 1) * n;
+            b.tsp = tseg + j;
+            b.X = nullptr;
+            b.Cin = nullptr;
+            b.Cout = nullptr;
+            k_adj_stage1<T><<<grid, kAdjThreads, 0, cs>>>(b);
+            b.X = pstar;
+            b.Cout = C1;
+            k_adj_vjp_star<T><<<grid, kAdjThreads, 0, cs>>>(b);
+            b.X = b.pa;
+            b.Cin = C1;
+            b.Cout = C2;
+            k_adj_vjp_n<T><<<grid, kAdjThreads, 0, cs>>>(b);
+            b.Cin = C2;
+            k_adj_finish<T><<<grid, kAdjThreads, 0, cs>>>(b);
         }
+        return cudaGetLastError();
+    };
+    unsigned long long *keys = nullptr;
+    cudaGraphExec_t *graphs = ctx_adjoint_graphs(c, &keys);
+    auto mix = [](unsigned long long h, unsigned long long x) {
+        return (h ^ x) * 0x100000001b3ULL + (h >> 29);
+    };
+    unsigned long long key0 = 0xcbf29ce484222325ULL;
+    const void *ptrs[] = {ws, u, v, tobs, sa.mult, sa.coef, sa.fuel, sa.dzdy, sa.dzdx, sa.tign};
+    for (const void *q : ptrs) key0 = mix(key0, (unsigned long long)(uintptr_t)q);
+    unsigned long long dtb;
+    memcpy(&dtb, &dt, sizeof dtb);
+    key0 = mix(mix(mix(mix(mix(key0, dtb), (unsigned long long)K), (unsigned long long)n),
+                   (unsigned long long)variant),
+               (unsigned long long)(sa.kx * 65536 + sa.ky));
+    key0 = mix(key0, (unsigned long long)grid);
+    for (int q = nseg - 1; q >= 0; --q) {
+        const int s0 = q * K, s1 = (q + 1) * K <= nsteps ? (q + 1) * K : nsteps;
+        const int len = s1 - s0;
+        ADJ_CHECK(cudaMemcpyAsync(ring, ck + (size_t)q * n, n * E, cudaMemcpyDeviceToDevice, st));
+        ADJ_CHECK(cudaMemcpyAsync(tseg, tdev + s0, (len + 1) * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, st));
+        ADJ_CHECK(cudaMemcpyAsync(tsc, tign0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        const int slot = len == K ? 0 : 1;
+        const unsigned long long key = mix(key0, (unsigned long long)len);
+        if (!graphs[slot] || keys[slot] != key) {
+            if (graphs[slot]) {
+                ADJ_CHECK(cudaStreamSynchronize(st));  // the old graph may be in flight
+                cudaGraphExecDestroy(graphs[slot]);
+                graphs[slot] = nullptr;
+            }
+            cudaStream_t cs;
+            ADJ_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t gr = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                e = issue_segment(len, cs);
+                cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs[slot], gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) {
+                // capture refused: issue the segment directly
+                record_cuda_error(e, "capture of an adjoint segment");
+                cudaGetLastError();
+                graphs[slot] = nullptr;
+                ADJ_CHECK(issue_segment(len, st));
+                continue;
+            }
+            keys[slot] = key;
+        }
+        ADJ_CHECK(cudaGraphLaunch(graphs[slot], st));
     }
     if (g_u || g_v) {
         double *tmp = reinterpret_cast<double *>(ws + o_wind);

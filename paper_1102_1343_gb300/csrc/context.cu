@@ -60,6 +60,9 @@ struct fire_ctx {
     // workspace of fire_adjoint (grown on demand, freed with the context)
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // captured segments of fire_adjoint (full and ragged length) and their keys
+    cudaGraphExec_t adj_graph[2] = {nullptr, nullptr};
+    unsigned long long adj_key[2] = {0, 0};
 
     // timing
     bool timing = false;
@@ -101,6 +104,8 @@ int cuda_err_at(cudaError_t e, const char *where) {
 void release(fire_ctx *c) {
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaGraphExec_t g : c->adj_graph)
+        if (g) cudaGraphExecDestroy(g);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     void *bufs[] = {c->psi[0], c->psi[1], c->frac[0], c->frac[1], c->tign, c->fuel, c->dzdx,
                     c->dzdy, c->mult, c->classes_dev, c->coef, c->status, c->tdev,
@@ -355,10 +360,20 @@ int ctx_default_march(fire_ctx *c) { return default_march(c); }
 
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c) { return c->classes_dev; }
 
+cudaGraphExec_t *ctx_adjoint_graphs(fire_ctx *c, unsigned long long **keys) {
+    *keys = c->adj_key;
+    return c->adj_graph;
+}
+
 int ctx_workspace(fire_ctx *c, size_t bytes, void **out) {
     if (bytes > c->ws_bytes) {
         if (c->ws) {
             WF_CHECK(cudaStreamSynchronize(c->stream));  // the old one may be in use
+            // captured adjoint segments point into the old workspace
+            for (int k = 0; k < 2; ++k) {
+                if (c->adj_graph[k]) cudaGraphExecDestroy(c->adj_graph[k]);
+                c->adj_graph[k] = nullptr;
+            }
             cudaFree(c->ws);
             c->ws = nullptr;
             c->ws_bytes = 0;
