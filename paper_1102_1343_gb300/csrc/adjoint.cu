@@ -60,6 +60,7 @@ struct AdjArgs {
     const uint8_t *fuel;
     const T *zx, *zy, *mult;  // mult nullable (1)
     const T *u, *v;
+    const T *unv;  // [n][2] node wind of the run (interpolated once), or null
     const double *coef, *dcoef;  // [ncls][K_N]
     int ncls;
     const double *tign0, *tign, *tobs;
@@ -124,7 +125,12 @@ __device__ __forceinline__ void node_env(const AdjArgs<T> &a, int i, int j, Node
     e.m = a.mult ? a.mult[k] : T(1);
     e.zx = a.zx[k];
     e.zy = a.zy[k];
-    wind_at<T>(a.u, a.v, a.nxa, a.nya, a.srx, a.sry, i, j, e.un, e.vn);
+    if (a.unv) {
+        e.un = a.unv[2 * k];
+        e.vn = a.unv[2 * k + 1];
+    } else {
+        wind_at<T>(a.u, a.v, a.nxa, a.nya, a.srx, a.sry, i, j, e.un, e.vn);
+    }
 }
 
 // Partial derivatives of the right-hand side of eq. (F-disc) at one node,
@@ -233,6 +239,19 @@ __device__ __forceinline__ bool crossed(const AdjArgs<T> &a, size_t k, double &q
     if (!(q0 > 0.0 && q1 <= 0.0 && ti >= a.tsp[0] && ti <= a.tsp[1])) return false;
     r = ti - to;
     return true;
+}
+
+// the node wind of the run (the wind is held constant over it), once
+template <typename T>
+__global__ void k_adj_node_wind(const AdjArgs<T> a, T *unv) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % a.nx), j = (int)(k / a.nx);
+        T un, vn;
+        wind_at<T>(a.u, a.v, a.nxa, a.nya, a.srx, a.sry, i, j, un, vn);
+        unv[2 * k] = un;
+        unv[2 * k + 1] = vn;
+    }
 }
 
 // seeds mu = lambda + dJ/dpsi^{s+1} and forms psi* = psi^s + dt F(psi^s)
@@ -495,6 +514,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t o_lam = take(3 * n * sizeof(double));
     const size_t o_C = take(10 * n * sizeof(double));
     const size_t o_g = take(4 * n * sizeof(double));
+    const size_t o_unv = take(2 * n * E);
     const size_t nu = (size_t)c_nya(c) * (c_nxa(c) + 1), nv = (size_t)(c_nya(c) + 1) * c_nxa(c);
     const size_t o_dco = take(sizeof(double) * K_N * ncls);
     const size_t o_wind = take(sizeof(double) * (nu + nv));
@@ -598,6 +618,14 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     int dev = 0, sms = 0;
     ADJ_CHECK(cudaGetDevice(&dev));
     ADJ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    {
+        T *unv = reinterpret_cast<T *>(ws + o_unv);
+        const size_t wn = (n + kAdjThreads - 1) / kAdjThreads;
+        k_adj_node_wind<T><<<(int)(wn < (size_t)sms * 8 ? wn : (size_t)sms * 8), kAdjThreads, 0,
+                             st>>>(a, unv);
+        ADJ_CHECK(cudaGetLastError());
+        a.unv = unv;
+    }
     const size_t want = (n + kAdjThreads - 1) / kAdjThreads;
     const int grid = (int)(want < (size_t)sms * 8 ? want : (size_t)sms * 8);
 
