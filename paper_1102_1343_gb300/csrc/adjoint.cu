@@ -183,7 +183,7 @@ __device__ __forceinline__ void node_partials(T p, T pl, T pr, T pd, T pu, T idx
     const T dSt_dT = (active && tp > T(0)) ? T(2) * e.co[K_D] * tp : T(0);
     // the unit normal n = c/|c|: dn/dc = (I - n n^T)/|c|
     T dS_dcx = T(0), dS_dcy = T(0);
-    if (cn2 > T(0)) {
+    if (cn2 > Mth<T>::kNormMin) {
         const T rc = T(1) / Mth<T>::sqr(cn2);
         const T dU_dcx = (e.un - U * nxv) * rc, dU_dcy = (e.vn - U * nyv) * rc;
         const T dT_dcx = (e.zx - tp * nxv) * rc, dT_dcy = (e.zy - tp * nyv) * rc;

@@ -147,12 +147,12 @@ __global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks)
     }
 }
 
-// dynamic shared memory of the warp form: per warp a class table, its Hq
-// column, heat column sums and the wind-row weights of up to max_rows + 4 rows
+// dynamic shared memory of the warp form: per warp a class table, the same
+// coefficients doubled for pair loads, the Hq column, heat column sums and
+// the wind-row weights of up to max_rows + 4 rows
 template <typename T>
 __host__ __device__ size_t ens_warp_slice(int max_rows) {
-    size_t b = (size_t)FIRE_MAX_CLASSES * 8 * sizeof(T) + (size_t)FIRE_MAX_CLASSES * sizeof(T) +
-               128 * sizeof(T);
+    size_t b = (size_t)FIRE_MAX_CLASSES * 21 * sizeof(T) + 128 * sizeof(T);
     b = (b + 15) & ~(size_t)15;
     b += (size_t)(max_rows + 4) * sizeof(WRow<T>);
     return (b + 15) & ~(size_t)15;
@@ -165,10 +165,11 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *slice = dyn_smem + (size_t)warp * ens_warp_slice<T>(max_rows);
     T *lut = reinterpret_cast<T *>(slice);
-    T *lutq = lut + FIRE_MAX_CLASSES * 8;
+    T *lut2 = lut + FIRE_MAX_CLASSES * 8;
+    T *lutq = lut2 + FIRE_MAX_CLASSES * 12;
     T *hw = lutq + FIRE_MAX_CLASSES;
     WRow<T> *rows = reinterpret_cast<WRow<T> *>(
-        slice + (((size_t)FIRE_MAX_CLASSES * 9 + 128) * sizeof(T) + 15 & ~(size_t)15));
+        slice + (((size_t)FIRE_MAX_CLASSES * 21 + 128) * sizeof(T) + 15 & ~(size_t)15));
     const EnsRun run = *e.run;
     double t = run.t0;
     for (int s = 0; s < run.nsteps; ++s) {
@@ -196,6 +197,8 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks)
                 l[6] = T(co[K_TF]);
                 l[7] = T(co[K_HS]);
                 lutq[k] = T(co[K_HQ]);
+                T *l2 = lut2 + k * 12;
+                for (int j = 0; j < 6; ++j) l2[2 * j] = l2[2 * j + 1] = l[j];
             }
             const int La = min(a.ky * a.sry, a.ny - it.y0);
             for (int q = lane; q < La + 4; q += 32) {
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks)
                 rows[q] = w;
             }
             __syncwarp();
-            WarpStrip<T> strip(a, lut, lutq, hw, rows);
+            WarpStrip<T> strip(a, lut, lut2, lutq, hw, rows);
             strip.run(it.x0, it.y0, t);
             const int stw = __reduce_or_sync(0xffffffffu, strip.st);
             if (lane == 0 && stw) atomicOr(a.status, stw);

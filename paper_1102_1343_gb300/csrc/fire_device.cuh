@@ -20,17 +20,47 @@ namespace wf {
 template <typename T>
 struct Mth;
 
+// FP32: the hardware approximations of log2, 2^x, sqrt and 1/sqrt (PTX
+// .approx, a few ulp) with subnormal inputs and results flushed to zero, one
+// instruction each and no rescaling of subnormals around them
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_ftz(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <>
 struct Mth<float> {
     static constexpr float kGradZero = 1e-6f;
-    static __device__ __forceinline__ float pw(float x, float b) { return __powf(x, b); }
+    // smallest squared norm that unit() normalises (below it the vector is
+    // scaled by 1/sqrt of this value and stays shorter than one)
+    static constexpr float kNormMin = 1.17549435e-38f;
+    // x^b for x >= 0 and b > 0 (the wind exponent of Table 2, 1 for
+    // chaparral): 2^(b log2 x), and 2^-inf = 0 at x = 0
+    static __device__ __forceinline__ float pw(float x, float b) { return ex2_ftz(b * lg2_ftz(x)); }
     static __device__ __forceinline__ float ex(float x) { return __expf(x); }
     static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float sqr(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+    // x >= 0 (a sum of squares)
+    static __device__ __forceinline__ float sqr(float x) { return sqrt_ftz(x); }
     // unit vector of (cx, cy); zero vector when the norm vanishes
     static __device__ __forceinline__ void unit(float cx, float cy, float &nx, float &ny) {
-        float n2 = cx * cx + cy * cy;
-        float r = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+        const float n2 = fmaf(cx, cx, cy * cy);
+        const float r = rsqrt_ftz(fmaxf(n2, kNormMin));
         nx = cx * r;
         ny = cy * r;
     }
@@ -39,6 +69,7 @@ struct Mth<float> {
 template <>
 struct Mth<double> {
     static constexpr double kGradZero = 1e-9;
+    static constexpr double kNormMin = 0.0;
     static __device__ __forceinline__ double pw(double x, double b) { return pow(x, b); }
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double dv(double a, double b) { return a / b; }

@@ -132,4 +132,43 @@ __device__ __forceinline__ void coef_pair(const T *lut, int cls0, int cls1, WCoe
     }
 }
 
+// the same from a table of the six coefficients with each value twice
+// (S0 S0 R0 R0 b b c c d d e e, 16-byte aligned rows): in FP32 the three
+// 16-byte loads of class cls0 give both columns' pairs, and only where a
+// column of the warp has a class cls1 != cls0 (a fuel boundary) are the
+// second components reloaded.  Called by all 32 lanes of a warp.
+template <typename T>
+__device__ __forceinline__ void coef_pair_dup(const T *lut2, int cls0, int cls1, WCoef<T> &co) {
+    const T *l0 = lut2 + cls0 * 12;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(l0);
+        const float4 b = *reinterpret_cast<const float4 *>(l0 + 4);
+        const float4 c = *reinterpret_cast<const float4 *>(l0 + 8);
+        co.S0 = mk2(a.x, a.y);
+        co.R0 = mk2(a.z, a.w);
+        co.b = mk2(b.x, b.y);
+        co.c = mk2(b.z, b.w);
+        co.d = mk2(c.x, c.y);
+        co.e = mk2(c.z, c.w);
+    } else {
+        co.S0 = splat<typename PairT<T>::t>(l0[0]);
+        co.R0 = splat<typename PairT<T>::t>(l0[2]);
+        co.b = splat<typename PairT<T>::t>(l0[4]);
+        co.c = splat<typename PairT<T>::t>(l0[6]);
+        co.d = splat<typename PairT<T>::t>(l0[8]);
+        co.e = splat<typename PairT<T>::t>(l0[10]);
+    }
+    if (__any_sync(0xffffffffu, cls1 != cls0)) {
+        if (cls1 != cls0) {
+            const T *l1 = lut2 + cls1 * 12;
+            co.S0.y = l1[0];
+            co.R0.y = l1[2];
+            co.b.y = l1[4];
+            co.c.y = l1[6];
+            co.d.y = l1[8];
+            co.e.y = l1[10];
+        }
+    }
+}
+
 }  // namespace wf

@@ -61,6 +61,7 @@ struct WarpStrip {
     using V = typename PairT<T>::t;
     const StepArgs &a;
     const T *lut;   // [ncls][8] S0 R0 b c d e Tf Hs
+    const T *lut2;  // [ncls][12] S0 S0 R0 R0 b b c c d d e e
     const T *lutq;  // [ncls] Hq
     T *hw;          // [2][64] heat column sums of this warp
     const WRow<T> *rows;  // rows y0 - 2 .. y0 + La + 1 of the CTA's strips
@@ -81,12 +82,12 @@ struct WarpStrip {
     int iu0[2], iu1[2], iv0[2], iv1[2];
     T wxu[2], wxv[2];
     int ju_cur, jv_cur;
-    V UA, UB, VA, VB;
+    V UA, dU, VA, dV;  // wind of atmos rows j0 and the difference to row j0 + 1
     V acc_s, acc_q;
 
-    __device__ __forceinline__ WarpStrip(const StepArgs &args, const T *l, const T *lq, T *h,
-                                         const WRow<T> *rw)
-        : a(args), lut(l), lutq(lq), hw(h), rows(rw) {}
+    __device__ __forceinline__ WarpStrip(const StepArgs &args, const T *l, const T *l2,
+                                         const T *lq, T *h, const WRow<T> *rw)
+        : a(args), lut(l), lut2(l2), lutq(lq), hw(h), rows(rw) {}
 
     // paired load of row r at the lane's columns.  Every lane loads, columns
     // outside the domain from the nearest inside one (their values are never
@@ -125,7 +126,7 @@ struct WarpStrip {
     }
 
     __device__ __forceinline__ void coef(const WEnv<T> &e, WCoef<T> &co) const {
-        coef_pair<T>(lut, e.cls0, e.cls1, co);
+        coef_pair_dup<T>(lut2, e.cls0, e.cls1, co);
     }
 
     // x-interpolated wind of atmos row J at this lane's columns
@@ -140,23 +141,27 @@ struct WarpStrip {
                    (T(1) - wxv[1]) * __ldg(v + iv0[1]) + wxv[1] * __ldg(v + iv1[1]));
     }
 
-    // bilinear wind at fire row r (Sect. 5), rows of the atmos wind cached
+    // bilinear wind at fire row r (Sect. 5), rows of the atmos wind cached;
+    // a non-finite wind value sets the poison when its row is loaded
     __device__ __forceinline__ void wind(int r, V &un, V &vn) {
         const WRow<T> w = rows[r - (y0 - 2)];
         const int ju0 = w.ju0, jv0 = w.jv0, ju1 = nya == 1 ? ju0 : ju0 + 1, jv1 = jv0 + 1;
-        const T wyu = w.wyu, wyv = w.wyv;
         if (ju0 != ju_cur) {
             UA = wind_u_row(ju0);
-            UB = ju1 == ju0 ? UA : wind_u_row(ju1);
+            const V UB = ju1 == ju0 ? UA : wind_u_row(ju1);
+            poison = fma2(UB, splat<V>(T(0)), fma2(UA, splat<V>(T(0)), poison));
+            dU = sub2(UB, UA);
             ju_cur = ju0;
         }
         if (jv0 != jv_cur) {
             VA = wind_v_row(jv0);
-            VB = wind_v_row(jv1);
+            const V VB = wind_v_row(jv1);
+            poison = fma2(VB, splat<V>(T(0)), fma2(VA, splat<V>(T(0)), poison));
+            dV = sub2(VB, VA);
             jv_cur = jv0;
         }
-        un = mk2((T(1) - wyu) * UA.x + wyu * UB.x, (T(1) - wyu) * UA.y + wyu * UB.y);
-        vn = mk2((T(1) - wyv) * VA.x + wyv * VB.x, (T(1) - wyv) * VA.y + wyv * VB.y);
+        un = mk2(fma(w.wyu, dU.x, UA.x), fma(w.wyu, dU.y, UA.y));
+        vn = mk2(fma(w.wyv, dV.x, VA.x), fma(w.wyv, dV.y, VA.y));
     }
 
     // horizontal neighbours of a row of pairs: left of .x, right of .y
@@ -286,8 +291,6 @@ struct WarpStrip {
             load_env(min(max(rB + 1, 0), ny - 1), envPre);
             if (rB >= 0 && rB < ny) {
                 wind(rB, envB.un, envB.vn);
-                poison = fma2(envB.un, splat<V>(T(0)), poison);
-                poison = fma2(envB.vn, splat<V>(T(0)), poison);
                 V L, R, D, U;
                 stencil(P0, P1, P2, rB, true, hl1, hr1, L, R, D, U);
                 WCoef<T> co;
@@ -532,6 +535,7 @@ struct WarpStrip {
 template <typename T>
 __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(const StepArgs a) {
     __shared__ __align__(16) T lut[FIRE_MAX_CLASSES * 8];
+    __shared__ __align__(16) T lut2[FIRE_MAX_CLASSES * 12];
     __shared__ T lutq[FIRE_MAX_CLASSES];
     __shared__ __align__(16) T hw[kWarpStrips][128];
     __shared__ __align__(16) WRow<T> rows[kWarpMaxRows + 4];
@@ -562,6 +566,8 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
         l[6] = T(co[K_TF]);
         l[7] = T(co[K_HS]);
         lutq[k] = T(co[K_HQ]);
+        T *l2 = lut2 + k * 12;
+        for (int j = 0; j < 6; ++j) l2[2 * j] = l2[2 * j + 1] = l[j];
     }
     __syncthreads();
     const int w = threadIdx.x >> 5;
@@ -570,7 +576,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
     const int W = a.kx * a.srx;
     const int x0 = (blockIdx.x * kWarpStrips + w) * W;
     if (x0 >= a.nx) return;  // whole warp
-    WarpStrip<T> s(a, lut, lutq, hw[w], rows);
+    WarpStrip<T> s(a, lut, lut2, lutq, hw[w], rows);
     s.run(x0, y0, tstart);
     const int stw = __reduce_or_sync(0xffffffffu, s.st);
     if ((threadIdx.x & 31) == 0 && stw) atomicOr(a.status, stw);
