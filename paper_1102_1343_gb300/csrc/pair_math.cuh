@@ -43,6 +43,26 @@ __device__ __forceinline__ V splat(T v) {
 
 __device__ __forceinline__ float max_val(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double max_val(double a, double b) { return fmax(a, b); }
+// max of three (one three-input instruction in FP32)
+__device__ __forceinline__ float max3_val(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double max3_val(double a, double b, double c) { return fmax(fmax(a, b), c); }
+
+// unit vectors of two (cx, cy): Mth::unit on pairs
+__device__ __forceinline__ void unit2(float2 cx, float2 cy, float2 &nx, float2 &ny) {
+    const float2 n2 = fma2(cx, cx, mul2(cy, cy));
+    const float2 r = make_float2(rsqrt_ftz(fmaxf(n2.x, Mth<float>::kNormMin)),
+                                 rsqrt_ftz(fmaxf(n2.y, Mth<float>::kNormMin)));
+    nx = mul2(cx, r);
+    ny = mul2(cy, r);
+}
+__device__ __forceinline__ void unit2(double2 cx, double2 cy, double2 &nx, double2 &ny) {
+    Mth<double>::unit(cx.x, cy.x, nx.x, ny.x);
+    Mth<double>::unit(cx.y, cy.y, nx.y, ny.y);
+}
 
 // coefficients of eq. (spread-WRF-Fire) for the two columns
 template <typename T>
@@ -68,10 +88,10 @@ __device__ __forceinline__ typename PairT<T>::t rhs2(
     const V dym = mul2(sub2(p, pd), idy2), dyp = mul2(sub2(pu, p), idy2);
     // Godunov (eq. Godunov): |D| = max(D-, -D+, 0) per direction
     V gx, gy;
-    gx.x = max_val(max_val(dxm.x, -dxp.x), T(0));
-    gx.y = max_val(max_val(dxm.y, -dxp.y), T(0));
-    gy.x = max_val(max_val(dym.x, -dyp.x), T(0));
-    gy.y = max_val(max_val(dym.y, -dyp.y), T(0));
+    gx.x = max3_val(dxm.x, -dxp.x, T(0));
+    gx.y = max3_val(dxm.y, -dxp.y, T(0));
+    gy.x = max3_val(dym.x, -dyp.x, T(0));
+    gy.y = max3_val(dym.y, -dyp.y, T(0));
     const V g2 = fma2(gx, gx, mul2(gy, gy));
     // central differences, zeroed at the rounding level of their values
     V ddx = sub2(pr, pl), ddy = sub2(pu, pd);
@@ -82,8 +102,7 @@ __device__ __forceinline__ typename PairT<T>::t rhs2(
     ddy.y = abs_val(ddy.y) <= z * (abs_val(pu.y) + abs_val(pd.y)) ? T(0) : ddy.y;
     const V cx = mul2(ddx, i2dx2), cy = mul2(ddy, i2dy2);
     V nxv, nyv;
-    Mth<T>::unit(cx.x, cy.x, nxv.x, nyv.x);
-    Mth<T>::unit(cx.y, cy.y, nxv.y, nyv.y);
+    unit2(cx, cy, nxv, nyv);
     const V U = fma2(un, nxv, mul2(vn, nyv));
     const V tp = fma2(zx, nxv, mul2(zy, nyv));
     // spread rate, eq. (spread-WRF-Fire)

@@ -72,9 +72,12 @@ struct WarpStrip {
     bool vec;        // paired vector access (nx even)
     bool inA, inB;   // columns inside the domain
     bool outA, outB; // output columns of this warp
+    bool pst;        // both columns are output columns and stored as a pair
+    bool slow;       // some lane of the warp stores single columns (warp-uniform)
+    int xcv, xcA, xcB;  // clamped columns of the paired / single loads
     bool xedge;      // the strip touches the left or right domain boundary
     bool bedge;      // the strip touches the boundary band in x
-    V idx2, idy2, i2dx2, i2dy2, eps2, dt2, hlf2;
+    V idx2, idy2, i2dx2, i2dy2, eps2, dt2, dth2;
     double tstart, t1, hscale;
     int st;
     V poison;
@@ -95,12 +98,8 @@ struct WarpStrip {
     // iteration later and the prefetch hides the memory latency.
     __device__ __forceinline__ V ld(const T *__restrict__ f, int r) const {
         const size_t rowb = (size_t)r * nx;
-        if (vec) {
-            const int xc = min(max(xa, 0), nx - 2);
-            return *reinterpret_cast<const V *>(f + rowb + xc);
-        }
-        const int xA = min(max(xa, 0), nx - 1), xB = min(max(xa + 1, 0), nx - 1);
-        return mk2(f[rowb + xA], f[rowb + xB]);
+        if (vec) return *reinterpret_cast<const V *>(f + rowb + xcv);
+        return mk2(f[rowb + xcA], f[rowb + xcB]);
     }
 
     // prefetch of a row's environment: raw fuel bytes (decoded by decode()
@@ -108,11 +107,10 @@ struct WarpStrip {
     __device__ __forceinline__ void load_env(int r, WEnv<T> &e) const {
         const size_t rowb = (size_t)r * nx;
         if (vec) {
-            const int xc = min(max(xa, 0), nx - 2);
-            e.cls0 = *reinterpret_cast<const uint16_t *>(a.fuel + rowb + xc);
+            e.cls0 = *reinterpret_cast<const uint16_t *>(a.fuel + rowb + xcv);
         } else {
-            e.cls0 = a.fuel[rowb + min(max(xa, 0), nx - 1)];
-            e.cls1 = a.fuel[rowb + min(max(xa + 1, 0), nx - 1)];
+            e.cls0 = a.fuel[rowb + xcA];
+            e.cls1 = a.fuel[rowb + xcB];
         }
         e.zx = ld(static_cast<const T *>(a.dzdx), r);
         e.zy = ld(static_cast<const T *>(a.dzdy), r);
@@ -213,6 +211,11 @@ struct WarpStrip {
         inB = xa + 1 >= 0 && xa + 1 < nx;
         outA = xa >= x0 && xa < x0 + Wa;
         outB = xa + 1 >= x0 && xa + 1 < x0 + Wa;
+        pst = vec && outA && outB;
+        slow = __any_sync(0xffffffffu, !pst && (outA || outB));
+        xcv = min(max(xa, 0), nx - 2);
+        xcA = min(max(xa, 0), nx - 1);
+        xcB = min(max(xa + 1, 0), nx - 1);
         xedge = x0 - 2 <= 0 || x0 + 62 >= nx - 1;
         band = a.band;
         bedge = x0 < band || x0 + Wa > nx - band;
@@ -223,7 +226,7 @@ struct WarpStrip {
         i2dy2 = splat<V>(T(1) / (T(2) * T(a.dy)));
         eps2 = splat<V>(T(a.eps));
         dt2 = splat<V>(T(a.dt));
-        hlf2 = splat<V>(T(0.5));
+        dth2 = splat<V>(T(0.5) * T(a.dt));
         tstart = tstart_;
         t1 = tstart + a.dt;
         hscale = 1.0 / (a.dt * (double)srx * (double)sry);
@@ -308,11 +311,14 @@ struct WarpStrip {
                 coef(envC, co);
                 const V F2 = rhs2<T>(Q0, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, envC.m,
                                      envC.un, envC.vn, envC.zx, envC.zy);
-                N0 = fma2(dt2, fma2(hlf2, FA0, mul2(hlf2, F2)), P0);
+                // P0 + dt (F0/2 + F2/2), the halving exact
+                N0 = fma2(dth2, add2(FA0, F2), P0);
+                // every column of the warp is computed from in-domain values,
+                // so a non-finite value anywhere in it comes from a
+                // non-finite value of the step
+                poison = fma2(N0, splat<V>(T(0)), poison);
                 const bool own_row = rC >= y0 && rC < y0 + La;
                 if (own_row) {
-                    if (outA) poison.x = fma(N0.x, T(0), poison.x);
-                    if (outB) poison.y = fma(N0.y, T(0), poison.y);
                     if (bedge || rC < band || rC >= ny - band) {
                         const bool ea = xa < band || xa >= nx - band || rC < band || rC >= ny - band;
                         const bool eb = xa + 1 < band || xa + 1 >= nx - band || rC < band ||
@@ -348,11 +354,10 @@ struct WarpStrip {
                 if (own_row) {
                     T *po = static_cast<T *>(a.psi_out);
                     const size_t g = (size_t)rC * nx + xa;
-                    if (vec && outA && outB) {
-                        *reinterpret_cast<V *>(po + g) = N0;
-                    } else {
-                        if (outA) po[g] = N0.x;
-                        if (outB) po[g + 1] = N0.y;
+                    if (pst) *reinterpret_cast<V *>(po + g) = N0;
+                    if (slow) {
+                        if (!pst && outA) po[g] = N0.x;
+                        if (!pst && outB) po[g + 1] = N0.y;
                     }
                 }
             }
@@ -484,15 +489,16 @@ struct WarpStrip {
     __device__ __forceinline__ void finish_row(int rD, V Fn, V F1) {
         const size_t g = (size_t)rD * nx + xa;
         T *fo = static_cast<T *>(a.F_out);
-        if (vec && outA && outB) {
-            *reinterpret_cast<V *>(fo + g) = F1;
-        } else {
-            if (outA) fo[g] = F1.x;
-            if (outB) fo[g + 1] = F1.y;
+        if (pst) *reinterpret_cast<V *>(fo + g) = F1;
+        if (slow) {
+            if (!pst && outA) fo[g] = F1.x;
+            if (!pst && outB) fo[g + 1] = F1.y;
         }
         // heat flux densities of the row, summed per column over the band
-        const T dFa = outA ? Fn.x - F1.x : T(0), dFb = outB ? Fn.y - F1.y : T(0);
-        if (__any_sync(0xffffffffu, dFa != T(0) || dFb != T(0))) {
+        // (the vote on every column of the warp, the sums on output columns)
+        const V dF = sub2(Fn, F1);
+        if (__any_sync(0xffffffffu, dF.x != T(0) || dF.y != T(0))) {
+            const T dFa = outA ? dF.x : T(0), dFb = outB ? dF.y : T(0);
             if (dFa != T(0)) {
                 int cls = a.fuel[g];
                 cls = cls > ncm1 ? ncm1 : cls;
