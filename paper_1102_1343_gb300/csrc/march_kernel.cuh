@@ -76,7 +76,7 @@ struct MarchCol {  // x-interpolation of the wind for one fire column
 template <typename T>
 struct MarchSmem {
     using T2 = typename Vec2<T>::type;
-    T2 *S0, *S1, *SF, *SQ, *SD;  // [4][NT] psi^n, psi*, F(psi^n), psi^{n+1}, t - t_i
+    T2 *S0, *S1, *SF, *SQ, *SD;  // [4][NT] psi^n, psi*, -F(psi^n), psi^{n+1}, t - t_i
     T2 *UX, *VX;                 // [4][NT] x-interpolated wind of 4 atmos rows (per thread)
     T *lut;                      // [ncls][8] S0 R0 b c d e Tf Hs
     T *lutq;                     // [ncls] Hq
@@ -141,7 +141,7 @@ struct MarchStrip {
     bool vec;  // paired vector access allowed (nx and x even)
     bool m_load[2], m_s1[2], m_s2[2], m_out[2];
     T dt, idx, idy, i2dx, i2dy, eps;
-    T2 dt2, idx2, idy2, i2dx2, i2dy2, eps2, hlf2;
+    T2 ndt2, idx2, idy2, i2dx2, i2dy2, eps2, ndth2;
     double tstart, t1;
     // running state
     T2 pf_psi;    // psi^n of the next row to stage
@@ -232,31 +232,9 @@ struct MarchStrip {
         vn.y = (T(1) - w.wyv) * va.y + w.wyv * vb.y;
     }
 
-    // the 5-point values of column j at row r from ring slot sr of a staged
-    // field B (down: slot sd, up: value pu given), with ghosts at the domain
-    // boundary (Sect. 3.1)
-    __device__ __forceinline__ T stage_rhs(const T2 *B, int sr, int sd, T2 up, int r, int j,
-                                           int cls, T zx, T zy, T m, T un, T vn) const {
-        const int NT = kMarchThreads;
-        const T2 own = B[sr * NT + c];
-        const T p = pick<T>(own, j);
-        T pl = j == 0 ? B[sr * NT + c - 1].y : own.x;
-        T pr = j == 0 ? own.y : B[sr * NT + c + 1].x;
-        T pd = pick<T>(B[sd * NT + c], j);
-        T pu = pick<T>(up, j);
-        const int x = xa + j;
-        if (x == 0 || x == nx - 1 || r == 0 || r == ny - 1) {
-            const T pl0 = pl, pr0 = pr, pd0 = pd, pu0 = pu;
-            if (x == 0) pl = ghost_value<T>(p, pr0);
-            if (x == nx - 1) pr = ghost_value<T>(p, pl0);
-            if (r == 0) pd = ghost_value<T>(p, pu0);
-            if (r == ny - 1) pu = ghost_value<T>(p, pd0);
-        }
-        const T *co = sm.lut + cls * 8;
-        return rhs_vals<T>(p, pl, pr, pd, pu, idx, idy, i2dx, i2dy, eps, co, m, un, vn, zx, zy);
-    }
-
-    // the same for both columns of the thread at once (pair arithmetic)
+    // the 5-point values of both columns of the thread at row r from ring
+    // slot sr of a staged field B (down: slot sd, up: value given), with
+    // ghosts at the domain boundary (Sect. 3.1), and -F there (pair arithmetic)
     __device__ __forceinline__ T2 stage_rhs2(const T2 *B, int sr, int sd, T2 up, int r, int cls0,
                                              int cls1, T2 zx, T2 zy, T2 m, T2 un, T2 vn) const {
         const int NT = kMarchThreads;
@@ -273,7 +251,7 @@ struct MarchStrip {
         }
         WCoef<T> co;
         coef_pair<T>(sm.lut, cls0 > ncm1 ? ncm1 : cls0, cls1 > ncm1 ? ncm1 : cls1, co);
-        return rhs2<T>(own, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, m, un, vn, zx, zy);
+        return neg_rhs2<T>(own, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, m, un, vn, zx, zy);
     }
 
     __device__ __forceinline__ void iter(int k) {
@@ -315,7 +293,7 @@ struct MarchStrip {
                 F.x = m_s1[0] ? F.x : T(0);
                 F.y = m_s1[1] ? F.y : T(0);
                 const T2 own = sm.S0[s2 * NT + c];
-                sm.S1[s2 * NT + c] = fma2(dt2, F, own);
+                sm.S1[s2 * NT + c] = fma2(ndt2, F, own);
                 sm.SF[s2 * NT + c] = F;
             }
         }
@@ -331,7 +309,7 @@ struct MarchStrip {
                 T2 DL;
                 const T2 F2 = stage_rhs2(sm.S1, s1, s0, up, r, eb_cls0, eb_cls1, eb_zx, eb_zy, eb_m,
                                          eb_un, eb_vn);
-                T2 PN = fma2(dt2, fma2(hlf2, f1v, mul2(hlf2, F2)), p0v);
+                T2 PN = fma2(ndth2, add2(f1v, F2), p0v);
                 PN.x = m_s2[0] ? PN.x : T(0);
                 PN.y = m_s2[1] ? PN.y : T(0);
                 bool need[2] = {m_s2[0] && PN.x <= T(0), m_s2[1] && PN.y <= T(0)};
@@ -558,13 +536,13 @@ struct MarchStrip {
         i2dx = T(1) / (T(2) * T(a.dx));
         i2dy = T(1) / (T(2) * T(a.dy));
         eps = T(a.eps);
-        dt2 = mk2(dt, dt);
+        ndt2 = mk2(-dt, -dt);
         idx2 = mk2(idx, idx);
         idy2 = mk2(idy, idy);
         i2dx2 = mk2(i2dx, i2dx);
         i2dy2 = mk2(i2dy, i2dy);
         eps2 = mk2(eps, eps);
-        hlf2 = mk2(T(0.5), T(0.5));
+        ndth2 = mk2(-(T(0.5) * dt), -(T(0.5) * dt));
         tstart = tstart_;
         t1 = tstart + a.dt;
         ncm1 = a.ncls - 1;

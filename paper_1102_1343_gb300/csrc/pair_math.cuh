@@ -1,7 +1,7 @@
 // Arithmetic on pairs of values: the two fire-mesh columns a thread holds.
 // FP32 uses the packed f32x2 instructions of sm_100 and later (one
-// instruction for both columns); FP64 works element by element.  rhs2 is the
-// right-hand side of eq. (F-disc) for such a pair.
+// instruction for both columns); FP64 works element by element.  neg_rhs2 is
+// the negated right-hand side of eq. (F-disc) for such a pair.
 #pragma once
 
 #include "fire_device.cuh"
@@ -26,7 +26,15 @@ __device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, 
 __device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rr;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rr, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
 }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -71,12 +79,17 @@ struct WCoef {
     V S0, R0, b, c, d, e;
 };
 
-// Right-hand side of eq. (F-disc) for two columns (the arithmetic of
-// rhs_vals on pairs): node values p, neighbours left / right / down / up,
-// the grid constants 1/dx, 1/dy, 1/(2dx), 1/(2dy), eps as pairs, the
-// coefficients, multiplier, node wind and terrain gradient of each column.
+// Negated right-hand side G = -F of eq. (F-disc) for two columns (the
+// arithmetic of rhs_vals on pairs): node values p, neighbours left / right /
+// down / up, the grid constants 1/dx, 1/dy, 1/(2dx), 1/(2dy), eps as pairs,
+// the coefficients, multiplier, node wind and terrain gradient of each
+// column.  With the one-sided differences D-x = (p - pl)/dx and
+// D+x = (pr - p)/dx formed as D-x and -D+x = (p - pr)/dx (likewise in y),
+// Godunov's |D| = max(D-, -D+, 0) and the Laplacian -(D-x + (-D+x)) - (...)
+// need no negated operand, and G = S (|grad psi| - eps Lap) =
+// S (|grad psi| + eps (D-x - D+x + D-y - D+y)).
 template <typename T>
-__device__ __forceinline__ typename PairT<T>::t rhs2(
+__device__ __forceinline__ typename PairT<T>::t neg_rhs2(
     typename PairT<T>::t p, typename PairT<T>::t pl, typename PairT<T>::t pr,
     typename PairT<T>::t pd, typename PairT<T>::t pu, typename PairT<T>::t idx2,
     typename PairT<T>::t idy2, typename PairT<T>::t i2dx2, typename PairT<T>::t i2dy2,
@@ -84,14 +97,14 @@ __device__ __forceinline__ typename PairT<T>::t rhs2(
     typename PairT<T>::t un, typename PairT<T>::t vn, typename PairT<T>::t zx,
     typename PairT<T>::t zy) {
     using V = typename PairT<T>::t;
-    const V dxm = mul2(sub2(p, pl), idx2), dxp = mul2(sub2(pr, p), idx2);
-    const V dym = mul2(sub2(p, pd), idy2), dyp = mul2(sub2(pu, p), idy2);
+    const V dxm = mul2(sub2(p, pl), idx2), ndxp = mul2(sub2(p, pr), idx2);
+    const V dym = mul2(sub2(p, pd), idy2), ndyp = mul2(sub2(p, pu), idy2);
     // Godunov (eq. Godunov): |D| = max(D-, -D+, 0) per direction
     V gx, gy;
-    gx.x = max3_val(dxm.x, -dxp.x, T(0));
-    gx.y = max3_val(dxm.y, -dxp.y, T(0));
-    gy.x = max3_val(dym.x, -dyp.x, T(0));
-    gy.y = max3_val(dym.y, -dyp.y, T(0));
+    gx.x = max3_val(dxm.x, ndxp.x, T(0));
+    gx.y = max3_val(dxm.y, ndxp.y, T(0));
+    gy.x = max3_val(dym.x, ndyp.x, T(0));
+    gy.y = max3_val(dym.y, ndyp.y, T(0));
     const V g2 = fma2(gx, gx, mul2(gy, gy));
     // central differences, zeroed at the rounding level of their values
     V ddx = sub2(pr, pl), ddy = sub2(pu, pd);
@@ -117,12 +130,12 @@ __device__ __forceinline__ typename PairT<T>::t rhs2(
     s.x = max_val(s.x, co.S0.x);
     s.y = max_val(s.y, co.S0.y);
     const V S = mul2(m, s);
-    const V lap = add2(sub2(dxp, dxm), sub2(dyp, dym));
+    const V nlap = add2(add2(dxm, ndxp), add2(dym, ndyp));  // -Lap
     V grad;
     grad.x = Mth<T>::sqr(g2.x);
     grad.y = Mth<T>::sqr(g2.y);
-    // -S |grad| + eps S Lap
-    return mul2(S, sub2(mul2(eps2, lap), grad));
+    // S |grad| - eps S Lap
+    return mul2(S, fma2(eps2, nlap, grad));
 }
 
 // the six coefficients of two classes from a per-class table of 8 values

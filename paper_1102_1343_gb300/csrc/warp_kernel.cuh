@@ -77,7 +77,7 @@ struct WarpStrip {
     int xcv, xcA, xcB;  // clamped columns of the paired / single loads
     bool xedge;      // the strip touches the left or right domain boundary
     bool bedge;      // the strip touches the boundary band in x
-    V idx2, idy2, i2dx2, i2dy2, eps2, dt2, dth2;
+    V idx2, idy2, i2dx2, i2dy2, eps2, ndt2, ndth2;
     double tstart, t1, hscale;
     int st;
     V poison;
@@ -225,8 +225,8 @@ struct WarpStrip {
         i2dx2 = splat<V>(T(1) / (T(2) * T(a.dx)));
         i2dy2 = splat<V>(T(1) / (T(2) * T(a.dy)));
         eps2 = splat<V>(T(a.eps));
-        dt2 = splat<V>(T(a.dt));
-        dth2 = splat<V>(T(0.5) * T(a.dt));
+        ndt2 = splat<V>(-T(a.dt));
+        ndth2 = splat<V>(-(T(0.5) * T(a.dt)));
         tstart = tstart_;
         t1 = tstart + a.dt;
         hscale = 1.0 / (a.dt * (double)srx * (double)sry);
@@ -250,7 +250,7 @@ struct WarpStrip {
         V P0 = splat<V>(T(0)), P1 = P0, P2 = P0, Ppre = P0;  // psi^n rows k, k+1, k+2, prefetch
         T hl1 = T(0), hr1 = T(0), hl2 = T(0), hr2 = T(0), hlp = T(0), hrp = T(0);
         V Qm = P0, Q0 = P0, Q1 = P0;       // psi* rows k-1, k, k+1
-        V FA0 = P0, FA1 = P0;              // F(psi^n) rows k, k+1
+        V FA0 = P0, FA1 = P0;              // -F(psi^n) rows k, k+1
         V Nm2 = P0, Nm1 = P0, N0 = P0;     // psi^{n+1} rows k-2, k-1, k
         V Dm2 = P0, Dm1 = P0, D0 = P0;     // t - t_i rows k-2, k-1, k
         V Fpre = splat<V>(T(1));           // F^n of row k-1 (at the top of iteration k)
@@ -298,9 +298,9 @@ struct WarpStrip {
                 stencil(P0, P1, P2, rB, true, hl1, hr1, L, R, D, U);
                 WCoef<T> co;
                 coef(envB, co);
-                FA1 = rhs2<T>(P1, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, envB.m, envB.un,
-                              envB.vn, envB.zx, envB.zy);
-                Q1 = fma2(dt2, FA1, P1);
+                FA1 = neg_rhs2<T>(P1, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, envB.m,
+                                  envB.un, envB.vn, envB.zx, envB.zy);
+                Q1 = fma2(ndt2, FA1, P1);
             }
             // ---- C: stage 2, crossing and t - t_i on row k
             const int rC = k;
@@ -309,10 +309,10 @@ struct WarpStrip {
                 stencil(Qm, Q0, Q1, rC, false, T(0), T(0), L, R, D, U);
                 WCoef<T> co;
                 coef(envC, co);
-                const V F2 = rhs2<T>(Q0, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, envC.m,
-                                     envC.un, envC.vn, envC.zx, envC.zy);
-                // P0 + dt (F0/2 + F2/2), the halving exact
-                N0 = fma2(dth2, add2(FA0, F2), P0);
+                const V G2 = neg_rhs2<T>(Q0, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co,
+                                         envC.m, envC.un, envC.vn, envC.zx, envC.zy);
+                // P0 + dt (F0/2 + F2/2) = P0 - dt/2 (G0 + G2), the halving exact
+                N0 = fma2(ndth2, add2(FA0, G2), P0);
                 // every column of the warp is computed from in-domain values,
                 // so a non-finite value anywhere in it comes from a
                 // non-finite value of the step
