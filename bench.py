@@ -61,10 +61,10 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(path=None):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, PROFILE_SUMMARY)
+    path = path or os.path.join(ROOT, PROFILE_SUMMARY)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -75,7 +75,7 @@ def profiled_traffic():
     if vals.get("kernel_source_hash") != kernel_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["dram_bytes_per_launch"].split()[0])
     except (KeyError, ValueError):
         return None
 
