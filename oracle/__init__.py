@@ -45,7 +45,10 @@ def build(force: bool = False) -> str:
     tmp = _LIB + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
            "-shared", _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    # with OpenMP where the compiler has it (the per-node loops over rows;
+    # results do not depend on the thread count), else single-threaded
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -100,8 +103,18 @@ def lib():
             L.orc_adjoint.restype = C.c_double
             L.orc_adjoint.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double, C.c_double,
                                       C.c_int] + [_D] * 8)
+            L.orc_set_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads(1)  # one thread unless asked (set_threads)
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's per-node loops (OpenMP builds); returns the
+    count in effect, 1 where the oracle was built without OpenMP.  The
+    results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _dp(a):

@@ -19,6 +19,12 @@
  * closed form, an exactness claim of the paper, an invariant or a brute
  * force computation, except where its comment says "parity unpinned".
  *
+ * Threads: built with OpenMP, the per-node loops of one step run over rows
+ * in parallel (orc_set_threads; one thread unless asked).  Each such loop
+ * computes every output value alone with the same operations in the same
+ * order, and the two status flags are OR-reduced, so the results do not
+ * depend on the number of threads.
+ *
  * Layout conventions: fire mesh nodes (cell centres) are indexed (i, j),
  * i = 0..nx-1 along x, j = 0..ny-1 along y, stored row-major a[j*nx + i];
  * node (i, j) sits at ((i+1/2) dx, (j+1/2) dy).  The atmospheric mesh has
@@ -29,6 +35,23 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the per-node loops; returns the count in effect (1 without
+ * OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n < 1) n = 1;
+    omp_set_num_threads(n);
+    return n;
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ */
 /* Fuel properties (Table 1), one class = 13 doubles in this order.    */
@@ -246,6 +269,7 @@ static double ghost(double p0, double p1)
 void orc_extend(int nx, int ny, const double *a, double *ext)
 {
     int W = nx + 2;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             ext[(j + 1) * W + (i + 1)] = a[j * nx + i];
@@ -282,6 +306,7 @@ void orc_wind_at_nodes(int nxa, int nya, int srx, int sry,
                        const double *u, const double *v, double *un, double *vn)
 {
     int nx = nxa * srx, ny = nya * sry;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             double xa = ((double)i + 0.5) / (double)srx;  /* atmos index units */
@@ -328,6 +353,7 @@ void orc_rhs(int nx, int ny, double dx, double dy, double eps,
              const double *dzdx, const double *dzdy, double *F)
 {
     int W = nx + 2;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             long k = (long)j * nx + i;
@@ -572,22 +598,27 @@ int orc_step(const orc_grid *g, const double *co, const double *mult,
     /* wind at the fire nodes; a non-finite wind is reported (the clamps of
      * eq. spread-WRF-Fire would otherwise read it as calm) */
     orc_wind_at_nodes(g->nxa, g->nya, g->srx, g->sry, u, v, un, vn);
+#pragma omp parallel for schedule(static) reduction(|:status)
     for (long k = 0; k < n; ++k)
         if (!isfinite(un[k]) || !isfinite(vn[k])) status |= ORC_NONFINITE;
 
     /* 2. Heun: psi* = psi + dt F(psi); psi^{n+1} = psi + dt (F(psi)/2 + F(psi*)/2) */
     orc_extend(nx, ny, psi, ext);
     orc_rhs(nx, ny, dx, dy, g->eps, ext, co, mult, un, vn, dzdx, dzdy, F1);
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) ps[k] = psi[k] + dt * F1[k];
     orc_extend(nx, ny, ps, ext);
     orc_rhs(nx, ny, dx, dy, g->eps, ext, co, mult, un, vn, dzdx, dzdy, F2);
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) pn[k] = psi[k] + dt * (0.5 * F1[k] + 0.5 * F2[k]);
 
     /* 3. ignition time at the sign change, eq. (set-ignition-time) */
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) {
         if (psi[k] > 0.0 && pn[k] <= 0.0 && isinf(tign[k]))
             tign[k] = t + psi[k] * dt / (psi[k] - pn[k]);
     }
+#pragma omp parallel for schedule(static) reduction(|:status)
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             double pv = pn[(long)j * nx + i];
@@ -596,16 +627,19 @@ int orc_step(const orc_grid *g, const double *co, const double *mult,
             if (edge && pv < 0.0) status |= ORC_BOUNDARY;
         }
     }
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) psi[k] = pn[k];
 
     /* 4. fuel fraction at t1 = t + dt */
     double t1 = t + dt;
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) th[k] = psi[k] < 0.0 ? tign[k] : t1;   /* eq. (ti-comp) */
     orc_extend(nx, ny, psi, ext);
     /* Reading: ghost ignition times copy the adjacent node's (x first, then
      * y, as for psi), then eq. (ti-comp) is applied with the ghost psi. */
     {
         int W = nx + 2;
+#pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
                 ext_t[(j + 1) * W + (i + 1)] = th[(long)j * nx + i];
@@ -617,9 +651,11 @@ int orc_step(const orc_grid *g, const double *co, const double *mult,
             ext_t[i] = ext_t[W + i];
             ext_t[(ny + 1) * W + i] = ext_t[ny * W + i];
         }
+#pragma omp parallel for schedule(static)
         for (long k = 0; k < ne; ++k)
             if (ext[k] >= 0.0) ext_t[k] = t1;
     }
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             int W = nx + 2;
@@ -635,6 +671,7 @@ int orc_step(const orc_grid *g, const double *co, const double *mult,
     }
 
     /* 5-6. heat flux densities and their average over each atmos cell */
+#pragma omp parallel for schedule(static)
     for (int J = 0; J < g->nya; ++J) {
         for (int I = 0; I < g->nxa; ++I) {
             double sh = 0.0, sl = 0.0;
@@ -650,6 +687,7 @@ int orc_step(const orc_grid *g, const double *co, const double *mult,
             heat_l[J * g->nxa + I] = sl / (double)(g->srx * g->sry);
         }
     }
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < n; ++k) frac[k] = fnew[k];
 
     free(un); free(vn); free(ext); free(F1); free(F2); free(ps); free(pn);
