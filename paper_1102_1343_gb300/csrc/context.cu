@@ -45,6 +45,7 @@ struct fire_ctx {
     int kx = 0, ky = 0;
     size_t smem = 0;
     size_t smem_max = 0;
+    int n_sm = 1;  // SMs of the device (sizes the default launch shape)
 
     // host-buffer staging
     void *stage_u = nullptr, *stage_v = nullptr;
@@ -259,22 +260,26 @@ int default_march(fire_ctx *c) {
     return configure_kernel(c, FIRE_KERNEL_MARCH, kx, ky);
 }
 
+// the warp strips of the large-mesh default (~60 x 160 nodes), FP32 only
+int default_warp_strips(fire_ctx *c) {
+    if (c->prec != FIRE_FP32 || c->g.sr_x > kWarpMaxColumns / 2) return FIRE_ERR_ARG;
+    int kx = kWarpMaxColumns / c->g.sr_x, ky = 160 / c->g.sr_y;
+    if (kx > c->g.nx_atm) kx = c->g.nx_atm;
+    if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 0;
+    if (ky < 1) ky = 1;
+    if (ky > c->g.ny_atm) ky = c->g.ny_atm;
+    if (kx < 1) return FIRE_ERR_ARG;
+    return configure_kernel(c, FIRE_KERNEL_WARP, kx, ky);
+}
+
 int default_kernel(fire_ctx *c) {
-    // FP32: warp strips of up to 60 columns (an even number) x ~160 rows
-    // when the refinement allows; then marching strips of up to 248 columns
-    // x ~60 rows (FP64 starts here); else 2-D tiles of ~80 x 40 (FP32) /
-    // 40 x 40 (FP64) nodes
-    if (c->prec == FIRE_FP32 && c->g.sr_x <= kWarpMaxColumns / 2) {
-        int kx = kWarpMaxColumns / c->g.sr_x, ky = 160 / c->g.sr_y;
-        if (kx > c->g.nx_atm) kx = c->g.nx_atm;
-        if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 0;
-        if (ky < 1) ky = 1;
-        if (ky > c->g.ny_atm) ky = c->g.ny_atm;
-        if (kx >= 1 && configure_kernel(c, FIRE_KERNEL_WARP, kx, ky) == FIRE_OK) return FIRE_OK;
-    }
-    if (default_march(c) == FIRE_OK) return FIRE_OK;
-    int tx = c->prec == FIRE_FP64 ? 40 : 80, tyy = 40;
-    int kx = tx / c->g.sr_x, ky = tyy / c->g.sr_y;
+    const DefaultShape d = default_shape(c->prec == FIRE_FP64, c->g.nx_atm, c->g.ny_atm,
+                                         c->g.sr_x, c->g.sr_y, c->n_sm);
+    if (configure_kernel(c, d.variant, d.kx, d.ky) == FIRE_OK) return FIRE_OK;
+    // a strip shape whose shared memory does not fit: 2-D tiles, halved until
+    // they fit
+    int kx = d.variant == FIRE_KERNEL_TILE ? d.kx : (c->prec == FIRE_FP64 ? 40 : 80) / c->g.sr_x;
+    int ky = d.variant == FIRE_KERNEL_TILE ? d.ky : 40 / c->g.sr_y;
     if (kx < 1) kx = 1;
     if (ky < 1) ky = 1;
     if (kx > c->g.nx_atm) kx = c->g.nx_atm;
@@ -315,6 +320,49 @@ int one_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, d
 
 // accessors used by the ensemble (ensemble.cu)
 namespace wf {
+
+static long cdiv_l(long a, long b) { return (a + b - 1) / b; }
+
+DefaultShape default_shape(bool fp64, int nx_atm, int ny_atm, int srx, int sry, int n_sm) {
+    const long nx = (long)nx_atm * srx, ny = (long)ny_atm * sry;
+    if (n_sm < 1) n_sm = 1;
+    // tallest strips (ky atmospheric rows, at most ky_max) with at least
+    // waves2/2 waves of CTAs; 0 when even one-cell strips give under a
+    // quarter wave
+    auto height = [&](long ctas_x, int ky_max, long slots, int waves2) {
+        int ky = ky_max < 1 ? 1 : (ky_max > ny_atm ? ny_atm : ky_max);
+        while (ky > 1 && 2 * ctas_x * cdiv_l(ny, (long)ky * sry) < waves2 * slots) --ky;
+        return 4 * ctas_x * cdiv_l(ny, (long)sry) < slots ? 0 : ky;
+    };
+    if (!fp64 && srx <= kWarpMaxColumns / 2) {
+        int kx = kWarpMaxColumns / srx;
+        if (kx > nx_atm) kx = nx_atm;
+        if ((kx * srx) & 1) kx = kx > 1 ? kx - 1 : 0;
+        if (kx >= 1) {
+            const long ctas_x = cdiv_l(cdiv_l(nx, (long)kx * srx), kWarpStrips);
+            const int ky = height(ctas_x, 160 / sry, (long)n_sm * kWarpCtasPerSmF32, 7);
+            if (ky >= 1) return {FIRE_KERNEL_WARP, kx, ky};
+            return {FIRE_KERNEL_TILE, 1, 1};
+        }
+    }
+    if (srx <= kMarchMaxColumns / 2) {
+        int kx = kMarchMaxColumns / srx;
+        if (kx > nx_atm) kx = nx_atm;
+        if ((kx * srx) & 1) kx = kx > 1 ? kx - 1 : 2;
+        const long ctas_x = cdiv_l(nx, (long)kx * srx);
+        const long slots = (long)n_sm * (fp64 ? kMarchCtasPerSmF64 : kMarchCtasPerSmF32);
+        const int ky = height(ctas_x, 60 / sry, slots, 5);
+        if (ky >= 1) return {FIRE_KERNEL_MARCH, kx, ky};
+        return {FIRE_KERNEL_TILE, 1, 1};
+    }
+    int kx = (fp64 ? 40 : 80) / srx, ky = 40 / sry;
+    if (kx < 1) kx = 1;
+    if (ky < 1) ky = 1;
+    if (kx > nx_atm) kx = nx_atm;
+    if (ky > ny_atm) ky = ny_atm;
+    return {FIRE_KERNEL_TILE, kx, ky};
+}
+
 int ctx_step_args(fire_ctx *c, int parity, const void *u, const void *v, double dt, double *hs,
                   double *hl, StepArgs &a) {
     const int save = c->cur;
@@ -357,6 +405,7 @@ bool ctx_ignition_active(fire_ctx *c, double t) {
 cudaStream_t ctx_stream(const fire_ctx *c) { return c->stream; }
 
 int ctx_default_march(fire_ctx *c) { return default_march(c); }
+int ctx_default_warp_strips(fire_ctx *c) { return default_warp_strips(c); }
 
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c) { return c->classes_dev; }
 
@@ -465,6 +514,7 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
     int smo = 0;
     WF_TRY(cudaDeviceGetAttribute(&smo, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     c->smem_max = (size_t)smo;
+    WF_TRY(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device));
     const size_t N = c->n, E = c->esz;
     WF_TRY(cudaMalloc(&c->psi[0], N * E));
     WF_TRY(cudaMalloc(&c->psi[1], N * E));

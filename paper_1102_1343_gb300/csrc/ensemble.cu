@@ -251,6 +251,7 @@ bool ctx_ignition_active(fire_ctx *c, double t);
 cudaStream_t ctx_stream(const fire_ctx *c);
 int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
 int ctx_default_march(fire_ctx *c);
+int ctx_default_warp_strips(fire_ctx *c);
 }  // namespace wf
 
 struct fire_ensemble {
@@ -463,20 +464,22 @@ int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_d
                       d.spread_mult_dev, d.dzdx_dev, d.dzdy_dev, d.ignitions, d.n_ign, cuda_stream);
         if (r == FIRE_OK) e->members.push_back(c);
     }
-    // the warp form when every member took the warp kernel (FP32, refinement
-    // <= 30), else the marching form for all
+    // the warp form when every member can take warp strips (FP32, refinement
+    // <= 30), else the marching form for all; members start from the
+    // large-mesh strips of that form (the persistent launch balances the
+    // items itself, whatever a member's size)
     if (r == FIRE_OK) {
         bool warp = prec == FIRE_FP32;
         for (fire_ctx *c : e->members) {
             int prc, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
             double t;
             ctx_info(c, &prc, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
-            warp = warp && variant == FIRE_KERNEL_WARP;
+            warp = warp && srx <= kWarpMaxColumns / 2;
         }
         e->variant = warp ? FIRE_KERNEL_WARP : FIRE_KERNEL_MARCH;
-        if (!warp)
-            for (fire_ctx *c : e->members)
-                if (r == FIRE_OK && ctx_default_march(c) != FIRE_OK) r = FIRE_ERR_ARG;
+        for (fire_ctx *c : e->members)
+            if (r == FIRE_OK && (warp ? ctx_default_warp_strips(c) : ctx_default_march(c)) != FIRE_OK)
+                r = FIRE_ERR_ARG;
     }
 #define ENS_TRY(call)                 \
     do {                              \

@@ -89,8 +89,29 @@ constexpr int kMarchMaxColumns = 248;  // output columns of one marching strip (
 template <typename T>
 cudaError_t launch_warp(const StepArgs &a, cudaStream_t s);
 
+constexpr int kWarpStrips = 4;       // warps (strips) per CTA of the warp kernel
 constexpr int kWarpMaxColumns = 60;  // output columns of one warp strip (even)
 constexpr int kWarpMaxRows = 512;    // output rows of one warp strip
+
+// resident CTAs per SM of the strip kernels (the minimum blocks of their
+// __launch_bounds__, checked where the kernels are defined)
+constexpr int kWarpCtasPerSmF32 = 3;
+constexpr int kMarchCtasPerSmF32 = 5;
+constexpr int kMarchCtasPerSmF64 = 2;
+
+// Default launch shape of a single run's step (fire_init and
+// fire_step_noalloc).  Strips (warp strips of <= 60 columns in FP32 when the
+// refinement allows, else marching strips of <= 248 columns) of the largest
+// height up to ~160 rows (warp) / ~60 rows (march) that still gives 3.5
+// (warp) / 2.5 (march) waves of resident CTAs on n_sm SMs, else strips one
+// atmospheric cell high; where even those fill under a quarter of one wave,
+// 2-D tiles of one atmospheric cell; for refinements too large for either
+// strip kernel, tiles of ~80x40 (FP32) / 40x40 (FP64) nodes.  The caller
+// checks the shape's shared memory and halves tiles that do not fit.
+struct DefaultShape {
+    int variant, kx, ky;
+};
+DefaultShape default_shape(bool fp64, int nx_atm, int ny_atm, int srx, int sry, int n_sm);
 
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s);

@@ -48,6 +48,9 @@ template <>
 struct MarchOccupancy<double> {
     static constexpr int blocks = 2;
 };
+static_assert(MarchOccupancy<float>::blocks == kMarchCtasPerSmF32 &&
+                  MarchOccupancy<double>::blocks == kMarchCtasPerSmF64,
+              "default launch shapes assume these");
 
 template <typename T>
 struct Vec2;

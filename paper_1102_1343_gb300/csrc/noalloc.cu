@@ -153,43 +153,35 @@ extern "C" int fire_step_noalloc(const fire_grid_desc *grid, const fire_fuel_cla
     a.eps = g.eps_visc;
     a.dt = dt;
 
-    // the step kernel fire_init would choose by default: warp strips (FP32)
-    // or marching strips when the refinement allows, 2-D tiles otherwise
-    int smo = 0, dev = 0;
+    // the step kernel fire_init would choose by default (default_shape)
+    int smo = 0, dev = 0, n_sm = 1;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smo, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        cudaDeviceGetAttribute(&smo, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return FIRE_ERR_CUDA;
+    const DefaultShape d = default_shape(fp64, g.nx_atm, g.ny_atm, g.sr_x, g.sr_y, n_sm);
     cudaError_t e = cudaErrorInvalidValue;
-    if (!fp64 && g.sr_x <= kWarpMaxColumns / 2) {
-        int kx = kWarpMaxColumns / g.sr_x, ky = 160 / g.sr_y;
-        if (kx > g.nx_atm) kx = g.nx_atm;
-        if ((kx * g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 0;
-        if (ky < 1) ky = 1;
-        if (ky > g.ny_atm) ky = g.ny_atm;
-        if (kx >= 1 && (long long)ky * g.sr_y <= kWarpMaxRows) {
-            a.kx = kx;
-            a.ky = ky;
-            e = launch_warp<float>(a, st);
-            return e == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
-        }
+    if (d.variant == FIRE_KERNEL_WARP && (long long)d.ky * g.sr_y <= kWarpMaxRows) {
+        a.kx = d.kx;
+        a.ky = d.ky;
+        e = launch_warp<float>(a, st);
+        return e == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
     }
-    if (g.sr_x <= kMarchMaxColumns / 2) {
-        int kx = kMarchMaxColumns / g.sr_x, ky = 60 / g.sr_y;
-        if (kx > g.nx_atm) kx = g.nx_atm;
-        if ((kx * g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 2;
-        if (ky < 1) ky = 1;
-        if (ky > g.ny_atm) ky = g.ny_atm;
-        a.kx = kx;
-        a.ky = ky;
-        const size_t sm = fp64 ? march_smem_bytes<double>(ky, g.sr_y, n_classes)
-                               : march_smem_bytes<float>(ky, g.sr_y, n_classes);
-        if ((long long)kx * g.sr_x <= kMarchMaxColumns && sm <= (size_t)smo) {
+    if (d.variant == FIRE_KERNEL_MARCH) {
+        const size_t sm = fp64 ? march_smem_bytes<double>(d.ky, g.sr_y, n_classes)
+                               : march_smem_bytes<float>(d.ky, g.sr_y, n_classes);
+        if ((long long)d.kx * g.sr_x <= kMarchMaxColumns && sm <= (size_t)smo) {
+            a.kx = d.kx;
+            a.ky = d.ky;
             e = fp64 ? prepare_march_kernel<double>(sm) : prepare_march_kernel<float>(sm);
             if (e == cudaSuccess) e = fp64 ? launch_march<double>(a, st) : launch_march<float>(a, st);
             return e == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
         }
     }
-    int kx = (fp64 ? 40 : 80) / g.sr_x, ky = 40 / g.sr_y;
+    // tiles: the chosen one, else the large-refinement size, halved until
+    // the shared memory fits
+    int kx = d.variant == FIRE_KERNEL_TILE ? d.kx : (fp64 ? 40 : 80) / g.sr_x;
+    int ky = d.variant == FIRE_KERNEL_TILE ? d.ky : 40 / g.sr_y;
     if (kx < 1) kx = 1;
     if (ky < 1) ky = 1;
     if (kx > g.nx_atm) kx = g.nx_atm;

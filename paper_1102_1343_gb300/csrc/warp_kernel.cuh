@@ -31,7 +31,6 @@
 
 namespace wf {
 
-constexpr int kWarpStrips = 4;  // warps (strips) per CTA
 constexpr int kWarpCtaThreads = 32 * kWarpStrips;
 
 template <typename T>
@@ -48,6 +47,7 @@ template <>
 struct WOcc<double> {
     static constexpr int blocks = 1;
 };
+static_assert(WOcc<float>::blocks == kWarpCtasPerSmF32, "default launch shapes assume this");
 
 template <typename T>
 struct WEnv {  // what stage 2 reuses from stage 1 of the same row

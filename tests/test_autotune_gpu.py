@@ -35,7 +35,10 @@ def test_autotune_keeps_state_and_parity(pkg, prec):
         assert np.array_equal(a, b)
     assert before[3] == after[3]
     assert pkg.fire_get_kernel(m.ctx) == (variant, kx, ky)
-    assert variant in (pkg.FIRE_KERNEL_TILE, pkg.FIRE_KERNEL_MARCH)
+    allowed = {pkg.FIRE_KERNEL_TILE, pkg.FIRE_KERNEL_MARCH}
+    if prec == "fp32":
+        allowed.add(pkg.FIRE_KERNEL_WARP)
+    assert variant in allowed
     assert 1 <= kx <= w.nxa and 1 <= ky <= w.nya
     m.run(30, u, v, w.dt)
     if prec == "fp64":
@@ -102,3 +105,37 @@ def test_ensemble_autotune(pkg):
             assert np.array_equal(x, y)
         single.close()
     pkg.fire_ensemble_destroy(ens)
+
+
+def _ctas(variant, kx, ky, nx, ny, srx, sry):
+    W, L = kx * srx, ky * sry
+    if variant == 2:  # warp strips, 4 per CTA
+        return -(-(-(-nx // W)) // 4) * -(-ny // L)
+    return -(-nx // W) * -(-ny // L)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_default_shape_follows_mesh_size(pkg, prec):
+    """fire_init's default: tiles of one atmospheric cell on a mesh too small
+    for strips, strips on larger ones, as tall as the waves of CTAs allow."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tiny = synth.plain_circle()
+    m = pkg.FireModel.from_workload(tiny, precision=prec)
+    assert pkg.fire_get_kernel(m.ctx) == (pkg.FIRE_KERNEL_TILE, 1, 1)
+    m.close()
+    w = synth.random_landscape(200, 200, seed=3, ignition="line", steps=1)
+    m = pkg.FireModel.from_workload(w, precision=prec)
+    variant, kx, ky = pkg.fire_get_kernel(m.ctx)
+    m.close()
+    if prec == "fp32":
+        assert (variant, kx) == (pkg.FIRE_KERNEL_WARP, 6)
+        slots, waves2, ky_max = 3 * sms, 7, 16
+    else:
+        assert (variant, kx) == (pkg.FIRE_KERNEL_MARCH, 24)
+        slots, waves2, ky_max = 2 * sms, 5, 6
+    n = _ctas(variant, kx, ky, w.nx, w.ny, 10, 10)
+    # the tallest strips with enough waves (or one atmospheric cell high)
+    assert ky == 1 or 2 * n >= waves2 * slots
+    if ky < ky_max:
+        assert 2 * _ctas(variant, kx, ky + 1, w.nx, w.ny, 10, 10) < waves2 * slots
