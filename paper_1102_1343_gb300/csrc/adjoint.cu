@@ -25,8 +25,11 @@
 // writes every node's five stencil contributions v_j dF_j/dpsi_k, the next
 // gathers them per node k, so results do not depend on scheduling.
 //
-// Precision: the state and the partial derivatives are evaluated in the
-// path precision T; adjoint fields, contributions and gradients are double.
+// Precision: the state, the partial derivatives, the adjoint fields and the
+// stencil contributions are in the path precision T (FP32 or FP64); the
+// parameter gradients, summed over the whole run, and the arrival-time seeds
+// are double.  The FP32 path thus keeps the (1/64-rate) FP64 pipe to one
+// conversion and add per gradient and node, and to the nodes that cross.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -66,12 +69,12 @@ struct AdjArgs {
     const double *tign0, *tign, *tobs;
     const double *tsp;  // [2] start and end time of the step (device)
     double dt;
-    double *lam, *mu, *ls;
-    const double *Cin;  // contributions gathered by this kernel [5][n]
-    double *Cout;       // contributions written by this kernel [5][n]
+    T *lam, *mu, *ls;
+    const T *Cin;  // contributions gathered by this kernel [5][n]
+    T *Cout;       // contributions written by this kernel [5][n]
     double *gm, *gM, *gun, *gvn;
     int nx, ny, nxa, nya, srx, sry;
-    T idx, idy, i2dx, i2dy, eps, dtT;
+    T idx, idy, i2dx, i2dy, eps, dtT, hdtT;  // dtT = dt, hdtT = dt/2 in T
     size_t n;
 };
 
@@ -91,19 +94,19 @@ __device__ __forceinline__ void stencil(const T *X, int nx, int ny, int i, int j
 
 // d(ghost)/d(p0), d(ghost)/d(p1) for the branch ghost_value takes
 template <typename T>
-__device__ __forceinline__ void ghost_partials(T p0, T p1, double &d0, double &d1) {
+__device__ __forceinline__ void ghost_partials(T p0, T p1, T &d0, T &d1) {
     const T g = p0 + (p0 - p1);
-    d0 = 2.0;
-    d1 = -1.0;
+    d0 = T(2);
+    d1 = T(-1);
     T h = g;
     if (p0 > h) {
         h = p0;
-        d0 = 1.0;
-        d1 = 0.0;
+        d0 = T(1);
+        d1 = T(0);
     }
     if (p1 > h) {
-        d0 = 0.0;
-        d1 = 1.0;
+        d0 = T(0);
+        d1 = T(1);
     }
 }
 
@@ -229,14 +232,24 @@ __device__ __forceinline__ void node_partials(T p, T pl, T pr, T pd, T pu, T idx
 // whether node k's ignition time was set in step s (the forward test of
 // eq. set-ignition-time: first crossing from > 0 to <= 0, the recorded time
 // inside the step) and the node is observed
+// (the tests that every node takes are on the bits and in T; only crossing
+// nodes compare times in double)
+__device__ __forceinline__ bool inf_bits(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) == 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
 template <typename T>
 __device__ __forceinline__ bool crossed(const AdjArgs<T> &a, size_t k, double &q0, double &q1,
                                         double &r) {
     const double t0 = a.tign0[k], ti = a.tign[k], to = a.tobs[k];
-    if (!isinf(t0) || !isfinite(ti) || !isfinite(to)) return false;
-    q0 = (double)a.pa[k];
-    q1 = (double)a.pb[k];
-    if (!(q0 > 0.0 && q1 <= 0.0 && ti >= a.tsp[0] && ti <= a.tsp[1])) return false;
+    if (!inf_bits(t0) || !finite_bits(ti) || !finite_bits(to)) return false;
+    const T p0 = a.pa[k], p1 = a.pb[k];
+    if (!(p0 > T(0) && p1 <= T(0))) return false;
+    if (!(ti >= a.tsp[0] && ti <= a.tsp[1])) return false;
+    q0 = (double)p0;
+    q1 = (double)p1;
     r = ti - to;
     return true;
 }
@@ -260,10 +273,11 @@ __global__ void k_adj_stage1(const AdjArgs<T> a) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
          k += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(k % a.nx), j = (int)(k / a.nx);
-        double mu = a.lam[k], q0, q1, r;
+        T mu = a.lam[k];
+        double q0, q1, r;
         if (crossed(a, k, q0, q1, r)) {
             const double den = q0 - q1;
-            mu += r * a.dt * q0 / (den * den);
+            mu = T((double)mu + r * a.dt * q0 / (den * den));
         }
         a.mu[k] = mu;
         NodeEnv<T> e;
@@ -279,7 +293,7 @@ __global__ void k_adj_stage1(const AdjArgs<T> a) {
 // v^T dF/dp at node k added to the parameter gradients, and the node's five
 // stencil contributions v dF/dpsi written to Cout
 template <typename T>
-__device__ __forceinline__ void vjp_node(const AdjArgs<T> &a, size_t k, int i, int j, double v) {
+__device__ __forceinline__ void vjp_node(const AdjArgs<T> &a, size_t k, int i, int j, T v) {
     NodeEnv<T> e;
     node_env(a, i, j, e);
     T p, pl, pr, pd, pu;
@@ -287,14 +301,14 @@ __device__ __forceinline__ void vjp_node(const AdjArgs<T> &a, size_t k, int i, i
     Partials<T> o;
     node_partials<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e, o);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) a.Cout[q * a.n + k] = v * (double)o.dpsi[q];
+    for (int q = 0; q < 5; ++q) a.Cout[q * a.n + k] = v * o.dpsi[q];
     const double *dc = a.dcoef + (size_t)e.cls * K_N;
-    a.gm[k] += v * (double)o.dm;
-    a.gM[k] += v * ((double)o.dS0 * dc[K_S0] + (double)o.dR0 * dc[K_R0] +
-                    (double)o.dc * dc[K_C] + (double)o.dd * dc[K_D]);
+    a.gm[k] += (double)(v * o.dm);
+    a.gM[k] += (double)(v * (o.dS0 * T(dc[K_S0]) + o.dR0 * T(dc[K_R0]) + o.dc * T(dc[K_C]) +
+                             o.dd * T(dc[K_D])));
     if (a.gun) {
-        a.gun[k] += v * (double)o.dun;
-        a.gvn[k] += v * (double)o.dvn;
+        a.gun[k] += (double)(v * o.dun);
+        a.gvn[k] += (double)(v * o.dvn);
     }
 }
 
@@ -302,16 +316,15 @@ __device__ __forceinline__ void vjp_node(const AdjArgs<T> &a, size_t k, int i, i
 // the extrapolated ghosts of the boundary rows and columns mapped back to
 // the two nodes each was extrapolated from
 template <typename T>
-__device__ __forceinline__ double gather(const AdjArgs<T> &a, const double *C, const T *X,
-                                         int i, int j) {
+__device__ __forceinline__ T gather(const AdjArgs<T> &a, const T *C, const T *X, int i, int j) {
     const int nx = a.nx, ny = a.ny;
     const size_t n = a.n, k = (size_t)j * nx + i;
-    double r = C[P_C * n + k];
+    T r = C[P_C * n + k];
     if (i > 0) r += C[P_R * n + k - 1];
     if (i < nx - 1) r += C[P_L * n + k + 1];
     if (j > 0) r += C[P_U * n + k - nx];
     if (j < ny - 1) r += C[P_D * n + k + nx];
-    double d0, d1;
+    T d0, d1;
     const size_t row = (size_t)j * nx, col = (size_t)i;
     if (i <= 1) {  // left ghost of row j = ghost(X[j][0], X[j][1])
         ghost_partials<T>(X[row], X[row + 1], d0, d1);
@@ -339,7 +352,7 @@ __global__ void k_adj_vjp_star(const AdjArgs<T> a) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
          k += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(k % a.nx), j = (int)(k / a.nx);
-        vjp_node(a, k, i, j, 0.5 * a.dt * a.mu[k]);
+        vjp_node(a, k, i, j, a.hdtT * a.mu[k]);
     }
 }
 
@@ -350,9 +363,9 @@ __global__ void k_adj_vjp_n(AdjArgs<T> a) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
          k += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(k % a.nx), j = (int)(k / a.nx);
-        const double ls = gather(a, a.Cin, a.pstar, i, j);
+        const T ls = gather(a, a.Cin, a.pstar, i, j);
         a.ls[k] = ls;
-        vjp_node(a, k, i, j, 0.5 * a.dt * a.mu[k] + a.dt * ls);
+        vjp_node(a, k, i, j, a.hdtT * a.mu[k] + a.dtT * ls);
     }
 }
 
@@ -362,11 +375,11 @@ __global__ void k_adj_finish(const AdjArgs<T> a) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
          k += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(k % a.nx), j = (int)(k / a.nx);
-        double lam = a.mu[k] + a.ls[k] + gather(a, a.Cin, a.pa, i, j);
+        T lam = a.mu[k] + a.ls[k] + gather(a, a.Cin, a.pa, i, j);
         double q0, q1, r;
         if (crossed(a, k, q0, q1, r)) {
             const double den = q0 - q1;
-            lam += r * (-a.dt * q1 / (den * den));
+            lam = T((double)lam + r * (-a.dt * q1 / (den * den)));
         }
         a.lam[k] = lam;
     }
@@ -511,8 +524,8 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t o_times = take((nsteps + 2) * sizeof(double));
     const size_t o_tseg = take((K + 2) * sizeof(double));
     const size_t o_small = take(16 + kMisfitBlocks * sizeof(double) + 16);
-    const size_t o_lam = take(3 * n * sizeof(double));
-    const size_t o_C = take(10 * n * sizeof(double));
+    const size_t o_lam = take(3 * n * E);
+    const size_t o_C = take(10 * n * E);
     const size_t o_g = take(4 * n * sizeof(double));
     const size_t o_unv = take(2 * n * E);
     const size_t nu = (size_t)c_nya(c) * (c_nxa(c) + 1), nv = (size_t)(c_nya(c) + 1) * c_nxa(c);
@@ -564,12 +577,12 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         return FIRE_OK;
     }
 
-    double *lam = reinterpret_cast<double *>(ws + o_lam);
-    double *mu = lam + n, *ls = lam + 2 * n;
-    double *C1 = reinterpret_cast<double *>(ws + o_C), *C2 = C1 + 5 * n;
+    T *lam = reinterpret_cast<T *>(ws + o_lam);
+    T *mu = lam + n, *ls = lam + 2 * n;
+    T *C1 = reinterpret_cast<T *>(ws + o_C), *C2 = C1 + 5 * n;
     double *gm = reinterpret_cast<double *>(ws + o_g);
     double *gM = gm + n, *gun = gm + 2 * n, *gvn = gm + 3 * n;
-    ADJ_CHECK(cudaMemsetAsync(lam, 0, n * sizeof(double), st));
+    ADJ_CHECK(cudaMemsetAsync(lam, 0, n * E, st));
     ADJ_CHECK(cudaMemsetAsync(gm, 0, 4 * n * sizeof(double), st));
     ADJ_CHECK(cudaMemsetAsync(Fs, 0, 2 * n * E, st));
 
@@ -612,6 +625,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     a.i2dy = T(1) / (T(2) * T(sa.dy));
     a.eps = T(sa.eps);
     a.dtT = T(dt);
+    a.hdtT = T(0.5 * dt);
     a.n = n;
     a.pstar = pstar;
 
