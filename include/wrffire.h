@@ -162,7 +162,10 @@ int fire_step(fire_ctx *ctx, const void *wind_u_dev, const void *wind_v_dev, dou
 
 /* fire_step with host buffers: copies the wind to the device, runs the step,
  * copies the heat fluxes back and waits for them.  Buffers as in fire_step
- * but on the host; heat outputs may be NULL. */
+ * but on the host; heat outputs may be NULL.  Heat outputs in page-locked
+ * host memory that the device can address (cudaHostAlloc / cudaHostRegister,
+ * e.g. torch's pin_memory) are written by the step kernel directly, with no
+ * separate copy; pageable ones go through a device buffer and a copy. */
 int fire_step_host(fire_ctx *ctx, const void *wind_u_host, const void *wind_v_host,
                    double dt, double *heat_sens_host, double *heat_lat_host);
 

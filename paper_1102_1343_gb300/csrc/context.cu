@@ -585,6 +585,18 @@ int fire_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, 
     return one_step(c, u, v, dt, hs, hl);
 }
 
+// device address of a page-locked host buffer the device can write, else
+// null (pageable memory; the failed query's error is cleared)
+static double *mapped_host(double *h) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return static_cast<double *>(at.devicePointer);
+}
+
 int fire_step_host(fire_ctx *c, const void *u, const void *v, double dt, double *hs,
                    double *hl) {
     if (!c || !u || !v || !finite_pos(dt)) return FIRE_ERR_ARG;
@@ -599,11 +611,16 @@ int fire_step_host(fire_ctx *c, const void *u, const void *v, double dt, double 
     }
     WF_CHECK(cudaMemcpyAsync(c->stage_u, u, nu, cudaMemcpyHostToDevice, c->stream));
     WF_CHECK(cudaMemcpyAsync(c->stage_v, v, nv, cudaMemcpyHostToDevice, c->stream));
-    int r = one_step(c, c->stage_u, c->stage_v, dt, hs ? c->stage_hs : nullptr,
-                     hl ? c->stage_hl : nullptr);
+    // heat written by the kernel straight into page-locked, device-mapped
+    // host buffers (visible to the host once the stream is synchronised)
+    double *hs_k = hs ? mapped_host(hs) : nullptr, *hl_k = hl ? mapped_host(hl) : nullptr;
+    int r = one_step(c, c->stage_u, c->stage_v, dt, hs ? (hs_k ? hs_k : c->stage_hs) : nullptr,
+                     hl ? (hl_k ? hl_k : c->stage_hl) : nullptr);
     if (r) return r;
-    if (hs) WF_CHECK(cudaMemcpyAsync(hs, c->stage_hs, nh, cudaMemcpyDeviceToHost, c->stream));
-    if (hl) WF_CHECK(cudaMemcpyAsync(hl, c->stage_hl, nh, cudaMemcpyDeviceToHost, c->stream));
+    if (hs && !hs_k)
+        WF_CHECK(cudaMemcpyAsync(hs, c->stage_hs, nh, cudaMemcpyDeviceToHost, c->stream));
+    if (hl && !hl_k)
+        WF_CHECK(cudaMemcpyAsync(hl, c->stage_hl, nh, cudaMemcpyDeviceToHost, c->stream));
     WF_CHECK(cudaStreamSynchronize(c->stream));
     return FIRE_OK;
 }

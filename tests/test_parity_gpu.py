@@ -178,10 +178,12 @@ def test_boundary_and_nonfinite_status(pkg):
     assert m2.status() == pkg.FIRE_ERR_NONFINITE
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_run_graph_and_host_path_equal_steps(pkg, prec):
+@pytest.mark.parametrize("prec,pinned", [("fp32", False), ("fp64", False), ("fp32", True),
+                                          ("fp64", True)])
+def test_run_graph_and_host_path_equal_steps(pkg, prec, pinned):
     """fire_run (graph replay) and fire_step_host give the same bits as a
-    sequence of fire_step calls."""
+    sequence of fire_step calls; with page-locked heat buffers the kernel
+    writes them directly, with pageable ones through a copy."""
     import torch
     w = synth.random_landscape(12, 9, seed=5, ignition="center", steps=15)
     a = pkg.FireModel.from_workload(w, precision=prec)
@@ -194,8 +196,12 @@ def test_run_graph_and_host_path_equal_steps(pkg, prec):
     dt_np = np.float64 if prec == "fp64" else np.float32
     uh = np.ascontiguousarray(w.u, dt_np)
     vh = np.ascontiguousarray(w.v, dt_np)
-    hs_c = np.zeros((w.nya, w.nxa))
-    hl_c = np.zeros((w.nya, w.nxa))
+    if pinned:
+        hs_c = torch.zeros((w.nya, w.nxa), dtype=torch.float64).pin_memory().numpy()
+        hl_c = torch.zeros((w.nya, w.nxa), dtype=torch.float64).pin_memory().numpy()
+    else:
+        hs_c = np.zeros((w.nya, w.nxa))
+        hl_c = np.zeros((w.nya, w.nxa))
     for _ in range(w.steps):
         pkg.fire_step_host(c.ctx, uh, vh, w.dt, hs_c, hl_c)
     torch.cuda.synchronize()
@@ -205,6 +211,7 @@ def test_run_graph_and_host_path_equal_steps(pkg, prec):
             assert np.array_equal(x[k], y[k])
         assert x[3] == y[3]
     assert np.array_equal(hs_a.cpu().numpy(), hs_b.cpu().numpy())
+    assert np.any(hs_c != 0.0) and np.any(hl_c != 0.0)
     assert np.array_equal(hs_a.cpu().numpy(), hs_c)
     assert np.array_equal(hl_a.cpu().numpy(), hl_c)
 
