@@ -322,3 +322,28 @@ def test_full_size_sampled_cells(pkg, name, prec, warm, tile):
             assert abs(hs[J, I] - hs_o) <= 1e-4 * Hs_max / w.dt
             assert abs(hl[J, I] - hl_o) <= 1e-4 * Hq_max / w.dt
     assert burning_cells >= 4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_multiplier_of_ones_changes_no_bit(pkg, prec):
+    """A spread multiplier of ones (loaded and multiplied per node) gives the
+    same bits as no multiplier: m = 1 multiplies exactly."""
+    w = synth.random_landscape(24, 10, seed=31, ignition="points", n_points=6, edge_margin=150.0,
+                               steps=200)
+    a = pkg.FireModel.from_workload(w, precision=prec)
+    w.mult = np.ones((w.ny, w.nx))
+    b = pkg.FireModel.from_workload(w, precision=prec)
+    for m in (a, b):
+        pkg.fire_set_kernel(m.ctx, pkg.FIRE_KERNEL_WARP, 6, 3)
+    u, v = a.wind(w.u, w.v)
+    for _ in range(w.steps):
+        hs_a, hl_a = a.step(u, v, w.dt)
+        hs_b, hl_b = b.step(u, v, w.dt)
+    sa, sb = state_np(a), state_np(b)
+    assert np.isfinite(sa[1]).sum() > 50
+    for k in range(3):
+        assert np.array_equal(sa[k], sb[k])
+    assert np.array_equal(hs_a.cpu().numpy(), hs_b.cpu().numpy())
+    assert np.array_equal(hl_a.cpu().numpy(), hl_b.cpu().numpy())
+    a.close()
+    b.close()
