@@ -70,15 +70,23 @@ template <>
 struct Mth<double> {
     static constexpr double kGradZero = 1e-9;
     static constexpr double kNormMin = 0.0;
-    static __device__ __forceinline__ double pw(double x, double b) { return pow(x, b); }
+    // x^b for x >= 0 and b > 0: pow(0, b) = 0 exactly, so x = 0 (the capped
+    // wind component on the upwind side of the front) skips the call; warps
+    // whose nodes all face away from the wind skip it entirely
+    static __device__ __forceinline__ double pw(double x, double b) {
+        return x > 0.0 ? pow(x, b) : 0.0;
+    }
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
     static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
+    // unit vector of (cx, cy) (one reciprocal of the norm, two products);
+    // zero vector when the norm vanishes
     static __device__ __forceinline__ void unit(double cx, double cy, double &nx, double &ny) {
         double n = sqrt(cx * cx + cy * cy);
         if (n > 0.0) {
-            nx = cx / n;
-            ny = cy / n;
+            const double r = 1.0 / n;
+            nx = cx * r;
+            ny = cy * r;
         } else {
             nx = 0.0;
             ny = 0.0;
