@@ -266,6 +266,19 @@ int fire_get_kernel(const fire_ctx *ctx, int *variant, int *kx, int *ky);
 int fire_autotune(fire_ctx *ctx, const void *wind_u_dev, const void *wind_v_dev, double dt,
                   int probe_steps, int *variant, int *kx, int *ky);
 
+/* The launch shape fire_init (and fire_step_noalloc) takes by default for a
+ * mesh of nx_atm x ny_atm atmospheric cells refined sr_x x sr_y, in the given
+ * precision, on a device with n_sm SMs: strips (warp strips in FP32 when
+ * sr_x <= 30, else marching strips) as tall as the large-mesh shapes (~160 /
+ * ~60 rows) while that still gives 3.5 / 2.5 waves of resident CTAs, else
+ * shorter, down to one atmospheric cell; 2-D tiles of one atmospheric cell
+ * where even those fill under a quarter of one wave.  A pure host
+ * computation (no device needed); fire_init falls back to smaller tiles if
+ * the shape's shared memory does not fit.  Returns FIRE_ERR_ARG for
+ * non-positive sizes or an unknown precision. */
+int fire_default_kernel(int precision, int nx_atm, int ny_atm, int sr_x, int sr_y, int n_sm,
+                        int *variant, int *kx, int *ky);
+
 /* Kernel timing: when enabled, CUDA events bracket every launch of the fused
  * step kernel on the context's stream; fire_kernel_time_ms waits for them and
  * returns the summed device time and the launch count since the last reset. */

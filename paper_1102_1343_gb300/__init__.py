@@ -47,7 +47,8 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
                "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test",
                "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
-               "fire_adjoint", "fire_autotune", "fire_ensemble_autotune")
+               "fire_adjoint", "fire_autotune", "fire_ensemble_autotune",
+               "fire_default_kernel")
 
 
 class FireError(RuntimeError):
@@ -150,6 +151,8 @@ def load_library(path: str | None = None):
     L.fire_ensemble_autotune.argtypes = [_P, C.c_int, C.c_double, C.POINTER(_P), C.POINTER(_P),
                                          C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.fire_ensemble_autotune.restype = C.c_int
+    L.fire_default_kernel.argtypes = [C.c_int] * 6 + [C.POINTER(C.c_int)] * 3
+    L.fire_default_kernel.restype = C.c_int
     for name in ("fire_ensemble_create", "fire_ensemble_step", "fire_ensemble_member",
                  "fire_ensemble_status", "fire_ensemble_clear_status", "fire_ensemble_set_kernel",
                  "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test"):
@@ -292,6 +295,17 @@ def fire_time(ctx) -> float:
 def fire_set_kernel(ctx, variant, kx, ky) -> int:
     return _check(load_library().fire_set_kernel(ctx, int(variant), int(kx), int(ky)),
                   "fire_set_kernel")
+
+
+def fire_default_kernel(precision, nx_atm, ny_atm, sr_x, sr_y, n_sm):
+    """(variant, kx, ky) that fire_init takes by default on a device with
+    n_sm SMs (host computation, no device needed)."""
+    v, kx, ky = C.c_int(), C.c_int(), C.c_int()
+    prec = {"fp32": FIRE_FP32, "fp64": FIRE_FP64}.get(precision, precision)
+    _check(load_library().fire_default_kernel(int(prec), int(nx_atm), int(ny_atm), int(sr_x),
+                                              int(sr_y), int(n_sm), C.byref(v), C.byref(kx),
+                                              C.byref(ky)), "fire_default_kernel")
+    return v.value, kx.value, ky.value
 
 
 def fire_get_kernel(ctx):

@@ -794,6 +794,19 @@ int fire_set_kernel(fire_ctx *c, int variant, int kx, int ky) {
 // marching strip over widths of about 16..248 columns and heights of about
 // 8..512 rows, and the 2-D tile over a few shapes; the fastest average of
 // probe_steps launches (after one warm-up launch) is kept.
+int fire_default_kernel(int precision, int nx_atm, int ny_atm, int sr_x, int sr_y, int n_sm,
+                        int *variant, int *kx, int *ky) {
+    if ((precision != FIRE_FP32 && precision != FIRE_FP64) || nx_atm < 1 || ny_atm < 1 ||
+        sr_x < 1 || sr_y < 1 || n_sm < 1 || !variant || !kx || !ky)
+        return FIRE_ERR_ARG;
+    const DefaultShape d =
+        default_shape(precision == FIRE_FP64, nx_atm, ny_atm, sr_x, sr_y, n_sm);
+    *variant = d.variant;
+    *kx = d.kx;
+    *ky = d.ky;
+    return FIRE_OK;
+}
+
 int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int probe_steps,
                   int *variant_out, int *kx_out, int *ky_out) {
     if (!c || !u || !v || !finite_pos(dt) || probe_steps < 1) return FIRE_ERR_ARG;
