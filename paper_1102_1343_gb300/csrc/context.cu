@@ -230,7 +230,8 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
         e = c->prec == FIRE_FP64 ? prepare_march_kernel<double>(sm) : prepare_march_kernel<float>(sm);
     } else if (variant == FIRE_KERNEL_WARP) {
         const long long W = (long long)kx * c->g.sr_x, L = (long long)ky * c->g.sr_y;
-        if (W > kWarpMaxColumns || (W & 1) || L > kWarpMaxRows) return FIRE_ERR_ARG;
+        if (W > kWarpMaxColumns || (W & 1) || L > kWarpMaxRows || (long long)c->n > kWarpMaxNodes)
+            return FIRE_ERR_ARG;
         sm = 0;
         e = cudaSuccess;
     } else if (variant == FIRE_KERNEL_TILE) {
@@ -262,7 +263,8 @@ int default_march(fire_ctx *c) {
 
 // the warp strips of the large-mesh default (~60 x 160 nodes), FP32 only
 int default_warp_strips(fire_ctx *c) {
-    if (c->prec != FIRE_FP32 || c->g.sr_x > kWarpMaxColumns / 2) return FIRE_ERR_ARG;
+    if (c->prec != FIRE_FP32 || c->g.sr_x > kWarpMaxColumns / 2 || (long long)c->n > kWarpMaxNodes)
+        return FIRE_ERR_ARG;
     int kx = kWarpMaxColumns / c->g.sr_x, ky = 160 / c->g.sr_y;
     if (kx > c->g.nx_atm) kx = c->g.nx_atm;
     if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 0;
@@ -334,7 +336,7 @@ DefaultShape default_shape(bool fp64, int nx_atm, int ny_atm, int srx, int sry, 
         while (ky > 1 && 2 * ctas_x * cdiv_l(ny, (long)ky * sry) < waves2 * slots) --ky;
         return 4 * ctas_x * cdiv_l(ny, (long)sry) < slots ? 0 : ky;
     };
-    if (!fp64 && srx <= kWarpMaxColumns / 2) {
+    if (!fp64 && srx <= kWarpMaxColumns / 2 && (long long)nx * ny <= kWarpMaxNodes) {
         int kx = kWarpMaxColumns / srx;
         if (kx > nx_atm) kx = nx_atm;
         if ((kx * srx) & 1) kx = kx > 1 ? kx - 1 : 0;

@@ -474,7 +474,7 @@ int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_d
             int prc, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
             double t;
             ctx_info(c, &prc, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
-            warp = warp && srx <= kWarpMaxColumns / 2;
+            warp = warp && srx <= kWarpMaxColumns / 2 && (long long)nx * ny <= kWarpMaxNodes;
         }
         e->variant = warp ? FIRE_KERNEL_WARP : FIRE_KERNEL_MARCH;
         for (fire_ctx *c : e->members)

@@ -92,6 +92,8 @@ cudaError_t launch_warp(const StepArgs &a, cudaStream_t s);
 constexpr int kWarpStrips = 4;       // warps (strips) per CTA of the warp kernel
 constexpr int kWarpMaxColumns = 60;  // output columns of one warp strip (even)
 constexpr int kWarpMaxRows = 512;    // output rows of one warp strip
+// the warp kernel indexes the mesh with 32-bit offsets: nx * ny below 2^31
+constexpr long long kWarpMaxNodes = 2147483647LL;
 
 // resident CTAs per SM of the strip kernels (the minimum blocks of their
 // __launch_bounds__, checked where the kernels are defined)

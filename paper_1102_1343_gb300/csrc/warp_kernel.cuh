@@ -97,17 +97,17 @@ struct WarpStrip {
     // used), so a loaded register is not touched before its use one
     // iteration later and the prefetch hides the memory latency.
     __device__ __forceinline__ V ld(const T *__restrict__ f, int r) const {
-        const size_t rowb = (size_t)r * nx;
-        if (vec) return *reinterpret_cast<const V *>(f + rowb + xcv);
+        const int rowb = r * nx;
+        if (vec) return *reinterpret_cast<const V *>(f + (rowb + xcv));
         return mk2(f[rowb + xcA], f[rowb + xcB]);
     }
 
     // prefetch of a row's environment: raw fuel bytes (decoded by decode()
     // at use), terrain gradient and multiplier
     __device__ __forceinline__ void load_env(int r, WEnv<T> &e) const {
-        const size_t rowb = (size_t)r * nx;
+        const int rowb = r * nx;
         if (vec) {
-            e.cls0 = *reinterpret_cast<const uint16_t *>(a.fuel + rowb + xcv);
+            e.cls0 = *reinterpret_cast<const uint16_t *>(a.fuel + (rowb + xcv));
         } else {
             e.cls0 = a.fuel[rowb + xcA];
             e.cls1 = a.fuel[rowb + xcB];
@@ -170,14 +170,15 @@ struct WarpStrip {
 
     // 5-point values of the lane's two columns at row r from the rows below
     // (d), at (c) and above (u), with the ghosts of Sect. 3.1 at the domain
-    // boundary; hl / hr replace the left / right neighbour of lanes 0 / 31
-    __device__ __forceinline__ void stencil(V d, V c, V u, int r, bool use_halo, T hl, T hr, V &L,
-                                            V &R, V &D, V &Uu) const {
+    // boundary; h replaces the left neighbour of lane 0 and the right one of
+    // lane 31 (each lane's own halo column)
+    __device__ __forceinline__ void stencil(V d, V c, V u, int r, bool use_halo, T h, V &L, V &R,
+                                            V &D, V &Uu) const {
         T l, rr;
         sides(c, l, rr);
         if (use_halo) {
-            if (lane == 0) l = hl;
-            if (lane == 31) rr = hr;
+            if (lane == 0) l = h;
+            if (lane == 31) rr = h;
         }
         L = mk2(l, c.x);
         R = mk2(c.y, rr);
@@ -248,7 +249,7 @@ struct WarpStrip {
         const int kb = y0 - 3, ke = y0 + La;
         // rows in registers (names by offset from the iteration's row k)
         V P0 = splat<V>(T(0)), P1 = P0, P2 = P0, Ppre = P0;  // psi^n rows k, k+1, k+2, prefetch
-        T hl1 = T(0), hr1 = T(0), hl2 = T(0), hr2 = T(0), hlp = T(0), hrp = T(0);
+        T h1 = T(0), h2 = T(0), hp = T(0);  // halo column of lanes 0 / 31, rows k+1, k+2, prefetch
         V Qm = P0, Q0 = P0, Q1 = P0;       // psi* rows k-1, k, k+1
         V FA0 = P0, FA1 = P0;              // -F(psi^n) rows k, k+1
         V Nm2 = P0, Nm1 = P0, N0 = P0;     // psi^{n+1} rows k-2, k-1, k
@@ -264,16 +265,18 @@ struct WarpStrip {
         // unconditional loads (rows outside the domain from the nearest
         // inside row: their values are never used), so that the loaded
         // registers are not merged with older values when they arrive
-        auto load_psi = [&](int r, V &v, T &hl, T &hr) {
+        // lanes 0 and 31 also load the one column beyond the warp on their
+        // side (x0 - 3, x0 + 62, clamped into the domain)
+        const bool hlane = lane == 0 || lane == 31;
+        const int hcol = lane == 0 ? max(xa - 1, 0) : min(xa + 2, nx - 1);
+        auto load_psi = [&](int r, V &v, T &h) {
             r = min(max(r, 0), ny - 1);
             v = ld(psi_in, r);
-            const size_t g = (size_t)r * nx;
-            if (lane == 0) hl = psi_in[g + max(xa - 1, 0)];
-            if (lane == 31) hr = psi_in[g + min(xa + 2, nx - 1)];
+            if (hlane) h = psi_in[r * nx + hcol];
         };
-        load_psi(kb, P0, hl1, hr1);  // hl1/hr1 of row kb are not used
-        load_psi(kb + 1, P1, hl1, hr1);
-        load_psi(kb + 2, Ppre, hlp, hrp);
+        load_psi(kb, P0, h1);  // h1 of row kb is not used
+        load_psi(kb + 1, P1, h1);
+        load_psi(kb + 2, Ppre, hp);
         load_env(min(max(kb + 1, 0), ny - 1), envPre);
 
 #pragma unroll 1
@@ -284,9 +287,8 @@ struct WarpStrip {
             const V Fcur = Fpre;
             Fpre = ld(static_cast<const T *>(a.F_in), min(max(k, 0), ny - 1));
             P2 = Ppre;
-            hl2 = hlp;
-            hr2 = hrp;
-            load_psi(k + 3, Ppre, hlp, hrp);
+            h2 = hp;
+            load_psi(k + 3, Ppre, hp);
             // ---- B: stage 1 on row k+1
             const int rB = k + 1;
             envB = envPre;
@@ -295,7 +297,7 @@ struct WarpStrip {
             if (rB >= 0 && rB < ny) {
                 wind(rB, envB.un, envB.vn);
                 V L, R, D, U;
-                stencil(P0, P1, P2, rB, true, hl1, hr1, L, R, D, U);
+                stencil(P0, P1, P2, rB, true, h1, L, R, D, U);
                 WCoef<T> co;
                 coef(envB, co);
                 FA1 = neg_rhs2<T>(P1, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, envB.m,
@@ -306,7 +308,7 @@ struct WarpStrip {
             const int rC = k;
             if (rC >= y0 - 1 && rC >= 0 && rC < ny) {
                 V L, R, D, U;
-                stencil(Qm, Q0, Q1, rC, false, T(0), T(0), L, R, D, U);
+                stencil(Qm, Q0, Q1, rC, false, T(0), L, R, D, U);
                 WCoef<T> co;
                 coef(envC, co);
                 const V G2 = neg_rhs2<T>(Q0, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co,
@@ -334,7 +336,7 @@ struct WarpStrip {
                 const bool burn = __any_sync(0xffffffffu, na || nb);
                 hist |= burn ? 1u : 0u;
                 if (burn) {
-                    const size_t g = (size_t)rC * nx + xa;
+                    const int g = rC * nx + xa;
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
                         if (!(j == 0 ? na : nb)) continue;
@@ -353,7 +355,7 @@ struct WarpStrip {
                 }
                 if (own_row) {
                     T *po = static_cast<T *>(a.psi_out);
-                    const size_t g = (size_t)rC * nx + xa;
+                    const int g = rC * nx + xa;
                     if (pst) *reinterpret_cast<V *>(po + g) = N0;
                     if (slow) {
                         if (!pst && outA) po[g] = N0.x;
@@ -369,8 +371,7 @@ struct WarpStrip {
             // ---- rotate
             P0 = P1;
             P1 = P2;
-            hl1 = hl2;
-            hr1 = hr2;
+            h1 = h2;
             Qm = Q0;
             Q0 = Q1;
             FA0 = FA1;
@@ -472,7 +473,7 @@ struct WarpStrip {
                         }
                     }
                 }
-                const int cls0 = a.fuel[(size_t)rD * nx + x];
+                const int cls0 = a.fuel[rD * nx + x];
                 const int cls = cls0 > ncm1 ? ncm1 : cls0;
                 const T f = cell_fraction_vals<T>(q[0][0], q[0][1], q[0][2], q[1][0], q[1][1],
                                                   q[1][2], q[2][0], q[2][1], q[2][2], e[0][0],
@@ -487,7 +488,7 @@ struct WarpStrip {
     // store F^{n+1} of the row, heat flux densities summed per column over
     // the band, and the per-cell average after the band's last row
     __device__ __forceinline__ void finish_row(int rD, V Fn, V F1) {
-        const size_t g = (size_t)rD * nx + xa;
+        const int g = rD * nx + xa;
         T *fo = static_cast<T *>(a.F_out);
         if (pst) *reinterpret_cast<V *>(fo + g) = F1;
         if (slow) {
@@ -591,7 +592,8 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
 template <typename T>
 cudaError_t launch_warp(const StepArgs &a, cudaStream_t s) {
     const int W = a.kx * a.srx, L = a.ky * a.sry;
-    if (W > 60 || (W & 1) || W < 2 || L > kWarpMaxRows) return cudaErrorInvalidValue;
+    if (W > 60 || (W & 1) || W < 2 || L > kWarpMaxRows || (long long)a.nx * a.ny > kWarpMaxNodes)
+        return cudaErrorInvalidValue;
     const int strips = (a.nx + W - 1) / W;
     dim3 grid((strips + kWarpStrips - 1) / kWarpStrips, (a.ny + L - 1) / L);
     k_fire_warp<T><<<grid, kWarpCtaThreads, 0, s>>>(a);
