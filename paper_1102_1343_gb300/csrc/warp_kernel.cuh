@@ -289,12 +289,18 @@ struct WarpStrip {
             P2 = Ppre;
             h2 = hp;
             load_psi(k + 3, Ppre, hp);
-            // ---- B: stage 1 on row k+1
+            // ---- B: stage 1 on row k+1.  Both stages run on every
+            // iteration, also on rows outside the domain or before the
+            // strip's first stage-2 row, from the clamped rows loaded there:
+            // such values are never read (boundary rows take ghosts, the
+            // quadrature starts at the strip's first row), and with no
+            // branch around them the two stages share one basic block, so
+            // their independent parts can be scheduled together
             const int rB = k + 1;
             envB = envPre;
             decode(envB);
             load_env(min(max(rB + 1, 0), ny - 1), envPre);
-            if (rB >= 0 && rB < ny) {
+            {
                 wind(rB, envB.un, envB.vn);
                 V L, R, D, U;
                 stencil(P0, P1, P2, rB, true, h1, L, R, D, U);
@@ -306,7 +312,7 @@ struct WarpStrip {
             }
             // ---- C: stage 2, crossing and t - t_i on row k
             const int rC = k;
-            if (rC >= y0 - 1 && rC >= 0 && rC < ny) {
+            {
                 V L, R, D, U;
                 stencil(Qm, Q0, Q1, rC, false, T(0), L, R, D, U);
                 WCoef<T> co;
@@ -315,6 +321,8 @@ struct WarpStrip {
                                          envC.m, envC.un, envC.vn, envC.zx, envC.zy);
                 // P0 + dt (F0/2 + F2/2) = P0 - dt/2 (G0 + G2), the halving exact
                 N0 = fma2(ndth2, add2(FA0, G2), P0);
+            }
+            if (rC >= y0 - 1 && rC >= 0 && rC < ny) {
                 // every column of the warp is computed from in-domain values,
                 // so a non-finite value anywhere in it comes from a
                 // non-finite value of the step
