@@ -217,8 +217,8 @@ def random_landscape(nxa, nya, sr=10, dx_atm=60.0, seed=BASE_SEED, steps=1200, d
     length), 20 Gaussian hills with max slope 0.4, 13 Voronoi fuel classes
     (load 0.1-2 kg/m^2, moisture 0.04-0.2, one chaparral), and either a 1 km
     line ignition perpendicular to the wind at x = 3 km ("line"), n random
-    point ignitions at least edge_margin from the edges ("points"), or one
-    central point ("center").  Sizes are free so the same recipe serves the
+    point ignitions at least edge_margin from the edges ("points"), one
+    central point ("center") or none ("none").  Sizes are free so the same recipe serves the
     2000x2000 and 8200x8200 meshes and small parity cases."""
     rng = np.random.default_rng(seed)
     srx = sry = sr
@@ -245,6 +245,8 @@ def random_landscape(nxa, nya, sr=10, dx_atm=60.0, seed=BASE_SEED, steps=1200, d
         ign = [point_ignition(a, b, radius=10.0) for a, b in zip(xs, ys)]
     elif ignition == "center":
         ign = [point_ignition(Lx / 2, Ly / 2, radius=10.0)]
+    elif ignition == "none":
+        ign = []
     else:
         raise ValueError(ignition)
     return Workload(name or f"landscape-{nx}x{ny}", nxa, nya, srx, sry, dx_atm, dx_atm,

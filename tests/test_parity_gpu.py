@@ -83,6 +83,27 @@ def test_fp64_landscape_ragged_tiles(pkg, tile):
     assert Qo > 0
 
 
+@pytest.mark.parametrize("mesh", [(1, 1, 10, "center"), (12, 1, 10, "center"),
+                                  (1, 9, 10, "center"), (6, 4, 2, "center"), (8, 6, 10, "none")])
+@pytest.mark.parametrize("tile", [None, (0, 1, 1), (1, 1, 1), (2, 1, 1)])
+def test_fp64_degenerate_meshes(pkg, mesh, tile):
+    """Edge cases of the mesh: one atmospheric cell, one atmospheric row (the
+    wind interpolation's single-row case), one column, refinement 2, and a
+    fire with no ignition at all (psi stays psi_far, no heat); each kernel
+    with strips or tiles one atmospheric cell wide, against the oracle; the
+    fire reaching the boundary ring sets the same status on both sides."""
+    nxa, nya, sr, ign = mesh
+    w = synth.random_landscape(nxa, nya, sr=sr, seed=41, ignition=ign, steps=30)
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    boundary = bool(orc.status & oracle.STATUS_BOUNDARY)
+    assert (m.status() == pkg.FIRE_ERR_BOUNDARY) == boundary
+    if ign == "none":
+        assert Qo == 0.0 and Qg == 0.0 and not np.isfinite(orc.tign).any()
+
+
 @pytest.mark.parametrize("tile", [None, (1, 2, 3), (0, 4, 4), (2, 12, 3), (2, 4, 7)])
 def test_fp64_odd_mesh_width(pkg, tile):
     """Refinement 5 on 23x17 atmos cells: an odd fire-mesh width (115), so the
