@@ -181,6 +181,26 @@ def oracle_sample(name: str, budget_cell_steps: float):
     return w, side_atm
 
 
+def host_cpu_model() -> str:
+    """The host CPU model (lscpu's model name, else /proc/cpuinfo, else the
+    machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -211,6 +231,7 @@ def time_oracle(name: str, seconds: float = 12.0, max_steps: int | None = None,
     cells = w.nx * w.ny
     how = "single thread" if used == 1 else f"{used} threads (OpenMP over rows)"
     return dict(value=cells * n / el, unit=UNIT, cores=used, kind="oracle",
+                cpu=f"{host_cpu_model()}, {host_cores()} cores available",
                 sample=f"{w.nx}x{w.ny} fire mesh of the same recipe ({w.name}), "
                        f"{n} FP64 oracle steps, {how}, {el:.1f} s")
 
@@ -253,6 +274,7 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES[args.workload], "oracle_sample": f"{w.nx}x{w.ny}"},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "cpu": f"{host_cpu_model()}, {host_cores()} cores available",
                          "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
