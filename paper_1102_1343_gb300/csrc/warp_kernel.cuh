@@ -7,9 +7,11 @@
 // the warp computes 64 columns: the strip, two halo columns on the left and
 // up to two on the right (the outermost of them are garbage nobody reads).
 // Horizontal neighbours come from the adjacent lane by shuffle, vertical
-// ones from the rows the lane keeps in registers; nothing goes through
-// shared memory and warps never wait for one another.  Per row (iteration
-// k) the stages lag behind the loads:
+// ones from the rows the lane keeps in registers; no row of the state goes
+// through shared memory (it holds the class tables, the wind-row weights
+// and a heat buffer) and warps never wait for one another.  Mesh offsets
+// are 32-bit (meshes below 2^31 nodes).  Per row (iteration k) the stages
+// lag behind the loads:
 //   B  stage 1 (eq. Heun, first line) on row k+1
 //   C  stage 2 (eq. Heun, second line), ignition-time crossing
 //      (eq. set-ignition-time) and t - t_i on row k

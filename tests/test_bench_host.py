@@ -17,9 +17,21 @@ def write_summary(tmp_path, source_hash, traffic_line):
 
 
 def test_traffic_read_when_hash_matches(tmp_path):
-    p = write_summary(tmp_path, bench.kernel_hash(),
+    p = write_summary(tmp_path, bench.kernel_hash() + " (sources without comments)",
                       "- dram_bytes_per_launch: 1.62e9 (24.1 B x 67.24 M cells, scaled)")
     assert bench.profiled_traffic(p) == 1.62e9
+
+
+def test_hash_ignores_comments(tmp_path, monkeypatch):
+    a = tmp_path / "a.cuh"
+    a.write_text("int f(int x) {  // one\n  return x + 1; /* two */\n}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ["a.cuh"])
+    h1 = bench.kernel_hash()
+    a.write_text("int f(int x) {\n  // changed comment\n  return x + 1;\n}\n")
+    assert bench.kernel_hash() == h1
+    a.write_text("int f(int x) { return x + 2; }\n")
+    assert bench.kernel_hash() != h1
 
 
 def test_traffic_dropped_for_another_source(tmp_path):
