@@ -103,6 +103,8 @@ def lib():
             L.orc_adjoint.restype = C.c_double
             L.orc_adjoint.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double, C.c_double,
                                       C.c_int] + [_D] * 8)
+            L.orc_step_vjp.restype = None
+            L.orc_step_vjp.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double] + [_D] * 7)
             L.orc_set_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_set_threads(1)  # one thread unless asked (set_threads)
@@ -314,6 +316,23 @@ class OracleFire:
         for _ in range(int(nsteps)):
             self.t = self.t + float(dt)
         return J, gm, gM, gu, gv
+
+    def step_vjp(self, u, v, dt, w):
+        """For one level-set step from the current state with the wind u, v:
+        lam = (d psi^{n+1} / d psi^n)^T w and the parameter terms
+        w^T d psi^{n+1} / dp for the per-node multiplier, the per-node
+        moisture and the node wind (un, vn), each [ny][nx].  The state is
+        not advanced."""
+        u, v, w = _f64(u), _f64(v), _f64(w)
+        assert w.shape == (self.ny, self.nx)
+        dco = node_coefficients_dMf(self.classes, self.fuel, self.moisture)
+        lam = np.zeros((self.ny, self.nx))
+        gm, gM, gun, gvn = (np.zeros_like(lam) for _ in range(4))
+        lib().orc_step_vjp(C.byref(self.g), _dp(self.coef), _dp(dco), _dp(self.mult),
+                           _dp(self.dzdx), _dp(self.dzdy), _dp(u), _dp(v), float(dt),
+                           _dp(self.psi), _dp(w), _dp(lam), _dp(gm), _dp(gM), _dp(gun),
+                           _dp(gvn))
+        return lam, gm, gM, gun, gvn
 
     def set_state(self, psi, tign, frac, t):
         self.psi = _f64(psi).copy()

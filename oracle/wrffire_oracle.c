@@ -953,6 +953,29 @@ static void adjoint_step(int nx, int ny, double dx, double dy, double eps, const
     free(ext0); free(ext1); free(F1); free(ps); free(v); free(ls); free(r1);
 }
 
+/* Vector-Jacobian product of one level-set step of the state psi (the two
+ * Heun stages of eq. Heun with eq. F-disc, ghosts as in orc_step, the wind
+ * of u, v interpolated to the nodes): for a cotangent w on psi^{n+1},
+ * lam = (d psi^{n+1} / d psi^n)^T w, and w^T d psi^{n+1} / dp added to gm
+ * (per-node multiplier), gMf (per-node moisture, through dco = dco/dM_f
+ * per node) and gun, gvn (node wind components).  The reverse step of
+ * orc_adjoint without the arrival-time seeds; pinned by the dot-product
+ * test against central differences of the forward step. */
+void orc_step_vjp(const orc_grid *g, const double *co, const double *dco, const double *mult,
+                  const double *dzdx, const double *dzdy, const double *u, const double *v,
+                  double dt, const double *psi, const double *w, double *lam, double *gm,
+                  double *gMf, double *gun, double *gvn)
+{
+    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
+    long n = (long)nx * ny;
+    double dx = g->dx_atm / g->srx, dy = g->dy_atm / g->sry;
+    double *un = malloc(sizeof(double) * n), *vn = malloc(sizeof(double) * n);
+    orc_wind_at_nodes(g->nxa, g->nya, g->srx, g->sry, u, v, un, vn);
+    adjoint_step(nx, ny, dx, dy, g->eps, psi, co, dco, mult, un, vn, dzdx, dzdy, dt, w, lam, gm,
+                 gMf, gun, gvn);
+    free(un); free(vn);
+}
+
 /* Whether node k's ignition time was set in the step [t_s, t_s + dt] that
  * took psi from a to b (eq. set-ignition-time): it was not ignited before
  * the run, the step crossed from > 0 to <= 0, and the recorded time lies in

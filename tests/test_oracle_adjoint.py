@@ -10,7 +10,9 @@ assimilation use of Sect. 7 that motivates the level-set formulation):
 - central finite differences along random directions on a random landscape
   (wind, slope, patchy fuel), away from switch points (the set of ignited nodes
   is the same in the perturbed runs);
-- a zero misfit gives a zero gradient.
+- a zero misfit gives a zero gradient;
+- the dot-product test of one linearised step, <J v, w> = <v, J^T w>, for
+  directions of the state, the multiplier and the moisture.
 """
 import numpy as np
 import pytest
@@ -189,3 +191,57 @@ def test_zero_misfit_zero_gradient(orc):
     # the adjoint call advanced the state exactly like the plain steps
     assert np.array_equal(g.psi, f.psi) and np.array_equal(g.tign, f.tign)
     assert np.array_equal(g.frac, f.frac) and g.t == f.t
+
+
+@pytest.mark.parametrize("dy_atm", [None, 14.0])
+def test_step_vjp_dot_product(orc, dy_atm):
+    """Dot-product test of the linearised level-set step: <J v, w> from
+    central differences of the forward step equals <v, J^T w> from the
+    reverse step (orc_step_vjp), for random directions v of the state psi,
+    the multiplier and the moisture and a random cotangent w.  Directions
+    whose +-h steps straddle a switch point (a Godunov selection, a clamp,
+    a zeroed central difference) show up as central differences that
+    change when h is halved; those are skipped."""
+    w = landscape(dy_atm=dy_atm)
+    ny, nx = w.ny, w.nx
+    rng = np.random.default_rng(23)
+    mult = 3.0 * (1.0 + 0.05 * rng.standard_normal((ny, nx)))
+    moist = np.array([w.classes[c]["fuelmc_g"] for c in w.fuel.ravel()]).reshape(ny, nx)
+    f = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    for _ in range(30):
+        f.step(w.u, w.v, w.dt)
+    psi0, tign0, frac0, t0 = f.psi.copy(), f.tign.copy(), f.frac.copy(), f.t
+
+    def step_psi(psi, m, M):
+        g = oracle.OracleFire(w.nxa, w.nya, w.srx, w.dx_atm, w.classes, w.fuel, w.dzdx, w.dzdy,
+                              [], moisture=M, mult=m, dy_atm=w.dy_atm)
+        g.set_state(psi, tign0, frac0, t0)
+        g.step(w.u, w.v, w.dt)
+        return g.psi
+
+    cot = rng.standard_normal((ny, nx))
+    lam, gm, gM, _, _ = f.step_vjp(w.u, w.v, w.dt, cot)
+    assert np.abs(lam).max() > 0 and np.abs(gm).max() > 0 and np.abs(gM).max() > 0
+    checked, worst = 0, 0.0
+    for q in range(6):
+        for which in ("psi", "m", "M"):
+            d = rng.standard_normal((ny, nx)) * (0.01 if which == "M" else 1.0)
+            fd = []
+            for h in (1e-6, 5e-7):
+                args_p = [psi0, mult, moist]
+                args_m = [psi0, mult, moist]
+                k = ("psi", "m", "M").index(which)
+                args_p[k] = args_p[k] + h * d
+                args_m[k] = args_m[k] - h * d
+                fd.append(float(np.sum((step_psi(*args_p) - step_psi(*args_m)) * cot)) / (2 * h))
+            if abs(fd[0] - fd[1]) > 1e-6 * max(abs(fd[0]), 1e-12):
+                continue  # a switch point within the step
+            ad = float(np.sum(d * (lam, gm, gM)[("psi", "m", "M").index(which)]))
+            err = abs(fd[0] - ad) / max(abs(fd[0]), 1e-12)
+            # central differences agree to ~1e-6 here (truncation); an
+            # error of the transposition would be of order one
+            assert err <= 1e-5, (which, q, fd, ad)
+            worst = max(worst, err)
+            checked += 1
+    print("checked", checked, "worst rel", worst)
+    assert checked >= 12
