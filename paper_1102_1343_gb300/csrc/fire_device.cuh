@@ -14,8 +14,8 @@ namespace wf {
 
 // ---------------------------------------------------------------------------
 // precision-dependent math.  FP32: hardware approximations (the FP32 path is
-// judged on ignition time, burnt area and total heat, not ulps); FP64: the
-// IEEE operations the plain formulas name.
+// held to tolerances on ignition time, burnt area and total heat, not to
+// ulps); FP64: the IEEE operations the plain formulas name.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Mth;
