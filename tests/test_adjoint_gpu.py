@@ -249,3 +249,74 @@ def test_full_size_fp64_matches_oracle(pkg):
         e = rel(g, gr)
         print(f"510x510 fp64 d{name}: rel err {e:.2e}")
         assert e <= 1e-8, (name, e)
+
+
+def test_full_size_central_differences_32_directions(pkg):
+    """The 510x510 adjoint workload (400 steps of 0.5 s, checkpoints every
+    20, FP64): the gradient against central differences of the GPU forward
+    misfit along 32 random directions (8 each of the multiplier, u, v and the
+    class moisture), skipping directions whose perturbed runs change the set
+    of ignited nodes (a switch point)."""
+    import os
+    import torch
+    w, truth = synth.adjoint_case()
+    threads = oracle.set_threads(len(os.sched_getaffinity(0)))
+    try:
+        f = oracle.OracleFire.from_workload(w, classes=truth["classes"], mult=truth["mult"])
+        for _ in range(w.steps):
+            f.step(w.u * truth["wind_scale"], w.v * truth["wind_scale"], w.dt)
+    finally:
+        oracle.set_threads(1)
+    assert threads >= 1
+    tobs = np.where(np.isfinite(f.tign), f.tign, np.nan)
+    m = pkg.FireModel.from_workload(w, precision="fp64")
+    st0 = m.state()
+    st0 = tuple(x.clone() if hasattr(x, "clone") else x for x in st0)
+    u0, v0 = m.wind(w.u, w.v)
+    mult0 = torch.ones((w.ny, w.nx), dtype=torch.float64, device="cuda")
+    classes0 = [dict(c) for c in w.classes]
+    J, gm, gM, gu, gv = m.adjoint(u0, v0, w.dt, w.steps, tobs, ckpt_every=20)
+    fuel = torch.as_tensor(w.fuel).cuda().long()
+    gcls = torch.zeros(len(classes0), dtype=torch.float64, device="cuda").index_add_(
+        0, fuel.flatten(), gM.flatten())
+    ign0 = torch.isfinite(m.state()[1]).cpu().numpy()
+    # a slow fire: by t = 200 s a handful of nodes around the centre ignited
+    assert J > 0 and ign0.sum() >= 10
+
+    def J_at(mult, classes, u, v):
+        m.set_state(*st0)
+        m.set_mult(mult)
+        m.set_classes(classes)
+        Jv, *_ = m.adjoint(u, v, w.dt, w.steps, tobs, ckpt_every=20, grads=False)
+        return Jv, torch.isfinite(m.state()[1]).cpu().numpy()
+
+    rng = np.random.default_rng(404)
+    h = 1e-6
+    checked, worst = 0, 0.0
+    for q in range(8):
+        dm = torch.as_tensor(rng.standard_normal((w.ny, w.nx))).cuda()
+        du = torch.as_tensor(rng.standard_normal(w.u.shape)).cuda()
+        dv = torch.as_tensor(rng.standard_normal(w.v.shape)).cuda()
+        dc = rng.standard_normal(len(classes0)) * 0.01
+        cases = {
+            "m": (lambda s: (mult0 + s * h * dm, classes0, u0, v0), float((gm * dm).sum())),
+            "u": (lambda s: (mult0, classes0, u0 + s * h * du, v0), float((gu * du).sum())),
+            "v": (lambda s: (mult0, classes0, u0, v0 + s * h * dv), float((gv * dv).sum())),
+            "M": (lambda s: (mult0, [dict(c, fuelmc_g=c["fuelmc_g"] + s * h * dc[k])
+                                     for k, c in enumerate(classes0)], u0, v0),
+                  float(np.dot(gcls.cpu().numpy(), dc))),
+        }
+        for name, (args, ad) in cases.items():
+            Jp, ip = J_at(*args(1.0))
+            Jm, im = J_at(*args(-1.0))
+            if not (np.array_equal(ip, ign0) and np.array_equal(im, ign0)):
+                continue
+            fd = (Jp - Jm) / (2 * h)
+            err = abs(fd - ad) / max(abs(fd), 1e-3 * J)
+            print(f"{name} {q}: fd {fd:.6e} adjoint {ad:.6e} rel {err:.1e}")
+            assert err <= 1e-5, (name, q, fd, ad)
+            worst = max(worst, err)
+            checked += 1
+    print("checked", checked, "of 32, worst rel", worst)
+    assert checked >= 16
+    m.close()
