@@ -103,6 +103,11 @@ def lib():
             L.orc_adjoint.restype = C.c_double
             L.orc_adjoint.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double, C.c_double,
                                       C.c_int] + [_D] * 8)
+            L.orc_adjoint_heat.restype = C.c_double
+            L.orc_adjoint_heat.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double, C.c_double,
+                                           C.c_int] + [_D] * 8)
+            L.orc_extend_vjp.restype = None
+            L.orc_extend_vjp.argtypes = [C.c_int, C.c_int, _D, _D, _D]
             L.orc_step_vjp.restype = None
             L.orc_step_vjp.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double] + [_D] * 7)
             L.orc_set_threads.restype = C.c_int
@@ -199,6 +204,17 @@ def extend(a) -> np.ndarray:
     ext = np.zeros((ny + 2, nx + 2))
     lib().orc_extend(nx, ny, _dp(a), _dp(ext))
     return ext
+
+
+def extend_vjp(a, D) -> np.ndarray:
+    """(d extend(a) / d a)^T D for D of the extended shape (ny+2, nx+2)."""
+    a = _f64(a)
+    ny, nx = a.shape
+    D = _f64(D)
+    assert D.shape == (ny + 2, nx + 2)
+    out = np.zeros_like(a)
+    lib().orc_extend_vjp(nx, ny, _dp(a), _dp(D), _dp(out))
+    return out
 
 
 def wind_at_nodes(nxa, nya, srx, sry, u, v):
@@ -313,6 +329,28 @@ class OracleFire:
                               _dp(self.dzdx), _dp(self.dzdy), _dp(u), _dp(v), self.t,
                               float(dt), int(nsteps), _dp(self.psi), _dp(self.tign),
                               _dp(self.frac), _dp(tobs), _dp(gm), _dp(gM), _dp(gu), _dp(gv))
+        for _ in range(int(nsteps)):
+            self.t = self.t + float(dt)
+        return J, gm, gM, gu, gv
+
+    def adjoint_heat(self, u, v, dt, nsteps, qobs):
+        """Reference adjoint of the heat misfit: advance nsteps (no ignition
+        may become active), return J = 1/2 sum over atmospheric cells with a
+        finite observation of (Q - qobs)^2, Q the sensible heat released per
+        unit area over the run [nya][nxa], and the gradients as adjoint()."""
+        u, v = _f64(u), _f64(v)
+        g = self.g
+        qobs = _f64(qobs)
+        assert qobs.shape == (g.nya, g.nxa)
+        dco = node_coefficients_dMf(self.classes, self.fuel, self.moisture)
+        gm = np.zeros((self.ny, self.nx))
+        gM = np.zeros_like(gm)
+        gu = np.zeros((g.nya, g.nxa + 1))
+        gv = np.zeros((g.nya + 1, g.nxa))
+        J = lib().orc_adjoint_heat(C.byref(g), _dp(self.coef), _dp(dco), _dp(self.mult),
+                                   _dp(self.dzdx), _dp(self.dzdy), _dp(u), _dp(v), self.t,
+                                   float(dt), int(nsteps), _dp(self.psi), _dp(self.tign),
+                                   _dp(self.frac), _dp(qobs), _dp(gm), _dp(gM), _dp(gu), _dp(gv))
         for _ in range(int(nsteps)):
             self.t = self.t + float(dt)
         return J, gm, gM, gu, gv

@@ -992,20 +992,16 @@ static int crossed_in_step(double tign0, double ti, double ts, double ts1, doubl
  * staggered wind u, v.  On return psi, tign, frac hold the final state.
  * Outputs g_* are overwritten.  Nodes without an observation carry a
  * non-finite tobs. */
-double orc_adjoint(const orc_grid *g, const double *co, const double *dco, const double *mult,
-                   const double *dzdx, const double *dzdy, const double *u, const double *v,
-                   double t0, double dt, int nsteps, double *psi, double *tign, double *frac,
-                   const double *tobs, double *g_mult, double *g_moist, double *g_u, double *g_v)
+/* Forward run of nsteps steps (no ignitions), keeping every state and the
+ * step start times (used by both adjoints below). */
+static void forward_run(const orc_grid *g, const double *co, const double *mult,
+                        const double *dzdx, const double *dzdy, const double *u, const double *v,
+                        double t0, double dt, int nsteps, double *psi, double *tign, double *frac,
+                        double *states, double *times)
 {
-    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
-    long n = (long)nx * ny;
-    double dx = g->dx_atm / g->srx, dy = g->dy_atm / g->sry;
-    double *states = malloc(sizeof(double) * n * (nsteps + 1));
-    double *times = malloc(sizeof(double) * (nsteps + 1));
-    double *tign0 = malloc(sizeof(double) * n);
+    long n = (long)g->nxa * g->srx * g->nya * g->sry;
     double *hs = malloc(sizeof(double) * g->nxa * g->nya), *hl = malloc(sizeof(double) * g->nxa * g->nya);
     unsigned char applied[1] = {1};
-    memcpy(tign0, tign, sizeof(double) * n);
     memcpy(states, psi, sizeof(double) * n);
     double t = t0;
     times[0] = t;
@@ -1015,37 +1011,55 @@ double orc_adjoint(const orc_grid *g, const double *co, const double *dco, const
         times[s + 1] = t;
         memcpy(states + (long)(s + 1) * n, psi, sizeof(double) * n);
     }
-    double J = 0.0;
-    for (long k = 0; k < n; ++k)
-        if (isfinite(tign[k]) && isfinite(tobs[k])) J += 0.5 * (tign[k] - tobs[k]) * (tign[k] - tobs[k]);
+    free(hs); free(hl);
+}
 
-    double *un = malloc(sizeof(double) * n), *vn = malloc(sizeof(double) * n);
-    double *gun = calloc(n, sizeof(double)), *gvn = calloc(n, sizeof(double));
-    double *lam = calloc(n, sizeof(double)), *mu = malloc(sizeof(double) * n);
-    orc_wind_at_nodes(g->nxa, g->nya, g->srx, g->sry, u, v, un, vn);
-    for (long k = 0; k < n; ++k) { g_mult[k] = 0.0; g_moist[k] = 0.0; }
+/* The reverse sweep over the stored states: lam enters as dJ/dpsi at the
+ * end of the run and leaves as dJ/dpsi at its start; dJdt[k] (finite where
+ * J depends on node k's ignition time) seeds the nodes whose first crossing
+ * was the step, through eq. (set-ignition-time); the parameter terms go to
+ * g_mult, g_moist (added to) and the node wind gradients gun, gvn. */
+static void adjoint_sweep(const orc_grid *g, const double *co, const double *dco,
+                          const double *mult, const double *dzdx, const double *dzdy,
+                          const double *un, const double *vn, double dt, int nsteps,
+                          const double *states, const double *times, const double *tign0,
+                          const double *tign, const double *dJdt, double *lam, double *g_mult,
+                          double *g_moist, double *gun, double *gvn)
+{
+    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
+    long n = (long)nx * ny;
+    double dx = g->dx_atm / g->srx, dy = g->dy_atm / g->sry;
+    double *mu = malloc(sizeof(double) * n);
     for (int s = nsteps - 1; s >= 0; --s) {
         const double *pa = states + (long)s * n, *pb = states + (long)(s + 1) * n;
         /* eq. (set-ignition-time) at the nodes whose first crossing was this step */
         for (long k = 0; k < n; ++k) {
             mu[k] = lam[k];
-            if (isfinite(tobs[k]) &&
+            if (isfinite(dJdt[k]) &&
                 crossed_in_step(tign0[k], tign[k], times[s], times[s + 1], pa[k], pb[k])) {
-                double a = pa[k], b = pb[k], r = tign[k] - tobs[k];
+                double a = pa[k], b = pb[k], r = dJdt[k];
                 mu[k] += r * dt * a / ((a - b) * (a - b));
             }
         }
         adjoint_step(nx, ny, dx, dy, g->eps, pa, co, dco, mult, un, vn, dzdx, dzdy, dt, mu, lam,
                      g_mult, g_moist, gun, gvn);
         for (long k = 0; k < n; ++k) {
-            if (isfinite(tobs[k]) &&
+            if (isfinite(dJdt[k]) &&
                 crossed_in_step(tign0[k], tign[k], times[s], times[s + 1], pa[k], pb[k])) {
-                double a = pa[k], b = pb[k], r = tign[k] - tobs[k];
+                double a = pa[k], b = pb[k], r = dJdt[k];
                 lam[k] += r * (-dt * b / ((a - b) * (a - b)));
             }
         }
     }
-    /* wind: adjoint of the bilinear interpolation of Sect. 5 */
+    free(mu);
+}
+
+/* Adjoint of the bilinear wind interpolation of Sect. 5: every staggered
+ * face sums the node gradients times the weights the forward gave it. */
+static void wind_gather(const orc_grid *g, const double *gun, const double *gvn, double *g_u,
+                        double *g_v)
+{
+    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
     for (long q = 0; q < (long)g->nya * (g->nxa + 1); ++q) g_u[q] = 0.0;
     for (long q = 0; q < (long)(g->nya + 1) * g->nxa; ++q) g_v[q] = 0.0;
     for (int j = 0; j < ny; ++j) {
@@ -1071,7 +1085,280 @@ double orc_adjoint(const orc_grid *g, const double *co, const double *dco, const
             g_v[j1 * W + i1] += gvn[k] * wy * wx;
         }
     }
-    free(states); free(times); free(tign0); free(hs); free(hl); free(un); free(vn);
-    free(gun); free(gvn); free(lam); free(mu);
+}
+
+/* Partial derivatives of orc_cell_fuel_fraction with respect to its nine
+ * psi and nine th window values, the branches frozen as the forward took
+ * them (which vertices have psi >= 0 and so take t instead of the
+ * interpolated th; the signs in sum |psi|; beta = 0 where sum |psi| = 0).
+ * Reading: d|x|/dx = sign(x), 0 at x = 0. */
+static void cell_fraction_partials(const double *p, const double *th, double t, double Tf,
+                                   double *dp, double *dth)
+{
+    double ps[3][3], ts[3][3], w[3][3][9];
+    int tfix[3][3];
+    for (int b = 0; b < 3; ++b) {
+        for (int a = 0; a < 3; ++a) {
+            int ia0 = a == 0 ? 0 : 1, ia1 = a == 2 ? 2 : 1;
+            int ib0 = b == 0 ? 0 : 1, ib1 = b == 2 ? 2 : 1;
+            for (int q = 0; q < 9; ++q) w[b][a][q] = 0.0;
+            /* the bilinear weights of the nodes bracketing the sample point */
+            w[b][a][ib0 * 3 + ia0] += 0.25;
+            w[b][a][ib0 * 3 + ia1] += 0.25;
+            w[b][a][ib1 * 3 + ia0] += 0.25;
+            w[b][a][ib1 * 3 + ia1] += 0.25;
+            /* the sample values computed as orc_cell_fuel_fraction does */
+            double pv, tv;
+            if (ia0 == ia1 && ib0 == ib1) {
+                pv = p[4];
+                tv = th[4];
+            } else if (ib0 == ib1) {
+                pv = 0.5 * (p[ib0 * 3 + ia0] + p[ib0 * 3 + ia1]);
+                tv = 0.5 * (th[ib0 * 3 + ia0] + th[ib0 * 3 + ia1]);
+            } else if (ia0 == ia1) {
+                pv = 0.5 * (p[ib0 * 3 + ia0] + p[ib1 * 3 + ia0]);
+                tv = 0.5 * (th[ib0 * 3 + ia0] + th[ib1 * 3 + ia0]);
+            } else {
+                pv = 0.25 * (p[ib0 * 3 + ia0] + p[ib0 * 3 + ia1]
+                           + p[ib1 * 3 + ia0] + p[ib1 * 3 + ia1]);
+                tv = 0.25 * (th[ib0 * 3 + ia0] + th[ib0 * 3 + ia1]
+                           + th[ib1 * 3 + ia0] + th[ib1 * 3 + ia1]);
+            }
+            tfix[b][a] = pv >= 0.0;
+            ps[b][a] = pv;
+            ts[b][a] = tfix[b][a] ? t : tv;
+        }
+    }
+    double gps[3][3] = {{0.0}}, gts[3][3] = {{0.0}};
+    for (int sb = 0; sb < 2; ++sb) {
+        for (int sa = 0; sa < 2; ++sa) {
+            int ax = 2 * sa, by = 2 * sb;
+            int pb[4] = {1, 1, by, by}, pa[4] = {1, ax, 1, ax};
+            double sp = 0.0, sabs = 0.0, sum = 0.0;
+            for (int k = 0; k < 4; ++k) {
+                double x = ps[pb[k]][pa[k]];
+                sp += x;
+                sabs += fabs(x);
+                sum += t - ts[pb[k]][pa[k]];
+            }
+            double e = exp(-0.25 * sum / Tf);
+            double beta = sabs > 0.0 ? 0.5 * (1.0 - sp / sabs) : 0.0;
+            /* F = 1 - sum over subcells of burned / 4, burned = beta (1 - e) */
+            for (int k = 0; k < 4; ++k) {
+                double x = ps[pb[k]][pa[k]];
+                double sg = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
+                double dbeta = sabs > 0.0 ? 0.5 * (-1.0 / sabs + sp * sg / (sabs * sabs)) : 0.0;
+                gps[pb[k]][pa[k]] += -0.25 * (1.0 - e) * dbeta;
+                gts[pb[k]][pa[k]] += -0.25 * (-beta * e * 0.25 / Tf);
+            }
+        }
+    }
+    for (int q = 0; q < 9; ++q) { dp[q] = 0.0; dth[q] = 0.0; }
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+            for (int q = 0; q < 9; ++q) {
+                dp[q] += gps[b][a] * w[b][a][q];
+                if (!tfix[b][a]) dth[q] += gts[b][a] * w[b][a][q];
+            }
+}
+
+/* Adjoint of orc_extend: D holds d/d(ext) on the (nx+2) x (ny+2) extension
+ * of a; adds the derivative with respect to the nodes of a to da (the y
+ * ghosts first, as they were filled last, then the x ghosts). */
+static void extend_adjoint(int nx, int ny, const double *a, double *D, double *da)
+{
+    int W = nx + 2;
+    double *ext = malloc(sizeof(double) * W * (ny + 2));
+    orc_extend(nx, ny, a, ext);
+    for (int i = 0; i < W; ++i) {
+        double d0, d1;
+        ghost_partials(ext[W + i], ext[2 * W + i], &d0, &d1);
+        D[W + i] += D[i] * d0;
+        D[2 * W + i] += D[i] * d1;
+        ghost_partials(ext[ny * W + i], ext[(ny - 1) * W + i], &d0, &d1);
+        D[ny * W + i] += D[(ny + 1) * W + i] * d0;
+        D[(ny - 1) * W + i] += D[(ny + 1) * W + i] * d1;
+    }
+    for (int j = 1; j <= ny; ++j) {
+        double d0, d1;
+        double *row = ext + j * W, *Dr = D + j * W;
+        ghost_partials(row[1], row[2], &d0, &d1);
+        Dr[1] += Dr[0] * d0;
+        Dr[2] += Dr[0] * d1;
+        ghost_partials(row[nx], row[nx - 1], &d0, &d1);
+        Dr[nx] += Dr[nx + 1] * d0;
+        Dr[nx - 1] += Dr[nx + 1] * d1;
+    }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) da[(long)j * nx + i] += D[(j + 1) * W + (i + 1)];
+    free(ext);
+}
+
+/* orc_extend's transpose for tests: da = (d ext / d a)^T D (da overwritten;
+ * D is left unchanged). */
+void orc_extend_vjp(int nx, int ny, const double *a, const double *D, double *da)
+{
+    long ne = (long)(nx + 2) * (ny + 2);
+    double *Dc = malloc(sizeof(double) * ne);
+    memcpy(Dc, D, sizeof(double) * ne);
+    for (long k = 0; k < (long)nx * ny; ++k) da[k] = 0.0;
+    extend_adjoint(nx, ny, a, Dc, da);
+    free(Dc);
+}
+
+/* Heat misfit: the sensible heat released per unit area of each atmospheric
+ * cell over the run, Q_I = sum over the fire cells k of I of
+ * (F_k(start) - F_k(end)) H_s,k / (srx sry) -- the time integral of the
+ * heat flux of eqs. (sensible-heat-flux, average), which telescopes -- and
+ * J = 1/2 sum over the cells with a finite observation of (Q_I - q_obs,I)^2.
+ * The run, gradients and outputs as in orc_adjoint.  Its seeds: dJ/dF at
+ * the end through the quadrature of Sect. 3.3 (orc_cell_fuel_fraction with
+ * the ghosts of orc_step) into dJ/dpsi at the end and dJ/dt_i (then eq.
+ * set-ignition-time at each node's crossing step), and the moisture
+ * dependence of H_s. */
+double orc_adjoint_heat(const orc_grid *g, const double *co, const double *dco,
+                        const double *mult, const double *dzdx, const double *dzdy,
+                        const double *u, const double *v, double t0, double dt, int nsteps,
+                        double *psi, double *tign, double *frac, const double *qobs,
+                        double *g_mult, double *g_moist, double *g_u, double *g_v)
+{
+    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
+    long n = (long)nx * ny;
+    int W = nx + 2;
+    long ne = (long)W * (ny + 2);
+    double r2 = (double)(g->srx * g->sry);
+    double *states = malloc(sizeof(double) * n * (nsteps + 1));
+    double *times = malloc(sizeof(double) * (nsteps + 1));
+    double *tign0 = malloc(sizeof(double) * n), *frac0 = malloc(sizeof(double) * n);
+    memcpy(tign0, tign, sizeof(double) * n);
+    memcpy(frac0, frac, sizeof(double) * n);
+    forward_run(g, co, mult, dzdx, dzdy, u, v, t0, dt, nsteps, psi, tign, frac, states, times);
+    double t1 = times[nsteps];
+
+    /* Q, J and dJ/dF per fire cell (0 under unobserved atmospheric cells) */
+    double J = 0.0;
+    double *gF = calloc(n, sizeof(double));
+    for (long k = 0; k < n; ++k) g_moist[k] = 0.0;
+    for (int Jc = 0; Jc < g->nya; ++Jc) {
+        for (int Ic = 0; Ic < g->nxa; ++Ic) {
+            double qo = qobs[Jc * g->nxa + Ic];
+            if (!isfinite(qo)) continue;
+            double q = 0.0;
+            for (int j = Jc * g->sry; j < (Jc + 1) * g->sry; ++j)
+                for (int i = Ic * g->srx; i < (Ic + 1) * g->srx; ++i) {
+                    long k = (long)j * nx + i;
+                    q += (frac0[k] - frac[k]) * co[k * CO_N + CO_HS];
+                }
+            q /= r2;
+            J += 0.5 * (q - qo) * (q - qo);
+            for (int j = Jc * g->sry; j < (Jc + 1) * g->sry; ++j)
+                for (int i = Ic * g->srx; i < (Ic + 1) * g->srx; ++i) {
+                    long k = (long)j * nx + i;
+                    gF[k] = -(q - qo) * co[k * CO_N + CO_HS] / r2;
+                    g_moist[k] = (q - qo) * (frac0[k] - frac[k]) * dco[k * CO_N + CO_HS] / r2;
+                }
+        }
+    }
+
+    /* the quadrature at the end of the run, as orc_step evaluated it */
+    double *ext = malloc(sizeof(double) * ne), *ext_t = malloc(sizeof(double) * ne);
+    orc_extend(nx, ny, psi, ext);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            ext_t[(j + 1) * W + (i + 1)] = psi[k] < 0.0 ? tign[k] : t1;
+        }
+    for (int j = 1; j <= ny; ++j) {
+        ext_t[j * W] = ext_t[j * W + 1];
+        ext_t[j * W + nx + 1] = ext_t[j * W + nx];
+    }
+    for (int i = 0; i < W; ++i) {
+        ext_t[i] = ext_t[W + i];
+        ext_t[(ny + 1) * W + i] = ext_t[ny * W + i];
+    }
+    for (long k = 0; k < ne; ++k)
+        if (ext[k] >= 0.0) ext_t[k] = t1;
+    double *Dp = calloc(ne, sizeof(double)), *Dt = calloc(ne, sizeof(double));
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            if (gF[k] == 0.0) continue;
+            double p9[9], t9[9], dp9[9], dt9[9];
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    p9[b * 3 + a] = ext[(j + b) * W + (i + a)];
+                    t9[b * 3 + a] = ext_t[(j + b) * W + (i + a)];
+                }
+            cell_fraction_partials(p9, t9, t1, co[k * CO_N + CO_TF], dp9, dt9);
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    Dp[(j + b) * W + (i + a)] += gF[k] * dp9[b * 3 + a];
+                    Dt[(j + b) * W + (i + a)] += gF[k] * dt9[b * 3 + a];
+                }
+        }
+    }
+    /* dJ/dpsi at the end: through the ghosts of orc_extend */
+    double *lam = calloc(n, sizeof(double));
+    extend_adjoint(nx, ny, psi, Dp, lam);
+    /* dJ/dt_i: the positions set to t1 carry nothing, the ghost copies
+     * return to their sources (y then x), t_i only where psi < 0 */
+    for (long k = 0; k < ne; ++k)
+        if (ext[k] >= 0.0) Dt[k] = 0.0;
+    for (int i = 0; i < W; ++i) {
+        Dt[W + i] += Dt[i];
+        Dt[ny * W + i] += Dt[(ny + 1) * W + i];
+    }
+    for (int j = 1; j <= ny; ++j) {
+        Dt[j * W + 1] += Dt[j * W];
+        Dt[j * W + nx] += Dt[j * W + nx + 1];
+    }
+    double *dJdt = malloc(sizeof(double) * n);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            dJdt[k] = psi[k] < 0.0 ? Dt[(j + 1) * W + (i + 1)] : 0.0;
+        }
+
+    double *un = malloc(sizeof(double) * n), *vn = malloc(sizeof(double) * n);
+    double *gun = calloc(n, sizeof(double)), *gvn = calloc(n, sizeof(double));
+    orc_wind_at_nodes(g->nxa, g->nya, g->srx, g->sry, u, v, un, vn);
+    for (long k = 0; k < n; ++k) g_mult[k] = 0.0;
+    adjoint_sweep(g, co, dco, mult, dzdx, dzdy, un, vn, dt, nsteps, states, times, tign0, tign,
+                  dJdt, lam, g_mult, g_moist, gun, gvn);
+    wind_gather(g, gun, gvn, g_u, g_v);
+    free(states); free(times); free(tign0); free(frac0); free(gF); free(ext); free(ext_t);
+    free(Dp); free(Dt); free(lam); free(dJdt); free(un); free(vn); free(gun); free(gvn);
+    return J;
+}
+
+double orc_adjoint(const orc_grid *g, const double *co, const double *dco, const double *mult,
+                   const double *dzdx, const double *dzdy, const double *u, const double *v,
+                   double t0, double dt, int nsteps, double *psi, double *tign, double *frac,
+                   const double *tobs, double *g_mult, double *g_moist, double *g_u, double *g_v)
+{
+    int nx = g->nxa * g->srx, ny = g->nya * g->sry;
+    long n = (long)nx * ny;
+    double *states = malloc(sizeof(double) * n * (nsteps + 1));
+    double *times = malloc(sizeof(double) * (nsteps + 1));
+    double *tign0 = malloc(sizeof(double) * n);
+    memcpy(tign0, tign, sizeof(double) * n);
+    forward_run(g, co, mult, dzdx, dzdy, u, v, t0, dt, nsteps, psi, tign, frac, states, times);
+    double J = 0.0;
+    for (long k = 0; k < n; ++k)
+        if (isfinite(tign[k]) && isfinite(tobs[k])) J += 0.5 * (tign[k] - tobs[k]) * (tign[k] - tobs[k]);
+    /* dJ/dt_i at the observed nodes (NaN elsewhere) */
+    double *dJdt = malloc(sizeof(double) * n);
+    for (long k = 0; k < n; ++k) dJdt[k] = isfinite(tobs[k]) ? tign[k] - tobs[k] : NAN;
+
+    double *un = malloc(sizeof(double) * n), *vn = malloc(sizeof(double) * n);
+    double *gun = calloc(n, sizeof(double)), *gvn = calloc(n, sizeof(double));
+    double *lam = calloc(n, sizeof(double));
+    orc_wind_at_nodes(g->nxa, g->nya, g->srx, g->sry, u, v, un, vn);
+    for (long k = 0; k < n; ++k) { g_mult[k] = 0.0; g_moist[k] = 0.0; }
+    adjoint_sweep(g, co, dco, mult, dzdx, dzdy, un, vn, dt, nsteps, states, times, tign0, tign,
+                  dJdt, lam, g_mult, g_moist, gun, gvn);
+    wind_gather(g, gun, gvn, g_u, g_v);
+    free(states); free(times); free(tign0); free(dJdt); free(un); free(vn);
+    free(gun); free(gvn); free(lam);
     return J;
 }

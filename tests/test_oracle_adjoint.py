@@ -245,3 +245,138 @@ def test_step_vjp_dot_product(orc, dy_atm):
             checked += 1
     print("checked", checked, "worst rel", worst)
     assert checked >= 12
+
+
+# ---------------------------------------------------------------------------
+# heat misfit: Q = sensible heat released per unit area of each atmospheric
+# cell over the run, J = 1/2 sum (Q - q_obs)^2
+# ---------------------------------------------------------------------------
+
+def released_heat(w, mult, moist, u, v, nsteps):
+    """Q per atmospheric cell as the time integral of the step's sensible
+    heat flux output (eqs. sensible-heat-flux, average)."""
+    f = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    Q = np.zeros((w.nya, w.nxa))
+    for _ in range(nsteps):
+        hs, _, _ = f.step(u, v, w.dt)
+        Q += hs * w.dt
+    return Q
+
+
+def heat_case(seed=7, dy_atm=None, corner=False):
+    """The small landscape; corner=True ignites at the domain corner instead,
+    so that the quadrature's ghost nodes (x, y and corner) carry ignition
+    times."""
+    w = landscape(seed=seed, dy_atm=dy_atm)
+    if corner:
+        w.ignitions = [synth.point_ignition(1.0, 1.0, radius=7.0)]
+    rng = np.random.default_rng(seed + 40)
+    mult = 3.0 * (1.0 + 0.05 * rng.standard_normal((w.ny, w.nx)))
+    moist = np.array([w.classes[c]["fuelmc_g"] for c in w.fuel.ravel()]).reshape(w.ny, w.nx)
+    return w, mult, moist
+
+
+def test_heat_objective_is_the_integrated_heat_flux(orc):
+    """J with observations Q_flux + delta equals 1/2 sum delta^2: the Q of the
+    objective (from the fuel fractions at the start and the end) is the time
+    integral of the step's heat flux output (the sum telescopes)."""
+    w, mult, moist = heat_case()
+    nsteps = 40
+    Q = released_heat(w, mult, moist, w.u, w.v, nsteps)
+    assert Q.max() > 0
+    rng = np.random.default_rng(1)
+    delta = rng.standard_normal(Q.shape) * Q.max()
+    f = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    J, *_ = f.adjoint_heat(w.u, w.v, w.dt, nsteps, Q + delta)
+    assert abs(J - 0.5 * np.sum(delta ** 2)) <= 1e-9 * J
+    # unobserved cells do not count
+    qobs = Q + delta
+    qobs[0, :] = np.nan
+    g = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    J2, *_ = g.adjoint_heat(w.u, w.v, w.dt, nsteps, qobs)
+    assert abs(J2 - 0.5 * np.sum(delta[1:] ** 2)) <= 1e-9 * J2
+
+
+def test_heat_misfit_zero_gives_zero_gradient(orc):
+    w, mult, moist = heat_case(seed=8)
+    nsteps = 30
+    Q = released_heat(w, mult, moist, w.u, w.v, nsteps)
+    f = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    J, gm, gM, gu, gv = f.adjoint_heat(w.u, w.v, w.dt, nsteps, Q)
+    g = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    J1, gm1, gM1, gu1, gv1 = g.adjoint_heat(w.u, w.v, w.dt, nsteps, Q * 0.9)
+    assert J <= 1e-24 * max(J1, 1.0)
+    for a, b in ((gm, gm1), (gM, gM1), (gu, gu1), (gv, gv1)):
+        assert np.abs(a).max() <= 1e-9 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("dy_atm,corner", [(None, False), (14.0, False), (None, True)])
+def test_heat_gradient_matches_central_differences(orc, dy_atm, corner):
+    """Central differences of J_heat along random directions of the
+    multiplier, the moisture and the wind; directions whose +-h runs cross a
+    switch point (ignited set, quadrature branches) show up as differences
+    that change when h is halved, and are skipped."""
+    w, mult, moist = heat_case(dy_atm=dy_atm, corner=corner)
+    nsteps = 50
+    # observations: a truth run with a stronger fire, drier fuel, more wind
+    qobs = released_heat(w, mult * 1.2, moist - 0.02, w.u * 1.1, w.v * 1.1, nsteps)
+    base = oracle.OracleFire.from_workload(w, mult=mult, moisture=moist)
+    J, gm, gM, gu, gv = base.adjoint_heat(w.u, w.v, w.dt, nsteps, qobs)
+    assert J > 0
+
+    def J_at(m, M, u, v):
+        f = oracle.OracleFire.from_workload(w, mult=m, moisture=M)
+        Jv, *_ = f.adjoint_heat(u, v, w.dt, nsteps, qobs)
+        return Jv
+
+    rng = np.random.default_rng(17)
+    checked, worst = 0, 0.0
+    for q in range(8):
+        dirs = {"m": rng.standard_normal((w.ny, w.nx)),
+                "M": rng.standard_normal((w.ny, w.nx)) * 0.01,
+                "u": rng.standard_normal(w.u.shape),
+                "v": rng.standard_normal(w.v.shape)}
+        for name, d in dirs.items():
+            k = "mMuv".index(name)
+            fd = []
+            for h in (1e-6, 5e-7):
+                ap = [mult, moist, w.u, w.v]
+                am = [mult, moist, w.u, w.v]
+                ap[k] = ap[k] + h * d
+                am[k] = am[k] - h * d
+                fd.append((J_at(*ap) - J_at(*am)) / (2 * h))
+            if abs(fd[0] - fd[1]) > 1e-6 * max(abs(fd[0]), 1e-3 * J):
+                continue
+            ad = float(np.sum((gm, gM, gu, gv)[k] * d))
+            err = abs(fd[0] - ad) / max(abs(fd[0]), 1e-3 * J)
+            assert err <= 1e-5, (name, q, fd, ad)
+            worst = max(worst, err)
+            checked += 1
+    print("checked", checked, "worst rel", worst)
+    assert checked >= 20
+
+
+@pytest.mark.parametrize("shape", [(6, 5), (2, 2), (9, 3)])
+def test_extend_vjp_dot_product(orc, shape):
+    """The transpose of the ghost extension (x ghosts, then y ghosts over the
+    extended rows, corners included) used by the heat adjoint:
+    <extend(a + h v) - extend(a - h v), D> / 2h = <v, extend^T D>.  The
+    extension is piecewise linear, so away from its kinks (fields without
+    ties in the ghosts' max) the two agree to rounding; fields of each branch
+    type are tried."""
+    ny, nx = shape
+    rng = np.random.default_rng(nx * 10 + ny)
+    for field in ("random", "linear", "bowl"):
+        y, x = np.mgrid[0:ny, 0:nx]
+        a = {"random": rng.standard_normal((ny, nx)),
+             "linear": 0.7 * x - 0.3 * y + 0.1,          # 2 p0 - p1 branch
+             # off-centre, so that no ghost sits on a tie of its max
+             "bowl": (x - nx / 2.0 - 0.37) ** 2 + (y - ny / 2.0 - 0.21) ** 2}[field]
+        for _ in range(4):
+            v = rng.standard_normal((ny, nx))
+            D = rng.standard_normal((ny + 2, nx + 2))
+            h = 1e-7
+            ep, em = oracle.extend(a + h * v), oracle.extend(a - h * v)
+            lhs = float(np.sum((ep - em) * D)) / (2 * h)
+            rhs = float(np.sum(v * oracle.extend_vjp(a, D)))
+            assert abs(lhs - rhs) <= 1e-6 * max(1.0, abs(rhs)), (field, lhs, rhs)
