@@ -222,12 +222,31 @@ int fire_set_fuel_classes(fire_ctx *ctx, const fire_fuel_class *classes, int n_c
  * Derivatives follow the branches the forward values take (upwind
  * selection, limits of the spread rate, boundary extrapolation), so they are
  * one-sided at switch points.  Workspace: about (nsteps/ckpt_every +
- * ckpt_every + 4) states plus 19 doubles per node, kept by the context.
+ * ckpt_every + 4) states plus 13 path-precision values and 6 doubles per node,
+ * kept by the context.
  * Synchronous: returns after J and the gradients are written. */
 int fire_adjoint(fire_ctx *ctx, int nsteps, double dt, const void *wind_u_dev,
                  const void *wind_v_dev, const double *t_obs_dev, int ckpt_every,
                  double *J_host, double *g_mult_dev, double *g_moist_dev, double *g_u_dev,
                  double *g_v_dev);
+
+/* The same for a heat misfit (a data-assimilation objective for observed
+ * fire heat release):
+ *
+ *     J = 1/2 sum over atmospheric cells with a finite q_obs of (Q - q_obs)^2,
+ *     Q = sensible heat released per unit area of the cell over the nsteps
+ *         steps = sum over its fire cells of (F_start - F_end) H_s / (sr_x sr_y)
+ *
+ * (J m^-2; the time integral of the heat_sens output of fire_step, whose sum
+ * over steps telescopes).  The gradient also carries the moisture dependence
+ * of H_s and, through the fuel-fraction quadrature of Sect. 3.3, the
+ * dependence of F_end on psi and on the ignition times.
+ *   q_obs_dev    [ny_atm][nx_atm] double device; NaN or +-inf where not observed
+ * Everything else as fire_adjoint (the mesh needs at least 2 x 2 fire nodes). */
+int fire_adjoint_heat(fire_ctx *ctx, int nsteps, double dt, const void *wind_u_dev,
+                      const void *wind_v_dev, const double *q_obs_dev, int ckpt_every,
+                      double *J_host, double *g_mult_dev, double *g_moist_dev, double *g_u_dev,
+                      double *g_v_dev);
 
 /* Waits for the context's stream and returns the first sticky device fault
  * (FIRE_ERR_BOUNDARY, FIRE_ERR_NONFINITE, FIRE_ERR_TIMEOUT) or FIRE_OK;

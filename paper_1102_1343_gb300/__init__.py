@@ -48,7 +48,7 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test",
                "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
                "fire_adjoint", "fire_autotune", "fire_ensemble_autotune",
-               "fire_default_kernel")
+               "fire_default_kernel", "fire_adjoint_heat")
 
 
 class FireError(RuntimeError):
@@ -145,6 +145,8 @@ def load_library(path: str | None = None):
     L.fire_adjoint.argtypes = [_P, C.c_int, C.c_double, _P, _P, _P, C.c_int,
                                C.POINTER(C.c_double), _P, _P, _P, _P]
     L.fire_adjoint.restype = C.c_int
+    L.fire_adjoint_heat.argtypes = L.fire_adjoint.argtypes
+    L.fire_adjoint_heat.restype = C.c_int
     L.fire_autotune.argtypes = [_P, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.fire_autotune.restype = C.c_int
@@ -450,6 +452,17 @@ def fire_adjoint(ctx, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, ckpt_every=
     return J.value
 
 
+def fire_adjoint_heat(ctx, nsteps, dt, wind_u_dev, wind_v_dev, q_obs_dev, ckpt_every=20,
+                      g_mult_dev=None, g_moist_dev=None, g_u_dev=None, g_v_dev=None) -> float:
+    """The heat misfit and its adjoint; returns J (gradients written in place)."""
+    J = C.c_double()
+    _check(load_library().fire_adjoint_heat(ctx, int(nsteps), float(dt), _ptr(wind_u_dev),
+                                            _ptr(wind_v_dev), _ptr(q_obs_dev), int(ckpt_every),
+                                            C.byref(J), _ptr(g_mult_dev), _ptr(g_moist_dev),
+                                            _ptr(g_u_dev), _ptr(g_v_dev)), "fire_adjoint_heat")
+    return J.value
+
+
 def fire_autotune(ctx, wind_u_dev, wind_v_dev, dt, probe_steps=3):
     """Times candidate step-kernel shapes, keeps the fastest; returns
     (variant, kx, ky)."""
@@ -577,6 +590,23 @@ class FireModel:
         gu = torch.empty((self.nya, self.nxa + 1), **f64)
         gv = torch.empty((self.nya + 1, self.nxa), **f64)
         J = fire_adjoint(self.ctx, nsteps, dt, u, v, tobs, ckpt_every, gm, gM, gu, gv)
+        return J, gm, gM, gu, gv
+
+    def adjoint_heat(self, u, v, dt, nsteps, qobs, ckpt_every=20, grads=True):
+        """J = 1/2 sum over atmospheric cells of (Q - q_obs)^2, Q the sensible
+        heat released per unit area over the nsteps steps, and (if grads) its
+        gradients as adjoint().  Advances the model like run()."""
+        torch = self.torch
+        qobs = torch.as_tensor(qobs).to(self.device, torch.float64).contiguous()
+        if not grads:
+            return (fire_adjoint_heat(self.ctx, nsteps, dt, u, v, qobs, ckpt_every), None, None,
+                    None, None)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        gm = torch.empty((self.ny, self.nx), **f64)
+        gM = torch.empty_like(gm)
+        gu = torch.empty((self.nya, self.nxa + 1), **f64)
+        gv = torch.empty((self.nya + 1, self.nxa), **f64)
+        J = fire_adjoint_heat(self.ctx, nsteps, dt, u, v, qobs, ckpt_every, gm, gM, gu, gv)
         return J, gm, gM, gu, gv
 
     @property

@@ -67,6 +67,7 @@ struct AdjArgs {
     const double *coef, *dcoef;  // [ncls][K_N]
     int ncls;
     const double *tign0, *tign, *tobs;
+    const double *dJdt;  // dJ/dt_i per node instead of t_i - t_obs (heat misfit), or null
     const double *tsp;  // [2] start and end time of the step (device)
     double dt;
     T *lam, *mu, *ls;
@@ -243,14 +244,14 @@ __device__ __forceinline__ bool finite_bits(double x) {
 template <typename T>
 __device__ __forceinline__ bool crossed(const AdjArgs<T> &a, size_t k, double &q0, double &q1,
                                         double &r) {
-    const double t0 = a.tign0[k], ti = a.tign[k], to = a.tobs[k];
+    const double t0 = a.tign0[k], ti = a.tign[k], to = a.dJdt ? a.dJdt[k] : a.tobs[k];
     if (!inf_bits(t0) || !finite_bits(ti) || !finite_bits(to)) return false;
     const T p0 = a.pa[k], p1 = a.pb[k];
     if (!(p0 > T(0) && p1 <= T(0))) return false;
     if (!(ti >= a.tsp[0] && ti <= a.tsp[1])) return false;
     q0 = (double)p0;
     q1 = (double)p1;
-    r = ti - to;
+    r = a.dJdt ? to : ti - to;
     return true;
 }
 
@@ -427,6 +428,262 @@ __global__ void k_adj_wind(const AdjArgs<T> a, double *gu, double *gv) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Heat misfit.  Q_I = sensible heat released per unit area of atmospheric
+// cell I over the run = sum over its fire cells of (F_start - F_end) H_s /
+// (srx sry) (the time integral of eqs. sensible-heat-flux / average, which
+// telescopes), J = 1/2 sum over observed cells of (Q_I - q_obs,I)^2.  Its
+// seeds for the reverse sweep: dJ/dF_end through the quadrature of Sect. 3.3
+// into dJ/dpsi_end and dJ/dt_i, and the moisture dependence of H_s.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct HeatArgs {
+    const T *psi, *F0, *F1;  // psi and F at the end, F at the start of the run
+    const double *tign;      // t_i at the end
+    const uint8_t *fuel;
+    const double *coef, *dcoef;
+    int ncls, nx, ny, nxa, nya, srx, sry;
+    double t1;               // model time at the end
+    const double *qobs;      // [nya][nxa], NaN where unobserved
+    double *Q, *res;         // [nya][nxa]
+    double *gF, *gM;         // [n]: dJ/dF_end, moisture gradient (direct term)
+    double *lamd, *dJdt;     // [n]: dJ/dpsi_end, dJ/dt_i
+};
+
+// Q and the residual per atmospheric cell (the fire cells summed row by row)
+template <typename T>
+__global__ void k_heat_residual(const HeatArgs<T> h) {
+    const int na = h.nxa * h.nya;
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < na; I += gridDim.x * blockDim.x) {
+        const int ia = I % h.nxa, ja = I / h.nxa;
+        double q = 0.0;
+        for (int j = ja * h.sry; j < (ja + 1) * h.sry; ++j)
+            for (int i = ia * h.srx; i < (ia + 1) * h.srx; ++i) {
+                const size_t k = (size_t)j * h.nx + i;
+                const int c = min((int)h.fuel[k], h.ncls - 1);
+                q += ((double)h.F0[k] - (double)h.F1[k]) * h.coef[(size_t)c * K_N + K_HS];
+            }
+        q /= (double)(h.srx * h.sry);
+        h.Q[I] = q;
+        h.res[I] = finite_bits(h.qobs[I]) ? q - h.qobs[I] : 0.0;
+    }
+}
+
+// per fire cell: dJ/dF_end = -res H_s / (srx sry), and the direct moisture
+// term res (F_start - F_end) dH_s/dM_f / (srx sry)
+template <typename T>
+__global__ void k_heat_seed(const HeatArgs<T> h) {
+    const size_t n = (size_t)h.nx * h.ny;
+    const double r2 = (double)(h.srx * h.sry);
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % h.nx), j = (int)(k / h.nx);
+        const double r = h.res[(j / h.sry) * h.nxa + i / h.srx];
+        const int c = min((int)h.fuel[k], h.ncls - 1);
+        h.gF[k] = -r * h.coef[(size_t)c * K_N + K_HS] / r2;
+        h.gM[k] = r * ((double)h.F0[k] - (double)h.F1[k]) * h.dcoef[(size_t)c * K_N + K_HS] / r2;
+    }
+}
+
+// psi at position (x, y) of the ghost-extended mesh (x in -1..nx, y in
+// -1..ny): the extrapolated ghosts of Sect. 3.1, x first, then y
+template <typename T>
+__device__ double ext_psi(const T *psi, int nx, int ny, int x, int y) {
+    auto row = [&](int xx, int yy) -> double {  // yy inside the mesh
+        if (xx >= 0 && xx < nx) return (double)psi[(size_t)yy * nx + xx];
+        const size_t b = (size_t)yy * nx;
+        return xx < 0 ? ghost_value<double>((double)psi[b], (double)psi[b + 1])
+                      : ghost_value<double>((double)psi[b + nx - 1], (double)psi[b + nx - 2]);
+    };
+    if (y >= 0 && y < ny) return row(x, y);
+    return y < 0 ? ghost_value<double>(row(x, 0), row(x, 1))
+                 : ghost_value<double>(row(x, ny - 1), row(x, ny - 2));
+}
+
+// d F_cell / d(window psi) and d F_cell / d(window t^) of the quadrature of
+// Sect. 3.3 (eqs. fuel_left_subcells, approx-fraction, ti-comp) for the cell
+// whose 3x3 node window is w[9] (psi) and th[9] (t^, already t1 where the
+// node's psi >= 0): four subcells of the cell centre, two edge midpoints
+// and a corner (bilinear means of the nodes), burned = beta (1 - e),
+// beta = (1 - sum psi / sum |psi|) / 2, e = exp(-sum (t1 - t^) / (4 T_f)),
+// F = 1 - mean of the four burned fractions.  Branches as the forward took
+// them: a vertex with psi >= 0 takes t1 (no t^ dependence), |x|' = sign(x).
+__device__ void quad_partials(const double *w, const double *th, double t1, double Tf,
+                              double *dw, double *dth) {
+    // vertices: node lists (up to 4 nodes, mean) of the centre, the four edge
+    // midpoints and the four corners, indexed by window position 3b + a
+    double vp[9], vt[9];
+    int vn[9][4], vc[9];
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const int v = 3 * b + a, xs[2] = {a == 0 ? 0 : 1, a == 2 ? 2 : 1},
+                      ys[2] = {b == 0 ? 0 : 1, b == 2 ? 2 : 1};
+            int m = 0;
+            for (int yy = 0; yy < (ys[0] == ys[1] ? 1 : 2); ++yy)
+                for (int xx = 0; xx < (xs[0] == xs[1] ? 1 : 2); ++xx) vn[v][m++] = 3 * ys[yy] + xs[xx];
+            vc[v] = m;
+            double sp = 0.0, st = 0.0;
+            if (m == 1) {
+                sp = w[vn[v][0]];
+                st = th[vn[v][0]];
+            } else if (m == 2) {
+                sp = 0.5 * (w[vn[v][0]] + w[vn[v][1]]);
+                st = 0.5 * (th[vn[v][0]] + th[vn[v][1]]);
+            } else {
+                sp = 0.25 * (w[vn[v][0]] + w[vn[v][1]] + w[vn[v][2]] + w[vn[v][3]]);
+                st = 0.25 * (th[vn[v][0]] + th[vn[v][1]] + th[vn[v][2]] + th[vn[v][3]]);
+            }
+            vp[v] = sp;
+            vt[v] = sp >= 0.0 ? t1 : st;
+        }
+    double gv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int sub = 0; sub < 4; ++sub) {
+        const int cx = (sub & 1) ? 2 : 0, cy = (sub & 2) ? 2 : 0;
+        const int vs[4] = {4, 3 + cx, 3 * cy + 1, 3 * cy + cx};  // centre, x-edge, y-edge, corner
+        double s = 0.0, a = 0.0, tau = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            s += vp[vs[q]];
+            a += fabs(vp[vs[q]]);
+            tau += t1 - vt[vs[q]];
+        }
+        const double e = exp(-0.25 * tau / Tf);
+        const double beta = a > 0.0 ? 0.5 * (1.0 - s / a) : 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const double x = vp[vs[q]];
+            const double sg = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
+            // dF/dbeta = -(1 - e)/4; dbeta/dx = (s sg / a - 1) / (2 a)
+            if (a > 0.0) gv[vs[q]] += -0.25 * (1.0 - e) * 0.5 * (s * sg / a - 1.0) / a;
+            // dF/dt^_vertex = -(1/4) d burned / dt^ = beta e / (16 T_f)
+            gt[vs[q]] += 0.0625 * beta * e / Tf;
+        }
+    }
+    for (int q = 0; q < 9; ++q) {
+        dw[q] = 0.0;
+        dth[q] = 0.0;
+    }
+    for (int v = 0; v < 9; ++v) {
+        const double f = 1.0 / vc[v];
+        for (int m = 0; m < vc[v]; ++m) {
+            dw[vn[v][m]] += f * gv[v];
+            if (vp[v] < 0.0) dth[vn[v][m]] += f * gt[v];
+        }
+    }
+}
+
+// the window of cell (i, j) at the end of the run and its partials times
+// dJ/dF of the cell; false when the cell contributes nothing
+template <typename T>
+__device__ bool heat_cell(const HeatArgs<T> &h, int i, int j, double *dw, double *dth,
+                          double *w) {
+    const size_t k = (size_t)j * h.nx + i;
+    const double g = h.gF[k];
+    if (g == 0.0) return false;
+    double th[9];
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const int x = i + a - 1, y = j + b - 1;
+            const double p = ext_psi(h.psi, h.nx, h.ny, x, y);
+            // t^ of the position: t1 where its psi >= 0, else the copied t^ of
+            // the nearest node (t_i where that node's psi < 0, else t1)
+            const int xc = min(max(x, 0), h.nx - 1), yc = min(max(y, 0), h.ny - 1);
+            const size_t kc = (size_t)yc * h.nx + xc;
+            w[3 * b + a] = p;
+            th[3 * b + a] = (p >= 0.0 || !((double)h.psi[kc] < 0.0)) ? h.t1 : h.tign[kc];
+        }
+    const int c = min((int)h.fuel[k], h.ncls - 1);
+    quad_partials(w, th, h.t1, h.coef[(size_t)c * K_N + K_TF], dw, dth);
+    for (int q = 0; q < 9; ++q) {
+        dw[q] *= g;
+        dth[q] *= g;
+    }
+    return true;
+}
+
+// per node: the contributions of the (up to 9) cells whose window holds the
+// node itself (the ghost positions of the boundary cells are added by
+// k_heat_ghosts)
+template <typename T>
+__global__ void k_heat_gather(const HeatArgs<T> h) {
+    const size_t n = (size_t)h.nx * h.ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % h.nx), j = (int)(k / h.nx);
+        const bool tnode = (double)h.psi[k] < 0.0;
+        double lp = 0.0, lt = 0.0, dw[9], dth[9], w[9];
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int ci = i - dx, cj = j - dy;  // cell whose window has this node at (dx, dy)
+                if (ci < 0 || ci >= h.nx || cj < 0 || cj >= h.ny) continue;
+                if (!heat_cell(h, ci, cj, dw, dth, w)) continue;
+                const int q = 3 * (dy + 1) + (dx + 1);
+                lp += dw[q];
+                if (tnode) lt += dth[q];
+            }
+        h.lamd[k] = lp;
+        h.dJdt[k] = lt;
+    }
+}
+
+// the ghost positions of the boundary cells' windows, one thread in a fixed
+// order: psi ghosts back to the nodes they extrapolate (x ghosts, and y
+// ghosts of the extended columns, corners included), t^ ghosts to the node
+// they copy
+template <typename T>
+__global__ void k_heat_ghosts(const HeatArgs<T> h) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int nx = h.nx, ny = h.ny;
+    auto add_row = [&](int x, int y, double d) {  // d/d(psi at (x, y)), y inside
+        if (x >= 0 && x < nx) {
+            h.lamd[(size_t)y * nx + x] += d;
+            return;
+        }
+        const size_t b = (size_t)y * nx;
+        const int e0 = x < 0 ? 0 : nx - 1, e1 = x < 0 ? 1 : nx - 2;
+        double d0, d1;
+        ghost_partials<double>((double)h.psi[b + e0], (double)h.psi[b + e1], d0, d1);
+        h.lamd[b + e0] += d * d0;
+        h.lamd[b + e1] += d * d1;
+    };
+    auto add_psi = [&](int x, int y, double d) {
+        if (y >= 0 && y < ny) {
+            add_row(x, y, d);
+            return;
+        }
+        const int f0 = y < 0 ? 0 : ny - 1, f1 = y < 0 ? 1 : ny - 2;
+        double d0, d1;
+        ghost_partials<double>(ext_psi(h.psi, nx, ny, x, f0), ext_psi(h.psi, nx, ny, x, f1), d0,
+                               d1);
+        add_row(x, f0, d * d0);
+        add_row(x, f1, d * d1);
+    };
+    double dw[9], dth[9], w[9];
+    const long nb = 2L * nx + 2L * (ny - 2);
+    for (long q = 0; q < nb; ++q) {
+        int i, j;  // boundary cells: bottom row, top row, then the side columns
+        if (q < nx) { i = (int)q; j = 0; }
+        else if (q < 2L * nx) { i = (int)(q - nx); j = ny - 1; }
+        else { const long r = q - 2L * nx; i = (r & 1) ? nx - 1 : 0; j = 1 + (int)(r >> 1); }
+        if (!heat_cell(h, i, j, dw, dth, w)) continue;
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) {
+                const int x = i + a - 1, y = j + b - 1;
+                if (x >= 0 && x < nx && y >= 0 && y < ny) continue;  // k_heat_gather's
+                add_psi(x, y, dw[3 * b + a]);
+                const int xc = min(max(x, 0), nx - 1), yc = min(max(y, 0), ny - 1);
+                const size_t kc = (size_t)yc * nx + xc;
+                if (w[3 * b + a] < 0.0 && (double)h.psi[kc] < 0.0) h.dJdt[kc] += dth[3 * b + a];
+            }
+    }
+}
+
+// lambda (path precision) at the end of the run from dJ/dpsi_end
+template <typename T>
+__global__ void k_heat_lambda(const double *lamd, T *lam, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        lam[k] = T(lamd[k]);
+}
+
 // J = 1/2 sum (t_i - t_obs)^2 over nodes ignited in both: fixed-shape tree
 // sums (block partials, then one block), so the result is reproducible
 __global__ void k_misfit_partial(const double *tign, const double *tobs, size_t n, double *part) {
@@ -489,10 +746,11 @@ int c_nya(fire_ctx *c) {
     return a.nya;
 }
 
+// tobs: the arrival-time misfit; qobs (with tobs null): the heat misfit
 template <typename T>
 int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v,
-                const double *tobs, int K, double *J_host, double *g_mult, double *g_moist,
-                double *g_u, double *g_v) {
+                const double *tobs, const double *qobs, int K, double *J_host, double *g_mult,
+                double *g_moist, double *g_u, double *g_v) {
     int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
     double t0;
     ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t0);
@@ -524,6 +782,9 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t o_times = take((nsteps + 2) * sizeof(double));
     const size_t o_tseg = take((K + 2) * sizeof(double));
     const size_t o_small = take(16 + kMisfitBlocks * sizeof(double) + 16);
+    const size_t na = (size_t)c_nxa(c) * c_nya(c);
+    const size_t o_F0 = take(qobs ? n * E : 0);                   // F at the start (heat)
+    const size_t o_Qr = take(qobs ? 2 * na * sizeof(double) : 0);  // Q, residual (heat)
     const size_t o_lam = take(3 * n * E);
     const size_t o_C = take(10 * n * E);
     const size_t o_g = take(4 * n * sizeof(double));
@@ -531,6 +792,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t nu = (size_t)c_nya(c) * (c_nxa(c) + 1), nv = (size_t)(c_nya(c) + 1) * c_nxa(c);
     const size_t o_dco = take(sizeof(double) * K_N * ncls);
     const size_t o_wind = take(sizeof(double) * (nu + nv));
+    const size_t o_hs = take(qobs ? 3 * n * sizeof(double) : 0);  // dJ/dF, dJ/dpsi, dJ/dt_i
     void *wsv = nullptr;
     int r = ctx_workspace(c, grads ? off : o_lam, &wsv);
     if (r) return r;
@@ -550,6 +812,8 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     StepArgs sa;
     ctx_step_args(c, cur, u, v, dt, nullptr, nullptr, sa);
     ADJ_CHECK(cudaMemcpyAsync(tign0, sa.tign, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    T *F0 = reinterpret_cast<T *>(ws + o_F0);
+    if (qobs) ADJ_CHECK(cudaMemcpyAsync(F0, sa.F_in, n * E, cudaMemcpyDeviceToDevice, st));
     ADJ_CHECK(cudaMemcpyAsync(tdev, times.data(), (nsteps + 1) * sizeof(double),
                               cudaMemcpyHostToDevice, st));
 
@@ -568,7 +832,37 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     }
     const double *tign_final = sa.tign;
     ADJ_CHECK(cudaGetLastError());
-    k_misfit_partial<<<kMisfitBlocks, kAdjThreads, 0, st>>>(tign_final, tobs, n, part);
+    HeatArgs<T> h;
+    memset(&h, 0, sizeof h);
+    if (qobs) {
+        // the state at the end of the run
+        StepArgs fin;
+        int pc, pv, a1, a2, a3, a4, a5, a6, a7, pcur;
+        double tt;
+        ctx_info(c, &pc, &pv, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &pcur, &tt);
+        ctx_step_args(c, pcur, u, v, dt, nullptr, nullptr, fin);
+        h.psi = static_cast<const T *>(fin.psi_in);
+        h.F0 = F0;
+        h.F1 = static_cast<const T *>(fin.F_in);
+        h.tign = tign_final;
+        h.fuel = sa.fuel;
+        h.coef = sa.coef;
+        h.ncls = ncls;
+        h.nx = nx;
+        h.ny = ny;
+        h.nxa = sa.nxa;
+        h.nya = sa.nya;
+        h.srx = srx;
+        h.sry = sry;
+        h.t1 = times[nsteps];
+        h.qobs = qobs;
+        h.Q = reinterpret_cast<double *>(ws + o_Qr);
+        h.res = h.Q + na;
+        k_heat_residual<T><<<(int)((na + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, st>>>(h);
+        k_misfit_partial<<<kMisfitBlocks, kAdjThreads, 0, st>>>(h.Q, qobs, na, part);
+    } else {
+        k_misfit_partial<<<kMisfitBlocks, kAdjThreads, 0, st>>>(tign_final, tobs, n, part);
+    }
     k_misfit_final<<<1, kAdjThreads, 0, st>>>(part, kMisfitBlocks, Jdev);
     ADJ_CHECK(cudaGetLastError());
     ADJ_CHECK(cudaMemcpyAsync(J_host, Jdev, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -604,6 +898,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     a.tign0 = tign0;
     a.tign = tign_final;
     a.tobs = tobs;
+    a.dJdt = nullptr;
     a.dt = dt;
     a.lam = lam;
     a.mu = mu;
@@ -642,6 +937,22 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     }
     const size_t want = (n + kAdjThreads - 1) / kAdjThreads;
     const int grid = (int)(want < (size_t)sms * 8 ? want : (size_t)sms * 8);
+    if (qobs) {
+        // seeds of the heat misfit: dJ/dF and the H_s moisture term, the
+        // quadrature's transpose into dJ/dpsi_end (lambda) and dJ/dt_i
+        double *hs = reinterpret_cast<double *>(ws + o_hs);
+        h.dcoef = dcoef;
+        h.gF = hs;
+        h.gM = gM;
+        h.lamd = hs + n;
+        h.dJdt = hs + 2 * n;
+        k_heat_seed<T><<<grid, kAdjThreads, 0, st>>>(h);
+        k_heat_gather<T><<<grid, kAdjThreads, 0, st>>>(h);
+        k_heat_ghosts<T><<<1, 1, 0, st>>>(h);
+        k_heat_lambda<T><<<grid, kAdjThreads, 0, st>>>(h.lamd, lam, n);
+        ADJ_CHECK(cudaGetLastError());
+        a.dJdt = h.dJdt;
+    }
 
     // One segment: ring slot 0 holds its checkpoint and tseg its step times,
     // so every segment of a given length issues the same launches: the
@@ -694,7 +1005,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         return (h ^ x) * 0x100000001b3ULL + (h >> 29);
     };
     unsigned long long key0 = 0xcbf29ce484222325ULL;
-    const void *ptrs[] = {ws, u, v, tobs, sa.mult, sa.coef, sa.fuel, sa.dzdy, sa.dzdx, sa.tign};
+    const void *ptrs[] = {ws, u, v, tobs, qobs, sa.mult, sa.coef, sa.fuel, sa.dzdy, sa.dzdx, sa.tign};
     for (const void *q : ptrs) key0 = mix(key0, (unsigned long long)(uintptr_t)q);
     unsigned long long dtb;
     memcpy(&dtb, &dt, sizeof dtb);
@@ -771,8 +1082,27 @@ extern "C" int fire_adjoint(fire_ctx *c, int nsteps, double dt, const void *wind
     wf::ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
     const int K = ckpt_every < nsteps ? ckpt_every : nsteps;
     return prec == FIRE_FP64
-               ? wf::run_adjoint<double>(c, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, K,
-                                         J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev)
-               : wf::run_adjoint<float>(c, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, K,
-                                        J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev);
+               ? wf::run_adjoint<double>(c, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, nullptr,
+                                         K, J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev)
+               : wf::run_adjoint<float>(c, nsteps, dt, wind_u_dev, wind_v_dev, t_obs_dev, nullptr,
+                                        K, J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev);
+}
+
+extern "C" int fire_adjoint_heat(fire_ctx *c, int nsteps, double dt, const void *wind_u_dev,
+                                 const void *wind_v_dev, const double *q_obs_dev, int ckpt_every,
+                                 double *J_host, double *g_mult_dev, double *g_moist_dev,
+                                 double *g_u_dev, double *g_v_dev) {
+    if (!c || !wind_u_dev || !wind_v_dev || !q_obs_dev || !J_host || nsteps < 1 ||
+        ckpt_every < 1 || !isfinite(dt) || !(dt > 0.0))
+        return FIRE_ERR_ARG;
+    int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
+    double t;
+    wf::ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
+    if (nx < 2 || ny < 2) return FIRE_ERR_ARG;
+    const int K = ckpt_every < nsteps ? ckpt_every : nsteps;
+    return prec == FIRE_FP64
+               ? wf::run_adjoint<double>(c, nsteps, dt, wind_u_dev, wind_v_dev, nullptr, q_obs_dev,
+                                         K, J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev)
+               : wf::run_adjoint<float>(c, nsteps, dt, wind_u_dev, wind_v_dev, nullptr, q_obs_dev,
+                                        K, J_host, g_mult_dev, g_moist_dev, g_u_dev, g_v_dev);
 }

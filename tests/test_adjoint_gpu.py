@@ -320,3 +320,82 @@ def test_full_size_central_differences_32_directions(pkg):
     print("checked", checked, "of 32, worst rel", worst)
     assert checked >= 16
     m.close()
+
+
+# ---------------------------------------------------------------------------
+# heat misfit (fire_adjoint_heat)
+# ---------------------------------------------------------------------------
+
+def heat_observations(w, nsteps):
+    """Sensible heat released per atmospheric cell over the run by an oracle
+    'truth' run (multiplier x1.2, moisture -0.02, wind x1.1): the time
+    integral of its heat flux output."""
+    classes = [dict(c, fuelmc_g=max(0.01, c["fuelmc_g"] - 0.02)) for c in w.classes]
+    f = oracle.OracleFire.from_workload(w, classes=classes, mult=w.mult * 1.2)
+    Q = np.zeros((w.nya, w.nxa))
+    for _ in range(nsteps):
+        hs, _, _ = f.step(w.u * 1.1, w.v * 1.1, w.dt)
+        Q += hs * w.dt
+    return Q
+
+
+def gpu_adjoint_heat(pkg, w, prec, nsteps, qobs, ckpt):
+    m = pkg.FireModel.from_workload(w, precision=prec)
+    u, v = m.wind(w.u, w.v)
+    J, gm, gM, gu, gv = m.adjoint_heat(u, v, w.dt, nsteps, qobs, ckpt_every=ckpt)
+    out = (J, gm.cpu().numpy(), gM.cpu().numpy(), gu.cpu().numpy(), gv.cpu().numpy())
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("variant", ["center", "anisotropic", "corner"])
+def test_heat_fp64_matches_oracle_adjoint(pkg, variant):
+    w = small_case(dy_atm=14.0 if variant == "anisotropic" else None)
+    if variant == "corner":
+        # the fire at the domain corner: the quadrature's ghosts carry t_i
+        w.ignitions = [synth.point_ignition(1.0, 1.0, radius=7.0)]
+    nsteps = 50
+    qobs = heat_observations(w, nsteps)
+    qobs[0, 0] = np.nan  # an unobserved cell
+    ref = oracle.OracleFire.from_workload(w)
+    Jr, gmr, gMr, gur, gvr = ref.adjoint_heat(w.u, w.v, w.dt, nsteps, qobs)
+    assert Jr > 0
+    J, gm, gM, gu, gv = gpu_adjoint_heat(pkg, w, "fp64", nsteps, qobs, ckpt=7)
+    assert abs(J - Jr) <= 1e-10 * Jr
+    for g, gr, name in ((gm, gmr, "mult"), (gM, gMr, "moist"), (gu, gur, "u"), (gv, gvr, "v")):
+        e = rel(g, gr)
+        print(f"heat {variant} fp64 d{name}: rel err {e:.2e}")
+        assert e <= 1e-8, (name, e)
+
+
+def test_heat_checkpoint_interval_and_misfit_only_call(pkg):
+    w = small_case(seed=9)
+    nsteps = 40
+    qobs = heat_observations(w, nsteps)
+    outs = [gpu_adjoint_heat(pkg, w, "fp64", nsteps, qobs, ckpt=k) for k in (1, 7, 40)]
+    for o in outs[1:]:
+        assert o[0] == outs[0][0]
+        for a, b in zip(o[1:], outs[0][1:]):
+            assert np.array_equal(a, b)
+    m = pkg.FireModel.from_workload(w, precision="fp64")
+    u, v = m.wind(w.u, w.v)
+    J, *rest = m.adjoint_heat(u, v, w.dt, nsteps, qobs, grads=False)
+    assert J == outs[0][0] and all(r is None for r in rest)
+    m.close()
+
+
+def test_heat_fp32_against_fp64_oracle(pkg):
+    """FP32 state and partials: the heat-misfit gradient within 2e-3 of the
+    FP64 oracle's in norm."""
+    w = small_case(seed=13)
+    nsteps = 50
+    qobs = heat_observations(w, nsteps)
+    ref = oracle.OracleFire.from_workload(w)
+    Jr, gmr, gMr, gur, gvr = ref.adjoint_heat(w.u, w.v, w.dt, nsteps, qobs)
+    J, gm, gM, gu, gv = gpu_adjoint_heat(pkg, w, "fp32", nsteps, qobs, ckpt=10)
+    print("heat fp32 J", J, Jr)
+    assert abs(J - Jr) <= 2e-3 * Jr
+    for g, gr, name in ((gm, gmr, "mult"), (gM, gMr, "moist"), (gu, gur, "u"), (gv, gvr, "v")):
+        e = rel(g, gr)
+        print(f"heat fp32 d{name}: rel err {e:.2e}")
+        assert e <= 2e-3, (name, e)
