@@ -490,7 +490,9 @@ def _clone_state(st):
 def bench_adjoint(pkg, dev, ckpt=20):
     """fire_adjoint on the 510x510 adjoint workload (400 steps of 0.5 s,
     checkpoints every 20): misfit against the arrival times of a perturbed
-    truth run, gradients w.r.t. multiplier, moisture and wind.  Cell-steps/s
+    truth run, gradients w.r.t. multiplier, moisture and wind; and
+    fire_adjoint_heat against the heat that run released per atmospheric
+    cell.  Cell-steps/s
     of the whole call (forward with checkpoints + reverse sweep) and of the
     plain FP64 forward on the same mesh, each with its autotuned kernel."""
     import torch
@@ -502,7 +504,12 @@ def bench_adjoint(pkg, dev, ckpt=20):
     tr = pkg.FireModel.from_workload(wt, precision="fp64", device=dev)
     ut, vt = tr.wind(w.u * truth["wind_scale"], w.v * truth["wind_scale"])
     tr.autotune(ut, vt, w.dt)
-    tr.run(w.steps, ut, vt, w.dt)
+    # the truth run, also summing its heat flux for the heat-misfit
+    # observations (sensible heat released per atmospheric cell)
+    qobs = torch.zeros((w.nya, w.nxa), dtype=torch.float64, device=dev)
+    for _ in range(w.steps):
+        hs, _ = tr.step(ut, vt, w.dt)
+        qobs += hs * w.dt
     tobs = tr.state()[1]
     tobs = torch.where(torch.isfinite(tobs), tobs, torch.full_like(tobs, float("nan")))
     tr.close()
@@ -531,6 +538,17 @@ def bench_adjoint(pkg, dev, ckpt=20):
         rec = {"value": n / (ms / 1e3), "ms": ms, "J": J,
                "kernel": {"variant": ["tile", "march", "warp"][kern[0]],
                           "tile_atmos_cells": list(kern[1:])}}
+        # the heat-misfit adjoint on the same run (warm-up, then timed)
+        m.set_state(*st0)
+        m.adjoint_heat(u, v, w.dt, w.steps, qobs, ckpt)
+        m.set_state(*st0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        Jh, *_ = m.adjoint_heat(u, v, w.dt, w.steps, qobs, ckpt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hms = e0.elapsed_time(e1)
+        rec["heat_misfit"] = {"value": n / (hms / 1e3), "ms": hms, "J": Jh}
         # the plain forward on the same mesh and kernel
         m.set_state(*st0)
         m.run(2, u, v, w.dt)
@@ -546,6 +564,8 @@ def bench_adjoint(pkg, dev, ckpt=20):
         m.close()
     base = out["fp64"]["plain_forward"]["value"]
     out["speedup_vs_fp64_plain_forward"] = {p: out[p]["value"] / base for p in ("fp64", "fp32")}
+    out["heat_misfit_speedup_vs_fp64_plain_forward"] = {
+        p: out[p]["heat_misfit"]["value"] / base for p in ("fp64", "fp32")}
 
     def rel(a, b):
         return float(torch.linalg.norm((a - b).flatten()) / max(float(torch.linalg.norm(b.flatten())), 1e-300))

@@ -625,24 +625,14 @@ class FireModel:
             pass
 
 
-def _fire_adjoint_function():
+def _fire_adjoint_function(objective="arrival"):
     import torch
 
-    class FireAdjointFn(torch.autograd.Function):
-        """J(m, M_f, u, v) = 1/2 sum over nodes ignited in both of
-        (t_i - t_obs)^2 after nsteps steps from the given initial state, as a
-        differentiable torch function of the per-node spread multiplier m
-        [ny][nx], the per-class fuel moisture [n_classes] and the staggered
-        wind u [nya][nxa+1], v [nya+1][nxa].  The forward call runs
-        fire_adjoint (forward sweep, checkpoints and the reverse sweep in the
-        CUDA library) and keeps the gradients; backward scales them.  The
-        per-class moisture gradient sums the per-node one over the class map.
+    heat = objective == "heat"
 
-        apply(model, state0, mult, moisture, u, v, t_obs, dt, nsteps, ckpt_every)
-        with state0 = (psi, tign, frac, t) as returned by FireModel.state()."""
-
+    class _Fn(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, model, state0, mult, moisture, u, v, t_obs, dt, nsteps, ckpt_every):
+        def forward(ctx, model, state0, mult, moisture, u, v, obs, dt, nsteps, ckpt_every):
             psi0, tign0, frac0, t0 = state0
             model.set_state(psi0, tign0, frac0, t0)
             model.set_mult(mult.detach())
@@ -652,7 +642,8 @@ def _fire_adjoint_function():
             model.set_classes(classes)
             ud = u.detach().to(model.device, model.dtype).contiguous()
             vd = v.detach().to(model.device, model.dtype).contiguous()
-            J, gm, gM, gu, gv = model.adjoint(ud, vd, dt, nsteps, t_obs, ckpt_every)
+            run = model.adjoint_heat if heat else model.adjoint
+            J, gm, gM, gu, gv = run(ud, vd, dt, nsteps, obs, ckpt_every)
             gcls = torch.zeros(len(classes), dtype=torch.float64, device=model.device)
             gcls.index_add_(0, model.fuel_dev.long().clamp(max=len(classes) - 1).flatten(),
                             gM.flatten())
@@ -668,12 +659,42 @@ def _fire_adjoint_function():
                                                              ctx.devices)]
             return (None, None, out[0], out[1], out[2], out[3], None, None, None, None)
 
+    if heat:
+        class FireHeatAdjointFn(_Fn):
+            """J(m, M_f, u, v) = 1/2 sum over atmospheric cells with a finite
+            observation of (Q - q_obs)^2, Q the sensible heat released per
+            unit area over nsteps steps from the given initial state, as a
+            differentiable torch function of the per-node spread multiplier
+            m [ny][nx], the per-class fuel moisture [n_classes] and the
+            staggered wind u [nya][nxa+1], v [nya+1][nxa].  The forward call
+            runs fire_adjoint_heat and keeps the gradients; backward scales
+            them.
+
+            apply(model, state0, mult, moisture, u, v, q_obs, dt, nsteps,
+            ckpt_every) with q_obs [nya][nxa] and state0 as for
+            FireAdjointFn."""
+
+        return FireHeatAdjointFn
+
+    class FireAdjointFn(_Fn):
+        """J(m, M_f, u, v) = 1/2 sum over nodes ignited in both of
+        (t_i - t_obs)^2 after nsteps steps from the given initial state, as a
+        differentiable torch function of the per-node spread multiplier m
+        [ny][nx], the per-class fuel moisture [n_classes] and the staggered
+        wind u [nya][nxa+1], v [nya+1][nxa].  The forward call runs
+        fire_adjoint (forward sweep, checkpoints and the reverse sweep in the
+        CUDA library) and keeps the gradients; backward scales them.  The
+        per-class moisture gradient sums the per-node one over the class map.
+
+        apply(model, state0, mult, moisture, u, v, t_obs, dt, nsteps, ckpt_every)
+        with state0 = (psi, tign, frac, t) as returned by FireModel.state()."""
+
     return FireAdjointFn
 
 
 def __getattr__(name):
-    if name == "FireAdjointFn":
-        fn = _fire_adjoint_function()
-        globals()["FireAdjointFn"] = fn
+    if name in ("FireAdjointFn", "FireHeatAdjointFn"):
+        fn = _fire_adjoint_function("heat" if name == "FireHeatAdjointFn" else "arrival")
+        globals()[name] = fn
         return fn
     raise AttributeError(name)

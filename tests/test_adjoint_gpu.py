@@ -399,3 +399,30 @@ def test_heat_fp32_against_fp64_oracle(pkg):
         e = rel(g, gr)
         print(f"heat fp32 d{name}: rel err {e:.2e}")
         assert e <= 2e-3, (name, e)
+
+
+def test_heat_autograd_function(pkg):
+    import torch
+    w = small_case(seed=13)
+    nsteps = 40
+    qobs = torch.as_tensor(heat_observations(w, nsteps)).cuda()
+    m = pkg.FireModel.from_workload(w, precision="fp64")
+    st0 = tuple(x.clone() if hasattr(x, "clone") else x for x in m.state())
+    mult = torch.as_tensor(w.mult).cuda().double().requires_grad_(True)
+    moist = torch.tensor([c["fuelmc_g"] for c in w.classes], dtype=torch.float64,
+                         requires_grad=True)
+    u = torch.as_tensor(w.u).cuda().double().requires_grad_(True)
+    v = torch.as_tensor(w.v).cuda().double().requires_grad_(True)
+    J = pkg.FireHeatAdjointFn.apply(m, st0, mult, moist, u, v, qobs, w.dt, nsteps, 10)
+    (0.5 * J).backward()
+    m2 = pkg.FireModel.from_workload(w, precision="fp64")
+    J2, gm, gM, gu, gv = m2.adjoint_heat(*m2.wind(w.u, w.v), w.dt, nsteps, qobs, ckpt_every=10)
+    assert float(J.detach()) == J2 and J2 > 0
+    assert torch.equal(mult.grad, 0.5 * gm)
+    assert torch.equal(u.grad, 0.5 * gu) and torch.equal(v.grad, 0.5 * gv)
+    fuel = torch.as_tensor(w.fuel).cuda().long().flatten()
+    gcls = torch.zeros(len(w.classes), dtype=torch.float64, device="cuda").index_add_(
+        0, fuel, gM.flatten())
+    assert torch.allclose(moist.grad, 0.5 * gcls.cpu(), rtol=1e-14, atol=0)
+    m.close()
+    m2.close()
