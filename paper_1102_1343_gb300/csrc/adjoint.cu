@@ -1,5 +1,7 @@
 // fire_adjoint: gradient of the arrival-time misfit
 //   J = 1/2 sum over nodes ignited in both runs of (t_i - t_obs)^2
+// (fire_adjoint_heat: of the heat misfit, see the HeatArgs section below,
+// whose seeds enter the same reverse sweep)
 // with respect to the per-node spread multiplier, the per-node fuel moisture
 // and the staggered wind, by a reverse sweep through the Heun stages
 // (eq. Heun), the upwinded right-hand side (eqs. F-disc, Godunov,
