@@ -56,3 +56,27 @@ def test_strerror_and_argument_checks_without_gpu(lib):
                          None) == pkg.FIRE_ERR_ARG
     assert lib.fire_step(None, None, None, 0.5, None, None) == pkg.FIRE_ERR_ARG
     assert lib.fire_status(None) == pkg.FIRE_ERR_ARG
+
+
+def test_null_context_is_rejected_by_every_entry_point(lib):
+    """Each call returns a status and never aborts: a null context (or null
+    required pointers) gives FIRE_ERR_ARG before any device work, so this
+    runs without a GPU."""
+    import paper_1102_1343_gb300 as pkg
+    J = C.c_double()
+    i1, i2, i3 = C.c_int(), C.c_int(), C.c_int()
+    E = pkg.FIRE_ERR_ARG
+    assert lib.fire_run(None, 3, 0.5, None, None, None, None) == E
+    assert lib.fire_step_host(None, None, None, 0.5, None, None) == E
+    assert lib.fire_get_state(None, None, None, None, None) == E
+    assert lib.fire_set_state(None, None, None, None, 0.0) == E
+    assert lib.fire_set_kernel(None, 0, 1, 1) == E
+    assert lib.fire_get_kernel(None, C.byref(i1), C.byref(i2), C.byref(i3)) == E
+    assert lib.fire_adjoint(None, 10, 0.5, None, None, None, 5, C.byref(J), None, None, None,
+                            None) == E
+    assert lib.fire_adjoint_heat(None, 10, 0.5, None, None, None, 5, C.byref(J), None, None,
+                                 None, None) == E
+    assert lib.fire_autotune(None, None, None, 0.5, 2, C.byref(i1), C.byref(i2),
+                             C.byref(i3)) == E
+    assert lib.fire_default_kernel(pkg.FIRE_FP32, 10, 10, 10, 10, 0, C.byref(i1), C.byref(i2),
+                                   C.byref(i3)) == E
