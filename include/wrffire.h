@@ -242,7 +242,9 @@ int fire_adjoint(fire_ctx *ctx, int nsteps, double dt, const void *wind_u_dev,
  * of H_s and, through the fuel-fraction quadrature of Sect. 3.3, the
  * dependence of F_end on psi and on the ignition times.
  *   q_obs_dev    [ny_atm][nx_atm] double device; NaN or +-inf where not observed
- * Everything else as fire_adjoint (the mesh needs at least 2 x 2 fire nodes). */
+ * Everything else as fire_adjoint (the mesh needs at least 2 x 2 fire nodes);
+ * the workspace also holds F at the start of the run (one path-precision
+ * value per node) and three doubles per node for the seeds. */
 int fire_adjoint_heat(fire_ctx *ctx, int nsteps, double dt, const void *wind_u_dev,
                       const void *wind_v_dev, const double *q_obs_dev, int ckpt_every,
                       double *J_host, double *g_mult_dev, double *g_moist_dev, double *g_u_dev,
