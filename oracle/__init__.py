@@ -70,6 +70,8 @@ def lib():
             L = C.CDLL(build())
             L.orc_rothermel_rate.restype = C.c_double
             L.orc_rothermel_rate.argtypes = [_D, C.c_double, C.c_double, C.c_double]
+            L.orc_rothermel_intermediates.restype = None
+            L.orc_rothermel_intermediates.argtypes = [_D, C.c_double, _D]
             L.orc_fuel_coefficients.restype = None
             L.orc_fuel_coefficients.argtypes = [_D, C.c_double, _D]
             L.orc_spread_rate.restype = C.c_double
@@ -152,6 +154,23 @@ def rothermel_rate(cls: dict, U: float, tanphi: float, Mf: float | None = None) 
     v = fuel_vector(cls)
     return lib().orc_rothermel_rate(_dp(v), -1.0 if Mf is None else float(Mf), float(U),
                                     float(tanphi))
+
+
+# names of the values orc_rothermel_intermediates returns (English units)
+ROTHERMEL_FIELDS = ("sigma", "wl", "depth", "rho_p", "h", "w0", "rho_b", "beta", "beta_op", "A",
+                    "Gmax", "Gamma", "wn", "etaM", "etaS", "IR", "xi", "eps", "Qig", "R0_ftmin",
+                    "B", "C", "E", "nofuel")
+
+
+def rothermel_intermediates(cls: dict, Mf: float | None = None, library=None) -> dict:
+    """Every intermediate of the oracle's Table 2 chain for one class (dict
+    keyed by ROTHERMEL_FIELDS, English units).  ``library`` selects another
+    build of the oracle source (the mutation tests)."""
+    v = fuel_vector(cls)
+    out = np.zeros(len(ROTHERMEL_FIELDS))
+    (library or lib()).orc_rothermel_intermediates(_dp(v), -1.0 if Mf is None else float(Mf),
+                                                   _dp(out))
+    return dict(zip(ROTHERMEL_FIELDS, out.tolist()))
 
 
 def fuel_coefficients(cls: dict, Mf: float | None = None) -> np.ndarray:

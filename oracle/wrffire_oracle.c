@@ -101,6 +101,9 @@ enum { CO_S0 = 0, CO_R0, CO_B, CO_C, CO_D, CO_E, CO_TF, CO_HS, CO_HQ, CO_N };
 typedef struct {
     double R0_ftmin, B, C, E, beta, beta_op;
     int nofuel;
+    /* every intermediate of the chain, English units (for the pins) */
+    double sigma, wl, depth, rho_p, h, w0, rho_b, A, Gmax, Gamma, wn, etaM, etaS, IR, xi,
+           epsh, Qig;
 } orc_rothermel_parts;
 
 static orc_rothermel_parts rothermel_parts(const double *fc, double Mf)
@@ -144,7 +147,27 @@ static orc_rothermel_parts rothermel_parts(const double *fc, double Mf)
     p.E           = 0.715 * exp(-3.59e-4 * sigma);   /* Eq. (50) */
     p.beta        = beta;
     p.beta_op     = beta_op;
+    p.sigma = sigma; p.wl = wl; p.depth = depth; p.rho_p = rho_p; p.h = h; p.w0 = w0;
+    p.rho_b = rho_b; p.A = A; p.Gmax = Gmax; p.Gamma = Gamma; p.wn = wn; p.etaM = etaM;
+    p.etaS = etaS; p.IR = IR; p.xi = xi; p.epsh = epsh; p.Qig = Qig;
     return p;
+}
+
+/* The intermediates of the Table 2 chain for one class at moisture Mf (< 0:
+ * the class moisture), English units (BTU-lb-ft-min), in this order:
+ * sigma (1/ft), w_l (lb/ft^2), delta (ft), rho_P (lb/ft^3), h (BTU/lb), w_0,
+ * rho_b (lb/ft^3), beta, beta_op, A, Gamma_max, Gamma (1/min), w_n, eta_M,
+ * eta_S, I_R (BTU/ft^2/min), xi, epsilon, Q_ig (BTU/lb), R0 (ft/min), B, C,
+ * E, nofuel -- 24 values.  Bookkeeping only: the values rothermel_parts
+ * computes, returned so that tests can pin each step. */
+void orc_rothermel_intermediates(const double *fc, double Mf, double *out)
+{
+    if (Mf < 0.0) Mf = fc[FC_MF];
+    orc_rothermel_parts p = rothermel_parts(fc, Mf);
+    double v[24] = {p.sigma, p.wl, p.depth, p.rho_p, p.h, p.w0, p.rho_b, p.beta, p.beta_op,
+                    p.A, p.Gmax, p.Gamma, p.wn, p.etaM, p.etaS, p.IR, p.xi, p.epsh, p.Qig,
+                    p.R0_ftmin, p.B, p.C, p.E, (double)p.nofuel};
+    for (int k = 0; k < 24; ++k) out[k] = v[k];
 }
 
 /* Direct evaluation of eq. (spread): S = R0 (1 + phi_W + phi_S), in m/s,
