@@ -308,12 +308,13 @@ int fire_kernel_time_ms(fire_ctx *ctx, double *ms, long *launches);
 
 /* One fire step on caller-owned state that allocates no memory: no
  * cudaMalloc, cudaFree or allocating library call, and no context.  For
- * callers that cannot allocate device memory while they run: code being
- * captured into a CUDA graph, applications whose device memory comes from
- * their own pool or from a host framework that forbids driver allocations
- * after start-up, coupled models that must not touch the allocator inside
- * their time loop.  The paper has no counterpart: it is a way of calling the
- * same step as fire_step (same kernels, same results) without a fire_ctx.
+ * callers that cannot allocate device memory while they run: applications
+ * whose device memory comes from their own pool or from a host framework
+ * that forbids driver allocations after start-up, coupled models that must
+ * not touch the allocator inside their time loop (an allocation there can
+ * synchronise the device, or fail once the pool holds the memory).  The
+ * paper has no counterpart: it is a way of calling the same step as
+ * fire_step (same kernels, same results) without a fire_ctx.
  *   grid, classes[n_classes]  as for fire_init; 1 <= n_classes <= 64
  *                             (FIRE_MAX_CLASSES), more is FIRE_ERR_ARG
  *   psi_in/out, frac_in/out   [NY][NX] device, context precision; in and out
@@ -324,9 +325,14 @@ int fire_kernel_time_ms(fire_ctx *ctx, double *ms, long *launches);
  *   t, dt                     model time at the step start, time step (s)
  *   heat_sens_dev, heat_lat_dev  [ny_atm][nx_atm] device double, nullable
  *   status_dev                device int that faults are OR-ed into
- *                             (bit 1 boundary, 2 non-finite), nullable
+ *                             (bit 1 boundary, 2 non-finite), nullable; with
+ *                             NULL the faults go to a status word inside the
+ *                             library's fixed array that no call reads back,
+ *                             so they cannot be seen: pass status_dev to
+ *                             detect fire at the boundary or non-finite input
  *   cuda_stream               stream for all work of the call
  * Ignitions are not applied: the state passed in already holds them.
+ * Fuel classes are checked as fire_init checks them (FIRE_ERR_ARG).
  * Intermediate values (the class table, its coefficients, the start and end
  * time, and the status word when status_dev is NULL) live in one file-scope
  * device array of about 11 KB per device, held until the process exits.

@@ -328,12 +328,53 @@ def fire_kernel_time_ms(ctx):
     return ms.value, n.value
 
 
+def _check_noalloc_tensors(items):
+    """Each (name, tensor, dtype name, elements) with a torch tensor: on the
+    current CUDA device, contiguous, of that dtype and element count."""
+    dev = None
+    for name, x, dtype, n in items:
+        if x is None or not hasattr(x, "data_ptr"):
+            continue
+        import torch
+        if not x.is_cuda:
+            raise FireError(FIRE_ERR_ARG, f"fire_step_noalloc: {name} is not a CUDA tensor")
+        if dev is None:
+            dev = torch.cuda.current_device()
+        if x.device.index != dev:
+            raise FireError(FIRE_ERR_ARG,
+                            f"fire_step_noalloc: {name} is on cuda:{x.device.index}, "
+                            f"the current device is cuda:{dev}")
+        if not x.is_contiguous():
+            raise FireError(FIRE_ERR_ARG, f"fire_step_noalloc: {name} is not contiguous")
+        if x.dtype != getattr(torch, dtype):
+            raise FireError(FIRE_ERR_ARG,
+                            f"fire_step_noalloc: {name} is {x.dtype}, expected torch.{dtype}")
+        if (x.numel() != n) if name != "status" else (x.numel() < n):
+            raise FireError(FIRE_ERR_ARG,
+                            f"fire_step_noalloc: {name} has {x.numel()} elements, expected {n}")
+
+
 def fire_step_noalloc(grid: fire_grid_desc, classes, psi_in_dev, psi_out_dev, frac_in_dev,
                       frac_out_dev, tign_dev, fuel_class_dev, spread_mult_dev, dzdx_dev,
                       dzdy_dev, wind_u_dev, wind_v_dev, t, dt, heat_sens_dev=None,
                       heat_lat_dev=None, status_dev=None, cuda_stream=None) -> int:
     """One fire step on caller-owned buffers without any allocation (see the
-    header): the state is passed in and out, nothing is kept between calls."""
+    header): the state is passed in and out, nothing is kept between calls.
+    Torch tensors are checked before the call (device, layout, dtype and
+    size; FireError FIRE_ERR_ARG on a mismatch), so that a wrong buffer never
+    reaches the kernels; raw integer pointers are passed through as given."""
+    nx, ny = grid.nx_atm * grid.sr_x, grid.ny_atm * grid.sr_y
+    nxa, nya = grid.nx_atm, grid.ny_atm
+    path = "float64" if grid.precision == FIRE_FP64 else "float32"
+    _check_noalloc_tensors(
+        [("psi_in", psi_in_dev, path, nx * ny), ("psi_out", psi_out_dev, path, nx * ny),
+         ("frac_in", frac_in_dev, path, nx * ny), ("frac_out", frac_out_dev, path, nx * ny),
+         ("tign", tign_dev, "float64", nx * ny), ("fuel_class", fuel_class_dev, "uint8", nx * ny),
+         ("spread_mult", spread_mult_dev, path, nx * ny), ("dzdx", dzdx_dev, path, nx * ny),
+         ("dzdy", dzdy_dev, path, nx * ny), ("wind_u", wind_u_dev, path, nya * (nxa + 1)),
+         ("wind_v", wind_v_dev, path, (nya + 1) * nxa),
+         ("heat_sens", heat_sens_dev, "float64", nya * nxa),
+         ("heat_lat", heat_lat_dev, "float64", nya * nxa), ("status", status_dev, "int32", 1)])
     L = load_library()
     cls = make_classes(classes)
     code = L.fire_step_noalloc(C.byref(grid), cls, len(classes), _ptr(psi_in_dev),

@@ -480,13 +480,8 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
             !isfinite(s.t_start) || !isfinite(s.radius) || !isfinite(s.speed) || s.radius < 0)
             return FIRE_ERR_ARG;
     }
-    for (int k = 0; k < n_classes; ++k) {
-        const fire_fuel_class &f = classes[k];
-        if (f.fgi > 0 && !f.chaparral &&
-            !(f.savr > 0 && f.fueldepthm > 0 && f.fueldens > 0 && f.fuelmce > 0 && f.se > 0))
-            return FIRE_ERR_ARG;
-        if (!(f.weight > 0)) return FIRE_ERR_ARG;
-    }
+    for (int k = 0; k < n_classes; ++k)
+        if (!valid_fuel_class(classes[k])) return FIRE_ERR_ARG;
 
     fire_ctx *c = new (std::nothrow) fire_ctx();
     if (!c) return FIRE_ERR_OOM;
@@ -747,13 +742,8 @@ int fire_set_spread_mult(fire_ctx *c, const void *mult_dev) {
 
 int fire_set_fuel_classes(fire_ctx *c, const fire_fuel_class *classes, int n_classes) {
     if (!c || !classes || n_classes != c->ncls) return FIRE_ERR_ARG;
-    for (int k = 0; k < n_classes; ++k) {
-        const fire_fuel_class &f = classes[k];
-        if (f.fgi > 0 && !f.chaparral &&
-            !(f.savr > 0 && f.fueldepthm > 0 && f.fueldens > 0 && f.fuelmce > 0 && f.se > 0))
-            return FIRE_ERR_ARG;
-        if (!(f.weight > 0)) return FIRE_ERR_ARG;
-    }
+    for (int k = 0; k < n_classes; ++k)
+        if (!valid_fuel_class(classes[k])) return FIRE_ERR_ARG;
     WF_CHECK(cudaMemcpyAsync(c->classes_dev, classes, sizeof(fire_fuel_class) * n_classes,
                              cudaMemcpyHostToDevice, c->stream));
     WF_CHECK(launch_coefficients(c->classes_dev, n_classes, c->coef, c->stream));

@@ -122,6 +122,18 @@ cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, doubl
 cudaError_t launch_coefficients_dMf(const fire_fuel_class *classes_dev, int n, double *dcoef_dev,
                                     cudaStream_t s);
 
+// a fuel class fire_init accepts: a positive weight (burn time), and for a
+// Rothermel class with fuel (Table 2) a positive surface-area-to-volume
+// ratio, depth, particle density, moisture of extinction and effective
+// mineral content (the chain divides by or takes powers of each)
+inline bool valid_fuel_class(const fire_fuel_class &f) {
+    if (!(f.weight > 0)) return false;
+    if (f.fgi > 0 && !f.chaparral &&
+        !(f.savr > 0 && f.fueldepthm > 0 && f.fueldens > 0 && f.fuelmce > 0 && f.se > 0))
+        return false;
+    return true;
+}
+
 // remembers the last CUDA error an entry point saw on this host thread
 // (read back through fire_last_cuda_error)
 void record_cuda_error(cudaError_t e, const char *where);

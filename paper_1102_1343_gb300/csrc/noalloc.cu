@@ -1,16 +1,18 @@
 // fire_step_noalloc: one fire step on caller-owned state that allocates no
 // memory.
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA graph
-// being captured, host applications whose GPU memory is handed out by their
-// own pool or by a host framework that forbids driver allocations after
-// start-up, and coupled models that must not touch the allocator from their
-// time loop.  This entry point serves them: the caller passes every input
-// and output buffer, and the few intermediate values the step needs (the
-// fuel-class table, its spread-rate coefficients, the step's start and end
-// time and, when the caller passes none, the status word) live in one
-// file-scope __device__ array of fixed size instead of a cudaMalloc'ed
-// buffer.  It launches the same kernels as fire_step.
+// Some callers cannot call cudaMalloc: host applications whose GPU memory is
+// handed out by their own pool or by a host framework that forbids driver
+// allocations after start-up, and coupled models that must not touch the
+// allocator from their time loop (an allocation there can synchronise the
+// device or fail once the pool owns the memory).  This entry point serves
+// them: the caller passes every input and output buffer, and the few
+// intermediate values the step needs (the fuel-class table, its spread-rate
+// coefficients, the step's start and end time and, when the caller passes
+// none, the status word) live in one file-scope __device__ array of fixed
+// size instead of a cudaMalloc'ed buffer.  It launches the same kernels as
+// fire_step.  With no status_dev the faults go to that array's status word,
+// which no call reads back: a caller who wants to see faults passes one.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -102,7 +104,7 @@ extern "C" int fire_step_noalloc(const fire_grid_desc *grid, const fire_fuel_cla
     const long long NX = (long long)g.nx_atm * g.sr_x, NY = (long long)g.ny_atm * g.sr_y;
     if (NX < 2 || NY < 2 || NX > (1 << 30) || NY > (1 << 30)) return FIRE_ERR_ARG;
     for (int k = 0; k < n_classes; ++k)
-        if (!(classes[k].weight > 0)) return FIRE_ERR_ARG;
+        if (!valid_fuel_class(classes[k])) return FIRE_ERR_ARG;
 
     NoAllocScratch *s = nullptr;
     int r = scratch_address(&s);

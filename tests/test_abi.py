@@ -80,3 +80,49 @@ def test_null_context_is_rejected_by_every_entry_point(lib):
                              C.byref(i3)) == E
     assert lib.fire_default_kernel(pkg.FIRE_FP32, 10, 10, 10, 10, 0, C.byref(i1), C.byref(i2),
                                    C.byref(i3)) == E
+
+
+def test_absurd_mesh_is_out_of_memory_without_gpu(lib):
+    """A mesh whose state fits on no device (6.9e10 nodes) is refused with
+    FIRE_ERR_OOM before anything is allocated (no device needed)."""
+    import paper_1102_1343_gb300 as pkg
+    out = C.c_void_p()
+    g = pkg.make_grid(26214, 26214, 10, 10, 60.0, 60.0)
+    cls = pkg.make_classes([{"fgi": 0.5, "weight": 7.0, "savr": 1e4, "fueldepthm": 0.3,
+                             "fueldens": 500.0, "fuelmce": 0.3, "se": 0.01}])
+    assert lib.fire_init(C.byref(out), C.byref(g), cls, 1, 1, None, None, 1, 1, None, 0,
+                         None) == pkg.FIRE_ERR_OOM
+    assert out.value is None
+
+
+@pytest.mark.parametrize("field", ["savr", "fueldepthm", "fueldens", "fuelmce", "se", "weight"])
+def test_noalloc_checks_fuel_classes_like_fire_init(lib, field):
+    """fire_step_noalloc refuses the fuel classes fire_init refuses (a
+    Rothermel class with a non-positive sigma, depth, density, moisture of
+    extinction or mineral content, or a non-positive weight), before any
+    device call."""
+    import paper_1102_1343_gb300 as pkg
+    from paper_1102_1343_gb300 import synth
+    bad = dict(synth.nominal_class(), **{field: 0.0})
+    g = pkg.make_grid(4, 4, 10, 10, 60.0, 60.0)
+    with pytest.raises(pkg.FireError) as e:
+        pkg.fire_step_noalloc(g, [bad], 1, 2, 3, 4, 5, 6, None, 7, 8, 9, 10, 0.0, 0.5)
+    assert e.value.code == pkg.FIRE_ERR_ARG
+    out = C.c_void_p()
+    assert lib.fire_init(C.byref(out), C.byref(g), pkg.make_classes([bad]), 1, 1, None, None, 1,
+                         1, None, 0, None) == pkg.FIRE_ERR_ARG
+
+
+def test_noalloc_binding_refuses_host_tensors(lib):
+    """The binding checks torch tensors before the call: a host tensor never
+    reaches the kernels (FIRE_ERR_ARG, no device needed)."""
+    import torch
+
+    import paper_1102_1343_gb300 as pkg
+    from paper_1102_1343_gb300 import synth
+    g = pkg.make_grid(4, 4, 10, 10, 60.0, 60.0)
+    psi = torch.zeros(40 * 40, dtype=torch.float64)
+    with pytest.raises(pkg.FireError) as e:
+        pkg.fire_step_noalloc(g, [synth.nominal_class()], psi, 2, 3, 4, 5, 6, None, 7, 8, 9, 10,
+                              0.0, 0.5)
+    assert e.value.code == pkg.FIRE_ERR_ARG and "psi_in" in str(e.value)
