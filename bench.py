@@ -164,6 +164,8 @@ def make_workload(name: str):
         return synth.line_fire_2000()
     if name == "circle100":
         return synth.plain_circle()
+    if name == "burning8200":
+        return synth.burning_fire_8200()
     if name == "points4000":
         # a smaller case of the same recipe (4000x4000 nodes, state 0.53 GB > L2) for
         # profiler captures that the 8200x8200 mesh is too large for
@@ -290,7 +292,9 @@ def run_reference(args, rank, world):
 WORKLOAD_NAMES = {"points8200": "points-fire-8200x8200 (820x820 atmos x10, 50 point ignitions)",
                   "points4000": "points-fire-4000x4000 (400x400 atmos x10, 12 point ignitions)",
                   "line2000": "line-fire-2000x2000 (200x200 atmos x10, 1 km line ignition)",
-                  "circle100": "circle-fp64-100x100 (10x10 atmos x10)"}
+                  "circle100": "circle-fp64-100x100 (10x10 atmos x10)",
+                  "burning8200": "burning-fire-8200x8200 (820x820 atmos x10, 50 ignitions "
+                                 "of radius 3 km)"}
 
 
 # ---------------------------------------------------------------------------
@@ -426,6 +430,11 @@ def run_gpu(args, rank, world):
                 "speedup_fp32_over_fp64": value / world / v64}
         m64.close()
 
+    burn = None
+    if rank == 0 and prec == "fp32" and args.workload == "points8200" and not args.no_burning:
+        burn = bench_burning(pkg, dev, args.burning_steps)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(args.workload, seconds=args.cpu_seconds)
@@ -470,6 +479,8 @@ def run_gpu(args, rank, world):
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "cpu_baseline": cpu,
+            "accuracy": accuracy_record(),
+            "burning": burn,
             "fp64_plain_gpu": fp64,
             "adjoint": adj,
             "ensemble": ens,
@@ -477,6 +488,83 @@ def run_gpu(args, rank, world):
             "status": pkg.fire_strerror(status if status else final_status),
         }
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# accuracy record and the heavily burning state
+# ---------------------------------------------------------------------------
+
+ACCURACY_SUMMARY = "profiles/accuracy_line2000_fp32_fp64.md"
+
+
+def accuracy_record(path=None):
+    """The errors of the FP32 and FP64 paths against the FP64 oracle on the
+    2000x2000 line fire over all 1200 steps, as recorded by the full-run GPU
+    test (tests/test_fullrun_gpu.py) in the committed summary: the JSON block
+    of the summary, with a flag saying whether it was taken on the current
+    step-kernel source."""
+    path = path or os.path.join(ROOT, ACCURACY_SUMMARY)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    a, b = txt.find("```json"), txt.rfind("```")
+    if a < 0 or b <= a:
+        return None
+    try:
+        rec = json.loads(txt[a + len("```json"):b])
+    except ValueError:
+        return None
+    rec["current_kernel_source"] = rec.get("kernel_source_hash") == kernel_hash()
+    rec["source"] = ACCURACY_SUMMARY
+    return rec
+
+
+def bench_burning(pkg, dev, steps):
+    """The 8200x8200 mesh in a heavily burning state (50 ignitions of radius
+    3 km, about 40 % of the domain burnt from the start): cell-steps/s and the
+    roofline fraction of the step kernel where most warps run the
+    fuel-fraction quadrature and the ignition-time path."""
+    import torch
+    from paper_1102_1343_gb300 import synth
+    w = synth.burning_fire_8200()
+    cells = w.nx * w.ny
+    m = pkg.FireModel.from_workload(w, precision="fp32", device=dev)
+    u, v = m.wind(w.u, w.v)
+    for _ in range(5):
+        m.step(u, v, w.dt)
+    psi = m.state()[0]
+    burnt = float((psi <= 0).float().mean())
+    del psi
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pkg.fire_enable_timing(m.ctx, True)
+    pkg.fire_kernel_time_ms(m.ctx)
+    for _ in range(min(steps, 100)):
+        pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
+    k_ms, k_n = pkg.fire_kernel_time_ms(m.ctx)
+    pkg.fire_enable_timing(m.ctx, False)
+    k_avg = k_ms / max(1, k_n)
+    kernel = pkg.fire_get_kernel(m.ctx)
+    status = m.status()
+    m.close()
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_CELL_STEP["fp32"] * cells / (k_avg / 1000.0) / 1e9
+    return {"workload": f"{w.name} (820x820 atmos x10, 50 ignitions of radius 3 km)",
+            "burnt_fraction_at_start": burnt, "value": cells * steps / (ms / 1e3), "unit": UNIT,
+            "steps": steps, "ms_per_step": ms / steps, "kernel_ms": k_avg,
+            "kernel": ["k_fire_step", "k_fire_march", "k_fire_warp"][kernel[0]] + "<float>",
+            "tile_atmos_cells": list(kernel[1:]),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"},
+            "status": pkg.fire_strerror(status)}
 
 
 # ---------------------------------------------------------------------------
@@ -657,7 +745,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["points8200", "line2000", "circle100", "points4000"],
+    ap.add_argument("--workload", choices=["points8200", "line2000", "circle100", "points4000",
+                                           "burning8200"],
                     default="points8200")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--kernel", type=int, nargs=3, default=None,
@@ -674,6 +763,8 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="time the shape fire_autotune picks instead of fire_init's default")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-burning", action="store_true")
+    ap.add_argument("--burning-steps", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

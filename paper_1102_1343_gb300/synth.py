@@ -212,7 +212,8 @@ def plain_circle(nxa=10, nya=10, sr=10, dx_atm=60.0, steps=120, dt=0.5, U=3.0, V
 
 def random_landscape(nxa, nya, sr=10, dx_atm=60.0, seed=BASE_SEED, steps=1200, dt=0.5,
                      ignition="line", n_points=50, edge_margin=2000.0, wind_mean=(5.0, 0.0),
-                     wind_scale=1.0, moisture_shift=0.0, name=None) -> Workload:
+                     wind_scale=1.0, moisture_shift=0.0, name=None,
+                     ignition_radius=10.0) -> Workload:
     """Random landscape: smooth wind (mean 5 m/s, std 1.5 m/s, 300 m filter
     length), 20 Gaussian hills with max slope 0.4, 13 Voronoi fuel classes
     (load 0.1-2 kg/m^2, moisture 0.04-0.2, one chaparral), and either a 1 km
@@ -242,7 +243,7 @@ def random_landscape(nxa, nya, sr=10, dx_atm=60.0, seed=BASE_SEED, steps=1200, d
         m = min(edge_margin, 0.25 * min(Lx, Ly))
         xs = rng.uniform(m, Lx - m, n_points)
         ys = rng.uniform(m, Ly - m, n_points)
-        ign = [point_ignition(a, b, radius=10.0) for a, b in zip(xs, ys)]
+        ign = [point_ignition(a, b, radius=ignition_radius) for a, b in zip(xs, ys)]
     elif ignition == "center":
         ign = [point_ignition(Lx / 2, Ly / 2, radius=10.0)]
     elif ignition == "none":
@@ -266,6 +267,16 @@ def points_fire_8200(seed=BASE_SEED) -> Workload:
     2000 steps."""
     return random_landscape(820, 820, seed=seed, steps=2000, ignition="points",
                             n_points=50, name="points-fire-8200x8200")
+
+
+def burning_fire_8200(seed=BASE_SEED) -> Workload:
+    """The large mesh in a heavily burning state: the 8200x8200 recipe with
+    50 point ignitions of radius 3 km (centres at least 3.5 km from the edges),
+    so that about half of the domain is burnt from t = 0 and its cells run the
+    fuel-fraction quadrature and the ignition-time path every step."""
+    return random_landscape(820, 820, seed=seed, steps=2000, ignition="points", n_points=50,
+                            edge_margin=3500.0, ignition_radius=3000.0,
+                            name="burning-fire-8200x8200")
 
 
 def ensemble_sizes(n_members=64, seed=BASE_SEED, lo=26, hi=205):
