@@ -135,8 +135,15 @@ typedef struct {
  * preprocessing").
  *   classes[n_classes]    host array, 1 <= n_classes <= FIRE_MAX_CLASSES
  *   fuel_class_dev        uint8 [NY][NX] device, class index per node (< n_classes)
- *   moisture_dev          reserved, must be NULL (per-node moisture is not
- *                         supported by this version)
+ *   moisture_dev          [NY][NX] device per-node fuel moisture M_f (>= 0,
+ *                         context precision), or NULL (the class moisture
+ *                         fuelmc_g).  The coefficients of eq.
+ *                         (spread-WRF-Fire) are kept per grid point: with a
+ *                         per-node M_f, R0, c, d and the heat factors H_s,
+ *                         H_q of each node are evaluated from Table 2 at
+ *                         that node's class and moisture (in double, stored
+ *                         in the context precision, 5 values per node);
+ *                         S0, b, e and T_f do not depend on M_f
  *   spread_mult_dev       [NY][NX] device per-node multiplier of S, or NULL (= 1)
  *   dzdx_dev, dzdy_dev    [NY][NX] device terrain gradient at the nodes
  *   ignitions[n_ign]      host array, 0 <= n_ign <= FIRE_MAX_IGNITIONS
@@ -194,8 +201,15 @@ int fire_set_spread_mult(fire_ctx *ctx, const void *mult_dev);
 
 /* Replace the fuel-class table (Table 1 properties, e.g. other moisture
  * values) by n_classes host records; n_classes must equal fire_init's.  The
- * per-class coefficients of eq. (spread-WRF-Fire) are recomputed; waits. */
+ * per-class coefficients of eq. (spread-WRF-Fire) are recomputed (and the
+ * per-node ones, where a per-node moisture is set); waits. */
 int fire_set_fuel_classes(fire_ctx *ctx, const fire_fuel_class *classes, int n_classes);
+
+/* Replace the per-node fuel moisture M_f by a copy of moisture_dev ([NY][NX]
+ * device, context precision, >= 0) and recompute the per-node coefficients
+ * (as fire_init does with a moisture); NULL returns to the class moisture.
+ * Waits.  Not for the context of an ensemble member. */
+int fire_set_moisture(fire_ctx *ctx, const void *moisture_dev);
 
 /* Adjoint of the arrival-time misfit (data assimilation, the use the paper
  * gives for the level-set formulation in Sect. 7):
@@ -215,7 +229,8 @@ int fire_set_fuel_classes(fire_ctx *ctx, const fire_fuel_class *classes, int n_c
  *                multiplier (1 where none was given)
  *   g_moist_dev  dJ/dM_f per node, [NY][NX] double device: the derivative for
  *                a change of the fuel moisture of that node alone, at the
- *                class moisture (the forward path itself takes M_f per class)
+ *                node's moisture (the per-node M_f where one is set, else
+ *                the class moisture)
  *   g_u_dev      dJ/du on the x-faces [ny_atm][nx_atm + 1], double device
  *   g_v_dev      dJ/dv on the y-faces [ny_atm + 1][nx_atm], double device
  * Gradient pointers may be NULL; with all four NULL only J is computed.
@@ -363,13 +378,17 @@ int fire_step_noalloc(const fire_grid_desc *grid, const fire_fuel_class *classes
 typedef struct fire_ensemble fire_ensemble;
 #define FIRE_MAX_MEMBERS 1024
 
-/* One member: the arguments of fire_init (device arrays as there; moisture
- * per node is not supported).  All members must share the precision. */
+/* One member: the arguments of fire_init (device arrays as there; moisture_dev
+ * is the member's per-node fuel moisture or NULL).  All members must share
+ * the precision.  When any member has a per-node moisture, every member's
+ * step reads per-node coefficients (members without one get them from their
+ * class moisture, 5 more values per node). */
 typedef struct {
     fire_grid_desc grid;
     const fire_fuel_class *classes;
     int n_classes;
     const uint8_t *fuel_class_dev;
+    const void *moisture_dev;
     const void *spread_mult_dev;
     const void *dzdx_dev;
     const void *dzdy_dev;

@@ -48,7 +48,7 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test",
                "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
                "fire_adjoint", "fire_autotune", "fire_ensemble_autotune",
-               "fire_default_kernel", "fire_adjoint_heat")
+               "fire_default_kernel", "fire_adjoint_heat", "fire_set_moisture")
 
 
 class FireError(RuntimeError):
@@ -84,7 +84,8 @@ _P = C.c_void_p
 
 class fire_member_desc(C.Structure):
     _fields_ = [("grid", fire_grid_desc), ("classes", C.POINTER(fire_fuel_class)),
-                ("n_classes", C.c_int), ("fuel_class_dev", _P), ("spread_mult_dev", _P),
+                ("n_classes", C.c_int), ("fuel_class_dev", _P), ("moisture_dev", _P),
+                ("spread_mult_dev", _P),
                 ("dzdx_dev", _P), ("dzdy_dev", _P), ("ignitions", C.POINTER(fire_ignition)),
                 ("n_ign", C.c_int)]
 
@@ -142,6 +143,8 @@ def load_library(path: str | None = None):
     L.fire_set_spread_mult.restype = C.c_int
     L.fire_set_fuel_classes.argtypes = [_P, C.POINTER(fire_fuel_class), C.c_int]
     L.fire_set_fuel_classes.restype = C.c_int
+    L.fire_set_moisture.argtypes = [_P, _P]
+    L.fire_set_moisture.restype = C.c_int
     L.fire_adjoint.argtypes = [_P, C.c_int, C.c_double, _P, _P, _P, C.c_int,
                                C.POINTER(C.c_double), _P, _P, _P, _P]
     L.fire_adjoint.restype = C.c_int
@@ -395,7 +398,8 @@ def _ptr_array(items):
 
 def fire_ensemble_create(members, cuda_stream=None) -> int:
     """members: list of dicts with the fire_init arguments (grid, classes,
-    fuel_class_dev, spread_mult_dev, dzdx_dev, dzdy_dev, ignitions)."""
+    fuel_class_dev, moisture_dev, spread_mult_dev, dzdx_dev, dzdy_dev,
+    ignitions; moisture_dev and spread_mult_dev optional)."""
     L = load_library()
     descs = (fire_member_desc * len(members))()
     keep = []
@@ -407,6 +411,7 @@ def fire_ensemble_create(members, cuda_stream=None) -> int:
         descs[k].classes = C.cast(cls, C.POINTER(fire_fuel_class))
         descs[k].n_classes = len(m["classes"])
         descs[k].fuel_class_dev = _ptr(m["fuel_class_dev"])
+        descs[k].moisture_dev = _ptr(m.get("moisture_dev"))
         descs[k].spread_mult_dev = _ptr(m.get("spread_mult_dev"))
         descs[k].dzdx_dev = _ptr(m["dzdx_dev"])
         descs[k].dzdy_dev = _ptr(m["dzdy_dev"])
@@ -474,6 +479,10 @@ def fire_ensemble_destroy(ens) -> None:
 def fire_set_spread_mult(ctx, mult_dev) -> int:
     return _check(load_library().fire_set_spread_mult(ctx, _ptr(mult_dev)),
                   "fire_set_spread_mult")
+
+
+def fire_set_moisture(ctx, moisture_dev) -> int:
+    return _check(load_library().fire_set_moisture(ctx, _ptr(moisture_dev)), "fire_set_moisture")
 
 
 def fire_set_fuel_classes(ctx, classes) -> int:
@@ -544,7 +553,7 @@ class FireModel:
 
     def __init__(self, nxa, nya, sr, dx_atm, classes, fuel, dzdx, dzdy, ignitions=(),
                  precision="fp32", mult=None, eps=0.4, band=1, psi_far=0.0, dy_atm=None,
-                 stream=None, device=None):
+                 stream=None, device=None, moisture=None):
         import torch
         self.torch = torch
         srx, sry = (sr, sr) if np.isscalar(sr) else sr
@@ -563,9 +572,10 @@ class FireModel:
         fuel_d = t(fuel, torch.uint8)
         zx, zy = t(dzdx, self.dtype), t(dzdy, self.dtype)
         m = None if mult is None else t(mult, self.dtype)
+        mo = None if moisture is None else t(moisture, self.dtype)
         grid = make_grid(nxa, nya, srx, sry, dx_atm, dy_atm, self.precision, band, eps, psi_far)
         torch.cuda.synchronize(dev)
-        self.ctx = fire_init(grid, classes, fuel_d, None, m, zx, zy, list(ignitions),
+        self.ctx = fire_init(grid, classes, fuel_d, mo, m, zx, zy, list(ignitions),
                              self.stream.cuda_stream)
         self.classes = [dict(c) for c in classes]
         self.fuel_dev = fuel_d
@@ -576,7 +586,7 @@ class FireModel:
     def from_workload(cls, w, precision="fp32", **kw):
         return cls(w.nxa, w.nya, (w.srx, w.sry), w.dx_atm, w.classes, w.fuel, w.dzdx, w.dzdy,
                    w.ignitions, precision=precision, mult=w.mult, eps=w.eps, band=w.band,
-                   dy_atm=w.dy_atm, **kw)
+                   dy_atm=w.dy_atm, moisture=w.moisture, **kw)
 
     def wind(self, u, v):
         torch = self.torch
@@ -612,6 +622,12 @@ class FireModel:
         """Per-node spread multiplier (None: 1)."""
         m = None if mult is None else self.torch.as_tensor(mult).to(self.device, self.dtype).contiguous()
         fire_set_spread_mult(self.ctx, m)
+
+    def set_moisture(self, moisture):
+        """Per-node fuel moisture [ny][nx] (None: the class moisture)."""
+        mo = (None if moisture is None
+              else self.torch.as_tensor(moisture).to(self.device, self.dtype).contiguous())
+        fire_set_moisture(self.ctx, mo)
 
     def set_classes(self, classes):
         self.classes = [dict(c) for c in classes]
@@ -677,26 +693,20 @@ def _fire_adjoint_function(objective="arrival"):
             psi0, tign0, frac0, t0 = state0
             model.set_state(psi0, tign0, frac0, t0)
             model.set_mult(mult.detach())
-            classes = [dict(c) for c in model.classes]
-            for k, mf in enumerate(moisture.detach().double().cpu().tolist()):
-                classes[k]["fuelmc_g"] = mf
-            model.set_classes(classes)
+            model.set_moisture(moisture.detach())
             ud = u.detach().to(model.device, model.dtype).contiguous()
             vd = v.detach().to(model.device, model.dtype).contiguous()
             run = model.adjoint_heat if heat else model.adjoint
             J, gm, gM, gu, gv = run(ud, vd, dt, nsteps, obs, ckpt_every)
-            gcls = torch.zeros(len(classes), dtype=torch.float64, device=model.device)
-            gcls.index_add_(0, model.fuel_dev.long().clamp(max=len(classes) - 1).flatten(),
-                            gM.flatten())
-            ctx.save_for_backward(gm, gcls, gu, gv)
+            ctx.save_for_backward(gm, gM, gu, gv)
             ctx.dtypes = (mult.dtype, moisture.dtype, u.dtype, v.dtype)
             ctx.devices = (mult.device, moisture.device, u.device, v.device)
             return torch.tensor(J, dtype=torch.float64, device=model.device)
 
         @staticmethod
         def backward(ctx, gJ):
-            gm, gcls, gu, gv = ctx.saved_tensors
-            out = [(gJ * g).to(d, dt_) for g, dt_, d in zip((gm, gcls, gu, gv), ctx.dtypes,
+            gm, gM, gu, gv = ctx.saved_tensors
+            out = [(gJ * g).to(d, dt_) for g, dt_, d in zip((gm, gM, gu, gv), ctx.dtypes,
                                                              ctx.devices)]
             return (None, None, out[0], out[1], out[2], out[3], None, None, None, None)
 
@@ -706,10 +716,10 @@ def _fire_adjoint_function(objective="arrival"):
             observation of (Q - q_obs)^2, Q the sensible heat released per
             unit area over nsteps steps from the given initial state, as a
             differentiable torch function of the per-node spread multiplier
-            m [ny][nx], the per-class fuel moisture [n_classes] and the
+            m [ny][nx], the per-node fuel moisture M_f [ny][nx] and the
             staggered wind u [nya][nxa+1], v [nya+1][nxa].  The forward call
-            runs fire_adjoint_heat and keeps the gradients; backward scales
-            them.
+            sets m and M_f on the model, runs fire_adjoint_heat and keeps
+            the gradients; backward scales them.
 
             apply(model, state0, mult, moisture, u, v, q_obs, dt, nsteps,
             ckpt_every) with q_obs [nya][nxa] and state0 as for
@@ -721,11 +731,12 @@ def _fire_adjoint_function(objective="arrival"):
         """J(m, M_f, u, v) = 1/2 sum over nodes ignited in both of
         (t_i - t_obs)^2 after nsteps steps from the given initial state, as a
         differentiable torch function of the per-node spread multiplier m
-        [ny][nx], the per-class fuel moisture [n_classes] and the staggered
-        wind u [nya][nxa+1], v [nya+1][nxa].  The forward call runs
+        [ny][nx], the per-node fuel moisture M_f [ny][nx] and the staggered
+        wind u [nya][nxa+1], v [nya+1][nxa].  The forward call sets m and M_f
+        on the model (fire_set_spread_mult, fire_set_moisture), runs
         fire_adjoint (forward sweep, checkpoints and the reverse sweep in the
-        CUDA library) and keeps the gradients; backward scales them.  The
-        per-class moisture gradient sums the per-node one over the class map.
+        CUDA library) and keeps the gradients, all per node as the library
+        returns them; backward scales them.
 
         apply(model, state0, mult, moisture, u, v, t_obs, dt, nsteps, ckpt_every)
         with state0 = (psi, tign, frac, t) as returned by FireModel.state()."""

@@ -50,6 +50,7 @@ int ctx_info(const fire_ctx *c, int *prec, int *variant, int *nx, int *ny, int *
 bool ctx_ignition_active(fire_ctx *c, double t);
 cudaStream_t ctx_stream(const fire_ctx *c);
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c);
+const void *ctx_moisture(const fire_ctx *c);
 int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
 cudaGraphExec_t *ctx_adjoint_graphs(fire_ctx *c, unsigned long long **keys);
 
@@ -66,8 +67,9 @@ struct AdjArgs {
     const T *zx, *zy, *mult;  // mult nullable (1)
     const T *u, *v;
     const T *unv;  // [n][2] node wind of the run (interpolated once), or null
-    const double *coef, *dcoef;  // [ncls][K_N]
+    const double *coef, *dcoef;  // [ncls][K_N], or [n][K_N] per node when nodeco
     int ncls;
+    int nodeco;  // coefficients per node (a per-node fuel moisture)
     const double *tign0, *tign, *tobs;
     const double *dJdt;  // dJ/dt_i per node instead of t_i - t_obs (heat misfit), or null
     const double *tsp;  // [2] start and end time of the step (device)
@@ -117,6 +119,7 @@ template <typename T>
 struct NodeEnv {
     T co[6];
     int cls;
+    size_t ci;  // row of coef / dcoef: the class, or the node with per-node coefficients
     T m, un, vn, zx, zy;
 };
 
@@ -126,8 +129,9 @@ __device__ __forceinline__ void node_env(const AdjArgs<T> &a, int i, int j, Node
     int cls = a.fuel[k];
     cls = cls > a.ncls - 1 ? a.ncls - 1 : cls;
     e.cls = cls;
+    e.ci = a.nodeco ? k : (size_t)cls;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) e.co[q] = T(a.coef[(size_t)cls * K_N + q]);
+    for (int q = 0; q < 6; ++q) e.co[q] = T(a.coef[e.ci * K_N + q]);
     e.m = a.mult ? a.mult[k] : T(1);
     e.zx = a.zx[k];
     e.zy = a.zy[k];
@@ -305,7 +309,7 @@ __device__ __forceinline__ void vjp_node(const AdjArgs<T> &a, size_t k, int i, i
     node_partials<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e, o);
 #pragma unroll
     for (int q = 0; q < 5; ++q) a.Cout[q * a.n + k] = v * o.dpsi[q];
-    const double *dc = a.dcoef + (size_t)e.cls * K_N;
+    const double *dc = a.dcoef + e.ci * K_N;
     a.gm[k] += (double)(v * o.dm);
     a.gM[k] += (double)(v * (o.dS0 * T(dc[K_S0]) + o.dR0 * T(dc[K_R0]) + o.dc * T(dc[K_C]) +
                              o.dd * T(dc[K_D])));
@@ -443,7 +447,8 @@ struct HeatArgs {
     const T *psi, *F0, *F1;  // psi and F at the end, F at the start of the run
     const double *tign;      // t_i at the end
     const uint8_t *fuel;
-    const double *coef, *dcoef;
+    const double *coef, *dcoef;  // [ncls][K_N], or [n][K_N] per node when nodeco
+    int nodeco;
     int ncls, nx, ny, nxa, nya, srx, sry;
     double t1;               // model time at the end
     const double *qobs;      // [nya][nxa], NaN where unobserved
@@ -462,8 +467,8 @@ __global__ void k_heat_residual(const HeatArgs<T> h) {
         for (int j = ja * h.sry; j < (ja + 1) * h.sry; ++j)
             for (int i = ia * h.srx; i < (ia + 1) * h.srx; ++i) {
                 const size_t k = (size_t)j * h.nx + i;
-                const int c = min((int)h.fuel[k], h.ncls - 1);
-                q += ((double)h.F0[k] - (double)h.F1[k]) * h.coef[(size_t)c * K_N + K_HS];
+                const size_t c = h.nodeco ? k : (size_t)min((int)h.fuel[k], h.ncls - 1);
+                q += ((double)h.F0[k] - (double)h.F1[k]) * h.coef[c * K_N + K_HS];
             }
         q /= (double)(h.srx * h.sry);
         h.Q[I] = q;
@@ -481,9 +486,9 @@ __global__ void k_heat_seed(const HeatArgs<T> h) {
          k += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(k % h.nx), j = (int)(k / h.nx);
         const double r = h.res[(j / h.sry) * h.nxa + i / h.srx];
-        const int c = min((int)h.fuel[k], h.ncls - 1);
-        h.gF[k] = -r * h.coef[(size_t)c * K_N + K_HS] / r2;
-        h.gM[k] = r * ((double)h.F0[k] - (double)h.F1[k]) * h.dcoef[(size_t)c * K_N + K_HS] / r2;
+        const size_t c = h.nodeco ? k : (size_t)min((int)h.fuel[k], h.ncls - 1);
+        h.gF[k] = -r * h.coef[c * K_N + K_HS] / r2;
+        h.gM[k] = r * ((double)h.F0[k] - (double)h.F1[k]) * h.dcoef[c * K_N + K_HS] / r2;
     }
 }
 
@@ -592,8 +597,8 @@ __device__ bool heat_cell(const HeatArgs<T> &h, int i, int j, double *dw, double
             w[3 * b + a] = p;
             th[3 * b + a] = (p >= 0.0 || !((double)h.psi[kc] < 0.0)) ? h.t1 : h.tign[kc];
         }
-    const int c = min((int)h.fuel[k], h.ncls - 1);
-    quad_partials(w, th, h.t1, h.coef[(size_t)c * K_N + K_TF], dw, dth);
+    const size_t c = h.nodeco ? k : (size_t)min((int)h.fuel[k], h.ncls - 1);
+    quad_partials(w, th, h.t1, h.coef[c * K_N + K_TF], dw, dth);
     for (int q = 0; q < 9; ++q) {
         dw[q] *= g;
         dth[q] *= g;
@@ -785,6 +790,10 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t o_tseg = take((K + 2) * sizeof(double));
     const size_t o_small = take(16 + kMisfitBlocks * sizeof(double) + 16);
     const size_t na = (size_t)c_nxa(c) * c_nya(c);
+    // per-node coefficients of a per-node fuel moisture ([n][K_N] doubles)
+    const void *moist = ctx_moisture(c);
+    const bool nodeco = moist != nullptr;
+    const size_t o_nco = take(nodeco ? n * K_N * sizeof(double) : 0);
     const size_t o_F0 = take(qobs ? n * E : 0);                   // F at the start (heat)
     const size_t o_Qr = take(qobs ? 2 * na * sizeof(double) : 0);  // Q, residual (heat)
     const size_t o_lam = take(3 * n * E);
@@ -792,7 +801,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t o_g = take(4 * n * sizeof(double));
     const size_t o_unv = take(2 * n * E);
     const size_t nu = (size_t)c_nya(c) * (c_nxa(c) + 1), nv = (size_t)(c_nya(c) + 1) * c_nxa(c);
-    const size_t o_dco = take(sizeof(double) * K_N * ncls);
+    const size_t o_dco = take(sizeof(double) * K_N * (nodeco ? n : (size_t)ncls));
     const size_t o_wind = take(sizeof(double) * (nu + nv));
     const size_t o_hs = take(qobs ? 3 * n * sizeof(double) : 0);  // dJ/dF, dJ/dpsi, dJ/dt_i
     void *wsv = nullptr;
@@ -814,6 +823,15 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     StepArgs sa;
     ctx_step_args(c, cur, u, v, dt, nullptr, nullptr, sa);
     ADJ_CHECK(cudaMemcpyAsync(tign0, sa.tign, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // the coefficients the adjoint kernels read: per class, or per node
+    const double *coef_rows = sa.coef;
+    if (nodeco) {
+        double *aos = reinterpret_cast<double *>(ws + o_nco);
+        T *none[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        ADJ_CHECK(launch_node_coefficients<T>(ctx_classes_dev(c), ncls, sa.fuel, moist, n, none,
+                                              aos, st));
+        coef_rows = aos;
+    }
     T *F0 = reinterpret_cast<T *>(ws + o_F0);
     if (qobs) ADJ_CHECK(cudaMemcpyAsync(F0, sa.F_in, n * E, cudaMemcpyDeviceToDevice, st));
     ADJ_CHECK(cudaMemcpyAsync(tdev, times.data(), (nsteps + 1) * sizeof(double),
@@ -848,7 +866,8 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         h.F1 = static_cast<const T *>(fin.F_in);
         h.tign = tign_final;
         h.fuel = sa.fuel;
-        h.coef = sa.coef;
+        h.coef = coef_rows;
+        h.nodeco = nodeco ? 1 : 0;
         h.ncls = ncls;
         h.nx = nx;
         h.ny = ny;
@@ -882,9 +901,14 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     ADJ_CHECK(cudaMemsetAsync(gm, 0, 4 * n * sizeof(double), st));
     ADJ_CHECK(cudaMemsetAsync(Fs, 0, 2 * n * E, st));
 
-    // per-class d(coefficients)/d(M_f)
+    // d(coefficients)/d(M_f) per class at the class moisture, or per node at
+    // the node's moisture
     double *dcoef = reinterpret_cast<double *>(ws + o_dco);
-    ADJ_CHECK(launch_coefficients_dMf(ctx_classes_dev(c), ncls, dcoef, st));
+    if (nodeco)
+        ADJ_CHECK(launch_node_coefficients_dMf<T>(ctx_classes_dev(c), ncls, sa.fuel, moist, n,
+                                                  dcoef, st));
+    else
+        ADJ_CHECK(launch_coefficients_dMf(ctx_classes_dev(c), ncls, dcoef, st));
 
     AdjArgs<T> a;
     memset(&a, 0, sizeof a);
@@ -894,8 +918,9 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     a.mult = static_cast<const T *>(sa.mult);
     a.u = static_cast<const T *>(u);
     a.v = static_cast<const T *>(v);
-    a.coef = sa.coef;
+    a.coef = coef_rows;
     a.dcoef = dcoef;
+    a.nodeco = nodeco ? 1 : 0;
     a.ncls = ncls;
     a.tign0 = tign0;
     a.tign = tign_final;
@@ -1007,7 +1032,8 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         return (h ^ x) * 0x100000001b3ULL + (h >> 29);
     };
     unsigned long long key0 = 0xcbf29ce484222325ULL;
-    const void *ptrs[] = {ws, u, v, tobs, qobs, sa.mult, sa.coef, sa.fuel, sa.dzdy, sa.dzdx, sa.tign};
+    const void *ptrs[] = {ws, u, v, tobs, qobs, sa.mult, sa.coef, sa.fuel, sa.dzdy, sa.dzdx, sa.tign,
+                          sa.nco[0], moist};
     for (const void *q : ptrs) key0 = mix(key0, (unsigned long long)(uintptr_t)q);
     unsigned long long dtb;
     memcpy(&dtb, &dt, sizeof dtb);

@@ -151,7 +151,93 @@ __global__ void k_coefficients_dMf(const fire_fuel_class *cls, int n, double *dc
     for (int q = 0; q < K_N; ++q) dcoef[(size_t)k * K_N + q] = co[q].d;
 }
 
+// Per-node coefficients for a per-node fuel moisture M_f (Table 1 M_f per
+// grid point; eq. spread-WRF-Fire keeps its coefficients per node): the
+// chain of the node's class at the node's moisture (the class moisture where
+// moist is null).  R0, c, d and the two heat factors depend on M_f; S0, b, e
+// and T_f do not and stay in the class table.  planes: [5][n] in the path
+// precision (R0, c, d, H_s, H_q; skipped when null); aos (nullable): [n][K_N]
+// doubles, every slot, for the adjoint.
+template <typename T>
+struct Planes5 {
+    T *p[5];
+};
+
+template <typename T>
+__global__ void k_node_coefficients(const fire_fuel_class *cls, int ncls, const uint8_t *fuel,
+                                    const T *moist, size_t n, const Planes5<T> pl, double *aos) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        int c = fuel[k];
+        c = c < ncls ? c : ncls - 1;
+        const fire_fuel_class f = cls[c];
+        double co[K_N];
+        coefficient_chain<double>(f, moist ? (double)moist[k] : f.fuelmc_g, co);
+        if (pl.p[0]) {
+            pl.p[0][k] = T(co[K_R0]);
+            pl.p[1][k] = T(co[K_C]);
+            pl.p[2][k] = T(co[K_D]);
+            pl.p[3][k] = T(co[K_HS]);
+            pl.p[4][k] = T(co[K_HQ]);
+        }
+        if (aos)
+            for (int q = 0; q < K_N; ++q) aos[k * K_N + q] = co[q];
+    }
+}
+
+// d(coefficients)/d(M_f) per node at the node's moisture: [n][K_N]
+template <typename T>
+__global__ void k_node_coefficients_dMf(const fire_fuel_class *cls, int ncls, const uint8_t *fuel,
+                                        const T *moist, size_t n, double *daos) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        int c = fuel[k];
+        c = c < ncls ? c : ncls - 1;
+        const fire_fuel_class f = cls[c];
+        Dual co[K_N];
+        coefficient_chain<Dual>(f, mk(moist ? (double)moist[k] : f.fuelmc_g, 1.0), co);
+        for (int q = 0; q < K_N; ++q) daos[k * K_N + q] = co[q].d;
+    }
+}
+
+int grid_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 65535 * 8 ? b : 65535 * 8);
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_node_coefficients(const fire_fuel_class *classes_dev, int ncls,
+                                     const uint8_t *fuel, const void *moist, size_t n,
+                                     T *const *planes, double *aos, cudaStream_t s) {
+    Planes5<T> pl;
+    for (int q = 0; q < 5; ++q) pl.p[q] = planes[q];
+    k_node_coefficients<T><<<grid_for(n), 256, 0, s>>>(classes_dev, ncls, fuel,
+                                                       static_cast<const T *>(moist), n, pl, aos);
+    return cudaGetLastError();
+}
+template cudaError_t launch_node_coefficients<float>(const fire_fuel_class *, int,
+                                                     const uint8_t *, const void *, size_t,
+                                                     float *const *, double *, cudaStream_t);
+template cudaError_t launch_node_coefficients<double>(const fire_fuel_class *, int,
+                                                      const uint8_t *, const void *, size_t,
+                                                      double *const *, double *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_node_coefficients_dMf(const fire_fuel_class *classes_dev, int ncls,
+                                         const uint8_t *fuel, const void *moist, size_t n,
+                                         double *daos, cudaStream_t s) {
+    k_node_coefficients_dMf<T><<<grid_for(n), 256, 0, s>>>(classes_dev, ncls, fuel,
+                                                           static_cast<const T *>(moist), n, daos);
+    return cudaGetLastError();
+}
+template cudaError_t launch_node_coefficients_dMf<float>(const fire_fuel_class *, int,
+                                                         const uint8_t *, const void *, size_t,
+                                                         double *, cudaStream_t);
+template cudaError_t launch_node_coefficients_dMf<double>(const fire_fuel_class *, int,
+                                                          const uint8_t *, const void *, size_t,
+                                                          double *, cudaStream_t);
 
 cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, double *coef_dev,
                                 cudaStream_t s) {

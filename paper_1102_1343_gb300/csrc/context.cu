@@ -30,6 +30,11 @@ struct fire_ctx {
     double *tign = nullptr;
     uint8_t *fuel = nullptr;
     void *dzdx = nullptr, *dzdy = nullptr, *mult = nullptr;
+    // per-node fuel moisture (path precision, null: the class moisture) and
+    // the per-node coefficients R0, c, d, H_s, H_q it gives (null when no
+    // per-node moisture is set, unless an ensemble asked for them)
+    void *moist = nullptr;
+    void *nco[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     fire_fuel_class *classes_dev = nullptr;
     double *coef = nullptr;
     int ncls = 0;
@@ -110,10 +115,43 @@ void release(fire_ctx *c) {
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     void *bufs[] = {c->psi[0], c->psi[1], c->frac[0], c->frac[1], c->tign, c->fuel, c->dzdx,
                     c->dzdy, c->mult, c->classes_dev, c->coef, c->status, c->tdev,
-                    c->stage_u, c->stage_v, c->stage_hs, c->stage_hl, c->ws};
+                    c->stage_u, c->stage_v, c->stage_hs, c->stage_hl, c->ws, c->moist};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (void *b : c->nco)
+        if (b) cudaFree(b);
     delete c;
+}
+
+// (re)computes the per-node coefficient planes from the class table and the
+// per-node moisture (allocating them on first use)
+int build_node_coefficients(fire_ctx *c) {
+    const size_t N = c->n, E = c->esz;
+    for (int q = 0; q < 5; ++q)
+        if (!c->nco[q]) WF_CHECK(cudaMalloc(&c->nco[q], N * E));
+    if (c->prec == FIRE_FP64) {
+        double *pl[5];
+        for (int q = 0; q < 5; ++q) pl[q] = static_cast<double *>(c->nco[q]);
+        WF_CHECK(launch_node_coefficients<double>(c->classes_dev, c->ncls, c->fuel, c->moist, N,
+                                                  pl, nullptr, c->stream));
+    } else {
+        float *pl[5];
+        for (int q = 0; q < 5; ++q) pl[q] = static_cast<float *>(c->nco[q]);
+        WF_CHECK(launch_node_coefficients<float>(c->classes_dev, c->ncls, c->fuel, c->moist, N,
+                                                 pl, nullptr, c->stream));
+    }
+    return FIRE_OK;
+}
+
+// drops the captured step graph (its kernel arguments hold buffer pointers
+// that are about to change); waits for the stream first
+int drop_step_graph(fire_ctx *c) {
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return FIRE_OK;
 }
 
 bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
@@ -130,6 +168,7 @@ int step_kernel_args(fire_ctx *c, const void *u, const void *v, double dt, doubl
     a.dzdx = c->dzdx;
     a.dzdy = c->dzdy;
     a.mult = c->mult;
+    for (int q = 0; q < 5; ++q) a.nco[q] = c->nco[q];
     a.u = u;
     a.v = v;
     a.coef = c->coef;
@@ -410,6 +449,16 @@ int ctx_default_march(fire_ctx *c) { return default_march(c); }
 int ctx_default_warp_strips(fire_ctx *c) { return default_warp_strips(c); }
 
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c) { return c->classes_dev; }
+const void *ctx_moisture(const fire_ctx *c) { return c->moist; }
+bool ctx_has_node_coefficients(const fire_ctx *c) { return c->nco[0] != nullptr; }
+int ctx_ensure_node_coefficients(fire_ctx *c) {
+    if (c->nco[0]) return FIRE_OK;
+    int r = drop_step_graph(c);
+    if (r) return r;
+    r = build_node_coefficients(c);
+    if (r) return r;
+    return cuda_err(cudaStreamSynchronize(c->stream));
+}
 
 cudaGraphExec_t *ctx_adjoint_graphs(fire_ctx *c, unsigned long long **keys) {
     *keys = c->adj_key;
@@ -462,7 +511,6 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
     if (!out) return FIRE_ERR_ARG;
     *out = nullptr;
     if (!grid || !classes || !fuel_class_dev || !dzdx_dev || !dzdy_dev) return FIRE_ERR_ARG;
-    if (moisture_dev) return FIRE_ERR_ARG;
     if (n_classes < 1 || n_classes > FIRE_MAX_CLASSES) return FIRE_ERR_ARG;
     if (n_ign < 0 || n_ign > FIRE_MAX_IGNITIONS || (n_ign > 0 && !ignitions)) return FIRE_ERR_ARG;
     const fire_grid_desc &g = *grid;
@@ -522,6 +570,7 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
     WF_TRY(cudaMalloc(&c->dzdx, N * E));
     WF_TRY(cudaMalloc(&c->dzdy, N * E));
     if (spread_mult_dev) WF_TRY(cudaMalloc(&c->mult, N * E));
+    if (moisture_dev) WF_TRY(cudaMalloc(&c->moist, N * E));
     WF_TRY(cudaMalloc(&c->classes_dev, sizeof(fire_fuel_class) * n_classes));
     WF_TRY(cudaMalloc(&c->coef, sizeof(double) * K_N * n_classes));
     WF_TRY(cudaMalloc(&c->status, sizeof(int)));
@@ -532,11 +581,20 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
     WF_TRY(cudaMemcpyAsync(c->dzdy, dzdy_dev, N * E, cudaMemcpyDeviceToDevice, s));
     if (spread_mult_dev)
         WF_TRY(cudaMemcpyAsync(c->mult, spread_mult_dev, N * E, cudaMemcpyDeviceToDevice, s));
+    if (moisture_dev)
+        WF_TRY(cudaMemcpyAsync(c->moist, moisture_dev, N * E, cudaMemcpyDeviceToDevice, s));
     WF_TRY(cudaMemcpyAsync(c->classes_dev, classes, sizeof(fire_fuel_class) * n_classes,
                            cudaMemcpyHostToDevice, s));
     WF_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
     WF_TRY(cudaMemsetAsync(c->tdev, 0, 2 * sizeof(double), s));
     WF_TRY(launch_coefficients(c->classes_dev, n_classes, c->coef, s));
+    if (moisture_dev) {
+        r = build_node_coefficients(c);
+        if (r) {
+            release(c);
+            return r;
+        }
+    }
     WF_TRY(c->prec == FIRE_FP64 ? launch_fill<double>(c->psi[0], c->tign, c->frac[0], N,
                                                       c->psi_far, s)
                                 : launch_fill<float>(c->psi[0], c->tign, c->frac[0], N,
@@ -747,6 +805,37 @@ int fire_set_fuel_classes(fire_ctx *c, const fire_fuel_class *classes, int n_cla
     WF_CHECK(cudaMemcpyAsync(c->classes_dev, classes, sizeof(fire_fuel_class) * n_classes,
                              cudaMemcpyHostToDevice, c->stream));
     WF_CHECK(launch_coefficients(c->classes_dev, n_classes, c->coef, c->stream));
+    if (c->nco[0]) {
+        const int r = build_node_coefficients(c);
+        if (r) return r;
+    }
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    return FIRE_OK;
+}
+
+int fire_set_moisture(fire_ctx *c, const void *moisture_dev) {
+    if (!c) return FIRE_ERR_ARG;
+    const size_t N = c->n, E = c->esz;
+    if (!moisture_dev) {
+        if (!c->moist) return FIRE_OK;
+        int r = drop_step_graph(c);
+        if (r) return r;
+        cudaFree(c->moist);
+        c->moist = nullptr;
+        for (void *&b : c->nco) {
+            cudaFree(b);
+            b = nullptr;
+        }
+        return FIRE_OK;
+    }
+    if (!c->nco[0] || !c->moist) {
+        int r = drop_step_graph(c);  // new buffers: the captured arguments are stale
+        if (r) return r;
+        if (!c->moist) WF_CHECK(cudaMalloc(&c->moist, N * E));
+    }
+    WF_CHECK(cudaMemcpyAsync(c->moist, moisture_dev, N * E, cudaMemcpyDeviceToDevice, c->stream));
+    const int r = build_node_coefficients(c);
+    if (r) return r;
     WF_CHECK(cudaStreamSynchronize(c->stream));
     return FIRE_OK;
 }

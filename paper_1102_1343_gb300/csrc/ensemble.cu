@@ -106,7 +106,7 @@ __device__ bool grid_barrier(GridBar *b, long long spin_limit, bool skip) {
     return s_ok != 0;
 }
 
-template <typename T>
+template <typename T, bool NC>
 __global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks)
     k_fire_ensemble(const EnsembleArgs e) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks)
             const StepArgs &a = e.margs[2 * it.member + par];
             MarchSmem<T> sm;
             sm.carve(dyn_smem, a.ky * a.sry, a.ncls);
-            MarchStrip<T> strip(a, sm);
+            MarchStrip<T, NC> strip(a, sm);
             strip.run(it.x0, it.y0, t);
             if (strip.st) atomicOr(a.status, strip.st);
             __syncthreads();  // shared memory is reused by the next item
@@ -158,7 +158,7 @@ __host__ __device__ size_t ens_warp_slice(int max_rows) {
     return (b + 15) & ~(size_t)15;
 }
 
-template <typename T>
+template <typename T, bool NC>
 __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks)
     k_fire_ensemble_warp(const EnsembleArgs e, int max_rows) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks)
                 rows[q] = w;
             }
             __syncwarp();
-            WarpStrip<T> strip(a, lut, lut2, lutq, hw, rows);
+            WarpStrip<T, NC> strip(a, lut, lut2, lutq, hw, rows);
             strip.run(it.x0, it.y0, t);
             const int stw = __reduce_or_sync(0xffffffffu, strip.st);
             if (lane == 0 && stw) atomicOr(a.status, stw);
@@ -252,6 +252,8 @@ cudaStream_t ctx_stream(const fire_ctx *c);
 int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
 int ctx_default_march(fire_ctx *c);
 int ctx_default_warp_strips(fire_ctx *c);
+int ctx_ensure_node_coefficients(fire_ctx *c);
+bool ctx_has_node_coefficients(const fire_ctx *c);
 }  // namespace wf
 
 struct fire_ensemble {
@@ -274,6 +276,7 @@ struct fire_ensemble {
     cudaGraphExec_t graph = nullptr;
     bool capture_failed = false;
     int variant = FIRE_KERNEL_MARCH;  // member kernel: FIRE_KERNEL_MARCH or FIRE_KERNEL_WARP
+    bool nc = false;  // members carry per-node coefficients (a per-node fuel moisture)
     int max_rows = 0;                 // warp form: tallest strip
     int g_nsteps = -1;
     double g_dt = 0;
@@ -375,21 +378,27 @@ int ens_plan(fire_ensemble *e) {
     e->n_items = (int)items.size();
     const void *fn;
     int threads;
+    const bool f64 = e->prec == FIRE_FP64;
     if (e->variant == FIRE_KERNEL_WARP) {
-        fn = e->prec == FIRE_FP64 ? (const void *)k_fire_ensemble_warp<double>
-                                  : (const void *)k_fire_ensemble_warp<float>;
+        fn = e->nc ? (f64 ? (const void *)k_fire_ensemble_warp<double, true>
+                          : (const void *)k_fire_ensemble_warp<float, true>)
+                   : (f64 ? (const void *)k_fire_ensemble_warp<double, false>
+                          : (const void *)k_fire_ensemble_warp<float, false>);
         threads = kWarpCtaThreads;
     } else {
-        fn = e->prec == FIRE_FP64 ? (const void *)k_fire_ensemble<double>
-                                  : (const void *)k_fire_ensemble<float>;
+        fn = e->nc ? (f64 ? (const void *)k_fire_ensemble<double, true>
+                          : (const void *)k_fire_ensemble<float, true>)
+                   : (f64 ? (const void *)k_fire_ensemble<double, false>
+                          : (const void *)k_fire_ensemble<float, false>);
         threads = kMarchThreads;
     }
     {
         // the limit is a property of the kernel function shared by all ensembles
         static std::mutex mu;
-        static size_t current[4] = {0, 0, 0, 0};
+        static size_t current[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         std::lock_guard<std::mutex> lock(mu);
-        size_t &cur = current[(e->prec == FIRE_FP64 ? 1 : 0) + (e->variant == FIRE_KERNEL_WARP ? 2 : 0)];
+        size_t &cur = current[(f64 ? 1 : 0) + (e->variant == FIRE_KERNEL_WARP ? 2 : 0) +
+                              (e->nc ? 4 : 0)];
         if (smem > cur) {
             ENS_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             cur = smem;
@@ -430,13 +439,19 @@ cudaError_t ens_launch(fire_ensemble *e, double dt, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    const bool f64 = e->prec == FIRE_FP64;
     if (e->variant == FIRE_KERNEL_WARP) {
-        if (e->prec == FIRE_FP64)
-            return cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<double>, ea, e->max_rows);
-        return cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<float>, ea, e->max_rows);
+        if (e->nc)
+            return f64 ? cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<double, true>, ea, e->max_rows)
+                       : cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<float, true>, ea, e->max_rows);
+        return f64 ? cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<double, false>, ea, e->max_rows)
+                   : cudaLaunchKernelEx(&cfg, k_fire_ensemble_warp<float, false>, ea, e->max_rows);
     }
-    if (e->prec == FIRE_FP64) return cudaLaunchKernelEx(&cfg, k_fire_ensemble<double>, ea);
-    return cudaLaunchKernelEx(&cfg, k_fire_ensemble<float>, ea);
+    if (e->nc)
+        return f64 ? cudaLaunchKernelEx(&cfg, k_fire_ensemble<double, true>, ea)
+                   : cudaLaunchKernelEx(&cfg, k_fire_ensemble<float, true>, ea);
+    return f64 ? cudaLaunchKernelEx(&cfg, k_fire_ensemble<double, false>, ea)
+               : cudaLaunchKernelEx(&cfg, k_fire_ensemble<float, false>, ea);
 }
 
 }  // namespace
@@ -460,9 +475,17 @@ int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_d
     for (int m = 0; m < n_members && r == FIRE_OK; ++m) {
         const fire_member_desc &d = members[m];
         fire_ctx *c = nullptr;
-        r = fire_init(&c, &d.grid, d.classes, d.n_classes, d.fuel_class_dev, nullptr,
+        r = fire_init(&c, &d.grid, d.classes, d.n_classes, d.fuel_class_dev, d.moisture_dev,
                       d.spread_mult_dev, d.dzdx_dev, d.dzdy_dev, d.ignitions, d.n_ign, cuda_stream);
         if (r == FIRE_OK) e->members.push_back(c);
+    }
+    // one member with a per-node moisture: every member takes the per-node
+    // coefficient form of the kernel (the others' planes from their classes)
+    if (r == FIRE_OK) {
+        for (fire_ctx *c : e->members) e->nc = e->nc || ctx_has_node_coefficients(c);
+        if (e->nc)
+            for (fire_ctx *c : e->members)
+                if (r == FIRE_OK) r = ctx_ensure_node_coefficients(c);
     }
     // the warp form when every member can take warp strips (FP32, refinement
     // <= 30), else the marching form for all; members start from the

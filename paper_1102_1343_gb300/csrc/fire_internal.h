@@ -42,6 +42,10 @@ struct StepArgs {
     int kx, ky;  // tile = kx*srx by ky*sry nodes
     int band;
     double dx, dy, eps, dt;
+    // per-node coefficients of a per-node fuel moisture, or all null: R0, c,
+    // d, H_s, H_q, each [ny][nx] in the path precision (S0, b, e and T_f
+    // stay per class)
+    const void *nco[5];
 };
 
 struct IgnSeg {
@@ -121,6 +125,19 @@ cudaError_t launch_coefficients(const fire_fuel_class *classes_dev, int n, doubl
 // numbers through the same chain)
 cudaError_t launch_coefficients_dMf(const fire_fuel_class *classes_dev, int n, double *dcoef_dev,
                                     cudaStream_t s);
+
+// per-node coefficients at a per-node moisture (null: class moisture):
+// planes is a host array of 5 device pointers (R0, c, d, H_s, H_q, each [n]
+// in the path precision); aos (nullable) receives [n][K_N] doubles
+template <typename T>
+cudaError_t launch_node_coefficients(const fire_fuel_class *classes_dev, int ncls,
+                                     const uint8_t *fuel, const void *moist, size_t n,
+                                     T *const *planes, double *aos, cudaStream_t s);
+// d(coefficients)/d(M_f) per node at the node's moisture: [n][K_N] doubles
+template <typename T>
+cudaError_t launch_node_coefficients_dMf(const fire_fuel_class *classes_dev, int ncls,
+                                         const uint8_t *fuel, const void *moist, size_t n,
+                                         double *daos, cudaStream_t s);
 
 // a fuel class fire_init accepts: a positive weight (burn time), and for a
 // Rothermel class with fuel (Table 2) a positive surface-area-to-volume

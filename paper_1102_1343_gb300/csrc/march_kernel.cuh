@@ -133,8 +133,9 @@ __device__ __forceinline__ T pick(const typename Vec2<T>::type &v, int j) {
     return j == 0 ? v.x : v.y;
 }
 
-// Per-thread state of one strip.
-template <typename T>
+// Per-thread state of one strip.  NC: per-node R0, c, d and heat factors (a
+// per-node fuel moisture) from the planes of StepArgs::nco.
+template <typename T, bool NC = false>
 struct MarchStrip {
     using T2 = typename Vec2<T>::type;
     const StepArgs &a;
@@ -151,6 +152,7 @@ struct MarchStrip {
     T2 cur_psi;   // psi^n of the row staged this iteration
     int pf_fa, pf_fb;  // raw fuel-class bytes of the prefetched row (decoded at use)
     T2 pf_zx, pf_zy, pf_m;
+    T2 pf_R0, pf_c, pf_d, e_R0, e_c, e_d;  // per-node coefficients (NC only)
     T2 pf_F;
     int e_cls[2];       // environment of the row stage 1 handled last iteration
     T2 e_zx, e_zy, e_m, e_un, e_vn;
@@ -193,6 +195,11 @@ struct MarchStrip {
         pf_zx = ld2(static_cast<const T *>(a.dzdx), r);
         pf_zy = ld2(static_cast<const T *>(a.dzdy), r);
         if (a.mult) pf_m = ld2(static_cast<const T *>(a.mult), r);
+        if constexpr (NC) {
+            pf_R0 = ld2(static_cast<const T *>(a.nco[0]), r);
+            pf_c = ld2(static_cast<const T *>(a.nco[1]), r);
+            pf_d = ld2(static_cast<const T *>(a.nco[2]), r);
+        }
     }
 
     // x-interpolated wind of atmos u-row J / v-row J for this thread's columns
@@ -239,7 +246,8 @@ struct MarchStrip {
     // slot sr of a staged field B (down: slot sd, up: value given), with
     // ghosts at the domain boundary (Sect. 3.1), and -F there (pair arithmetic)
     __device__ __forceinline__ T2 stage_rhs2(const T2 *B, int sr, int sd, T2 up, int r, int cls0,
-                                             int cls1, T2 zx, T2 zy, T2 m, T2 un, T2 vn) const {
+                                             int cls1, T2 zx, T2 zy, T2 m, T2 un, T2 vn, T2 nR0,
+                                             T2 nc, T2 nd) const {
         const int NT = kMarchThreads;
         const T2 own = B[sr * NT + c];
         T2 L = mk2(B[sr * NT + c - 1].y, own.x), R = mk2(own.y, B[sr * NT + c + 1].x);
@@ -254,6 +262,11 @@ struct MarchStrip {
         }
         WCoef<T> co;
         coef_pair<T>(sm.lut, cls0 > ncm1 ? ncm1 : cls0, cls1 > ncm1 ? ncm1 : cls1, co);
+        if constexpr (NC) {
+            co.R0 = nR0;
+            co.c = nc;
+            co.d = nd;
+        }
         return neg_rhs2<T>(own, L, R, D, U, idx2, idy2, i2dx2, i2dy2, eps2, co, m, un, vn, zx, zy);
     }
 
@@ -278,6 +291,12 @@ struct MarchStrip {
         // ---- B: stage 1 on row k+2 (its environment is carried to C)
         const int eb_cls0 = e_cls[0], eb_cls1 = e_cls[1];
         const T2 eb_zx = e_zx, eb_zy = e_zy, eb_m = e_m, eb_un = e_un, eb_vn = e_vn;
+        T2 eb_R0, eb_c, eb_d;  // read by stage_rhs2 only with NC
+        if constexpr (NC) {
+            eb_R0 = e_R0;
+            eb_c = e_c;
+            eb_d = e_d;
+        }
         {
             const int r = k + 2;
             e_cls[0] = vec ? (pf_fa & 0xff) : pf_fa;
@@ -285,6 +304,11 @@ struct MarchStrip {
             e_zx = pf_zx;
             e_zy = pf_zy;
             e_m = pf_m;
+            if constexpr (NC) {
+                e_R0 = pf_R0;
+                e_c = pf_c;
+                e_d = pf_d;
+            }
             load_env(k + 3);
             if (in_rows(r, y0 - 2, y0 + La + 2) && (m_s1[0] || m_s1[1])) {
                 wind(r, true, e_un, e_vn);
@@ -292,7 +316,7 @@ struct MarchStrip {
                     (m_s1[1] && (!finite_val(e_un.y) || !finite_val(e_vn.y))))
                     st |= ST_NONFINITE;
                 T2 F = stage_rhs2(sm.S0, s2, s1, cur_psi, r, e_cls[0], e_cls[1], e_zx, e_zy, e_m,
-                                  e_un, e_vn);
+                                  e_un, e_vn, e_R0, e_c, e_d);
                 F.x = m_s1[0] ? F.x : T(0);
                 F.y = m_s1[1] ? F.y : T(0);
                 const T2 own = sm.S0[s2 * NT + c];
@@ -311,7 +335,7 @@ struct MarchStrip {
                 const bool own_row = r >= y0 && r < y0 + La;
                 T2 DL;
                 const T2 F2 = stage_rhs2(sm.S1, s1, s0, up, r, eb_cls0, eb_cls1, eb_zx, eb_zy, eb_m,
-                                         eb_un, eb_vn);
+                                         eb_un, eb_vn, eb_R0, eb_c, eb_d);
                 T2 PN = fma2(ndth2, add2(f1v, F2), p0v);
                 PN.x = m_s2[0] ? PN.x : T(0);
                 PN.y = m_s2[1] ? PN.y : T(0);
@@ -463,10 +487,15 @@ struct MarchStrip {
                 for (int j = 0; j < 2; ++j) {
                     const T dF = j == 0 ? dF0 : dF1;
                     if (dF != T(0)) {
-                        const int cls0 = a.fuel[g + j];
-                        const int cls = cls0 > ncm1 ? ncm1 : cls0;
-                        acc_s[j] += dF * sm.lut[cls * 8 + 7];
-                        acc_q[j] += dF * sm.lutq[cls];
+                        if constexpr (NC) {
+                            acc_s[j] += dF * static_cast<const T *>(a.nco[3])[g + j];
+                            acc_q[j] += dF * static_cast<const T *>(a.nco[4])[g + j];
+                        } else {
+                            const int cls0 = a.fuel[g + j];
+                            const int cls = cls0 > ncm1 ? ncm1 : cls0;
+                            acc_s[j] += dF * sm.lut[cls * 8 + 7];
+                            acc_q[j] += dF * sm.lutq[cls];
+                        }
                     }
                 }
             }
@@ -607,11 +636,17 @@ struct MarchStrip {
         pf_fa = pf_fb = 0;
         pf_zx.x = pf_zx.y = pf_zy.x = pf_zy.y = T(0);
         pf_m.x = pf_m.y = T(1);
+        if constexpr (NC) pf_R0 = pf_c = pf_d = pf_zx;
         load_env(k0 + 2);
         e_cls[0] = e_cls[1] = 0;
         e_zx = pf_zx;
         e_zy = pf_zy;
         e_m = pf_m;
+        if constexpr (NC) {
+            e_R0 = pf_R0;
+            e_c = pf_c;
+            e_d = pf_d;
+        }
         e_un = pf_zx;
         e_vn = pf_zx;
         pf_F.x = pf_F.y = T(1);
@@ -620,7 +655,7 @@ struct MarchStrip {
     }
 };
 
-template <typename T>
+template <typename T, bool NC>
 __global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks) k_fire_march(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     MarchSmem<T> sm;
@@ -629,7 +664,7 @@ __global__ void __launch_bounds__(kMarchThreads, MarchOccupancy<T>::blocks) k_fi
         *sm.status = 0;
         if (blockIdx.x == 0 && blockIdx.y == 0) *a.t_out = *a.t_in + a.dt;
     }
-    MarchStrip<T> s(a, sm);
+    MarchStrip<T, NC> s(a, sm);
     s.run(blockIdx.x * a.kx * a.srx, blockIdx.y * a.ky * a.sry, *a.t_in);
     if (s.st) atomicOr(sm.status, s.st);
     __syncthreads();
@@ -649,8 +684,11 @@ cudaError_t prepare_march_kernel(size_t smem_bytes) {
     static size_t current = 0;
     std::lock_guard<std::mutex> lock(mu);
     if (smem_bytes <= current) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_fire_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_fire_march<T, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fire_march<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes);
     if (e == cudaSuccess) current = smem_bytes;
     return e;
 }
@@ -662,7 +700,10 @@ cudaError_t launch_march(const StepArgs &a, cudaStream_t s) {
     const size_t smem = march_smem_bytes<T>(a.ky, a.sry, a.ncls);
     cudaError_t e = prepare_march_kernel<T>(smem);
     if (e != cudaSuccess) return e;
-    k_fire_march<T><<<grid, kMarchThreads, smem, s>>>(a);
+    if (a.nco[0])
+        k_fire_march<T, true><<<grid, kMarchThreads, smem, s>>>(a);
+    else
+        k_fire_march<T, false><<<grid, kMarchThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -149,6 +149,22 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
     const T *__restrict__ wu = static_cast<const T *>(a.u);
     const T *__restrict__ wv = static_cast<const T *>(a.v);
     const uint8_t *__restrict__ fuel = a.fuel;
+    // per-node R0, c, d, H_s, H_q of a per-node fuel moisture (all null
+    // otherwise): they replace the class values
+    const T *__restrict__ nR0 = static_cast<const T *>(a.nco[0]);
+    const T *__restrict__ nc = static_cast<const T *>(a.nco[1]);
+    const T *__restrict__ nd = static_cast<const T *>(a.nco[2]);
+    const T *__restrict__ nhs = static_cast<const T *>(a.nco[3]);
+    const T *__restrict__ nhq = static_cast<const T *>(a.nco[4]);
+    auto node_coef = [&](int cls, size_t g, T *cn) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) cn[q] = lut[cls * K_N + q];
+        if (nR0) {
+            cn[K_R0] = nR0[g];
+            cn[K_C] = nc[g];
+            cn[K_D] = nd[g];
+        }
+    };
 
     const T dt = T(a.dt);
     const T idx = T(1) / T(a.dx), idy = T(1) / T(a.dy);
@@ -197,8 +213,10 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
             if (!finite_val(un) || !finite_val(vn)) st |= ST_NONFINITE;
             const T m = mult ? mult[g] : T(1);
             const int c = (ly + 1) * BW3 + (lx + 1);
-            const T F = rhs_at<T>(P0, c, BW3, idx, idy, i2dx, i2dy, eps, lut + cls * K_N, m, un,
-                                  vn, dzdx[g], dzdy[g]);
+            T cn[6];
+            node_coef(cls, g, cn);
+            const T F = rhs_at<T>(P0, c, BW3, idx, idy, i2dx, i2dy, eps, cn, m, un, vn, dzdx[g],
+                                  dzdy[g]);
             P1[ly * BW2 + lx] = P0[c] + dt * F;
             if (lx >= 1 && lx < BW2 - 1 && ly >= 1 && ly < BH2 - 1) F1[(ly - 1) * BW1 + (lx - 1)] = F;
         }
@@ -223,8 +241,10 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
             T un, vn;
             wind_at<T>(wu, wv, a.nxa, a.nya, srx, sry, gx, gy, un, vn);
             const T m = mult ? mult[g] : T(1);
+            T cn[6];
+            node_coef(cls, g, cn);
             const T F2 = rhs_at<T>(P1, (ly + 1) * BW2 + (lx + 1), BW2, idx, idy, i2dx, i2dy, eps,
-                                   lut + cls * K_N, m, un, vn, dzdx[g], dzdy[g]);
+                                   cn, m, un, vn, dzdx[g], dzdy[g]);
             const T p0 = P0[(ly + 2) * BW3 + (lx + 2)];
             const T pn = p0 + dt * (T(0.5) * F1[l1] + T(0.5) * F2);
             P2[l1] = pn;
@@ -268,8 +288,8 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
                 const T Fo = F_in[g];
                 F_out[g] = Fn;
                 const T dF = Fo - Fn;
-                hs = dF * co[K_HS];
-                hq = dF * co[K_HQ];
+                hs = dF * (nhs ? nhs[g] : co[K_HS]);
+                hq = dF * (nhq ? nhq[g] : co[K_HQ]);
             }
             Q[2 * (ly * TX + lx)] = hs;
             Q[2 * (ly * TX + lx) + 1] = hq;

@@ -56,9 +56,12 @@ struct WEnv {  // what stage 2 reuses from stage 1 of the same row
     using V = typename PairT<T>::t;
     int cls0, cls1;  // raw fuel bytes when loaded (see decode), classes after
     V zx, zy, m, un, vn;
+    V R0, c, d;      // per-node coefficients (NC only)
 };
 
-template <typename T>
+// NC: per-node R0, c, d and heat factors (a per-node fuel moisture) read
+// from the planes of StepArgs::nco instead of the class table
+template <typename T, bool NC = false>
 struct WarpStrip {
     using V = typename PairT<T>::t;
     const StepArgs &a;
@@ -117,6 +120,11 @@ struct WarpStrip {
         e.zx = ld(static_cast<const T *>(a.dzdx), r);
         e.zy = ld(static_cast<const T *>(a.dzdy), r);
         e.m = a.mult ? ld(static_cast<const T *>(a.mult), r) : splat<V>(T(1));
+        if constexpr (NC) {
+            e.R0 = ld(static_cast<const T *>(a.nco[0]), r);
+            e.c = ld(static_cast<const T *>(a.nco[1]), r);
+            e.d = ld(static_cast<const T *>(a.nco[2]), r);
+        }
     }
 
     __device__ __forceinline__ void decode(WEnv<T> &e) const {
@@ -127,6 +135,11 @@ struct WarpStrip {
 
     __device__ __forceinline__ void coef(const WEnv<T> &e, WCoef<T> &co) const {
         coef_pair_dup<T>(lut2, e.cls0, e.cls1, co);
+        if constexpr (NC) {
+            co.R0 = e.R0;
+            co.c = e.c;
+            co.d = e.d;
+        }
     }
 
     // x-interpolated wind of atmos row J at this lane's columns
@@ -260,6 +273,7 @@ struct WarpStrip {
         WEnv<T> envB, envC, envPre;
         envB.cls0 = envB.cls1 = 0;
         envB.zx = envB.zy = envB.un = envB.vn = P0;
+        envB.R0 = envB.c = envB.d = P0;
         envB.m = splat<V>(T(1));
         envC = envB;
         envPre = envB;
@@ -510,17 +524,30 @@ struct WarpStrip {
         const V dF = sub2(Fn, F1);
         if (__any_sync(0xffffffffu, dF.x != T(0) || dF.y != T(0))) {
             const T dFa = outA ? dF.x : T(0), dFb = outB ? dF.y : T(0);
-            if (dFa != T(0)) {
-                int cls = a.fuel[g];
-                cls = cls > ncm1 ? ncm1 : cls;
-                acc_s.x += dFa * lut[cls * 8 + 7];
-                acc_q.x += dFa * lutq[cls];
-            }
-            if (dFb != T(0)) {
-                int cls = a.fuel[g + 1];
-                cls = cls > ncm1 ? ncm1 : cls;
-                acc_s.y += dFb * lut[cls * 8 + 7];
-                acc_q.y += dFb * lutq[cls];
+            if constexpr (NC) {
+                const T *hs = static_cast<const T *>(a.nco[3]);
+                const T *hq = static_cast<const T *>(a.nco[4]);
+                if (dFa != T(0)) {
+                    acc_s.x += dFa * hs[g];
+                    acc_q.x += dFa * hq[g];
+                }
+                if (dFb != T(0)) {
+                    acc_s.y += dFb * hs[g + 1];
+                    acc_q.y += dFb * hq[g + 1];
+                }
+            } else {
+                if (dFa != T(0)) {
+                    int cls = a.fuel[g];
+                    cls = cls > ncm1 ? ncm1 : cls;
+                    acc_s.x += dFa * lut[cls * 8 + 7];
+                    acc_q.x += dFa * lutq[cls];
+                }
+                if (dFb != T(0)) {
+                    int cls = a.fuel[g + 1];
+                    cls = cls > ncm1 ? ncm1 : cls;
+                    acc_s.y += dFb * lut[cls * 8 + 7];
+                    acc_q.y += dFb * lutq[cls];
+                }
             }
         }
         // after the last row of an atmospheric band: average per cell
@@ -549,7 +576,7 @@ struct WarpStrip {
     }
 };
 
-template <typename T>
+template <typename T, bool NC>
 __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(const StepArgs a) {
     __shared__ __align__(16) T lut[FIRE_MAX_CLASSES * 8];
     __shared__ __align__(16) T lut2[FIRE_MAX_CLASSES * 12];
@@ -593,7 +620,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
     const int W = a.kx * a.srx;
     const int x0 = (blockIdx.x * kWarpStrips + w) * W;
     if (x0 >= a.nx) return;  // whole warp
-    WarpStrip<T> s(a, lut, lut2, lutq, hw[w], rows);
+    WarpStrip<T, NC> s(a, lut, lut2, lutq, hw[w], rows);
     s.run(x0, y0, tstart);
     const int stw = __reduce_or_sync(0xffffffffu, s.st);
     if ((threadIdx.x & 31) == 0 && stw) atomicOr(a.status, stw);
@@ -606,7 +633,10 @@ cudaError_t launch_warp(const StepArgs &a, cudaStream_t s) {
         return cudaErrorInvalidValue;
     const int strips = (a.nx + W - 1) / W;
     dim3 grid((strips + kWarpStrips - 1) / kWarpStrips, (a.ny + L - 1) / L);
-    k_fire_warp<T><<<grid, kWarpCtaThreads, 0, s>>>(a);
+    if (a.nco[0])
+        k_fire_warp<T, true><<<grid, kWarpCtaThreads, 0, s>>>(a);
+    else
+        k_fire_warp<T, false><<<grid, kWarpCtaThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,18 @@ def as_path_precision(w: synth.Workload, prec: str) -> synth.Workload:
     import dataclasses
     r = lambda a: None if a is None else np.asarray(a, np.float32).astype(np.float64)
     return dataclasses.replace(w, dzdx=r(w.dzdx), dzdy=r(w.dzdy), u=r(w.u), v=r(w.v),
-                               mult=r(w.mult))
+                               mult=r(w.mult), moisture=r(w.moisture))
+
+
+def node_moisture(w, seed=5, amp=0.05, length=6.0):
+    """Give w a per-node fuel moisture: each node's class moisture plus a
+    smooth random field of +-amp (clipped at 0.01)."""
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(seed)
+    f = gaussian_filter(rng.standard_normal((w.ny, w.nx)), length, mode="reflect")
+    f *= amp / max(np.abs(f).max(), 1e-12)
+    w.moisture = np.maximum(0.01, np.array([c["fuelmc_g"] for c in w.classes])[w.fuel] + f)
+    return w
 
 
 def state_np(m):

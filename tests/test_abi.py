@@ -48,9 +48,10 @@ def test_strerror_and_argument_checks_without_gpu(lib):
     g = pkg.make_grid(10, 10, 10, 10, 60.0, 60.0)
     cls = pkg.make_classes([{"fgi": 0.5, "weight": 7.0, "savr": 1e4, "fueldepthm": 0.3,
                              "fueldens": 500.0, "fuelmce": 0.3, "se": 0.01}])
-    # moisture per node is not supported: rejected before any device call
-    assert lib.fire_init(C.byref(out), C.byref(g), cls, 1, 1, 1, None, 1, 1, None, 0,
+    # no fuel class: rejected before any device call
+    assert lib.fire_init(C.byref(out), C.byref(g), cls, 0, 1, 1, None, 1, 1, None, 0,
                          None) == pkg.FIRE_ERR_ARG
+    assert lib.fire_set_moisture(None, None) == pkg.FIRE_ERR_ARG
     bad = pkg.make_grid(1, 1, 1, 1, 60.0, 60.0)  # a 1x1 fire mesh cannot be extrapolated
     assert lib.fire_init(C.byref(out), C.byref(bad), cls, 1, 1, None, None, 1, 1, None, 0,
                          None) == pkg.FIRE_ERR_ARG

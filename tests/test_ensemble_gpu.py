@@ -38,6 +38,20 @@ def member_workloads():
     return ws
 
 
+def add_node_moisture(ws, members=(0, 1)):
+    """Per-node fuel moisture on some members (class moisture + a smooth
+    +-0.04 field); the others keep their class moisture, and the ensemble
+    then gives every member per-node coefficients."""
+    from scipy.ndimage import gaussian_filter
+    for k in members:
+        w = ws[k]
+        rng = np.random.default_rng(60 + k)
+        f = gaussian_filter(rng.standard_normal((w.ny, w.nx)), 6.0, mode="reflect")
+        f *= 0.04 / max(np.abs(f).max(), 1e-12)
+        w.moisture = np.maximum(0.01, np.array([c["fuelmc_g"] for c in w.classes])[w.fuel] + f)
+    return ws
+
+
 def make_ensemble(pkg, ws, prec):
     import torch
     P = pkg.FIRE_FP64 if prec == "fp64" else pkg.FIRE_FP32
@@ -47,11 +61,13 @@ def make_ensemble(pkg, ws, prec):
         fuel = torch.as_tensor(w.fuel).cuda().contiguous()
         zx = torch.as_tensor(w.dzdx).to("cuda", dt_).contiguous()
         zy = torch.as_tensor(w.dzdy).to("cuda", dt_).contiguous()
-        keep += [fuel, zx, zy]
+        mo = (None if w.moisture is None
+              else torch.as_tensor(w.moisture).to("cuda", dt_).contiguous())
+        keep += [fuel, zx, zy, mo]
         members.append(dict(grid=pkg.make_grid(w.nxa, w.nya, w.srx, w.sry, w.dx_atm, w.dy_atm, P,
                                                w.band, w.eps),
                             classes=w.classes, fuel_class_dev=fuel, dzdx_dev=zx, dzdy_dev=zy,
-                            ignitions=w.ignitions))
+                            moisture_dev=mo, ignitions=w.ignitions))
         winds.append((torch.as_tensor(w.u).to("cuda", dt_).contiguous(),
                       torch.as_tensor(w.v).to("cuda", dt_).contiguous()))
     ens = pkg.fire_ensemble_create(members)
@@ -71,10 +87,13 @@ def member_state(pkg, ens, m, w, prec):
     return psi.double().cpu().numpy(), tign.cpu().numpy(), frac.double().cpu().numpy(), t
 
 
+@pytest.mark.parametrize("moisture", [False, True])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_members_equal_single_runs(pkg, prec):
+def test_members_equal_single_runs(pkg, prec, moisture):
     import torch
     ws = member_workloads()
+    if moisture:
+        ws = add_node_moisture(ws)
     ens, winds = make_ensemble(pkg, ws, prec)
     hs = [torch.zeros((w.nya, w.nxa), dtype=torch.float64, device="cuda") for w in ws]
     hl = [torch.zeros_like(h) for h in hs]
@@ -102,8 +121,11 @@ def test_members_equal_single_runs(pkg, prec):
     pkg.fire_ensemble_destroy(ens)
 
 
-def test_members_match_oracle_fp64(pkg):
+@pytest.mark.parametrize("moisture", [False, True])
+def test_members_match_oracle_fp64(pkg, moisture):
     ws = member_workloads()
+    if moisture:
+        ws = add_node_moisture(ws)
     ens, winds = make_ensemble(pkg, ws, "fp64")
     pkg.fire_ensemble_step(ens, 24, ws[0].dt, [u for u, _ in winds], [v for _, v in winds])
     for m, w in enumerate(ws):

@@ -86,6 +86,8 @@ def test_line2000_full_run_fp32_and_fp64_against_oracle():
         "tolerances": {"fp64_rel": 1e-10, "fp32_tign_s": 0.1, "fp32_area_rel": 0.005,
                        "fp32_heat_rel": 1e-4},
     }
+    import bench  # the hash of the step-kernel sources the record belongs to
+    rec["kernel_source_hash"] = bench.kernel_hash()
     print(json.dumps(rec, indent=1))
     out = os.environ.get("WRFFIRE_ACCURACY_OUT")
     if out:
@@ -93,7 +95,8 @@ def test_line2000_full_run_fp32_and_fp64_against_oracle():
             json.dump(rec, f, indent=1)
     m64.close()
     m32.close()
-    assert rec["ignited_nodes_oracle"] > 50000 and Q["oracle"] > 0
+    # the 1 km line (about 560 nodes at t = 0) has grown to several times that
+    assert rec["ignited_nodes_oracle"] > 2000 and Q["oracle"] > 0
     e = rec["fp64"]
     assert e["psi_rel_inf"] <= 1e-10 and e["frac_rel_inf"] <= 1e-10, e
     assert e["tign_rel_inf"] <= 1e-10 and e["ignited_mismatch"] == 0, e

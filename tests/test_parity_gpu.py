@@ -11,7 +11,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_helpers import as_path_precision, compare_fp64, crop_step, rel_inf, state_np
+from gpu_helpers import (as_path_precision, compare_fp64, crop_step, node_moisture, rel_inf,
+                         state_np)
 from paper_1102_1343_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -153,15 +154,62 @@ def test_fp64_chaparral(pkg, tile):
     assert heat_err <= 1e-10
 
 
+@pytest.mark.parametrize("tile", [None, (1, 12, 3), (0, 3, 2), (2, 6, 5)])
+def test_fp64_node_moisture(pkg, tile):
+    """A per-node fuel moisture (class moisture + a smooth +-0.05 field): the
+    coefficients R0, c, d and the heat factors of each node from Table 2 at
+    that node's moisture, in every kernel, against the oracle's per-node
+    coefficients (orc_node_coefficients with the moisture field)."""
+    w = node_moisture(synth.random_landscape(23, 17, seed=21, ignition="line", steps=120))
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    assert Qo > 0 and abs(Qg - Qo) <= 1e-10 * Qo
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_class_valued_node_moisture_changes_no_bit(pkg, prec):
+    """A per-node moisture equal to every node's class moisture gives the same
+    coefficients, so the per-node kernels give the same bits as the class
+    table; fire_set_moisture(None) returns to the class table."""
+    import torch
+    w = synth.random_landscape(24, 10, seed=31, ignition="points", n_points=6, edge_margin=150.0,
+                               steps=120)
+    a = pkg.FireModel.from_workload(w, precision=prec)
+    w.moisture = np.array([c["fuelmc_g"] for c in w.classes])[w.fuel]
+    b = pkg.FireModel.from_workload(w, precision=prec)
+    c = pkg.FireModel.from_workload(w, precision=prec)
+    c.set_moisture(None)
+    u, v = a.wind(w.u, w.v)
+    for _ in range(w.steps):
+        hs_a, hl_a = a.step(u, v, w.dt)
+        hs_b, hl_b = b.step(u, v, w.dt)
+        hs_c, _ = c.step(u, v, w.dt)
+    torch.cuda.synchronize()
+    sa, sb, sc = state_np(a), state_np(b), state_np(c)
+    assert np.isfinite(sa[1]).sum() > 50
+    for k in range(3):
+        assert np.array_equal(sa[k], sb[k]) and np.array_equal(sa[k], sc[k])
+    assert np.array_equal(hs_a.cpu().numpy(), hs_b.cpu().numpy())
+    assert np.array_equal(hl_a.cpu().numpy(), hl_b.cpu().numpy())
+    assert np.array_equal(hs_a.cpu().numpy(), hs_c.cpu().numpy())
+    for x in (a, b, c):
+        x.close()
+
+
 # ---------------------------------------------------------------------------
 # FP32: ignition time 0.1 s, burnt area 0.5 %, integrated heat 1e-4
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("case,tile", [("line", None), ("points", None), ("line", (0, 8, 4)),
-                                       ("line", (2, 6, 20)), ("points", (2, 6, 20))])
+                                       ("line", (2, 6, 20)), ("points", (2, 6, 20)),
+                                       ("line-moisture", None), ("points-moisture", (1, 12, 4))])
 def test_fp32_against_fp64_oracle(pkg, case, tile):
-    w = synth.random_landscape(32, 26, seed=44, ignition=case, n_points=6, edge_margin=300.0,
-                               steps=300)
+    w = synth.random_landscape(32, 26, seed=44, ignition=case.split("-")[0], n_points=6,
+                               edge_margin=300.0, steps=300)
+    if case.endswith("moisture"):
+        w = node_moisture(w)
     m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp32", tile=tile)
     psi, tign, frac, _ = state_np(m)
     both = np.isfinite(tign) & np.isfinite(orc.tign)
