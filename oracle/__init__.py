@@ -31,7 +31,7 @@ FUEL_FIELDS = ("windrf", "weight", "weight_is_tf", "fgi", "fueldepthm", "savr",
                "fuelmce", "fueldens", "st", "se", "cmbcnst", "fuelmc_g", "chaparral")
 # order of the 9 coefficients (eq. spread-WRF-Fire + T_f + heat factors)
 COEF_FIELDS = ("S0", "R0", "b", "c", "d", "e", "Tf", "Hs", "Hq")
-IGN_FIELDS = ("ax", "ay", "bx", "by", "t_start", "radius", "speed")
+IGN_FIELDS = ("ax", "ay", "bx", "by", "t_start", "radius", "speed", "vx", "vy", "t_end")
 STATUS_BOUNDARY = 1
 STATUS_NONFINITE = 2
 
@@ -147,7 +147,8 @@ def ignition_table(ignitions) -> np.ndarray:
     if not ignitions:
         return np.zeros((1, len(IGN_FIELDS)), dtype=np.float64)
     return np.ascontiguousarray(
-        np.array([[float(g[k]) for k in IGN_FIELDS] for g in ignitions], dtype=np.float64))
+        np.array([[float(g.get(k, 0.0)) for k in IGN_FIELDS] for g in ignitions],
+                 dtype=np.float64))
 
 
 def rothermel_rate(cls: dict, U: float, tanphi: float, Mf: float | None = None) -> float:

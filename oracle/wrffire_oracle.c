@@ -409,15 +409,30 @@ void orc_rhs(int nx, int ny, double dx, double dy, double eps,
 /* Ignition (Sect. "Ignition").                                        */
 /* ------------------------------------------------------------------ */
 
-/* One ignition segment: 7 doubles {ax, ay, bx, by, t_g, r_g, S_g}.
- * S_g > 0: the fire grows from the segment at S_g until r_g is reached,
- * eqs. (ignition-lfn), (ignition-min); active at the start of every step
- * with t_g <= t <= t_g + r_g/S_g; newly ignited nodes get the arrival time
- * t_g + dist/S_g.
+/* One ignition: 10 doubles {ax, ay, bx, by, t_g, r_g, S_g, vx, vy, t_h}.
+ * S_g > 0, v = 0: the fire grows from the segment [a, b] at S_g until r_g is
+ * reached, eqs. (ignition-lfn), (ignition-min); active at the start of
+ * every step with t_g <= t <= t_g + r_g/S_g; newly ignited nodes get the
+ * arrival time t_g + dist/S_g.
+ * S_g > 0, v != 0: the drip torch of Sect. "Ignition": a torch leaves a at
+ * t_g with velocity v until t_h, the ignition line at t is the segment
+ * [a, a + v (min{t, t_h} - t_g)] (b is not used) and psi_g = dist - min{r_g,
+ * S_g (t - t_g)}, applied at every step start with t_g <= t <= t_h +
+ * r_g/S_g.  Reading of "the arrival time of the fire at the spread rate S_g
+ * from the nearest point on the ignition segment": the fire at the nearest
+ * point p starts when the torch lays p, at t_p = t_g + s (min{t, t_h} -
+ * t_g) for p = a + s (b(t) - a), and reaches the node dist/S_g later; a node
+ * psi_g covers at step start t is burning by t, so its time is min{t, t_p +
+ * dist/S_g} (with v = 0, t_p = t_g: the fixed segment's t_g + dist/S_g).
  * S_g <= 0: reading for an instantaneous ignition of radius r_g (the earlier
  * mechanism the section describes): applied once, at the first step start
  * t >= t_g (or at initialisation when t_g <= 0), with ignition time t_g. */
-enum { IG_AX = 0, IG_AY, IG_BX, IG_BY, IG_TG, IG_RG, IG_SG, IG_N };
+enum { IG_AX = 0, IG_AY, IG_BX, IG_BY, IG_TG, IG_RG, IG_SG, IG_VX, IG_VY, IG_TH, IG_N };
+
+static int is_drip(const double *g)
+{
+    return g[IG_SG] > 0.0 && (g[IG_VX] != 0.0 || g[IG_VY] != 0.0);
+}
 
 static double dist_to_segment(double x, double y, const double *g)
 {
@@ -441,6 +456,40 @@ static double dist_to_segment(double x, double y, const double *g)
 static void apply_segment(int nx, int ny, double dx, double dy, const double *g,
                           double t, double *psi, double *tign)
 {
+    if (is_drip(g)) {
+        /* the drip torch's segment and radius at t (Sect. "Ignition") */
+        double seg[IG_N];
+        for (int k = 0; k < IG_N; ++k) seg[k] = g[k];
+        double tt = t < g[IG_TH] ? t : g[IG_TH];
+        seg[IG_BX] = g[IG_AX] + g[IG_VX] * (tt - g[IG_TG]);
+        seg[IG_BY] = g[IG_AY] + g[IG_VY] * (tt - g[IG_TG]);
+        double R = g[IG_SG] * (t - g[IG_TG]);
+        if (R > g[IG_RG]) R = g[IG_RG];
+        double dxs = seg[IG_BX] - seg[IG_AX], dys = seg[IG_BY] - seg[IG_AY];
+        double L2 = dxs * dxs + dys * dys;
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                long k = (long)j * nx + i;
+                double x = ((double)i + 0.5) * dx, y = ((double)j + 0.5) * dy;
+                double d = dist_to_segment(x, y, seg);
+                double pg = d - R;
+                if (psi[k] > 0.0 && pg <= 0.0 && isinf(tign[k])) {
+                    /* parameter of the nearest point, as in dist_to_segment */
+                    double sp = 0.0;
+                    if (L2 > 0.0) {
+                        sp = ((x - seg[IG_AX]) * dxs + (y - seg[IG_AY]) * dys) / L2;
+                        if (sp < 0.0) sp = 0.0;
+                        if (sp > 1.0) sp = 1.0;
+                    }
+                    double tp = g[IG_TG] + sp * (tt - g[IG_TG]);
+                    double ta = tp + d / g[IG_SG];
+                    tign[k] = ta < t ? ta : t;
+                }
+                if (pg < psi[k]) psi[k] = pg;
+            }
+        }
+        return;
+    }
     int instant = !(g[IG_SG] > 0.0);
     double rho = instant ? g[IG_RG] : g[IG_SG] * (t - g[IG_TG]);
     for (int j = 0; j < ny; ++j) {
@@ -469,6 +518,9 @@ void orc_ignite(int nx, int ny, double dx, double dy, const double *ign, int n_i
                 apply_segment(nx, ny, dx, dy, g, t, psi, tign);
                 applied[q] = 1;
             }
+        } else if (is_drip(g)) {
+            if (g[IG_TG] <= t && t <= g[IG_TH] + g[IG_RG] / g[IG_SG])
+                apply_segment(nx, ny, dx, dy, g, t, psi, tign);
         } else if (g[IG_TG] <= t && t <= g[IG_TG] + g[IG_RG] / g[IG_SG]) {
             apply_segment(nx, ny, dx, dy, g, t, psi, tign);
         }

@@ -190,6 +190,15 @@ def line_ignition(ax, ay, bx, by, radius=10.0, t_start=0.0, speed=0.0):
                 t_start=float(t_start), radius=float(radius), speed=float(speed))
 
 
+def drip_torch(ax, ay, vx, vy, t_start, t_end, radius, speed):
+    """A drip torch leaving (ax, ay) at t_start with velocity (vx, vy) m/s
+    until t_end, its fire growing at `speed` to `radius` around the line it
+    has laid."""
+    return dict(ax=float(ax), ay=float(ay), bx=float(ax), by=float(ay), t_start=float(t_start),
+                radius=float(radius), speed=float(speed), vx=float(vx), vy=float(vy),
+                t_end=float(t_end))
+
+
 # ---------------------------------------------------------------------------
 # the workloads
 # ---------------------------------------------------------------------------
