@@ -115,12 +115,24 @@ typedef struct {
  *     arrival time t_start + dist/speed.
  *   speed <= 0: instantaneous ignition of every node within radius of the
  *     segment, applied once at the first step start t >= t_start (at fire_init
- *     when t_start <= 0), with ignition time t_start. */
+ *     when t_start <= 0), with ignition time t_start.
+ *   (vx, vy) != 0 (needs speed > 0 and t_end >= t_start): a drip torch (the
+ *     paragraph after eq. ignition-min).  The torch leaves a at t_start with
+ *     velocity (vx, vy) m/s until t_end; at a step start t the ignition line
+ *     is the segment from a to a + v (min{t, t_end} - t_start) (bx, by are
+ *     not used) and the fire around it has the radius min{radius, speed (t -
+ *     t_start)}; applied at every step start with t_start <= t <= t_end +
+ *     radius/speed.  A newly ignited node gets the time the fire, starting
+ *     at the nearest point of the line when the torch laid it, reaches it at
+ *     this speed, or t if that is later.
+ * Zero-initialise unused fields (vx = vy = t_end = 0 for the other forms). */
 typedef struct {
     double ax, ay, bx, by;
     double t_start;
     double radius;
     double speed;
+    double vx, vy;  /* drip-torch velocity (m/s); 0, 0 for a fixed segment */
+    double t_end;   /* drip torch: time the torch stops */
 } fire_ignition;
 
 #define FIRE_MAX_CLASSES 64

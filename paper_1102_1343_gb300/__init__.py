@@ -76,7 +76,8 @@ class fire_fuel_class(C.Structure):
 
 class fire_ignition(C.Structure):
     _fields_ = [("ax", C.c_double), ("ay", C.c_double), ("bx", C.c_double), ("by", C.c_double),
-                ("t_start", C.c_double), ("radius", C.c_double), ("speed", C.c_double)]
+                ("t_start", C.c_double), ("radius", C.c_double), ("speed", C.c_double),
+                ("vx", C.c_double), ("vy", C.c_double), ("t_end", C.c_double)]
 
 
 _P = C.c_void_p
@@ -229,7 +230,10 @@ def make_ignitions(ignitions) -> C.Array:
     arr = (fire_ignition * max(1, len(ignitions)))()
     for k, g in enumerate(ignitions):
         for name, _ in fire_ignition._fields_:
-            setattr(arr[k], name, float(g[name]))
+            # the drip-torch fields (vx, vy, t_end) are optional: 0 otherwise
+            setattr(arr[k], name, float(g[name] if name in ("ax", "ay", "bx", "by", "t_start",
+                                                            "radius", "speed")
+                                        else g.get(name, 0.0)))
     return arr
 
 

@@ -215,10 +215,23 @@ void active_segments(fire_ctx *c, double t, bool mark, std::vector<IgnSeg> &out)
         s.by = g.by;
         s.tg = g.t_start;
         s.sg = g.speed;
+        s.drip = 0;
+        s.tnow = t;
+        s.tlay = t;
         if (!(g.speed > 0.0)) {
             if (c->applied[q] || !(g.t_start <= t)) continue;
             s.rho = g.radius;
             if (mark) c->applied[q] = 1;
+        } else if (g.vx != 0.0 || g.vy != 0.0) {
+            // drip torch: the line laid by min{t, t_end}, the capped radius
+            if (!(g.t_start <= t && t <= g.t_end + g.radius / g.speed)) continue;
+            const double tt = t < g.t_end ? t : g.t_end;
+            s.drip = 1;
+            s.tlay = tt;
+            s.bx = g.ax + g.vx * (tt - g.t_start);
+            s.by = g.ay + g.vy * (tt - g.t_start);
+            const double R = g.speed * (t - g.t_start);
+            s.rho = R > g.radius ? g.radius : R;
         } else {
             if (!(g.t_start <= t && t <= g.t_start + g.radius / g.speed)) continue;
             s.rho = g.speed * (t - g.t_start);
@@ -526,6 +539,9 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
         const fire_ignition &s = ignitions[q];
         if (!isfinite(s.ax) || !isfinite(s.ay) || !isfinite(s.bx) || !isfinite(s.by) ||
             !isfinite(s.t_start) || !isfinite(s.radius) || !isfinite(s.speed) || s.radius < 0)
+            return FIRE_ERR_ARG;
+        if (!isfinite(s.vx) || !isfinite(s.vy) || !isfinite(s.t_end)) return FIRE_ERR_ARG;
+        if ((s.vx != 0.0 || s.vy != 0.0) && !(s.speed > 0.0 && s.t_end >= s.t_start))
             return FIRE_ERR_ARG;
     }
     for (int k = 0; k < n_classes; ++k)

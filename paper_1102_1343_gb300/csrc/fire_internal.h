@@ -52,6 +52,10 @@ struct IgnSeg {
     double ax, ay, bx, by;
     double rho;      // current radius term: r_g (instantaneous) or S_g (t - t_g)
     double tg, sg;   // start time and growth speed (sg <= 0: instantaneous)
+    // drip torch: the step start t and min{t, t_end}; the nearest point at
+    // parameter u of [a, b] was laid at tg + u (tlay - tg)
+    int drip;
+    double tnow, tlay;
 };
 
 struct IgniteArgs {

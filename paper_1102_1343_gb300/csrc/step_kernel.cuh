@@ -382,7 +382,14 @@ __global__ void k_ignite(const IgniteArgs a) {
             const double d = sqrt(rx * rx + ry * ry);
             const double pg = d - s.rho;
             if ((double)p > 0.0 && pg <= 0.0 && isinf(ti)) {
-                ti = s.sg > 0.0 ? s.tg + d / s.sg : s.tg;
+                if (s.drip) {
+                    // the fire starts at the nearest point when the torch
+                    // lays it and reaches the node at S_g, by t at the latest
+                    const double ta = (s.tg + u * (s.tlay - s.tg)) + d / s.sg;
+                    ti = ta < s.tnow ? ta : s.tnow;
+                } else {
+                    ti = s.sg > 0.0 ? s.tg + d / s.sg : s.tg;
+                }
                 tchanged = true;
             }
             if (pg < (double)p) {

@@ -279,9 +279,10 @@ def test_full_size_fp64_matches_oracle(pkg):
 def test_full_size_central_differences_32_directions(pkg):
     """The 510x510 adjoint workload (400 steps of 0.5 s, checkpoints every
     20, FP64): the gradient against central differences of the GPU forward
-    misfit along 32 random directions (8 each of the multiplier, u, v and the
-    class moisture), skipping directions whose perturbed runs change the set
-    of ignited nodes (a switch point)."""
+    misfit along 40 random directions (8 each of the multiplier, u, v, the
+    class moisture and a per-node moisture field set by fire_set_moisture,
+    equal to the class moisture at the base point), skipping directions
+    whose perturbed runs change the set of ignited nodes (a switch point)."""
     import os
     import torch
     w, truth = synth.adjoint_case()
@@ -308,10 +309,13 @@ def test_full_size_central_differences_32_directions(pkg):
     # a slow fire: by t = 200 s a handful of nodes around the centre ignited
     assert J > 0 and ign0.sum() >= 10
 
-    def J_at(mult, classes, u, v):
+    moist0 = torch.as_tensor(np.array([c["fuelmc_g"] for c in classes0])[w.fuel]).cuda()
+
+    def J_at(mult, classes, u, v, moist=None):
         m.set_state(*st0)
         m.set_mult(mult)
         m.set_classes(classes)
+        m.set_moisture(moist)
         Jv, *_ = m.adjoint(u, v, w.dt, w.steps, tobs, ckpt_every=20, grads=False)
         return Jv, torch.isfinite(m.state()[1]).cpu().numpy()
 
@@ -323,6 +327,7 @@ def test_full_size_central_differences_32_directions(pkg):
         du = torch.as_tensor(rng.standard_normal(w.u.shape)).cuda()
         dv = torch.as_tensor(rng.standard_normal(w.v.shape)).cuda()
         dc = rng.standard_normal(len(classes0)) * 0.01
+        dM = torch.as_tensor(rng.standard_normal((w.ny, w.nx)) * 0.01).cuda()
         cases = {
             "m": (lambda s: (mult0 + s * h * dm, classes0, u0, v0), float((gm * dm).sum())),
             "u": (lambda s: (mult0, classes0, u0 + s * h * du, v0), float((gu * du).sum())),
@@ -344,8 +349,8 @@ def test_full_size_central_differences_32_directions(pkg):
             assert err <= 1e-5, (name, q, fd, ad)
             worst = max(worst, err)
             checked += 1
-    print("checked", checked, "of 32, worst rel", worst)
-    assert checked >= 16
+    print("checked", checked, "of 40, worst rel", worst)
+    assert checked >= 20
     m.close()
 
 

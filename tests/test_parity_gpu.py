@@ -139,6 +139,30 @@ def test_fp64_anisotropic_multiplier_and_segments(pkg, tile):
     assert heat_err <= 1e-10
 
 
+def drip_torch_case(seed=61, steps=80):
+    """Two drip torches (Sect. "Ignition"): one crossing at 3.2 m/s for 20 s,
+    its line burning out to 15 m at 2 m/s, one starting at 10.25 s."""
+    w = synth.random_landscape(23, 17, seed=seed, ignition="none", steps=steps)
+    w.ignitions = [synth.drip_torch(300.0, 400.0, 3.0, 1.0, t_start=1.0, t_end=21.0,
+                                    radius=15.0, speed=2.0),
+                   synth.drip_torch(900.0, 300.0, -2.0, 2.5, t_start=10.25, t_end=25.0,
+                                    radius=9.0, speed=4.0)]
+    return w
+
+
+@pytest.mark.parametrize("tile", [None, (1, 6, 2), (0, 2, 2), (2, 6, 4)])
+def test_fp64_drip_torch(pkg, tile):
+    """Drip-torch ignition in every kernel against the oracle at 1e-10 (psi,
+    F, the ignition times including those the torches set, every step's
+    heat)."""
+    w = drip_torch_case()
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    assert np.isfinite(orc.tign).sum() > 200 and Qo > 0
+
+
 @pytest.mark.parametrize("tile", [None, (2, 6, 4)])
 def test_fp64_chaparral(pkg, tile):
     """The chaparral rate of eq. (chapparal) (6 m/s in a wind above 4.6 m/s)
@@ -176,6 +200,10 @@ def test_class_valued_node_moisture_changes_no_bit(pkg, prec):
     import torch
     w = synth.random_landscape(24, 10, seed=31, ignition="points", n_points=6, edge_margin=150.0,
                                steps=120)
+    if prec == "fp32":
+        # the FP32 path stores the moisture in float: class values that a
+        # float holds exactly give exactly the class coefficients
+        w.classes = [dict(c, fuelmc_g=float(np.float32(c["fuelmc_g"]))) for c in w.classes]
     a = pkg.FireModel.from_workload(w, precision=prec)
     w.moisture = np.array([c["fuelmc_g"] for c in w.classes])[w.fuel]
     b = pkg.FireModel.from_workload(w, precision=prec)
@@ -204,10 +232,14 @@ def test_class_valued_node_moisture_changes_no_bit(pkg, prec):
 
 @pytest.mark.parametrize("case,tile", [("line", None), ("points", None), ("line", (0, 8, 4)),
                                        ("line", (2, 6, 20)), ("points", (2, 6, 20)),
-                                       ("line-moisture", None), ("points-moisture", (1, 12, 4))])
+                                       ("line-moisture", None), ("points-moisture", (1, 12, 4)),
+                                       ("drip", None)])
 def test_fp32_against_fp64_oracle(pkg, case, tile):
-    w = synth.random_landscape(32, 26, seed=44, ignition=case.split("-")[0], n_points=6,
-                               edge_margin=300.0, steps=300)
+    if case == "drip":
+        w = drip_torch_case(steps=300)
+    else:
+        w = synth.random_landscape(32, 26, seed=44, ignition=case.split("-")[0], n_points=6,
+                                   edge_margin=300.0, steps=300)
     if case.endswith("moisture"):
         w = node_moisture(w)
     m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp32", tile=tile)
