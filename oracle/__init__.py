@@ -112,6 +112,11 @@ def lib():
             L.orc_extend_vjp.argtypes = [C.c_int, C.c_int, _D, _D, _D]
             L.orc_step_vjp.restype = None
             L.orc_step_vjp.argtypes = ([C.POINTER(_Grid)] + [_D] * 7 + [C.c_double] + [_D] * 7)
+            L.orc_wind_at_height.restype = None
+            L.orc_wind_at_height.argtypes = [C.c_int, C.c_long, _D, _D, _D, C.c_double, _D]
+            L.orc_heat_insertion.restype = None
+            L.orc_heat_insertion.argtypes = ([C.c_int, C.c_long] + [_D] * 5
+                                             + [C.c_double] * 3 + [_D, _D])
             L.orc_set_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_set_threads(1)  # one thread unless asked (set_threads)
@@ -271,6 +276,31 @@ def cell_fuel_fraction(psi3, tign3, t: float, Tf: float) -> float:
     th = np.ascontiguousarray(np.where(p < 0.0, ti, t))
     p = np.ascontiguousarray(p)
     return lib().orc_cell_fuel_fraction(_dp(p), _dp(th), float(t), float(Tf))
+
+
+def wind_at_height(u3d, z3d, z0, zf):
+    """Vertical log-linear interpolation of a wind component to height zf
+    (Sect. "Coupling"): u3d, z3d [nz][...] (levels first), z0 [...];
+    returns [...]."""
+    u3d, z3d, z0 = _f64(u3d), _f64(z3d), _f64(z0)
+    nz = u3d.shape[0]
+    assert z3d.shape == u3d.shape and z0.shape == u3d.shape[1:]
+    out = np.zeros(u3d.shape[1:])
+    lib().orc_wind_at_height(nz, z0.size, _dp(u3d), _dp(z3d), _dp(z0), float(zf), _dp(out))
+    return out
+
+
+def heat_insertion(hs, hl, zw, rho, mu, zext, cp=1004.0, L=2.5e6, rth=None, rqv=None):
+    """Sources added to the tendencies of mu theta and mu q_m (Sect.
+    "Coupling", the heat insertion): hs, hl, mu [...], zw [nz+1][...], rho
+    [nz][...]; returns (rth, rqv) [nz][...] (added to the given arrays)."""
+    hs, hl, zw, rho, mu = map(_f64, (hs, hl, zw, rho, mu))
+    nz = rho.shape[0]
+    rth = np.zeros(rho.shape) if rth is None else _f64(rth).copy()
+    rqv = np.zeros(rho.shape) if rqv is None else _f64(rqv).copy()
+    lib().orc_heat_insertion(nz, hs.size, _dp(hs), _dp(hl), _dp(zw), _dp(rho), _dp(mu),
+                             float(zext), float(cp), float(L), _dp(rth), _dp(rqv))
+    return rth, rqv
 
 
 def default_psi_far(nx, ny, dx, dy) -> float:

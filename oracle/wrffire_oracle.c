@@ -1437,3 +1437,76 @@ double orc_adjoint(const orc_grid *g, const double *co, const double *dco, const
     free(gun); free(gvn); free(lam);
     return J;
 }
+
+/* ------------------------------------------------------------------ */
+/* Coupling with the atmosphere (Sect. "Coupling of the fire and the   */
+/* atmospheric models"): the wind at z_f and the heat insertion.       */
+/* ------------------------------------------------------------------ */
+
+/* Wind at height z_f above the terrain by vertical log-linear
+ * interpolation: at each of npts horizontal points, the piecewise linear
+ * interpolant in ln z of the values u(z_0) = 0, u(z_1), u(z_2), ... at
+ * ln z_0, ln z_1, ..., evaluated at ln z_f; 0 where z_f <= z_0.
+ * u3d, z3d: [nz][npts] (level k of point p at k*npts + p), the wind and the
+ * height above the terrain of the cell centres, increasing with k; z0:
+ * [npts] roughness heights; out: [npts].
+ * Readings: levels at or below z_0 are not used (the profile is 0 up to
+ * z_0); above the highest level the top value is kept (the paper only
+ * interpolates). */
+void orc_wind_at_height(int nz, long npts, const double *u3d, const double *z3d,
+                        const double *z0, double zf, double *out)
+{
+    for (long p = 0; p < npts; ++p) {
+        double r = z0[p];
+        if (!(zf > r)) { out[p] = 0.0; continue; }
+        /* points of the interpolant: (ln z_0, 0), then levels above z_0 */
+        double xl = log(r), ul = 0.0;   /* last point at or below ln z_f */
+        double x = log(zf);
+        double val = 0.0;
+        int done = 0;
+        for (int k = 0; k < nz; ++k) {
+            double zk = z3d[(long)k * npts + p];
+            if (!(zk > r)) continue;
+            double xk = log(zk), uk = u3d[(long)k * npts + p];
+            if (x <= xk) {
+                val = ul + (uk - ul) * (x - xl) / (xk - xl);
+                done = 1;
+                break;
+            }
+            xl = xk;
+            ul = uk;
+        }
+        out[p] = done ? val : ul;
+    }
+}
+
+/* Heat insertion into the atmospheric tendencies of the potential
+ * temperature and the vapour (the two equations after the fire step list):
+ *   d(mu theta)/dt += mu phi_h / (sigma rho) * S(z),
+ *   d(mu q_m)/dt   += mu phi_q / (L rho) * S(z),
+ * with S the vertical profile of the inserted flux, exp(-z/z_ext).
+ * Reading of the printed d/dz exp(-z/z_ext), whose sign would cool the air:
+ * the source is the convergence of the upward flux phi exp(-z/z_ext), and
+ * in a model layer between the face heights zw_k < zw_{k+1} it is the
+ * layer average of that convergence,
+ *   S_k = (exp(-zw_k/z_ext) - exp(-zw_{k+1}/z_ext)) / (zw_{k+1} - zw_k),
+ * so that the column integral of sigma rho S_k dz_k times the heating is
+ * phi_h (1 - exp(-zw_top/z_ext)).
+ * hs, hl: [n] (n = nx*ny columns) sensible and latent flux densities
+ * (W m^-2); zw: [nz+1][n] face heights above the terrain (zw_0 = 0);
+ * rho: [nz][n] density (kg m^-3); mu: [n] (Pa); cp = sigma (J kg^-1 K^-1),
+ * L (J kg^-1); rth, rqv: [nz][n], the sources are added to them. */
+void orc_heat_insertion(int nz, long n, const double *hs, const double *hl,
+                        const double *zw, const double *rho, const double *mu,
+                        double zext, double cp, double L, double *rth, double *rqv)
+{
+    for (int k = 0; k < nz; ++k) {
+        for (long p = 0; p < n; ++p) {
+            double za = zw[(long)k * n + p], zb = zw[(long)(k + 1) * n + p];
+            double S = (exp(-za / zext) - exp(-zb / zext)) / (zb - za);
+            double r = rho[(long)k * n + p];
+            rth[(long)k * n + p] += mu[p] * hs[p] / (cp * r) * S;
+            rqv[(long)k * n + p] += mu[p] * hl[p] / (L * r) * S;
+        }
+    }
+}

@@ -263,6 +263,38 @@ def random_landscape(nxa, nya, sr=10, dx_atm=60.0, seed=BASE_SEED, steps=1200, d
                     classes, fuel, dzdx, dzdy, u, v, ign, dt, steps)
 
 
+def atmos_columns(rng, shape, nz=20, top=3000.0, stretch=1.6, z0_range=(0.02, 0.5),
+                  ustar_range=(0.2, 0.6), noise=0.3):
+    """Synthetic atmospheric columns at the points of `shape` (the u- or
+    v-points of the staggered grid, or the mass points): face heights above
+    the terrain zw [nz+1][...] (0 at the surface, stretched toward the top,
+    varied by a few per cent from column to column), cell-centre heights z
+    [nz][...], roughness heights z0 [...] and a wind component [nz][...]
+    following a logarithmic profile u*/0.4 ln(z/z0) (u* per point, either
+    sign) plus noise.  Stand-ins for WRF's geopotential heights and winds,
+    which are not available here."""
+    shape = tuple(shape)
+    k = np.arange(nz + 1, dtype=np.float64).reshape((nz + 1,) + (1,) * len(shape))
+    base = top * (k / nz) ** stretch
+    wobble = 1.0 + 0.03 * rng.standard_normal(shape)
+    zw = base * wobble
+    z = 0.5 * (zw[1:] + zw[:-1])
+    z0 = rng.uniform(*z0_range, size=shape)
+    ustar = rng.uniform(*ustar_range, size=shape) * rng.choice([-1.0, 1.0], size=shape)
+    u = ustar / 0.4 * np.log(np.maximum(z, 1e-3) / z0) + noise * rng.standard_normal(z.shape)
+    return zw, z, z0, u
+
+
+def air_columns(rng, shape, zw):
+    """Density [nz][...] (kg m^-3, exponential with an 8 km scale height) at
+    the cell centres of face heights zw, and the dry-air column mass mu [...]
+    (Pa) for the heat insertion."""
+    z = 0.5 * (zw[1:] + zw[:-1])
+    rho = 1.2 * np.exp(-z / 8000.0) * (1.0 + 0.01 * rng.standard_normal(z.shape))
+    mu = 9.0e4 * (1.0 + 0.02 * rng.standard_normal(tuple(shape)))
+    return rho, mu
+
+
 def line_fire_2000(seed=BASE_SEED) -> Workload:
     """FP32-vs-FP64 forward case: 200x200 atmos -> 2000x2000 fire mesh, 1 km
     line ignition, 1200 steps of 0.5 s."""
