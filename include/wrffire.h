@@ -455,6 +455,55 @@ int fire_ensemble_set_barrier_test(fire_ensemble *ens, int skip_block, long long
 
 void fire_ensemble_destroy(fire_ensemble *ens);
 
+/* ---------------------------------------------------------------------
+ * Coupling with the atmospheric model (Sect. "Coupling of the fire and the
+ * atmospheric models"): the steps before and after the fire step.
+ * --------------------------------------------------------------------- */
+
+/* The wind at the height z_f above the terrain (6.1 m in the paper, after
+ * BEHAVE) by vertical log-linear interpolation: at each of npts horizontal
+ * points (e.g. the u-points [ny_atm][nx_atm+1] or the v-points
+ * [ny_atm+1][nx_atm] of the staggered grid) the piecewise linear interpolant
+ * in ln z of the values u(z0) = 0, u(z_1), u(z_2), ... at ln z0, ln z_1, ...,
+ * evaluated at ln z_f; 0 where z_f <= z0.  Levels at or below z0 are not
+ * used; above the highest level the top value is returned.
+ *   precision        FIRE_FP32 or FIRE_FP64: the element type of all arrays
+ *   u3d_dev, z3d_dev [nz][npts] device: the wind component and the height
+ *                    above the terrain of the cell centres, level k of point
+ *                    p at k*npts + p, heights increasing with k
+ *   z0_dev           [npts] device roughness heights (m)
+ *   out_dev          [npts] device: the wind at z_f (the input of fire_step)
+ * Enqueued on cuda_stream; FIRE_ERR_ARG for bad sizes or null arrays. */
+int fire_wind_at_height(int precision, int nz, long long npts, const void *u3d_dev,
+                        const void *z3d_dev, const void *z0_dev, double z_f, void *out_dev,
+                        void *cuda_stream);
+
+/* Insertion of the fire's heat fluxes into the atmospheric tendencies, as
+ * forcing in a layer above the surface with exponential decay in height:
+ *   d(mu theta)/dt += mu phi_h / (cp rho) S_k,  d(mu q_m)/dt += mu phi_q / (L rho) S_k
+ * in the model layer k between the face heights zw_k < zw_{k+1}, where S_k
+ * is the layer average of the convergence of the flux phi exp(-z/z_ext),
+ *   S_k = (exp(-zw_k/z_ext) - exp(-zw_{k+1}/z_ext)) / (zw_{k+1} - zw_k)
+ * (reading: the paper's d/dz exp(-z/z_ext) with the sign of a heating; the
+ * column integral of cp rho S_k dz is phi (1 - exp(-zw_top/z_ext))).
+ *   ncols                 horizontal columns (the atmospheric cells, ny_atm*nx_atm)
+ *   heat_sens_dev, heat_lat_dev [ncols] device double: phi_h, phi_q (W m^-2),
+ *                         e.g. fire_step's outputs
+ *   zw_dev                [nz+1][ncols] device double: face heights above the
+ *                         terrain (m), zw_0 = 0, increasing
+ *   rho_dev               [nz][ncols] device double: air density (kg m^-3)
+ *   mu_dev                [ncols] device double: dry-air column mass mu (Pa)
+ *   z_ext                 heat extinction depth (m, fire_ext_grnd), > 0
+ *   cp, latent            specific heat of air (J kg^-1 K^-1) and L (J kg^-1)
+ *   rth_dev, rqv_dev      [nz][ncols] device double: the sources are ADDED to
+ *                         these tendencies; either may be NULL (skipped, and
+ *                         then its flux array may be NULL too)
+ * Enqueued on cuda_stream. */
+int fire_heat_insertion(int nz, long long ncols, const double *heat_sens_dev,
+                        const double *heat_lat_dev, const double *zw_dev, const double *rho_dev,
+                        const double *mu_dev, double z_ext, double cp, double latent,
+                        double *rth_dev, double *rqv_dev, void *cuda_stream);
+
 const char *fire_strerror(int code);
 
 /* Name and message of the last CUDA error an entry point saw on the calling

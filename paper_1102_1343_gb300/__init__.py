@@ -48,7 +48,8 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_get_kernel", "fire_ensemble_set_barrier_test",
                "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
                "fire_adjoint", "fire_autotune", "fire_ensemble_autotune",
-               "fire_default_kernel", "fire_adjoint_heat", "fire_set_moisture")
+               "fire_default_kernel", "fire_adjoint_heat", "fire_set_moisture",
+               "fire_wind_at_height", "fire_heat_insertion")
 
 
 class FireError(RuntimeError):
@@ -146,6 +147,12 @@ def load_library(path: str | None = None):
     L.fire_set_fuel_classes.restype = C.c_int
     L.fire_set_moisture.argtypes = [_P, _P]
     L.fire_set_moisture.restype = C.c_int
+    L.fire_wind_at_height.argtypes = [C.c_int, C.c_int, C.c_longlong, _P, _P, _P, C.c_double,
+                                      _P, _P]
+    L.fire_wind_at_height.restype = C.c_int
+    L.fire_heat_insertion.argtypes = ([C.c_int, C.c_longlong] + [_P] * 5
+                                      + [C.c_double] * 3 + [_P, _P, _P])
+    L.fire_heat_insertion.restype = C.c_int
     L.fire_adjoint.argtypes = [_P, C.c_int, C.c_double, _P, _P, _P, C.c_int,
                                C.POINTER(C.c_double), _P, _P, _P, _P]
     L.fire_adjoint.restype = C.c_int
@@ -487,6 +494,48 @@ def fire_set_spread_mult(ctx, mult_dev) -> int:
 
 def fire_set_moisture(ctx, moisture_dev) -> int:
     return _check(load_library().fire_set_moisture(ctx, _ptr(moisture_dev)), "fire_set_moisture")
+
+
+def fire_wind_at_height(u3d, z3d, z0, z_f, out=None, cuda_stream=None):
+    """The wind component at height z_f by vertical log-linear interpolation
+    (fire_wind_at_height): u3d, z3d [nz][...] and z0 [...] CUDA tensors of one
+    precision (float32 or float64); returns `out` (allocated like z0 if None)."""
+    import torch
+    nz = u3d.shape[0]
+    if z3d.shape != u3d.shape or z0.shape != u3d.shape[1:]:
+        raise FireError(FIRE_ERR_ARG, "fire_wind_at_height: shapes")
+    if out is None:
+        out = torch.empty_like(z0)
+    for x in (u3d, z3d, z0, out):
+        if not (x.is_cuda and x.is_contiguous() and x.dtype == z0.dtype):
+            raise FireError(FIRE_ERR_ARG, "fire_wind_at_height: tensors must be contiguous "
+                                          "CUDA tensors of one dtype")
+    prec = FIRE_FP64 if z0.dtype == torch.float64 else FIRE_FP32
+    _check(load_library().fire_wind_at_height(prec, nz, z0.numel(), _ptr(u3d), _ptr(z3d),
+                                              _ptr(z0), float(z_f), _ptr(out),
+                                              _ptr(cuda_stream) or None), "fire_wind_at_height")
+    return out
+
+
+def fire_heat_insertion(heat_sens, heat_lat, zw, rho, mu, z_ext, rth, rqv, cp=1004.0,
+                        latent=2.5e6, cuda_stream=None) -> int:
+    """Add the fire's heat sources to the tendencies rth, rqv [nz][...]
+    (fire_heat_insertion); all float64 CUDA tensors, zw [nz+1][...], rho
+    [nz][...], the fluxes and mu [...]; rth or rqv may be None."""
+    nz = rho.shape[0]
+    ncols = mu.numel()
+    for name, x, n in (("heat_sens", heat_sens, ncols), ("heat_lat", heat_lat, ncols),
+                       ("zw", zw, (nz + 1) * ncols), ("rho", rho, nz * ncols), ("mu", mu, ncols),
+                       ("rth", rth, nz * ncols), ("rqv", rqv, nz * ncols)):
+        if x is None:
+            continue
+        import torch
+        if not (x.is_cuda and x.is_contiguous() and x.dtype == torch.float64 and x.numel() == n):
+            raise FireError(FIRE_ERR_ARG, f"fire_heat_insertion: {name}")
+    return _check(load_library().fire_heat_insertion(
+        nz, ncols, _ptr(heat_sens), _ptr(heat_lat), _ptr(zw), _ptr(rho), _ptr(mu), float(z_ext),
+        float(cp), float(latent), _ptr(rth), _ptr(rqv), _ptr(cuda_stream) or None),
+        "fire_heat_insertion")
 
 
 def fire_set_fuel_classes(ctx, classes) -> int:

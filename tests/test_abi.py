@@ -127,3 +127,16 @@ def test_noalloc_binding_refuses_host_tensors(lib):
         pkg.fire_step_noalloc(g, [synth.nominal_class()], psi, 2, 3, 4, 5, 6, None, 7, 8, 9, 10,
                               0.0, 0.5)
     assert e.value.code == pkg.FIRE_ERR_ARG and "psi_in" in str(e.value)
+
+
+def test_coupling_entry_points_check_arguments_without_gpu(lib):
+    import paper_1102_1343_gb300 as pkg
+    E = pkg.FIRE_ERR_ARG
+    assert lib.fire_wind_at_height(pkg.FIRE_FP64, 0, 10, 1, 1, 1, 6.1, 1, None) == E
+    assert lib.fire_wind_at_height(7, 5, 10, 1, 1, 1, 6.1, 1, None) == E
+    assert lib.fire_wind_at_height(pkg.FIRE_FP32, 5, 10, None, 1, 1, 6.1, 1, None) == E
+    assert lib.fire_heat_insertion(10, 100, 1, 1, 1, 1, 1, 0.0, 1004.0, 2.5e6, 1, 1, None) == E
+    assert lib.fire_heat_insertion(10, 100, None, 1, 1, 1, 1, 50.0, 1004.0, 2.5e6, 1, 1,
+                                   None) == E
+    assert lib.fire_heat_insertion(10, 100, 1, 1, 1, 1, 1, 50.0, 1004.0, 2.5e6, None, None,
+                                   None) == E
