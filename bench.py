@@ -50,8 +50,11 @@ KERNEL_SOURCES = ["paper_1102_1343_gb300/csrc/march_kernel.cuh",
                   "paper_1102_1343_gb300/csrc/warp_kernel.cuh",
                   "paper_1102_1343_gb300/csrc/fire_device.cuh",
                   "paper_1102_1343_gb300/csrc/fire_internal.h",
-                  "paper_1102_1343_gb300/csrc/step_f32.cu"]
+                  "paper_1102_1343_gb300/csrc/step_f32.cu",
+                  "paper_1102_1343_gb300/csrc/warp4_kernel.cuh",
+                  "paper_1102_1343_gb300/csrc/step_warp4.cu"]
 PROFILE_SUMMARY = "profiles/fire_warp_f32_points8200.md"
+KERNEL_NAMES = ["k_fire_step", "k_fire_march", "k_fire_warp", "k_fire_warp4"]
 
 
 def kernel_hash() -> str:
@@ -463,7 +466,7 @@ def run_gpu(args, rank, world):
                        "refinement": [w.srx, w.sry], "precision": prec,
                        "state_in_hbm": "yes; state 2.2 GB > L2, no flush needed"
                        if args.workload == "points8200" else "yes",
-                       "kernel": {"variant": ["tile", "march", "warp"][kernel[0]],
+                       "kernel": {"variant": ["tile", "march", "warp", "warp4"][kernel[0]],
                                   "tile_atmos_cells": list(kernel[1:]),
                                   "chosen_by": "--kernel" if args.kernel else
                                   ("fire_autotune" if args.autotune else "fire_init default")},
@@ -473,8 +476,7 @@ def run_gpu(args, rank, world):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": ["k_fire_step", "k_fire_march", "k_fire_warp"][kernel[0]]
-                         + ("<float>" if prec == "fp32" else "<double>"),
+                         "kernel": KERNEL_NAMES[kernel[0]] + ("<float>" if prec == "fp32" else "<double>"),
                          "kernel_ms": k_avg,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_kind} hbm_gbs"},
@@ -560,7 +562,7 @@ def bench_burning(pkg, dev, steps):
     return {"workload": f"{w.name} (820x820 atmos x10, 50 ignitions of radius 3 km)",
             "burnt_fraction_at_start": burnt, "value": cells * steps / (ms / 1e3), "unit": UNIT,
             "steps": steps, "ms_per_step": ms / steps, "kernel_ms": k_avg,
-            "kernel": ["k_fire_step", "k_fire_march", "k_fire_warp"][kernel[0]] + "<float>",
+            "kernel": KERNEL_NAMES[kernel[0]] + "<float>",
             "tile_atmos_cells": list(kernel[1:]),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"},
@@ -624,7 +626,7 @@ def bench_adjoint(pkg, dev, ckpt=20):
         ms = e0.elapsed_time(e1)
         grads[prec] = (J, gm, gM, gu, gv)
         rec = {"value": n / (ms / 1e3), "ms": ms, "J": J,
-               "kernel": {"variant": ["tile", "march", "warp"][kern[0]],
+               "kernel": {"variant": ["tile", "march", "warp", "warp4"][kern[0]],
                           "tile_atmos_cells": list(kern[1:])}}
         # the heat-misfit adjoint on the same run (warm-up, then timed)
         m.set_state(*st0)

@@ -298,9 +298,17 @@ double fire_time(const fire_ctx *ctx);
  *                      a 3-node halo in shared memory (any refinement);
  *   FIRE_KERNEL_WARP   each warp marches alone down a strip of kx*sr_x
  *                      columns (an even number <= 60) and ky*sr_y rows, rows
- *                      held in registers, neighbours exchanged by shuffles.
+ *                      held in registers, neighbours exchanged by shuffles;
+ *   FIRE_KERNEL_WARP4  (FIRE_FP32 only) the same with four columns per lane:
+ *                      strips of kx*sr_x <= 120 columns, the per-row control
+ *                      shared by four columns.
  * FIRE_ERR_ARG if the shape does not fit the variant or the device. */
-enum fire_kernel_variant { FIRE_KERNEL_TILE = 0, FIRE_KERNEL_MARCH = 1, FIRE_KERNEL_WARP = 2 };
+enum fire_kernel_variant {
+    FIRE_KERNEL_TILE = 0,
+    FIRE_KERNEL_MARCH = 1,
+    FIRE_KERNEL_WARP = 2,
+    FIRE_KERNEL_WARP4 = 3
+};
 int fire_set_kernel(fire_ctx *ctx, int variant, int kx, int ky);
 int fire_get_kernel(const fire_ctx *ctx, int *variant, int *kx, int *ky);
 

@@ -34,6 +34,7 @@ FIRE_ERR_STATE = -7
 FIRE_KERNEL_TILE = 0
 FIRE_KERNEL_MARCH = 1
 FIRE_KERNEL_WARP = 2
+FIRE_KERNEL_WARP4 = 3
 FIRE_MAX_CLASSES = 64
 FIRE_MAX_IGNITIONS = 256
 

@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwrffire_gb300.so")
 SOURCES = ["step_f32.cu", "step_f64.cu", "coeffs.cu", "context.cu", "noalloc.cu",
-           "ensemble.cu", "adjoint.cu", "coupling.cu"]
-HEADERS = ["step_kernel.cuh", "march_kernel.cuh", "warp_kernel.cuh", "pair_math.cuh", "fire_device.cuh", "fire_internal.h"]
+           "ensemble.cu", "adjoint.cu", "coupling.cu", "step_warp4.cu"]
+HEADERS = ["step_kernel.cuh", "march_kernel.cuh", "warp_kernel.cuh", "warp4_kernel.cuh", "pair_math.cuh", "fire_device.cuh", "fire_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]

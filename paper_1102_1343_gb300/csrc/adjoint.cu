@@ -1000,9 +1000,11 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
             ra.t_in = tseg + j;
             ra.t_out = tseg + K + 1;
             ra.dt = dt;
-            cudaError_t e = variant == FIRE_KERNEL_MARCH  ? launch_march<T>(ra, cs)
-                            : variant == FIRE_KERNEL_WARP ? launch_warp<T>(ra, cs)
-                                                          : launch_step<T>(ra, cs);
+            cudaError_t e = variant == FIRE_KERNEL_MARCH   ? launch_march<T>(ra, cs)
+                            : variant == FIRE_KERNEL_WARP  ? launch_warp<T>(ra, cs)
+                            : variant == FIRE_KERNEL_WARP4 ? (sizeof(T) == 4 ? launch_warp4(ra, cs)
+                                                                             : cudaErrorInvalidValue)
+                                                           : launch_step<T>(ra, cs);
             if (e != cudaSuccess) return e;
         }
         AdjArgs<T> b = a;

@@ -199,6 +199,8 @@ cudaError_t launch_variant(const fire_ctx *c, const StepArgs &a, cudaStream_t s)
         return c->prec == FIRE_FP64 ? launch_march<double>(a, s) : launch_march<float>(a, s);
     if (c->variant == FIRE_KERNEL_WARP)
         return c->prec == FIRE_FP64 ? launch_warp<double>(a, s) : launch_warp<float>(a, s);
+    if (c->variant == FIRE_KERNEL_WARP4)
+        return c->prec == FIRE_FP32 ? launch_warp4(a, s) : cudaErrorInvalidValue;
     return c->prec == FIRE_FP64 ? launch_step<double>(a, s) : launch_step<float>(a, s);
 }
 
@@ -208,7 +210,7 @@ void active_segments(fire_ctx *c, double t, bool mark, std::vector<IgnSeg> &out)
     out.clear();
     for (size_t q = 0; q < c->ign.size(); ++q) {
         const fire_ignition &g = c->ign[q];
-        IgnSeg s;
+        IgnSeg s{};
         s.ax = g.ax;
         s.ay = g.ay;
         s.bx = g.bx;
@@ -283,6 +285,13 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
     } else if (variant == FIRE_KERNEL_WARP) {
         const long long W = (long long)kx * c->g.sr_x, L = (long long)ky * c->g.sr_y;
         if (W > kWarpMaxColumns || (W & 1) || L > kWarpMaxRows || (long long)c->n > kWarpMaxNodes)
+            return FIRE_ERR_ARG;
+        sm = 0;
+        e = cudaSuccess;
+    } else if (variant == FIRE_KERNEL_WARP4) {
+        const long long W = (long long)kx * c->g.sr_x, L = (long long)ky * c->g.sr_y;
+        if (c->prec != FIRE_FP32 || W > kWarp4MaxColumns || L > kWarpMaxRows ||
+            (long long)c->n > kWarpMaxNodes)
             return FIRE_ERR_ARG;
         sm = 0;
         e = cudaSuccess;
@@ -621,7 +630,7 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
         for (size_t q = 0; q < c->ign.size(); ++q) {
             const fire_ignition &gq = c->ign[q];
             if (!(gq.speed > 0.0) && gq.t_start <= 0.0) {
-                IgnSeg sg;
+                IgnSeg sg{};
                 sg.ax = gq.ax;
                 sg.ay = gq.ay;
                 sg.bx = gq.bx;

@@ -97,6 +97,10 @@ constexpr int kMarchMaxColumns = 248;  // output columns of one marching strip (
 template <typename T>
 cudaError_t launch_warp(const StepArgs &a, cudaStream_t s);
 
+// four columns per lane (FP32 only): strips of <= 120 output columns
+constexpr int kWarp4MaxColumns = 120;
+cudaError_t launch_warp4(const StepArgs &a, cudaStream_t s);
+
 constexpr int kWarpStrips = 4;       // warps (strips) per CTA of the warp kernel
 constexpr int kWarpMaxColumns = 60;  // output columns of one warp strip (even)
 constexpr int kWarpMaxRows = 512;    // output rows of one warp strip

@@ -233,7 +233,9 @@ def test_class_valued_node_moisture_changes_no_bit(pkg, prec):
 @pytest.mark.parametrize("case,tile", [("line", None), ("points", None), ("line", (0, 8, 4)),
                                        ("line", (2, 6, 20)), ("points", (2, 6, 20)),
                                        ("line-moisture", None), ("points-moisture", (1, 12, 4)),
-                                       ("drip", None)])
+                                       ("drip", None), ("line", (3, 12, 8)),
+                                       ("points", (3, 12, 20)), ("points-moisture", (3, 6, 4)),
+                                       ("drip", (3, 12, 5))])
 def test_fp32_against_fp64_oracle(pkg, case, tile):
     if case == "drip":
         w = drip_torch_case(steps=300)
@@ -423,6 +425,48 @@ def test_full_size_sampled_cells(pkg, name, prec, warm, tile):
             assert abs(hs[J, I] - hs_o) <= 1e-4 * Hs_max / w.dt
             assert abs(hl[J, I] - hl_o) <= 1e-4 * Hq_max / w.dt
     assert burning_cells >= 4
+
+
+@pytest.mark.parametrize("mesh", [(32, 26, 10), (23, 17, 10), (23, 17, 5), (13, 40, 10)])
+def test_warp4_equals_two_column_warp_kernel(pkg, mesh):
+    """The four-column warp kernel computes every node with the same
+    operations as the two-column one: the same bits for psi, t_i, F and both
+    heat grids (meshes whose width is a multiple of 4 (float4 rows), even
+    (float2 pairs) and odd (scalars); strips of 12 and of 6 atmospheric
+    cells), with multipliers and a per-node moisture on one mesh."""
+    import torch
+    nxa, nya, sr = mesh
+    w = synth.random_landscape(nxa, nya, sr=sr, seed=46, ignition="points", n_points=5,
+                               edge_margin=150.0, steps=150)
+    if nxa == 13:
+        w = node_moisture(w)
+        w.mult = np.random.default_rng(5).uniform(0.7, 1.3, (w.ny, w.nx))
+    a = pkg.FireModel.from_workload(w, precision="fp32")
+    b = pkg.FireModel.from_workload(w, precision="fp32")
+    c = pkg.FireModel.from_workload(w, precision="fp32")
+    ky = max(1, 30 // sr)
+    pkg.fire_set_kernel(a.ctx, pkg.FIRE_KERNEL_WARP, 60 // sr, ky)
+    pkg.fire_set_kernel(b.ctx, pkg.FIRE_KERNEL_WARP4, 120 // sr, ky)
+    pkg.fire_set_kernel(c.ctx, pkg.FIRE_KERNEL_WARP4, 60 // sr, 2 * ky)
+    u, v = a.wind(w.u, w.v)
+    for _ in range(w.steps):
+        ha = a.step(u, v, w.dt)
+        hb = b.step(u, v, w.dt)
+        hc = c.step(u, v, w.dt)
+    torch.cuda.synchronize()
+    sa, sb, sc = state_np(a), state_np(b), state_np(c)
+    assert np.isfinite(sa[1]).sum() > 50
+    for k in range(3):
+        assert np.array_equal(sa[k], sb[k]) and np.array_equal(sa[k], sc[k]), k
+    for x, y in ((ha, hb), (ha, hc)):
+        assert np.array_equal(x[0].cpu().numpy(), y[0].cpu().numpy())
+        assert np.array_equal(x[1].cpu().numpy(), y[1].cpu().numpy())
+    assert a.status() == b.status() == c.status() == pkg.FIRE_OK
+    m64 = pkg.FireModel.from_workload(w, precision="fp64")
+    with pytest.raises(pkg.FireError):
+        pkg.fire_set_kernel(m64.ctx, pkg.FIRE_KERNEL_WARP4, 120 // sr, ky)
+    for x in (a, b, c, m64):
+        x.close()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
