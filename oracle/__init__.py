@@ -56,7 +56,7 @@ def build(force: bool = False) -> str:
 class _Grid(C.Structure):
     _fields_ = [("nxa", C.c_int), ("nya", C.c_int), ("srx", C.c_int), ("sry", C.c_int),
                 ("dx_atm", C.c_double), ("dy_atm", C.c_double), ("eps", C.c_double),
-                ("band", C.c_int)]
+                ("band", C.c_int), ("scheme", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -89,6 +89,8 @@ def lib():
                                   _D, _D, _D, _D, _D, _D, _D, _D]
             L.orc_cell_fuel_fraction.restype = C.c_double
             L.orc_cell_fuel_fraction.argtypes = [_D, _D, C.c_double, C.c_double]
+            L.orc_cell_fuel_fraction_linear.restype = C.c_double
+            L.orc_cell_fuel_fraction_linear.argtypes = [_D, _D, C.c_double, C.c_double]
             L.orc_ignite.restype = None
             L.orc_ignite.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _D, C.c_int,
                                      _U8, C.c_double, _D, _D]
@@ -303,6 +305,17 @@ def heat_insertion(hs, hl, zw, rho, mu, zext, cp=1004.0, L=2.5e6, rth=None, rqv=
     return rth, rqv
 
 
+def cell_fuel_fraction_linear(psi3, tign3, t: float, Tf: float) -> float:
+    """Fuel fraction of the cell at the centre of a 3x3 node neighbourhood by
+    the scheme exact for linear psi and t_i (tign3: node ignition times;
+    eq. (ti-comp) applied here as in cell_fuel_fraction)."""
+    p = _f64(psi3).reshape(3, 3)
+    ti = _f64(tign3).reshape(3, 3)
+    th = np.ascontiguousarray(np.where(p < 0.0, ti, t))
+    p = np.ascontiguousarray(p)
+    return lib().orc_cell_fuel_fraction_linear(_dp(p), _dp(th), float(t), float(Tf))
+
+
 def default_psi_far(nx, ny, dx, dy) -> float:
     """Reading of "const > 0" for the initial level-set function: the domain diagonal."""
     return float(np.hypot(nx * dx, ny * dy))
@@ -312,10 +325,12 @@ class OracleFire:
     """The oracle's fire model: state + the six-item step, FP64."""
 
     def __init__(self, nxa, nya, sr, dx_atm, classes, fuel, dzdx, dzdy, ignitions=(),
-                 moisture=None, mult=None, eps=0.4, band=1, psi_far=None, dy_atm=None):
+                 moisture=None, mult=None, eps=0.4, band=1, psi_far=None, dy_atm=None,
+                 scheme=0):
         srx, sry = (sr, sr) if np.isscalar(sr) else sr
         dy_atm = dx_atm if dy_atm is None else dy_atm
-        self.g = _Grid(nxa, nya, srx, sry, float(dx_atm), float(dy_atm), float(eps), int(band))
+        self.g = _Grid(nxa, nya, srx, sry, float(dx_atm), float(dy_atm), float(eps), int(band),
+                       int(scheme))
         self.nx, self.ny = nxa * srx, nya * sry
         self.dx, self.dy = dx_atm / srx, dy_atm / sry
         fuel = np.ascontiguousarray(fuel, dtype=np.uint8)

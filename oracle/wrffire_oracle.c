@@ -621,6 +621,132 @@ double orc_cell_fuel_fraction(const double *p, const double *th, double t, doubl
     return 1.0 - 0.25 * burned;
 }
 
+/* ---- The alternative scheme of the Discussion: exact when psi and the
+ * time from ignition are linear in space (the paper names its property,
+ * not its formula; this construction is the reading).
+ * The cell is split into 8 triangles (each subcell of eq.
+ * (fuel_left_subcells) along its diagonal from the cell centre to the cell
+ * corner); on each, psi and D = t - t_i are the linear interpolants of the
+ * vertex values (the same 9 vertex values as the subcell scheme: a node, a
+ * 2-node mean, a 4-node mean, all exact for linear data).  The triangle is
+ * clipped to psi <= 0 (on the cut D = 0: t_i = t on the fireline, eq.
+ * ti-comp), and 1 - exp(-D/T_f) is integrated exactly over the clipped
+ * polygon (fan triangles, the integral of exp of a linear function).
+ * Nodes not yet ignited have no t_i: there D is extended as -lambda psi,
+ * lambda = sum (t - t_i) / sum (-psi) over the neighbourhood's nodes with
+ * psi < 0 (for linear psi and t_i the two are proportional, with that
+ * constant of proportionality).  No node with psi < 0: nothing burns. */
+
+/* (e^a - e^b)/(a - b) with its limit e^a at a == b (a, b <= 0 or small) */
+static double dd1_exp(double a, double b)
+{
+    double d = a - b;
+    if (d == 0.0) return exp(a);
+    return exp(b) * (expm1(d) / d);
+}
+
+/* second divided difference of exp at a, b, c: integral of exp over a
+ * triangle with vertex values a, b, c is 2 area dd2_exp(a, b, c) */
+static double dd2_exp(double a, double b, double c)
+{
+    /* order x0 <= x1 <= x2 */
+    double x0 = a, x1 = b, x2 = c, tmp;
+    if (x0 > x1) { tmp = x0; x0 = x1; x1 = tmp; }
+    if (x1 > x2) { tmp = x1; x1 = x2; x2 = tmp; }
+    if (x0 > x1) { tmp = x0; x0 = x1; x1 = tmp; }
+    double R = x2 - x0;
+    if (R < 1.0) {
+        /* sum over k of h_k(u, v)/(k+2)!, h_k the complete homogeneous
+         * polynomial of degree k in u = x1 - x0, v = x2 - x0 (both in [0, 1)) */
+        double u = x1 - x0, v = x2 - x0, sum = 0.0, fact = 2.0;
+        for (int k = 0; k <= 24; ++k) {
+            double h = 0.0, ui = 1.0;
+            for (int i = 0; i <= k; ++i) {
+                double vj = 1.0;
+                for (int j = 0; j < k - i; ++j) vj *= v;
+                h += ui * vj;
+                ui *= u;
+            }
+            sum += h / fact;
+            fact *= (double)(k + 3);
+        }
+        return exp(x0) * sum;
+    }
+    return (dd1_exp(x0, x1) - dd1_exp(x1, x2)) / (x0 - x2);
+}
+
+/* integral of 1 - exp(-D/Tf) over the part psi <= 0 of the triangle with
+ * vertices (x[k], y[k]) and vertex values ps[k], ds[k] */
+static double tri_burn(const double *x, const double *y, const double *ps, const double *ds,
+                       double Tf)
+{
+    double px[4], py[4], pd[4];
+    int m = 0;
+    for (int k = 0; k < 3; ++k) {
+        int q = (k + 1) % 3;
+        if (ps[k] <= 0.0) { px[m] = x[k]; py[m] = y[k]; pd[m] = ds[k]; ++m; }
+        if ((ps[k] < 0.0 && ps[q] > 0.0) || (ps[k] > 0.0 && ps[q] < 0.0)) {
+            double s = ps[k] / (ps[k] - ps[q]);
+            px[m] = x[k] + s * (x[q] - x[k]);
+            py[m] = y[k] + s * (y[q] - y[k]);
+            pd[m] = 0.0;   /* on the fireline t_i = t */
+            ++m;
+        }
+    }
+    double total = 0.0;
+    for (int k = 1; k + 1 < m; ++k) {
+        double ar = 0.5 * fabs((px[k] - px[0]) * (py[k + 1] - py[0])
+                               - (px[k + 1] - px[0]) * (py[k] - py[0]));
+        if (ar == 0.0) continue;
+        double e = 2.0 * ar * dd2_exp(-pd[0] / Tf, -pd[k] / Tf, -pd[k + 1] / Tf);
+        total += ar - e;
+    }
+    return total;
+}
+
+/* The cell's fuel fraction by this scheme from the same inputs as
+ * orc_cell_fuel_fraction (3x3 psi and compatible ignition times). */
+double orc_cell_fuel_fraction_linear(const double *p, const double *th, double t, double Tf)
+{
+    double sD = 0.0, sP = 0.0;
+    for (int k = 0; k < 9; ++k)
+        if (p[k] < 0.0) { sD += t - th[k]; sP += -p[k]; }
+    if (!(sP > 0.0)) return 1.0;
+    double lambda = sD / sP;
+    double dn[9];
+    for (int k = 0; k < 9; ++k) dn[k] = p[k] < 0.0 ? t - th[k] : -lambda * p[k];
+    /* vertex values on the unit cell [-1/2, 1/2]^2 (the fraction is the
+     * same on the real cell: an affine map keeps area ratios and linear
+     * interpolants) */
+    double vp[3][3], vd[3][3];
+    for (int b = 0; b < 3; ++b) {
+        for (int a = 0; a < 3; ++a) {
+            int ia0 = a == 0 ? 0 : 1, ia1 = a == 2 ? 2 : 1;
+            int ib0 = b == 0 ? 0 : 1, ib1 = b == 2 ? 2 : 1;
+            vp[b][a] = 0.25 * ((p[ib0 * 3 + ia0] + p[ib0 * 3 + ia1])
+                               + (p[ib1 * 3 + ia0] + p[ib1 * 3 + ia1]));
+            vd[b][a] = 0.25 * ((dn[ib0 * 3 + ia0] + dn[ib0 * 3 + ia1])
+                               + (dn[ib1 * 3 + ia0] + dn[ib1 * 3 + ia1]));
+        }
+    }
+    double burned = 0.0;
+    for (int sb = 0; sb < 2; ++sb) {
+        for (int sa = 0; sa < 2; ++sa) {
+            int ax = 2 * sa, by = 2 * sb;
+            double cx = 0.0, cy = 0.0, kx = ax - 1.0, ky = by - 1.0;
+            /* triangles (centre, x-edge midpoint, corner), (centre, corner, y-edge midpoint) */
+            double x1[3] = {cx, 0.5 * kx, 0.5 * kx}, y1[3] = {cy, 0.0, 0.5 * ky};
+            double p1[3] = {vp[1][1], vp[1][ax], vp[by][ax]};
+            double d1[3] = {vd[1][1], vd[1][ax], vd[by][ax]};
+            double x2[3] = {cx, 0.5 * kx, 0.0}, y2[3] = {cy, 0.5 * ky, 0.5 * ky};
+            double p2[3] = {vp[1][1], vp[by][ax], vp[by][1]};
+            double d2[3] = {vd[1][1], vd[by][ax], vd[by][1]};
+            burned += tri_burn(x1, y1, p1, d1, Tf) + tri_burn(x2, y2, p2, d2, Tf);
+        }
+    }
+    return 1.0 - burned;
+}
+
 /* ------------------------------------------------------------------ */
 /* The fire step (Sect. "Coupling", the six-item list).                */
 /* ------------------------------------------------------------------ */
@@ -630,6 +756,8 @@ typedef struct {
     double dx_atm, dy_atm;
     double eps;        /* artificial viscosity, 0.4 in the paper */
     int band;          /* width of the boundary ring checked for fire */
+    int scheme;        /* fuel fraction: 0 the subcell scheme of Sect. 3.3,
+                          1 the scheme exact for linear psi and t_i */
 } orc_grid;
 
 enum { ORC_BOUNDARY = 1, ORC_NONFINITE = 2 };
@@ -741,7 +869,9 @@ int orc_step(const orc_grid *g, const double *co, const double *mult,
                     t9[b * 3 + a] = ext_t[(j + b) * W + (i + a)];
                 }
             long k = (long)j * nx + i;
-            fnew[k] = orc_cell_fuel_fraction(p9, t9, t1, co[k * CO_N + CO_TF]);
+            fnew[k] = g->scheme == 1
+                          ? orc_cell_fuel_fraction_linear(p9, t9, t1, co[k * CO_N + CO_TF])
+                          : orc_cell_fuel_fraction(p9, t9, t1, co[k * CO_N + CO_TF]);
         }
     }
 
