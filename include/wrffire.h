@@ -310,6 +310,27 @@ enum fire_kernel_variant {
     FIRE_KERNEL_WARP4 = 3
 };
 int fire_set_kernel(fire_ctx *ctx, int variant, int kx, int ky);
+
+/* Fuel-fraction scheme of the context's steps:
+ *   FIRE_FRACTION_SUBCELL (default)  the 4-subcell scheme of Sect. 3.3,
+ *                 eqs. (approx-area), (approx-fraction);
+ *   FIRE_FRACTION_LINEAR  the alternative the Discussion describes, exact
+ *                 when psi and the time from ignition are linear in space.
+ *                 Each subcell is split along its centre-corner diagonal;
+ *                 on each triangle psi and t - t_i are the linear
+ *                 interpolants of the same vertex values, the triangle is
+ *                 clipped to psi <= 0 (t_i = t on the cut) and
+ *                 1 - exp(-(t - t_i)/T_f) is integrated exactly; nodes not
+ *                 ignited extend t - t_i as -lambda psi, lambda fitted on the
+ *                 3x3 neighbourhood's burning nodes (exact for linear data).
+ *                 Runs on the 2-D tile kernel only: selecting it switches the
+ *                 context to tiles, and fire_set_kernel then refuses other
+ *                 variants; fire_adjoint and fire_adjoint_heat refuse it
+ *                 (FIRE_ERR_STATE).  More expensive per burning cell.
+ * Not for the context of an ensemble member.  FIRE_ERR_ARG for an unknown
+ * scheme. */
+enum fire_fraction_scheme { FIRE_FRACTION_SUBCELL = 0, FIRE_FRACTION_LINEAR = 1 };
+int fire_set_fraction_scheme(fire_ctx *ctx, int scheme);
 int fire_get_kernel(const fire_ctx *ctx, int *variant, int *kx, int *ky);
 
 /* Autotuner of the step kernel: times candidate shapes (the marching strip

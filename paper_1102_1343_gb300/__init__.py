@@ -50,7 +50,9 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
                "fire_adjoint", "fire_autotune", "fire_ensemble_autotune",
                "fire_default_kernel", "fire_adjoint_heat", "fire_set_moisture",
-               "fire_wind_at_height", "fire_heat_insertion")
+               "fire_wind_at_height", "fire_heat_insertion", "fire_set_fraction_scheme")
+FIRE_FRACTION_SUBCELL = 0
+FIRE_FRACTION_LINEAR = 1
 
 
 class FireError(RuntimeError):
@@ -148,6 +150,8 @@ def load_library(path: str | None = None):
     L.fire_set_fuel_classes.restype = C.c_int
     L.fire_set_moisture.argtypes = [_P, _P]
     L.fire_set_moisture.restype = C.c_int
+    L.fire_set_fraction_scheme.argtypes = [_P, C.c_int]
+    L.fire_set_fraction_scheme.restype = C.c_int
     L.fire_wind_at_height.argtypes = [C.c_int, C.c_int, C.c_longlong, _P, _P, _P, C.c_double,
                                       _P, _P]
     L.fire_wind_at_height.restype = C.c_int
@@ -495,6 +499,11 @@ def fire_set_spread_mult(ctx, mult_dev) -> int:
 
 def fire_set_moisture(ctx, moisture_dev) -> int:
     return _check(load_library().fire_set_moisture(ctx, _ptr(moisture_dev)), "fire_set_moisture")
+
+
+def fire_set_fraction_scheme(ctx, scheme) -> int:
+    return _check(load_library().fire_set_fraction_scheme(ctx, int(scheme)),
+                  "fire_set_fraction_scheme")
 
 
 def fire_wind_at_height(u3d, z3d, z0, z_f, out=None, cuda_stream=None):

@@ -51,6 +51,7 @@ bool ctx_ignition_active(fire_ctx *c, double t);
 cudaStream_t ctx_stream(const fire_ctx *c);
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c);
 const void *ctx_moisture(const fire_ctx *c);
+int ctx_scheme(const fire_ctx *c);
 int ctx_workspace(fire_ctx *c, size_t bytes, void **out);
 cudaGraphExec_t *ctx_adjoint_graphs(fire_ctx *c, unsigned long long **keys);
 
@@ -772,6 +773,8 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     for (int s = 0; s < nsteps; ++s) times[s + 1] = times[s] + dt;
     for (int s = 0; s <= nsteps; ++s)
         if (ctx_ignition_active(c, times[s])) return FIRE_ERR_STATE;
+    // the reverse sweep differentiates the subcell fuel-fraction scheme
+    if (ctx_scheme(c) != 0) return FIRE_ERR_STATE;
 
     // workspace
     size_t off = 0;

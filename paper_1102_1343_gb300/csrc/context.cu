@@ -48,6 +48,7 @@ struct fire_ctx {
 
     int variant = FIRE_KERNEL_MARCH;
     int kx = 0, ky = 0;
+    int scheme = 0;  // fuel fraction: 0 subcell scheme, 1 exact for linear data (tiles)
     size_t smem = 0;
     size_t smem_max = 0;
     int n_sm = 1;  // SMs of the device (sizes the default launch shape)
@@ -169,6 +170,7 @@ int step_kernel_args(fire_ctx *c, const void *u, const void *v, double dt, doubl
     a.dzdy = c->dzdy;
     a.mult = c->mult;
     for (int q = 0; q < 5; ++q) a.nco[q] = c->nco[q];
+    a.scheme = c->scheme;
     a.u = u;
     a.v = v;
     a.coef = c->coef;
@@ -473,6 +475,7 @@ int ctx_default_warp_strips(fire_ctx *c) { return default_warp_strips(c); }
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c) { return c->classes_dev; }
 const void *ctx_moisture(const fire_ctx *c) { return c->moist; }
 bool ctx_has_node_coefficients(const fire_ctx *c) { return c->nco[0] != nullptr; }
+int ctx_scheme(const fire_ctx *c) { return c->scheme; }
 int ctx_ensure_node_coefficients(fire_ctx *c) {
     if (c->nco[0]) return FIRE_OK;
     int r = drop_step_graph(c);
@@ -893,7 +896,31 @@ double fire_time(const fire_ctx *c) { return c ? c->t : NAN; }
 
 int fire_set_kernel(fire_ctx *c, int variant, int kx, int ky) {
     if (!c) return FIRE_ERR_ARG;
+    if (c->scheme == 1 && variant != FIRE_KERNEL_TILE) return FIRE_ERR_ARG;
     return configure_kernel(c, variant, kx, ky);
+}
+
+int fire_set_fraction_scheme(fire_ctx *c, int scheme) {
+    if (!c || (scheme != 0 && scheme != 1)) return FIRE_ERR_ARG;
+    if (scheme == c->scheme) return FIRE_OK;
+    int r = drop_step_graph(c);  // the captured steps carry the scheme
+    if (r) return r;
+    if (scheme == 1 && c->variant != FIRE_KERNEL_TILE) {
+        // the 2-D tile kernel at the large-refinement tile size, halved
+        // until its shared memory fits
+        const bool fp64 = c->prec == FIRE_FP64;
+        int kx = (fp64 ? 40 : 80) / c->g.sr_x, ky = 40 / c->g.sr_y;
+        kx = kx < 1 ? 1 : (kx > c->g.nx_atm ? c->g.nx_atm : kx);
+        ky = ky < 1 ? 1 : (ky > c->g.ny_atm ? c->g.ny_atm : ky);
+        for (;;) {
+            if (configure_kernel(c, FIRE_KERNEL_TILE, kx, ky) == FIRE_OK) break;
+            if (kx == 1 && ky == 1) return FIRE_ERR_ARG;
+            if (kx >= ky && kx > 1) kx = (kx + 1) / 2;
+            else ky = (ky + 1) / 2;
+        }
+    }
+    c->scheme = scheme;
+    return FIRE_OK;
 }
 
 // Candidate step-kernel shapes timed on a scratch copy of the state: the
@@ -939,6 +966,7 @@ int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int prob
     std::vector<Cand> cands;
     const int srx = c->g.sr_x, sry = c->g.sr_y, nxa = c->g.nx_atm, nya = c->g.ny_atm;
     auto add = [&](int variant, int kx, int ky) {
+        if (c->scheme == 1 && variant != FIRE_KERNEL_TILE) return;  // tiles only
         kx = kx < 1 ? 1 : (kx > nxa ? nxa : kx);
         ky = ky < 1 ? 1 : (ky > nya ? nya : ky);
         if (variant != FIRE_KERNEL_TILE && ((kx * srx) & 1)) {
@@ -964,6 +992,14 @@ int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int prob
         for (int W : widths) {
             if (W / srx * srx > kWarpMaxColumns || W / srx < 1) continue;
             for (int L : heights) add(FIRE_KERNEL_WARP, W / srx, L / sry);
+        }
+    }
+    if (c->prec == FIRE_FP32 && srx <= kWarp4MaxColumns / 2) {
+        const int widths[] = {60, 80, 100, 120};
+        const int heights[] = {16, 32, 64, 128, 256};
+        for (int W : widths) {
+            if (W / srx * srx > kWarp4MaxColumns || W / srx < 1) continue;
+            for (int L : heights) add(FIRE_KERNEL_WARP4, W / srx, L / sry);
         }
     }
     {

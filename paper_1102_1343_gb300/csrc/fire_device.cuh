@@ -257,4 +257,134 @@ __device__ __forceinline__ T cell_fraction_vals(T p00, T p01, T p02, T p10, T p1
     return T(1) - q * (((bSW + bSE) + bNW) + bNE);
 }
 
+// ---------------------------------------------------------------------------
+// The fuel-fraction scheme exact for linear psi and t - t_i (the
+// alternative of the Discussion, which names the property, not a formula):
+// the cell's 8 triangles (each subcell split along its centre-corner
+// diagonal) carry the linear interpolants of the 9 vertex values, each is
+// clipped to psi <= 0 (t - t_i = 0 on the cut, eq. ti-comp) and
+// 1 - exp(-(t - t_i)/T_f) is integrated exactly over the clipped part.
+// Nodes not yet ignited extend t - t_i as -lambda psi, lambda fitted on the
+// neighbourhood's burning nodes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float expm1_t(float x) { return expm1f(x); }
+__device__ __forceinline__ double expm1_t(double x) { return expm1(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+
+// (e^a - e^b)/(a - b), e^a at a == b
+template <typename T>
+__device__ __forceinline__ T dd1_exp(T a, T b) {
+    const T d = a - b;
+    if (d == T(0)) return exp_t(a);
+    return exp_t(b) * (expm1_t(d) / d);
+}
+
+// second divided difference of exp: the integral of exp over a triangle with
+// vertex values a, b, c is 2 area dd2_exp(a, b, c); a series in the spreads
+// below a spread of 1, differences of dd1 above
+template <typename T>
+__device__ __forceinline__ T dd2_exp(T a, T b, T c) {
+    T x0 = a, x1 = b, x2 = c, tmp;
+    if (x0 > x1) { tmp = x0; x0 = x1; x1 = tmp; }
+    if (x1 > x2) { tmp = x1; x1 = x2; x2 = tmp; }
+    if (x0 > x1) { tmp = x0; x0 = x1; x1 = tmp; }
+    const T R = x2 - x0;
+    if (R < T(1)) {
+        // sum over k of h_k(u, v)/(k+2)!, h_k the complete homogeneous
+        // polynomial of degree k (h_k = u h_{k-1} + v^k)
+        constexpr int K = sizeof(T) == 8 ? 24 : 12;
+        const T u = x1 - x0, v = x2 - x0;
+        T sum = T(0), h = T(1), vk = T(1), inv = T(0.5);
+        for (int k = 0; k <= K; ++k) {
+            if (k > 0) {
+                vk *= v;
+                h = u * h + vk;
+            }
+            sum += h * inv;
+            inv /= T(k + 3);
+        }
+        return exp_t(x0) * sum;
+    }
+    return (dd1_exp<T>(x0, x1) - dd1_exp<T>(x1, x2)) / (x0 - x2);
+}
+
+// integral of 1 - exp(-D/Tf) over the part psi <= 0 of a triangle
+template <typename T>
+__device__ __forceinline__ T tri_burn(const T *x, const T *y, const T *ps, const T *ds, T Tf) {
+    T px[4], py[4], pd[4];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = k == 2 ? 0 : k + 1;
+        if (ps[k] <= T(0)) {
+            px[m] = x[k];
+            py[m] = y[k];
+            pd[m] = ds[k];
+            ++m;
+        }
+        if ((ps[k] < T(0) && ps[q] > T(0)) || (ps[k] > T(0) && ps[q] < T(0))) {
+            const T s = ps[k] / (ps[k] - ps[q]);
+            px[m] = x[k] + s * (x[q] - x[k]);
+            py[m] = y[k] + s * (y[q] - y[k]);
+            pd[m] = T(0);
+            ++m;
+        }
+    }
+    T total = T(0);
+    for (int k = 1; k + 1 < m; ++k) {
+        const T ar = T(0.5) * abs_val((px[k] - px[0]) * (py[k + 1] - py[0]) -
+                                      (px[k + 1] - px[0]) * (py[k] - py[0]));
+        if (ar == T(0)) continue;
+        total += ar - T(2) * ar * dd2_exp<T>(-pd[0] / Tf, -pd[k] / Tf, -pd[k + 1] / Tf);
+    }
+    return total;
+}
+
+// The cell's fuel fraction from the 3x3 node values of psi (p, row-major,
+// [4] the cell's node) and of D = t - t_i (0 where psi >= 0)
+template <typename T>
+__device__ __forceinline__ T cell_fraction_linear_vals(const T *p, const T *D, T Tf) {
+    T sD = T(0), sP = T(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        if (p[k] < T(0)) {
+            sD += D[k];
+            sP += -p[k];
+        }
+    if (!(sP > T(0))) return T(1);
+    const T lambda = sD / sP;
+    T dn[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dn[k] = p[k] < T(0) ? D[k] : -lambda * p[k];
+    T vp[3][3], vd[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int ia0 = a == 0 ? 0 : 1, ia1 = a == 2 ? 2 : 1;
+            const int ib0 = b == 0 ? 0 : 1, ib1 = b == 2 ? 2 : 1;
+            vp[b][a] = T(0.25) * ((p[ib0 * 3 + ia0] + p[ib0 * 3 + ia1]) +
+                                  (p[ib1 * 3 + ia0] + p[ib1 * 3 + ia1]));
+            vd[b][a] = T(0.25) * ((dn[ib0 * 3 + ia0] + dn[ib0 * 3 + ia1]) +
+                                  (dn[ib1 * 3 + ia0] + dn[ib1 * 3 + ia1]));
+        }
+    T burned = T(0);
+#pragma unroll
+    for (int sb = 0; sb < 2; ++sb)
+#pragma unroll
+        for (int sa = 0; sa < 2; ++sa) {
+            const int ax = 2 * sa, by = 2 * sb;
+            const T kx = T(ax - 1), ky = T(by - 1);
+            const T x1[3] = {T(0), T(0.5) * kx, T(0.5) * kx}, y1[3] = {T(0), T(0), T(0.5) * ky};
+            const T p1[3] = {vp[1][1], vp[1][ax], vp[by][ax]};
+            const T d1[3] = {vd[1][1], vd[1][ax], vd[by][ax]};
+            const T x2[3] = {T(0), T(0.5) * kx, T(0)}, y2[3] = {T(0), T(0.5) * ky, T(0.5) * ky};
+            const T p2[3] = {vp[1][1], vp[by][ax], vp[by][1]};
+            const T d2[3] = {vd[1][1], vd[by][ax], vd[by][1]};
+            burned += tri_burn<T>(x1, y1, p1, d1, Tf) + tri_burn<T>(x2, y2, p2, d2, Tf);
+        }
+    return T(1) - burned;
+}
+
 }  // namespace wf

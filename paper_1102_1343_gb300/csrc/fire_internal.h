@@ -46,6 +46,9 @@ struct StepArgs {
     // d, H_s, H_q, each [ny][nx] in the path precision (S0, b, e and T_f
     // stay per class)
     const void *nco[5];
+    // fuel fraction: 0 the subcell scheme of Sect. 3.3, 1 the scheme exact
+    // for linear psi and t_i (2-D tile kernel only)
+    int scheme;
 };
 
 struct IgnSeg {

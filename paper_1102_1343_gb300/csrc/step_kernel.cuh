@@ -284,7 +284,21 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
                 int cls = fuel[g];
                 cls = cls > ncm1 ? ncm1 : cls;
                 const T *co = lut + cls * K_N;
-                const T Fn = cell_fraction<T>(P2, Dl, (ly + 1) * BW1 + (lx + 1), BW1, co[K_TF]);
+                const int cc = (ly + 1) * BW1 + (lx + 1);
+                T Fn;
+                if (a.scheme == 1) {
+                    T p9[9], d9[9];
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+#pragma unroll
+                        for (int h = 0; h < 3; ++h) {
+                            p9[b * 3 + h] = P2[cc + (b - 1) * BW1 + (h - 1)];
+                            d9[b * 3 + h] = Dl[cc + (b - 1) * BW1 + (h - 1)];
+                        }
+                    Fn = cell_fraction_linear_vals<T>(p9, d9, co[K_TF]);
+                } else {
+                    Fn = cell_fraction<T>(P2, Dl, cc, BW1, co[K_TF]);
+                }
                 const T Fo = F_in[g];
                 F_out[g] = Fn;
                 const T dF = Fo - Fn;

@@ -29,14 +29,16 @@ def pkg():
     return p
 
 
-def run_pair(pkg, w, prec, steps=None, tile=None, check_every=None, heat_tol=1e-10):
+def run_pair(pkg, w, prec, steps=None, tile=None, check_every=None, heat_tol=1e-10, scheme=0):
     """Run the CUDA path and the oracle side by side; returns both and the
     worst per-step heat error and the integrated heats."""
     import torch
     steps = w.steps if steps is None else steps
     wp = as_path_precision(w, prec)
-    orc = oracle.OracleFire.from_workload(wp)
+    orc = oracle.OracleFire.from_workload(wp, scheme=scheme)
     m = pkg.FireModel.from_workload(w, precision=prec)
+    if scheme:
+        pkg.fire_set_fraction_scheme(m.ctx, scheme)
     if tile:
         pkg.fire_set_kernel(m.ctx, *tile)
     u, v = m.wind(w.u, w.v)
@@ -161,6 +163,44 @@ def test_fp64_drip_torch(pkg, tile):
     assert ok, e
     assert heat_err <= 1e-10
     assert np.isfinite(orc.tign).sum() > 100 and Qo > 0
+
+
+@pytest.mark.parametrize("case,tile", [("line", None), ("line", (0, 2, 2)), ("points", (0, 3, 1))])
+def test_fp64_linear_fraction_scheme(pkg, case, tile):
+    """The fuel-fraction scheme exact for linear psi and t_i (the tile
+    kernel) against the oracle's, at 1e-10 on psi, F, t_i and the heat."""
+    w = synth.random_landscape(23, 17, seed=21, ignition=case, n_points=4, edge_margin=200.0,
+                               steps=120)
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile, scheme=1)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    assert Qo > 0 and pkg.fire_get_kernel(m.ctx)[0] == pkg.FIRE_KERNEL_TILE
+    # other kernels are refused while the scheme is set, and so is the adjoint
+    with pytest.raises(pkg.FireError):
+        pkg.fire_set_kernel(m.ctx, pkg.FIRE_KERNEL_MARCH, 2, 2)
+    u, v = m.wind(w.u, w.v)
+    with pytest.raises(pkg.FireError) as ex:
+        m.adjoint(u, v, w.dt, 5, np.full((w.ny, w.nx), np.nan), grads=False)
+    assert ex.value.code == pkg.FIRE_ERR_STATE
+    pkg.fire_set_fraction_scheme(m.ctx, pkg.FIRE_FRACTION_SUBCELL)
+    pkg.fire_set_kernel(m.ctx, pkg.FIRE_KERNEL_MARCH, 2, 2)
+    m.close()
+
+
+def test_fp32_linear_fraction_scheme(pkg):
+    w = synth.random_landscape(32, 26, seed=44, ignition="line", steps=300)
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp32", scheme=1)
+    psi, tign, frac, _ = state_np(m)
+    both = np.isfinite(tign) & np.isfinite(orc.tign)
+    assert both.sum() > 100
+    dti = np.abs(tign[both] - orc.tign[both]).max()
+    B, Bo = (1 - frac).sum(), (1 - orc.frac).sum()
+    assert dti <= 0.1
+    assert abs((psi <= 0).sum() - (orc.psi <= 0).sum()) / (orc.psi <= 0).sum() <= 0.005
+    assert abs(B - Bo) / Bo <= 0.005
+    assert abs(Qg - Qo) / Qo <= 1e-4
+    m.close()
 
 
 @pytest.mark.parametrize("tile", [None, (2, 6, 4)])
