@@ -477,11 +477,10 @@ def test_warp4_equals_two_column_warp_kernel(pkg, mesh):
     import torch
     nxa, nya, sr = mesh
     w = synth.random_landscape(nxa, nya, sr=sr, seed=46, ignition="points", n_points=5,
-                               edge_margin=150.0, steps=150)
+                               edge_margin=150.0, steps=150, ignition_radius=25.0)
     if nxa == 13:
         w = node_moisture(w)
         w.mult = np.random.default_rng(5).uniform(0.7, 1.3, (w.ny, w.nx))
-    w.mult = (w.mult if w.mult is not None else np.ones((w.ny, w.nx))) * (3.0 if sr == 5 else 1.0)
     a = pkg.FireModel.from_workload(w, precision="fp32")
     b = pkg.FireModel.from_workload(w, precision="fp32")
     c = pkg.FireModel.from_workload(w, precision="fp32")
