@@ -175,6 +175,12 @@ def make_workload(name: str):
         return synth.random_landscape(400, 400, seed=synth.BASE_SEED, ignition="points",
                                       n_points=12, edge_margin=500.0, steps=2000,
                                       name="points-fire-4000x4000")
+    if name == "burning4000":
+        # the burning recipe on the same smaller mesh, for profiler captures
+        # of the quadrature-heavy regime
+        return synth.random_landscape(400, 400, seed=synth.BASE_SEED, ignition="points",
+                                      n_points=12, edge_margin=3500.0, ignition_radius=3000.0,
+                                      steps=2000, name="burning-fire-4000x4000")
     raise ValueError(name)
 
 
@@ -297,6 +303,8 @@ WORKLOAD_NAMES = {"points8200": "points-fire-8200x8200 (820x820 atmos x10, 50 po
                   "line2000": "line-fire-2000x2000 (200x200 atmos x10, 1 km line ignition)",
                   "circle100": "circle-fp64-100x100 (10x10 atmos x10)",
                   "burning8200": "burning-fire-8200x8200 (820x820 atmos x10, 50 ignitions "
+                                 "of radius 3 km)",
+                  "burning4000": "burning-fire-4000x4000 (400x400 atmos x10, 12 ignitions "
                                  "of radius 3 km)"}
 
 
@@ -748,7 +756,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["points8200", "line2000", "circle100", "points4000",
-                                           "burning8200"],
+                                           "burning8200", "burning4000"],
                     default="points8200")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--kernel", type=int, nargs=3, default=None,
