@@ -587,12 +587,12 @@ def _clone_state(st):
 
 def bench_adjoint(pkg, dev, ckpt=20):
     """fire_adjoint on the 510x510 adjoint workload (400 steps of 0.5 s,
-    checkpoints every 20): misfit against the arrival times of a perturbed
-    truth run, gradients w.r.t. multiplier, moisture and wind; and
-    fire_adjoint_heat against the heat that run released per atmospheric
-    cell.  Cell-steps/s
-    of the whole call (forward with checkpoints + reverse sweep) and of the
-    plain FP64 forward on the same mesh, each with its autotuned kernel."""
+    checkpoints every 20, and every state kept): misfit against the arrival
+    times of a perturbed truth run, gradients w.r.t. multiplier, moisture and
+    wind; and fire_adjoint_heat against the heat that run released per
+    atmospheric cell.  Cell-steps/s of the whole call (forward with
+    checkpoints + reverse sweep) and of the plain forward on the same mesh,
+    each with its autotuned kernel."""
     import torch
     from paper_1102_1343_gb300 import synth
     w, truth = synth.adjoint_case()
@@ -636,6 +636,20 @@ def bench_adjoint(pkg, dev, ckpt=20):
         rec = {"value": n / (ms / 1e3), "ms": ms, "J": J,
                "kernel": {"variant": ["tile", "march", "warp", "warp4"][kern[0]],
                           "tile_atmos_cells": list(kern[1:])}}
+        # every state kept (checkpoint interval 1: no recomputed forward;
+        # 401 states of the mesh in HBM)
+        m.set_state(*st0)
+        m.adjoint(u, v, w.dt, w.steps, tobs, 1)
+        m.set_state(*st0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        J1, *_ = m.adjoint(u, v, w.dt, w.steps, tobs, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        rec["every_state_kept"] = {"value": n / (ms1 / 1e3), "ms": ms1, "J": J1,
+                                   "state_bytes": (w.steps + 1) * w.nx * w.ny *
+                                   (8 if prec == "fp64" else 4)}
         # the heat-misfit adjoint on the same run (warm-up, then timed)
         m.set_state(*st0)
         m.adjoint_heat(u, v, w.dt, w.steps, qobs, ckpt)
@@ -658,6 +672,7 @@ def bench_adjoint(pkg, dev, ckpt=20):
         torch.cuda.synchronize()
         fms = e0.elapsed_time(e1)
         rec["plain_forward"] = {"value": n / (fms / 1e3), "ms": fms}
+        rec["ratio_to_plain_forward"] = {f"ckpt{ckpt}": fms / ms, "ckpt1": fms / ms1}
         out[prec] = rec
         m.close()
     base = out["fp64"]["plain_forward"]["value"]

@@ -11,10 +11,11 @@
 // needs.
 //
 // Forward: the context advances nsteps steps with the step kernel it uses
-// for fire_step, saving psi every K steps (checkpoints).  Reverse: for each
-// K-step segment, last first, the states psi^s of the segment are recomputed
-// from its checkpoint with the same step kernel (bitwise the same values,
-// hence the same branches), then each step is reversed:
+// for fire_step, saving psi every K steps (checkpoints; with K = 1 every
+// state is kept and nothing is recomputed).  Reverse: for each K-step
+// segment, last first, the states psi^s of the segment are recomputed from
+// its checkpoint with the same step kernel (bitwise the same values, hence
+// the same branches), then each step is reversed:
 //   mu      = lambda + dJ/dpsi^{s+1}   (nodes whose t_i was set in step s)
 //   psi*    = psi^s + dt F(psi^s)
 //   lam*    = J_F(psi*)^T (dt/2 mu)
@@ -23,15 +24,18 @@
 // with the parameter terms v^T dF/dp of both products summed per node.
 // Branches (Godunov selection, max/min of the spread rate, the
 // extrapolated ghosts, zeroed central differences) are those the forward
-// values take.  Each product J^T v is formed without atomics: one kernel
-// writes every node's five stencil contributions v_j dF_j/dpsi_k, the next
-// gathers them per node k, so results do not depend on scheduling.
+// values take.  A reverse step is one launch of tiles that form the whole
+// chain above for their nodes in shared memory (k_adj_step); each product
+// J^T v is formed without atomics, every node's five stencil contributions
+// v_j dF_j/dpsi_k written first and then gathered per node k in a fixed
+// order, so results do not depend on scheduling.
 //
 // Precision: the state, the partial derivatives, the adjoint fields and the
 // stencil contributions are in the path precision T (FP32 or FP64); the
-// parameter gradients, summed over the whole run, and the arrival-time seeds
-// are double.  The FP32 path thus keeps the (1/64-rate) FP64 pipe to one
-// conversion and add per gradient and node, and to the nodes that cross.
+// arrival-time seeds are double, and the parameter gradients, summed over
+// the whole run, are double in FP64 and compensated float pairs in FP32
+// (double at the end), so the FP32 reverse step uses the FP64 pipe (a small
+// fraction of the FP32 rate on this part) only at the nodes that cross.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -47,6 +51,7 @@ int ctx_step_args(fire_ctx *c, int parity, const void *u, const void *v, double 
                   double *hl, StepArgs &a);
 int ctx_info(const fire_ctx *c, int *prec, int *variant, int *nx, int *ny, int *srx, int *sry,
              int *kx, int *ky, int *ncls, int *cur, double *t);
+int ctx_advance(fire_ctx *c, int nsteps, double dt);
 bool ctx_ignition_active(fire_ctx *c, double t);
 cudaStream_t ctx_stream(const fire_ctx *c);
 const fire_fuel_class *ctx_classes_dev(const fire_ctx *c);
@@ -59,11 +64,39 @@ namespace {
 
 constexpr int kAdjThreads = 256;
 
+// A sum over the run's steps of per-step contributions in T: FP64 adds in
+// place; FP32 keeps a compensated pair (Kahan summation: the sum is s - c),
+// so that the sum of 10^2..10^4 steps stays at FP32 rounding without an FP64
+// instruction in the reverse step (the FP64 pipe of this part issues at a
+// small fraction of the FP32 rate).
+template <typename T>
+struct GAcc;
+template <>
+struct GAcc<double> {
+    using t = double;
+    static __device__ __forceinline__ void add(double &g, double x) { g += x; }
+};
+template <>
+struct GAcc<float> {
+    using t = float2;  // (s, c)
+    static __device__ __forceinline__ void add(float2 &g, float x) {
+        const float y = x - g.y;
+        const float t = g.x + y;
+        g.y = (t - g.x) - y;
+        g.x = t;
+    }
+};
+
 template <typename T>
 struct AdjArgs {
     const T *pa, *pb;  // psi^s, psi^{s+1}
-    const T *X;        // field of the current Jacobian product
-    T *pstar;          // psi* of step s
+    // the unfused reverse step (FP64): the field of the current Jacobian
+    // product, psi*, mu, lam*, and the stencil contributions [5][n] that a
+    // kernel writes (Cout) and the next gathers (Cin)
+    const T *X;
+    T *pstar, *mu, *ls;
+    const T *Cin;
+    T *Cout;
     const uint8_t *fuel;
     const T *zx, *zy, *mult;  // mult nullable (1)
     const T *u, *v;
@@ -75,10 +108,12 @@ struct AdjArgs {
     const double *dJdt;  // dJ/dt_i per node instead of t_i - t_obs (heat misfit), or null
     const double *tsp;  // [2] start and end time of the step (device)
     double dt;
-    T *lam, *mu, *ls;
-    const T *Cin;  // contributions gathered by this kernel [5][n]
-    T *Cout;       // contributions written by this kernel [5][n]
-    double *gm, *gM, *gun, *gvn;
+    const T *lin;  // lambda^{s+1}
+    T *lout;       // lambda^s
+    // parameter gradients summed over the run, [4][n]: multiplier, moisture,
+    // node wind u, v (GAcc<T>::t each; the wind pair only with wind_grads)
+    typename GAcc<T>::t *acc;
+    int wind_grads;
     int nx, ny, nxa, nya, srx, sry;
     T idx, idy, i2dx, i2dy, eps, dtT, hdtT;  // dtT = dt, hdtT = dt/2 in T
     size_t n;
@@ -86,17 +121,6 @@ struct AdjArgs {
 
 // stencil slots: centre, left, right, down, up
 enum { P_C = 0, P_L, P_R, P_D, P_U };
-
-template <typename T>
-__device__ __forceinline__ void stencil(const T *X, int nx, int ny, int i, int j, T &p, T &pl,
-                                        T &pr, T &pd, T &pu) {
-    const size_t k = (size_t)j * nx + i;
-    p = X[k];
-    pl = i > 0 ? X[k - 1] : ghost_value<T>(p, X[k + 1]);
-    pr = i < nx - 1 ? X[k + 1] : ghost_value<T>(p, X[k - 1]);
-    pd = j > 0 ? X[k - nx] : ghost_value<T>(p, X[k + nx]);
-    pu = j < ny - 1 ? X[k + nx] : ghost_value<T>(p, X[k - nx]);
-}
 
 // d(ghost)/d(p0), d(ghost)/d(p1) for the branch ghost_value takes
 template <typename T>
@@ -118,30 +142,50 @@ __device__ __forceinline__ void ghost_partials(T p0, T p1, T &d0, T &d1) {
 
 template <typename T>
 struct NodeEnv {
-    T co[6];
-    int cls;
-    size_t ci;  // row of coef / dcoef: the class, or the node with per-node coefficients
+    T co[6];   // S0, R0, b, c, d, e
+    T dco[4];  // d/dM_f of S0, R0, c, d
     T m, un, vn, zx, zy;
 };
 
+// the coefficients of node k (from the class table lut, [ncls][10] in T:
+// the six coefficients, then d/dM_f of S0, R0, c, d; from the double tables
+// when lut is null or the coefficients are per node), its multiplier, slope
+// and node wind
 template <typename T>
-__device__ __forceinline__ void node_env(const AdjArgs<T> &a, int i, int j, NodeEnv<T> &e) {
-    const size_t k = (size_t)j * a.nx + i;
-    int cls = a.fuel[k];
-    cls = cls > a.ncls - 1 ? a.ncls - 1 : cls;
-    e.cls = cls;
-    e.ci = a.nodeco ? k : (size_t)cls;
+__device__ __forceinline__ void node_env(const AdjArgs<T> &a, const T *lut, size_t k, bool want_d,
+                                         NodeEnv<T> &e) {
+    if (a.nodeco || !lut) {
+        size_t row = k;
+        if (!a.nodeco) {
+            const int cls = a.fuel[k];
+            row = (size_t)(cls > a.ncls - 1 ? a.ncls - 1 : cls);
+        }
+        const double *co = a.coef + row * K_N;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) e.co[q] = T(a.coef[e.ci * K_N + q]);
+        for (int q = 0; q < 6; ++q) e.co[q] = T(co[q]);
+        if (want_d) {
+            const double *dc = a.dcoef + row * K_N;
+            e.dco[0] = T(dc[K_S0]);
+            e.dco[1] = T(dc[K_R0]);
+            e.dco[2] = T(dc[K_C]);
+            e.dco[3] = T(dc[K_D]);
+        }
+    } else {
+        int cls = a.fuel[k];
+        cls = cls > a.ncls - 1 ? a.ncls - 1 : cls;
+        const T *l = lut + cls * 10;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) e.co[q] = l[q];
+        if (want_d) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) e.dco[q] = l[6 + q];
+        }
+    }
     e.m = a.mult ? a.mult[k] : T(1);
     e.zx = a.zx[k];
     e.zy = a.zy[k];
-    if (a.unv) {
-        e.un = a.unv[2 * k];
-        e.vn = a.unv[2 * k + 1];
-    } else {
-        wind_at<T>(a.u, a.v, a.nxa, a.nya, a.srx, a.sry, i, j, e.un, e.vn);
-    }
+    e.un = a.unv[2 * k];
+    e.vn = a.unv[2 * k + 1];
 }
 
 // Partial derivatives of the right-hand side of eq. (F-disc) at one node,
@@ -190,12 +234,13 @@ __device__ __forceinline__ void node_partials(T p, T pl, T pr, T pd, T pu, T idx
     const T S = e.m * St;
     const T lap = (dxp - dxm) + (dyp - dym);
     const T Fs = -grad + eps * lap;  // dF/dS
-    const T dSt_dU = (active && U > T(0) && U < e.co[K_E]) ? e.co[K_C] * e.co[K_B] * pwv / Ue : T(0);
+    const T dSt_dU =
+        (active && U > T(0) && U < e.co[K_E]) ? Mth<T>::dv(e.co[K_C] * e.co[K_B] * pwv, Ue) : T(0);
     const T dSt_dT = (active && tp > T(0)) ? T(2) * e.co[K_D] * tp : T(0);
     // the unit normal n = c/|c|: dn/dc = (I - n n^T)/|c|
     T dS_dcx = T(0), dS_dcy = T(0);
     if (cn2 > Mth<T>::kNormMin) {
-        const T rc = T(1) / Mth<T>::sqr(cn2);
+        const T rc = Mth<T>::dv(T(1), Mth<T>::sqr(cn2));
         const T dU_dcx = (e.un - U * nxv) * rc, dU_dcy = (e.vn - U * nyv) * rc;
         const T dT_dcx = (e.zx - tp * nxv) * rc, dT_dcy = (e.zy - tp * nyv) * rc;
         dS_dcx = e.m * (dSt_dU * dU_dcx + dSt_dT * dT_dcx);
@@ -205,8 +250,8 @@ __device__ __forceinline__ void node_partials(T p, T pl, T pr, T pd, T pu, T idx
     // d|grad|/d(one-sided differences) through the taken branch
     T wx = T(0), wy = T(0);
     if (grad > T(0)) {
-        wx = gx / grad;
-        wy = gy / grad;
+        wx = Mth<T>::dv(gx, grad);
+        wy = Mth<T>::dv(gy, grad);
     }
     T dG[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (xm) {
@@ -275,13 +320,31 @@ __global__ void k_adj_node_wind(const AdjArgs<T> a, T *unv) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// The reverse step of FP64 in four grid-wide kernels: no node's work is
+// repeated (FP64 arithmetic bounds the step on this part).
+// ---------------------------------------------------------------------------
+
+// the five stencil values of node (i, j) of field X with the extrapolated
+// ghosts of Sect. 3.1 at the domain boundary (nx, ny >= 2)
+template <typename T>
+__device__ __forceinline__ void stencil(const T *X, int nx, int ny, int i, int j, T &p, T &pl,
+                                        T &pr, T &pd, T &pu) {
+    const size_t k = (size_t)j * nx + i;
+    p = X[k];
+    pl = i > 0 ? X[k - 1] : ghost_value<T>(p, X[k + 1]);
+    pr = i < nx - 1 ? X[k + 1] : ghost_value<T>(p, X[k - 1]);
+    pd = j > 0 ? X[k - nx] : ghost_value<T>(p, X[k + nx]);
+    pu = j < ny - 1 ? X[k + nx] : ghost_value<T>(p, X[k - nx]);
+}
+
 // seeds mu = lambda + dJ/dpsi^{s+1} and forms psi* = psi^s + dt F(psi^s)
 template <typename T>
 __global__ void k_adj_stage1(const AdjArgs<T> a) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < a.n;
          k += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(k % a.nx), j = (int)(k / a.nx);
-        T mu = a.lam[k];
+        T mu = a.lin[k];
         double q0, q1, r;
         if (crossed(a, k, q0, q1, r)) {
             const double den = q0 - q1;
@@ -289,7 +352,7 @@ __global__ void k_adj_stage1(const AdjArgs<T> a) {
         }
         a.mu[k] = mu;
         NodeEnv<T> e;
-        node_env(a, i, j, e);
+        node_env<T>(a, nullptr, k, false, e);
         T p, pl, pr, pd, pu;
         stencil(a.pa, a.nx, a.ny, i, j, p, pl, pr, pd, pu);
         const T F = rhs_vals<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e.co,
@@ -298,26 +361,23 @@ __global__ void k_adj_stage1(const AdjArgs<T> a) {
     }
 }
 
-// v^T dF/dp at node k added to the parameter gradients, and the node's five
+// v^T dF/dp at node k added to the parameter sums, and the node's five
 // stencil contributions v dF/dpsi written to Cout
 template <typename T>
 __device__ __forceinline__ void vjp_node(const AdjArgs<T> &a, size_t k, int i, int j, T v) {
     NodeEnv<T> e;
-    node_env(a, i, j, e);
+    node_env<T>(a, nullptr, k, true, e);
     T p, pl, pr, pd, pu;
     stencil(a.X, a.nx, a.ny, i, j, p, pl, pr, pd, pu);
     Partials<T> o;
     node_partials<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e, o);
 #pragma unroll
     for (int q = 0; q < 5; ++q) a.Cout[q * a.n + k] = v * o.dpsi[q];
-    const double *dc = a.dcoef + e.ci * K_N;
-    a.gm[k] += (double)(v * o.dm);
-    a.gM[k] += (double)(v * (o.dS0 * T(dc[K_S0]) + o.dR0 * T(dc[K_R0]) + o.dc * T(dc[K_C]) +
-                             o.dd * T(dc[K_D])));
-    if (a.gun) {
-        a.gun[k] += (double)(v * o.dun);
-        a.gvn[k] += (double)(v * o.dvn);
-    }
+    const T g[4] = {v * o.dm,
+                    v * (o.dS0 * e.dco[0] + o.dR0 * e.dco[1] + o.dc * e.dco[2] + o.dd * e.dco[3]),
+                    v * o.dun, v * o.dvn};
+    const int nq = a.wind_grads ? 4 : 2;
+    for (int q = 0; q < nq; ++q) GAcc<T>::add(a.acc[q * a.n + k], g[q]);
 }
 
 // (J_X^T v)_k: the contributions of the stencils that contain node k, with
@@ -389,7 +449,406 @@ __global__ void k_adj_finish(const AdjArgs<T> a) {
             const double den = q0 - q1;
             lam = T((double)lam + r * (-a.dt * q1 / (den * den)));
         }
-        a.lam[k] = lam;
+        a.lout[k] = lam;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The reverse step of FP32 in one launch (memory latency and launch gaps,
+// not arithmetic, bound the unfused FP32 step).  A CTA owns a tile of
+// kRevTX x kRevTY nodes and forms, in shared memory, in the frame of the
+// tile with a halo of kRevHalo nodes, what its nodes' lambda^s needs:
+//   psi^s            radius 4  (read)
+//   node inputs      radius 3  class, multiplier, slope, node wind (read)
+//   mu               radius 2  lambda^{s+1} + the seed of crossing nodes
+//   psi*             radius 3  psi^s + dt F(psi^s)
+//   C* = v dF/dpsi   radius 2  at psi*, v = dt/2 mu, five stencil slots
+//   lam*             radius 1  gather of C*
+//   C  = w dF/dpsi   radius 1  at psi^s, w = dt/2 mu + dt lam*
+//   lambda^s         the tile  mu + lam* + gather of C + the seed
+// (a gather at a node reads contributions and psi within one node, the
+// boundary ghosts included).  All reads from global memory happen in the
+// first stage, in unrolled loops, so that they are in flight together.
+// Halo values are recomputed by every CTA that needs them with the same
+// arithmetic, so a node's value does not depend on the tile that forms it;
+// each node's parameter terms are added once, by its owner, the product at
+// psi* first.  lambda^{s+1} and lambda^s are separate fields (CTAs read
+// their neighbours' lambda^{s+1}).
+// ---------------------------------------------------------------------------
+constexpr int kRevTX = 32, kRevTY = 16, kRevHalo = 4, kRevThreads = 256;
+constexpr int kRevW = kRevTX + 2 * kRevHalo, kRevH = kRevTY + 2 * kRevHalo;
+constexpr int kRevF = kRevW * kRevH;  // one field in the frame
+constexpr int kRevO = kRevTX * kRevTY;  // the tile
+constexpr int rev_rsize(int h) { return (kRevTX + 2 * h) * (kRevTY + 2 * h); }
+constexpr int rev_iters(int h) { return (rev_rsize(h) + kRevThreads - 1) / kRevThreads; }
+
+// fields of T: psi^s, psi*, mu, lam*, C[5], multiplier, slope x, y, node
+// wind u, v, terms at psi* [4][tile], class table; then the seeds of the
+// tile (double) and the classes (bytes)
+template <typename T>
+constexpr size_t rev_smem_bytes() {
+    return sizeof(T) * ((size_t)14 * kRevF + 4 * kRevO + FIRE_MAX_CLASSES * 10) +
+           sizeof(double) * kRevO + kRevF;
+}
+
+// the five stencil values of frame position l (global node (x, y)) with the
+// extrapolated ghosts of Sect. 3.1 at the domain boundary (nx, ny >= 2)
+template <typename T>
+__device__ __forceinline__ void rev_stencil(const T *X, int l, int x, int y, int nx, int ny, T &p,
+                                            T &pl, T &pr, T &pd, T &pu) {
+    p = X[l];
+    pl = x > 0 ? X[l - 1] : ghost_value<T>(p, X[l + 1]);
+    pr = x < nx - 1 ? X[l + 1] : ghost_value<T>(p, X[l - 1]);
+    pd = y > 0 ? X[l - kRevW] : ghost_value<T>(p, X[l + kRevW]);
+    pu = y < ny - 1 ? X[l + kRevW] : ghost_value<T>(p, X[l - kRevW]);
+}
+
+// gather of the frame's contributions C ([5][kRevF]) at frame position l,
+// as gather() above
+template <typename T>
+__device__ __forceinline__ T rev_gather(const T *C, const T *X, int l, int x, int y, int nx,
+                                        int ny) {
+    T r = C[P_C * kRevF + l];
+    if (x > 0) r += C[P_R * kRevF + l - 1];
+    if (x < nx - 1) r += C[P_L * kRevF + l + 1];
+    if (y > 0) r += C[P_U * kRevF + l - kRevW];
+    if (y < ny - 1) r += C[P_D * kRevF + l + kRevW];
+    T d0, d1;
+    if (x <= 1) {  // left ghost of row y = ghost(X[y][0], X[y][1])
+        const int b = l - x;
+        ghost_partials<T>(X[b], X[b + 1], d0, d1);
+        r += C[P_L * kRevF + b] * (x == 0 ? d0 : d1);
+    }
+    if (x >= nx - 2) {  // right ghost = ghost(X[y][nx-1], X[y][nx-2])
+        const int b = l + (nx - 1 - x);
+        ghost_partials<T>(X[b], X[b - 1], d0, d1);
+        r += C[P_R * kRevF + b] * (x == nx - 1 ? d0 : d1);
+    }
+    if (y <= 1) {  // bottom ghost of column x = ghost(X[0][x], X[1][x])
+        const int b = l - y * kRevW;
+        ghost_partials<T>(X[b], X[b + kRevW], d0, d1);
+        r += C[P_D * kRevF + b] * (y == 0 ? d0 : d1);
+    }
+    if (y >= ny - 2) {  // top ghost = ghost(X[ny-1][x], X[ny-2][x])
+        const int b = l + (ny - 1 - y) * kRevW;
+        ghost_partials<T>(X[b], X[b - kRevW], d0, d1);
+        r += C[P_U * kRevF + b] * (y == ny - 1 ? d0 : d1);
+    }
+    return r;
+}
+
+template <typename T>
+struct RevSm {
+    T *pa, *ps, *mu, *ls, *C, *m, *zx, *zy, *un, *vn, *G, *lut;
+    double *seed;
+    unsigned char *cls;
+};
+
+// node inputs of frame position l from the staged fields (the coefficients
+// of a per-node moisture from global memory)
+template <typename T>
+__device__ __forceinline__ void rev_env(const AdjArgs<T> &a, const RevSm<T> &sm, int l, size_t k,
+                                        bool want_d, NodeEnv<T> &e) {
+    if (a.nodeco) {
+        const double *co = a.coef + k * K_N;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) e.co[q] = T(co[q]);
+        if (want_d) {
+            const double *dc = a.dcoef + k * K_N;
+            e.dco[0] = T(dc[K_S0]);
+            e.dco[1] = T(dc[K_R0]);
+            e.dco[2] = T(dc[K_C]);
+            e.dco[3] = T(dc[K_D]);
+        }
+    } else {
+        const T *c = sm.lut + sm.cls[l] * 10;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) e.co[q] = c[q];
+        if (want_d) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) e.dco[q] = c[6 + q];
+        }
+    }
+    e.m = sm.m[l];
+    e.zx = sm.zx[l];
+    e.zy = sm.zy[l];
+    e.un = sm.un[l];
+    e.vn = sm.vn[l];
+}
+
+// the product v J_F^T at frame position l against the field X: its five
+// stencil contributions into C and its parameter terms (multiplier,
+// moisture, node wind) into g[4]
+template <typename T>
+__device__ __forceinline__ void rev_vjp(const AdjArgs<T> &a, const RevSm<T> &sm, const T *X,
+                                        int l, int x, int y, size_t k, T v, T g[4]) {
+    NodeEnv<T> e;
+    rev_env(a, sm, l, k, true, e);
+    T p, pl, pr, pd, pu;
+    rev_stencil(X, l, x, y, a.nx, a.ny, p, pl, pr, pd, pu);
+    Partials<T> o;
+    node_partials<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e, o);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sm.C[q * kRevF + l] = v * o.dpsi[q];
+    g[0] = v * o.dm;
+    g[1] = v * (o.dS0 * e.dco[0] + o.dR0 * e.dco[1] + o.dc * e.dco[2] + o.dd * e.dco[3]);
+    g[2] = v * o.dun;
+    g[3] = v * o.dvn;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char rev_sm[];
+    RevSm<T> sm;
+    sm.seed = reinterpret_cast<double *>(rev_sm);
+    T *f = reinterpret_cast<T *>(sm.seed + kRevO);
+    sm.pa = f;
+    sm.ps = f + kRevF;
+    sm.mu = f + 2 * kRevF;
+    sm.ls = f + 3 * kRevF;
+    sm.C = f + 4 * kRevF;
+    sm.m = f + 9 * kRevF;
+    sm.zx = f + 10 * kRevF;
+    sm.zy = f + 11 * kRevF;
+    sm.un = f + 12 * kRevF;
+    sm.vn = f + 13 * kRevF;
+    sm.G = f + 14 * kRevF;
+    sm.lut = sm.G + 4 * kRevO;
+    sm.cls = reinterpret_cast<unsigned char *>(sm.lut + FIRE_MAX_CLASSES * 10);
+    const int nx = a.nx, ny = a.ny;
+    const int x0 = blockIdx.x * kRevTX, y0 = blockIdx.y * kRevTY;
+    const int tid = threadIdx.x;
+    // a region of radius h around the tile, clipped to the domain: position
+    // e -> global (x, y), frame index l
+    auto region = [&](int h, int e, int &x, int &y, int &l) -> bool {
+        const int w = kRevTX + 2 * h;
+        x = x0 - h + e % w;
+        y = y0 - h + e / w;
+        l = (y - y0 + kRevHalo) * kRevW + (x - x0 + kRevHalo);
+        return e < rev_rsize(h) && x >= 0 && x < nx && y >= 0 && y < ny;
+    };
+    // ---- every read from global memory
+    if (!a.nodeco) {
+        for (int q = tid; q < a.ncls * 10; q += kRevThreads) {
+            const int c = q / 10, m = q % 10;
+            const int src = m < 6 ? m : (m == 6 ? K_S0 : m == 7 ? K_R0 : m == 8 ? K_C : K_D);
+            sm.lut[q] = T((m < 6 ? a.coef : a.dcoef)[(size_t)c * K_N + src]);
+        }
+    }
+    // each loop loads into registers first and stores to shared memory
+    // after, so that its loads are in flight together
+    {
+        constexpr int I4 = rev_iters(4);
+        T v[I4];
+        int ls[I4];
+#pragma unroll
+        for (int it = 0; it < I4; ++it) {
+            int x, y;
+            ls[it] = -1;
+            if (region(4, tid + it * kRevThreads, x, y, ls[it]))
+                v[it] = a.pa[(size_t)y * nx + x];
+            else
+                ls[it] = -1;
+        }
+#pragma unroll
+        for (int it = 0; it < I4; ++it)
+            if (ls[it] >= 0) sm.pa[ls[it]] = v[it];
+    }
+    {
+        constexpr int I3 = rev_iters(3);
+        T vm[I3], vx[I3], vy[I3], vu[I3], vv[I3];
+        int vc[I3], ls[I3];
+#pragma unroll
+        for (int it = 0; it < I3; ++it) {
+            int x, y;
+            if (region(3, tid + it * kRevThreads, x, y, ls[it])) {
+                const size_t k = (size_t)y * nx + x;
+                vc[it] = a.fuel[k];
+                vm[it] = a.mult ? a.mult[k] : T(1);
+                vx[it] = a.zx[k];
+                vy[it] = a.zy[k];
+                vu[it] = a.unv[2 * k];
+                vv[it] = a.unv[2 * k + 1];
+            } else {
+                ls[it] = -1;
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < I3; ++it) {
+            const int l = ls[it];
+            if (l < 0) continue;
+            sm.cls[l] = (unsigned char)(vc[it] > a.ncls - 1 ? a.ncls - 1 : vc[it]);
+            sm.m[l] = vm[it];
+            sm.zx[l] = vx[it];
+            sm.zy[l] = vy[it];
+            sm.un[l] = vu[it];
+            sm.vn[l] = vv[it];
+        }
+    }
+    // mu (radius 2) and the seeds of the tile; the crossing test of a node
+    // (crossed(), its reads issued together) needs psi^s, psi^{s+1}, both
+    // ignition times and the observation
+    auto cross_seed = [&](double t0, double ti, double to, T p0, T p1, double tlo, double thi,
+                          double &q0, double &q1, double &rr) -> bool {
+        if (!inf_bits(t0) || !finite_bits(ti) || !finite_bits(to)) return false;
+        if (!(p0 > T(0) && p1 <= T(0))) return false;
+        if (!(ti >= tlo && ti <= thi)) return false;
+        q0 = (double)p0;
+        q1 = (double)p1;
+        rr = a.dJdt ? to : ti - to;
+        return true;
+    };
+    const double *tobs = a.dJdt ? a.dJdt : a.tobs;
+    {
+        constexpr int I2 = rev_iters(2);
+        T vl[I2], p0[I2], p1[I2];
+        double t0[I2], ti[I2], to[I2];
+        int ls[I2];
+#pragma unroll
+        for (int it = 0; it < I2; ++it) {
+            int x, y;
+            if (region(2, tid + it * kRevThreads, x, y, ls[it])) {
+                const size_t k = (size_t)y * nx + x;
+                vl[it] = a.lin[k];
+                t0[it] = a.tign0[k];
+                ti[it] = a.tign[k];
+                to[it] = tobs[k];
+                p0[it] = a.pa[k];
+                p1[it] = a.pb[k];
+            } else {
+                ls[it] = -1;
+            }
+        }
+        const double tlo = a.tsp[0], thi = a.tsp[1];
+#pragma unroll
+        for (int it = 0; it < I2; ++it) {
+            if (ls[it] < 0) continue;
+            T mu = vl[it];
+            double q0, q1, r;
+            if (cross_seed(t0[it], ti[it], to[it], p0[it], p1[it], tlo, thi, q0, q1, r)) {
+                const double den = q0 - q1;
+                mu = T((double)mu + r * a.dt * q0 / (den * den));
+            }
+            sm.mu[ls[it]] = mu;
+        }
+    }
+    {
+        constexpr int I0 = (kRevO + kRevThreads - 1) / kRevThreads;
+        T p0[I0], p1[I0];
+        double t0[I0], ti[I0], to[I0];
+        bool in[I0];
+#pragma unroll
+        for (int it = 0; it < I0; ++it) {
+            const int e = tid + it * kRevThreads;
+            const int x = x0 + e % kRevTX, y = y0 + e / kRevTX;
+            in[it] = x < nx && y < ny;
+            if (in[it]) {
+                const size_t k = (size_t)y * nx + x;
+                t0[it] = a.tign0[k];
+                ti[it] = a.tign[k];
+                to[it] = tobs[k];
+                p0[it] = a.pa[k];
+                p1[it] = a.pb[k];
+            }
+        }
+        const double tlo = a.tsp[0], thi = a.tsp[1];
+#pragma unroll
+        for (int it = 0; it < I0; ++it) {
+            double sd = 0.0, q0, q1, r;
+            if (in[it] && cross_seed(t0[it], ti[it], to[it], p0[it], p1[it], tlo, thi, q0, q1, r)) {
+                const double den = q0 - q1;
+                sd = r * (-a.dt * q1 / (den * den));
+            }
+            sm.seed[tid + it * kRevThreads] = sd;
+        }
+    }
+    __syncthreads();
+    // ---- psi* = psi^s + dt F(psi^s) (radius 3)
+    for (int e = tid; e < rev_rsize(3); e += kRevThreads) {
+        int x, y, l;
+        if (!region(3, e, x, y, l)) continue;
+        NodeEnv<T> en;
+        rev_env(a, sm, l, (size_t)y * nx + x, false, en);
+        T p, pl, pr, pd, pu;
+        rev_stencil(sm.pa, l, x, y, nx, ny, p, pl, pr, pd, pu);
+        const T F = rhs_vals<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, en.co,
+                                en.m, en.un, en.vn, en.zx, en.zy);
+        sm.ps[l] = p + a.dtT * F;
+    }
+    __syncthreads();
+    // ---- the product at psi* with v = dt/2 mu (radius 2)
+    for (int e = tid; e < rev_rsize(2); e += kRevThreads) {
+        int x, y, l;
+        if (!region(2, e, x, y, l)) continue;
+        T g[4];
+        rev_vjp(a, sm, sm.ps, l, x, y, (size_t)y * nx + x, a.hdtT * sm.mu[l], g);
+        const int ox = x - x0, oy = y - y0;
+        if (ox >= 0 && ox < kRevTX && oy >= 0 && oy < kRevTY) {
+            const int o = oy * kRevTX + ox;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sm.G[q * kRevO + o] = g[q];
+        }
+    }
+    __syncthreads();
+    // ---- lam* (radius 1)
+    for (int e = tid; e < rev_rsize(1); e += kRevThreads) {
+        int x, y, l;
+        if (region(1, e, x, y, l)) sm.ls[l] = rev_gather(sm.C, sm.ps, l, x, y, nx, ny);
+    }
+    __syncthreads();
+    // ---- the product at psi^s with w = dt/2 mu + dt lam* (radius 1); the
+    // owner adds both products' parameter terms
+    for (int e = tid; e < rev_rsize(1); e += kRevThreads) {
+        int x, y, l;
+        if (!region(1, e, x, y, l)) continue;
+        const size_t k = (size_t)y * nx + x;
+        T g[4];
+        rev_vjp(a, sm, sm.pa, l, x, y, k, a.hdtT * sm.mu[l] + a.dtT * sm.ls[l], g);
+        const int ox = x - x0, oy = y - y0;
+        if (ox >= 0 && ox < kRevTX && oy >= 0 && oy < kRevTY) {
+            const int o = oy * kRevTX + ox;
+            const int nq = a.wind_grads ? 4 : 2;
+            typename GAcc<T>::t acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nq) acc[q] = a.acc[q * a.n + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q >= nq) continue;
+                GAcc<T>::add(acc[q], sm.G[q * kRevO + o]);
+                GAcc<T>::add(acc[q], g[q]);
+                a.acc[q * a.n + k] = acc[q];
+            }
+        }
+    }
+    __syncthreads();
+    // ---- lambda^s on the tile
+    for (int e = tid; e < kRevO; e += kRevThreads) {
+        const int x = x0 + e % kRevTX, y = y0 + e / kRevTX;
+        if (x >= nx || y >= ny) continue;
+        const int l = (y - y0 + kRevHalo) * kRevW + (x - x0 + kRevHalo);
+        T lam = sm.mu[l] + sm.ls[l] + rev_gather(sm.C, sm.pa, l, x, y, nx, ny);
+        const double sd = sm.seed[e];
+        if (sd != 0.0) lam = T((double)lam + sd);
+        a.lout[(size_t)y * nx + x] = lam;
+    }
+}
+
+// the FP32 sums of the run: a seed (the heat misfit's direct moisture term)
+// into a compensated pair, and the pairs back to double at the end
+__global__ void k_acc_seed(double *g, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const double x = g[k];
+        const float s = (float)x;
+        reinterpret_cast<float2 *>(g)[k] = make_float2(s, (float)((double)s - x));
+    }
+}
+__global__ void k_acc_final(double *g, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const float2 p = reinterpret_cast<const float2 *>(g)[k];
+        g[k] = (double)p.x - (double)p.y;
     }
 }
 
@@ -397,7 +856,8 @@ __global__ void k_adj_finish(const AdjArgs<T> a) {
 // face sums the node gradients times the weights the forward gave it.
 // One thread per face; the candidate nodes are those within two cells.
 template <typename T>
-__global__ void k_adj_wind(const AdjArgs<T> a, double *gu, double *gv) {
+__global__ void k_adj_wind(const AdjArgs<T> a, const double *gun, const double *gvn, double *gu,
+                           double *gv) {
     const int nu = a.nya * (a.nxa + 1), nv = (a.nya + 1) * a.nxa;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nu + nv; f += gridDim.x * blockDim.x) {
         const bool isu = f < nu;
@@ -417,7 +877,7 @@ __global__ void k_adj_wind(const AdjArgs<T> a, double *gu, double *gv) {
             if (j0 == J) cy += (double)(T(1) - wy);
             if (j1 == J) cy += (double)wy;
             if (cy == 0.0) continue;
-            const double *gn = (isu ? a.gun : a.gvn) + (size_t)j * a.nx;
+            const double *gn = (isu ? gun : gvn) + (size_t)j * a.nx;
             for (int i = i_lo; i < i_hi; ++i) {
                 const T xr = (T(i) + T(0.5)) / T(a.srx);
                 int i0, i1;
@@ -783,9 +1243,10 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         off += align_up(bytes);
         return o;
     };
-    const size_t o_ck = take((size_t)nseg * n * E);
-    const size_t o_ring = take((size_t)(K + 1) * n * E);
-    const size_t o_pstar = take(n * E);
+    // checkpoints; with K = 1 every state psi^0..psi^nsteps
+    const size_t o_ck = take((size_t)(K == 1 ? nsteps + 1 : nseg) * n * E);
+    // the recomputed states of a segment (none when every state is kept)
+    const size_t o_ring = take(K > 1 ? (size_t)(K + 1) * n * E : 0);
     const size_t o_F = take(2 * n * E);
     const size_t o_t0 = take(n * sizeof(double));
     const size_t o_ts = take(n * sizeof(double));
@@ -799,8 +1260,11 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     const size_t o_nco = take(nodeco ? n * K_N * sizeof(double) : 0);
     const size_t o_F0 = take(qobs ? n * E : 0);                   // F at the start (heat)
     const size_t o_Qr = take(qobs ? 2 * na * sizeof(double) : 0);  // Q, residual (heat)
-    const size_t o_lam = take(3 * n * E);
-    const size_t o_C = take(10 * n * E);
+    const size_t o_lam = take(2 * n * E);  // lambda^{s+1}, lambda^s
+    // the unfused FP64 step: psi*, mu, lam* and two sets of stencil
+    // contributions
+    const bool fused = sizeof(T) == 4;
+    const size_t o_mid = take(fused ? 0 : 13 * n * E);
     const size_t o_g = take(4 * n * sizeof(double));
     const size_t o_unv = take(2 * n * E);
     const size_t nu = (size_t)c_nya(c) * (c_nxa(c) + 1), nv = (size_t)(c_nya(c) + 1) * c_nxa(c);
@@ -813,7 +1277,6 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     unsigned char *ws = static_cast<unsigned char *>(wsv);
     T *ck = reinterpret_cast<T *>(ws + o_ck);
     T *ring = reinterpret_cast<T *>(ws + o_ring);
-    T *pstar = reinterpret_cast<T *>(ws + o_pstar);
     T *Fs = reinterpret_cast<T *>(ws + o_F);
     double *tign0 = reinterpret_cast<double *>(ws + o_t0);
     double *tsc = reinterpret_cast<double *>(ws + o_ts);
@@ -822,6 +1285,47 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     double *Jdev = reinterpret_cast<double *>(ws + o_small);
     int *stdev = reinterpret_cast<int *>(ws + o_small + 8);
     double *part = reinterpret_cast<double *>(ws + o_small + 16);
+
+    // launches replayed from graphs the context keeps (two slots, each
+    // with the key of what its launches read; captured on first use, issued
+    // directly if the capture is refused)
+    unsigned long long *keys = nullptr;
+    cudaGraphExec_t *graphs = ctx_adjoint_graphs(c, &keys);
+    auto mix = [](unsigned long long h, unsigned long long x) {
+        return (h ^ x) * 0x100000001b3ULL + (h >> 29);
+    };
+    auto replay = [&](int slot, unsigned long long key, auto &&issue) -> int {
+        if (!graphs[slot] || keys[slot] != key) {
+            if (graphs[slot]) {
+                ADJ_CHECK(cudaStreamSynchronize(st));  // the old graph may be in flight
+                cudaGraphExecDestroy(graphs[slot]);
+                graphs[slot] = nullptr;
+            }
+            cudaStream_t cs;
+            ADJ_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t gr = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                e = issue(cs);
+                cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs[slot], gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) {
+                record_cuda_error(e, "capture of adjoint launches");
+                cudaGetLastError();
+                graphs[slot] = nullptr;
+                keys[slot] = 0;
+                ADJ_CHECK(issue(st));
+                return FIRE_OK;
+            }
+            keys[slot] = key;
+        }
+        ADJ_CHECK(cudaGraphLaunch(graphs[slot], st));
+        return FIRE_OK;
+    };
 
     StepArgs sa;
     ctx_step_args(c, cur, u, v, dt, nullptr, nullptr, sa);
@@ -840,8 +1344,53 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     ADJ_CHECK(cudaMemcpyAsync(tdev, times.data(), (nsteps + 1) * sizeof(double),
                               cudaMemcpyHostToDevice, st));
 
+    // the step kernel the context uses, on a state it does not own
+    auto launch_step_kernel = [&](const StepArgs &ra, cudaStream_t cs) -> cudaError_t {
+        return variant == FIRE_KERNEL_MARCH   ? launch_march<T>(ra, cs)
+               : variant == FIRE_KERNEL_WARP  ? launch_warp<T>(ra, cs)
+               : variant == FIRE_KERNEL_WARP4 ? (sizeof(T) == 4 ? launch_warp4(ra, cs)
+                                                                : cudaErrorInvalidValue)
+                                              : launch_step<T>(ra, cs);
+    };
     // forward with checkpoints
-    for (int q = 0; q < nseg; ++q) {
+    if (K == 1) {
+        // every state is a checkpoint: each step reads and writes its slots
+        // directly (the context's fraction, t_i, time and status buffers as
+        // fire_run uses them), then the last state goes back to the context
+        int pc, pv, a1, a2, a3, a4, a5, a6, a7, pcur;
+        double tt;
+        ctx_info(c, &pc, &pv, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &pcur, &tt);
+        unsigned long long fk = 0x84222325cbf29ce4ULL;
+        unsigned long long dtb;
+        memcpy(&dtb, &dt, sizeof dtb);
+        const void *fp[] = {ws, u, v, sa.mult, sa.coef, sa.fuel, sa.dzdy, sa.dzdx, sa.tign,
+                            sa.nco[0], moist};
+        for (const void *q : fp) fk = mix(fk, (unsigned long long)(uintptr_t)q);
+        fk = mix(mix(mix(mix(mix(fk, dtb), (unsigned long long)nsteps), (unsigned long long)pcur),
+                     (unsigned long long)variant),
+                 (unsigned long long)(sa.kx * 65536 + sa.ky));
+        r = replay(1, fk, [&](cudaStream_t cs) -> cudaError_t {
+            StepArgs now;
+            ctx_step_args(c, pcur, u, v, dt, nullptr, nullptr, now);
+            cudaError_t e = cudaMemcpyAsync(ck, now.psi_in, n * E, cudaMemcpyDeviceToDevice, cs);
+            for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+                StepArgs ra;
+                ctx_step_args(c, (pcur + s) & 1, u, v, dt, nullptr, nullptr, ra);
+                ra.psi_in = ck + (size_t)s * n;
+                ra.psi_out = ck + (size_t)(s + 1) * n;
+                e = launch_step_kernel(ra, cs);
+            }
+            StepArgs fin;
+            ctx_step_args(c, (pcur + nsteps) & 1, u, v, dt, nullptr, nullptr, fin);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(const_cast<void *>(fin.psi_in), ck + (size_t)nsteps * n,
+                                    n * E, cudaMemcpyDeviceToDevice, cs);
+            return e;
+        });
+        if (r) return r;
+        ctx_advance(c, nsteps, dt);
+    }
+    for (int q = 0; q < (K == 1 ? 0 : nseg); ++q) {
         StepArgs now;
         int pc, pv, a1, a2, a3, a4, a5, a6, a7, pcur;
         double tt;
@@ -895,11 +1444,14 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         return FIRE_OK;
     }
 
+    // lambda ping-pongs between lam and lam + n, starting in lam; the
+    // parameter sums are four fields of n doubles (FP64), or of n
+    // compensated float pairs in the same bytes (FP32), turned into doubles
+    // in place after the sweep
     T *lam = reinterpret_cast<T *>(ws + o_lam);
-    T *mu = lam + n, *ls = lam + 2 * n;
-    T *C1 = reinterpret_cast<T *>(ws + o_C), *C2 = C1 + 5 * n;
     double *gm = reinterpret_cast<double *>(ws + o_g);
     double *gM = gm + n, *gun = gm + 2 * n, *gvn = gm + 3 * n;
+    static_assert(sizeof(typename GAcc<T>::t) == sizeof(double), "sums in place of doubles");
     ADJ_CHECK(cudaMemsetAsync(lam, 0, n * E, st));
     ADJ_CHECK(cudaMemsetAsync(gm, 0, 4 * n * sizeof(double), st));
     ADJ_CHECK(cudaMemsetAsync(Fs, 0, 2 * n * E, st));
@@ -930,13 +1482,8 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     a.tobs = tobs;
     a.dJdt = nullptr;
     a.dt = dt;
-    a.lam = lam;
-    a.mu = mu;
-    a.ls = ls;
-    a.gm = gm;
-    a.gM = gM;
-    a.gun = gun;
-    a.gvn = gvn;
+    a.acc = reinterpret_cast<typename GAcc<T>::t *>(gm);
+    a.wind_grads = (g_u || g_v) ? 1 : 0;
     a.nx = nx;
     a.ny = ny;
     a.nxa = sa.nxa;
@@ -952,7 +1499,6 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     a.dtT = T(dt);
     a.hdtT = T(0.5 * dt);
     a.n = n;
-    a.pstar = pstar;
 
     int dev = 0, sms = 0;
     ADJ_CHECK(cudaGetDevice(&dev));
@@ -980,9 +1526,53 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         k_heat_gather<T><<<grid, kAdjThreads, 0, st>>>(h);
         k_heat_ghosts<T><<<1, 1, 0, st>>>(h);
         k_heat_lambda<T><<<grid, kAdjThreads, 0, st>>>(h.lamd, lam, n);
+        if (sizeof(T) == 4) k_acc_seed<<<grid, kAdjThreads, 0, st>>>(gM, n);
         ADJ_CHECK(cudaGetLastError());
         a.dJdt = h.dJdt;
     }
+
+    // the reverse steps: tiles of the fused kernel, lambda^{s+1} in
+    // lam + (r & 1) n for the r-th reverse step of a run of them
+    if constexpr (sizeof(T) == 4) {
+        static bool rev_attr = false;
+        if (!rev_attr) {
+            ADJ_CHECK(cudaFuncSetAttribute(k_adj_step<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)rev_smem_bytes<T>()));
+            rev_attr = true;
+        }
+    }
+    const dim3 rgrid((nx + kRevTX - 1) / kRevTX, (ny + kRevTY - 1) / kRevTY);
+    T *mid = reinterpret_cast<T *>(ws + o_mid);
+    auto reverse = [&](AdjArgs<T> &b, const T *pa, const T *pb, const double *tsp, int r,
+                       cudaStream_t cs) {
+        b.pa = pa;
+        b.pb = pb;
+        b.tsp = tsp;
+        b.lin = lam + (size_t)(r & 1) * n;
+        b.lout = lam + (size_t)((r + 1) & 1) * n;
+        if constexpr (sizeof(T) == 4) {
+            k_adj_step<T><<<rgrid, kRevThreads, rev_smem_bytes<T>(), cs>>>(b);
+        } else {
+            T *C1 = mid + 3 * n, *C2 = mid + 8 * n;
+            b.pstar = mid;
+            b.mu = mid + n;
+            b.ls = mid + 2 * n;
+            b.X = nullptr;
+            b.Cin = nullptr;
+            b.Cout = nullptr;
+            k_adj_stage1<T><<<grid, kAdjThreads, 0, cs>>>(b);
+            b.X = b.pstar;
+            b.Cout = C1;
+            k_adj_vjp_star<T><<<grid, kAdjThreads, 0, cs>>>(b);
+            b.X = b.pa;
+            b.Cin = C1;
+            b.Cout = C2;
+            k_adj_vjp_n<T><<<grid, kAdjThreads, 0, cs>>>(b);
+            b.Cin = C2;
+            k_adj_finish<T><<<grid, kAdjThreads, 0, cs>>>(b);
+        }
+    };
 
     // One segment: ring slot 0 holds its checkpoint and tseg its step times,
     // so every segment of a given length issues the same launches: the
@@ -1003,38 +1593,19 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
             ra.t_in = tseg + j;
             ra.t_out = tseg + K + 1;
             ra.dt = dt;
-            cudaError_t e = variant == FIRE_KERNEL_MARCH   ? launch_march<T>(ra, cs)
-                            : variant == FIRE_KERNEL_WARP  ? launch_warp<T>(ra, cs)
-                            : variant == FIRE_KERNEL_WARP4 ? (sizeof(T) == 4 ? launch_warp4(ra, cs)
-                                                                             : cudaErrorInvalidValue)
-                                                           : launch_step<T>(ra, cs);
+            cudaError_t e = launch_step_kernel(ra, cs);
             if (e != cudaSuccess) return e;
         }
         AdjArgs<T> b = a;
-        for (int j = len - 1; j >= 0; --j) {
-            b.pa = ring + (size_t)j * n;
-            b.pb = ring + (size_t)(j + 1) * n;
-            b.tsp = tseg + j;
-            b.X = nullptr;
-            b.Cin = nullptr;
-            b.Cout = nullptr;
-            k_adj_stage1<T><<<grid, kAdjThreads, 0, cs>>>(b);
-            b.X = pstar;
-            b.Cout = C1;
-            k_adj_vjp_star<T><<<grid, kAdjThreads, 0, cs>>>(b);
-            b.X = b.pa;
-            b.Cin = C1;
-            b.Cout = C2;
-            k_adj_vjp_n<T><<<grid, kAdjThreads, 0, cs>>>(b);
-            b.Cin = C2;
-            k_adj_finish<T><<<grid, kAdjThreads, 0, cs>>>(b);
+        int rr = 0;
+        for (int j = len - 1; j >= 0; --j, ++rr)
+            reverse(b, ring + (size_t)j * n, ring + (size_t)(j + 1) * n, tseg + j, rr, cs);
+        // every segment starts with lambda in lam
+        if (len & 1) {
+            cudaError_t e = cudaMemcpyAsync(lam, lam + n, n * E, cudaMemcpyDeviceToDevice, cs);
+            if (e != cudaSuccess) return e;
         }
         return cudaGetLastError();
-    };
-    unsigned long long *keys = nullptr;
-    cudaGraphExec_t *graphs = ctx_adjoint_graphs(c, &keys);
-    auto mix = [](unsigned long long h, unsigned long long x) {
-        return (h ^ x) * 0x100000001b3ULL + (h >> 29);
     };
     unsigned long long key0 = 0xcbf29ce484222325ULL;
     const void *ptrs[] = {ws, u, v, tobs, qobs, sa.mult, sa.coef, sa.fuel, sa.dzdy, sa.dzdx, sa.tign,
@@ -1045,51 +1616,40 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     key0 = mix(mix(mix(mix(mix(key0, dtb), (unsigned long long)K), (unsigned long long)n),
                    (unsigned long long)variant),
                (unsigned long long)(sa.kx * 65536 + sa.ky));
-    key0 = mix(key0, (unsigned long long)grid);
-    for (int q = nseg - 1; q >= 0; --q) {
+    key0 = mix(mix(key0, (unsigned long long)grid), (unsigned long long)a.wind_grads);
+    if (K == 1) {
+        // every state is a checkpoint: the reverse steps read them, nothing
+        // is recomputed; the sweep is one graph
+        r = replay(0, mix(mix(key0, (unsigned long long)nsteps), 0x5eedULL),
+                   [&](cudaStream_t cs) -> cudaError_t {
+                       AdjArgs<T> b = a;
+                       for (int s = nsteps - 1, rr = 0; s >= 0; --s, ++rr)
+                           reverse(b, ck + (size_t)s * n, ck + (size_t)(s + 1) * n, tdev + s, rr,
+                                   cs);
+                       return cudaGetLastError();
+                   });
+        if (r) return r;
+    }
+    for (int q = K == 1 ? -1 : nseg - 1; q >= 0; --q) {
         const int s0 = q * K, s1 = (q + 1) * K <= nsteps ? (q + 1) * K : nsteps;
         const int len = s1 - s0;
         ADJ_CHECK(cudaMemcpyAsync(ring, ck + (size_t)q * n, n * E, cudaMemcpyDeviceToDevice, st));
         ADJ_CHECK(cudaMemcpyAsync(tseg, tdev + s0, (len + 1) * sizeof(double),
                                   cudaMemcpyDeviceToDevice, st));
         ADJ_CHECK(cudaMemcpyAsync(tsc, tign0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        const int slot = len == K ? 0 : 1;
-        const unsigned long long key = mix(key0, (unsigned long long)len);
-        if (!graphs[slot] || keys[slot] != key) {
-            if (graphs[slot]) {
-                ADJ_CHECK(cudaStreamSynchronize(st));  // the old graph may be in flight
-                cudaGraphExecDestroy(graphs[slot]);
-                graphs[slot] = nullptr;
-            }
-            cudaStream_t cs;
-            ADJ_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-            cudaGraph_t gr = nullptr;
-            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                e = issue_segment(len, cs);
-                cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
-                if (e == cudaSuccess) e = e2;
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs[slot], gr, 0);
-            if (gr) cudaGraphDestroy(gr);
-            cudaStreamDestroy(cs);
-            if (e != cudaSuccess) {
-                // capture refused: issue the segment directly
-                record_cuda_error(e, "capture of an adjoint segment");
-                cudaGetLastError();
-                graphs[slot] = nullptr;
-                ADJ_CHECK(issue_segment(len, st));
-                continue;
-            }
-            keys[slot] = key;
-        }
-        ADJ_CHECK(cudaGraphLaunch(graphs[slot], st));
+        r = replay(len == K ? 0 : 1, mix(key0, (unsigned long long)len),
+                   [&](cudaStream_t cs) { return issue_segment(len, cs); });
+        if (r) return r;
+    }
+    if (sizeof(T) == 4) {
+        k_acc_final<<<grid, kAdjThreads, 0, st>>>(gm, (a.wind_grads ? 4 : 2) * n);
+        ADJ_CHECK(cudaGetLastError());
     }
     if (g_u || g_v) {
         double *tmp = reinterpret_cast<double *>(ws + o_wind);
         double *gu = g_u ? g_u : tmp, *gv = g_v ? g_v : tmp + nu;
         const int wg = (int)((nu + nv + kAdjThreads - 1) / kAdjThreads);
-        k_adj_wind<T><<<wg, kAdjThreads, 0, st>>>(a, gu, gv);
+        k_adj_wind<T><<<wg, kAdjThreads, 0, st>>>(a, gun, gvn, gu, gv);
         ADJ_CHECK(cudaGetLastError());
     }
     if (g_mult)

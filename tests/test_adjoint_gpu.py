@@ -224,15 +224,21 @@ def test_autograd_function(pkg):
     m2.close()
 
 
-def test_misfit_only_call_advances_like_run(pkg):
+@pytest.mark.parametrize("prec,nsteps,ckpt,grads", [("fp32", 30, 20, False),
+                                                    ("fp32", 31, 1, False),
+                                                    ("fp64", 30, 1, True),
+                                                    ("fp32", 29, 1, True)])
+def test_misfit_only_call_advances_like_run(pkg, prec, nsteps, ckpt, grads):
+    """The adjoint call leaves the context where fire_run leaves it, also
+    when every state is kept (its forward then launches the step kernel on
+    the checkpoint slots itself)."""
     import torch
     w = small_case(seed=7)
-    nsteps = 30
     tobs = observations(w, nsteps)
-    a = pkg.FireModel.from_workload(w, precision="fp32")
-    b = pkg.FireModel.from_workload(w, precision="fp32")
+    a = pkg.FireModel.from_workload(w, precision=prec)
+    b = pkg.FireModel.from_workload(w, precision=prec)
     u, v = a.wind(w.u, w.v)
-    J, *_ = a.adjoint(u, v, w.dt, nsteps, tobs, grads=False)
+    J, *_ = a.adjoint(u, v, w.dt, nsteps, tobs, ckpt_every=ckpt, grads=grads)
     b.run(nsteps, u, v, w.dt)
     sa, sb = a.state(), b.state()
     for x, y in zip(sa[:3], sb[:3]):
