@@ -456,8 +456,9 @@ __global__ void k_adj_finish(const AdjArgs<T> a) {
 // ---------------------------------------------------------------------------
 // The reverse step of FP32 in one launch (memory latency and launch gaps,
 // not arithmetic, bound the unfused FP32 step).  A CTA owns a tile of
-// kRevTX x kRevTY nodes and forms, in shared memory, in the frame of the
-// tile with a halo of kRevHalo nodes, what its nodes' lambda^s needs:
+// kRevTX x kRevTY nodes and forms in shared memory what its nodes'
+// lambda^s needs, each field in a frame of the tile with the halo radius
+// that field needs:
 //   psi^s            radius 4  (read)
 //   node inputs      radius 3  class, multiplier, slope, node wind (read)
 //   mu               radius 2  lambda^{s+1} + the seed of crossing nodes
@@ -468,71 +469,72 @@ __global__ void k_adj_finish(const AdjArgs<T> a) {
 //   lambda^s         the tile  mu + lam* + gather of C + the seed
 // (a gather at a node reads contributions and psi within one node, the
 // boundary ghosts included).  All reads from global memory happen in the
-// first stage, in unrolled loops, so that they are in flight together.
-// Halo values are recomputed by every CTA that needs them with the same
-// arithmetic, so a node's value does not depend on the tile that forms it;
-// each node's parameter terms are added once, by its owner, the product at
-// psi* first.  lambda^{s+1} and lambda^s are separate fields (CTAs read
-// their neighbours' lambda^{s+1}).
+// first stage, in unrolled loops that load into registers before they
+// store, so that the loads are in flight together.  Halo values are
+// recomputed by every CTA that needs them with the same arithmetic, so a
+// node's value does not depend on the tile that forms it; each node's
+// parameter terms are added once, by its owner, the product at psi* first.
+// lambda^{s+1} and lambda^s are separate fields (CTAs read their
+// neighbours' lambda^{s+1}).
 // ---------------------------------------------------------------------------
-constexpr int kRevTX = 32, kRevTY = 16, kRevHalo = 4, kRevThreads = 256;
-constexpr int kRevW = kRevTX + 2 * kRevHalo, kRevH = kRevTY + 2 * kRevHalo;
-constexpr int kRevF = kRevW * kRevH;  // one field in the frame
+constexpr int kRevTX = 32, kRevTY = 16, kRevThreads = 256;
 constexpr int kRevO = kRevTX * kRevTY;  // the tile
+constexpr int rev_w(int h) { return kRevTX + 2 * h; }
 constexpr int rev_rsize(int h) { return (kRevTX + 2 * h) * (kRevTY + 2 * h); }
 constexpr int rev_iters(int h) { return (rev_rsize(h) + kRevThreads - 1) / kRevThreads; }
 
-// fields of T: psi^s, psi*, mu, lam*, C[5], multiplier, slope x, y, node
-// wind u, v, terms at psi* [4][tile], class table; then the seeds of the
-// tile (double) and the classes (bytes)
+// shared memory: the seeds of the tile (double); fields of T: psi^s (radius
+// 4), psi* and the multiplier, slope x, y, node wind u, v (radius 3), mu and
+// the five contribution slots (radius 2), lam* (radius 1), the terms at psi*
+// [4][tile], the class table [ncls][10]; the classes (bytes, radius 3)
 template <typename T>
-constexpr size_t rev_smem_bytes() {
-    return sizeof(T) * ((size_t)14 * kRevF + 4 * kRevO + FIRE_MAX_CLASSES * 10) +
-           sizeof(double) * kRevO + kRevF;
+size_t rev_smem_bytes(int ncls) {
+    const size_t nT = (size_t)rev_rsize(4) + 6 * rev_rsize(3) + 6 * rev_rsize(2) + rev_rsize(1) +
+                      4 * kRevO + (size_t)ncls * 10;
+    return sizeof(double) * kRevO + sizeof(T) * nT + rev_rsize(3);
 }
 
-// the five stencil values of frame position l (global node (x, y)) with the
-// extrapolated ghosts of Sect. 3.1 at the domain boundary (nx, ny >= 2)
+// the five stencil values of frame position l (frame row width W, global
+// node (x, y)) with the extrapolated ghosts of Sect. 3.1 at the domain
+// boundary (nx, ny >= 2)
 template <typename T>
-__device__ __forceinline__ void rev_stencil(const T *X, int l, int x, int y, int nx, int ny, T &p,
-                                            T &pl, T &pr, T &pd, T &pu) {
+__device__ __forceinline__ void rev_stencil(const T *X, int l, int W, int x, int y, int nx, int ny,
+                                            T &p, T &pl, T &pr, T &pd, T &pu) {
     p = X[l];
     pl = x > 0 ? X[l - 1] : ghost_value<T>(p, X[l + 1]);
     pr = x < nx - 1 ? X[l + 1] : ghost_value<T>(p, X[l - 1]);
-    pd = y > 0 ? X[l - kRevW] : ghost_value<T>(p, X[l + kRevW]);
-    pu = y < ny - 1 ? X[l + kRevW] : ghost_value<T>(p, X[l - kRevW]);
+    pd = y > 0 ? X[l - W] : ghost_value<T>(p, X[l + W]);
+    pu = y < ny - 1 ? X[l + W] : ghost_value<T>(p, X[l - W]);
 }
 
-// gather of the frame's contributions C ([5][kRevF]) at frame position l,
-// as gather() above
+// gather() above on the frames: contributions C at lc (slots F apart, row
+// width Wc), psi X at lx (row width Wx)
 template <typename T>
-__device__ __forceinline__ T rev_gather(const T *C, const T *X, int l, int x, int y, int nx,
-                                        int ny) {
-    T r = C[P_C * kRevF + l];
-    if (x > 0) r += C[P_R * kRevF + l - 1];
-    if (x < nx - 1) r += C[P_L * kRevF + l + 1];
-    if (y > 0) r += C[P_U * kRevF + l - kRevW];
-    if (y < ny - 1) r += C[P_D * kRevF + l + kRevW];
+__device__ __forceinline__ T rev_gather(const T *C, int lc, int Wc, int F, const T *X, int lx,
+                                        int Wx, int x, int y, int nx, int ny) {
+    T r = C[P_C * F + lc];
+    if (x > 0) r += C[P_R * F + lc - 1];
+    if (x < nx - 1) r += C[P_L * F + lc + 1];
+    if (y > 0) r += C[P_U * F + lc - Wc];
+    if (y < ny - 1) r += C[P_D * F + lc + Wc];
     T d0, d1;
     if (x <= 1) {  // left ghost of row y = ghost(X[y][0], X[y][1])
-        const int b = l - x;
-        ghost_partials<T>(X[b], X[b + 1], d0, d1);
-        r += C[P_L * kRevF + b] * (x == 0 ? d0 : d1);
+        ghost_partials<T>(X[lx - x], X[lx - x + 1], d0, d1);
+        r += C[P_L * F + lc - x] * (x == 0 ? d0 : d1);
     }
     if (x >= nx - 2) {  // right ghost = ghost(X[y][nx-1], X[y][nx-2])
-        const int b = l + (nx - 1 - x);
-        ghost_partials<T>(X[b], X[b - 1], d0, d1);
-        r += C[P_R * kRevF + b] * (x == nx - 1 ? d0 : d1);
+        const int o = nx - 1 - x;
+        ghost_partials<T>(X[lx + o], X[lx + o - 1], d0, d1);
+        r += C[P_R * F + lc + o] * (x == nx - 1 ? d0 : d1);
     }
     if (y <= 1) {  // bottom ghost of column x = ghost(X[0][x], X[1][x])
-        const int b = l - y * kRevW;
-        ghost_partials<T>(X[b], X[b + kRevW], d0, d1);
-        r += C[P_D * kRevF + b] * (y == 0 ? d0 : d1);
+        ghost_partials<T>(X[lx - y * Wx], X[lx - y * Wx + Wx], d0, d1);
+        r += C[P_D * F + lc - y * Wc] * (y == 0 ? d0 : d1);
     }
     if (y >= ny - 2) {  // top ghost = ghost(X[ny-1][x], X[ny-2][x])
-        const int b = l + (ny - 1 - y) * kRevW;
-        ghost_partials<T>(X[b], X[b - kRevW], d0, d1);
-        r += C[P_U * kRevF + b] * (y == ny - 1 ? d0 : d1);
+        const int o = ny - 1 - y;
+        ghost_partials<T>(X[lx + o * Wx], X[lx + o * Wx - Wx], d0, d1);
+        r += C[P_U * F + lc + o * Wc] * (y == ny - 1 ? d0 : d1);
     }
     return r;
 }
@@ -544,10 +546,10 @@ struct RevSm {
     unsigned char *cls;
 };
 
-// node inputs of frame position l from the staged fields (the coefficients
-// of a per-node moisture from global memory)
+// node inputs at radius-3 frame position l3 (the coefficients of a per-node
+// moisture from global memory)
 template <typename T>
-__device__ __forceinline__ void rev_env(const AdjArgs<T> &a, const RevSm<T> &sm, int l, size_t k,
+__device__ __forceinline__ void rev_env(const AdjArgs<T> &a, const RevSm<T> &sm, int l3, size_t k,
                                         bool want_d, NodeEnv<T> &e) {
     if (a.nodeco) {
         const double *co = a.coef + k * K_N;
@@ -561,7 +563,7 @@ __device__ __forceinline__ void rev_env(const AdjArgs<T> &a, const RevSm<T> &sm,
             e.dco[3] = T(dc[K_D]);
         }
     } else {
-        const T *c = sm.lut + sm.cls[l] * 10;
+        const T *c = sm.lut + sm.cls[l3] * 10;
 #pragma unroll
         for (int q = 0; q < 6; ++q) e.co[q] = c[q];
         if (want_d) {
@@ -569,27 +571,28 @@ __device__ __forceinline__ void rev_env(const AdjArgs<T> &a, const RevSm<T> &sm,
             for (int q = 0; q < 4; ++q) e.dco[q] = c[6 + q];
         }
     }
-    e.m = sm.m[l];
-    e.zx = sm.zx[l];
-    e.zy = sm.zy[l];
-    e.un = sm.un[l];
-    e.vn = sm.vn[l];
+    e.m = sm.m[l3];
+    e.zx = sm.zx[l3];
+    e.zy = sm.zy[l3];
+    e.un = sm.un[l3];
+    e.vn = sm.vn[l3];
 }
 
-// the product v J_F^T at frame position l against the field X: its five
-// stencil contributions into C and its parameter terms (multiplier,
-// moisture, node wind) into g[4]
+// the product v J_F^T at node (x, y) against X (its stencil at lx, row
+// width Wx): the five stencil contributions into the radius-2 slots at l2
+// and its parameter terms (multiplier, moisture, node wind) into g[4]
 template <typename T>
 __device__ __forceinline__ void rev_vjp(const AdjArgs<T> &a, const RevSm<T> &sm, const T *X,
-                                        int l, int x, int y, size_t k, T v, T g[4]) {
+                                        int lx, int Wx, int l3, int l2, int x, int y, size_t k,
+                                        T v, T g[4]) {
     NodeEnv<T> e;
-    rev_env(a, sm, l, k, true, e);
+    rev_env(a, sm, l3, k, true, e);
     T p, pl, pr, pd, pu;
-    rev_stencil(X, l, x, y, a.nx, a.ny, p, pl, pr, pd, pu);
+    rev_stencil(X, lx, Wx, x, y, a.nx, a.ny, p, pl, pr, pd, pu);
     Partials<T> o;
     node_partials<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, e, o);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) sm.C[q * kRevF + l] = v * o.dpsi[q];
+    for (int q = 0; q < 5; ++q) sm.C[q * rev_rsize(2) + l2] = v * o.dpsi[q];
     g[0] = v * o.dm;
     g[1] = v * (o.dS0 * e.dco[0] + o.dR0 * e.dco[1] + o.dc * e.dco[2] + o.dd * e.dco[3]);
     g[2] = v * o.dun;
@@ -599,35 +602,44 @@ __device__ __forceinline__ void rev_vjp(const AdjArgs<T> &a, const RevSm<T> &sm,
 template <typename T>
 __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
     extern __shared__ __align__(16) unsigned char rev_sm[];
+    constexpr int F4 = rev_rsize(4), F3 = rev_rsize(3), F2 = rev_rsize(2), F1 = rev_rsize(1);
+    constexpr int W4 = rev_w(4), W3 = rev_w(3), W2 = rev_w(2);
     RevSm<T> sm;
     sm.seed = reinterpret_cast<double *>(rev_sm);
     T *f = reinterpret_cast<T *>(sm.seed + kRevO);
     sm.pa = f;
-    sm.ps = f + kRevF;
-    sm.mu = f + 2 * kRevF;
-    sm.ls = f + 3 * kRevF;
-    sm.C = f + 4 * kRevF;
-    sm.m = f + 9 * kRevF;
-    sm.zx = f + 10 * kRevF;
-    sm.zy = f + 11 * kRevF;
-    sm.un = f + 12 * kRevF;
-    sm.vn = f + 13 * kRevF;
-    sm.G = f + 14 * kRevF;
-    sm.lut = sm.G + 4 * kRevO;
-    sm.cls = reinterpret_cast<unsigned char *>(sm.lut + FIRE_MAX_CLASSES * 10);
+    f += F4;
+    sm.ps = f;
+    sm.m = f + F3;
+    sm.zx = f + 2 * F3;
+    sm.zy = f + 3 * F3;
+    sm.un = f + 4 * F3;
+    sm.vn = f + 5 * F3;
+    f += 6 * F3;
+    sm.mu = f;
+    sm.C = f + F2;
+    f += 6 * F2;
+    sm.ls = f;
+    f += F1;
+    sm.G = f;
+    f += 4 * kRevO;
+    sm.lut = f;
+    sm.cls = reinterpret_cast<unsigned char *>(f + a.ncls * 10);
     const int nx = a.nx, ny = a.ny;
     const int x0 = blockIdx.x * kRevTX, y0 = blockIdx.y * kRevTY;
     const int tid = threadIdx.x;
+    // frame position of node (x, y) in the frame of radius h
+    auto at = [&](int h, int x, int y) { return (y - y0 + h) * rev_w(h) + (x - x0 + h); };
     // a region of radius h around the tile, clipped to the domain: position
-    // e -> global (x, y), frame index l
-    auto region = [&](int h, int e, int &x, int &y, int &l) -> bool {
-        const int w = kRevTX + 2 * h;
+    // e -> global (x, y)
+    auto region = [&](int h, int e, int &x, int &y) -> bool {
+        const int w = rev_w(h);
         x = x0 - h + e % w;
         y = y0 - h + e / w;
-        l = (y - y0 + kRevHalo) * kRevW + (x - x0 + kRevHalo);
         return e < rev_rsize(h) && x >= 0 && x < nx && y >= 0 && y < ny;
     };
-    // ---- every read from global memory
+    // ---- every read from global memory (each loop loads into registers
+    // first and stores to shared memory after)
     if (!a.nodeco) {
         for (int q = tid; q < a.ncls * 10; q += kRevThreads) {
             const int c = q / 10, m = q % 10;
@@ -635,8 +647,6 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
             sm.lut[q] = T((m < 6 ? a.coef : a.dcoef)[(size_t)c * K_N + src]);
         }
     }
-    // each loop loads into registers first and stores to shared memory
-    // after, so that its loads are in flight together
     {
         constexpr int I4 = rev_iters(4);
         T v[I4];
@@ -645,10 +655,10 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
         for (int it = 0; it < I4; ++it) {
             int x, y;
             ls[it] = -1;
-            if (region(4, tid + it * kRevThreads, x, y, ls[it]))
+            if (region(4, tid + it * kRevThreads, x, y)) {
                 v[it] = a.pa[(size_t)y * nx + x];
-            else
-                ls[it] = -1;
+                ls[it] = at(4, x, y);
+            }
         }
 #pragma unroll
         for (int it = 0; it < I4; ++it)
@@ -661,7 +671,8 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
 #pragma unroll
         for (int it = 0; it < I3; ++it) {
             int x, y;
-            if (region(3, tid + it * kRevThreads, x, y, ls[it])) {
+            ls[it] = -1;
+            if (region(3, tid + it * kRevThreads, x, y)) {
                 const size_t k = (size_t)y * nx + x;
                 vc[it] = a.fuel[k];
                 vm[it] = a.mult ? a.mult[k] : T(1);
@@ -669,8 +680,7 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
                 vy[it] = a.zy[k];
                 vu[it] = a.unv[2 * k];
                 vv[it] = a.unv[2 * k + 1];
-            } else {
-                ls[it] = -1;
+                ls[it] = at(3, x, y);
             }
         }
 #pragma unroll
@@ -707,7 +717,8 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
 #pragma unroll
         for (int it = 0; it < I2; ++it) {
             int x, y;
-            if (region(2, tid + it * kRevThreads, x, y, ls[it])) {
+            ls[it] = -1;
+            if (region(2, tid + it * kRevThreads, x, y)) {
                 const size_t k = (size_t)y * nx + x;
                 vl[it] = a.lin[k];
                 t0[it] = a.tign0[k];
@@ -715,8 +726,7 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
                 to[it] = tobs[k];
                 p0[it] = a.pa[k];
                 p1[it] = a.pb[k];
-            } else {
-                ls[it] = -1;
+                ls[it] = at(2, x, y);
             }
         }
         const double tlo = a.tsp[0], thi = a.tsp[1];
@@ -764,24 +774,26 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
     }
     __syncthreads();
     // ---- psi* = psi^s + dt F(psi^s) (radius 3)
-    for (int e = tid; e < rev_rsize(3); e += kRevThreads) {
-        int x, y, l;
-        if (!region(3, e, x, y, l)) continue;
+    for (int e = tid; e < F3; e += kRevThreads) {
+        int x, y;
+        if (!region(3, e, x, y)) continue;
+        const int l3 = at(3, x, y);
         NodeEnv<T> en;
-        rev_env(a, sm, l, (size_t)y * nx + x, false, en);
+        rev_env(a, sm, l3, (size_t)y * nx + x, false, en);
         T p, pl, pr, pd, pu;
-        rev_stencil(sm.pa, l, x, y, nx, ny, p, pl, pr, pd, pu);
+        rev_stencil(sm.pa, at(4, x, y), W4, x, y, nx, ny, p, pl, pr, pd, pu);
         const T F = rhs_vals<T>(p, pl, pr, pd, pu, a.idx, a.idy, a.i2dx, a.i2dy, a.eps, en.co,
                                 en.m, en.un, en.vn, en.zx, en.zy);
-        sm.ps[l] = p + a.dtT * F;
+        sm.ps[l3] = p + a.dtT * F;
     }
     __syncthreads();
     // ---- the product at psi* with v = dt/2 mu (radius 2)
-    for (int e = tid; e < rev_rsize(2); e += kRevThreads) {
-        int x, y, l;
-        if (!region(2, e, x, y, l)) continue;
+    for (int e = tid; e < F2; e += kRevThreads) {
+        int x, y;
+        if (!region(2, e, x, y)) continue;
+        const int l3 = at(3, x, y), l2 = at(2, x, y);
         T g[4];
-        rev_vjp(a, sm, sm.ps, l, x, y, (size_t)y * nx + x, a.hdtT * sm.mu[l], g);
+        rev_vjp(a, sm, sm.ps, l3, W3, l3, l2, x, y, (size_t)y * nx + x, a.hdtT * sm.mu[l2], g);
         const int ox = x - x0, oy = y - y0;
         if (ox >= 0 && ox < kRevTX && oy >= 0 && oy < kRevTY) {
             const int o = oy * kRevTX + ox;
@@ -791,19 +803,23 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
     }
     __syncthreads();
     // ---- lam* (radius 1)
-    for (int e = tid; e < rev_rsize(1); e += kRevThreads) {
-        int x, y, l;
-        if (region(1, e, x, y, l)) sm.ls[l] = rev_gather(sm.C, sm.ps, l, x, y, nx, ny);
+    for (int e = tid; e < F1; e += kRevThreads) {
+        int x, y;
+        if (region(1, e, x, y))
+            sm.ls[at(1, x, y)] =
+                rev_gather(sm.C, at(2, x, y), W2, F2, sm.ps, at(3, x, y), W3, x, y, nx, ny);
     }
     __syncthreads();
     // ---- the product at psi^s with w = dt/2 mu + dt lam* (radius 1); the
     // owner adds both products' parameter terms
-    for (int e = tid; e < rev_rsize(1); e += kRevThreads) {
-        int x, y, l;
-        if (!region(1, e, x, y, l)) continue;
+    for (int e = tid; e < F1; e += kRevThreads) {
+        int x, y;
+        if (!region(1, e, x, y)) continue;
         const size_t k = (size_t)y * nx + x;
+        const int l2 = at(2, x, y);
         T g[4];
-        rev_vjp(a, sm, sm.pa, l, x, y, k, a.hdtT * sm.mu[l] + a.dtT * sm.ls[l], g);
+        rev_vjp(a, sm, sm.pa, at(4, x, y), W4, at(3, x, y), l2, x, y, k,
+                a.hdtT * sm.mu[l2] + a.dtT * sm.ls[at(1, x, y)], g);
         const int ox = x - x0, oy = y - y0;
         if (ox >= 0 && ox < kRevTX && oy >= 0 && oy < kRevTY) {
             const int o = oy * kRevTX + ox;
@@ -826,8 +842,9 @@ __global__ void __launch_bounds__(kRevThreads) k_adj_step(const AdjArgs<T> a) {
     for (int e = tid; e < kRevO; e += kRevThreads) {
         const int x = x0 + e % kRevTX, y = y0 + e / kRevTX;
         if (x >= nx || y >= ny) continue;
-        const int l = (y - y0 + kRevHalo) * kRevW + (x - x0 + kRevHalo);
-        T lam = sm.mu[l] + sm.ls[l] + rev_gather(sm.C, sm.pa, l, x, y, nx, ny);
+        const int l2 = at(2, x, y);
+        T lam = sm.mu[l2] + sm.ls[at(1, x, y)] +
+                rev_gather(sm.C, l2, W2, F2, sm.pa, at(4, x, y), W4, x, y, nx, ny);
         const double sd = sm.seed[e];
         if (sd != 0.0) lam = T((double)lam + sd);
         a.lout[(size_t)y * nx + x] = lam;
@@ -1538,7 +1555,10 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         if (!rev_attr) {
             ADJ_CHECK(cudaFuncSetAttribute(k_adj_step<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)rev_smem_bytes<T>()));
+                                           (int)rev_smem_bytes<T>(FIRE_MAX_CLASSES)));
+            // all of the unified L1 as shared memory: four tiles per SM
+            ADJ_CHECK(cudaFuncSetAttribute(k_adj_step<T>,
+                                           cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             rev_attr = true;
         }
     }
@@ -1552,7 +1572,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
         b.lin = lam + (size_t)(r & 1) * n;
         b.lout = lam + (size_t)((r + 1) & 1) * n;
         if constexpr (sizeof(T) == 4) {
-            k_adj_step<T><<<rgrid, kRevThreads, rev_smem_bytes<T>(), cs>>>(b);
+            k_adj_step<T><<<rgrid, kRevThreads, rev_smem_bytes<T>(ncls), cs>>>(b);
         } else {
             T *C1 = mid + 3 * n, *C2 = mid + 8 * n;
             b.pstar = mid;
