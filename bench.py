@@ -54,7 +54,8 @@ KERNEL_SOURCES = ["paper_1102_1343_gb300/csrc/march_kernel.cuh",
                   "paper_1102_1343_gb300/csrc/warp4_kernel.cuh",
                   "paper_1102_1343_gb300/csrc/step_warp4.cu"]
 PROFILE_SUMMARY = "profiles/fire_warp_f32_points8200.md"
-KERNEL_NAMES = ["k_fire_step", "k_fire_march", "k_fire_warp", "k_fire_warp4"]
+KERNEL_VARIANTS = ["tile", "march", "warp", "warp4", "warp_dense"]  # FIRE_KERNEL_* order
+KERNEL_NAMES = ["k_fire_step", "k_fire_march", "k_fire_warp", "k_fire_warp4", "k_fire_warp"]
 
 
 def kernel_hash() -> str:
@@ -474,7 +475,7 @@ def run_gpu(args, rank, world):
                        "refinement": [w.srx, w.sry], "precision": prec,
                        "state_in_hbm": "yes; state 2.2 GB > L2, no flush needed"
                        if args.workload == "points8200" else "yes",
-                       "kernel": {"variant": ["tile", "march", "warp", "warp4"][kernel[0]],
+                       "kernel": {"variant": KERNEL_VARIANTS[kernel[0]],
                                   "tile_atmos_cells": list(kernel[1:]),
                                   "chosen_by": "--kernel" if args.kernel else
                                   ("fire_autotune" if args.autotune else "fire_init default")},
@@ -533,7 +534,8 @@ def bench_burning(pkg, dev, steps):
     """The 8200x8200 mesh in a heavily burning state (50 ignitions of radius
     3 km, about 40 % of the domain burnt from the start): cell-steps/s and the
     roofline fraction of the step kernel where most warps run the
-    fuel-fraction quadrature and the ignition-time path."""
+    fuel-fraction quadrature and the ignition-time path, with fire_init's
+    default kernel and then with the one the autotuner picks there."""
     import torch
     from paper_1102_1343_gb300 import synth
     w = synth.burning_fire_8200()
@@ -548,33 +550,44 @@ def bench_burning(pkg, dev, steps):
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    pkg.fire_enable_timing(m.ctx, True)
-    pkg.fire_kernel_time_ms(m.ctx)
-    for _ in range(min(steps, 100)):
-        pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
-    k_ms, k_n = pkg.fire_kernel_time_ms(m.ctx)
-    pkg.fire_enable_timing(m.ctx, False)
-    k_avg = k_ms / max(1, k_n)
-    kernel = pkg.fire_get_kernel(m.ctx)
-    status = m.status()
-    m.close()
     peak, peak_kind = measured_peaks()
-    achieved = BYTES_PER_CELL_STEP["fp32"] * cells / (k_avg / 1000.0) / 1e9
-    return {"workload": f"{w.name} (820x820 atmos x10, 50 ignitions of radius 3 km)",
-            "burnt_fraction_at_start": burnt, "value": cells * steps / (ms / 1e3), "unit": UNIT,
-            "steps": steps, "ms_per_step": ms / steps, "kernel_ms": k_avg,
-            "kernel": KERNEL_NAMES[kernel[0]] + "<float>",
-            "tile_atmos_cells": list(kernel[1:]),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"},
-            "status": pkg.fire_strerror(status)}
+
+    def timed():
+        """steps from the current state: events around the whole loop, then
+        the step kernel's own events over up to 100 more steps"""
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        pkg.fire_enable_timing(m.ctx, True)
+        pkg.fire_kernel_time_ms(m.ctx)
+        for _ in range(min(steps, 100)):
+            pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
+        k_ms, k_n = pkg.fire_kernel_time_ms(m.ctx)
+        pkg.fire_enable_timing(m.ctx, False)
+        k_avg = k_ms / max(1, k_n)
+        kernel = pkg.fire_get_kernel(m.ctx)
+        achieved = BYTES_PER_CELL_STEP["fp32"] * cells / (k_avg / 1000.0) / 1e9
+        return {"value": cells * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+                "ms_per_step": ms / steps, "kernel_ms": k_avg,
+                "kernel": KERNEL_NAMES[kernel[0]] + "<float>",
+                "variant": KERNEL_VARIANTS[kernel[0]], "tile_atmos_cells": list(kernel[1:]),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"}}
+
+    out = {"workload": f"{w.name} (820x820 atmos x10, 50 ignitions of radius 3 km)",
+           "burnt_fraction_at_start": burnt}
+    out.update(timed())
+    # the kernel the autotuner picks on this state (timed from where the
+    # default kernel's steps left the fire)
+    m.autotune(u, v, w.dt)
+    out["autotuned"] = timed()
+    out["status"] = pkg.fire_strerror(m.status())
+    m.close()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -634,7 +647,7 @@ def bench_adjoint(pkg, dev, ckpt=20):
         ms = e0.elapsed_time(e1)
         grads[prec] = (J, gm, gM, gu, gv)
         rec = {"value": n / (ms / 1e3), "ms": ms, "J": J,
-               "kernel": {"variant": ["tile", "march", "warp", "warp4"][kern[0]],
+               "kernel": {"variant": KERNEL_VARIANTS[kern[0]],
                           "tile_atmos_cells": list(kern[1:])}}
         # every state kept (checkpoint interval 1: no recomputed forward;
         # 401 states of the mesh in HBM)

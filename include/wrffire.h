@@ -301,13 +301,21 @@ double fire_time(const fire_ctx *ctx);
  *                      held in registers, neighbours exchanged by shuffles;
  *   FIRE_KERNEL_WARP4  (FIRE_FP32 only) the same with four columns per lane:
  *                      strips of kx*sr_x <= 120 columns, the per-row control
- *                      shared by four columns.
+ *                      shared by four columns;
+ *   FIRE_KERNEL_WARP_DENSE  (FIRE_FP32 only) FIRE_KERNEL_WARP's strips
+ *                      with t_i read a row ahead where psi <= 0 and the two
+ *                      cells of a lane in one packed fuel-fraction
+ *                      evaluation: the same results bit for bit, faster
+ *                      where much of the mesh burns, slower where little
+ *                      does (with a per-node moisture it runs as
+ *                      FIRE_KERNEL_WARP).
  * FIRE_ERR_ARG if the shape does not fit the variant or the device. */
 enum fire_kernel_variant {
     FIRE_KERNEL_TILE = 0,
     FIRE_KERNEL_MARCH = 1,
     FIRE_KERNEL_WARP = 2,
-    FIRE_KERNEL_WARP4 = 3
+    FIRE_KERNEL_WARP4 = 3,
+    FIRE_KERNEL_WARP_DENSE = 4
 };
 int fire_set_kernel(fire_ctx *ctx, int variant, int kx, int ky);
 

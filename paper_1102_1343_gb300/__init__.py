@@ -35,6 +35,7 @@ FIRE_KERNEL_TILE = 0
 FIRE_KERNEL_MARCH = 1
 FIRE_KERNEL_WARP = 2
 FIRE_KERNEL_WARP4 = 3
+FIRE_KERNEL_WARP_DENSE = 4
 FIRE_MAX_CLASSES = 64
 FIRE_MAX_IGNITIONS = 256
 

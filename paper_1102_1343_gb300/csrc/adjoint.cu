@@ -1365,6 +1365,7 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     auto launch_step_kernel = [&](const StepArgs &ra, cudaStream_t cs) -> cudaError_t {
         return variant == FIRE_KERNEL_MARCH   ? launch_march<T>(ra, cs)
                : variant == FIRE_KERNEL_WARP  ? launch_warp<T>(ra, cs)
+               : variant == FIRE_KERNEL_WARP_DENSE ? launch_warp<T>(ra, cs, true)
                : variant == FIRE_KERNEL_WARP4 ? (sizeof(T) == 4 ? launch_warp4(ra, cs)
                                                                 : cudaErrorInvalidValue)
                                               : launch_step<T>(ra, cs);

@@ -203,6 +203,8 @@ cudaError_t launch_variant(const fire_ctx *c, const StepArgs &a, cudaStream_t s)
         return c->prec == FIRE_FP64 ? launch_warp<double>(a, s) : launch_warp<float>(a, s);
     if (c->variant == FIRE_KERNEL_WARP4)
         return c->prec == FIRE_FP32 ? launch_warp4(a, s) : cudaErrorInvalidValue;
+    if (c->variant == FIRE_KERNEL_WARP_DENSE)
+        return c->prec == FIRE_FP32 ? launch_warp<float>(a, s, true) : cudaErrorInvalidValue;
     return c->prec == FIRE_FP64 ? launch_step<double>(a, s) : launch_step<float>(a, s);
 }
 
@@ -284,10 +286,11 @@ int configure_kernel(fire_ctx *c, int variant, int kx, int ky) {
                                   : march_smem_bytes<float>(ky, c->g.sr_y, c->ncls);
         if (sm > c->smem_max) return FIRE_ERR_ARG;
         e = c->prec == FIRE_FP64 ? prepare_march_kernel<double>(sm) : prepare_march_kernel<float>(sm);
-    } else if (variant == FIRE_KERNEL_WARP) {
+    } else if (variant == FIRE_KERNEL_WARP || variant == FIRE_KERNEL_WARP_DENSE) {
         const long long W = (long long)kx * c->g.sr_x, L = (long long)ky * c->g.sr_y;
         if (W > kWarpMaxColumns || (W & 1) || L > kWarpMaxRows || (long long)c->n > kWarpMaxNodes)
             return FIRE_ERR_ARG;
+        if (variant == FIRE_KERNEL_WARP_DENSE && c->prec != FIRE_FP32) return FIRE_ERR_ARG;
         sm = 0;
         e = cudaSuccess;
     } else if (variant == FIRE_KERNEL_WARP4) {
@@ -991,7 +994,10 @@ int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int prob
         const int heights[] = {16, 32, 64, 128, 256, 512};
         for (int W : widths) {
             if (W / srx * srx > kWarpMaxColumns || W / srx < 1) continue;
-            for (int L : heights) add(FIRE_KERNEL_WARP, W / srx, L / sry);
+            for (int L : heights) {
+                add(FIRE_KERNEL_WARP, W / srx, L / sry);
+                if (c->prec == FIRE_FP32) add(FIRE_KERNEL_WARP_DENSE, W / srx, L / sry);
+            }
         }
     }
     if (c->prec == FIRE_FP32 && srx <= kWarp4MaxColumns / 2) {

@@ -43,6 +43,11 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 template <>
 struct Mth<float> {
@@ -55,6 +60,12 @@ struct Mth<float> {
     static __device__ __forceinline__ float pw(float x, float b) { return ex2_ftz(b * lg2_ftz(x)); }
     static __device__ __forceinline__ float ex(float x) { return __expf(x); }
     static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+    // 1 - a/b as one fused multiply-add with the hardware reciprocal (the
+    // same rounding wherever it is formed, scalar or packed; b a normal
+    // float, as __fdividef wants it)
+    static __device__ __forceinline__ float one_minus_div(float a, float b) {
+        return fmaf(-a, rcp_ftz(b), 1.0f);
+    }
     // x >= 0 (a sum of squares)
     static __device__ __forceinline__ float sqr(float x) { return sqrt_ftz(x); }
     // unit vector of (cx, cy); zero vector when the norm vanishes
@@ -78,6 +89,9 @@ struct Mth<double> {
     }
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double one_minus_div(double a, double b) {
+        return 1.0 - a / b;
+    }
     static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
     // unit vector of (cx, cy) (one reciprocal of the norm, two products);
     // zero vector when the norm vanishes
@@ -214,7 +228,7 @@ __device__ __forceinline__ T subcell_burned(T p0, T p1, T p2, T p3, T d0, T d1, 
                                             T mquarter_over_tf) {
     T sp = ((p0 + p1) + p2) + p3;
     T sa = ((abs_val(p0) + abs_val(p1)) + abs_val(p2)) + abs_val(p3);
-    T beta = sa > T(0) ? T(0.5) * (T(1) - Mth<T>::dv(sp, sa)) : T(0);
+    T beta = sa > T(0) ? T(0.5) * Mth<T>::one_minus_div(sp, sa) : T(0);
     T s = ((d0 + d1) + d2) + d3;
     return beta * (T(1) - Mth<T>::ex(s * mquarter_over_tf));
 }
@@ -254,7 +268,8 @@ __device__ __forceinline__ T cell_fraction_vals(T p00, T p01, T p02, T p10, T p1
     T bSE = subcell_burned<T>(p11, pE, pS, pSE, dC, dE, dS, dSE, k);
     T bNW = subcell_burned<T>(p11, pW, pN, pNW, dC, dW, dN, dNW, k);
     T bNE = subcell_burned<T>(p11, pE, pN, pNE, dC, dE, dN, dNE, k);
-    return T(1) - q * (((bSW + bSE) + bNW) + bNE);
+    // one fused multiply-add, as in the packed two-cell version
+    return fma(-q, ((bSW + bSE) + bNW) + bNE, T(1));
 }
 
 // ---------------------------------------------------------------------------

@@ -98,7 +98,7 @@ cudaError_t prepare_march_kernel(size_t smem_bytes);
 constexpr int kMarchMaxColumns = 248;  // output columns of one marching strip (even)
 
 template <typename T>
-cudaError_t launch_warp(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_warp(const StepArgs &a, cudaStream_t s, bool dense = false);
 
 // four columns per lane (FP32 only): strips of <= 120 output columns
 constexpr int kWarp4MaxColumns = 120;

@@ -203,4 +203,66 @@ __device__ __forceinline__ void coef_pair_dup(const T *lut2, int cls0, int cls1,
     }
 }
 
+// Fuel fraction (Sect. 3.3, the subcell scheme of cell_fraction_vals) of two
+// cells at once, the two columns of a lane: q[b][h], e[b][h] the 3x3
+// neighbourhoods of psi^{n+1} and t - t_i (0 where psi >= 0) of both cells
+// as pairs, Tf the two burn times.  The sums, means and products are packed
+// f32x2; the compatibility tests, |psi|, divisions and exponentials stay per
+// element.  Each cell must have a node with psi < 0 in its neighbourhood
+// (the caller keeps F = 1 for the others).
+__device__ __forceinline__ float2 cell_fraction_pair(const float2 (&q)[3][3],
+                                                     const float2 (&e)[3][3], float2 Tf) {
+    const float2 h = make_float2(0.5f, 0.5f), qq = make_float2(0.25f, 0.25f);
+    // vertices: centre, edge midpoints W E S N, corners SW SE NW NE
+    const float2 pC = q[1][1];
+    const float2 pW = mul2(h, add2(q[1][0], q[1][1])), pE = mul2(h, add2(q[1][1], q[1][2]));
+    const float2 pS = mul2(h, add2(q[0][1], q[1][1])), pN = mul2(h, add2(q[1][1], q[2][1]));
+    float2 dW = mul2(h, add2(e[1][0], e[1][1])), dE = mul2(h, add2(e[1][1], e[1][2]));
+    float2 dS = mul2(h, add2(e[0][1], e[1][1])), dN = mul2(h, add2(e[1][1], e[2][1]));
+    const float2 pSW = mul2(qq, add2(add2(add2(q[0][0], q[0][1]), q[1][0]), q[1][1]));
+    const float2 pSE = mul2(qq, add2(add2(add2(q[0][1], q[0][2]), q[1][1]), q[1][2]));
+    const float2 pNW = mul2(qq, add2(add2(add2(q[1][0], q[1][1]), q[2][0]), q[2][1]));
+    const float2 pNE = mul2(qq, add2(add2(add2(q[1][1], q[1][2]), q[2][1]), q[2][2]));
+    float2 dSW = mul2(qq, add2(add2(add2(e[0][0], e[0][1]), e[1][0]), e[1][1]));
+    float2 dSE = mul2(qq, add2(add2(add2(e[0][1], e[0][2]), e[1][1]), e[1][2]));
+    float2 dNW = mul2(qq, add2(add2(add2(e[1][0], e[1][1]), e[2][0]), e[2][1]));
+    float2 dNE = mul2(qq, add2(add2(add2(e[1][1], e[1][2]), e[2][1]), e[2][2]));
+    // compatibility at the vertices: t_i := t where psi >= 0
+    auto compat = [](float2 p, float2 d) {
+        return make_float2(p.x >= 0.0f ? 0.0f : d.x, p.y >= 0.0f ? 0.0f : d.y);
+    };
+    const float2 dC = compat(pC, e[1][1]);
+    dW = compat(pW, dW);
+    dE = compat(pE, dE);
+    dS = compat(pS, dS);
+    dN = compat(pN, dN);
+    dSW = compat(pSW, dSW);
+    dSE = compat(pSE, dSE);
+    dNW = compat(pNW, dNW);
+    dNE = compat(pNE, dNE);
+    const float2 k = make_float2(-0.25f / Tf.x, -0.25f / Tf.y);
+    // burned fraction of one subcell, eqs. (approx-area), (approx-fraction)
+    auto sub = [&](float2 p0, float2 p1, float2 p2, float2 p3, float2 d0, float2 d1, float2 d2,
+                   float2 d3) {
+        const float2 sp = add2(add2(add2(p0, p1), p2), p3);
+        const float sax = ((fabsf(p0.x) + fabsf(p1.x)) + fabsf(p2.x)) + fabsf(p3.x);
+        const float say = ((fabsf(p0.y) + fabsf(p1.y)) + fabsf(p2.y)) + fabsf(p3.y);
+        // beta = (1 - sum / sum of |.|) / 2 as Mth<float>::one_minus_div
+        // forms it, 0 where every vertex value is 0
+        const float2 ns = make_float2(sax > 0.0f ? -sp.x : -1.0f, say > 0.0f ? -sp.y : -1.0f);
+        const float2 rc = make_float2(sax > 0.0f ? rcp_ftz(sax) : 1.0f,
+                                      say > 0.0f ? rcp_ftz(say) : 1.0f);
+        const float2 beta = mul2(h, fma2(ns, rc, make_float2(1.0f, 1.0f)));
+        const float2 s = mul2(add2(add2(add2(d0, d1), d2), d3), k);
+        const float2 ex = make_float2(__expf(s.x), __expf(s.y));
+        return mul2(beta, sub2(make_float2(1.0f, 1.0f), ex));
+    };
+    const float2 bSW = sub(pC, pW, pS, pSW, dC, dW, dS, dSW);
+    const float2 bSE = sub(pC, pE, pS, pSE, dC, dE, dS, dSE);
+    const float2 bNW = sub(pC, pW, pN, pNW, dC, dW, dN, dNW);
+    const float2 bNE = sub(pC, pE, pN, pNE, dC, dE, dN, dNE);
+    return fma2(make_float2(-0.25f, -0.25f), add2(add2(add2(bSW, bSE), bNW), bNE),
+                make_float2(1.0f, 1.0f));
+}
+
 }  // namespace wf

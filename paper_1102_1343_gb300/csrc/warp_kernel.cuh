@@ -60,8 +60,13 @@ struct WEnv {  // what stage 2 reuses from stage 1 of the same row
 };
 
 // NC: per-node R0, c, d and heat factors (a per-node fuel moisture) read
-// from the planes of StepArgs::nco instead of the class table
-template <typename T, bool NC = false>
+// from the planes of StepArgs::nco instead of the class table.
+// Dense (FP32, the FIRE_KERNEL_WARP_DENSE variant): t_i read one row ahead
+// where psi^n <= 0 and the quadrature of the lane's two cells in one packed
+// evaluation away from the domain boundary; the same results as the other
+// instantiation bit for bit, faster where much of the mesh burns and slower
+// where little does.
+template <typename T, bool NC = false, bool Dense = false>
 struct WarpStrip {
     using V = typename PairT<T>::t;
     const StepArgs &a;
@@ -270,6 +275,7 @@ struct WarpStrip {
         V Nm2 = P0, Nm1 = P0, N0 = P0;     // psi^{n+1} rows k-2, k-1, k
         V Dm2 = P0, Dm1 = P0, D0 = P0;     // t - t_i rows k-2, k-1, k
         V Fpre = splat<V>(T(1));           // F^n of row k-1 (at the top of iteration k)
+        double tiA = 0.0, tiB = 0.0;       // t_i of row k where psi^n <= 0 (prefetched)
         WEnv<T> envB, envC, envPre;
         envB.cls0 = envB.cls1 = 0;
         envB.zx = envB.zy = envB.un = envB.vn = P0;
@@ -365,7 +371,10 @@ struct WarpStrip {
                     for (int j = 0; j < 2; ++j) {
                         if (!(j == 0 ? na : nb)) continue;
                         const T p0 = j == 0 ? P0.x : P0.y, pn = j == 0 ? N0.x : N0.y;
-                        double ti = a.tign[g + j];
+                        // Dense: prefetched where psi^n <= 0, read here at a crossing
+                        double ti;
+                        if constexpr (Dense) ti = p0 <= T(0) ? (j == 0 ? tiA : tiB) : a.tign[g + j];
+                        else ti = a.tign[g + j];
                         if (p0 > T(0) && isinf(ti)) {
                             const double q0 = (double)p0, q1 = (double)pn;
                             ti = tstart + q0 * a.dt / (q0 - q1);
@@ -386,6 +395,17 @@ struct WarpStrip {
                         if (!pst && outB) po[g + 1] = N0.y;
                     }
                 }
+            }
+            // Dense: t_i of row k+1 where psi^n <= 0, for stage C of the
+            // next iteration (such nodes get no new t_i in this step, so no
+            // other warp writes them); skipped by warps with no such node,
+            // whose stage C then reads no prefetched value
+            if (Dense && __any_sync(0xffffffffu, P1.x <= T(0) || P1.y <= T(0))) {
+                const int rn = k + 1;
+                const bool rin = rn >= y0 - 1 && rn >= 0 && rn < ny;
+                const int g = rn * nx + xa;
+                if (rin && inA && lane > 0 && P1.x <= T(0)) tiA = a.tign[g];
+                if (rin && inB && lane < 31 && P1.y <= T(0)) tiB = a.tign[g + 1];
             }
             // ---- D: fuel fraction and heat on row k-1
             const int rD = k - 1;
@@ -447,6 +467,33 @@ struct WarpStrip {
             sides(Db, dl[1], dr[1]);
             sides(Dc, dl[2], dr[2]);
             const V Nr[3] = {Na, Nb, Nc}, Dr[3] = {Da, Db, Dc};
+            if constexpr (Dense && sizeof(T) == 4) {
+                // away from the domain boundary: both cells of the lane in
+                // one packed evaluation; F = 1 stays where no node of a
+                // cell's neighbourhood burns
+                if (rD > 0 && rD < ny - 1 && xa > 0 && xa + 1 < nx - 1) {
+                    if (ba || bb) {
+                        float2 qp[3][3], ep[3][3];
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            qp[b][0] = mk2(pl[b], Nr[b].x);
+                            qp[b][1] = Nr[b];
+                            qp[b][2] = mk2(Nr[b].y, pr[b]);
+                            ep[b][0] = mk2(dl[b], Dr[b].x);
+                            ep[b][1] = Dr[b];
+                            ep[b][2] = mk2(Dr[b].y, dr[b]);
+                        }
+                        const int g = rD * nx + xa;
+                        const int ca = ba ? a.fuel[g] : 0, cb = bb ? a.fuel[g + 1] : 0;
+                        const float2 tf = mk2(lut[(ca > ncm1 ? ncm1 : ca) * 8 + 6],
+                                              lut[(cb > ncm1 ? ncm1 : cb) * 8 + 6]);
+                        const float2 f = cell_fraction_pair(qp, ep, tf);
+                        F1.x = ba ? f.x : 1.0f;
+                        F1.y = bb ? f.y : 1.0f;
+                    }
+                    return;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 if (!(j == 0 ? ba : bb)) continue;
@@ -576,7 +623,7 @@ struct WarpStrip {
     }
 };
 
-template <typename T, bool NC>
+template <typename T, bool NC, bool Dense>
 __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(const StepArgs a) {
     __shared__ __align__(16) T lut[FIRE_MAX_CLASSES * 8];
     __shared__ __align__(16) T lut2[FIRE_MAX_CLASSES * 12];
@@ -620,26 +667,32 @@ __global__ void __launch_bounds__(kWarpCtaThreads, WOcc<T>::blocks) k_fire_warp(
     const int W = a.kx * a.srx;
     const int x0 = (blockIdx.x * kWarpStrips + w) * W;
     if (x0 >= a.nx) return;  // whole warp
-    WarpStrip<T, NC> s(a, lut, lut2, lutq, hw[w], rows);
+    WarpStrip<T, NC, Dense> s(a, lut, lut2, lutq, hw[w], rows);
     s.run(x0, y0, tstart);
     const int stw = __reduce_or_sync(0xffffffffu, s.st);
     if ((threadIdx.x & 31) == 0 && stw) atomicOr(a.status, stw);
 }
 
+// dense: the Dense instantiation (FP32 with the class table; elsewhere the
+// other one, which gives the same results)
 template <typename T>
-cudaError_t launch_warp(const StepArgs &a, cudaStream_t s) {
+cudaError_t launch_warp(const StepArgs &a, cudaStream_t s, bool dense) {
     const int W = a.kx * a.srx, L = a.ky * a.sry;
     if (W > 60 || (W & 1) || W < 2 || L > kWarpMaxRows || (long long)a.nx * a.ny > kWarpMaxNodes)
         return cudaErrorInvalidValue;
     const int strips = (a.nx + W - 1) / W;
     dim3 grid((strips + kWarpStrips - 1) / kWarpStrips, (a.ny + L - 1) / L);
-    if (a.nco[0])
-        k_fire_warp<T, true><<<grid, kWarpCtaThreads, 0, s>>>(a);
-    else
-        k_fire_warp<T, false><<<grid, kWarpCtaThreads, 0, s>>>(a);
+    if (a.nco[0]) {
+        k_fire_warp<T, true, false><<<grid, kWarpCtaThreads, 0, s>>>(a);
+    } else if (dense && sizeof(T) == 4) {
+        k_fire_warp<T, false, sizeof(T) == 4><<<grid, kWarpCtaThreads, 0, s>>>(a);
+    } else {
+        k_fire_warp<T, false, false><<<grid, kWarpCtaThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
-#define WF_INSTANTIATE_WARP(T) template cudaError_t launch_warp<T>(const StepArgs &, cudaStream_t);
+#define WF_INSTANTIATE_WARP(T) \
+    template cudaError_t launch_warp<T>(const StepArgs &, cudaStream_t, bool);
 
 }  // namespace wf

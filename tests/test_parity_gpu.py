@@ -469,7 +469,8 @@ def test_full_size_sampled_cells(pkg, name, prec, warm, tile):
 
 @pytest.mark.parametrize("mesh", [(32, 26, 10), (23, 17, 10), (23, 17, 5), (13, 40, 10)])
 def test_warp4_equals_two_column_warp_kernel(pkg, mesh):
-    """The four-column warp kernel computes every node with the same
+    """The four-column warp kernel and the dense two-column one (t_i read a
+    row ahead, packed fuel fractions) compute every node with the same
     operations as the two-column one: the same bits for psi, t_i, F and both
     heat grids (meshes whose width is a multiple of 4 (float4 rows), even
     (float2 pairs) and odd (scalars); strips of 12 and of 6 atmospheric
@@ -484,28 +485,33 @@ def test_warp4_equals_two_column_warp_kernel(pkg, mesh):
     a = pkg.FireModel.from_workload(w, precision="fp32")
     b = pkg.FireModel.from_workload(w, precision="fp32")
     c = pkg.FireModel.from_workload(w, precision="fp32")
+    d = pkg.FireModel.from_workload(w, precision="fp32")
     ky = max(1, 30 // sr)
     pkg.fire_set_kernel(a.ctx, pkg.FIRE_KERNEL_WARP, 60 // sr, ky)
     pkg.fire_set_kernel(b.ctx, pkg.FIRE_KERNEL_WARP4, 120 // sr, ky)
     pkg.fire_set_kernel(c.ctx, pkg.FIRE_KERNEL_WARP4, 60 // sr, 2 * ky)
+    pkg.fire_set_kernel(d.ctx, pkg.FIRE_KERNEL_WARP_DENSE, 60 // sr, ky)
     u, v = a.wind(w.u, w.v)
     for _ in range(w.steps):
         ha = a.step(u, v, w.dt)
         hb = b.step(u, v, w.dt)
         hc = c.step(u, v, w.dt)
+        hd = d.step(u, v, w.dt)
     torch.cuda.synchronize()
-    sa, sb, sc = state_np(a), state_np(b), state_np(c)
+    sa, sb, sc, sd = state_np(a), state_np(b), state_np(c), state_np(d)
     assert np.isfinite(sa[1]).sum() > 30
     for k in range(3):
         assert np.array_equal(sa[k], sb[k]) and np.array_equal(sa[k], sc[k]), k
-    for x, y in ((ha, hb), (ha, hc)):
+        assert np.array_equal(sa[k], sd[k]), k
+    for x, y in ((ha, hb), (ha, hc), (ha, hd)):
         assert np.array_equal(x[0].cpu().numpy(), y[0].cpu().numpy())
         assert np.array_equal(x[1].cpu().numpy(), y[1].cpu().numpy())
-    assert a.status() == b.status() == c.status() == pkg.FIRE_OK
+    assert a.status() == b.status() == c.status() == d.status() == pkg.FIRE_OK
     m64 = pkg.FireModel.from_workload(w, precision="fp64")
-    with pytest.raises(pkg.FireError):
-        pkg.fire_set_kernel(m64.ctx, pkg.FIRE_KERNEL_WARP4, 120 // sr, ky)
-    for x in (a, b, c, m64):
+    for variant in (pkg.FIRE_KERNEL_WARP4, pkg.FIRE_KERNEL_WARP_DENSE):
+        with pytest.raises(pkg.FireError):
+            pkg.fire_set_kernel(m64.ctx, variant, 60 // sr, ky)
+    for x in (a, b, c, d, m64):
         x.close()
 
 
