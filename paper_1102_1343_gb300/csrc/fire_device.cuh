@@ -221,6 +221,12 @@ __device__ __forceinline__ T rhs_at(const T *B, int c, int W, T idx, T idy, T i2
 }
 
 
+// an unset ignition time (+inf), tested on the bits (no FP64 instruction)
+__device__ __forceinline__ bool tign_unset(double ti) {
+    return ((unsigned long long)__double_as_longlong(ti) & 0x7fffffffffffffffull) ==
+           0x7ff0000000000000ull;
+}
+
 // burned fraction of one subcell from its 4 vertex values (eqs. approx-area,
 // approx-fraction with the exponent -(1/4) sum (t - t_i)/T_f)
 template <typename T>

@@ -375,7 +375,7 @@ struct WarpStrip {
                         double ti;
                         if constexpr (Dense) ti = p0 <= T(0) ? (j == 0 ? tiA : tiB) : a.tign[g + j];
                         else ti = a.tign[g + j];
-                        if (p0 > T(0) && isinf(ti)) {
+                        if (p0 > T(0) && tign_unset(ti)) {
                             const double q0 = (double)p0, q1 = (double)pn;
                             ti = tstart + q0 * a.dt / (q0 - q1);
                             if (own_row && (j == 0 ? outA : outB)) a.tign[g + j] = ti;
@@ -600,25 +600,33 @@ struct WarpStrip {
         // after the last row of an atmospheric band: average per cell
         if (++bcnt == sry) {
             bcnt = 0;
-            hw[2 * lane] = acc_s.x;
-            hw[2 * lane + 1] = acc_s.y;
-            hw[64 + 2 * lane] = acc_q.x;
-            hw[64 + 2 * lane + 1] = acc_q.y;
-            __syncwarp();
-            const int cells = Wa / srx;
-            if (lane < cells) {
-                T h0 = T(0), h1 = T(0);
-                for (int e = 0; e < srx; ++e) {
-                    const int lc = 2 + lane * srx + e;
-                    h0 += hw[lc];
-                    h1 += hw[64 + lc];
+            // a band with no heat anywhere in the warp (most of a sparse
+            // fire) writes its zero averages without the reduction
+            if (__any_sync(0xffffffffu, acc_s.x != T(0) || acc_s.y != T(0) ||
+                                            acc_q.x != T(0) || acc_q.y != T(0))) {
+                hw[2 * lane] = acc_s.x;
+                hw[2 * lane + 1] = acc_s.y;
+                hw[64 + 2 * lane] = acc_q.x;
+                hw[64 + 2 * lane + 1] = acc_q.y;
+                __syncwarp();
+                if (lane * srx < Wa) {  // one lane per atmospheric cell
+                    T h0 = T(0), h1 = T(0);
+                    for (int e = 0; e < srx; ++e) {
+                        const int lc = 2 + lane * srx + e;
+                        h0 += hw[lc];
+                        h1 += hw[64 + lc];
+                    }
+                    const size_t ga = (size_t)(rD / sry) * nxa + (x0 / srx + lane);
+                    if (a.heat_s) a.heat_s[ga] = (double)h0 * hscale;
+                    if (a.heat_l) a.heat_l[ga] = (double)h1 * hscale;
                 }
+                __syncwarp();
+                acc_s = acc_q = splat<V>(T(0));
+            } else if (lane * srx < Wa) {
                 const size_t ga = (size_t)(rD / sry) * nxa + (x0 / srx + lane);
-                if (a.heat_s) a.heat_s[ga] = (double)h0 * hscale;
-                if (a.heat_l) a.heat_l[ga] = (double)h1 * hscale;
+                if (a.heat_s) a.heat_s[ga] = 0.0;
+                if (a.heat_l) a.heat_l[ga] = 0.0;
             }
-            __syncwarp();
-            acc_s = acc_q = splat<V>(T(0));
         }
     }
 };
