@@ -686,6 +686,22 @@ def bench_adjoint(pkg, dev, ckpt=20):
         fms = e0.elapsed_time(e1)
         rec["plain_forward"] = {"value": n / (fms / 1e3), "ms": fms}
         rec["ratio_to_plain_forward"] = {f"ckpt{ckpt}": fms / ms, "ckpt1": fms / ms1}
+        # one reverse step: the call with every state kept less its forward
+        # (the plain forward's time), per step; algorithmic bytes per node of
+        # the FP32 fused step: psi^s, psi^{s+1}, lambda in and out, t_i at
+        # the start and end, t_obs, class, multiplier, slope, node wind, and
+        # the four compensated parameter sums read and written
+        E = 8 if prec == "fp64" else 4
+        b_node = 5 * E + 3 * 8 + 1 + (E if w.mult is not None else 0) + 2 * E + 4 * 2 * 8
+        us = (ms1 - fms) * 1e3 / w.steps
+        peak, peak_kind = measured_peaks()
+        gbs = b_node * w.nx * w.ny / (us * 1e-6) / 1e9
+        rec["reverse_step"] = {"us": us, "bytes_per_node": b_node, "achieved_gbs": gbs,
+                               "frac_of_hbm": gbs / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                               "kernel": "k_adj_step<float> (one launch)" if prec == "fp32" else
+                               "k_adj_stage1/vjp_star/vjp_n/finish<double> (four launches)",
+                               "note": "estimated as (every-state-kept call - plain forward) / "
+                                       "steps; the step's working set fits in L2"}
         out[prec] = rec
         m.close()
     base = out["fp64"]["plain_forward"]["value"]
@@ -789,7 +805,9 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--kernel", type=int, nargs=3, default=None,
                     metavar=("VARIANT", "KX", "KY"),
-                    help="step kernel: 0 = 2-D tile, 1 = column march; tile in atmos cells")
+                    help="step kernel (FIRE_KERNEL_*): 0 = 2-D tile, 1 = column march, "
+                         "2 = warp strips, 3 = four-column warp strips, 4 = dense warp strips; "
+                         "shape in atmos cells")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
