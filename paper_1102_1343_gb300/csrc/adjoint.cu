@@ -871,44 +871,53 @@ __global__ void k_acc_final(double *g, size_t n) {
 
 // Adjoint of the bilinear wind interpolation (Sect. 5): every staggered
 // face sums the node gradients times the weights the forward gave it.
-// One thread per face; the candidate nodes are those within two cells.
+// One warp per face: each lane takes every 32nd column of the candidate
+// nodes (those within two cells), its rows in order, then the lanes' sums
+// are added in a fixed tree, so the result does not depend on scheduling.
 template <typename T>
 __global__ void k_adj_wind(const AdjArgs<T> a, const double *gun, const double *gvn, double *gu,
                            double *gv) {
     const int nu = a.nya * (a.nxa + 1), nv = (a.nya + 1) * a.nxa;
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nu + nv; f += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int w0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int f = w0; f < nu + nv; f += nw) {
         const bool isu = f < nu;
         const int q = isu ? f : f - nu;
         const int W = isu ? a.nxa + 1 : a.nxa;
         const int I = q % W, J = q / W;
         const int i_lo = max(0, (I - 2) * a.srx), i_hi = min(a.nx, (I + 2) * a.srx);
         const int j_lo = max(0, (J - 2) * a.sry), j_hi = min(a.ny, (J + 2) * a.sry);
+        const double *g = isu ? gun : gvn;
         double s = 0.0;
-        for (int j = j_lo; j < j_hi; ++j) {
-            const T yr = (T(j) + T(0.5)) / T(a.sry);
-            int j0, j1;
-            T wy;
-            if (isu) lin_idx<T>(yr - T(0.5), a.nya, j0, j1, wy);
-            else lin_idx<T>(yr, a.nya + 1, j0, j1, wy);
-            double cy = 0.0;
-            if (j0 == J) cy += (double)(T(1) - wy);
-            if (j1 == J) cy += (double)wy;
-            if (cy == 0.0) continue;
-            const double *gn = (isu ? gun : gvn) + (size_t)j * a.nx;
-            for (int i = i_lo; i < i_hi; ++i) {
-                const T xr = (T(i) + T(0.5)) / T(a.srx);
-                int i0, i1;
-                T wx;
-                if (isu) lin_idx<T>(xr, a.nxa + 1, i0, i1, wx);
-                else lin_idx<T>(xr - T(0.5), a.nxa, i0, i1, wx);
-                double cx = 0.0;
-                if (i0 == I) cx += (double)(T(1) - wx);
-                if (i1 == I) cx += (double)wx;
-                if (cx != 0.0) s += gn[i] * (cy * cx);
+        for (int i = i_lo + lane; i < i_hi; i += 32) {
+            const T xr = (T(i) + T(0.5)) / T(a.srx);
+            int i0, i1;
+            T wx;
+            if (isu) lin_idx<T>(xr, a.nxa + 1, i0, i1, wx);
+            else lin_idx<T>(xr - T(0.5), a.nxa, i0, i1, wx);
+            double cx = 0.0;
+            if (i0 == I) cx += (double)(T(1) - wx);
+            if (i1 == I) cx += (double)wx;
+            if (cx == 0.0) continue;
+            for (int j = j_lo; j < j_hi; ++j) {
+                const T yr = (T(j) + T(0.5)) / T(a.sry);
+                int j0, j1;
+                T wy;
+                if (isu) lin_idx<T>(yr - T(0.5), a.nya, j0, j1, wy);
+                else lin_idx<T>(yr, a.nya + 1, j0, j1, wy);
+                double cy = 0.0;
+                if (j0 == J) cy += (double)(T(1) - wy);
+                if (j1 == J) cy += (double)wy;
+                if (cy != 0.0) s += g[(size_t)j * a.nx + i] * (cy * cx);
             }
         }
-        if (isu) gu[q] = s;
-        else gv[q] = s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            if (isu) gu[q] = s;
+            else gv[q] = s;
+        }
     }
 }
 
@@ -1669,7 +1678,9 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     if (g_u || g_v) {
         double *tmp = reinterpret_cast<double *>(ws + o_wind);
         double *gu = g_u ? g_u : tmp, *gv = g_v ? g_v : tmp + nu;
-        const int wg = (int)((nu + nv + kAdjThreads - 1) / kAdjThreads);
+        // one warp per face
+        const size_t wt = (nu + nv) * 32;
+        const int wg = (int)((wt + kAdjThreads - 1) / kAdjThreads);
         k_adj_wind<T><<<wg, kAdjThreads, 0, st>>>(a, gun, gvn, gu, gv);
         ADJ_CHECK(cudaGetLastError());
     }
