@@ -121,6 +121,47 @@ def test_members_equal_single_runs(pkg, prec, moisture):
     pkg.fire_ensemble_destroy(ens)
 
 
+def test_full_ensemble_members_equal_single_runs(pkg):
+    """The benchmark's ensemble: 64 members of fire meshes 390^2..2050^2
+    (96.8 M nodes), FP32, 60 steps in one call with the autotuned strips.
+    The smallest, the largest and two middle members equal the same members
+    run alone with the same strip shape bit for bit (psi, t_i, F and both
+    heat grids), so the single-run parity and FP32 tolerances carry over to
+    every member size of that workload."""
+    import torch
+    sizes = synth.ensemble_sizes(64)
+    ws = [synth.ensemble_member(k, s, steps=60) for k, s in enumerate(sizes)]
+    ens, winds = make_ensemble(pkg, ws, "fp32")
+    us = [u for u, _ in winds]
+    vs = [v for _, v in winds]
+    dt = ws[0].dt
+    pkg.fire_ensemble_autotune(ens, 3, dt, us, vs)
+    hs = [torch.zeros((w.nya, w.nxa), dtype=torch.float64, device="cuda") for w in ws]
+    hl = [torch.zeros_like(h) for h in hs]
+    pkg.fire_ensemble_step(ens, 60, dt, us, vs, hs, hl)
+    code, per = pkg.fire_ensemble_status(ens, len(ws))
+    assert code == pkg.FIRE_OK, per
+    order = sorted(range(len(ws)), key=lambda k: ws[k].nx * ws[k].ny)
+    for m in (order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]):
+        w = ws[m]
+        single = pkg.FireModel.from_workload(w, precision="fp32")
+        v_, kx, ky = pkg.fire_get_kernel(pkg.fire_ensemble_member(ens, m))
+        pkg.fire_set_kernel(single.ctx, v_, kx, ky)
+        u, v = winds[m]
+        for _ in range(60):
+            hs1, hl1 = single.step(u, v, w.dt)
+        a = state_np(single)
+        b = member_state(pkg, ens, m, w, "fp32")
+        assert np.isfinite(a[1]).sum() > 0, m
+        for k in range(3):
+            assert np.array_equal(a[k], b[k]), (m, w.nx, k)
+        assert a[3] == b[3]
+        assert np.array_equal(hs1.cpu().numpy(), hs[m].cpu().numpy())
+        assert np.array_equal(hl1.cpu().numpy(), hl[m].cpu().numpy())
+        single.close()
+    pkg.fire_ensemble_destroy(ens)
+
+
 @pytest.mark.parametrize("moisture", [False, True])
 def test_members_match_oracle_fp64(pkg, moisture):
     ws = member_workloads()
