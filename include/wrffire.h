@@ -65,8 +65,24 @@ enum fire_error {
     FIRE_ERR_BOUNDARY = -4,  /* fire reached the boundary band (Sect. 3.1, last paragraph) */
     FIRE_ERR_NONFINITE = -5, /* non-finite wind or level-set value */
     FIRE_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
-    FIRE_ERR_STATE = -7      /* call not valid in the context's state */
+    FIRE_ERR_STATE = -7,     /* call not valid in the context's state */
+    FIRE_ERR_BOUNDS = -8     /* a kernel formed an index outside its buffer (reported
+                              * only by libraries built with FIRE_BOUNDS_CHECK,
+                              * whose kernels check every global index; the
+                              * access then goes to the buffer's first element) */
 };
+
+/* 1 if this library was built with FIRE_BOUNDS_CHECK (every global index of
+ * the step kernels checked, FIRE_ERR_BOUNDS on a bad one; slower, for
+ * testing), else 0.  No counterpart in the paper. */
+int fire_bounds_checked(void);
+
+/* Test of the index check itself (FIRE_BOUNDS_CHECK builds): one device
+ * thread checks the indices -1, 0, 9 and 10 of a 10-element buffer, touching
+ * no memory through them, and flags_host[4] receives whether each was
+ * flagged (1 0 0 1 when the check works).  FIRE_ERR_STATE in other builds;
+ * FIRE_ERR_ARG for a NULL pointer.  No counterpart in the paper. */
+int fire_bounds_selftest(int *flags_host);
 
 /* Grid and numerical parameters.
  *   eps_visc       artificial viscosity eps of eq. (F-disc), 0.4 in the paper.
@@ -389,7 +405,9 @@ int fire_kernel_time_ms(fire_ctx *ctx, double *ms, long *launches);
  *   t, dt                     model time at the step start, time step (s)
  *   heat_sens_dev, heat_lat_dev  [ny_atm][nx_atm] device double, nullable
  *   status_dev                device int that faults are OR-ed into
- *                             (bit 1 boundary, 2 non-finite), nullable; with
+ *                             (bit 1 boundary, 2 non-finite, 8 an index
+ *                             outside its buffer in a FIRE_BOUNDS_CHECK
+ *                             build), nullable; with
  *                             NULL the faults go to a status word inside the
  *                             library's fixed array that no call reads back,
  *                             so they cannot be seen: pass status_dev to

@@ -19,7 +19,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libwrffire_gb300.so")
+# the library this module loads; WRFFIRE_LIBRARY names another build of it
+# (the bounds-checked one of build.build(checked=True), for tests)
+LIB_PATH = os.environ.get("WRFFIRE_LIBRARY") or os.path.join(_HERE, "libwrffire_gb300.so")
 
 FIRE_FP64 = 0
 FIRE_FP32 = 1
@@ -31,6 +33,7 @@ FIRE_ERR_BOUNDARY = -4
 FIRE_ERR_NONFINITE = -5
 FIRE_ERR_TIMEOUT = -6
 FIRE_ERR_STATE = -7
+FIRE_ERR_BOUNDS = -8
 FIRE_KERNEL_TILE = 0
 FIRE_KERNEL_MARCH = 1
 FIRE_KERNEL_WARP = 2
@@ -51,7 +54,8 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_ensemble_destroy", "fire_set_spread_mult", "fire_set_fuel_classes",
                "fire_adjoint", "fire_autotune", "fire_ensemble_autotune",
                "fire_default_kernel", "fire_adjoint_heat", "fire_set_moisture",
-               "fire_wind_at_height", "fire_heat_insertion", "fire_set_fraction_scheme")
+               "fire_wind_at_height", "fire_heat_insertion", "fire_set_fraction_scheme",
+               "fire_bounds_checked", "fire_bounds_selftest")
 FIRE_FRACTION_SUBCELL = 0
 FIRE_FRACTION_LINEAR = 1
 
@@ -127,6 +131,8 @@ def load_library(path: str | None = None):
     L.fire_kernel_time_ms.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_long)]
     L.fire_strerror.argtypes = [C.c_int]
     L.fire_strerror.restype = C.c_char_p
+    L.fire_bounds_checked.argtypes = []
+    L.fire_bounds_selftest.argtypes = [C.POINTER(C.c_int)]
     L.fire_last_cuda_error.argtypes = []
     L.fire_last_cuda_error.restype = C.c_char_p
     L.fire_destroy.argtypes = [_P]
@@ -217,6 +223,19 @@ def _check(code, what):
 
 def fire_strerror(code: int) -> str:
     return load_library().fire_strerror(int(code)).decode()
+
+
+def fire_bounds_checked() -> bool:
+    """Whether the loaded library is the bounds-checked build."""
+    return bool(load_library().fire_bounds_checked())
+
+
+def fire_bounds_selftest():
+    """The index check of a bounds-checked build on the indices -1, 0, 9, 10
+    of a 10-element buffer: whether each was flagged (1 0 0 1 expected)."""
+    f = (C.c_int * 4)()
+    _check(load_library().fire_bounds_selftest(f), "fire_bounds_selftest")
+    return list(f)
 
 
 def fire_last_cuda_error() -> str:

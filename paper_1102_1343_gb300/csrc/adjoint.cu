@@ -314,7 +314,8 @@ __global__ void k_adj_node_wind(const AdjArgs<T> a, T *unv) {
          k += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(k % a.nx), j = (int)(k / a.nx);
         T un, vn;
-        wind_at<T>(a.u, a.v, a.nxa, a.nya, a.srx, a.sry, i, j, un, vn);
+        int st = 0;  // indices are in range by construction; the step kernels report them
+        wind_at<T>(a.u, a.v, a.nxa, a.nya, a.srx, a.sry, i, j, un, vn, st);
         unv[2 * k] = un;
         unv[2 * k + 1] = vn;
     }

@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "fire_device.cuh"
 #include "fire_internal.h"
 
 using namespace wf;
@@ -389,6 +390,19 @@ int one_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, d
 // accessors used by the ensemble (ensemble.cu)
 namespace wf {
 
+#ifdef FIRE_BOUNDS_CHECK
+// fire_bounds_selftest: the index check on -1, 0, 9, 10 of a 10-element
+// buffer (the checked indices are not used for any access)
+__global__ void k_bounds_selftest(int *flags) {
+    const long long idx[4] = {-1, 0, 9, 10};
+    for (int q = 0; q < 4; ++q) {
+        int st = 0;
+        (void)bounds_checked(idx[q], 10, st);
+        flags[q] = (st & ST_BOUNDS) ? 1 : 0;
+    }
+}
+#endif
+
 static long cdiv_l(long a, long b) { return (a + b - 1) / b; }
 
 DefaultShape default_shape(bool fp64, int nx_atm, int ny_atm, int srx, int sry, int n_sm) {
@@ -518,6 +532,30 @@ extern "C" {
 
 const char *fire_last_cuda_error(void) { return wf::g_last_error_ptr(); }
 
+int fire_bounds_checked(void) {
+#ifdef FIRE_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int fire_bounds_selftest(int *flags_host) {
+    if (!flags_host) return FIRE_ERR_ARG;
+#ifdef FIRE_BOUNDS_CHECK
+    int *d = nullptr;
+    WF_CHECK(cudaMalloc(&d, 4 * sizeof(int)));
+    wf::k_bounds_selftest<<<1, 1>>>(d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(flags_host, d, 4 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    WF_CHECK(e);
+    return FIRE_OK;
+#else
+    return FIRE_ERR_STATE;
+#endif
+}
+
 const char *fire_strerror(int code) {
     switch (code) {
         case FIRE_OK: return "ok";
@@ -528,6 +566,7 @@ const char *fire_strerror(int code) {
         case FIRE_ERR_NONFINITE: return "non-finite wind or level-set value";
         case FIRE_ERR_TIMEOUT: return "a bounded device wait timed out";
         case FIRE_ERR_STATE: return "call not valid in this state";
+        case FIRE_ERR_BOUNDS: return "index outside its buffer (bounds-checked build)";
         default: return "unknown error";
     }
 }
@@ -876,6 +915,7 @@ int fire_status(fire_ctx *c) {
     WF_CHECK(cudaStreamSynchronize(c->stream));
     int st = 0;
     WF_CHECK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_BOUNDS) return FIRE_ERR_BOUNDS;
     if (st & ST_NONFINITE) return FIRE_ERR_NONFINITE;
     if (st & ST_BOUNDARY) return FIRE_ERR_BOUNDARY;
     if (st & ST_TIMEOUT) return FIRE_ERR_TIMEOUT;

@@ -644,7 +644,9 @@ int fire_ensemble_status(fire_ensemble *e, int *member_status) {
     for (int m = 0; m < e->n; ++m) {
         const int s = fire_status(e->members[m]);
         if (member_status) member_status[m] = s;
-        if (s != FIRE_OK && (worst == FIRE_OK || s == FIRE_ERR_NONFINITE)) worst = s;
+        if (s != FIRE_OK && worst != FIRE_ERR_BOUNDS &&
+            (worst == FIRE_OK || s == FIRE_ERR_NONFINITE || s == FIRE_ERR_BOUNDS))
+            worst = s;
     }
     if (b.status & ST_TIMEOUT) return FIRE_ERR_TIMEOUT;
     return worst;

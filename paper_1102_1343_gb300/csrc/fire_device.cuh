@@ -12,6 +12,30 @@
 
 namespace wf {
 
+// Index checks of the checked build (compiled with -DFIRE_BOUNDS_CHECK): an
+// index outside [0, n) sets ST_BOUNDS in the status variable st and becomes
+// 0, so the access stays inside its buffer and the kernel runs on (no trap,
+// the status reports it).  In the normal build WF_CHK(i, n, st) is i.  An
+// access of two adjacent elements checks its first index against n - 1.
+#ifdef FIRE_BOUNDS_CHECK
+__device__ __forceinline__ long long bounds_checked(long long i, long long n, int &st) {
+    if (i < 0 || i >= n) {
+        st |= ST_BOUNDS;
+        return 0;
+    }
+    return i;
+}
+#define WF_CHK(i, n, st) (::wf::bounds_checked((long long)(i), (long long)(n), (st)))
+// offset off from a row start base (a pointer already advanced by base):
+// base + off is checked, the offset returned
+#define WF_CHK_AT(base, off, n, st) \
+    (::wf::bounds_checked((long long)(base) + (long long)(off), (long long)(n), (st)) - \
+     (long long)(base))
+#else
+#define WF_CHK(i, n, st) (i)
+#define WF_CHK_AT(base, off, n, st) (off)
+#endif
+
 // ---------------------------------------------------------------------------
 // precision-dependent math.  FP32: hardware approximations (the FP32 path is
 // held to tolerances on ignition time, burnt area and total heat, not to
@@ -164,23 +188,27 @@ __device__ __forceinline__ void lin_idx(T f, int n, int &k0, int &k1, T &w) {
 template <typename T>
 __device__ __forceinline__ void wind_at(const T *__restrict__ u, const T *__restrict__ v,
                                         int nxa, int nya, int srx, int sry, int gx, int gy,
-                                        T &un, T &vn) {
+                                        T &un, T &vn, int &st) {
     T xa = (T(gx) + T(0.5)) / T(srx);
     T ya = (T(gy) + T(0.5)) / T(sry);
     int i0, i1, j0, j1;
     T wx, wy;
     lin_idx<T>(xa, nxa + 1, i0, i1, wx);
     lin_idx<T>(ya - T(0.5), nya, j0, j1, wy);
-    const T *r0 = u + (size_t)j0 * (nxa + 1);
-    const T *r1 = u + (size_t)j1 * (nxa + 1);
-    un = (T(1) - wy) * ((T(1) - wx) * __ldg(r0 + i0) + wx * __ldg(r0 + i1)) +
-         wy * ((T(1) - wx) * __ldg(r1 + i0) + wx * __ldg(r1 + i1));
+    const long long nu = (long long)nya * (nxa + 1);
+    const size_t b0 = (size_t)j0 * (nxa + 1), b1 = (size_t)j1 * (nxa + 1);
+    un = (T(1) - wy) * ((T(1) - wx) * __ldg(u + WF_CHK(b0 + i0, nu, st)) +
+                        wx * __ldg(u + WF_CHK(b0 + i1, nu, st))) +
+         wy * ((T(1) - wx) * __ldg(u + WF_CHK(b1 + i0, nu, st)) +
+               wx * __ldg(u + WF_CHK(b1 + i1, nu, st)));
     lin_idx<T>(xa - T(0.5), nxa, i0, i1, wx);
     lin_idx<T>(ya, nya + 1, j0, j1, wy);
-    r0 = v + (size_t)j0 * nxa;
-    r1 = v + (size_t)j1 * nxa;
-    vn = (T(1) - wy) * ((T(1) - wx) * __ldg(r0 + i0) + wx * __ldg(r0 + i1)) +
-         wy * ((T(1) - wx) * __ldg(r1 + i0) + wx * __ldg(r1 + i1));
+    const long long nv = (long long)(nya + 1) * nxa;
+    const size_t c0 = (size_t)j0 * nxa, c1 = (size_t)j1 * nxa;
+    vn = (T(1) - wy) * ((T(1) - wx) * __ldg(v + WF_CHK(c0 + i0, nv, st)) +
+                        wx * __ldg(v + WF_CHK(c0 + i1, nv, st))) +
+         wy * ((T(1) - wx) * __ldg(v + WF_CHK(c1 + i0, nv, st)) +
+               wx * __ldg(v + WF_CHK(c1 + i1, nv, st)));
 }
 
 // Right-hand side of eq. (F-disc) at a node from its value p and its four

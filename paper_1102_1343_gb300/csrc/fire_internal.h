@@ -10,8 +10,9 @@
 
 namespace wf {
 
-// sticky device status bits
-enum { ST_BOUNDARY = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
+// sticky device status bits (ST_BOUNDS only in libraries built with
+// FIRE_BOUNDS_CHECK)
+enum { ST_BOUNDARY = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_BOUNDS = 8 };
 
 // per-class coefficient slots: eq. (spread-WRF-Fire) + T_f + heat factors
 enum { K_S0 = 0, K_R0, K_B, K_C, K_D, K_E, K_TF, K_HS, K_HQ, K_N };

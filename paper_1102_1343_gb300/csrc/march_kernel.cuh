@@ -160,7 +160,7 @@ struct MarchStrip {
     double hscale;     // 1 / (dt srx sry)
     int ju_hi, jv_hi;  // highest atmos rows in this thread's wind ring
     int bcnt, bpar;    // rows done in the current band, band parity
-    int st;
+    mutable int st;  // status bits (also set by the const loaders' index checks)
 
     __device__ __forceinline__ MarchStrip(const StepArgs &args, MarchSmem<T> &s) : a(args), sm(s) {}
 
@@ -176,10 +176,10 @@ struct MarchStrip {
         const size_t rowb = (size_t)r * nx;
         if (vec) {
             const int xc = min(max(xa, 0), nx - 2);
-            return *reinterpret_cast<const T2 *>(f + rowb + xc);
+            return *reinterpret_cast<const T2 *>(f + WF_CHK(rowb + xc, (long long)nx * ny - 1, st));
         }
         const int xA = min(max(xa, 0), nx - 1), xB = min(max(xa + 1, 0), nx - 1);
-        return mk2(f[rowb + xA], f[rowb + xB]);
+        return mk2(f[WF_CHK(rowb + xA, (long long)nx * ny, st)], f[WF_CHK(rowb + xB, (long long)nx * ny, st)]);
     }
 
     __device__ __forceinline__ void load_env(int r) {
@@ -187,10 +187,10 @@ struct MarchStrip {
         const size_t rowb = (size_t)r * nx;
         if (vec) {
             const int xc = min(max(xa, 0), nx - 2);
-            pf_fa = *reinterpret_cast<const uint16_t *>(a.fuel + rowb + xc);
+            pf_fa = *reinterpret_cast<const uint16_t *>(a.fuel + WF_CHK(rowb + xc, (long long)nx * ny - 1, st));
         } else {
-            pf_fa = a.fuel[rowb + min(max(xa, 0), nx - 1)];
-            pf_fb = a.fuel[rowb + min(max(xa + 1, 0), nx - 1)];
+            pf_fa = a.fuel[WF_CHK(rowb + min(max(xa, 0), nx - 1), (long long)nx * ny, st)];
+            pf_fb = a.fuel[WF_CHK(rowb + min(max(xa + 1, 0), nx - 1), (long long)nx * ny, st)];
         }
         pf_zx = ld2(static_cast<const T *>(a.dzdx), r);
         pf_zy = ld2(static_cast<const T *>(a.dzdy), r);
@@ -204,19 +204,27 @@ struct MarchStrip {
 
     // x-interpolated wind of atmos u-row J / v-row J for this thread's columns
     __device__ __forceinline__ void fill_wind_u(int J) {
-        const T *u = static_cast<const T *>(a.u) + (size_t)J * (nxa + 1);
+        const T *u = static_cast<const T *>(a.u);
+        const size_t b = (size_t)J * (nxa + 1);
+        const long long n = (long long)nya * (nxa + 1);
         T2 v;
         const MarchCol<T> &c0 = sm.col[2 * c], &c1 = sm.col[2 * c + 1];
-        v.x = (T(1) - c0.wxu) * __ldg(u + c0.iu0) + c0.wxu * __ldg(u + c0.iu1);
-        v.y = (T(1) - c1.wxu) * __ldg(u + c1.iu0) + c1.wxu * __ldg(u + c1.iu1);
+        v.x = (T(1) - c0.wxu) * __ldg(u + WF_CHK(b + c0.iu0, n, st)) +
+              c0.wxu * __ldg(u + WF_CHK(b + c0.iu1, n, st));
+        v.y = (T(1) - c1.wxu) * __ldg(u + WF_CHK(b + c1.iu0, n, st)) +
+              c1.wxu * __ldg(u + WF_CHK(b + c1.iu1, n, st));
         sm.UX[(J & 3) * kMarchThreads + c] = v;
     }
     __device__ __forceinline__ void fill_wind_v(int J) {
-        const T *w = static_cast<const T *>(a.v) + (size_t)J * nxa;
+        const T *w = static_cast<const T *>(a.v);
+        const size_t b = (size_t)J * nxa;
+        const long long n = (long long)(nya + 1) * nxa;
         T2 v;
         const MarchCol<T> &c0 = sm.col[2 * c], &c1 = sm.col[2 * c + 1];
-        v.x = (T(1) - c0.wxv) * __ldg(w + c0.iv0) + c0.wxv * __ldg(w + c0.iv1);
-        v.y = (T(1) - c1.wxv) * __ldg(w + c1.iv0) + c1.wxv * __ldg(w + c1.iv1);
+        v.x = (T(1) - c0.wxv) * __ldg(w + WF_CHK(b + c0.iv0, n, st)) +
+              c0.wxv * __ldg(w + WF_CHK(b + c0.iv1, n, st));
+        v.y = (T(1) - c1.wxv) * __ldg(w + WF_CHK(b + c1.iv0, n, st)) +
+              c1.wxv * __ldg(w + WF_CHK(b + c1.iv1, n, st));
         sm.VX[(J & 3) * kMarchThreads + c] = v;
     }
 
@@ -361,11 +369,11 @@ struct MarchStrip {
                         if (!need[j]) continue;
                         const T p0 = pick<T>(p0v, j), pn = pick<T>(PN, j);
                         const bool cross = p0 > T(0);
-                        double ti = a.tign[g + j];
+                        double ti = a.tign[WF_CHK(g + j, (long long)nx * ny, st)];
                         if (cross && isinf(ti)) {
                             const double q0 = (double)p0, q1 = (double)pn;
                             ti = tstart + q0 * a.dt / (q0 - q1);
-                            if (own_row && m_out[j]) a.tign[g + j] = ti;
+                            if (own_row && m_out[j]) a.tign[WF_CHK(g + j, (long long)nx * ny, st)] = ti;
                         }
                         if (pn < T(0)) {
                             if (j == 0) DL.x = T(t1 - ti);
@@ -378,10 +386,10 @@ struct MarchStrip {
                 if (own_row) {
                     T *po = static_cast<T *>(a.psi_out);
                     if (vec && m_out[0] && m_out[1]) {
-                        *reinterpret_cast<T2 *>(po + g) = PN;
+                        *reinterpret_cast<T2 *>(po + WF_CHK(g, (long long)nx * ny - 1, st)) = PN;
                     } else {
-                        if (m_out[0]) po[g] = PN.x;
-                        if (m_out[1]) po[g + 1] = PN.y;
+                        if (m_out[0]) po[WF_CHK(g, (long long)nx * ny, st)] = PN.x;
+                        if (m_out[1]) po[WF_CHK(g + 1, (long long)nx * ny, st)] = PN.y;
                     }
                 }
             }
@@ -460,7 +468,7 @@ struct MarchStrip {
                             }
                         }
                     }
-                    const int cls0 = a.fuel[(size_t)rd * nx + x];
+                    const int cls0 = a.fuel[WF_CHK((size_t)rd * nx + x, (long long)nx * ny, st)];
                     const int cls = cls0 > ncm1 ? ncm1 : cls0;
                     Fn[j] = cell_fraction_vals<T>(q[0][0], q[0][1], q[0][2], q[1][0], q[1][1],
                                                   q[1][2], q[2][0], q[2][1], q[2][2], e[0][0],
@@ -474,10 +482,10 @@ struct MarchStrip {
             FN.x = Fn[0];
             FN.y = Fn[1];
             if (vec && m_out[0] && m_out[1]) {
-                *reinterpret_cast<T2 *>(fo + g) = FN;
+                *reinterpret_cast<T2 *>(fo + WF_CHK(g, (long long)nx * ny - 1, st)) = FN;
             } else {
-                if (m_out[0]) fo[g] = FN.x;
-                if (m_out[1]) fo[g + 1] = FN.y;
+                if (m_out[0]) fo[WF_CHK(g, (long long)nx * ny, st)] = FN.x;
+                if (m_out[1]) fo[WF_CHK(g + 1, (long long)nx * ny, st)] = FN.y;
             }
             // heat flux densities, only in warps where some fuel burned
             const T dF0 = m_out[0] ? Fcur.x - Fn[0] : T(0);
@@ -488,10 +496,10 @@ struct MarchStrip {
                     const T dF = j == 0 ? dF0 : dF1;
                     if (dF != T(0)) {
                         if constexpr (NC) {
-                            acc_s[j] += dF * static_cast<const T *>(a.nco[3])[g + j];
-                            acc_q[j] += dF * static_cast<const T *>(a.nco[4])[g + j];
+                            acc_s[j] += dF * static_cast<const T *>(a.nco[3])[WF_CHK(g + j, (long long)nx * ny, st)];
+                            acc_q[j] += dF * static_cast<const T *>(a.nco[4])[WF_CHK(g + j, (long long)nx * ny, st)];
                         } else {
-                            const int cls0 = a.fuel[g + j];
+                            const int cls0 = a.fuel[WF_CHK(g + j, (long long)nx * ny, st)];
                             const int cls = cls0 > ncm1 ? ncm1 : cls0;
                             acc_s[j] += dF * sm.lut[cls * 8 + 7];
                             acc_q[j] += dF * sm.lutq[cls];
@@ -527,7 +535,7 @@ struct MarchStrip {
                     h0 += hb[lc];
                     h1 += hb[2 * NT + lc];
                 }
-                const size_t ga = (size_t)(rd / sry) * nxa + (x0 / srx + c);
+                const size_t ga = WF_CHK((size_t)(rd / sry) * nxa + (x0 / srx + c), (long long)nxa * nya, st);
                 if (a.heat_s) a.heat_s[ga] = (double)h0 * hscale;
                 if (a.heat_l) a.heat_l[ga] = (double)h1 * hscale;
             }

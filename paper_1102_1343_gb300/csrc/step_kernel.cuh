@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
     }
     for (int k = tid; k < a.ncls * K_N; k += kThreads) lut[k] = T(a.coef[k]);
 
+    int st = 0;
     // ---- A: psi^n on the tile + 3 halo (0 outside the domain)
     for (int ly = ty; ly < BH3; ly += kThreadsY) {
         const int gy = y0 - 3 + ly;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
         for (int lx = tx; lx < BW3; lx += kThreadsX) {
             const int gx = x0 - 3 + lx;
             T val = T(0);
-            if (rowin && gx >= 0 && gx < nx) val = psi_in[(size_t)gy * nx + gx];
+            if (rowin && gx >= 0 && gx < nx) val = psi_in[WF_CHK((size_t)gy * nx + gx, (long long)nx * ny, st)];
             P0[ly * BW3 + lx] = val;
         }
     }
@@ -195,7 +196,6 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
     const bool edge_tile = (x0 - 3 < 0) || (y0 - 3 < 0) || (x0 + TX + 3 > nx) || (y0 + TY + 3 > ny);
     if (edge_tile) fill_ghosts<T>(P0, BW3, BH3, x0 - 3, y0 - 3, nx, ny, tid);
 
-    int st = 0;
     // ---- C: stage 1 on the tile + 2 halo: F1 = F(psi^n), psi* = psi^n + dt F1
     for (int ly = ty; ly < BH2; ly += kThreadsY) {
         const int gy = y0 - 2 + ly;
@@ -205,11 +205,11 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
                 P1[ly * BW2 + lx] = T(0);
                 continue;
             }
-            const size_t g = (size_t)gy * nx + gx;
+            const size_t g = WF_CHK((size_t)gy * nx + gx, (long long)nx * ny, st);
             int cls = fuel[g];
             cls = cls > ncm1 ? ncm1 : cls;
             T un, vn;
-            wind_at<T>(wu, wv, a.nxa, a.nya, srx, sry, gx, gy, un, vn);
+            wind_at<T>(wu, wv, a.nxa, a.nya, srx, sry, gx, gy, un, vn, st);
             if (!finite_val(un) || !finite_val(vn)) st |= ST_NONFINITE;
             const T m = mult ? mult[g] : T(1);
             const int c = (ly + 1) * BW3 + (lx + 1);
@@ -235,11 +235,11 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
                 Dl[l1] = T(0);
                 continue;
             }
-            const size_t g = (size_t)gy * nx + gx;
+            const size_t g = WF_CHK((size_t)gy * nx + gx, (long long)nx * ny, st);
             int cls = fuel[g];
             cls = cls > ncm1 ? ncm1 : cls;
             T un, vn;
-            wind_at<T>(wu, wv, a.nxa, a.nya, srx, sry, gx, gy, un, vn);
+            wind_at<T>(wu, wv, a.nxa, a.nya, srx, sry, gx, gy, un, vn, st);
             const T m = mult ? mult[g] : T(1);
             T cn[6];
             node_coef(cls, g, cn);
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
             T hs = T(0), hq = T(0);
             if (lx < TXa && ly < TYa) {
                 const int gx = x0 + lx;
-                const size_t g = (size_t)gy * nx + gx;
+                const size_t g = WF_CHK((size_t)gy * nx + gx, (long long)nx * ny, st);
                 int cls = fuel[g];
                 cls = cls > ncm1 ? ncm1 : cls;
                 const T *co = lut + cls * K_N;
@@ -338,9 +338,12 @@ __global__ void __launch_bounds__(kThreads) k_fire_step(const StepArgs a) {
             if (s[0] != T(0)) h0 += (double)s[0];
             if (s[1] != T(0)) h1 += (double)s[1];
         }
-        const size_t ga = (size_t)(y0 / sry + J) * a.nxa + (x0 / srx + I);
+        int sth = 0;
+        const size_t ga = WF_CHK((size_t)(y0 / sry + J) * a.nxa + (x0 / srx + I),
+                                 (long long)a.nxa * a.nya, sth);
         if (a.heat_s) a.heat_s[ga] = h0 * scale;
         if (a.heat_l) a.heat_l[ga] = h1 * scale;
+        if (sth) atomicOr(a.status, sth);
     }
     if (tid == 0 && s_status) atomicOr(a.status, s_status);
 }

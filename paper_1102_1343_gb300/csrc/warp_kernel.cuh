@@ -89,7 +89,7 @@ struct WarpStrip {
     bool bedge;      // the strip touches the boundary band in x
     V idx2, idy2, i2dx2, i2dy2, eps2, ndt2, ndth2;
     double tstart, t1, hscale;
-    int st;
+    mutable int st;  // status bits (also set by the const loaders' index checks)
     V poison;
     // wind: x-interpolation per column, two atmos rows held per component
     int iu0[2], iu1[2], iv0[2], iv1[2];
@@ -108,8 +108,8 @@ struct WarpStrip {
     // iteration later and the prefetch hides the memory latency.
     __device__ __forceinline__ V ld(const T *__restrict__ f, int r) const {
         const int rowb = r * nx;
-        if (vec) return *reinterpret_cast<const V *>(f + (rowb + xcv));
-        return mk2(f[rowb + xcA], f[rowb + xcB]);
+        if (vec) return *reinterpret_cast<const V *>(f + WF_CHK(rowb + xcv, nx * ny - 1, st));
+        return mk2(f[WF_CHK(rowb + xcA, nx * ny, st)], f[WF_CHK(rowb + xcB, nx * ny, st)]);
     }
 
     // prefetch of a row's environment: raw fuel bytes (decoded by decode()
@@ -117,10 +117,10 @@ struct WarpStrip {
     __device__ __forceinline__ void load_env(int r, WEnv<T> &e) const {
         const int rowb = r * nx;
         if (vec) {
-            e.cls0 = *reinterpret_cast<const uint16_t *>(a.fuel + (rowb + xcv));
+            e.cls0 = *reinterpret_cast<const uint16_t *>(a.fuel + WF_CHK(rowb + xcv, nx * ny - 1, st));
         } else {
-            e.cls0 = a.fuel[rowb + xcA];
-            e.cls1 = a.fuel[rowb + xcB];
+            e.cls0 = a.fuel[WF_CHK(rowb + xcA, nx * ny, st)];
+            e.cls1 = a.fuel[WF_CHK(rowb + xcB, nx * ny, st)];
         }
         e.zx = ld(static_cast<const T *>(a.dzdx), r);
         e.zy = ld(static_cast<const T *>(a.dzdy), r);
@@ -150,13 +150,19 @@ struct WarpStrip {
     // x-interpolated wind of atmos row J at this lane's columns
     __device__ __forceinline__ V wind_u_row(int J) const {
         const T *u = static_cast<const T *>(a.u) + (size_t)J * (nxa + 1);
-        return mk2((T(1) - wxu[0]) * __ldg(u + iu0[0]) + wxu[0] * __ldg(u + iu1[0]),
-                   (T(1) - wxu[1]) * __ldg(u + iu0[1]) + wxu[1] * __ldg(u + iu1[1]));
+        const int b = J * (nxa + 1), n = nya * (nxa + 1);  // (index checks only)
+        return mk2((T(1) - wxu[0]) * __ldg(u + WF_CHK_AT(b, iu0[0], n, st)) +
+                       wxu[0] * __ldg(u + WF_CHK_AT(b, iu1[0], n, st)),
+                   (T(1) - wxu[1]) * __ldg(u + WF_CHK_AT(b, iu0[1], n, st)) +
+                       wxu[1] * __ldg(u + WF_CHK_AT(b, iu1[1], n, st)));
     }
     __device__ __forceinline__ V wind_v_row(int J) const {
         const T *v = static_cast<const T *>(a.v) + (size_t)J * nxa;
-        return mk2((T(1) - wxv[0]) * __ldg(v + iv0[0]) + wxv[0] * __ldg(v + iv1[0]),
-                   (T(1) - wxv[1]) * __ldg(v + iv0[1]) + wxv[1] * __ldg(v + iv1[1]));
+        const int b = J * nxa, n = (nya + 1) * nxa;  // (index checks only)
+        return mk2((T(1) - wxv[0]) * __ldg(v + WF_CHK_AT(b, iv0[0], n, st)) +
+                       wxv[0] * __ldg(v + WF_CHK_AT(b, iv1[0], n, st)),
+                   (T(1) - wxv[1]) * __ldg(v + WF_CHK_AT(b, iv0[1], n, st)) +
+                       wxv[1] * __ldg(v + WF_CHK_AT(b, iv1[1], n, st)));
     }
 
     // bilinear wind at fire row r (Sect. 5), rows of the atmos wind cached;
@@ -294,7 +300,7 @@ struct WarpStrip {
         auto load_psi = [&](int r, V &v, T &h) {
             r = min(max(r, 0), ny - 1);
             v = ld(psi_in, r);
-            if (hlane) h = psi_in[r * nx + hcol];
+            if (hlane) h = psi_in[WF_CHK(r * nx + hcol, nx * ny, st)];
         };
         load_psi(kb, P0, h1);  // h1 of row kb is not used
         load_psi(kb + 1, P1, h1);
@@ -373,12 +379,14 @@ struct WarpStrip {
                         const T p0 = j == 0 ? P0.x : P0.y, pn = j == 0 ? N0.x : N0.y;
                         // Dense: prefetched where psi^n <= 0, read here at a crossing
                         double ti;
-                        if constexpr (Dense) ti = p0 <= T(0) ? (j == 0 ? tiA : tiB) : a.tign[g + j];
-                        else ti = a.tign[g + j];
+                        if constexpr (Dense)
+                            ti = p0 <= T(0) ? (j == 0 ? tiA : tiB) : a.tign[WF_CHK(g + j, nx * ny, st)];
+                        else
+                            ti = a.tign[WF_CHK(g + j, nx * ny, st)];
                         if (p0 > T(0) && tign_unset(ti)) {
                             const double q0 = (double)p0, q1 = (double)pn;
                             ti = tstart + q0 * a.dt / (q0 - q1);
-                            if (own_row && (j == 0 ? outA : outB)) a.tign[g + j] = ti;
+                            if (own_row && (j == 0 ? outA : outB)) a.tign[WF_CHK(g + j, nx * ny, st)] = ti;
                         }
                         if (pn < T(0)) {
                             if (j == 0) D0.x = T(t1 - ti);
@@ -389,10 +397,10 @@ struct WarpStrip {
                 if (own_row) {
                     T *po = static_cast<T *>(a.psi_out);
                     const int g = rC * nx + xa;
-                    if (pst) *reinterpret_cast<V *>(po + g) = N0;
+                    if (pst) *reinterpret_cast<V *>(po + WF_CHK(g, nx * ny - 1, st)) = N0;
                     if (slow) {
-                        if (!pst && outA) po[g] = N0.x;
-                        if (!pst && outB) po[g + 1] = N0.y;
+                        if (!pst && outA) po[WF_CHK(g, nx * ny, st)] = N0.x;
+                        if (!pst && outB) po[WF_CHK(g + 1, nx * ny, st)] = N0.y;
                     }
                 }
             }
@@ -404,8 +412,8 @@ struct WarpStrip {
                 const int rn = k + 1;
                 const bool rin = rn >= y0 - 1 && rn >= 0 && rn < ny;
                 const int g = rn * nx + xa;
-                if (rin && inA && lane > 0 && P1.x <= T(0)) tiA = a.tign[g];
-                if (rin && inB && lane < 31 && P1.y <= T(0)) tiB = a.tign[g + 1];
+                if (rin && inA && lane > 0 && P1.x <= T(0)) tiA = a.tign[WF_CHK(g, nx * ny, st)];
+                if (rin && inB && lane < 31 && P1.y <= T(0)) tiB = a.tign[WF_CHK(g + 1, nx * ny, st)];
             }
             // ---- D: fuel fraction and heat on row k-1
             const int rD = k - 1;
@@ -484,7 +492,8 @@ struct WarpStrip {
                             ep[b][2] = mk2(Dr[b].y, dr[b]);
                         }
                         const int g = rD * nx + xa;
-                        const int ca = ba ? a.fuel[g] : 0, cb = bb ? a.fuel[g + 1] : 0;
+                        const int ca = ba ? a.fuel[WF_CHK(g, nx * ny, st)] : 0;
+                        const int cb = bb ? a.fuel[WF_CHK(g + 1, nx * ny, st)] : 0;
                         const float2 tf = mk2(lut[(ca > ncm1 ? ncm1 : ca) * 8 + 6],
                                               lut[(cb > ncm1 ? ncm1 : cb) * 8 + 6]);
                         const float2 f = cell_fraction_pair(qp, ep, tf);
@@ -544,7 +553,7 @@ struct WarpStrip {
                         }
                     }
                 }
-                const int cls0 = a.fuel[rD * nx + x];
+                const int cls0 = a.fuel[WF_CHK(rD * nx + x, nx * ny, st)];
                 const int cls = cls0 > ncm1 ? ncm1 : cls0;
                 const T f = cell_fraction_vals<T>(q[0][0], q[0][1], q[0][2], q[1][0], q[1][1],
                                                   q[1][2], q[2][0], q[2][1], q[2][2], e[0][0],
@@ -561,10 +570,10 @@ struct WarpStrip {
     __device__ __forceinline__ void finish_row(int rD, V Fn, V F1) {
         const int g = rD * nx + xa;
         T *fo = static_cast<T *>(a.F_out);
-        if (pst) *reinterpret_cast<V *>(fo + g) = F1;
+        if (pst) *reinterpret_cast<V *>(fo + WF_CHK(g, nx * ny - 1, st)) = F1;
         if (slow) {
-            if (!pst && outA) fo[g] = F1.x;
-            if (!pst && outB) fo[g + 1] = F1.y;
+            if (!pst && outA) fo[WF_CHK(g, nx * ny, st)] = F1.x;
+            if (!pst && outB) fo[WF_CHK(g + 1, nx * ny, st)] = F1.y;
         }
         // heat flux densities of the row, summed per column over the band
         // (the vote on every column of the warp, the sums on output columns)
@@ -575,22 +584,22 @@ struct WarpStrip {
                 const T *hs = static_cast<const T *>(a.nco[3]);
                 const T *hq = static_cast<const T *>(a.nco[4]);
                 if (dFa != T(0)) {
-                    acc_s.x += dFa * hs[g];
-                    acc_q.x += dFa * hq[g];
+                    acc_s.x += dFa * hs[WF_CHK(g, nx * ny, st)];
+                    acc_q.x += dFa * hq[WF_CHK(g, nx * ny, st)];
                 }
                 if (dFb != T(0)) {
-                    acc_s.y += dFb * hs[g + 1];
-                    acc_q.y += dFb * hq[g + 1];
+                    acc_s.y += dFb * hs[WF_CHK(g + 1, nx * ny, st)];
+                    acc_q.y += dFb * hq[WF_CHK(g + 1, nx * ny, st)];
                 }
             } else {
                 if (dFa != T(0)) {
-                    int cls = a.fuel[g];
+                    int cls = a.fuel[WF_CHK(g, nx * ny, st)];
                     cls = cls > ncm1 ? ncm1 : cls;
                     acc_s.x += dFa * lut[cls * 8 + 7];
                     acc_q.x += dFa * lutq[cls];
                 }
                 if (dFb != T(0)) {
-                    int cls = a.fuel[g + 1];
+                    int cls = a.fuel[WF_CHK(g + 1, nx * ny, st)];
                     cls = cls > ncm1 ? ncm1 : cls;
                     acc_s.y += dFb * lut[cls * 8 + 7];
                     acc_q.y += dFb * lutq[cls];
@@ -616,14 +625,14 @@ struct WarpStrip {
                         h0 += hw[lc];
                         h1 += hw[64 + lc];
                     }
-                    const size_t ga = (size_t)(rD / sry) * nxa + (x0 / srx + lane);
+                    const size_t ga = WF_CHK((size_t)(rD / sry) * nxa + (x0 / srx + lane), nxa * nya, st);
                     if (a.heat_s) a.heat_s[ga] = (double)h0 * hscale;
                     if (a.heat_l) a.heat_l[ga] = (double)h1 * hscale;
                 }
                 __syncwarp();
                 acc_s = acc_q = splat<V>(T(0));
             } else if (lane * srx < Wa) {
-                const size_t ga = (size_t)(rD / sry) * nxa + (x0 / srx + lane);
+                const size_t ga = WF_CHK((size_t)(rD / sry) * nxa + (x0 / srx + lane), nxa * nya, st);
                 if (a.heat_s) a.heat_s[ga] = 0.0;
                 if (a.heat_l) a.heat_l[ga] = 0.0;
             }
