@@ -240,7 +240,7 @@ __device__ __forceinline__ void node_partials(T p, T pl, T pr, T pd, T pu, T idx
     // the unit normal n = c/|c|: dn/dc = (I - n n^T)/|c|
     T dS_dcx = T(0), dS_dcy = T(0);
     if (cn2 > Mth<T>::kNormMin) {
-        const T rc = Mth<T>::dv(T(1), Mth<T>::sqr(cn2));
+        const T rc = Mth<T>::rsq(cn2);
         const T dU_dcx = (e.un - U * nxv) * rc, dU_dcy = (e.vn - U * nyv) * rc;
         const T dT_dcx = (e.zx - tp * nxv) * rc, dT_dcy = (e.zy - tp * nyv) * rc;
         dS_dcx = e.m * (dSt_dU * dU_dcx + dSt_dT * dT_dcx);
@@ -250,8 +250,9 @@ __device__ __forceinline__ void node_partials(T p, T pl, T pr, T pd, T pu, T idx
     // d|grad|/d(one-sided differences) through the taken branch
     T wx = T(0), wy = T(0);
     if (grad > T(0)) {
-        wx = Mth<T>::dv(gx, grad);
-        wy = Mth<T>::dv(gy, grad);
+        const T rg = Mth<T>::dv(T(1), grad);
+        wx = gx * rg;
+        wy = gy * rg;
     }
     T dG[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (xm) {

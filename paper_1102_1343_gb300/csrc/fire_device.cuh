@@ -92,6 +92,8 @@ struct Mth<float> {
     }
     // x >= 0 (a sum of squares)
     static __device__ __forceinline__ float sqr(float x) { return sqrt_ftz(x); }
+    // 1/sqrt(x) for x > 0
+    static __device__ __forceinline__ float rsq(float x) { return rsqrt_ftz(x); }
     // unit vector of (cx, cy); zero vector when the norm vanishes
     static __device__ __forceinline__ void unit(float cx, float cy, float &nx, float &ny) {
         const float n2 = fmaf(cx, cx, cy * cy);
@@ -120,6 +122,7 @@ struct Mth<double> {
         return 1.0 - a / b;
     }
     static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
     // unit vector of (cx, cy) (the reciprocal square root of the squared
     // norm, two products); zero vector when the norm vanishes
     static __device__ __forceinline__ void unit(double cx, double cy, double &nx, double &ny) {
