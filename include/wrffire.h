@@ -249,7 +249,10 @@ int fire_set_moisture(fire_ctx *ctx, const void *moisture_dev);
  * pending in those steps (else FIRE_ERR_STATE).  The context advances exactly
  * as fire_run would (same kernels, same state afterwards); its psi is saved
  * every ckpt_every steps and the states in between are recomputed during the
- * reverse sweep.
+ * reverse sweep.  ckpt_every = 1 keeps every state (nsteps + 1 of them) and
+ * recomputes nothing: the fastest form where they fit in device memory
+ * (FIRE_ERR_OOM where they do not; a larger ckpt_every then trades memory
+ * for the recomputation).
  *
  *   t_obs_dev    [NY][NX] double device; NaN or +-inf where not observed
  *   J_host       receives J (host double)
@@ -264,9 +267,11 @@ int fire_set_moisture(fire_ctx *ctx, const void *moisture_dev);
  * Gradient pointers may be NULL; with all four NULL only J is computed.
  * Derivatives follow the branches the forward values take (upwind
  * selection, limits of the spread rate, boundary extrapolation), so they are
- * one-sided at switch points.  Workspace: about (nsteps/ckpt_every +
- * ckpt_every + 4) states plus 13 path-precision values and 6 doubles per node,
- * kept by the context.
+ * one-sided at switch points.  Workspace, kept by the context: the
+ * checkpoints (nsteps/ckpt_every states, nsteps + 1 with ckpt_every = 1),
+ * with ckpt_every > 1 a ring of ckpt_every + 1 recomputed states, and per
+ * node about 6 path-precision values and 6 doubles (13 path-precision values
+ * more in FP64, for its unfused reverse step).
  * Synchronous: returns after J and the gradients are written. */
 int fire_adjoint(fire_ctx *ctx, int nsteps, double dt, const void *wind_u_dev,
                  const void *wind_v_dev, const double *t_obs_dev, int ckpt_every,

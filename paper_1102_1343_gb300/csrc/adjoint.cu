@@ -1563,15 +1563,18 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     // the reverse steps: tiles of the fused kernel, lambda^{s+1} in
     // lam + (r & 1) n for the r-th reverse step of a run of them
     if constexpr (sizeof(T) == 4) {
-        static bool rev_attr = false;
-        if (!rev_attr) {
+        // the kernel's attributes, once per device
+        static bool rev_attr[64] = {};
+        int devid = 0;
+        ADJ_CHECK(cudaGetDevice(&devid));
+        if (devid < 0 || devid >= 64 || !rev_attr[devid]) {
             ADJ_CHECK(cudaFuncSetAttribute(k_adj_step<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)rev_smem_bytes<T>(FIRE_MAX_CLASSES)));
             // all of the unified L1 as shared memory: four tiles per SM
             ADJ_CHECK(cudaFuncSetAttribute(k_adj_step<T>,
                                            cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-            rev_attr = true;
+            if (devid >= 0 && devid < 64) rev_attr[devid] = true;
         }
     }
     const dim3 rgrid((nx + kRevTX - 1) / kRevTX, (ny + kRevTY - 1) / kRevTY);
