@@ -219,7 +219,7 @@ def test_autograd_function(pkg):
     # a second evaluation from the same initial state gives the same J
     J3 = pkg.FireAdjointFn.apply(m, st0, mult.detach(), moist.detach(), u.detach(),
                                  v.detach(), tobs, w.dt, nsteps, 10)
-    assert float(J3) == float(J)
+    assert float(J3) == float(J.detach())
     m.close()
     m2.close()
 
