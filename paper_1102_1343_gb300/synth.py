@@ -320,6 +320,64 @@ def burning_fire_8200(seed=BASE_SEED) -> Workload:
                             name="burning-fire-8200x8200")
 
 
+def large_landscape(nxa, nya, sr=10, dx_atm=60.0, seed=BASE_SEED, dtype="float32",
+                    device="cuda", ignition_cells=(), steps=20, dt=0.5, patch_nodes=50,
+                    n_hills=20, max_slope=0.4, row_chunk=2048, name=None) -> Workload:
+    """The landscape recipe on meshes too large to build on the host (billions
+    of fire nodes).  fuel, dzdx and dzdy of the returned workload are torch
+    tensors on `device` (uint8, and `dtype` for the gradients), built there in
+    chunks of rows; the wind and the classes are numpy and Python values made
+    as in random_landscape.  The terrain is the same sum of Gaussian hills
+    (hills_gradient, evaluated chunk by chunk); the fuel map is random classes
+    on square patches of patch_nodes nodes (a Voronoi map needs a distance
+    transform of the whole data grid).  Point ignitions of radius 10 m at the
+    centres of the atmospheric cells (I, J) of ignition_cells."""
+    import torch
+    rng = np.random.default_rng(seed)
+    nx, ny = nxa * sr, nya * sr
+    dx = dx_atm / sr
+    u, v = smooth_wind(rng, nxa, nya, std=1.5, sigma_cells=300.0 / dx_atm)
+    classes = random_classes(rng)
+    Lx, Ly = nx * dx, ny * dx
+    dev = torch.device(device)
+    f64 = torch.float64
+
+    def col(a):
+        return torch.as_tensor(a, dtype=f64, device=dev)[:, None]
+
+    cx, cy = col(rng.uniform(0.0, Lx, n_hills)), col(rng.uniform(0.0, Ly, n_hills))
+    s2 = col(rng.uniform(200.0, 800.0, n_hills)) ** 2
+    h = torch.as_tensor(rng.uniform(0.5, 1.0, n_hills), dtype=f64, device=dev)[None, :]
+    x = (torch.arange(nx, dtype=f64, device=dev) + 0.5) * dx
+    ex = torch.exp(-((x[None, :] - cx) ** 2) / (2 * s2))  # [K, nx]
+    dex = -(x[None, :] - cx) / s2 * ex
+    dzdx = torch.empty((ny, nx), dtype=getattr(torch, dtype), device=dev)
+    dzdy = torch.empty_like(dzdx)
+    m = 0.0
+    for j0 in range(0, ny, row_chunk):
+        j1 = min(ny, j0 + row_chunk)
+        y = (torch.arange(j0, j1, dtype=f64, device=dev) + 0.5) * dx
+        ey = torch.exp(-((y[None, :] - cy) ** 2) / (2 * s2))  # [K, rows]
+        dey = -(y[None, :] - cy) / s2 * ey
+        gx = (ey.T * h) @ dex
+        gy = (dey.T * h) @ ex
+        m = max(m, float(torch.sqrt(gx * gx + gy * gy).max()))
+        dzdx[j0:j1] = gx
+        dzdy[j0:j1] = gy
+        del gx, gy
+    if m > 0:
+        dzdx.mul_(max_slope / m)
+        dzdy.mul_(max_slope / m)
+    p = patch_nodes
+    coarse = rng.integers(0, len(classes), size=(-(-ny // p), -(-nx // p))).astype(np.uint8)
+    fuel = torch.as_tensor(coarse, device=dev).repeat_interleave(p, 0)[:ny]
+    fuel = fuel.repeat_interleave(p, 1)[:, :nx].contiguous()
+    ign = [point_ignition((I + 0.5) * dx_atm, (J + 0.5) * dx_atm, radius=10.0)
+           for I, J in ignition_cells]
+    return Workload(name or f"large-landscape-{nx}x{ny}", nxa, nya, sr, sr, dx_atm, dx_atm,
+                    classes, fuel, dzdx, dzdy, u, v, ign, dt, steps)
+
+
 def ensemble_sizes(n_members=64, seed=BASE_SEED, lo=26, hi=205):
     """Atmos sizes per member for the batched ensemble: fire meshes uniform in
     260^2..2050^2 (multiples of the refinement 10)."""

@@ -73,3 +73,40 @@ def crop_step(w, psi, tign, frac, t, I0, J0, dt, r=1):
     cy = slice(r * w.sry, (r + 1) * w.sry)
     cx = slice(r * w.srx, (r + 1) * w.srx)
     return sub, hs[r, r], hl[r, r], (cy, cx), (ys, xs)
+
+
+def check_step_on_cell(prec, sub, cy, cx, psi0, t0, psi1, tign1, frac1, hs, hl, hs_o, hl_o,
+                       Hs_max, Hq_max, dt):
+    """One GPU step against the oracle's crop step (crop_step) on one
+    atmospheric cell: psi0 the crop's nodes before the step (the scale of
+    the FP64 psi bound), psi1, tign1, frac1 the cell's nodes after it, hs / hl
+    the GPU's heat of the cell.  FP64 within 1e-10;
+    FP32 within the bounds of one step's rounding (psi 2e-6 relative, a
+    crossing only where psi^{n+1} is within that of 0, t_i 1e-2 s, F 1e-4,
+    heat the F bound times the largest heat factor / dt).  Returns whether
+    the oracle has a burning node in the cell."""
+    po, fo, to = sub.psi[cy, cx], sub.frac[cy, cx], sub.tign[cy, cx]
+    if prec == "fp64":
+        scale = max(np.abs(psi0).max(), 1.0)
+        assert np.abs(psi1 - po).max() <= 1e-10 * scale
+        assert np.abs(frac1 - fo).max() <= 1e-10
+        assert np.array_equal(np.isfinite(tign1), np.isfinite(to))
+        f = np.isfinite(to)
+        assert np.abs(tign1[f] - to[f]).max(initial=0) <= 1e-10 * max(1.0, t0)
+        assert abs(hs - hs_o) <= 1e-10 * max(abs(hs_o), 1.0)
+        assert abs(hl - hl_o) <= 1e-10 * max(abs(hl_o), 1.0)
+    else:
+        # FP32 rounding of psi (relative 6e-8), of the spread rate
+        # (fast pow/exp, ~1e-6) over one step
+        tol_psi = 2e-6 * (1.0 + np.abs(po))
+        assert np.all(np.abs(psi1 - po) <= tol_psi)
+        # crossings may differ only where psi^{n+1} is within rounding of 0
+        diff = np.isfinite(tign1) != np.isfinite(to)
+        assert np.all(np.abs(po[diff]) <= tol_psi[diff])
+        f = np.isfinite(tign1) & np.isfinite(to)
+        assert np.abs(tign1[f] - to[f]).max(initial=0) <= 1e-2
+        assert np.abs(frac1 - fo).max() <= 1e-4
+        # heat: per-node F error bound times the largest heat factor / dt
+        assert abs(hs - hs_o) <= 1e-4 * Hs_max / dt
+        assert abs(hl - hl_o) <= 1e-4 * Hq_max / dt
+    return bool((po <= 0).any())

@@ -68,3 +68,13 @@ def test_large_refinement_and_bad_arguments(lib):
         pkg.fire_default_kernel("fp32", 0, 10, 10, 10, SMS)
     with pytest.raises(pkg.FireError):
         pkg.fire_default_kernel(7, 10, 10, 10, 10, SMS)
+
+
+def test_32bit_offset_limit(lib):
+    """The warp kernels' 32-bit offsets take meshes of up to 2^31 - 1 nodes:
+    46340^2 = 2,147,395,600 nodes still gets the warp kernel in FP32, 46400 x
+    46340 = 2,150,176,000 the marching strips (64-bit offsets)."""
+    assert 46340 * 46340 <= 2**31 - 1 < 46400 * 46340
+    assert pkg.fire_default_kernel("fp32", 4634, 4634, 10, 10, SMS)[0] == WARP
+    assert pkg.fire_default_kernel("fp32", 4640, 4634, 10, 10, SMS)[0] == MARCH
+    assert pkg.fire_default_kernel("fp64", 4640, 4634, 10, 10, SMS)[0] == MARCH

@@ -11,8 +11,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_helpers import (as_path_precision, compare_fp64, crop_step, node_moisture, rel_inf,
-                         state_np)
+from gpu_helpers import (as_path_precision, check_step_on_cell, compare_fp64, crop_step,
+                         node_moisture, rel_inf, state_np)
 from paper_1102_1343_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -139,6 +139,68 @@ def test_fp64_anisotropic_multiplier_and_segments(pkg, tile):
     ok, e = compare_fp64(state_np(m), orc)
     assert ok, e
     assert heat_err <= 1e-10
+
+
+def max_tables_case(seed=91, steps=40):
+    """The limits of the tables: FIRE_MAX_CLASSES (64) fuel classes, every
+    one of them on the map, and FIRE_MAX_IGNITIONS (256) ignitions on 400x300
+    nodes: 160 instantaneous points, 48 delayed ones, 32 growing points and
+    16 growing line segments, many windows open at once."""
+    w = synth.random_landscape(40, 30, seed=seed, ignition="none", steps=steps)
+    rng = np.random.default_rng(seed)
+    classes = synth.random_classes(rng, n=64, chaparral_index=63)
+    fuel = synth.voronoi_fuel(rng, w.nx, w.ny, w.dx, n_classes=64, n_sites=3000)
+    Lx, Ly = w.nx * w.dx, w.ny * w.dy
+
+    def xy():
+        return float(rng.uniform(100.0, Lx - 100.0)), float(rng.uniform(100.0, Ly - 100.0))
+
+    ign = [synth.point_ignition(*xy(), radius=float(rng.uniform(5.0, 15.0)))
+           for _ in range(160)]
+    ign += [synth.point_ignition(*xy(), radius=float(rng.uniform(5.0, 15.0)),
+                                 t_start=float(rng.uniform(0.5, 15.0))) for _ in range(48)]
+    ign += [synth.point_ignition(*xy(), radius=float(rng.uniform(5.0, 15.0)),
+                                 t_start=float(rng.uniform(0.0, 10.0)),
+                                 speed=float(rng.uniform(0.5, 2.0))) for _ in range(32)]
+    for _ in range(16):
+        ax, ay = xy()
+        ign.append(synth.line_ignition(ax, ay, ax + float(rng.uniform(-60.0, 60.0)),
+                                       ay + float(rng.uniform(30.0, 60.0)), radius=8.0,
+                                       t_start=float(rng.uniform(0.0, 10.0)), speed=1.0))
+    return dataclasses.replace(w, classes=classes, fuel=fuel, ignitions=ign)
+
+
+@pytest.mark.parametrize("tile", [None, (0, 2, 2), (1, 6, 2), (2, 4, 2)])
+def test_fp64_max_classes_and_ignitions(pkg, tile):
+    """64 fuel classes and 256 ignitions (the tables' limits) through every
+    FP64 kernel, against the oracle at 1e-10."""
+    w = max_tables_case()
+    assert len(w.classes) == pkg.FIRE_MAX_CLASSES and len(w.ignitions) == pkg.FIRE_MAX_IGNITIONS
+    assert len(np.unique(w.fuel)) == 64
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    assert Qo > 0 and np.isfinite(orc.tign).sum() > 2000
+
+
+@pytest.mark.parametrize("tile", [None, (4, 4, 2), (3, 8, 2)])
+def test_fp32_max_classes_and_ignitions(pkg, tile):
+    """The same case through the FP32 warp kernels (two-column, dense and
+    four-column, each with its 64-class table in shared memory), against the
+    oracle within the FP32 bounds."""
+    w = max_tables_case()
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp32", tile=tile)
+    if tile is None:
+        assert pkg.fire_get_kernel(m.ctx)[0] in (pkg.FIRE_KERNEL_WARP, pkg.FIRE_KERNEL_TILE)
+    psi, tign, frac, _ = state_np(m)
+    both = np.isfinite(tign) & np.isfinite(orc.tign)
+    assert both.sum() > 2000
+    assert np.abs(tign[both] - orc.tign[both]).max() <= 0.1
+    A, Ao = (psi <= 0).sum(), (orc.psi <= 0).sum()
+    B, Bo = (1 - frac).sum(), (1 - orc.frac).sum()
+    assert abs(A - Ao) / Ao <= 0.005 and abs(B - Bo) / Bo <= 0.005
+    assert abs(Qg - Qo) / Qo <= 1e-4
 
 
 def drip_torch_case(seed=61, steps=120):
@@ -435,35 +497,10 @@ def test_full_size_sampled_cells(pkg, name, prec, warm, tile):
     burning_cells = 0
     for I, J in cells:
         sub, hs_o, hl_o, (cy, cx), (ys, xs) = crop_step(wp, psi0, tign0, frac0, t0, I, J, w.dt)
-        pg = psi1[ys, xs][cy, cx]
-        fg = frac1[ys, xs][cy, cx]
-        tg = tign1[ys, xs][cy, cx]
-        po, fo, to = sub.psi[cy, cx], sub.frac[cy, cx], sub.tign[cy, cx]
-        if (po <= 0).any():
-            burning_cells += 1
-        if prec == "fp64":
-            scale = max(np.abs(psi0[ys, xs]).max(), 1.0)
-            assert np.abs(pg - po).max() <= 1e-10 * scale
-            assert np.abs(fg - fo).max() <= 1e-10
-            assert np.array_equal(np.isfinite(tg), np.isfinite(to))
-            f = np.isfinite(to)
-            assert np.abs(tg[f] - to[f]).max(initial=0) <= 1e-10 * max(1.0, t0)
-            assert abs(hs[J, I] - hs_o) <= 1e-10 * max(abs(hs_o), 1.0)
-            assert abs(hl[J, I] - hl_o) <= 1e-10 * max(abs(hl_o), 1.0)
-        else:
-            # FP32 rounding of psi (relative 6e-8), of the spread rate
-            # (fast pow/exp, ~1e-6) over one step
-            tol_psi = 2e-6 * (1.0 + np.abs(po))
-            assert np.all(np.abs(pg - po) <= tol_psi)
-            # crossings may differ only where psi^{n+1} is within rounding of 0
-            diff = np.isfinite(tg) != np.isfinite(to)
-            assert np.all(np.abs(po[diff]) <= tol_psi[diff])
-            f = np.isfinite(tg) & np.isfinite(to)
-            assert np.abs(tg[f] - to[f]).max(initial=0) <= 1e-2
-            assert np.abs(fg - fo).max() <= 1e-4
-            # heat: per-node F error bound times the largest heat factor / dt
-            assert abs(hs[J, I] - hs_o) <= 1e-4 * Hs_max / w.dt
-            assert abs(hl[J, I] - hl_o) <= 1e-4 * Hq_max / w.dt
+        burning_cells += check_step_on_cell(
+            prec, sub, cy, cx, psi0[ys, xs], t0, psi1[ys, xs][cy, cx],
+            tign1[ys, xs][cy, cx], frac1[ys, xs][cy, cx], hs[J, I], hl[J, I], hs_o, hl_o,
+            Hs_max, Hq_max, w.dt)
     assert burning_cells >= 4
 
 
