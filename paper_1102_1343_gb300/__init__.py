@@ -41,6 +41,7 @@ FIRE_KERNEL_WARP4 = 3
 FIRE_KERNEL_WARP_DENSE = 4
 FIRE_MAX_CLASSES = 64
 FIRE_MAX_IGNITIONS = 256
+FIRE_MAX_MEMBERS = 1024
 
 # every entry point the header declares (checked by the ABI test)
 ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get_state",

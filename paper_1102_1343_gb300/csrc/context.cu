@@ -334,10 +334,11 @@ int default_warp_strips(fire_ctx *c) {
         return FIRE_ERR_ARG;
     int kx = kWarpMaxColumns / c->g.sr_x, ky = 160 / c->g.sr_y;
     if (kx > c->g.nx_atm) kx = c->g.nx_atm;
-    if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 0;
+    // strips of an even width; one atmospheric column at an odd refinement
+    // takes a strip of two (the kernel clips a strip at the mesh edge)
+    if ((kx * c->g.sr_x) & 1) kx = kx > 1 ? kx - 1 : 2;
     if (ky < 1) ky = 1;
     if (ky > c->g.ny_atm) ky = c->g.ny_atm;
-    if (kx < 1) return FIRE_ERR_ARG;
     return configure_kernel(c, FIRE_KERNEL_WARP, kx, ky);
 }
 

@@ -31,6 +31,24 @@ def test_header_declares_the_abi():
         assert s in syms
 
 
+def header_constants():
+    """FIRE_* names with their values: #define lines and enumerators."""
+    src = open(os.path.join(ROOT, "include", "wrffire.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {k: int(v) for k, v in re.findall(r"#define\s+(FIRE_[A-Z_0-9]+)\s+(-?\d+)", src)}
+    for body in re.findall(r"enum\s+\w+\s*\{(.*?)\}", src, flags=re.S):
+        out.update({k: int(v) for k, v in re.findall(r"(FIRE_[A-Z_0-9]+)\s*=\s*(-?\d+)", body)})
+    return out
+
+
+def test_binding_constants_match_the_header():
+    import paper_1102_1343_gb300 as pkg
+    consts = header_constants()
+    assert {"FIRE_OK", "FIRE_ERR_BOUNDS", "FIRE_KERNEL_WARP_DENSE", "FIRE_MAX_MEMBERS"} <= set(consts)
+    for k, v in consts.items():
+        assert getattr(pkg, k) == v, k
+
+
 def test_library_exports_every_declared_symbol(lib):
     import paper_1102_1343_gb300 as pkg
     for s in declared_symbols():

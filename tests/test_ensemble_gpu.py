@@ -162,6 +162,55 @@ def test_full_ensemble_members_equal_single_runs(pkg):
     pkg.fire_ensemble_destroy(ens)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_max_members_equal_single_runs(pkg, prec):
+    """FIRE_MAX_MEMBERS (1024) small members of 1x1 to 6x5 atmospheric cells
+    at refinement 10 or 5 (odd mesh widths among them) in one ensemble, 12
+    steps in two calls: the first, middle and last members, the smallest
+    and largest, and random others equal the same members run alone bit for
+    bit.  One member more is refused."""
+    import torch
+    rng = np.random.default_rng(17)
+    ws = []
+    for k in range(pkg.FIRE_MAX_MEMBERS):
+        nxa, nya = int(rng.integers(1, 7)), int(rng.integers(1, 6))
+        sr = 10 if k % 3 else 5
+        ws.append(synth.random_landscape(nxa, nya, sr=sr, seed=1000 + k, ignition="center",
+                                         steps=12))
+    ens, winds = make_ensemble(pkg, ws, prec)
+    hs = [torch.zeros((w.nya, w.nxa), dtype=torch.float64, device="cuda") for w in ws]
+    hl = [torch.zeros_like(h) for h in hs]
+    us = [u for u, _ in winds]
+    vs = [v for _, v in winds]
+    pkg.fire_ensemble_step(ens, 7, ws[0].dt, us, vs, hs, hl)
+    pkg.fire_ensemble_step(ens, 5, ws[0].dt, us, vs, hs, hl)
+    code, per = pkg.fire_ensemble_status(ens, len(ws))
+    assert code in (pkg.FIRE_OK, pkg.FIRE_ERR_BOUNDARY), per
+    size = [w.nx * w.ny for w in ws]
+    check = {0, 1, 511, 1022, 1023, int(np.argmin(size)), int(np.argmax(size))}
+    check |= {int(k) for k in rng.choice(len(ws), 9, replace=False)}
+    for m in sorted(check):
+        w = ws[m]
+        single = pkg.FireModel.from_workload(w, precision=prec)
+        v_, kx, ky = pkg.fire_get_kernel(pkg.fire_ensemble_member(ens, m))
+        pkg.fire_set_kernel(single.ctx, v_, kx, ky)
+        u, v = winds[m]
+        for _ in range(12):
+            hs1, hl1 = single.step(u, v, w.dt)
+        a = state_np(single)
+        b = member_state(pkg, ens, m, w, prec)
+        for k in range(3):
+            assert np.array_equal(a[k], b[k]), (m, k)
+        assert a[3] == b[3]
+        assert np.array_equal(hs1.cpu().numpy(), hs[m].cpu().numpy()), m
+        assert np.array_equal(hl1.cpu().numpy(), hl[m].cpu().numpy()), m
+        assert single.status() == per[m], m
+        single.close()
+    pkg.fire_ensemble_destroy(ens)
+    with pytest.raises(pkg.FireError):
+        make_ensemble(pkg, ws + ws[:1], prec)
+
+
 @pytest.mark.parametrize("moisture", [False, True])
 def test_members_match_oracle_fp64(pkg, moisture):
     ws = member_workloads()
