@@ -203,6 +203,114 @@ def test_fp32_max_classes_and_ignitions(pkg, tile):
     assert abs(Qg - Qo) / Qo <= 1e-4
 
 
+def ignition_edge_case(steps=40):
+    """Zero wind on hills and 13 fuels, 300x250 nodes, with the edge cases of
+    the ignition forms: a point of radius 0 on a node, a zero-length segment,
+    a segment partly and one wholly outside the domain, a growing point whose
+    window opens exactly at a step start (t = 4 dt), one that opens after the
+    run, two overlapping fires lit at different times, and a fire in the
+    boundary band (the boundary status on both sides)."""
+    w = synth.random_landscape(30, 25, seed=71, ignition="none", steps=steps)
+    u, v = synth.constant_wind(w.nxa, w.nya, 0.0, 0.0)
+    dx, dt = w.dx, w.dt
+    node = lambda i, j: ((i + 0.5) * dx, (j + 0.5) * dx)
+    ign = [synth.point_ignition(*node(40, 40), radius=0.0),
+           synth.line_ignition(*node(120, 60), *node(120, 60), radius=12.0),
+           synth.line_ignition(-80.0, 500.0, 60.0, 520.0, radius=9.0),
+           synth.line_ignition(-500.0, -500.0, -300.0, -450.0, radius=20.0),
+           synth.point_ignition(*node(200, 150), radius=15.0, t_start=4 * dt, speed=1.5),
+           synth.point_ignition(*node(60, 200), radius=15.0, t_start=(steps + 5) * dt,
+                                speed=1.0),
+           synth.point_ignition(*node(220, 60), radius=18.0),
+           synth.point_ignition(*node(225, 64), radius=10.0, t_start=3.0),
+           synth.point_ignition(*node(2, 120), radius=8.0)]
+    return dataclasses.replace(w, u=u, v=v, ignitions=ign)
+
+
+@pytest.mark.parametrize("tile", [None, (0, 3, 2), (1, 6, 3), (2, 4, 5)])
+def test_fp64_ignition_edge_cases(pkg, tile):
+    w = ignition_edge_case()
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+    tign = orc.tign
+    assert np.isfinite(tign[40, 40]) and tign[40, 40] == 0.0  # radius 0 on a node
+    assert tign[60, 120] == 0.0 and tign[64, 225] == 3.0  # zero-length segment, overlap
+    assert not np.isfinite(tign[200, 60])  # the window after the run never opened
+    assert np.isfinite(tign[80:90, 0:12]).any()  # the part of a segment inside the domain
+    assert np.isfinite(tign[150, 200]) and tign[150, 200] == 4 * w.dt  # opened at 4 dt
+    assert m.status() == pkg.FIRE_ERR_BOUNDARY and orc.status & oracle.STATUS_BOUNDARY
+
+
+def largest_shape(pkg, ctx, variant, ky_cap):
+    """The largest accepted (kx, ky): the widest kx, and the tallest ky at it
+    up to ky_cap (strips taller than the mesh change nothing); a shape one
+    step wider, or taller below the cap, is refused."""
+    def ok(a, b):
+        try:
+            pkg.fire_set_kernel(ctx, variant, a, b)
+            return True
+        except pkg.FireError:
+            return False
+    kx = 1
+    while ok(kx + 1, 1):
+        kx += 1
+    ky = 1
+    while ky < ky_cap and ok(kx, ky + 1):
+        ky += 1
+    assert ok(kx, ky) and not ok(kx + 1, 1)
+    assert ky == ky_cap or not ok(kx, ky + 1)
+    return kx, ky
+
+
+@pytest.mark.parametrize("prec,variant", [("fp64", "warp"), ("fp64", "march"), ("fp64", "tile"),
+                                          ("fp32", "warp4"), ("fp32", "dense")])
+def test_largest_strip_and_tile_shapes(pkg, prec, variant):
+    """Each kernel at the largest strip or tile shape fire_set_kernel accepts
+    on 500x600 nodes (warp strips of 60 x 510 rows, marching strips of 240
+    columns as tall as the mesh, the 2-D tiles and the FP32 four-column and
+    dense strips as large as their shared memory or row limit allows, strips
+    no taller than the mesh): FP64 against the oracle at
+    1e-10, FP32 bit for bit equal to the two-column warp kernel at the same
+    shape (the four-column kernel at its own widest strips against the
+    two-column kernel's widest)."""
+    w = synth.random_landscape(50, 60, seed=72, ignition="points", n_points=5,
+                               edge_margin=300.0, steps=30)
+    V = {"warp": pkg.FIRE_KERNEL_WARP, "march": pkg.FIRE_KERNEL_MARCH,
+         "tile": pkg.FIRE_KERNEL_TILE, "warp4": pkg.FIRE_KERNEL_WARP4,
+         "dense": pkg.FIRE_KERNEL_WARP_DENSE}[variant]
+    probe = pkg.FireModel.from_workload(w, precision=prec)
+    kx, ky = largest_shape(pkg, probe.ctx, V, w.nya)
+    probe.close()
+    if variant in ("warp", "dense"):
+        assert (kx, ky) == (6, 51)  # 60 columns, 510 rows (at most 512)
+    if variant == "march":
+        assert kx == 24  # 240 columns (at most 248)
+    if prec == "fp64":
+        m, orc, heat_err, Qg, Qo = run_pair(pkg, w, prec, tile=(V, kx, ky))
+        ok, e = compare_fp64(state_np(m), orc)
+        assert ok, e
+        assert heat_err <= 1e-10
+        assert m.status() == pkg.FIRE_OK
+        return
+    import torch
+    runs = []
+    for var, shape in ((V, (kx, ky)), (pkg.FIRE_KERNEL_WARP, (6, min(ky, 51)))):
+        m = pkg.FireModel.from_workload(w, precision=prec)
+        pkg.fire_set_kernel(m.ctx, var, *shape)
+        u, v = m.wind(w.u, w.v)
+        for _ in range(w.steps):
+            hs, hl = m.step(u, v, w.dt)
+        torch.cuda.synchronize()
+        runs.append(state_np(m)[:3] + (hs.cpu().numpy(), hl.cpu().numpy()))
+        assert m.status() == pkg.FIRE_OK
+        m.close()
+    assert np.isfinite(runs[0][1]).sum() > 20
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
+
 def drip_torch_case(seed=61, steps=120):
     """Two drip torches (Sect. "Ignition"): one crossing at 3.2 m/s for 20 s,
     its line burning out to 15 m at 2 m/s, one starting at 10.25 s."""
