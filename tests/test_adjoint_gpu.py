@@ -251,6 +251,38 @@ def test_misfit_only_call_advances_like_run(pkg, prec, nsteps, ckpt, grads):
     b.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_edge_cases(pkg, prec):
+    """One reverse step after 40 forward steps, against the oracle's adjoint
+    from the same state (only the nodes that cross in that step carry a
+    gradient; earlier ignition times are constants); a window with no
+    observed node (J = 0 and every gradient exactly 0); no step at all
+    (refused)."""
+    w = small_case(seed=11)
+    tobs = observations(w, 41)
+    ref = oracle.OracleFire.from_workload(w)
+    for _ in range(40):
+        ref.step(w.u, w.v, w.dt)
+    Jr, gmr, gMr, gur, gvr = ref.adjoint(w.u, w.v, w.dt, 1, tobs)
+    m = pkg.FireModel.from_workload(w, precision=prec)
+    u, v = m.wind(w.u, w.v)
+    m.run(40, u, v, w.dt)
+    J, gm, gM, gu, gv = m.adjoint(u, v, w.dt, 1, tobs)
+    tol = 1e-8 if prec == "fp64" else 2e-3
+    assert Jr > 0 and abs(J - Jr) <= (1e-10 if prec == "fp64" else 2e-3) * Jr
+    assert np.abs(gmr).max() > 0
+    for g, gr, name in ((gm, gmr, "mult"), (gM, gMr, "moist"), (gu, gur, "u"), (gv, gvr, "v")):
+        assert rel(g.cpu().numpy(), gr) <= tol, name
+    J0, *g0 = m.adjoint(u, v, w.dt, 5, np.full((w.ny, w.nx), np.nan))
+    assert J0 == 0.0
+    for g in g0:
+        assert not bool(g.any())
+    with pytest.raises(pkg.FireError) as e:
+        m.adjoint(u, v, w.dt, 0, tobs)
+    assert e.value.code == pkg.FIRE_ERR_ARG
+    m.close()
+
+
 def test_pending_ignition_is_rejected(pkg):
     w = small_case(seed=7)
     w.ignitions = w.ignitions + [synth.point_ignition(30.0, 30.0, radius=4.0, t_start=2.0)]
