@@ -376,12 +376,17 @@ def run_gpu(args, rank, world):
         clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    ad_on, counts0, _ = pkg.fire_adaptive_info(m.ctx)
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
         pkg.fire_step(m.ctx, u, v, w.dt, m.heat_s, m.heat_l)
     e1.record(stream)
     barrier()
+    # the adaptive kernel choice counts burnt nodes every 64 steps (one small
+    # kernel each, inside the timed region)
+    _, counts1, burnt_seen = pkg.fire_adaptive_info(m.ctx)
+    kernel_end = pkg.fire_get_kernel(m.ctx)
     clk = clocks.stop() if rank == 0 else {}
     ms = max_over_ranks(e0.elapsed_time(e1), dev, world)
     value = whole_job_rate(cells, args.steps, world, ms / 1000.0)
@@ -478,9 +483,13 @@ def run_gpu(args, rank, world):
                        "kernel": {"variant": KERNEL_VARIANTS[kernel[0]],
                                   "tile_atmos_cells": list(kernel[1:]),
                                   "chosen_by": "--kernel" if args.kernel else
-                                  ("fire_autotune" if args.autotune else "fire_init default")},
+                                  ("fire_autotune" if args.autotune else "fire_init default"),
+                                  "adaptive": {"on": ad_on, "burnt_fraction_seen": burnt_seen,
+                                               "counts_in_timed_region": counts1 - counts0,
+                                               "variant_at_end": KERNEL_VARIANTS[kernel_end[0]],
+                                               "tile_at_end": list(kernel_end[1:])}},
                        "parallelism": f"replicas x{world}"},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps + (counts1 - counts0),
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -535,7 +544,8 @@ def bench_burning(pkg, dev, steps):
     3 km, about 40 % of the domain burnt from the start): cell-steps/s and the
     roofline fraction of the step kernel where most warps run the
     fuel-fraction quadrature and the ignition-time path, with fire_init's
-    default kernel and then with the one the autotuner picks there."""
+    default (the adaptive choice between the two warp-strip kernels) and
+    then with the kernel the autotuner picks there."""
     import torch
     from paper_1102_1343_gb300 import synth
     w = synth.burning_fire_8200()

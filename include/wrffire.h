@@ -340,6 +340,26 @@ enum fire_kernel_variant {
 };
 int fire_set_kernel(fire_ctx *ctx, int variant, int kx, int ky);
 
+/* Adaptive choice between FIRE_KERNEL_WARP and FIRE_KERNEL_WARP_DENSE (same
+ * results bit for bit, so the choice changes no value): on from fire_init
+ * when its default is FIRE_KERNEL_WARP (FIRE_FP32); off after fire_set_kernel,
+ * fire_autotune or FIRE_FRACTION_LINEAR, and for ensemble members.  Every 64
+ * steps (and at fire_init, and after fire_set_state) a small kernel counts
+ * the nodes with psi <= 0 on the context's stream; the count is read on a
+ * later step without waiting (a host that runs ahead of the device sees it,
+ * and changes the kernel, that much later).  From a burnt fraction of 0.5 %
+ * the steps run FIRE_KERNEL_WARP_DENSE with strips of ky = min(ky, 60/sr_y)
+ * atmospheric rows; below 0.25 % the default strips come back.
+ *   fire_set_adaptive(ctx, 1) turns it on with the current warp strips as
+ *     the default shape (FIRE_ERR_ARG unless the context is FIRE_FP32 on
+ *     FIRE_KERNEL_WARP or FIRE_KERNEL_WARP_DENSE with the subcell scheme);
+ *     fire_set_adaptive(ctx, 0) turns it off and keeps the current kernel.
+ *   fire_adaptive_info reports whether it is on, how many counts were
+ *     launched so far and the last burnt fraction read (-1 before the
+ *     first); outputs nullable. */
+int fire_set_adaptive(fire_ctx *ctx, int on);
+int fire_adaptive_info(const fire_ctx *ctx, int *on, long long *counts, double *burnt_fraction);
+
 /* Fuel-fraction scheme of the context's steps:
  *   FIRE_FRACTION_SUBCELL (default)  the 4-subcell scheme of Sect. 3.3,
  *                 eqs. (approx-area), (approx-fraction);

@@ -56,7 +56,8 @@ ABI_SYMBOLS = ("fire_init", "fire_step", "fire_step_host", "fire_run", "fire_get
                "fire_adjoint", "fire_autotune", "fire_ensemble_autotune",
                "fire_default_kernel", "fire_adjoint_heat", "fire_set_moisture",
                "fire_wind_at_height", "fire_heat_insertion", "fire_set_fraction_scheme",
-               "fire_bounds_checked", "fire_bounds_selftest")
+               "fire_bounds_checked", "fire_bounds_selftest", "fire_set_adaptive",
+               "fire_adaptive_info")
 FIRE_FRACTION_SUBCELL = 0
 FIRE_FRACTION_LINEAR = 1
 
@@ -127,6 +128,9 @@ def load_library(path: str | None = None):
     L.fire_time.argtypes = [_P]
     L.fire_time.restype = C.c_double
     L.fire_set_kernel.argtypes = [_P, C.c_int, C.c_int, C.c_int]
+    L.fire_set_adaptive.argtypes = [_P, C.c_int]
+    L.fire_adaptive_info.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                     C.POINTER(C.c_double)]
     L.fire_get_kernel.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.fire_enable_timing.argtypes = [_P, C.c_int]
     L.fire_kernel_time_ms.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_long)]
@@ -348,6 +352,18 @@ def fire_default_kernel(precision, nx_atm, ny_atm, sr_x, sr_y, n_sm):
                                               int(sr_y), int(n_sm), C.byref(v), C.byref(kx),
                                               C.byref(ky)), "fire_default_kernel")
     return v.value, kx.value, ky.value
+
+
+def fire_set_adaptive(ctx, on=True) -> int:
+    return _check(load_library().fire_set_adaptive(ctx, int(bool(on))), "fire_set_adaptive")
+
+
+def fire_adaptive_info(ctx):
+    """(on, count launches so far, last burnt fraction or -1)."""
+    on, n, f = C.c_int(), C.c_longlong(), C.c_double()
+    _check(load_library().fire_adaptive_info(ctx, C.byref(on), C.byref(n), C.byref(f)),
+           "fire_adaptive_info")
+    return bool(on.value), n.value, f.value
 
 
 def fire_get_kernel(ctx):
