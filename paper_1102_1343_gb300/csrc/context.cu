@@ -404,14 +404,9 @@ int default_kernel(fire_ctx *c) {
 constexpr double kAdaptOn = 0.005, kAdaptOff = 0.0025;
 constexpr long kAdaptEvery = 64;  // steps between counts
 
-// enqueues a count of the current state's burnt nodes and its copy to the
-// host (read by adaptive_update once it has landed)
-int adaptive_enqueue(fire_ctx *c) {
-    if (!c->ad_count_dev) {
-        WF_CHECK(cudaMalloc(&c->ad_count_dev, sizeof(unsigned long long)));
-        WF_CHECK(cudaMallocHost(&c->ad_count_host, sizeof(unsigned long long)));
-        WF_CHECK(cudaEventCreateWithFlags(&c->ad_ready, cudaEventDisableTiming));
-    }
+// enqueues a count of the current state's burnt nodes into ad_count_dev
+int adaptive_count(fire_ctx *c) {
+    if (!c->ad_count_dev) WF_CHECK(cudaMalloc(&c->ad_count_dev, sizeof(unsigned long long)));
     WF_CHECK(cudaMemsetAsync(c->ad_count_dev, 0, sizeof(unsigned long long), c->stream));
     const int blocks = c->n_sm * 8;
     if (c->prec == FIRE_FP64)
@@ -421,13 +416,48 @@ int adaptive_enqueue(fire_ctx *c) {
         k_count_burnt<float><<<blocks, 256, 0, c->stream>>>(
             static_cast<const float *>(c->psi[c->cur]), c->n, c->ad_count_dev);
     WF_CHECK(cudaGetLastError());
+    c->ad_counts += 1;
+    return FIRE_OK;
+}
+
+// the kernel for a counted number of burnt nodes (with hysteresis)
+int adaptive_decide(fire_ctx *c, unsigned long long count) {
+    c->ad_fraction = (double)count / (double)c->n;
+    const bool dense = c->ad_dense ? c->ad_fraction >= kAdaptOff : c->ad_fraction >= kAdaptOn;
+    if (dense == c->ad_dense) return FIRE_OK;
+    const int r = configure_kernel(c, dense ? FIRE_KERNEL_WARP_DENSE : FIRE_KERNEL_WARP, c->ad_kx,
+                                   dense ? c->ad_dense_ky : c->ad_ky);
+    if (r == FIRE_OK) c->ad_dense = dense;
+    return r;
+}
+
+// a count and its copy to page-locked host memory, read by adaptive_update
+// once it has landed
+int adaptive_enqueue(fire_ctx *c) {
+    if (!c->ad_count_host) {
+        WF_CHECK(cudaMallocHost(&c->ad_count_host, sizeof(unsigned long long)));
+        WF_CHECK(cudaEventCreateWithFlags(&c->ad_ready, cudaEventDisableTiming));
+    }
+    int r = adaptive_count(c);
+    if (r) return r;
     WF_CHECK(cudaMemcpyAsync(c->ad_count_host, c->ad_count_dev, sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, c->stream));
     WF_CHECK(cudaEventRecord(c->ad_ready, c->stream));
     c->ad_pending = true;
     c->ad_steps = 0;
-    c->ad_counts += 1;
     return FIRE_OK;
+}
+
+// the count of the current state, waited for (fire_init, which waits anyway)
+int adaptive_count_now(fire_ctx *c) {
+    int r = adaptive_count(c);
+    if (r) return r;
+    unsigned long long count = 0;
+    WF_CHECK(cudaMemcpyAsync(&count, c->ad_count_dev, sizeof count, cudaMemcpyDeviceToHost,
+                             c->stream));
+    WF_CHECK(cudaStreamSynchronize(c->stream));
+    c->ad_steps = 0;
+    return adaptive_decide(c, count);
 }
 
 // before a step: take the last count if it has landed (no wait), switch the
@@ -439,15 +469,8 @@ int adaptive_update(fire_ctx *c) {
         const cudaError_t e = cudaEventQuery(c->ad_ready);
         if (e == cudaSuccess) {
             c->ad_pending = false;
-            c->ad_fraction = (double)*c->ad_count_host / (double)c->n;
-            const bool dense = c->ad_dense ? c->ad_fraction >= kAdaptOff
-                                           : c->ad_fraction >= kAdaptOn;
-            if (dense != c->ad_dense) {
-                int r = configure_kernel(c, dense ? FIRE_KERNEL_WARP_DENSE : FIRE_KERNEL_WARP,
-                                         c->ad_kx, dense ? c->ad_dense_ky : c->ad_ky);
-                if (r) return r;
-                c->ad_dense = dense;
-            }
+            const int r = adaptive_decide(c, *c->ad_count_host);
+            if (r) return r;
         } else if (e != cudaErrorNotReady) {
             WF_CHECK(e);
         }
@@ -809,7 +832,7 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
     }
     adaptive_setup(c);
     if (c->adaptive) {
-        r = adaptive_enqueue(c);
+        r = adaptive_count_now(c);  // the initial choice, from the state after the ignitions
         if (r) {
             release(c);
             return r;
@@ -817,11 +840,6 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
     }
     // the copies above read caller buffers: finish before returning
     WF_TRY(cudaStreamSynchronize(s));
-    r = adaptive_update(c);  // the initial choice from the count just taken
-    if (r) {
-        release(c);
-        return r;
-    }
 #undef WF_TRY
     *out = c;
     return FIRE_OK;
