@@ -660,6 +660,72 @@ def test_warp4_equals_two_column_warp_kernel(pkg, mesh):
         x.close()
 
 
+def test_fp32_warp_kernels_equal_on_anisotropic_refinement(pkg):
+    """Refinement 4 x 6 with unequal atmospheric spacing (40 x 54 m): the
+    two-column, four-column and dense warp kernels give the same bits."""
+    import torch
+    w = synth.random_landscape(31, 19, sr=5, seed=34, ignition="none", steps=80)
+    nx, ny = 31 * 4, 19 * 6
+    zx, zy = synth.hills_gradient(np.random.default_rng(4), nx, ny, 10.0, 9.0)
+    w = dataclasses.replace(w, srx=4, sry=6, dx_atm=40.0, dy_atm=54.0,
+                            fuel=synth.voronoi_fuel(np.random.default_rng(2), nx, ny, 10.0),
+                            dzdx=zx, dzdy=zy,
+                            ignitions=[synth.point_ignition(420.0, 500.0, radius=30.0),
+                                       synth.line_ignition(150.0, 200.0, 260.0, 330.0,
+                                                           radius=12.0)])
+    runs = []
+    for var, kx, ky in ((pkg.FIRE_KERNEL_WARP, 15, 5), (pkg.FIRE_KERNEL_WARP4, 30, 5),
+                        (pkg.FIRE_KERNEL_WARP_DENSE, 15, 3)):
+        m = pkg.FireModel.from_workload(w, precision="fp32")
+        pkg.fire_set_kernel(m.ctx, var, kx, ky)
+        u, v = m.wind(w.u, w.v)
+        for _ in range(w.steps):
+            hs, hl = m.step(u, v, w.dt)
+        torch.cuda.synchronize()
+        runs.append(state_np(m)[:3] + (hs.cpu().numpy(), hl.cpu().numpy()))
+        assert m.status() == pkg.FIRE_OK
+        m.close()
+    assert np.isfinite(runs[0][1]).sum() > 50
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tile", [None, (0, 2, 2), (1, 6, 3), (2, 4, 5)])
+def test_fp64_fully_burning_mesh(pkg, tile):
+    """One ignition larger than the domain: every node burns from t = 0, so
+    every cell runs the quadrature in every step and the fire sits in the
+    boundary band (the boundary status on both sides)."""
+    w = synth.random_landscape(20, 15, seed=73, ignition="none", steps=40)
+    w = dataclasses.replace(w, ignitions=[synth.point_ignition(600.0, 450.0, radius=5000.0)])
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10 and Qo > 0
+    assert (orc.tign == 0.0).all() and (orc.frac < 1.0).all()
+    assert m.status() == pkg.FIRE_ERR_BOUNDARY and orc.status & oracle.STATUS_BOUNDARY
+
+
+@pytest.mark.parametrize("tile", [None, (0, 3, 2), (2, 4, 5)])
+def test_fp64_fuel_at_and_above_extinction_moisture(pkg, tile):
+    """Classes whose fuel moisture equals, or exceeds, the moisture of
+    extinction (the reaction intensity's moisture damping is 0 there) beside
+    ordinary ones, against the oracle at 1e-10."""
+    w = synth.random_landscape(23, 17, seed=74, ignition="points", n_points=5,
+                               edge_margin=200.0, ignition_radius=30.0, steps=60)
+    classes = [dict(c) for c in w.classes]
+    for k in (0, 3, 5):
+        classes[k]["fuelmc_g"] = classes[k]["fuelmce"]
+    for k in (1, 7):
+        classes[k]["fuelmc_g"] = classes[k]["fuelmce"] + 0.05
+    w = dataclasses.replace(w, classes=classes)
+    assert any(np.isin(w.fuel, [0, 1, 3, 5, 7]).ravel())
+    m, orc, heat_err, Qg, Qo = run_pair(pkg, w, "fp64", tile=tile)
+    ok, e = compare_fp64(state_np(m), orc)
+    assert ok, e
+    assert heat_err <= 1e-10
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_multiplier_of_ones_changes_no_bit(pkg, prec):
     """A spread multiplier of ones (loaded and multiplied per node) gives the
