@@ -40,6 +40,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "fire_device.cuh"
@@ -1564,17 +1565,18 @@ int run_adjoint(fire_ctx *c, int nsteps, double dt, const void *u, const void *v
     // lam + (r & 1) n for the r-th reverse step of a run of them
     if constexpr (sizeof(T) == 4) {
         // the kernel's attributes, once per device
-        static bool rev_attr[64] = {};
-        int devid = 0;
-        ADJ_CHECK(cudaGetDevice(&devid));
-        if (devid < 0 || devid >= 64 || !rev_attr[devid]) {
+        static std::mutex rev_mu;
+        static bool rev_attr[kMaxDevices] = {};
+        std::lock_guard<std::mutex> rev_lock(rev_mu);
+        const int devid = attr_device();
+        if (devid < 0 || !rev_attr[devid]) {
             ADJ_CHECK(cudaFuncSetAttribute(k_adj_step<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)rev_smem_bytes<T>(FIRE_MAX_CLASSES)));
             // all of the unified L1 as shared memory: four tiles per SM
             ADJ_CHECK(cudaFuncSetAttribute(k_adj_step<T>,
                                            cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-            if (devid >= 0 && devid < 64) rev_attr[devid] = true;
+            if (devid >= 0) rev_attr[devid] = true;
         }
     }
     const dim3 rgrid((nx + kRevTX - 1) / kRevTX, (ny + kRevTY - 1) / kRevTY);
@@ -1707,6 +1709,7 @@ extern "C" int fire_adjoint(fire_ctx *c, int nsteps, double dt, const void *wind
     if (!c || !wind_u_dev || !wind_v_dev || !t_obs_dev || !J_host || nsteps < 1 ||
         ckpt_every < 1 || !isfinite(dt) || !(dt > 0.0))
         return FIRE_ERR_ARG;
+    wf::DeviceGuard dg(wf::ctx_device(c));
     int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
     double t;
     wf::ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);
@@ -1725,6 +1728,7 @@ extern "C" int fire_adjoint_heat(fire_ctx *c, int nsteps, double dt, const void 
     if (!c || !wind_u_dev || !wind_v_dev || !q_obs_dev || !J_host || nsteps < 1 ||
         ckpt_every < 1 || !isfinite(dt) || !(dt > 0.0))
         return FIRE_ERR_ARG;
+    wf::DeviceGuard dg(wf::ctx_device(c));
     int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
     double t;
     wf::ctx_info(c, &prec, &variant, &nx, &ny, &srx, &sry, &kx, &ky, &ncls, &cur, &t);

@@ -617,6 +617,7 @@ bool ctx_ignition_active(fire_ctx *c, double t) {
 }
 
 cudaStream_t ctx_stream(const fire_ctx *c) { return c->stream; }
+int ctx_device(const fire_ctx *c) { return c->device; }
 
 int ctx_default_march(fire_ctx *c) { return default_march(c); }
 int ctx_default_warp_strips(fire_ctx *c) { return default_warp_strips(c); }
@@ -847,6 +848,7 @@ int fire_init(fire_ctx **out, const fire_grid_desc *grid, const fire_fuel_class 
 
 int fire_step(fire_ctx *c, const void *u, const void *v, double dt, double *hs, double *hl) {
     if (!c || !u || !v || !finite_pos(dt)) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     return one_step(c, u, v, dt, hs, hl);
 }
 
@@ -865,6 +867,7 @@ static double *mapped_host(double *h) {
 int fire_step_host(fire_ctx *c, const void *u, const void *v, double dt, double *hs,
                    double *hl) {
     if (!c || !u || !v || !finite_pos(dt)) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     const size_t nu = (size_t)c->g.ny_atm * (c->g.nx_atm + 1) * c->esz;
     const size_t nv = (size_t)(c->g.ny_atm + 1) * c->g.nx_atm * c->esz;
     const size_t nh = (size_t)c->g.ny_atm * c->g.nx_atm * sizeof(double);
@@ -893,6 +896,7 @@ int fire_step_host(fire_ctx *c, const void *u, const void *v, double dt, double 
 int fire_run(fire_ctx *c, int nsteps, double dt, const void *u, const void *v, double *hs,
              double *hl) {
     if (!c || !u || !v || nsteps < 0 || !finite_pos(dt)) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     int k = 0;
     std::vector<IgnSeg> segs;
     while (k < nsteps) {
@@ -964,6 +968,7 @@ int fire_run(fire_ctx *c, int nsteps, double dt, const void *u, const void *v, d
 
 int fire_get_state(fire_ctx *c, void *psi, double *tign, void *frac, double *t_host) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     const size_t N = c->n, E = c->esz;
     if (psi) WF_CHECK(cudaMemcpyAsync(psi, c->psi[c->cur], N * E, cudaMemcpyDeviceToDevice, c->stream));
     if (tign)
@@ -975,6 +980,7 @@ int fire_get_state(fire_ctx *c, void *psi, double *tign, void *frac, double *t_h
 
 int fire_set_state(fire_ctx *c, const void *psi, const double *tign, const void *frac, double t) {
     if (!c || !psi || !tign || !frac || !isfinite(t)) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     const size_t N = c->n, E = c->esz;
     WF_CHECK(cudaMemcpyAsync(c->psi[c->cur], psi, N * E, cudaMemcpyDeviceToDevice, c->stream));
     WF_CHECK(cudaMemcpyAsync(c->tign, tign, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -990,6 +996,7 @@ int fire_set_state(fire_ctx *c, const void *psi, const double *tign, const void 
 
 int fire_set_spread_mult(fire_ctx *c, const void *mult_dev) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     const size_t N = c->n, E = c->esz;
     const bool had = c->mult != nullptr;
     if (had != (mult_dev != nullptr)) {
@@ -1014,6 +1021,7 @@ int fire_set_spread_mult(fire_ctx *c, const void *mult_dev) {
 
 int fire_set_fuel_classes(fire_ctx *c, const fire_fuel_class *classes, int n_classes) {
     if (!c || !classes || n_classes != c->ncls) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     for (int k = 0; k < n_classes; ++k)
         if (!valid_fuel_class(classes[k])) return FIRE_ERR_ARG;
     WF_CHECK(cudaMemcpyAsync(c->classes_dev, classes, sizeof(fire_fuel_class) * n_classes,
@@ -1029,6 +1037,7 @@ int fire_set_fuel_classes(fire_ctx *c, const fire_fuel_class *classes, int n_cla
 
 int fire_set_moisture(fire_ctx *c, const void *moisture_dev) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     const size_t N = c->n, E = c->esz;
     if (!moisture_dev) {
         if (!c->moist) return FIRE_OK;
@@ -1056,6 +1065,7 @@ int fire_set_moisture(fire_ctx *c, const void *moisture_dev) {
 
 int fire_status(fire_ctx *c) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     WF_CHECK(cudaStreamSynchronize(c->stream));
     int st = 0;
     WF_CHECK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1068,6 +1078,7 @@ int fire_status(fire_ctx *c) {
 
 int fire_clear_status(fire_ctx *c) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     WF_CHECK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     return FIRE_OK;
 }
@@ -1083,6 +1094,7 @@ double fire_time(const fire_ctx *c) { return c ? c->t : NAN; }
 
 int fire_set_kernel(fire_ctx *c, int variant, int kx, int ky) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     if (c->scheme == 1 && variant != FIRE_KERNEL_TILE) return FIRE_ERR_ARG;
     const int r = configure_kernel(c, variant, kx, ky);
     if (r == FIRE_OK) c->adaptive = false;  // the caller's choice stays
@@ -1091,6 +1103,7 @@ int fire_set_kernel(fire_ctx *c, int variant, int kx, int ky) {
 
 int fire_set_adaptive(fire_ctx *c, int on) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     if (!on) {
         c->adaptive = false;
         return FIRE_OK;
@@ -1119,6 +1132,7 @@ int fire_adaptive_info(const fire_ctx *c, int *on, long long *counts, double *bu
 
 int fire_set_fraction_scheme(fire_ctx *c, int scheme) {
     if (!c || (scheme != 0 && scheme != 1)) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     if (scheme == c->scheme) return FIRE_OK;
     if (scheme == 1) c->adaptive = false;  // tiles only
     int r = drop_step_graph(c);  // the captured steps carry the scheme
@@ -1161,6 +1175,7 @@ int fire_default_kernel(int precision, int nx_atm, int ny_atm, int sr_x, int sr_
 int fire_autotune(fire_ctx *c, const void *u, const void *v, double dt, int probe_steps,
                   int *variant_out, int *kx_out, int *ky_out) {
     if (!c || !u || !v || !finite_pos(dt) || probe_steps < 1) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     const size_t N = c->n, E = c->esz;
     const size_t na = (size_t)c->g.nx_atm * c->g.ny_atm;
     // scratch: psi x2, F x2, tign, heat x2, times, status
@@ -1290,12 +1305,14 @@ int fire_get_kernel(const fire_ctx *c, int *variant, int *kx, int *ky) {
 
 int fire_enable_timing(fire_ctx *c, int on) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     c->timing = on != 0;
     return FIRE_OK;
 }
 
 int fire_kernel_time_ms(fire_ctx *c, double *ms, long *launches) {
     if (!c) return FIRE_ERR_ARG;
+    DeviceGuard dg(c->device);
     double total = c->ms_done;
     for (size_t k = 0; k + 1 < c->ev.size(); k += 2) {
         WF_CHECK(cudaEventSynchronize(c->ev[k + 1]));
@@ -1314,6 +1331,7 @@ int fire_kernel_time_ms(fire_ctx *c, double *ms, long *launches) {
 
 void fire_destroy(fire_ctx *c) {
     if (!c) return;
+    DeviceGuard dg(c->device);
     cudaStreamSynchronize(c->stream);
     release(c);
 }

@@ -259,6 +259,7 @@ bool ctx_has_node_coefficients(const fire_ctx *c);
 struct fire_ensemble {
     std::vector<fire_ctx *> members;
     int n = 0;
+    int device = 0;  // the device current at fire_ensemble_create (its members')
     int prec = FIRE_FP32;
     cudaStream_t stream = nullptr;
     StepArgs *margs_dev = nullptr;
@@ -393,15 +394,16 @@ int ens_plan(fire_ensemble *e) {
         threads = kMarchThreads;
     }
     {
-        // the limit is a property of the kernel function shared by all ensembles
+        // the limit is a property of the kernel function on a device, shared by
+        // all ensembles there
         static std::mutex mu;
-        static size_t current[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        static size_t current[kMaxDevices][8] = {};
         std::lock_guard<std::mutex> lock(mu);
-        size_t &cur = current[(f64 ? 1 : 0) + (e->variant == FIRE_KERNEL_WARP ? 2 : 0) +
-                              (e->nc ? 4 : 0)];
-        if (smem > cur) {
+        const int dev = attr_device();
+        const int form = (f64 ? 1 : 0) + (e->variant == FIRE_KERNEL_WARP ? 2 : 0) + (e->nc ? 4 : 0);
+        if (dev < 0 || smem > current[dev][form]) {
             ENS_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            cur = smem;
+            if (dev >= 0) current[dev][form] = smem;
         }
     }
     int per_sm = 0, dev = 0, sms = 0;
@@ -470,6 +472,10 @@ int fire_ensemble_create(fire_ensemble **out, int n_members, const fire_member_d
     if (!e) return FIRE_ERR_OOM;
     e->n = n_members;
     e->prec = prec;
+    if (cudaGetDevice(&e->device) != cudaSuccess) {
+        delete e;
+        return FIRE_ERR_CUDA;
+    }
     e->stream = static_cast<cudaStream_t>(cuda_stream);
     int r = FIRE_OK;
     for (int m = 0; m < n_members && r == FIRE_OK; ++m) {
@@ -533,6 +539,7 @@ int fire_ensemble_step(fire_ensemble *e, int nsteps, double dt, const void *cons
         return FIRE_ERR_ARG;
     for (int m = 0; m < e->n; ++m)
         if (!wind_u_dev[m] || !wind_v_dev[m]) return FIRE_ERR_ARG;
+    DeviceGuard dg(e->device);
     int done = 0;
     while (done < nsteps) {
         // an active ignition window needs its own step (fire_step applies it)
@@ -637,6 +644,7 @@ int fire_ensemble_member(fire_ensemble *e, int member, fire_ctx **ctx) {
 
 int fire_ensemble_status(fire_ensemble *e, int *member_status) {
     if (!e) return FIRE_ERR_ARG;
+    DeviceGuard dg(e->device);
     ENS_CHECK(cudaStreamSynchronize(e->stream));
     GridBar b;
     ENS_CHECK(cudaMemcpy(&b, e->bar, sizeof b, cudaMemcpyDeviceToHost));
@@ -664,6 +672,7 @@ int fire_ensemble_clear_status(fire_ensemble *e) {
 
 int fire_ensemble_set_kernel(fire_ensemble *e, int strip_columns, int strip_rows) {
     if (!e || strip_columns < 2 || strip_rows < 1) return FIRE_ERR_ARG;
+    DeviceGuard dg(e->device);
     for (fire_ctx *c : e->members) {
         int prec, variant, nx, ny, srx, sry, kx, ky, ncls, cur;
         double t;
@@ -688,6 +697,7 @@ int fire_ensemble_autotune(fire_ensemble *e, int probe_steps, double dt,
                            int *strip_columns, int *strip_rows) {
     if (!e || probe_steps < 1 || !isfinite(dt) || !(dt > 0) || !wind_u_dev || !wind_v_dev)
         return FIRE_ERR_ARG;
+    DeviceGuard dg(e->device);
     // the probe must not cross an ignition window (it would apply it)
     std::vector<double> t0(e->n);
     for (int m = 0; m < e->n; ++m) {
@@ -791,6 +801,7 @@ int fire_ensemble_set_barrier_test(fire_ensemble *e, int skip_block, long long s
 
 void fire_ensemble_destroy(fire_ensemble *e) {
     if (!e) return;
+    DeviceGuard dg(e->device);
     cudaStreamSynchronize(e->stream);
     ens_release(e);
 }

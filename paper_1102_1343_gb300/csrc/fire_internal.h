@@ -17,6 +17,37 @@ enum { ST_BOUNDARY = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4, ST_BOUNDS = 8 };
 // per-class coefficient slots: eq. (spread-WRF-Fire) + T_f + heat factors
 enum { K_S0 = 0, K_R0, K_B, K_C, K_D, K_E, K_TF, K_HS, K_HQ, K_N };
 
+// Function attributes (the dynamic shared-memory limit of a kernel) are
+// per device: the caches that avoid setting them again are indexed by it.
+constexpr int kMaxDevices = 64;
+
+// The device of a context for the length of an entry point: switched to on
+// entry when another one is current, switched back on exit (a context's
+// stream and buffers belong to the device current at its fire_init).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess)
+            prev = cur;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
+// the device a context was created on (context.cu)
+int ctx_device(const fire_ctx *c);
+
+// the current device as an index of the attribute caches (-1: none of them)
+inline int attr_device() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+    return d;
+}
+
 constexpr int kThreadsX = 32;
 constexpr int kThreadsY = 8;
 constexpr int kThreads = kThreadsX * kThreadsY;

@@ -443,12 +443,13 @@ size_t step_smem_bytes(int kx, int ky, int srx, int sry, int ncls) {
 template <typename T>
 cudaError_t prepare_step_kernel(size_t smem_bytes) {
     static std::mutex mu;
-    static size_t current = 0;
+    static size_t current[kMaxDevices] = {};  // per device (the attribute is)
     std::lock_guard<std::mutex> lock(mu);
-    if (smem_bytes <= current) return cudaSuccess;
+    const int dev = attr_device();
+    if (dev >= 0 && smem_bytes <= current[dev]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_fire_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes);
-    if (e == cudaSuccess) current = smem_bytes;
+    if (e == cudaSuccess && dev >= 0) current[dev] = smem_bytes;
     return e;
 }
 
