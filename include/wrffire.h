@@ -42,6 +42,10 @@
  *    band, a non-finite level set or wind) are recorded in a sticky status
  *    word that fire_status reads.
  *  - Threads.  A context may be used by one host thread at a time.
+ *  - Devices.  A context (or an ensemble) lives on the device current at its
+ *    fire_init (fire_ensemble_create); every later call on it switches the
+ *    calling thread to that device for its duration and back on return, so
+ *    contexts of several GPUs may be used from one thread.
  */
 #ifndef WRFFIRE_H
 #define WRFFIRE_H
