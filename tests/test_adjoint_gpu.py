@@ -283,6 +283,34 @@ def test_adjoint_edge_cases(pkg, prec):
     m.close()
 
 
+@pytest.mark.parametrize("misfit", ["arrival", "heat"])
+def test_fp32_adjoint_does_not_depend_on_the_forward_kernel(pkg, misfit):
+    """The FP32 warp kernels (two-column, dense, four-column) give the same
+    forward bits, so the adjoint over them gives the same J and gradients bit
+    for bit (every state kept, and checkpoints every 7 steps)."""
+    w = synth.random_landscape(23, 17, seed=12, ignition="points", n_points=4,
+                               edge_margin=150.0, ignition_radius=25.0, steps=40)
+    w.mult = 1.0 + 0.05 * np.random.default_rng(13).standard_normal((w.ny, w.nx))
+    nsteps = 40
+    obs = observations(w, nsteps) if misfit == "arrival" else heat_observations(w, nsteps)
+    for ckpt in (1, 7):
+        outs = []
+        for var, kx in ((pkg.FIRE_KERNEL_WARP, 6), (pkg.FIRE_KERNEL_WARP_DENSE, 6),
+                        (pkg.FIRE_KERNEL_WARP4, 12)):
+            m = pkg.FireModel.from_workload(w, precision="fp32")
+            pkg.fire_set_kernel(m.ctx, var, kx, 2)
+            u, v = m.wind(w.u, w.v)
+            f = m.adjoint if misfit == "arrival" else m.adjoint_heat
+            J, *g = f(u, v, w.dt, nsteps, obs, ckpt_every=ckpt)
+            outs.append((J, [x.cpu().numpy() for x in g]))
+            m.close()
+        assert outs[0][0] > 0
+        for J, g in outs[1:]:
+            assert J == outs[0][0], ckpt
+            for a, b in zip(g, outs[0][1]):
+                assert np.array_equal(a, b), ckpt
+
+
 def test_pending_ignition_is_rejected(pkg):
     w = small_case(seed=7)
     w.ignitions = w.ignitions + [synth.point_ignition(30.0, 30.0, radius=4.0, t_start=2.0)]
