@@ -529,6 +529,46 @@ def test_run_graph_and_host_path_equal_steps(pkg, prec, pinned):
     assert np.array_equal(hl_a.cpu().numpy(), hl_c)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_run_follows_changed_arguments(pkg, prec):
+    """fire_run in several calls that change what its captured graph holds:
+    a new wind buffer, the same buffer with new contents, a new dt, no heat
+    outputs and then others, and a growing ignition window that opens between
+    them.  The state and the last heat grids equal a plain fire_step loop's
+    bit for bit."""
+    import torch
+    w = synth.random_landscape(30, 20, seed=6, ignition="center", steps=1)
+    # a window from t = 6 to 9 s on node (199, 116): the steps in it run one
+    # by one, the ones after it replay the graph again
+    w.ignitions = w.ignitions + [synth.point_ignition(1197.0, 699.0, radius=3.0, t_start=6.0,
+                                                      speed=1.0)]
+    a = pkg.FireModel.from_workload(w, precision=prec)
+    b = pkg.FireModel.from_workload(w, precision=prec)
+    u1, v1 = a.wind(w.u, w.v)
+    u2, v2 = a.wind(w.u * 1.3, w.v * 0.7)
+    u3, v3 = u1.clone(), v1.clone()
+    hs = torch.zeros_like(a.heat_s)
+    hl = torch.zeros_like(a.heat_l)
+    plan = [(9, u1, v1, 0.5, (a.heat_s, a.heat_l)), (10, u2, v2, 0.5, (None, None)),
+            (6, u3, v3, 0.5, (hs, hl)), (8, u3, v3, 0.25, (hs, hl))]
+    for n, u, v, dt, (h1, h2) in plan:
+        if u is u3 and dt == 0.25:
+            u3.mul_(0.9)  # new contents of the buffer the graph holds
+        for _ in range(n):
+            pkg.fire_step(a.ctx, u, v, dt, a.heat_s, a.heat_l)
+        pkg.fire_run(b.ctx, n, dt, u, v, h1, h2)
+    torch.cuda.synchronize()
+    sa, sb = state_np(a), state_np(b)
+    for k in range(3):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert sa[3] == sb[3] == 25 * 0.5 + 8 * 0.25
+    assert np.array_equal(a.heat_s.cpu().numpy(), hs.cpu().numpy())
+    assert np.array_equal(a.heat_l.cpu().numpy(), hl.cpu().numpy())
+    assert sa[1][116, 199] == 6.0  # the second fire
+    a.close()
+    b.close()
+
+
 def test_checkpoint_resume(pkg):
     """get_state / set_state: a resumed run continues with the same bits."""
     import torch
