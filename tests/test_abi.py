@@ -101,6 +101,54 @@ def test_null_context_is_rejected_by_every_entry_point(lib):
                                    C.byref(i3)) == E
 
 
+GOOD_CLASS = {"fgi": 0.5, "weight": 7.0, "savr": 1e4, "fueldepthm": 0.3, "fueldens": 500.0,
+              "fuelmce": 0.3, "se": 0.01}
+
+
+@pytest.mark.parametrize("case", ["dx0", "dxnan", "dyneg", "sr0", "nx0", "prec", "band0",
+                                  "epsneg", "epsnan", "psifarnan", "nxhuge", "ign_nan",
+                                  "ign_radius", "drip_speed", "drip_tend", "classes65",
+                                  "ign257"])
+def test_init_rejects_each_invalid_argument_without_gpu(lib, case):
+    """Every argument rule of fire_init answers FIRE_ERR_ARG before any device
+    call (so this runs without a GPU), and leaves no context."""
+    import paper_1102_1343_gb300 as pkg
+    grid = dict(nx_atm=10, ny_atm=10, sr_x=10, sr_y=10, dx_atm=60.0, dy_atm=60.0,
+                precision=pkg.FIRE_FP32, boundary_band=1, eps_visc=0.4, psi_far=0.0)
+    ign = [dict(ax=300.0, ay=300.0, bx=300.0, by=300.0, t_start=0.0, radius=10.0, speed=0.0)]
+    classes = [GOOD_CLASS]
+    bad_grid = {"dx0": ("dx_atm", 0.0), "dxnan": ("dx_atm", float("nan")),
+                "dyneg": ("dy_atm", -60.0), "sr0": ("sr_x", 0), "nx0": ("nx_atm", 0),
+                "prec": ("precision", 7), "band0": ("boundary_band", 0),
+                "epsneg": ("eps_visc", -0.1), "epsnan": ("eps_visc", float("nan")),
+                "psifarnan": ("psi_far", float("nan")), "nxhuge": ("nx_atm", 1 << 28)}
+    if case in bad_grid:
+        k, v = bad_grid[case]
+        grid[k] = v
+    elif case == "ign_nan":
+        ign[0]["ax"] = float("nan")
+    elif case == "ign_radius":
+        ign[0]["radius"] = -1.0
+    elif case == "drip_speed":  # a drip torch needs a growth speed
+        ign[0].update(vx=1.0, t_end=10.0)
+    elif case == "drip_tend":  # and an end no earlier than its start
+        ign[0].update(vx=1.0, speed=1.0, t_start=5.0, t_end=4.0)
+    elif case == "classes65":
+        classes = [GOOD_CLASS] * (pkg.FIRE_MAX_CLASSES + 1)
+    elif case == "ign257":
+        ign = ign * (pkg.FIRE_MAX_IGNITIONS + 1)
+    g = pkg.make_grid(grid["nx_atm"], grid["ny_atm"], grid["sr_x"], grid["sr_y"],
+                      grid["dx_atm"], grid["dy_atm"], grid["precision"], grid["boundary_band"],
+                      grid["eps_visc"], grid["psi_far"])
+    cls = pkg.make_classes(classes)
+    igs = pkg.make_ignitions(ign)
+    out = C.c_void_p()
+    # nonzero dummies stand for the device pointers: the checks come first
+    assert lib.fire_init(C.byref(out), C.byref(g), cls, len(classes), 1, None, None, 1, 1, igs,
+                         len(ign), None) == pkg.FIRE_ERR_ARG, case
+    assert out.value is None
+
+
 def test_absurd_mesh_is_out_of_memory_without_gpu(lib):
     """A mesh whose state fits on no device (6.9e10 nodes) is refused with
     FIRE_ERR_OOM before anything is allocated (no device needed)."""
