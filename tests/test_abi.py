@@ -149,6 +149,31 @@ def test_init_rejects_each_invalid_argument_without_gpu(lib, case):
     assert out.value is None
 
 
+def test_ensemble_create_checks_without_gpu(lib):
+    """No members, more than FIRE_MAX_MEMBERS, or members of two precisions:
+    FIRE_ERR_ARG before any device call."""
+    import paper_1102_1343_gb300 as pkg
+    cls = pkg.make_classes([GOOD_CLASS])
+
+    def descs(precs):
+        d = (pkg.fire_member_desc * max(1, len(precs)))()
+        for k, prec in enumerate(precs):
+            d[k].grid = pkg.make_grid(10, 10, 10, 10, 60.0, 60.0, prec)
+            d[k].classes = C.cast(cls, C.POINTER(pkg.fire_fuel_class))
+            d[k].n_classes = 1
+            d[k].fuel_class_dev = d[k].dzdx_dev = d[k].dzdy_dev = 1
+        return d
+    out = C.c_void_p()
+    E = pkg.FIRE_ERR_ARG
+    assert lib.fire_ensemble_create(C.byref(out), 0, descs([]), None) == E
+    n = pkg.FIRE_MAX_MEMBERS + 1
+    assert lib.fire_ensemble_create(C.byref(out), n, descs([pkg.FIRE_FP32] * n), None) == E
+    assert lib.fire_ensemble_create(C.byref(out), 2, descs([pkg.FIRE_FP32, pkg.FIRE_FP64]),
+                                    None) == E
+    assert lib.fire_ensemble_create(None, 1, descs([pkg.FIRE_FP32]), None) == E
+    assert out.value is None
+
+
 def test_absurd_mesh_is_out_of_memory_without_gpu(lib):
     """A mesh whose state fits on no device (6.9e10 nodes) is refused with
     FIRE_ERR_OOM before anything is allocated (no device needed)."""
