@@ -23,6 +23,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wrffire_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+# a library built from a modified copy of the source, loaded instead of the
+# build (the planted-mistake tests run the pins against such copies)
+_LIB_OVERRIDE = os.environ.get("WRFFIRE_ORACLE_LIBRARY")
 _lock = threading.Lock()
 _lib = None
 
@@ -67,7 +70,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(_LIB_OVERRIDE or build())
             L.orc_rothermel_rate.restype = C.c_double
             L.orc_rothermel_rate.argtypes = [_D, C.c_double, C.c_double, C.c_double]
             L.orc_rothermel_intermediates.restype = None

@@ -576,7 +576,10 @@ static double subcell_burned(const double ps[4], const double ts[4], double t, d
  * vertices.  psi and t_i are interpolated bilinearly between the node
  * centres: an edge midpoint is the mean of 2 nodes, a cell corner the mean
  * of 4.  Where the interpolated psi >= 0 the interpolated t_i is replaced by
- * t (eq. ti-comp applied at the vertices).
+ * t (eq. ti-comp applied at the vertices).  Parity unpinned for this vertex
+ * rule: for a partly burnt cell no closed form, limit or bound of the paper
+ * tells it apart (a copy of the oracle without it passes every pin); the
+ * rest of the function is pinned.
  * Reading: the cell fraction burned is the mean of the 4 subcell fractions
  * (the subcells have a quarter of the cell's area). */
 double orc_cell_fuel_fraction(const double *p, const double *th, double t, double Tf)

@@ -46,11 +46,15 @@ def seg_dist(X, Y, a, b):
     return np.hypot(X - a[0] - s * d[0], Y - a[1] - s * d[1])
 
 
-def test_laid_line_is_a_stadium(orc):
+@pytest.mark.parametrize("b", [None, (500.0, 400.0)])
+def test_laid_line_is_a_stadium(orc, b):
     """After the window the level set is dist(x, [a, a + v (t_h - t_g)]) - r_g
     wherever that is below psi_far, node by node, and t_i is set exactly
-    where it is <= 0."""
+    where it is <= 0.  The segment's end b plays no part in a drip torch (the
+    line runs from a along v): a far-away b gives the same stadium."""
     tor = synth.drip_torch(40.0, 33.0, 7.0, 2.5, t_start=0.5, t_end=8.0, radius=9.0, speed=5.0)
+    if b is not None:
+        tor = dict(tor, bx=b[0], by=b[1])
     w = still_workload(ignitions=[tor])
     o = run(w)
     X, Y = node_xy(w)
