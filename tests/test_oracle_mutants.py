@@ -21,7 +21,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(ROOT, "oracle", "wrffire_oracle.c")
 PINS = ["tests/test_oracle_levelset.py", "tests/test_oracle_fuel.py",
         "tests/test_oracle_driptorch.py", "tests/test_oracle_spread.py",
-        "tests/test_oracle_fraction_linear.py"]
+        "tests/test_oracle_fraction_linear.py", "tests/test_oracle_coupling.py"]
 
 # name: (function the slip is planted in, correct text, planted text)
 MUTANTS = {
@@ -85,6 +85,35 @@ MUTANTS = {
         "double Ue = Up;"),
     "slope term linear": (
         "double orc_spread_rate(", "co[CO_D] * tp * tp;", "co[CO_D] * tp;"),
+    # the fuel-fraction scheme exact for linear data (the Discussion)
+    "linear scheme: divided difference sign": (
+        "static double dd1_exp(", "return exp(b) * (expm1(d) / d);",
+        "return exp(b) * (expm1(-d) / d);"),
+    "linear scheme: fireline value not 0": (
+        "static double tri_burn(", "pd[m] = 0.0;   /* on the fireline t_i = t */",
+        "pd[m] = ds[k];"),
+    "linear scheme: triangle clipped to the unburnt side": (
+        "static double tri_burn(", "if (ps[k] <= 0.0) { px[m] = x[k];",
+        "if (ps[k] >= 0.0) { px[m] = x[k];"),
+    "linear scheme: extension sign": (
+        "double orc_cell_fuel_fraction_linear(", "dn[k] = p[k] < 0.0 ? t - th[k] : -lambda * p[k];",
+        "dn[k] = p[k] < 0.0 ? t - th[k] : lambda * p[k];"),
+    # the wind at the fire height and the heat insertion (Sect. Coupling)
+    "wind linear in z, not ln z": (
+        "void orc_wind_at_height(", "val = ul + (uk - ul) * (x - xl) / (xk - xl);",
+        "val = ul + (uk - ul) * (exp(x) - exp(xl)) / (exp(xk) - exp(xl));"),
+    "wind nonzero at the roughness height": (
+        "void orc_wind_at_height(", "double xl = log(r), ul = 0.0;",
+        "double xl = log(r), ul = u3d[p];"),
+    "heat decay with the wrong sign": (
+        "void orc_heat_insertion(", "double S = (exp(-za / zext) - exp(-zb / zext)) / (zb - za);",
+        "double S = (exp(za / zext) - exp(zb / zext)) / (zb - za);"),
+    "heat source not divided by the density": (
+        "void orc_heat_insertion(", "rth[(long)k * n + p] += mu[p] * hs[p] / (cp * r) * S;",
+        "rth[(long)k * n + p] += mu[p] * hs[p] / cp * S;"),
+    "latent source with the sensible flux": (
+        "void orc_heat_insertion(", "rqv[(long)k * n + p] += mu[p] * hl[p] / (L * r) * S;",
+        "rqv[(long)k * n + p] += mu[p] * hs[p] / (L * r) * S;"),
     "drip torch laid from b": (
         "static void apply_segment(", "seg[IG_BX] = g[IG_AX] + g[IG_VX] * (tt - g[IG_TG]);",
         "seg[IG_BX] = g[IG_BX] + g[IG_VX] * (tt - g[IG_TG]);"),
