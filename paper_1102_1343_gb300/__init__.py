@@ -13,7 +13,6 @@ the import of the native handle raises.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 
 import numpy as np

@@ -1,7 +1,6 @@
 """GPU adjoint of the arrival-time misfit (fire_adjoint, FireAdjointFn)
 against the oracle's reference adjoint and against central finite
 differences of the GPU forward, FP64 and FP32."""
-import math
 
 import numpy as np
 import pytest

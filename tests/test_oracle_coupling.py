@@ -9,7 +9,6 @@ import os
 import numpy as np
 import pytest
 
-import oracle
 from paper_1102_1343_gb300 import synth
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))

@@ -1,7 +1,6 @@
 """The oracle's OpenMP build: the per-node loops of a step run over rows in
 parallel, and the state and heat grids must be bitwise the same as with one
 thread (each value is computed alone, in the same order of operations)."""
-import os
 
 import numpy as np
 import pytest
