@@ -146,13 +146,14 @@ def run_whole(w):
 
 
 @pytest.mark.parametrize("px,py,boundary,poison", [(1, 2, False, False), (2, 1, True, False),
-                                                   (2, 2, False, False), (2, 2, True, True)])
+                                                   (2, 2, False, False), (2, 2, True, True),
+                                                   (3, 3, True, True)])
 def test_split_run_is_bitwise_the_whole_run(orc, px, py, boundary, poison):
-    """Refinement 8: patches of 1x2, 2x1 (with fire at the domain edge) and
-    2x2 ranks give the whole run's psi, t_i, F, every step's heat grids and
-    status, bit for bit; also when every halo node deeper than the 3
-    refreshed ones holds random values before each step (the step's reach
-    is 3 nodes)."""
+    """Refinement 8: patches of 1x2, 2x1 (with fire at the domain edge), 2x2
+    and 3x3 ranks (an interior patch exchanging with all eight neighbours)
+    give the whole run's psi, t_i, F, every step's heat grids and status,
+    bit for bit; also when every halo node deeper than the 3 refreshed ones
+    holds random values before each step (the step's reach is 3 nodes)."""
     w, psi, tign, frac, hs, hl, st = run_split(px, py, 8, boundary, poison=poison)
     o, hs_o, hl_o, st_o = run_whole(w)
     assert np.array_equal(psi, o.psi)
