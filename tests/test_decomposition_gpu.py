@@ -6,7 +6,8 @@ copies issued by the host between the steps; no kernel waits on another).
 With a power-of-two refinement (8) the assembled patches equal the whole-mesh
 run of the same kernel bit for bit: psi, t_i, F and every step's two heat
 grids, in FP64 and FP32, also when every halo node deeper than the refreshed
-ones holds random values before each step.  The ranks of a multi-GPU run
+ones holds random values before each step (also on a 3x3 split, whose
+interior patch takes its halo from all eight neighbours).  The ranks of a multi-GPU run
 would do the same copies over NVLink or NCCL; this test covers the patch
 arithmetic with the real kernels, tests/test_decomposition.py the exchange
 between processes."""
@@ -61,17 +62,18 @@ def model(pkg, w, prec, psi_far, sl=None, x0=0.0, y0=0.0, nxa=None, nya=None):
     return m
 
 
+@pytest.mark.parametrize("split", [(2, 2), (3, 3)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_patches_on_one_gpu_equal_the_whole_run(pkg, prec):
+def test_patches_on_one_gpu_equal_the_whole_run(pkg, prec, split):
     import torch
     w = case()
     psi_far = float(np.hypot(w.nx * w.dx, w.ny * w.dy))
     whole = model(pkg, w, prec, psi_far)
     uw, vw = whole.wind(w.u, w.v)
-    part = decomp.Partition(w.nxa, w.nya, w.srx, w.sry, 2, 2)
+    part = decomp.Partition(w.nxa, w.nya, w.srx, w.sry, *split)
     pats, models, winds, stale = [], [], [], []
     rng = np.random.default_rng(7)
-    for r in range(4):
+    for r in range(part.size):
         p = part.patch(r)
         ey, ex = part.ext_nodes(p)
         x0, y0 = part.origin(p, w.dx_atm, w.dy_atm)
