@@ -7,7 +7,8 @@ With a power-of-two refinement (8) the assembled patches equal the whole-mesh
 run of the same kernel bit for bit: psi, t_i, F and every step's two heat
 grids, in FP64 and FP32, also when every halo node deeper than the refreshed
 ones holds random values before each step (also on a 3x3 split, whose
-interior patch takes its halo from all eight neighbours).  The ranks of a multi-GPU run
+interior patch takes its halo from all eight neighbours), with the 2-D tile,
+the warp-strip and the marching-strip kernels.  The ranks of a multi-GPU run
 would do the same copies over NVLink or NCCL; this test covers the patch
 arithmetic with the real kernels, tests/test_decomposition.py the exchange
 between processes."""
@@ -18,7 +19,9 @@ from paper_1102_1343_gb300 import decomp, synth
 
 pytestmark = pytest.mark.gpu
 
-TILE = (0, 2, 2)  # FIRE_KERNEL_TILE, 2x2 atmospheric cells: valid on every patch
+# kernels valid on every patch: 2-D tiles of 2x2 atmospheric cells, warp
+# strips of 4x2 cells (32 columns), marching strips of 4x2 cells
+KERNELS = {"tile": (0, 2, 2), "warp": (2, 4, 2), "march": (1, 4, 2)}
 
 
 @pytest.fixture(scope="module")
@@ -51,24 +54,25 @@ def _shift(g, x0, y0):
     return g
 
 
-def model(pkg, w, prec, psi_far, sl=None, x0=0.0, y0=0.0, nxa=None, nya=None):
+def model(pkg, w, prec, psi_far, kernel, sl=None, x0=0.0, y0=0.0, nxa=None, nya=None):
     ey, ex = sl if sl is not None else (slice(None), slice(None))
     m = pkg.FireModel(nxa or w.nxa, nya or w.nya, (w.srx, w.sry), w.dx_atm, w.classes,
                       w.fuel[ey, ex], w.dzdx[ey, ex], w.dzdy[ey, ex],
                       [_shift(g, x0, y0) for g in w.ignitions], precision=prec,
                       mult=w.mult[ey, ex], eps=w.eps, band=w.band, psi_far=psi_far,
                       dy_atm=w.dy_atm)
-    pkg.fire_set_kernel(m.ctx, *TILE)
+    pkg.fire_set_kernel(m.ctx, *KERNELS[kernel])
     return m
 
 
+@pytest.mark.parametrize("kernel", sorted(KERNELS))
 @pytest.mark.parametrize("split", [(2, 2), (3, 3)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_patches_on_one_gpu_equal_the_whole_run(pkg, prec, split):
+def test_patches_on_one_gpu_equal_the_whole_run(pkg, prec, split, kernel):
     import torch
     w = case()
     psi_far = float(np.hypot(w.nx * w.dx, w.ny * w.dy))
-    whole = model(pkg, w, prec, psi_far)
+    whole = model(pkg, w, prec, psi_far, kernel)
     uw, vw = whole.wind(w.u, w.v)
     part = decomp.Partition(w.nxa, w.nya, w.srx, w.sry, *split)
     pats, models, winds, stale = [], [], [], []
@@ -77,7 +81,8 @@ def test_patches_on_one_gpu_equal_the_whole_run(pkg, prec, split):
         p = part.patch(r)
         ey, ex = part.ext_nodes(p)
         x0, y0 = part.origin(p, w.dx_atm, w.dy_atm)
-        m = model(pkg, w, prec, psi_far, (ey, ex), x0, y0, p.E_I1 - p.E_I0, p.E_J1 - p.E_J0)
+        m = model(pkg, w, prec, psi_far, kernel, (ey, ex), x0, y0, p.E_I1 - p.E_I0,
+                  p.E_J1 - p.E_J0)
         ue, ve = part.ext_wind(p, w.u, w.v)
         pats.append(p)
         models.append(m)
