@@ -1,13 +1,18 @@
-"""Planted mistakes in the oracle's forward step: each copy of
-oracle/wrffire_oracle.c below carries one plausible slip (a dropped or
-flipped term, a transposed operand, an index or weight off) in the level-set
-step, the ghosts, the wind interpolation, the ignition, the fuel-fraction
-quadrature or the heat average, and must fail at least one of the oracle's
-independent pins: the closed forms, invariants and brute-force integrals of
-test_oracle_levelset.py, test_oracle_fuel.py, test_oracle_driptorch.py,
-test_oracle_spread.py and test_oracle_fraction_linear.py (not the adjoint
-tests, which compare the oracle with itself).  The pins run in a child
-process on the mutant library (WRFFIRE_ORACLE_LIBRARY)."""
+"""Planted mistakes in the oracle: each copy of oracle/wrffire_oracle.c
+below carries one plausible slip (a dropped or flipped term, a transposed
+operand, an index or weight off).
+- In the forward step (the level set, the ghosts, the wind interpolation, the
+  ignition, the fuel-fraction quadratures, the heat average, the coupling
+  steps) it must fail one of the oracle's independent pins: the closed forms,
+  invariants and brute-force integrals of test_oracle_levelset.py,
+  test_oracle_fuel.py, test_oracle_driptorch.py, test_oracle_spread.py,
+  test_oracle_fraction_linear.py and test_oracle_coupling.py (not the
+  adjoint tests, which compare the oracle with itself).
+- In the reference adjoint's reverse sweep it must fail one of the pins of
+  test_oracle_adjoint.py: central differences of the (correct) forward step,
+  the dot-product identity of one linearised step and the closed forms.
+The pins run in a child process on the mutant library
+(WRFFIRE_ORACLE_LIBRARY)."""
 import concurrent.futures as cf
 import os
 import shutil
@@ -22,6 +27,9 @@ SRC = os.path.join(ROOT, "oracle", "wrffire_oracle.c")
 PINS = ["tests/test_oracle_levelset.py", "tests/test_oracle_fuel.py",
         "tests/test_oracle_driptorch.py", "tests/test_oracle_spread.py",
         "tests/test_oracle_fraction_linear.py", "tests/test_oracle_coupling.py"]
+# the reverse sweep's pins: central differences of the forward step, the
+# dot-product identity of one linearised step, the closed forms
+ADJOINT_PINS = ["tests/test_oracle_adjoint.py"]
 
 # name: (function the slip is planted in, correct text, planted text)
 MUTANTS = {
@@ -114,6 +122,39 @@ MUTANTS = {
     "latent source with the sensible flux": (
         "void orc_heat_insertion(", "rqv[(long)k * n + p] += mu[p] * hl[p] / (L * r) * S;",
         "rqv[(long)k * n + p] += mu[p] * hs[p] / (L * r) * S;"),
+    # the reference adjoint (its pins: the derivative of the forward step)
+    "adjoint: second Heun stage weight": (
+        "static void adjoint_step(", "v[k] = 0.5 * dt * mu[k] + dt * ls[k];",
+        "v[k] = 0.5 * dt * mu[k] + 0.5 * dt * ls[k];"),
+    "adjoint: stage cotangent dropped": (
+        "static void adjoint_step(", "lam[k] = mu[k] + ls[k] + r1[k];", "lam[k] = mu[k] + r1[k];"),
+    "adjoint: extrapolated ghost's weight": (
+        "static void ghost_partials(", "*d0 = 2.0;", "*d0 = 1.0;"),
+    "adjoint: left and right transposed": (
+        "static void rhs_vjp(", "int ii[5] = {i, i - 1, i + 1, i, i};",
+        "int ii[5] = {i, i + 1, i - 1, i, i};"),
+    "adjoint: normal not projected": (
+        "static void rhs_partials(", "dU_dcx = (un - U * nxv) / cn;", "dU_dcx = un / cn;"),
+    "adjoint: Laplacian's y weight dropped": (
+        "static void rhs_partials(", "double dL[5] = {-2.0 / dx - 2.0 / dy,",
+        "double dL[5] = {-2.0 / dx,"),
+    "adjoint: upwind difference sign": (
+        "static void rhs_partials(", "if (sx == -1) { dG[0] += wx / dx; dG[1] -= wx / dx; }",
+        "if (sx == -1) { dG[0] -= wx / dx; dG[1] += wx / dx; }"),
+    "adjoint: v gradient along x": (
+        "static void rhs_partials(", "o->dvn = Fs * m * dSt_dU * nyv;",
+        "o->dvn = Fs * m * dSt_dU * nxv;"),
+    "adjoint: multiplier partial scaled by m": (
+        "static void rhs_partials(", "o->dm = Fs * St;", "o->dm = Fs * St * m;"),
+    "adjoint: crossing seed with psi^{n+1}": (
+        "static void adjoint_sweep(", "mu[k] += r * dt * a / ((a - b) * (a - b));",
+        "mu[k] += r * dt * b / ((a - b) * (a - b));"),
+    "adjoint: crossing seed sign on psi^n": (
+        "static void adjoint_sweep(", "lam[k] += r * (-dt * b / ((a - b) * (a - b)));",
+        "lam[k] += r * (dt * b / ((a - b) * (a - b)));"),
+    "adjoint: wind gather weights swapped": (
+        "static void wind_gather(", "g_u[j0 * W + i1] += gun[k] * (1.0 - wy) * wx;",
+        "g_u[j0 * W + i1] += gun[k] * wy * wx;"),
     "drip torch laid from b": (
         "static void apply_segment(", "seg[IG_BX] = g[IG_AX] + g[IG_VX] * (tt - g[IG_TG]);",
         "seg[IG_BX] = g[IG_BX] + g[IG_VX] * (tt - g[IG_TG]);"),
@@ -135,10 +176,11 @@ def build_mutant(d, name):
     return str(so)
 
 
-def run_pins(so):
+def run_pins(job):
     """The pins on one mutant library: (exit code, end of the output)."""
+    so, pins = job
     env = dict(os.environ, WRFFIRE_ORACLE_LIBRARY=so)
-    p = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p",
+    p = subprocess.run([sys.executable, "-m", "pytest", *pins, "-x", "-q", "-p",
                         "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=900)
     return p.returncode, p.stdout[-1500:]
@@ -152,7 +194,8 @@ def results(tmp_path_factory):
     names = sorted(MUTANTS)
     libs = {n: build_mutant(root / f"m{k}", n) for k, n in enumerate(names)}
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        out = dict(zip(names, ex.map(run_pins, [libs[n] for n in names])))
+        jobs = [(libs[n], ADJOINT_PINS if n.startswith("adjoint:") else PINS) for n in names]
+        out = dict(zip(names, ex.map(run_pins, jobs)))
     return out
 
 
