@@ -155,6 +155,17 @@ MUTANTS = {
     "adjoint: wind gather weights swapped": (
         "static void wind_gather(", "g_u[j0 * W + i1] += gun[k] * (1.0 - wy) * wx;",
         "g_u[j0 * W + i1] += gun[k] * wy * wx;"),
+    # the heat-misfit adjoint's own pieces (the quadrature's partials)
+    "adjoint: area-fraction derivative sign": (
+        "static void cell_fraction_partials(",
+        "double dbeta = sabs > 0.0 ? 0.5 * (-1.0 / sabs + sp * sg / (sabs * sabs)) : 0.0;",
+        "double dbeta = sabs > 0.0 ? 0.5 * (1.0 / sabs + sp * sg / (sabs * sabs)) : 0.0;"),
+    "adjoint: decay derivative without the quarter": (
+        "static void cell_fraction_partials(", "gts[pb[k]][pa[k]] += -0.25 * (-beta * e * 0.25 / Tf);",
+        "gts[pb[k]][pa[k]] += -0.25 * (-beta * e / Tf);"),
+    "adjoint: t derivative at fixed vertices": (
+        "static void cell_fraction_partials(", "if (!tfix[b][a]) dth[q] += gts[b][a] * w[b][a][q];",
+        "dth[q] += gts[b][a] * w[b][a][q];"),
     "drip torch laid from b": (
         "static void apply_segment(", "seg[IG_BX] = g[IG_AX] + g[IG_VX] * (tt - g[IG_TG]);",
         "seg[IG_BX] = g[IG_BX] + g[IG_VX] * (tt - g[IG_TG]);"),
