@@ -616,21 +616,26 @@ def _sample_cells(w, rng, n_random, near):
                                                  ("line2000", "fp32", 200, None),
                                                  ("points8200", "fp32", 200, None),
                                                  ("points8200", "fp32", 200, (2, 6, 20)),
-                                                 ("line2000", "fp64", 60, (2, 6, 20))])
+                                                 ("line2000", "fp64", 60, (2, 6, 20)),
+                                                 ("burning8200", "fp32", 20, None)])
 def test_full_size_sampled_cells(pkg, name, prec, warm, tile):
-    """The 2000x2000 line-fire mesh (FP64 and FP32) and the 8200x8200
-    50-point mesh (FP32) in the tile shape the benchmark uses: after `warm`
-    steps, one more GPU step is compared on sampled atmospheric cells (around
-    the ignitions and at random) with the oracle run on 3x3-cell crops from the
-    same state."""
+    """The 2000x2000 line-fire mesh (FP64 and FP32), the 8200x8200 50-point
+    mesh (FP32) in the tile shape the benchmark uses, and the same mesh 42 %
+    burnt (the benchmark's burning leg, on the dense warp kernel that the
+    adaptive choice takes there): after `warm` steps, one more GPU step is
+    compared on sampled atmospheric cells (around the ignitions and at
+    random) with the oracle run on 3x3-cell crops from the same state."""
     import torch
-    w = synth.line_fire_2000() if name == "line2000" else synth.points_fire_8200()
+    w = {"line2000": synth.line_fire_2000, "points8200": synth.points_fire_8200,
+         "burning8200": synth.burning_fire_8200}[name]()
     wp = as_path_precision(w, prec)
     m = pkg.FireModel.from_workload(w, precision=prec)
     if tile:
         pkg.fire_set_kernel(m.ctx, *tile)
     u, v = m.wind(w.u, w.v)
     m.run(warm, u, v, w.dt)
+    if name == "burning8200":
+        assert pkg.fire_get_kernel(m.ctx)[0] == pkg.FIRE_KERNEL_WARP_DENSE
     psi0, tign0, frac0, t0 = state_np(m)
     hs, hl = m.step(u, v, w.dt)
     torch.cuda.synchronize()
